@@ -1,0 +1,213 @@
+/*
+ * ising.h — C ABI of the GB300 local-search library for Ising spin glasses.
+ *
+ * Method: García & Markov, "High-performance Energy Minimization in Spin-glasses
+ * with Applications to Adiabatic Quantum Computing" (arXiv:0912.3912).
+ *   - Energy with pair couplings and fields: Sec. II, Eq. 1.
+ *   - Energy with k-spin hyper-couplings: Sec. VI, Eq. 6.
+ *   - Gain of a single-spin move, random starts, passes, restarts: Sec. IV
+ *     (Fig. 3 and the text around it).
+ *   - Incremental ("efficient") gain updates after a move: Sec. IV.
+ *
+ * The library runs single-spin-flip descent to a 1-flip local minimum, with
+ * counter-based random restarts, over many replicas of many instances at once,
+ * on one GPU.  Every buffer argument is a plain pointer; nothing here depends on
+ * PyTorch.
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ *  Spins are +1/-1.  An instance has n spins, a symmetric CSR coupling graph
+ *  (J_ij = J_ji, no self loops, no repeated column in a row), optional fields h_i,
+ *  and optional hyper-edges e (>= 2 distinct members) with strengths J_e.
+ *
+ *  Energy (Eq. 1 extended by Eq. 6), each unordered pair counted once:
+ *      E(s) = - sum_{i<j, (i,j) in CSR} J_ij s_i s_j
+ *             - sum_e J_e prod_{k in e} s_k  -  sum_i h_i s_i
+ *  Local field of spin i:
+ *      f_i = h_i + sum_j J_ij s_j + sum_{e contains i} J_e prod_{k in e, k != i} s_k
+ *  Flipping spin i changes the energy by dE_i = 2 s_i f_i; the paper's gain is
+ *  -dE_i (positive gain = lower energy).  A descent flips a spin iff dE_i < 0.
+ *
+ *  Schedules.  A sweep visits every spin once.
+ *   - ISING_SCHED_COLOUR: colour classes c = 0..C-1 in ascending order; all
+ *     spins of a class decide against the same state, then flip together.  A
+ *     class is an independent set of the conflict graph (CSR edges plus every
+ *     pair inside one hyper-edge), so this equals visiting the class's spins
+ *     one after another in any order.
+ *   - ISING_SCHED_SEQUENTIAL: spins 0..n-1 in index order, each deciding on
+ *     the current state (the paper's one-move-at-a-time order).
+ *
+ *  Descent and restarts (per replica r of instance b):
+ *   descent k = 0,1,... starts from the random configuration R(b, r, k) below
+ *   and sweeps until a sweep makes no flip (converged: a 1-flip local minimum)
+ *   or max_sweeps sweeps were made (capped).  The replica runs `restarts`
+ *   descents, or stops earlier when its total sweep count reaches
+ *   sweep_budget (> 0).  Its result is the lowest-energy final state among its
+ *   converged descents, the earliest one on ties; if none converged, the final
+ *   state of its last descent.
+ *
+ *  Random starts R(b, r, k) (Sec. IV: uniform random configuration): Philox4x32-10
+ *  (Salmon, Moraes, Dror, Shaw, SC'11) with key = (low 32 bits of seeds[b],
+ *  high 32 bits of seeds[b]) and counter = (w, r, k, b).  Spin i of the start is
+ *  +1 iff bit (i mod 128) of the 128-bit output for w = i / 128 is 1, where bit t
+ *  of the output is bit (t mod 32) of output word t / 32.
+ *
+ *  Floating-point couplings (ISING_F32).  Local fields are kept in FP32 and
+ *  updated incrementally: at each visit of spin j, for every CSR neighbour i
+ *  (in j's row order) that flipped since j's previous visit, f_j += 2 J_ji s_i;
+ *  then for every hyper-edge e containing j (in ascending edge order) in which an
+ *  odd number of the other members flipped since that visit,
+ *  f_j += 2 J_e prod_{k in e, k != j} s_k (FP32 additions, round to nearest).
+ *  At descent sweeps d with d % refresh_every == 0 (and always at d == 0) the
+ *  visit instead recomputes f_j from scratch in FP64, in the same order, and
+ *  rounds it to FP32.  The flip decision is s_j * f_j < 0 in FP32.  Energies
+ *  are computed from scratch in FP64.  Integer couplings (ISING_I8) use exact
+ *  int32 fields and energies.
+ *
+ *  Layouts.  Spin outputs and inputs are int8 (+1/-1), ordered
+ *  [instance][replica][spin]; instance b's block starts at
+ *  replicas * (n_0 + ... + n_{b-1}).  Energies are [instance][replica].
+ *
+ *  Ownership.  The caller owns every buffer passed in.  ising_create copies the
+ *  instances to the device; the handle owns those copies, the colourings, the
+ *  work plans and the scratch memory it allocates.  Device-pointer arguments
+ *  must be allocated on the device that was current at ising_create.  Calls are
+ *  ordered on the stream passed in (NULL = the legacy default stream).
+ *
+ *  Errors.  Argument and instance errors are returned synchronously and leave
+ *  no partial state (a failed ising_create returns no handle).  A device-side
+ *  check that fails (for instance a wait that gave up) is latched in the
+ *  handle and returned by the next call on it.
+ */
+#ifndef ISING_GB300_H
+#define ISING_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *cudaStream_t;
+
+typedef enum {
+  ISING_OK = 0,
+  ISING_ERR_INVALID_ARG = 1,   /* NULL where a pointer is required, sizes out of range  */
+  ISING_ERR_ASYMMETRIC = 2,    /* CSR not symmetric (structure or values)               */
+  ISING_ERR_SELF_LOOP = 3,     /* CSR row i lists column i                              */
+  ISING_ERR_BAD_HYPEREDGE = 4, /* < 2 members, repeated member, member out of range     */
+  ISING_ERR_BAD_COLOURING = 5, /* colour out of range or two conflicting spins share it */
+  ISING_ERR_UNSUPPORTED = 6,   /* instance/kernel combination this build cannot run     */
+  ISING_ERR_OOM = 7,           /* device or host allocation failed                      */
+  ISING_ERR_CUDA = 8,          /* a CUDA runtime call failed                            */
+  ISING_ERR_TIMEOUT = 9,       /* a device-side bounded wait ran out                    */
+  ISING_ERR_DEVICE = 10        /* a device-side consistency check failed                */
+} ising_status;
+
+typedef enum { ISING_I8 = 0, ISING_F32 = 1 } ising_dtype;
+
+typedef enum { ISING_SCHED_COLOUR = 0, ISING_SCHED_SEQUENTIAL = 1 } ising_schedule;
+
+/* Kernel families.  AUTO lets the planner (and its tuning cache) choose. */
+typedef enum {
+  ISING_KERNEL_AUTO = 0,
+  ISING_KERNEL_TILE = 1,     /* one CTA per (instance, 32-replica group), lane = replica,
+                                persistent work queue over all tiles                    */
+  ISING_KERNEL_MSC = 2,      /* multi-spin coded tile: 32 replicas as bits of a word;
+                                needs J in {-1,+1}, h in {-1,0,+1}, no hyper-edges      */
+  ISING_KERNEL_SWEEP = 3,    /* large instances: one launch per colour class over the
+                                whole GPU, replayed from a CUDA graph                   */
+  ISING_KERNEL_DENSE_TC = 4, /* dense couplings: fields as a tcgen05 GEMM (BF16 hi+lo)  */
+  ISING_KERNEL_PLAIN = 5     /* plain comparator: one launch per instance and sweep,
+                                one thread per (spin, replica), FP32/int32 fields
+                                recomputed from the CSR, no packing, no graph           */
+} ising_kernel;
+
+/* One instance.  All pointers are HOST pointers; they are read during
+ * ising_create only.  J, h and hyper_J hold int8_t for ISING_I8 and float for
+ * ISING_F32.  Exactly one of (row_ptr, col, J) and J_dense is given.           */
+typedef struct {
+  int32_t n;                    /* number of spins, >= 1                            */
+  const int64_t *row_ptr;       /* [n+1], row_ptr[0] = 0, non-decreasing            */
+  const int32_t *col;           /* [row_ptr[n]] neighbour indices                   */
+  const void *J;                /* [row_ptr[n]] couplings, symmetric                */
+  const float *J_dense;         /* [n*n] row-major, symmetric, zero diagonal
+                                   (ISING_F32 only); NULL for CSR instances          */
+  const void *h;                /* [n] fields, or NULL for h = 0                    */
+  int32_t n_hyper;              /* number of hyper-edges, >= 0                      */
+  const int64_t *hyper_ptr;     /* [n_hyper+1] offsets into hyper_members           */
+  const int32_t *hyper_members; /* members of each hyper-edge                       */
+  const void *hyper_J;          /* [n_hyper] strengths J_e                          */
+  const int32_t *colour;        /* [n] colour class per spin, or NULL: the library
+                                   colours the conflict graph greedily in index
+                                   order (smallest colour unused by earlier
+                                   conflicting spins)                               */
+  ising_dtype dtype;
+} ising_instance_desc;
+
+typedef struct {
+  int32_t max_sweeps;    /* >= 1, cap on sweeps per descent                          */
+  int32_t restarts;      /* >= 1, descents per replica                               */
+  int32_t sweep_budget;  /* 0 = no budget; else total sweeps per replica             */
+  int32_t refresh_every; /* ISING_F32: FP64 field refresh period in descent sweeps;
+                            0 = only at the first sweep of a descent                 */
+  ising_schedule schedule;
+  ising_kernel kernel;
+} ising_search_params;
+
+/* Work counters of one ising_local_search call, summed over all replicas:
+ * flip_evals = spins visited (one gain computed and decided per visit),
+ * flips = accepted moves, minima = converged descents, descents = descents run,
+ * sweeps = sweeps run.  They depend only on the method's semantics, not on the
+ * kernel that ran it.                                                          */
+typedef struct {
+  uint64_t flip_evals, flips, minima, descents, sweeps;
+} ising_stats;
+
+typedef struct ising_handle ising_handle;
+
+/* Validate and upload n_instances instances (all of one dtype).  On success
+ * *out owns device copies; on failure *out is NULL.                           */
+ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
+                          ising_handle **out);
+
+/* Energies (Eq. 1 / Eq. 6) of caller-supplied configurations.
+ * spins_dev: device int8 +/-1, [instance][replica][spin] with `replicas`
+ * replicas per instance.  energy_dev: device double [instance][replica]
+ * (required).  energy_i32_dev: device int32 [instance][replica] or NULL;
+ * ISING_I8 handles only.                                                       */
+ising_status ising_energy(ising_handle *h, const int8_t *spins_dev, int32_t replicas,
+                          double *energy_dev, int32_t *energy_i32_dev, cudaStream_t stream);
+
+/* Descent with restarts for `replicas` replicas of every instance.
+ * seeds: HOST uint64 [n_instances].  spins_dev: device int8 out,
+ * [instance][replica][spin].  energy_dev: device double out [instance][replica].
+ * energy_i32_dev, minima_dev (device int32 [instance][replica], converged
+ * descents per replica) may be NULL.  stats (host) may be NULL; when given, the
+ * call waits for the stream to finish and fills it.                           */
+ising_status ising_local_search(ising_handle *h, const uint64_t *seeds, int32_t replicas,
+                                const ising_search_params *p, int8_t *spins_dev,
+                                double *energy_dev, int32_t *energy_i32_dev,
+                                int32_t *minima_dev, ising_stats *stats,
+                                cudaStream_t stream);
+
+/* The kernel family the planner would use for these arguments (after
+ * resolving ISING_KERNEL_AUTO), or a negative ising_status on invalid input.   */
+int32_t ising_plan_kernel(ising_handle *h, int32_t replicas, const ising_search_params *p);
+
+/* Time every eligible kernel family on this handle (on `stream`, synchronising
+ * it) and record the fastest per instance class in the tuning cache; later
+ * ISING_KERNEL_AUTO calls use it.  Writes the chosen family to *chosen.        */
+ising_status ising_autotune(ising_handle *h, int32_t replicas, const ising_search_params *p,
+                            int32_t *chosen, cudaStream_t stream);
+
+/* Free everything the handle owns.  ising_destroy(NULL) returns ISING_OK.      */
+ising_status ising_destroy(ising_handle *h);
+
+const char *ising_status_string(ising_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ISING_GB300_H */
