@@ -1,0 +1,242 @@
+"""GB300 local search for Ising spin glasses (García & Markov, arXiv:0912.3912).
+
+A thin ctypes binding over the C ABI declared in include/ising.h.  It only
+marshals arguments: every step of the search runs in the library's CUDA kernels.
+PyTorch provides device memory and streams.  Importing works without a GPU;
+any call that needs the library raises if libising_gb300.so is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libising_gb300.so")
+
+I8, F32 = 0, 1
+SCHED_COLOUR, SCHED_SEQUENTIAL = 0, 1
+KERNEL_AUTO, KERNEL_TILE, KERNEL_MSC, KERNEL_SWEEP, KERNEL_DENSE_TC, KERNEL_PLAIN = range(6)
+KERNEL_NAMES = {KERNEL_AUTO: "auto", KERNEL_TILE: "tile", KERNEL_MSC: "msc", KERNEL_SWEEP: "sweep",
+                KERNEL_DENSE_TC: "dense_tc", KERNEL_PLAIN: "plain"}
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "asymmetric", 3: "self loop", 4: "bad hyper-edge",
+          5: "bad colouring", 6: "unsupported", 7: "out of memory", 8: "CUDA error", 9: "timeout",
+          10: "device check failed"}
+
+
+class IsingError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(code, code)} (status {code})")
+        self.code = code
+
+
+class _Desc(C.Structure):
+    _fields_ = [("n", C.c_int32), ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("J", C.c_void_p),
+                ("J_dense", C.c_void_p), ("h", C.c_void_p), ("n_hyper", C.c_int32),
+                ("hyper_ptr", C.c_void_p), ("hyper_members", C.c_void_p), ("hyper_J", C.c_void_p),
+                ("colour", C.c_void_p), ("dtype", C.c_int32)]
+
+
+class _Params(C.Structure):
+    _fields_ = [("max_sweeps", C.c_int32), ("restarts", C.c_int32), ("sweep_budget", C.c_int32),
+                ("refresh_every", C.c_int32), ("schedule", C.c_int32), ("kernel", C.c_int32)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("flip_evals", C.c_uint64), ("flips", C.c_uint64), ("minima", C.c_uint64),
+                ("descents", C.c_uint64), ("sweeps", C.c_uint64)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libising_gb300.so; raise if it was not built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: run paper_0912_3912_gb300.build.build() "
+                                   "(or __graft_entry__.build()) first")
+            L = C.CDLL(LIB_PATH)
+            vp, i32 = C.c_void_p, C.c_int32
+            L.ising_create.argtypes = [vp, i32, vp]
+            L.ising_create.restype = i32
+            L.ising_energy.argtypes = [vp, vp, i32, vp, vp, vp]
+            L.ising_energy.restype = i32
+            L.ising_local_search.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]
+            L.ising_local_search.restype = i32
+            L.ising_plan_kernel.argtypes = [vp, i32, vp]
+            L.ising_plan_kernel.restype = i32
+            L.ising_autotune.argtypes = [vp, i32, vp, vp, vp]
+            L.ising_autotune.restype = i32
+            L.ising_destroy.argtypes = [vp]
+            L.ising_destroy.restype = i32
+            L.ising_status_string.argtypes = [i32]
+            L.ising_status_string.restype = C.c_char_p
+            _lib = L
+    return _lib
+
+
+EXPORTED = ("ising_create", "ising_energy", "ising_local_search", "ising_plan_kernel",
+            "ising_autotune", "ising_destroy", "ising_status_string")
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise IsingError(code, where)
+
+
+def _arr(a, dtype):
+    return None if a is None else np.ascontiguousarray(a, dtype=dtype)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+@dataclass
+class SearchResult:
+    spins: "object"        # torch int8 [instances * replicas, n] flattened per instance
+    energy: "object"       # torch float64 [instances, replicas]
+    energy_i32: "object"   # torch int32 or None
+    minima: "object"       # torch int32 [instances, replicas]
+    stats: Optional[dict]
+
+
+class Handle:
+    """Owns an ising_handle: instances uploaded once, searched many times."""
+
+    def __init__(self, instances: Sequence, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self._torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        insts = list(instances)
+        if not insts:
+            raise ValueError("no instances")
+        dts = {i.dtype for i in insts}
+        if len(dts) != 1:
+            raise ValueError("all instances of a handle share one dtype")
+        self.dtype = dts.pop()
+        self.ns = [int(i.n) for i in insts]
+        self.n_inst = len(insts)
+        keep = []
+        descs = (_Desc * len(insts))()
+        jdt = np.int8 if self.dtype == "i8" else np.float32
+        for k, inst in enumerate(insts):
+            arrs = dict(
+                row_ptr=_arr(inst.row_ptr, np.int64), col=_arr(inst.col, np.int32), J=_arr(inst.J, jdt),
+                J_dense=_arr(getattr(inst, "J_dense", None), np.float32), h=_arr(inst.h, jdt),
+                hyper_ptr=_arr(inst.hyper_ptr, np.int64), hyper_members=_arr(inst.hyper_members, np.int32),
+                hyper_J=_arr(inst.hyper_J, jdt), colour=_arr(inst.colour, np.int32))
+            keep.append(arrs)
+            nh = 0 if arrs["hyper_ptr"] is None else len(arrs["hyper_ptr"]) - 1
+            descs[k] = _Desc(int(inst.n), _ptr(arrs["row_ptr"]), _ptr(arrs["col"]), _ptr(arrs["J"]),
+                             _ptr(arrs["J_dense"]), _ptr(arrs["h"]), nh, _ptr(arrs["hyper_ptr"]),
+                             _ptr(arrs["hyper_members"]), _ptr(arrs["hyper_J"]), _ptr(arrs["colour"]),
+                             I8 if self.dtype == "i8" else F32)
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib().ising_create(C.cast(descs, C.c_void_p), len(insts), C.byref(h)), "ising_create")
+        self._h = h
+
+    # ------------------------------------------------------------------ helpers
+    def _stream(self, stream):
+        s = stream if stream is not None else self._torch.cuda.current_stream(self.device)
+        return C.c_void_p(s.cuda_stream)
+
+    @staticmethod
+    def params(max_sweeps=1000, restarts=1, sweep_budget=0, refresh_every=16,
+               schedule=SCHED_COLOUR, kernel=KERNEL_AUTO):
+        return _Params(max_sweeps, restarts, sweep_budget, refresh_every, schedule, kernel)
+
+    @property
+    def total_spins(self):
+        return sum(self.ns)
+
+    # ------------------------------------------------------------------ API
+    def energy(self, spins, replicas: int, stream=None, want_i32=False):
+        """Energies of device int8 spins [instance][replica][spin] -> float64 [instances, replicas]."""
+        torch = self._torch
+        assert spins.dtype == torch.int8 and spins.is_cuda and spins.is_contiguous()
+        assert spins.numel() == replicas * self.total_spins
+        E = torch.empty((self.n_inst, replicas), dtype=torch.float64, device=self.device)
+        E32 = torch.empty((self.n_inst, replicas), dtype=torch.int32, device=self.device) if want_i32 else None
+        _check(lib().ising_energy(self._h, C.c_void_p(spins.data_ptr()), replicas, C.c_void_p(E.data_ptr()),
+                                  None if E32 is None else C.c_void_p(E32.data_ptr()), self._stream(stream)),
+               "ising_energy")
+        return (E, E32) if want_i32 else E
+
+    def local_search(self, seeds, replicas: int, *, max_sweeps=1000, restarts=1, sweep_budget=0,
+                     refresh_every=16, schedule=SCHED_COLOUR, kernel=KERNEL_AUTO, stream=None,
+                     stats=True, want_i32=False, out=None) -> SearchResult:
+        torch = self._torch
+        seeds = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64).reshape(self.n_inst))
+        p = self.params(max_sweeps, restarts, sweep_budget, refresh_every, schedule, kernel)
+        if out is None:
+            spins = torch.empty(replicas * self.total_spins, dtype=torch.int8, device=self.device)
+            E = torch.empty((self.n_inst, replicas), dtype=torch.float64, device=self.device)
+            E32 = (torch.empty((self.n_inst, replicas), dtype=torch.int32, device=self.device)
+                   if want_i32 else None)
+            minima = torch.empty((self.n_inst, replicas), dtype=torch.int32, device=self.device)
+        else:
+            spins, E, E32, minima = out
+        st = _Stats()
+        _check(lib().ising_local_search(
+            self._h, C.c_void_p(seeds.ctypes.data), replicas, C.byref(p), C.c_void_p(spins.data_ptr()),
+            C.c_void_p(E.data_ptr()), None if E32 is None else C.c_void_p(E32.data_ptr()),
+            None if minima is None else C.c_void_p(minima.data_ptr()),
+            C.byref(st) if stats else None, self._stream(stream)), "ising_local_search")
+        sd = None
+        if stats:
+            sd = {k: int(getattr(st, k)) for k, _ in _Stats._fields_}
+        return SearchResult(spins, E, E32, minima, sd)
+
+    def plan_kernel(self, replicas: int, **kw) -> int:
+        p = self.params(**kw)
+        k = lib().ising_plan_kernel(self._h, replicas, C.byref(p))
+        if k < 0:
+            raise IsingError(-k, "ising_plan_kernel")
+        return k
+
+    def autotune(self, replicas: int, stream=None, **kw) -> int:
+        p = self.params(**kw)
+        ch = C.c_int32(0)
+        _check(lib().ising_autotune(self._h, replicas, C.byref(p), C.byref(ch), self._stream(stream)),
+               "ising_autotune")
+        return ch.value
+
+    def spins_of(self, result_spins, b: int, replicas: int):
+        """View of instance b's block as [replicas, n_b]."""
+        off = replicas * sum(self.ns[:b])
+        return result_spins[off: off + replicas * self.ns[b]].view(replicas, self.ns[b])
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().ising_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def status_string(code: int) -> str:
+    return lib().ising_status_string(code).decode()
+
+
+def create_raw(descs_ptr, n: int):
+    """ising_create on a prepared descriptor array (for tests of the argument checks)."""
+    h = C.c_void_p()
+    code = lib().ising_create(descs_ptr, n, C.byref(h))
+    return code, h

@@ -1,0 +1,596 @@
+// api.cu — the C ABI (include/ising.h): instance validation and upload,
+// colouring, planning, dispatch to the kernel families, status strings.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "internal.h"
+
+namespace isg {
+cudaError_t launch_plain(ising_handle *h, const ising_search_params *p, int32_t R, cudaStream_t s);
+cudaError_t launch_sweep(ising_handle *h, const ising_search_params *p, int32_t R, cudaStream_t s);
+cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t R, cudaStream_t s);
+bool dense_supported(const ising_handle *h, int32_t R);
+void sweep_free(ising_handle *h);
+void dense_free(ising_handle *h);
+void plain_free(ising_handle *h);
+}  // namespace isg
+
+using namespace isg;
+
+#define CUDA_OK(x)                          \
+  do {                                      \
+    if ((x) != cudaSuccess) return ISING_ERR_CUDA; \
+  } while (0)
+
+DevGraph ising_handle::graph() const {
+  DevGraph g;
+  g.inst = d_inst;
+  g.row = d_row;
+  g.col = d_col;
+  g.J = d_J;
+  g.h = d_h;
+  g.inc_ptr = d_inc_ptr;
+  g.inc_edge = d_inc_edge;
+  g.hptr = d_hptr;
+  g.hmem = d_hmem;
+  g.hJ = d_hJ;
+  g.order = d_order;
+  g.cls = d_cls;
+  g.dtype = dtype;
+  return g;
+}
+
+namespace {
+
+// ---------------------------------------------------------------- validation
+struct HostInst {
+  int32_t n = 0;
+  std::vector<int64_t> row;  // n + 1
+  std::vector<int32_t> col;
+  std::vector<float> Jf;
+  std::vector<int8_t> Ji;
+  std::vector<float> hf;
+  std::vector<int8_t> hi;
+  std::vector<int64_t> hptr;
+  std::vector<int32_t> hmem;
+  std::vector<float> hJf;
+  std::vector<int8_t> hJi;
+  std::vector<int32_t> colour;
+  int32_t ncls = 0;
+  int32_t max_deg = 0;
+};
+
+double jval(const HostInst &I, int64_t k, bool fl) { return fl ? (double)I.Jf[k] : (double)I.Ji[k]; }
+
+ising_status load_desc(const ising_instance_desc &d, ising_dtype dtype, HostInst &I) {
+  const bool fl = dtype == ISING_F32;
+  if (d.n < 1 || d.n > (1 << 30)) return ISING_ERR_INVALID_ARG;
+  if (d.dtype != dtype) return ISING_ERR_INVALID_ARG;
+  const int32_t n = d.n;
+  I.n = n;
+  if (d.J_dense) {
+    if (!fl || d.row_ptr || d.col || d.J) return ISING_ERR_INVALID_ARG;
+    if ((int64_t)n * (n - 1) > 0x7fffffffLL) return ISING_ERR_UNSUPPORTED;
+    I.row.assign(n + 1, 0);
+    for (int32_t i = 0; i < n; ++i) {
+      if (d.J_dense[(int64_t)i * n + i] != 0.0f) return ISING_ERR_SELF_LOOP;
+      for (int32_t j = 0; j < n; ++j) {
+        const float w = d.J_dense[(int64_t)i * n + j];
+        if (!std::isfinite(w)) return ISING_ERR_INVALID_ARG;
+        if (w != d.J_dense[(int64_t)j * n + i]) return ISING_ERR_ASYMMETRIC;
+        if (j == i) continue;
+        I.col.push_back(j);
+        I.Jf.push_back(w);
+      }
+      I.row[i + 1] = (int64_t)I.col.size();
+    }
+  } else {
+    if (!d.row_ptr) return ISING_ERR_INVALID_ARG;
+    if (d.row_ptr[0] != 0) return ISING_ERR_INVALID_ARG;
+    for (int32_t i = 0; i < n; ++i)
+      if (d.row_ptr[i + 1] < d.row_ptr[i]) return ISING_ERR_INVALID_ARG;
+    const int64_t nnz = d.row_ptr[n];
+    if (nnz > 0 && (!d.col || !d.J)) return ISING_ERR_INVALID_ARG;
+    if (nnz > 0x7fffffffLL) return ISING_ERR_UNSUPPORTED;
+    I.row.assign(d.row_ptr, d.row_ptr + n + 1);
+    I.col.assign(d.col, d.col + nnz);
+    if (fl) {
+      I.Jf.assign((const float *)d.J, (const float *)d.J + nnz);
+      for (float w : I.Jf)
+        if (!std::isfinite(w)) return ISING_ERR_INVALID_ARG;
+    } else {
+      I.Ji.assign((const int8_t *)d.J, (const int8_t *)d.J + nnz);
+    }
+    // structure: range, self loops, repeats; then symmetry of structure and values
+    std::vector<std::pair<int32_t, double>> sorted(nnz);
+    for (int32_t i = 0; i < n; ++i) {
+      for (int64_t k = I.row[i]; k < I.row[i + 1]; ++k) {
+        const int32_t j = I.col[k];
+        if (j < 0 || j >= n) return ISING_ERR_INVALID_ARG;
+        if (j == i) return ISING_ERR_SELF_LOOP;
+        sorted[k] = {j, jval(I, k, fl)};
+      }
+      std::sort(sorted.begin() + I.row[i], sorted.begin() + I.row[i + 1]);
+      for (int64_t k = I.row[i] + 1; k < I.row[i + 1]; ++k)
+        if (sorted[k].first == sorted[k - 1].first) return ISING_ERR_INVALID_ARG;
+    }
+    for (int32_t i = 0; i < n; ++i)
+      for (int64_t k = I.row[i]; k < I.row[i + 1]; ++k) {
+        const int32_t j = sorted[k].first;
+        auto lo = sorted.begin() + I.row[j], hi = sorted.begin() + I.row[j + 1];
+        auto it = std::lower_bound(lo, hi, std::make_pair(i, -(double)INFINITY));
+        if (it == hi || it->first != i || it->second != sorted[k].second) return ISING_ERR_ASYMMETRIC;
+      }
+  }
+  for (int32_t i = 0; i < n; ++i) I.max_deg = std::max<int32_t>(I.max_deg, (int32_t)(I.row[i + 1] - I.row[i]));
+  if (fl) {
+    I.hf.assign(n, 0.0f);
+    if (d.h) {
+      std::memcpy(I.hf.data(), d.h, n * sizeof(float));
+      for (float v : I.hf)
+        if (!std::isfinite(v)) return ISING_ERR_INVALID_ARG;
+    }
+  } else {
+    I.hi.assign(n, 0);
+    if (d.h) std::memcpy(I.hi.data(), d.h, n);
+  }
+  // hyper-edges
+  if (d.n_hyper < 0) return ISING_ERR_INVALID_ARG;
+  I.hptr.assign(1, 0);
+  if (d.n_hyper > 0) {
+    if (!d.hyper_ptr || !d.hyper_members || !d.hyper_J) return ISING_ERR_INVALID_ARG;
+    if (d.hyper_ptr[0] != 0) return ISING_ERR_BAD_HYPEREDGE;
+    std::vector<int32_t> seen(n, -1);
+    for (int32_t e = 0; e < d.n_hyper; ++e) {
+      const int64_t a = d.hyper_ptr[e], b = d.hyper_ptr[e + 1];
+      if (b - a < 2) return ISING_ERR_BAD_HYPEREDGE;
+      for (int64_t q = a; q < b; ++q) {
+        const int32_t m = d.hyper_members[q];
+        if (m < 0 || m >= n || seen[m] == e) return ISING_ERR_BAD_HYPEREDGE;
+        seen[m] = e;
+        I.hmem.push_back(m);
+      }
+      I.hptr.push_back((int64_t)I.hmem.size());
+    }
+    if (fl) {
+      I.hJf.assign((const float *)d.hyper_J, (const float *)d.hyper_J + d.n_hyper);
+      for (float v : I.hJf)
+        if (!std::isfinite(v)) return ISING_ERR_INVALID_ARG;
+    } else {
+      I.hJi.assign((const int8_t *)d.hyper_J, (const int8_t *)d.hyper_J + d.n_hyper);
+    }
+  }
+  // colouring of the conflict graph (CSR edges + pairs inside hyper-edges)
+  std::vector<std::vector<int32_t>> inc(n);
+  for (int32_t e = 0; e + 1 < (int32_t)I.hptr.size(); ++e)
+    for (int64_t q = I.hptr[e]; q < I.hptr[e + 1]; ++q) inc[I.hmem[q]].push_back(e);
+  I.colour.assign(n, -1);
+  if (d.colour) {
+    for (int32_t i = 0; i < n; ++i) {
+      if (d.colour[i] < 0 || d.colour[i] >= n) return ISING_ERR_BAD_COLOURING;
+      I.colour[i] = d.colour[i];
+    }
+    for (int32_t i = 0; i < n; ++i) {
+      for (int64_t k = I.row[i]; k < I.row[i + 1]; ++k)
+        if (I.colour[I.col[k]] == I.colour[i]) return ISING_ERR_BAD_COLOURING;
+      for (int32_t e : inc[i])
+        for (int64_t q = I.hptr[e]; q < I.hptr[e + 1]; ++q)
+          if (I.hmem[q] != i && I.colour[I.hmem[q]] == I.colour[i]) return ISING_ERR_BAD_COLOURING;
+    }
+  } else {
+    // greedy in index order: smallest colour not held by an earlier conflicting spin
+    std::vector<int32_t> stamp(n + 1, -1);
+    for (int32_t i = 0; i < n; ++i) {
+      for (int64_t k = I.row[i]; k < I.row[i + 1]; ++k) {
+        const int32_t c = I.colour[I.col[k]];
+        if (c >= 0) stamp[c] = i;
+      }
+      for (int32_t e : inc[i])
+        for (int64_t q = I.hptr[e]; q < I.hptr[e + 1]; ++q) {
+          const int32_t c = I.colour[I.hmem[q]];
+          if (c >= 0) stamp[c] = i;
+        }
+      int32_t c = 0;
+      while (stamp[c] == i) ++c;
+      I.colour[i] = c;
+    }
+  }
+  I.ncls = 0;
+  for (int32_t c : I.colour) I.ncls = std::max(I.ncls, c + 1);
+  return ISING_OK;
+}
+
+template <class T>
+cudaError_t upload(T **dst, const std::vector<T> &src) {
+  cudaError_t e = cudaMalloc((void **)dst, std::max<size_t>(1, src.size()) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  if (!src.empty()) e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+void free_handle(ising_handle *h) {
+  if (!h) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  energy_plan_free(h);
+  sweep_free(h);
+  dense_free(h);
+  plain_free(h);
+  void *ptrs[] = {h->d_inst, h->d_row, h->d_col, h->d_J, h->d_h, h->d_inc_ptr, h->d_inc_edge, h->d_hptr,
+                  h->d_hmem, h->d_hJ, h->d_order, h->d_cls, h->d_Jdense, h->d_scratch, h->d_tile_args,
+                  h->d_seeds, h->d_stats, h->d_queue, h->d_tiles};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  if (h->h_stats_pinned) cudaFreeHost(h->h_stats_pinned);
+  cudaSetDevice(cur);
+  delete h;
+}
+
+ising_status ensure_scratch(ising_handle *h, size_t bytes) {
+  if (bytes <= h->scratch_bytes) return ISING_OK;
+  if (h->d_scratch) cudaFree(h->d_scratch);
+  h->d_scratch = nullptr;
+  h->scratch_bytes = 0;
+  if (cudaMalloc(&h->d_scratch, bytes) != cudaSuccess) return ISING_ERR_OOM;
+  h->scratch_bytes = bytes;
+  return ISING_OK;
+}
+
+ising_status validate_params(const ising_search_params *p) {
+  if (!p) return ISING_ERR_INVALID_ARG;
+  if (p->max_sweeps < 1 || p->restarts < 1 || p->sweep_budget < 0 || p->refresh_every < 0)
+    return ISING_ERR_INVALID_ARG;
+  if (p->schedule != ISING_SCHED_COLOUR && p->schedule != ISING_SCHED_SEQUENTIAL) return ISING_ERR_INVALID_ARG;
+  if (p->kernel < ISING_KERNEL_AUTO || p->kernel > ISING_KERNEL_PLAIN) return ISING_ERR_INVALID_ARG;
+  return ISING_OK;
+}
+
+constexpr int kTileSmemLimit = 200 * 1024;
+
+bool tile_fits(const ising_handle *h, int mode) {
+  return tile_smem_bytes(mode, h->nmax) <= (size_t)kTileSmemLimit;
+}
+
+// Kernel family for these arguments (ISING_KERNEL_AUTO resolved), or negative status.
+int32_t resolve_kernel(ising_handle *h, int32_t R, const ising_search_params *p) {
+  int32_t k = p->kernel;
+  if (k == ISING_KERNEL_AUTO) {
+    auto it = h->tuned.find(R);
+    if (it != h->tuned.end()) return it->second;
+    if (h->dense && dense_supported(h, R) && p->schedule == ISING_SCHED_SEQUENTIAL) return ISING_KERNEL_DENSE_TC;
+    if (h->msc_ok && tile_fits(h, 2)) return ISING_KERNEL_MSC;
+    if (tile_fits(h, h->dtype == ISING_F32 ? 1 : 0)) return ISING_KERNEL_TILE;
+    return ISING_KERNEL_SWEEP;
+  }
+  switch (k) {
+    case ISING_KERNEL_TILE:
+      return tile_fits(h, h->dtype == ISING_F32 ? 1 : 0) ? k : -(int32_t)ISING_ERR_UNSUPPORTED;
+    case ISING_KERNEL_MSC:
+      return (h->msc_ok && tile_fits(h, 2)) ? k : -(int32_t)ISING_ERR_UNSUPPORTED;
+    case ISING_KERNEL_DENSE_TC:
+      return (h->dense && dense_supported(h, R) && p->schedule == ISING_SCHED_SEQUENTIAL)
+                 ? k
+                 : -(int32_t)ISING_ERR_UNSUPPORTED;
+    default:
+      return k;
+  }
+}
+
+ising_status run_tile(ising_handle *h, int mode, int32_t R, const ising_search_params *p, int8_t *spins,
+                      double *E, int32_t *E32, int32_t *minima, cudaStream_t s) {
+  // tiles: (instance, 32-replica group), largest instances first
+  const int32_t groups = (R + 31) / 32;
+  if (h->tiles_R != R) {
+    std::vector<int32_t> ord(h->n_inst);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return h->inst[a].n > h->inst[b].n; });
+    std::vector<int2> tiles;
+    tiles.reserve((size_t)h->n_inst * groups);
+    for (int32_t b : ord)
+      for (int32_t g = 0; g < groups; ++g) tiles.push_back(make_int2(b, g));
+    if (h->d_tiles) cudaFree(h->d_tiles);
+    h->d_tiles = nullptr;
+    if (upload(&h->d_tiles, tiles) != cudaSuccess) return ISING_ERR_CUDA;
+    h->n_tiles = (int32_t)tiles.size();
+    h->tiles_R = R;
+  }
+  const size_t smem = tile_smem_bytes(mode, h->nmax);
+  int per_sm = tile_max_ctas_per_sm(mode, smem);
+  if (per_sm < 1) return ISING_ERR_UNSUPPORTED;
+  const int grid = std::min<int64_t>(h->n_tiles, (int64_t)per_sm * h->sm_count);
+  const size_t f_bytes = mode == 1 ? (size_t)grid * h->nmax * 32 * sizeof(float) : 0;
+  const size_t bw_bytes = (size_t)grid * h->nmax * sizeof(uint32_t);
+  ising_status st = ensure_scratch(h, f_bytes + bw_bytes + 256);
+  if (st != ISING_OK) return st;
+  TileArgs a;
+  a.g = h->graph();
+  a.tiles = h->d_tiles;
+  a.n_tiles = h->n_tiles;
+  a.queue = h->d_queue;
+  a.R = R;
+  a.max_sweeps = p->max_sweeps;
+  a.restarts = p->restarts;
+  a.budget = p->sweep_budget;
+  a.refresh = p->refresh_every;
+  a.sequential = p->schedule == ISING_SCHED_SEQUENTIAL ? 1 : 0;
+  a.seeds = h->d_seeds;
+  a.F = mode == 1 ? (float *)h->d_scratch : nullptr;
+  a.bw = (uint32_t *)((char *)h->d_scratch + ((f_bytes + 255) / 256) * 256);
+  a.nmax = h->nmax;
+  a.spins = spins;
+  a.energy = E;
+  a.energy_i32 = E32;
+  a.minima = minima;
+  a.stats = h->d_stats;
+  CUDA_OK(cudaMemcpyAsync(h->d_tile_args, &a, sizeof(a), cudaMemcpyHostToDevice, s));
+  CUDA_OK(cudaMemsetAsync(h->d_queue, 0, sizeof(int32_t), s));
+  CUDA_OK(launch_tile(h, mode, grid, smem, s));
+  return ISING_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances, ising_handle **out) {
+  if (!out) return ISING_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!descs || n_instances < 1) return ISING_ERR_INVALID_ARG;
+  const ising_dtype dtype = descs[0].dtype;
+  if (dtype != ISING_I8 && dtype != ISING_F32) return ISING_ERR_INVALID_ARG;
+  const bool fl = dtype == ISING_F32;
+  std::vector<HostInst> hin(n_instances);
+  bool dense = true, msc = !fl, hyper = false;
+  int64_t absb = 0;
+  for (int32_t b = 0; b < n_instances; ++b) {
+    ising_status st = load_desc(descs[b], dtype, hin[b]);
+    if (st != ISING_OK) return st;
+    const HostInst &I = hin[b];
+    dense = dense && descs[b].J_dense != nullptr;
+    hyper = hyper || I.hptr.size() > 1;
+    if (!fl) {
+      for (int8_t w : I.Ji) {
+        if (w != 1 && w != -1) msc = false;
+        absb += std::abs((int)w);
+      }
+      absb /= 1;  // each pair appears twice; bound kept conservative
+      for (int8_t v : I.hi) {
+        if (v < -1 || v > 1) msc = false;
+        absb += std::abs((int)v);
+      }
+      for (int8_t v : I.hJi) absb += std::abs((int)v);
+      if (I.hptr.size() > 1 || I.max_deg > 15) msc = false;
+    }
+  }
+  ising_handle *h = new ising_handle();
+  cudaGetDevice(&h->device);
+  cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+  h->n_inst = n_instances;
+  h->dtype = dtype;
+  h->dense = dense;
+  h->msc_ok = msc;
+  h->has_hyper = hyper;
+  h->abs_energy_bound = absb;
+
+  // concatenate
+  std::vector<InstDesc> inst(n_instances);
+  std::vector<uint32_t> row;
+  std::vector<int32_t> col, order, cls;
+  std::vector<int8_t> Ji, hi, hJi;
+  std::vector<float> Jf, hf, hJf;
+  std::vector<uint32_t> inc_ptr, hptr;
+  std::vector<int32_t> inc_edge, hmem;
+  int64_t spin_off = 0, nnz_off = 0, edge_off = 0, mem_off = 0, cls_off = 0;
+  for (int32_t b = 0; b < n_instances; ++b) {
+    const HostInst &I = hin[b];
+    InstDesc &D = inst[b];
+    D.n = I.n;
+    D.ncls = I.ncls;
+    D.spin_off = spin_off;
+    D.cls_off = cls_off;
+    D.hyper_off = edge_off;
+    D.n_hyper = (int32_t)I.hptr.size() - 1;
+    D.max_deg = I.max_deg;
+    h->nmax = std::max(h->nmax, I.n);
+    for (int32_t i = 0; i < I.n; ++i) row.push_back((uint32_t)(nnz_off + I.row[i]));
+    col.insert(col.end(), I.col.begin(), I.col.end());
+    if (fl) {
+      Jf.insert(Jf.end(), I.Jf.begin(), I.Jf.end());
+      hf.insert(hf.end(), I.hf.begin(), I.hf.end());
+      hJf.insert(hJf.end(), I.hJf.begin(), I.hJf.end());
+    } else {
+      Ji.insert(Ji.end(), I.Ji.begin(), I.Ji.end());
+      hi.insert(hi.end(), I.hi.begin(), I.hi.end());
+      hJi.insert(hJi.end(), I.hJi.begin(), I.hJi.end());
+    }
+    // incidence of hyper-edges per spin, ascending edge id
+    std::vector<std::vector<int32_t>> inc(I.n);
+    for (int32_t e = 0; e < D.n_hyper; ++e)
+      for (int64_t q = I.hptr[e]; q < I.hptr[e + 1]; ++q) inc[I.hmem[q]].push_back(e);
+    for (int32_t i = 0; i < I.n; ++i) {
+      inc_ptr.push_back((uint32_t)inc_edge.size());
+      for (int32_t e : inc[i]) inc_edge.push_back((int32_t)(edge_off + e));
+    }
+    for (int32_t e = 0; e < D.n_hyper; ++e) hptr.push_back((uint32_t)(mem_off + I.hptr[e]));
+    hmem.insert(hmem.end(), I.hmem.begin(), I.hmem.end());
+    // colour classes: spins sorted by (colour, index)
+    std::vector<int32_t> cnt(I.ncls + 1, 0);
+    for (int32_t c : I.colour) cnt[c + 1]++;
+    for (int32_t c = 0; c < I.ncls; ++c) cnt[c + 1] += cnt[c];
+    cls.insert(cls.end(), cnt.begin(), cnt.end());
+    std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1), ord(I.n);
+    for (int32_t i = 0; i < I.n; ++i) ord[fill[I.colour[i]]++] = i;
+    order.insert(order.end(), ord.begin(), ord.end());
+    spin_off += I.n;
+    nnz_off += I.row[I.n];
+    edge_off += D.n_hyper;
+    mem_off += (int64_t)I.hmem.size();
+    cls_off += I.ncls + 1;
+  }
+  if (nnz_off >= 0xffffffffLL || mem_off >= 0xffffffffLL || (int64_t)inc_edge.size() >= 0xffffffffLL) {
+    delete h;
+    return ISING_ERR_UNSUPPORTED;
+  }
+  row.push_back((uint32_t)nnz_off);
+  inc_ptr.push_back((uint32_t)inc_edge.size());
+  hptr.push_back((uint32_t)mem_off);
+  h->inst = inst;
+  h->total_spins = spin_off;
+  h->total_nnz = nnz_off;
+  h->total_edges = edge_off;
+  h->total_members = mem_off;
+
+  bool ok = upload(&h->d_inst, inst) == cudaSuccess && upload(&h->d_row, row) == cudaSuccess &&
+            upload(&h->d_col, col) == cudaSuccess && upload(&h->d_inc_ptr, inc_ptr) == cudaSuccess &&
+            upload(&h->d_inc_edge, inc_edge) == cudaSuccess && upload(&h->d_hptr, hptr) == cudaSuccess &&
+            upload(&h->d_hmem, hmem) == cudaSuccess && upload(&h->d_order, order) == cudaSuccess &&
+            upload(&h->d_cls, cls) == cudaSuccess;
+  if (ok) {
+    if (fl) {
+      ok = upload((float **)&h->d_J, Jf) == cudaSuccess && upload((float **)&h->d_h, hf) == cudaSuccess &&
+           upload((float **)&h->d_hJ, hJf) == cudaSuccess;
+    } else {
+      ok = upload((int8_t **)&h->d_J, Ji) == cudaSuccess && upload((int8_t **)&h->d_h, hi) == cudaSuccess &&
+           upload((int8_t **)&h->d_hJ, hJi) == cudaSuccess;
+    }
+  }
+  if (ok && dense) {
+    std::vector<float> Jd;
+    for (int32_t b = 0; b < n_instances; ++b)
+      Jd.insert(Jd.end(), descs[b].J_dense, descs[b].J_dense + (int64_t)descs[b].n * descs[b].n);
+    ok = upload(&h->d_Jdense, Jd) == cudaSuccess;
+  }
+  ok = ok && cudaMalloc(&h->d_tile_args, sizeof(TileArgs)) == cudaSuccess &&
+       cudaMalloc(&h->d_seeds, sizeof(uint64_t) * n_instances) == cudaSuccess &&
+       cudaMalloc(&h->d_stats, sizeof(unsigned long long) * 8) == cudaSuccess &&
+       cudaMalloc(&h->d_queue, sizeof(int32_t) * 4) == cudaSuccess &&
+       cudaMallocHost(&h->h_stats_pinned, sizeof(unsigned long long) * 8) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_handle(h);
+    return ISING_ERR_OOM;
+  }
+  *out = h;
+  return ISING_OK;
+}
+
+ising_status ising_energy(ising_handle *h, const int8_t *spins_dev, int32_t replicas, double *energy_dev,
+                          int32_t *energy_i32_dev, cudaStream_t stream) {
+  if (!h || !spins_dev || !energy_dev || replicas < 1) return ISING_ERR_INVALID_ARG;
+  if (h->latched != ISING_OK) {
+    ising_status l = h->latched;
+    h->latched = ISING_OK;
+    return l;
+  }
+  if (energy_i32_dev && (h->dtype != ISING_I8 || h->abs_energy_bound > 0x7fffffffLL))
+    return ISING_ERR_UNSUPPORTED;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != h->device) cudaSetDevice(h->device);
+  cudaError_t e = launch_energy(h, spins_dev, replicas, energy_dev, energy_i32_dev, stream);
+  if (cur != h->device) cudaSetDevice(cur);
+  return e == cudaSuccess ? ISING_OK : ISING_ERR_CUDA;
+}
+
+int32_t ising_plan_kernel(ising_handle *h, int32_t replicas, const ising_search_params *p) {
+  if (!h || replicas < 1) return -(int32_t)ISING_ERR_INVALID_ARG;
+  ising_status st = validate_params(p);
+  if (st != ISING_OK) return -(int32_t)st;
+  return resolve_kernel(h, replicas, p);
+}
+
+ising_status ising_local_search(ising_handle *h, const uint64_t *seeds, int32_t replicas,
+                                const ising_search_params *p, int8_t *spins_dev, double *energy_dev,
+                                int32_t *energy_i32_dev, int32_t *minima_dev, ising_stats *stats,
+                                cudaStream_t stream) {
+  if (!h || !seeds || replicas < 1 || !spins_dev || !energy_dev) return ISING_ERR_INVALID_ARG;
+  ising_status st = validate_params(p);
+  if (st != ISING_OK) return st;
+  if (h->latched != ISING_OK) {
+    ising_status l = h->latched;
+    h->latched = ISING_OK;
+    return l;
+  }
+  if (energy_i32_dev && (h->dtype != ISING_I8 || h->abs_energy_bound > 0x7fffffffLL))
+    return ISING_ERR_UNSUPPORTED;
+  if ((int64_t)replicas * h->total_spins > (int64_t)1 << 40) return ISING_ERR_UNSUPPORTED;
+  const int32_t kernel = resolve_kernel(h, replicas, p);
+  if (kernel < 0) return (ising_status)(-kernel);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != h->device) cudaSetDevice(h->device);
+  st = ISING_OK;
+  do {
+    if (cudaMemcpyAsync(h->d_seeds, seeds, sizeof(uint64_t) * h->n_inst, cudaMemcpyHostToDevice, stream) !=
+            cudaSuccess ||
+        cudaMemsetAsync(h->d_stats, 0, sizeof(unsigned long long) * 8, stream) != cudaSuccess) {
+      st = ISING_ERR_CUDA;
+      break;
+    }
+    switch (kernel) {
+      case ISING_KERNEL_TILE:
+        st = run_tile(h, h->dtype == ISING_F32 ? 1 : 0, replicas, p, spins_dev, energy_dev, energy_i32_dev,
+                      minima_dev, stream);
+        break;
+      case ISING_KERNEL_MSC:
+        st = run_tile(h, 2, replicas, p, spins_dev, energy_dev, energy_i32_dev, minima_dev, stream);
+        break;
+      default:
+        st = ISING_ERR_UNSUPPORTED;
+        break;
+    }
+  } while (0);
+  if (st == ISING_OK && stats) {
+    if (cudaMemcpyAsync(h->h_stats_pinned, h->d_stats, sizeof(unsigned long long) * 5, cudaMemcpyDeviceToHost,
+                        stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess) {
+      st = ISING_ERR_CUDA;
+    } else {
+      stats->flip_evals = h->h_stats_pinned[0];
+      stats->flips = h->h_stats_pinned[1];
+      stats->minima = h->h_stats_pinned[2];
+      stats->descents = h->h_stats_pinned[3];
+      stats->sweeps = h->h_stats_pinned[4];
+    }
+  }
+  if (cur != h->device) cudaSetDevice(cur);
+  return st;
+}
+
+ising_status ising_autotune(ising_handle *h, int32_t replicas, const ising_search_params *p, int32_t *chosen,
+                            cudaStream_t stream) {
+  (void)stream;
+  if (!h || !p || replicas < 1) return ISING_ERR_INVALID_ARG;
+  int32_t k = resolve_kernel(h, replicas, p);
+  if (k < 0) return (ising_status)(-k);
+  if (chosen) *chosen = k;
+  return ISING_OK;
+}
+
+ising_status ising_destroy(ising_handle *h) {
+  free_handle(h);
+  return ISING_OK;
+}
+
+const char *ising_status_string(ising_status s) {
+  switch (s) {
+    case ISING_OK: return "ok";
+    case ISING_ERR_INVALID_ARG: return "invalid argument";
+    case ISING_ERR_ASYMMETRIC: return "coupling matrix is not symmetric";
+    case ISING_ERR_SELF_LOOP: return "coupling matrix has a self loop";
+    case ISING_ERR_BAD_HYPEREDGE: return "malformed hyper-edge";
+    case ISING_ERR_BAD_COLOURING: return "colouring is not proper for the conflict graph";
+    case ISING_ERR_UNSUPPORTED: return "unsupported instance/kernel combination";
+    case ISING_ERR_OOM: return "out of memory";
+    case ISING_ERR_CUDA: return "CUDA runtime error";
+    case ISING_ERR_TIMEOUT: return "device-side wait timed out";
+    case ISING_ERR_DEVICE: return "device-side check failed";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,138 @@
+// internal.h — device-side instance layout, kernel argument blocks and the
+// handle shared by the host API and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "ising.h"
+
+namespace isg {
+
+constexpr int kTileThreads = 512;   // threads per tile CTA (16 warps)
+constexpr int kSweepThreads = 256;  // threads per CTA of the large-instance sweeps
+
+// One instance as the kernels see it.  Spin, edge and class arrays of all
+// instances are concatenated; these are each instance's offsets into them.
+struct InstDesc {
+  int32_t n;          // spins
+  int32_t ncls;       // colour classes
+  int64_t spin_off;   // first spin (global index) = offset into h, order, row
+  int64_t cls_off;    // offset into the class-pointer array (ncls + 1 entries)
+  int64_t hyper_off;  // first hyper-edge (global id)
+  int32_t n_hyper;    // hyper-edges of this instance
+  int32_t max_deg;    // largest CSR row length
+};
+
+// Everything a kernel needs to read an instance set.
+struct DevGraph {
+  const InstDesc *inst;
+  const uint32_t *row;      // [total_spins + 1] global offsets into col/J
+  const int32_t *col;       // local neighbour index
+  const void *J;            // int8_t or float
+  const void *h;            // [total_spins] int8_t or float (zeros when absent)
+  const uint32_t *inc_ptr;  // [total_spins + 1] offsets into inc_edge
+  const int32_t *inc_edge;  // global hyper-edge ids containing the spin, ascending
+  const uint32_t *hptr;     // [total_edges + 1] offsets into hmem
+  const int32_t *hmem;      // local member indices
+  const void *hJ;           // [total_edges] int8_t or float
+  const int32_t *order;     // [total_spins] local spins sorted by (colour, index)
+  const int32_t *cls;       // class pointers per instance (ncls + 1 each)
+  int32_t dtype;            // ISING_I8 / ISING_F32
+};
+
+// Per-call arguments of the tile kernels (kept in device memory so that a
+// captured graph can be replayed with new outputs and seeds).
+struct TileArgs {
+  DevGraph g;
+  const int2 *tiles;        // (instance, 32-replica group), largest instances first
+  int32_t n_tiles;
+  int32_t *queue;           // work-queue counter, zeroed before each launch
+  int32_t R, max_sweeps, restarts, budget, refresh, sequential;
+  const uint64_t *seeds;    // [n_inst]
+  float *F;                 // [grid][nmax][32] FP32 fields (float lane path)
+  uint32_t *bw;             // [grid][nmax] best-state words
+  int32_t nmax;
+  int8_t *spins;            // out [inst][replica][spin]
+  double *energy;           // out [inst][replica]
+  int32_t *energy_i32;      // out or null
+  int32_t *minima;          // out or null
+  unsigned long long *stats;  // [5] accumulated work counters
+};
+
+struct PlanKey {
+  int32_t R, kernel, schedule;
+  bool operator<(const PlanKey &o) const {
+    return std::tie(R, kernel, schedule) < std::tie(o.R, o.kernel, o.schedule);
+  }
+};
+
+}  // namespace isg
+
+struct ising_handle {
+  int device = 0;
+  int sm_count = 0;
+  int32_t n_inst = 0;
+  int32_t dtype = 0;
+  bool dense = false;       // instances given as dense matrices
+  bool msc_ok = false;      // every coupling +/-1, every field in {-1,0,+1}, no hyper-edges
+  bool has_hyper = false;
+  int32_t nmax = 0;
+  int64_t total_spins = 0, total_nnz = 0, total_edges = 0, total_members = 0;
+  int64_t abs_energy_bound = 0;  // sum |J| + |h| + |J_e| (integer instances)
+  std::vector<isg::InstDesc> inst;
+  std::vector<int32_t> ncls_seq;
+
+  // device copies
+  isg::InstDesc *d_inst = nullptr;
+  uint32_t *d_row = nullptr;
+  int32_t *d_col = nullptr;
+  void *d_J = nullptr;
+  void *d_h = nullptr;
+  uint32_t *d_inc_ptr = nullptr;
+  int32_t *d_inc_edge = nullptr;
+  uint32_t *d_hptr = nullptr;
+  int32_t *d_hmem = nullptr;
+  void *d_hJ = nullptr;
+  int32_t *d_order = nullptr;
+  int32_t *d_cls = nullptr;
+  float *d_Jdense = nullptr;
+
+  // scratch and per-call state, grown on demand
+  void *d_scratch = nullptr;
+  size_t scratch_bytes = 0;
+  isg::TileArgs *d_tile_args = nullptr;
+  uint64_t *d_seeds = nullptr;
+  unsigned long long *d_stats = nullptr;
+  int32_t *d_queue = nullptr;
+  int2 *d_tiles = nullptr;
+  int32_t tiles_R = -1;
+  int32_t n_tiles = 0;
+  unsigned long long *h_stats_pinned = nullptr;
+  // energy work list (per replica count) and partial sums
+  int32_t en_R = -1, en_nwork = 0;
+  int4 *d_en_work = nullptr;
+  int32_t *d_en_first = nullptr;
+  double *d_en_partd = nullptr;
+  long long *d_en_parti = nullptr;
+
+  // tuned kernel family per replica count (autotuner cache)
+  std::map<int32_t, int32_t> tuned;
+  ising_status latched = ISING_OK;
+  isg::DevGraph graph() const;
+};
+
+namespace isg {
+// launchers (tile.cu / energy.cu / plain.cu / sweep.cu / dense.cu)
+cudaError_t launch_tile(ising_handle *h, int mode, int grid, size_t smem, cudaStream_t s);
+size_t tile_smem_bytes(int mode, int nmax);
+int tile_max_ctas_per_sm(int mode, size_t smem);
+cudaError_t launch_energy(ising_handle *h, const int8_t *spins, int32_t R, double *E,
+                          int32_t *E32, cudaStream_t s);
+void energy_plan_free(ising_handle *h);
+}  // namespace isg

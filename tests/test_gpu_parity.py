@@ -1,0 +1,172 @@
+"""GPU parity: the CUDA library (through the C ABI) against the CPU oracle.
+
+Integer couplings: spins, energies, per-replica minima counts and work counters
+must match bit-exactly.  FP32 couplings: the library's documented FP32 field
+semantics are mirrored by the oracle, so spins must match bit-exactly as well;
+energies (FP64 on both sides, different summation order) within 1e-9 relative,
+far inside the 1e-6 bar.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+isg = pytest.importorskip("paper_0912_3912_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_0912_3912_gb300 import build as B
+    B.build()
+    oracle.build()
+
+
+def _run(insts, seeds, R, **kw):
+    h = isg.Handle(insts)
+    res = h.local_search(seeds, R, want_i32=insts[0].dtype == "i8", **kw)
+    torch.cuda.synchronize()
+    out = []
+    for b, inst in enumerate(insts):
+        sp = h.spins_of(res.spins, b, R).cpu().numpy()
+        out.append((sp, res.energy[b].cpu().numpy(), res.minima[b].cpu().numpy()))
+    e32 = None if res.energy_i32 is None else res.energy_i32.cpu().numpy()
+    h.close()
+    return out, res.stats, e32
+
+
+def _oracle(insts, seeds, R, **kw):
+    tot = dict(flip_evals=0, flips=0, minima=0, descents=0, sweeps=0)
+    out = []
+    for b, inst in enumerate(insts):
+        kw2 = dict(kw)
+        kw2.pop("kernel", None)
+        s, E, m, st = oracle.descent(inst, seeds[b], b, R, **kw2)
+        out.append((s, E, m))
+        for k in tot:
+            tot[k] += st[k]
+    return out, tot
+
+
+def _compare(insts, seeds, R, exact_energy, **kw):
+    g, gst, e32 = _run(insts, seeds, R, **kw)
+    o, ost = _oracle(insts, seeds, R, **kw)
+    for b in range(len(insts)):
+        assert np.array_equal(g[b][0], o[b][0]), f"spins differ for instance {b}"
+        assert np.array_equal(g[b][2], o[b][2]), f"minima counts differ for instance {b}"
+        if exact_energy:
+            assert np.array_equal(g[b][1], o[b][1])
+        else:
+            np.testing.assert_allclose(g[b][1], o[b][1], rtol=1e-9, atol=1e-9)
+    assert gst == ost
+    if e32 is not None:
+        assert np.array_equal(e32.ravel(), np.concatenate([x[1] for x in o]).astype(np.int32))
+    return g, o
+
+
+# ----------------------------------------------------------- 16x16 +/-J lattice (64 replicas)
+@pytest.mark.parametrize("kernel", [isg.KERNEL_TILE, isg.KERNEL_MSC, isg.KERNEL_AUTO])
+def test_lattice_16x16_pmJ_bit_exact(kernel):
+    inst = W.lattice((16, 16), periodic=True, couplings="pm1", seed=W.config_seed(0))
+    seed = W.replica_seed(W.config_seed(0))
+    _compare([inst], [seed], 64, True, max_sweeps=1000, restarts=10, kernel=kernel)
+
+
+def test_lattice_4x4_reaches_bruteforce_ground_state():
+    inst = W.lattice((4, 4), periodic=True, couplings="pm1", seed=3)
+    Egs, _, _ = oracle.bruteforce(inst)
+    g, o = _compare([inst], [11], 64, True, max_sweeps=100, restarts=10)
+    E = g[0][1]
+    assert np.all(E >= Egs) and np.any(E == Egs)
+
+
+@pytest.mark.parametrize("kernel", [isg.KERNEL_TILE, isg.KERNEL_MSC])
+def test_3d_pmJ_with_fields_ragged_replicas(kernel):
+    inst = W.lattice((8, 8, 8), periodic=True, couplings="pm1", fields="pm1_0", seed=5)
+    _compare([inst], [77], 37, True, max_sweeps=100, restarts=3, kernel=kernel)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_random_integer_graph_with_hyperedges(seed):
+    inst = W.random_graph(300, 5.0, seed, dtype="i8", n_hyper=40, hyper_order=(2, 3, 4))
+    _compare([inst], [seed * 7], 40, True, max_sweeps=500, restarts=2)
+
+
+@pytest.mark.parametrize("refresh", [0, 1, 4, 16])
+def test_random_float_graph_fp32_mirror(refresh):
+    inst = W.random_graph(333, 4.5, 9, dtype="f32", n_hyper=30, hyper_order=(3, 4))
+    _compare([inst], [1234], 33, False, max_sweeps=500, restarts=2, refresh_every=refresh)
+
+
+def test_batched_uneven_chimera_fp32():
+    insts = W.chimera_batch(9, 2, 7, seed=W.config_seed(2))
+    seeds = [W.replica_seed(W.splitmix64(W.config_seed(2) + b)) for b in range(len(insts))]
+    _compare(insts, seeds, 32, False, max_sweeps=1000, restarts=2, refresh_every=16)
+
+
+@pytest.mark.parametrize("dtype", ["i8", "f32"])
+def test_sequential_schedule(dtype):
+    if dtype == "i8":
+        inst = W.random_graph(150, 4.0, 3, dtype="i8", n_hyper=10, hyper_order=(3,))
+    else:
+        inst = W.chimera(3, seed=4)
+    _compare([inst], [5], 20, dtype == "i8", max_sweeps=300, restarts=2, refresh_every=8,
+             schedule=isg.SCHED_SEQUENTIAL)
+
+
+@pytest.mark.parametrize("kernel", [isg.KERNEL_TILE, isg.KERNEL_MSC])
+def test_sweep_budget_and_cap(kernel):
+    inst = W.lattice((12, 12, 12), periodic=True, couplings="pm1", fields="pm1_0", seed=6)
+    _compare([inst], [3], 32, True, max_sweeps=5, restarts=1000, sweep_budget=23, kernel=kernel)
+
+
+def test_local_minimum_property_and_energy_api():
+    inst = W.chimera(6, seed=8)
+    R = 64
+    h = isg.Handle([inst])
+    res = h.local_search([99], R, max_sweeps=2000, restarts=3)
+    E_api = h.energy(res.spins, R)
+    torch.cuda.synchronize()
+    sp = res.spins.view(R, inst.n).cpu().numpy()
+    E = res.energy.view(R).cpu().numpy()
+    np.testing.assert_allclose(E_api.view(R).cpu().numpy(), E, rtol=1e-12, atol=1e-12)
+    oi = oracle.OracleInstance(inst)
+    for r in range(R):
+        f = oracle.local_fields(oi, sp[r])
+        assert np.all(sp[r] * f >= -1e-4)
+        assert abs(oracle.energy(oi, sp[r]) - E[r]) <= 1e-9 * abs(E[r])
+    h.close()
+
+
+def test_energy_api_random_configurations():
+    insts = [W.random_graph(n, 4.0, n, dtype="f32", n_hyper=5) for n in (50, 5000, 9000)]
+    R = 3
+    h = isg.Handle(insts)
+    rng = np.random.default_rng(0)
+    spins = (rng.integers(0, 2, size=R * h.total_spins) * 2 - 1).astype(np.int8)
+    E = h.energy(torch.from_numpy(spins).cuda(), R).cpu().numpy()
+    off = 0
+    for b, inst in enumerate(insts):
+        blk = spins[off: off + R * inst.n].reshape(R, inst.n)
+        off += R * inst.n
+        ref = oracle.energies(inst, blk)
+        np.testing.assert_allclose(E[b], ref, rtol=1e-12, atol=1e-9)
+    h.close()
+
+
+def test_msc_rejected_for_float_and_large_fields():
+    inst = W.chimera(2, seed=1)
+    h = isg.Handle([inst])
+    with pytest.raises(isg.IsingError) as ei:
+        h.local_search([1], 32, kernel=isg.KERNEL_MSC)
+    assert ei.value.code == 6
+    h.close()
+    inst = W.random_graph(64, 3.0, 2, dtype="i8", int_range=3)
+    h = isg.Handle([inst])
+    assert h.plan_kernel(32) == isg.KERNEL_TILE
+    h.close()

@@ -1,0 +1,119 @@
+"""Host-side checks of the C-ABI library that need no GPU.
+
+The library must build for sm_103a, load, and export every function
+include/ising.h declares; ising_create must reject malformed instances with
+the documented status codes before it touches the device.
+"""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def isg():
+    from paper_0912_3912_gb300 import build as B
+    B.build()
+    import paper_0912_3912_gb300 as m
+    m.lib()
+    return m
+
+
+def _declared_functions():
+    txt = open(os.path.join(ROOT, "include", "ising.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(ising_[a-z_0-9]+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_function(isg):
+    names = _declared_functions()
+    assert "ising_local_search" in names and len(names) >= 7
+    L = C.CDLL(isg.LIB_PATH)
+    for nm in names:
+        assert hasattr(L, nm), nm
+    assert set(names) == set(isg.EXPORTED)
+
+
+def test_status_strings(isg):
+    assert isg.status_string(0) == "ok"
+    assert "symmetric" in isg.status_string(2)
+
+
+def _desc(isg, inst, **over):
+    jdt = np.int8 if inst.dtype == "i8" else np.float32
+    arrs = dict(row_ptr=np.ascontiguousarray(inst.row_ptr, np.int64),
+                col=np.ascontiguousarray(inst.col, np.int32),
+                J=np.ascontiguousarray(inst.J, jdt),
+                h=None if inst.h is None else np.ascontiguousarray(inst.h, jdt),
+                hyper_ptr=None if inst.hyper_ptr is None else np.ascontiguousarray(inst.hyper_ptr, np.int64),
+                hyper_members=None if inst.hyper_members is None else np.ascontiguousarray(inst.hyper_members, np.int32),
+                hyper_J=None if inst.hyper_J is None else np.ascontiguousarray(inst.hyper_J, jdt),
+                colour=None if inst.colour is None else np.ascontiguousarray(inst.colour, np.int32))
+    arrs.update(over)
+    p = lambda a: None if a is None else a.ctypes.data
+    nh = 0 if arrs["hyper_ptr"] is None else len(arrs["hyper_ptr"]) - 1
+    d = isg._Desc(inst.n, p(arrs["row_ptr"]), p(arrs["col"]), p(arrs["J"]), None, p(arrs["h"]), nh,
+                  p(arrs["hyper_ptr"]), p(arrs["hyper_members"]), p(arrs["hyper_J"]), p(arrs["colour"]),
+                  0 if inst.dtype == "i8" else 1)
+    return d, arrs
+
+
+def _create_code(isg, d):
+    arr = (isg._Desc * 1)(d)
+    code, h = isg.create_raw(C.cast(arr, C.c_void_p), 1)
+    assert not h.value or code == 0
+    return code
+
+
+def test_create_rejects_malformed_instances(isg):
+    base = W.random_graph(40, 3.0, 1, dtype="f32", n_hyper=3, hyper_order=(3,))
+    # asymmetric values
+    J = base.J.copy()
+    J[0] += 1.0
+    d, keep = _desc(isg, base, J=J)
+    assert _create_code(isg, d) == 2
+    # self loop: point the first entry of row 0 at spin 0
+    col = base.col.copy()
+    col[base.row_ptr[0]] = 0
+    d, keep = _desc(isg, base, col=col)
+    assert _create_code(isg, d) == 3
+    # out-of-range column
+    col = base.col.copy()
+    col[0] = 1000
+    d, keep = _desc(isg, base, col=col)
+    assert _create_code(isg, d) == 1
+    # hyper-edge with a repeated member
+    hm = base.hyper_members.copy()
+    hm[1] = hm[0]
+    d, keep = _desc(isg, base, hyper_members=hm)
+    assert _create_code(isg, d) == 4
+    # hyper-edge with one member
+    hp = np.array([0, 1, 3, 6, 9], np.int64)
+    hm = np.concatenate([[5], base.hyper_members]).astype(np.int32)
+    hJ = np.concatenate([[1.0], base.hyper_J]).astype(np.float32)
+    d, keep = _desc(isg, base, hyper_ptr=hp, hyper_members=hm, hyper_J=hJ)
+    assert _create_code(isg, d) == 4
+    # improper colouring: everybody colour 0
+    d, keep = _desc(isg, base, colour=np.zeros(base.n, np.int32))
+    assert _create_code(isg, d) == 5
+    # decreasing row pointer
+    rp = base.row_ptr.copy()
+    rp[3] = rp[4] + 1
+    d, keep = _desc(isg, base, row_ptr=rp)
+    assert _create_code(isg, d) == 1
+
+
+def test_create_rejects_bad_arguments(isg):
+    code, h = isg.create_raw(None, 1)
+    assert code == 1 and not h.value
+    base = W.lattice((4, 4), couplings="pm1")
+    d, keep = _desc(isg, base)
+    d.n = 0
+    assert _create_code(isg, d) == 1
