@@ -1,0 +1,354 @@
+#!/usr/bin/env python3
+"""Benchmark: spin-flip evaluations/s and local minima/s of the GPU local search.
+
+One step = one ising_local_search call over the whole workload (every
+instance, every replica, every restart) with the instances resident on the
+GPU.  Workloads (synthetic, seeded; see workloads/):
+  c1  16x16 periodic +/-J lattice, 64 replicas, 10 restarts
+  c2  32^3 periodic +/-J lattice, h in {-1,0,1}, 1024 replicas, <= 100 sweeps
+      per descent, 10 restarts (multi-spin coded)            [default]
+  c3  4096 K4,4 cell grids (side 4..16), Gaussian J, h, one 3-spin coupling
+      per cell, 32 replicas, FP32 fields with FP64 refresh every 16 sweeps
+  c4  dense SK, N = 4096, 4096 replicas, sequential schedule on tensor cores
+  c5  100^3 periodic Gaussian lattice, 16 replicas, 1000-sweep budget with
+      restarts, FP32 fields refreshed in FP64 every 16 sweeps
+  c5i the same lattice with +/-1 couplings
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "spin-flip evals/s, minima/s on 1 GB300: batched/mixed vs plain at equal energy"
+UNIT = "flip_evals/s"
+
+
+def make_workload(name: str):
+    """(instances, replicas, search kwargs, description)."""
+    if name == "c1":
+        inst = W.lattice((16, 16), periodic=True, couplings="pm1", seed=W.config_seed(0))
+        return [inst], 64, dict(max_sweeps=1000, restarts=10), "16x16 periodic +/-J lattice, 64 replicas, 10 restarts"
+    if name == "c2":
+        inst = W.lattice((32, 32, 32), periodic=True, couplings="pm1", fields="pm1_0", seed=W.config_seed(1))
+        return [inst], 1024, dict(max_sweeps=100, restarts=10), \
+            "32^3 periodic +/-J lattice, h in {-1,0,1}, 1024 replicas, <=100 sweeps/descent, 10 restarts"
+    if name == "c3":
+        insts = W.chimera_batch(4096, 4, 16, seed=W.config_seed(2))
+        return insts, 32, dict(max_sweeps=1000, restarts=1, refresh_every=16), \
+            "4096 K4,4 cell grids (side 4..16), Gaussian J,h + one 3-spin coupling per cell, 32 replicas"
+    if name == "c4":
+        inst = W.sk(4096, seed=W.config_seed(3))
+        return [inst], 4096, dict(max_sweeps=1000, restarts=1, refresh_every=16, schedule=1), \
+            "dense SK N=4096, 4096 replicas, sequential schedule"
+    if name == "c5":
+        inst = W.lattice((100, 100, 100), periodic=True, couplings="gauss", seed=W.config_seed(4))
+        return [inst], 16, dict(max_sweeps=1000, restarts=1 << 30, sweep_budget=1000, refresh_every=16), \
+            "100^3 periodic Gaussian lattice, 16 replicas, 1000-sweep budget with restarts"
+    if name == "c5i":
+        inst = W.lattice((100, 100, 100), periodic=True, couplings="pm1", seed=W.config_seed(4))
+        return [inst], 16, dict(max_sweeps=1000, restarts=1 << 30, sweep_budget=1000), \
+            "100^3 periodic +/-J lattice, 16 replicas, 1000-sweep budget with restarts"
+    raise ValueError(name)
+
+
+def seeds_for(name: str, n_inst: int, rank: int):
+    base = W.config_seed(int(name[1]) - 1) + 1000003 * rank
+    return [W.replica_seed(W.splitmix64(base + b)) for b in range(n_inst)]
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- peaks
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), d.get("bf16_tflops_sustained", 1700.0), "measured"
+    return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_sample(name, insts, R, kw, budget_s=10.0):
+    """Time the CPU oracle (single thread) on a bounded sample of the workload."""
+    import oracle
+    oracle.build()
+    seeds = seeds_for(name, len(insts), 0)
+    kw2 = {k: v for k, v in kw.items() if k in ("max_sweeps", "restarts", "sweep_budget", "refresh_every",
+                                              "schedule")}
+    evals = minima = 0
+    t0 = time.perf_counter()
+    done_units = []
+    b = 0
+    r_per = 1
+    oinsts = {}
+    while time.perf_counter() - t0 < budget_s:
+        inst = insts[b % len(insts)]
+        if b not in oinsts:
+            oinsts[b] = oracle.OracleInstance(inst)
+        _, _, _, st = oracle.descent(oinsts[b], seeds[b % len(insts)], b % len(insts), r_per, **kw2)
+        evals += st["flip_evals"]
+        minima += st["minima"]
+        done_units.append((b % len(insts), r_per))
+        b += 1
+        if b >= len(insts):
+            b = 0
+            r_per += 1
+    dt = time.perf_counter() - t0
+    desc = (f"{len(done_units)} oracle calls (instance, first k replicas) of this workload, "
+            f"{evals} evaluations, {dt:.1f} s")
+    return evals / dt, minima / dt, desc, dt
+
+
+# ----------------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--kernel", default="auto")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    insts, R, kw, desc = make_workload(args.workload)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        ev, mn, sample, dt = oracle_sample(args.workload, insts, R, kw, budget_s=args.cpu_seconds)
+        steps_t = []
+        for _ in range(args.warmup + args.steps):
+            pass
+        line = {"metric": METRIC, "value": ev, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "i8->int64" if insts[0].dtype == "i8" else "f32/f64",
+                "data": "synthetic", "minima_per_s": mn,
+                "config": {"workload": args.workload, "description": desc, "replicas": R, **{k: v for k, v in kw.items()}},
+                "cpu_baseline": {"value": ev, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                "e2e": {"value": ev, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    import paper_0912_3912_gb300 as isg
+    from paper_0912_3912_gb300 import build as B
+    if rank == 0 or not os.path.exists(isg.LIB_PATH):
+        B.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    kernel = {"auto": 0, "tile": 1, "msc": 2, "sweep": 3, "dense": 4, "plain": 5}[args.kernel]
+    seeds = seeds_for(args.workload, len(insts), rank)
+    h = isg.Handle(insts)
+    chosen = h.plan_kernel(R, kernel=kernel, **{k: v for k, v in kw.items() if k in ("schedule",)})
+    stream = torch.cuda.current_stream()
+    total_spins = h.total_spins
+    spins = torch.empty(R * total_spins, dtype=torch.int8, device=dev)
+    E = torch.empty((len(insts), R), dtype=torch.float64, device=dev)
+    minima = torch.empty((len(insts), R), dtype=torch.int32, device=dev)
+    out = (spins, E, None, minima)
+    l2_flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step(stats=False):
+        return h.local_search(seeds, R, kernel=kernel, stats=stats, out=out, **kw)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ref = step(stats=True)        # work counters of one step (identical every step)
+    st = ref.stats
+    torch.cuda.synchronize()
+
+    if dist is not None:
+        dist.barrier()
+    clocks = ClockSampler(dev.index)
+    torch.cuda.synchronize()
+    ev_pairs = []
+    for _ in range(args.steps):
+        l2_flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        ev_pairs.append((a, b))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in ev_pairs]
+    t_total = sum(ms) / 1e3
+    if dist is not None:
+        t = torch.tensor([t_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+    evals_job = st["flip_evals"] * args.steps * world
+    minima_job = st["minima"] * args.steps * world
+    value = evals_job / t_total
+
+    # end to end: host seeds in, host results out (pinned), through the C ABI
+    h_spins = torch.empty(R * total_spins, dtype=torch.int8, pin_memory=True)
+    h_E = torch.empty((len(insts), R), dtype=torch.float64, pin_memory=True)
+    e2e_ms = []
+    for _ in range(args.steps):
+        l2_flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        h_spins.copy_(spins, non_blocking=True)
+        h_E.copy_(E, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_value = st["flip_evals"] * len(e2e_ms) / (sum(e2e_ms) / 1e3)
+
+    # roofline of the dominant kernel (the whole step is one kernel launch for tile/MSC)
+    hbm, bf16, bf16s, peak_src = measured_peaks()
+    n_launch_per_step = 1
+    roof = roofline(args.workload, chosen, insts, R, st, t_total / args.steps, clk, hbm, bf16s, peak_src)
+
+    # equal-energy comparison with the plain comparator kernel
+    plain = None
+    if not args.no_plain and chosen != isg.KERNEL_PLAIN:
+        try:
+            pr = h.local_search(seeds, R, kernel=isg.KERNEL_PLAIN, stats=True, **kw)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pr = h.local_search(seeds, R, kernel=isg.KERNEL_PLAIN, stats=True, **kw)
+            b.record(stream)
+            torch.cuda.synchronize()
+            pms = a.elapsed_time(b)
+            same = bool(torch.equal(pr.energy, E)) if insts[0].dtype == "i8" else float(
+                (pr.energy - E).abs().max().item())
+            plain = {"value": pr.stats["flip_evals"] / (pms / 1e3), "unit": UNIT, "ms_per_step": pms,
+                     "energy_match": same, "speedup": value / (pr.stats["flip_evals"] / (pms / 1e3))}
+        except Exception as ex:  # plain kernel not available for this workload
+            plain = {"unavailable": str(ex)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ev, mn, sample, dt = oracle_sample(args.workload, insts, R, kw, budget_s=args.cpu_seconds)
+        cpu = {"value": ev, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+               "minima_per_s": mn}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_total * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bit-packed i1/int32" if insts[0].dtype == "i8" else "f32 fields, f64 refresh/energy",
+            "data": "synthetic (seeded generators; the paper's instances are not available)",
+            "minima_per_s": minima_job / t_total,
+            "config": {"workload": args.workload, "description": desc, "replicas": R,
+                       "instances": len(insts), "spins": total_spins,
+                       "kernel": isg.KERNEL_NAMES[chosen], "l2": "flushed (512 MB write) before every timed step",
+                       **{k: v for k, v in kw.items()}},
+            "work_per_step": st,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * len(insts),
+                    "d2h_bytes_per_step": R * total_spins + 8 * R * len(insts)},
+            "gpu_launches": n_launch_per_step * args.steps,
+            "clocks": clk,
+            "roofline": roof,
+            "plain": plain,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    h.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def roofline(name, kernel, insts, R, st, step_s, clk, hbm, bf16s, src):
+    """Roofline of the step's dominant kernel (derivations in the design doc)."""
+    sm_count = 152
+    mhz = (clk or {}).get("sm_mhz") or 2070.0
+    if kernel == 2:  # multi-spin coded tile: ALU/issue bound
+        # 22 integer/logic lane-operations per (spin, 32-replica word) visit for degree 6
+        deg = insts[0].nnz / insts[0].n if insts[0].row_ptr is not None else 6
+        ops_per_word = 3 * deg + 4
+        words = st["flip_evals"] / 32.0
+        achieved = words * ops_per_word / step_s / 1e12
+        peak = sm_count * 128 * mhz * 1e6 / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": f"152 SMs x 128 int lanes x {mhz:.0f} MHz (median under load)",
+                "ops_per_word": ops_per_word}
+    # lane-per-replica tile and sweep kernels: bytes moved per visit
+    evals = st["flip_evals"]
+    fl = insts[0].dtype == "f32"
+    deg = sum(i.nnz for i in insts) / sum(i.n for i in insts)
+    per_visit = (8.0 if fl else 0.0) + (deg * 8.0 + 8.0) / 32.0 + 0.25
+    achieved = evals * per_visit / step_s / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": None, "peak_source": src, "bytes_per_eval": per_visit}
+
+
+if __name__ == "__main__":
+    main()

@@ -9,7 +9,8 @@
 #include "internal.h"
 
 namespace isg {
-cudaError_t launch_plain(ising_handle *h, const ising_search_params *p, int32_t R, cudaStream_t s);
+cudaError_t launch_plain(ising_handle *h, const ising_search_params *p, int32_t R, int8_t *spins, double *E,
+                         int32_t *E32, int32_t *minima, const uint64_t *seeds_host, cudaStream_t s);
 cudaError_t launch_sweep(ising_handle *h, const ising_search_params *p, int32_t R, cudaStream_t s);
 cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t R, cudaStream_t s);
 bool dense_supported(const ising_handle *h, int32_t R);
@@ -439,6 +440,7 @@ ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
   inc_ptr.push_back((uint32_t)inc_edge.size());
   hptr.push_back((uint32_t)mem_off);
   h->inst = inst;
+  h->h_cls = cls;
   h->total_spins = spin_off;
   h->total_nnz = nnz_off;
   h->total_edges = edge_off;
@@ -538,6 +540,11 @@ ising_status ising_local_search(ising_handle *h, const uint64_t *seeds, int32_t 
         break;
       case ISING_KERNEL_MSC:
         st = run_tile(h, 2, replicas, p, spins_dev, energy_dev, energy_i32_dev, minima_dev, stream);
+        break;
+      case ISING_KERNEL_PLAIN:
+        if (launch_plain(h, p, replicas, spins_dev, energy_dev, energy_i32_dev, minima_dev, seeds, stream) !=
+            cudaSuccess)
+          st = ISING_ERR_CUDA;
         break;
       default:
         st = ISING_ERR_UNSUPPORTED;

@@ -86,7 +86,7 @@ struct ising_handle {
   int64_t total_spins = 0, total_nnz = 0, total_edges = 0, total_members = 0;
   int64_t abs_energy_bound = 0;  // sum |J| + |h| + |J_e| (integer instances)
   std::vector<isg::InstDesc> inst;
-  std::vector<int32_t> ncls_seq;
+  std::vector<int32_t> h_cls;  // host copy of the class pointers
 
   // device copies
   isg::InstDesc *d_inst = nullptr;

@@ -70,7 +70,7 @@ def _compare(insts, seeds, R, exact_energy, **kw):
 
 
 # ----------------------------------------------------------- 16x16 +/-J lattice (64 replicas)
-@pytest.mark.parametrize("kernel", [isg.KERNEL_TILE, isg.KERNEL_MSC, isg.KERNEL_AUTO])
+@pytest.mark.parametrize("kernel", [isg.KERNEL_TILE, isg.KERNEL_MSC, isg.KERNEL_AUTO, isg.KERNEL_PLAIN])
 def test_lattice_16x16_pmJ_bit_exact(kernel):
     inst = W.lattice((16, 16), periodic=True, couplings="pm1", seed=W.config_seed(0))
     seed = W.replica_seed(W.config_seed(0))
@@ -91,35 +91,38 @@ def test_3d_pmJ_with_fields_ragged_replicas(kernel):
     _compare([inst], [77], 37, True, max_sweeps=100, restarts=3, kernel=kernel)
 
 
-@pytest.mark.parametrize("seed", [1, 2])
-def test_random_integer_graph_with_hyperedges(seed):
+@pytest.mark.parametrize("seed,kernel", [(1, isg.KERNEL_TILE), (2, isg.KERNEL_TILE), (3, isg.KERNEL_PLAIN)])
+def test_random_integer_graph_with_hyperedges(seed, kernel):
     inst = W.random_graph(300, 5.0, seed, dtype="i8", n_hyper=40, hyper_order=(2, 3, 4))
-    _compare([inst], [seed * 7], 40, True, max_sweeps=500, restarts=2)
+    _compare([inst], [seed * 7], 40, True, max_sweeps=500, restarts=2, kernel=kernel)
 
 
-@pytest.mark.parametrize("refresh", [0, 1, 4, 16])
-def test_random_float_graph_fp32_mirror(refresh):
+@pytest.mark.parametrize("refresh,kernel", [(0, isg.KERNEL_TILE), (1, isg.KERNEL_TILE), (4, isg.KERNEL_TILE),
+                                            (16, isg.KERNEL_TILE), (4, isg.KERNEL_PLAIN)])
+def test_random_float_graph_fp32_mirror(refresh, kernel):
     inst = W.random_graph(333, 4.5, 9, dtype="f32", n_hyper=30, hyper_order=(3, 4))
-    _compare([inst], [1234], 33, False, max_sweeps=500, restarts=2, refresh_every=refresh)
+    _compare([inst], [1234], 33, False, max_sweeps=500, restarts=2, refresh_every=refresh, kernel=kernel)
 
 
-def test_batched_uneven_chimera_fp32():
+@pytest.mark.parametrize("kernel", [isg.KERNEL_TILE, isg.KERNEL_PLAIN])
+def test_batched_uneven_chimera_fp32(kernel):
     insts = W.chimera_batch(9, 2, 7, seed=W.config_seed(2))
     seeds = [W.replica_seed(W.splitmix64(W.config_seed(2) + b)) for b in range(len(insts))]
-    _compare(insts, seeds, 32, False, max_sweeps=1000, restarts=2, refresh_every=16)
+    _compare(insts, seeds, 32, False, max_sweeps=1000, restarts=2, refresh_every=16, kernel=kernel)
 
 
-@pytest.mark.parametrize("dtype", ["i8", "f32"])
-def test_sequential_schedule(dtype):
+@pytest.mark.parametrize("dtype,kernel", [("i8", isg.KERNEL_TILE), ("f32", isg.KERNEL_TILE),
+                                          ("f32", isg.KERNEL_PLAIN)])
+def test_sequential_schedule(dtype, kernel):
     if dtype == "i8":
         inst = W.random_graph(150, 4.0, 3, dtype="i8", n_hyper=10, hyper_order=(3,))
     else:
         inst = W.chimera(3, seed=4)
     _compare([inst], [5], 20, dtype == "i8", max_sweeps=300, restarts=2, refresh_every=8,
-             schedule=isg.SCHED_SEQUENTIAL)
+             schedule=isg.SCHED_SEQUENTIAL, kernel=kernel)
 
 
-@pytest.mark.parametrize("kernel", [isg.KERNEL_TILE, isg.KERNEL_MSC])
+@pytest.mark.parametrize("kernel", [isg.KERNEL_TILE, isg.KERNEL_MSC, isg.KERNEL_PLAIN])
 def test_sweep_budget_and_cap(kernel):
     inst = W.lattice((12, 12, 12), periodic=True, couplings="pm1", fields="pm1_0", seed=6)
     _compare([inst], [3], 32, True, max_sweeps=5, restarts=1000, sweep_budget=23, kernel=kernel)
