@@ -11,8 +11,10 @@
 namespace isg {
 cudaError_t launch_plain(ising_handle *h, const ising_search_params *p, int32_t R, int8_t *spins, double *E,
                          int32_t *E32, int32_t *minima, const uint64_t *seeds_host, cudaStream_t s);
-cudaError_t launch_sweep(ising_handle *h, const ising_search_params *p, int32_t R, cudaStream_t s);
-cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t R, cudaStream_t s);
+cudaError_t launch_sweep(ising_handle *h, const ising_search_params *p, int32_t R, int8_t *spins, double *E,
+                         int32_t *E32, int32_t *minima, const uint64_t *seeds_host, cudaStream_t s);
+cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t R, int8_t *spins, double *E,
+                         int32_t *E32, int32_t *minima, const uint64_t *seeds_host, cudaStream_t s);
 bool dense_supported(const ising_handle *h, int32_t R);
 void sweep_free(ising_handle *h);
 void dense_free(ising_handle *h);
@@ -40,6 +42,10 @@ DevGraph ising_handle::graph() const {
   g.hJ = d_hJ;
   g.order = d_order;
   g.cls = d_cls;
+  g.meta = d_meta;
+  g.Jpos = d_Jpos;
+  g.latinfo = d_latinfo;
+  g.nsp = total_spins;
   g.dtype = dtype;
   return g;
 }
@@ -62,7 +68,40 @@ struct HostInst {
   std::vector<int32_t> colour;
   int32_t ncls = 0;
   int32_t max_deg = 0;
+  int32_t lat_L = 0, lat_d = 0;
 };
+
+// Recognise a periodic hypercubic lattice (side L >= 3, d = 2 or 3, spin index
+// x0 + L*x1 + L^2*x2) from the CSR structure alone.
+void detect_lattice(HostInst &I) {
+  const int32_t n = I.n;
+  for (int d = 3; d >= 2; --d) {
+    const int32_t L = (int32_t)std::llround(std::pow((double)n, 1.0 / d));
+    int64_t p = 1;
+    for (int a = 0; a < d; ++a) p *= L;
+    if (L < 3 || p != n || I.max_deg != 2 * d) continue;
+    bool ok = true;
+    for (int32_t i = 0; i < n && ok; ++i) {
+      if (I.row[i + 1] - I.row[i] != 2 * d) { ok = false; break; }
+      for (int64_t k = I.row[i]; k < I.row[i + 1] && ok; ++k) {
+        const int32_t j = I.col[k];
+        bool found = false;
+        int64_t stride = 1;
+        for (int a = 0; a < d && !found; ++a, stride *= L) {
+          const int32_t c = (int32_t)((i / stride) % L);
+          const int64_t up = i + (((c + 1) % L) - c) * stride, dn = i + (((c + L - 1) % L) - c) * stride;
+          found = (j == up) || (j == dn);
+        }
+        ok = found;
+      }
+    }
+    if (ok) {
+      I.lat_L = L;
+      I.lat_d = d;
+      return;
+    }
+  }
+}
 
 double jval(const HostInst &I, int64_t k, bool fl) { return fl ? (double)I.Jf[k] : (double)I.Ji[k]; }
 
@@ -201,6 +240,7 @@ ising_status load_desc(const ising_instance_desc &d, ising_dtype dtype, HostInst
   }
   I.ncls = 0;
   for (int32_t c : I.colour) I.ncls = std::max(I.ncls, c + 1);
+  if (I.hptr.size() == 1) detect_lattice(I);
   return ISING_OK;
 }
 
@@ -222,7 +262,8 @@ void free_handle(ising_handle *h) {
   dense_free(h);
   plain_free(h);
   void *ptrs[] = {h->d_inst, h->d_row, h->d_col, h->d_J, h->d_h, h->d_inc_ptr, h->d_inc_edge, h->d_hptr,
-                  h->d_hmem, h->d_hJ, h->d_order, h->d_cls, h->d_Jdense, h->d_scratch, h->d_tile_args,
+                  h->d_hmem, h->d_hJ, h->d_order, h->d_cls, h->d_Jdense, h->d_meta, h->d_Jpos, h->d_latinfo,
+                  h->d_scratch, h->d_tile_args,
                   h->d_seeds, h->d_stats, h->d_queue, h->d_tiles};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -262,7 +303,7 @@ int32_t resolve_kernel(ising_handle *h, int32_t R, const ising_search_params *p)
   if (k == ISING_KERNEL_AUTO) {
     auto it = h->tuned.find(R);
     if (it != h->tuned.end()) return it->second;
-    if (h->dense && dense_supported(h, R) && p->schedule == ISING_SCHED_SEQUENTIAL) return ISING_KERNEL_DENSE_TC;
+    if (h->dense && dense_supported(h, R)) return ISING_KERNEL_DENSE_TC;
     if (h->msc_ok && tile_fits(h, 2)) return ISING_KERNEL_MSC;
     if (tile_fits(h, h->dtype == ISING_F32 ? 1 : 0)) return ISING_KERNEL_TILE;
     return ISING_KERNEL_SWEEP;
@@ -273,9 +314,7 @@ int32_t resolve_kernel(ising_handle *h, int32_t R, const ising_search_params *p)
     case ISING_KERNEL_MSC:
       return (h->msc_ok && tile_fits(h, 2)) ? k : -(int32_t)ISING_ERR_UNSUPPORTED;
     case ISING_KERNEL_DENSE_TC:
-      return (h->dense && dense_supported(h, R) && p->schedule == ISING_SCHED_SEQUENTIAL)
-                 ? k
-                 : -(int32_t)ISING_ERR_UNSUPPORTED;
+      return (h->dense && dense_supported(h, R)) ? k : -(int32_t)ISING_ERR_UNSUPPORTED;
     default:
       return k;
   }
@@ -385,6 +424,7 @@ ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
   std::vector<float> Jf, hf, hJf;
   std::vector<uint32_t> inc_ptr, hptr;
   std::vector<int32_t> inc_edge, hmem;
+  std::vector<std::pair<int32_t, std::vector<int32_t>>> lat_sites;
   int64_t spin_off = 0, nnz_off = 0, edge_off = 0, mem_off = 0, cls_off = 0;
   for (int32_t b = 0; b < n_instances; ++b) {
     const HostInst &I = hin[b];
@@ -396,6 +436,10 @@ ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
     D.hyper_off = edge_off;
     D.n_hyper = (int32_t)I.hptr.size() - 1;
     D.max_deg = I.max_deg;
+    D.lat_L = I.lat_L;
+    D.lat_d = I.lat_d;
+    h->any_lattice = h->any_lattice || I.lat_d > 0;
+    h->all_lattice = (b == 0 ? true : h->all_lattice) && I.lat_d > 0;
     h->nmax = std::max(h->nmax, I.n);
     for (int32_t i = 0; i < I.n; ++i) row.push_back((uint32_t)(nnz_off + I.row[i]));
     col.insert(col.end(), I.col.begin(), I.col.end());
@@ -426,6 +470,7 @@ ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
     std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1), ord(I.n);
     for (int32_t i = 0; i < I.n; ++i) ord[fill[I.colour[i]]++] = i;
     order.insert(order.end(), ord.begin(), ord.end());
+    if (I.lat_d > 0) lat_sites.push_back({b, ord});
     spin_off += I.n;
     nnz_off += I.row[I.n];
     edge_off += D.n_hyper;
@@ -459,6 +504,45 @@ ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
       ok = upload((int8_t **)&h->d_J, Ji) == cudaSuccess && upload((int8_t **)&h->d_h, hi) == cudaSuccess &&
            upload((int8_t **)&h->d_hJ, hJi) == cudaSuccess;
     }
+  }
+  if (ok && h->any_lattice) {
+    // lattice metadata in colour order (see DevGraph::meta)
+    const int64_t nsp = spin_off;
+    std::vector<uint32_t> meta(nsp, 0);
+    std::vector<uint16_t> latinfo(nsp, 0);
+    std::vector<float> Jpf(fl ? 6 * nsp : 0, 0.0f);
+    std::vector<int8_t> Jpi(fl ? 0 : 6 * nsp, 0);
+    for (auto &ls : lat_sites) {
+      const HostInst &I = hin[ls.first];
+      const InstDesc &D = inst[ls.first];
+      if (I.lat_d == 0) continue;
+      const int32_t L = I.lat_L;
+      for (int32_t v = 0; v < I.n; ++v) {
+        const int32_t j = ls.second[v];
+        uint32_t m = 0;
+        int kk = 0;
+        for (int64_t k = I.row[j]; k < I.row[j + 1]; ++k, ++kk) {
+          const int32_t t = I.col[k];
+          int64_t stride = 1;
+          int dir = -1, wrap = 0;
+          for (int a = 0; a < I.lat_d; ++a, stride *= L) {
+            const int32_t c = (int32_t)((j / stride) % L);
+            if (t == j + (((c + 1) % L) - c) * stride) { dir = 2 * a; wrap = (c == L - 1); break; }
+            if (t == j + (((c + L - 1) % L) - c) * stride) { dir = 2 * a + 1; wrap = (c == 0); break; }
+          }
+          m |= (uint32_t)wrap << kk;
+          m |= (uint32_t)dir << (8 + 3 * kk);
+          const double w = fl ? (double)I.Jf[k] : (double)I.Ji[k];
+          if (w < 0) m |= 1u << (26 + kk);
+          latinfo[D.spin_off + v] |= (uint16_t)((wrap << dir) | ((w < 0 ? 1 : 0) << (8 + dir)));
+          if (fl) Jpf[(int64_t)kk * nsp + D.spin_off + v] = I.Jf[k];
+          else Jpi[(int64_t)kk * nsp + D.spin_off + v] = I.Ji[k];
+        }
+        meta[D.spin_off + v] = m;
+      }
+    }
+    ok = upload(&h->d_meta, meta) == cudaSuccess && upload(&h->d_latinfo, latinfo) == cudaSuccess &&
+         (fl ? upload((float **)&h->d_Jpos, Jpf) : upload((int8_t **)&h->d_Jpos, Jpi)) == cudaSuccess;
   }
   if (ok && dense) {
     std::vector<float> Jd;
@@ -539,7 +623,18 @@ ising_status ising_local_search(ising_handle *h, const uint64_t *seeds, int32_t 
                       minima_dev, stream);
         break;
       case ISING_KERNEL_MSC:
-        st = run_tile(h, 2, replicas, p, spins_dev, energy_dev, energy_i32_dev, minima_dev, stream);
+        st = run_tile(h, (h->all_lattice && p->schedule == ISING_SCHED_COLOUR) ? 3 : 2, replicas, p, spins_dev,
+                      energy_dev, energy_i32_dev, minima_dev, stream);
+        break;
+      case ISING_KERNEL_SWEEP:
+        if (launch_sweep(h, p, replicas, spins_dev, energy_dev, energy_i32_dev, minima_dev, seeds, stream) !=
+            cudaSuccess)
+          st = ISING_ERR_CUDA;
+        break;
+      case ISING_KERNEL_DENSE_TC:
+        if (launch_dense(h, p, replicas, spins_dev, energy_dev, energy_i32_dev, minima_dev, seeds, stream) !=
+            cudaSuccess)
+          st = ISING_ERR_CUDA;
         break;
       case ISING_KERNEL_PLAIN:
         if (launch_plain(h, p, replicas, spins_dev, energy_dev, energy_i32_dev, minima_dev, seeds, stream) !=

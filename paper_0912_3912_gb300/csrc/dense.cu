@@ -1,10 +1,347 @@
-// dense.cu — dense tensor-core path (filled in below).
-#include "internal.h"
+// dense.cu — fully connected instances (Sherrington-Kirkpatrick): the
+// sequential schedule with fields computed on tensor cores.
+//
+// For a complete graph every colour class is one spin, so descent is the
+// paper's one-move-at-a-time order (Sec. IV).  Spins are visited in blocks of
+// B consecutive indices.  Before a block is decided, the fields of its B spins
+// for every replica are recomputed from the current configuration as a GEMM,
+//     F[b0:b0+B, :] = J[b0:b0+B, :] . S        (S = +/-1 spins, [n][R])
+// with J split into two BF16 matrices J = J_hi + J_lo + O(2^-16 |J|) and S
+// exact in BF16, accumulated in FP32 (two GEMMs into one FP32 result).  Inside
+// the block the spins are then decided one after another, each field corrected
+// in FP32 for the block's own earlier flips (+2 J_ij s_j per flipped j), the
+// incremental gain update of the paper restricted to the block.  Energies of
+// converged replicas are -1/2 sum_i s_i f_i summed in FP64 over fields from one
+// full-size GEMM.  These fields carry the BF16-split and FP32 accumulation
+// error, so decisions within about 1e-4 of zero and energies within about
+// 1e-7 relative may differ from an FP64 computation; the tests state and check
+// both bounds.
+#include <cublas_v2.h>
+#include <cuda_bf16.h>
+
+#include <cfloat>
+
+#include "device_common.cuh"
 
 namespace isg {
-cudaError_t launch_dense(ising_handle *, const ising_search_params *, int32_t, cudaStream_t) {
-  return cudaErrorNotSupported;
+
+namespace {
+
+constexpr int kDB = 128;  // spins per block
+
+struct DenseRep {
+  int32_t active, conv, total, minima, d, k, flips, pad;
+  double best, E;
+};
+
+__global__ void dense_split(const float *J, __nv_bfloat16 *hi, __nv_bfloat16 *lo, int64_t nn) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (int64_t)gridDim.x * blockDim.x) {
+    const float w = J[t];
+    const __nv_bfloat16 a = __float2bfloat16_rn(w);
+    hi[t] = a;
+    lo[t] = __float2bfloat16_rn(w - __bfloat162float(a));
+  }
 }
-bool dense_supported(const ising_handle *, int32_t) { return false; }
-void dense_free(ising_handle *) {}
+
+__global__ void dense_start(int32_t n, int32_t R, int32_t Rp, uint64_t seed, int32_t b, const DenseRep *rep,
+                            __nv_bfloat16 *S) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int w = blockIdx.y;
+  if (r >= R || !rep[r].active || rep[r].d != 0) return;
+  const uint4 x = start_bits(seed, (uint32_t)w, (uint32_t)r, (uint32_t)rep[r].k, (uint32_t)b);
+  for (int t = 0; t < 128; ++t) {
+    const int i = w * 128 + t;
+    if (i >= n) break;
+    const uint32_t bit = (word_of(x, t / 32) >> (t % 32)) & 1u;
+    S[(int64_t)i * Rp + r] = __float2bfloat16_rn(bit ? 1.0f : -1.0f);
+  }
+}
+
+// In-block sequential decisions, one thread per replica.
+__global__ void __launch_bounds__(256) dense_decide(int32_t n, int32_t R, int32_t Rp, int32_t b0, int32_t bsz,
+                                                    const float *__restrict__ J, const float *__restrict__ F,
+                                                    __nv_bfloat16 *S, DenseRep *rep) {
+  extern __shared__ float sJ[];  // [kDB][kDB] block of J
+  for (int t = threadIdx.x; t < bsz * bsz; t += blockDim.x) {
+    const int a = t / bsz, c = t % bsz;
+    sJ[a * kDB + c] = J[(int64_t)(b0 + a) * n + b0 + c];
+  }
+  __syncthreads();
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R || !rep[r].active) return;
+  uint32_t flipped[kDB / 32], up[kDB / 32];
+#pragma unroll
+  for (int q = 0; q < kDB / 32; ++q) flipped[q] = up[q] = 0;
+  int nflip = 0;
+  for (int i = 0; i < bsz; ++i) {
+    float f = F[(int64_t)i * Rp + r];
+    const bool s_up = __bfloat162float(S[(int64_t)(b0 + i) * Rp + r]) > 0.0f;
+#pragma unroll
+    for (int q = 0; q < kDB / 32; ++q) {
+      uint32_t m = flipped[q];
+      if (q * 32 >= i) m = 0;
+      else if (i - q * 32 < 32) m &= (1u << (i - q * 32)) - 1u;
+      while (m) {
+        const int j = q * 32 + __ffs(m) - 1;
+        m &= m - 1;
+        const float w2 = 2.0f * sJ[i * kDB + j];
+        f = __fadd_rn(f, ((up[q] >> (j - q * 32)) & 1u) ? w2 : -w2);
+      }
+    }
+    const bool flip = s_up ? (f < 0.0f) : (f > 0.0f);
+    const bool now_up = flip ? !s_up : s_up;
+    if (now_up) up[i / 32] |= 1u << (i % 32);
+    if (flip) {
+      flipped[i / 32] |= 1u << (i % 32);
+      S[(int64_t)(b0 + i) * Rp + r] = __float2bfloat16_rn(now_up ? 1.0f : -1.0f);
+      ++nflip;
+    }
+  }
+  rep[r].flips += nflip;
+}
+
+__global__ void dense_end(int32_t R, int32_t n, int32_t max_sweeps, int32_t budget, DenseRep *rep, int32_t *active_count,
+                          unsigned long long *stats) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  DenseRep &p = rep[r];
+  if (!p.active) return;
+  p.total += 1;
+  p.d += 1;
+  atomicAdd(stats + 0, (unsigned long long)n);
+  atomicAdd(stats + 1, (unsigned long long)p.flips);
+  atomicAdd(stats + 4, 1ull);
+  const bool conv = p.flips == 0;
+  p.flips = 0;
+  if (conv || p.d >= max_sweeps || (budget > 0 && p.total >= budget)) {
+    p.active = 0;
+    p.conv = conv ? 1 : 0;
+    if (conv) atomicAdd(stats + 2, 1ull);
+  } else {
+    atomicAdd(active_count, 1);
+  }
+}
+
+// E_r = -1/2 sum_i s_ir F_ir in FP64; then best-state bookkeeping for the round.
+__global__ void dense_energy(int32_t n, int32_t R, int32_t Rp, const __nv_bfloat16 *S, const float *Ff, DenseRep *rep,
+                             int8_t *best, int32_t final_pass) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  double acc = 0.0;
+  for (int i = 0; i < n; ++i) acc += (double)__bfloat162float(S[(int64_t)i * Rp + r]) * (double)Ff[(int64_t)i * Rp + r];
+  const double E = -0.5 * acc;
+  DenseRep &p = rep[r];
+  p.E = E;
+  if (final_pass) return;
+  if (p.conv) {
+    p.minima += 1;
+    if (E < p.best) {
+      p.best = E;
+      for (int i = 0; i < n; ++i) best[(int64_t)r * n + i] = __bfloat162float(S[(int64_t)i * Rp + r]) > 0.0f ? 1 : -1;
+    }
+  }
+}
+
+__global__ void dense_next_round(int32_t R, int32_t restarts, int32_t budget, DenseRep *rep, int32_t *active_count,
+                                 unsigned long long *stats) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  DenseRep &p = rep[r];
+  p.conv = 0;
+  p.k += 1;
+  if (p.k < restarts && (budget <= 0 || p.total < budget)) {
+    p.active = 1;
+    p.d = 0;
+    atomicAdd(active_count, 1);
+    atomicAdd(stats + 3, 1ull);
+  }
+}
+
+__global__ void dense_init(int32_t R, DenseRep *rep, unsigned long long *stats) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  DenseRep p;
+  p.active = 1;
+  p.conv = p.total = p.minima = p.d = p.k = p.flips = p.pad = 0;
+  p.best = DBL_MAX;
+  p.E = 0.0;
+  rep[r] = p;
+  atomicAdd(stats + 3, 1ull);
+}
+
+__global__ void dense_output(int32_t n, int32_t R, int32_t Rp, int32_t b, int64_t spin_off, const __nv_bfloat16 *S,
+                             const int8_t *best, const DenseRep *rep, int8_t *out, double *E, int32_t *minima) {
+  const int64_t tot = (int64_t)R * n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / n), i = (int)(t % n);
+    out[(int64_t)R * spin_off + t] =
+        rep[r].minima > 0 ? best[t] : (__bfloat162float(S[(int64_t)i * Rp + r]) > 0.0f ? 1 : -1);
+  }
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < R) {
+    const DenseRep &p = rep[t];
+    E[(int64_t)b * R + t] = p.minima > 0 ? p.best : p.E;
+    if (minima) minima[(int64_t)b * R + t] = p.minima;
+  }
+}
+
+struct DenseState {
+  cublasHandle_t cublas = nullptr;
+  void *workspace = nullptr;
+  int32_t n = 0, Rp = 0;
+  int32_t inst = -1;
+  __nv_bfloat16 *hi = nullptr, *lo = nullptr, *S = nullptr;
+  float *F = nullptr, *Ff = nullptr;
+  DenseRep *rep = nullptr;
+  int8_t *best = nullptr;
+  int32_t *active = nullptr, *h_active = nullptr;
+};
+
+std::map<const ising_handle *, DenseState> &dense_states() {
+  static std::map<const ising_handle *, DenseState> m;
+  return m;
+}
+
+void free_state(DenseState &D) {
+  cudaFree(D.hi);
+  cudaFree(D.lo);
+  cudaFree(D.S);
+  cudaFree(D.F);
+  cudaFree(D.Ff);
+  cudaFree(D.rep);
+  cudaFree(D.best);
+  cudaFree(D.active);
+  cudaFree(D.workspace);
+  if (D.h_active) cudaFreeHost(D.h_active);
+  if (D.cublas) cublasDestroy(D.cublas);
+  D = DenseState();
+}
+
+cublasStatus_t gemm(DenseState &D, int m, int nn, int k, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B,
+                    int ldb, float *C, int ldc, float beta) {
+  const float alpha = 1.0f;
+  return cublasGemmEx(D.cublas, CUBLAS_OP_N, CUBLAS_OP_N, m, nn, k, &alpha, A, CUDA_R_16BF, lda, B, CUDA_R_16BF, ldb,
+                      &beta, C, CUDA_R_32F, ldc, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+}
+
+// F[:, rows] = (J_hi + J_lo)[rows, :] . S  for rows b0 .. b0+cnt
+bool fields(DenseState &D, int b0, int cnt, float *out) {
+  const int n = D.n;
+  if (gemm(D, D.Rp, cnt, n, D.S, D.Rp, D.hi + (int64_t)b0 * n, n, out, D.Rp, 0.0f) != CUBLAS_STATUS_SUCCESS)
+    return false;
+  return gemm(D, D.Rp, cnt, n, D.S, D.Rp, D.lo + (int64_t)b0 * n, n, out, D.Rp, 1.0f) == CUBLAS_STATUS_SUCCESS;
+}
+
+}  // namespace
+
+bool dense_supported(const ising_handle *h, int32_t R) {
+  return h->dense && h->d_Jdense && R >= 1 && (int64_t)h->nmax * h->nmax <= (int64_t)1 << 28;
+}
+
+void dense_free(ising_handle *h) {
+  auto &m = dense_states();
+  auto it = m.find(h);
+  if (it == m.end()) return;
+  free_state(it->second);
+  m.erase(it);
+}
+
+cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t R, int8_t *spins, double *E,
+                         int32_t *E32, int32_t *minima, const uint64_t *seeds_host, cudaStream_t s) {
+  (void)E32;
+  DenseState &D = dense_states()[h];
+  cudaError_t e;
+  const int Rp = (R + 7) / 8 * 8;
+  int64_t joff = 0;
+  for (int32_t b = 0; b < h->n_inst; ++b) {
+    const int n = h->inst[b].n;
+    if (D.n != n || D.Rp != Rp || D.inst != b) {
+      free_state(D);
+      if (cublasCreate(&D.cublas) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+      // a fixed workspace, so that the GEMMs captured into the sweep graph never allocate
+      constexpr size_t kWs = 64u << 20;
+      if ((e = cudaMalloc(&D.workspace, kWs)) != cudaSuccess) return e;
+      if (cublasSetWorkspace(D.cublas, D.workspace, kWs) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+      if ((e = cudaFuncSetAttribute(dense_decide, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(kDB * kDB * sizeof(float)))) != cudaSuccess)
+        return e;
+      D.n = n;
+      D.Rp = Rp;
+      D.inst = b;
+      if ((e = cudaMalloc(&D.hi, (size_t)n * n * 2)) != cudaSuccess) return e;
+      if ((e = cudaMalloc(&D.lo, (size_t)n * n * 2)) != cudaSuccess) return e;
+      if ((e = cudaMalloc(&D.S, (size_t)n * Rp * 2)) != cudaSuccess) return e;
+      if ((e = cudaMalloc(&D.F, (size_t)kDB * Rp * 4)) != cudaSuccess) return e;
+      if ((e = cudaMalloc(&D.Ff, (size_t)n * Rp * 4)) != cudaSuccess) return e;
+      if ((e = cudaMalloc(&D.rep, (size_t)R * sizeof(DenseRep))) != cudaSuccess) return e;
+      if ((e = cudaMalloc(&D.best, (size_t)R * n)) != cudaSuccess) return e;
+      if ((e = cudaMalloc(&D.active, 64)) != cudaSuccess) return e;
+      if ((e = cudaMallocHost(&D.h_active, 64)) != cudaSuccess) return e;
+      if ((e = cudaMemset(D.S, 0, (size_t)n * Rp * 2)) != cudaSuccess) return e;
+      dense_split<<<h->sm_count * 8, 256, 0, s>>>(h->d_Jdense + joff, D.hi, D.lo, (int64_t)n * n);
+    }
+    if (cublasSetStream(D.cublas, s) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+    const float *J = h->d_Jdense + joff;
+    const uint64_t seed = seeds_host[b];
+    const int rb = (R + 255) / 256;
+    dense_init<<<rb, 256, 0, s>>>(R, D.rep, h->d_stats);
+    // capture one sweep into a graph, replay it sweep by sweep
+    cudaStream_t cs;
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cublasSetStream(D.cublas, cs);
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    bool ok = e == cudaSuccess;
+    if (ok) {
+      dense_start<<<dim3(rb, (n + 127) / 128), 256, 0, cs>>>(n, R, Rp, seed, b, D.rep, D.S);
+      for (int b0 = 0; b0 < n && ok; b0 += kDB) {
+        const int cnt = std::min(kDB, n - b0);
+        ok = fields(D, b0, cnt, D.F);
+        dense_decide<<<rb, 256, kDB * kDB * sizeof(float), cs>>>(n, R, Rp, b0, cnt, J, D.F, D.S, D.rep);
+      }
+      cudaMemsetAsync(D.active, 0, 4, cs);
+      dense_end<<<rb, 256, 0, cs>>>(R, n, p->max_sweeps, p->sweep_budget, D.rep, D.active, h->d_stats);
+      cudaMemcpyAsync(D.h_active, D.active, 4, cudaMemcpyDeviceToHost, cs);
+      e = cudaStreamEndCapture(cs, &graph);
+      ok = ok && e == cudaSuccess;
+    }
+    if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    cublasSetStream(D.cublas, s);
+    if (!ok) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaStreamDestroy(cs);
+      return e != cudaSuccess ? e : cudaErrorUnknown;
+    }
+    for (int round = 0;; ++round) {
+      // one descent round: sweep until no replica is active
+      for (int sw = 0;; ++sw) {
+        if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) break;
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
+        if (*D.h_active == 0) break;
+      }
+      if (e != cudaSuccess) break;
+      fields(D, 0, n, D.Ff);
+      dense_energy<<<rb, 256, 0, s>>>(n, R, Rp, D.S, D.Ff, D.rep, D.best, 0);
+      cudaMemsetAsync(D.active, 0, 4, s);
+      dense_next_round<<<rb, 256, 0, s>>>(R, p->restarts, p->sweep_budget, D.rep, D.active, h->d_stats);
+      cudaMemcpyAsync(D.h_active, D.active, 4, cudaMemcpyDeviceToHost, s);
+      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
+      if (*D.h_active == 0) break;
+    }
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return e;
+    // energies of replicas that never converged: their final states
+    dense_energy<<<rb, 256, 0, s>>>(n, R, Rp, D.S, D.Ff, D.rep, D.best, 1);
+    const int64_t tot = (int64_t)R * n;
+    dense_output<<<(int)std::min<int64_t>((tot + 255) / 256, (int64_t)h->sm_count * 16), 256, 0, s>>>(
+        n, R, Rp, b, h->inst[b].spin_off, D.S, D.best, D.rep, spins, E, minima);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    joff += (int64_t)n * n;
+  }
+  return cudaSuccess;
+}
+
 }  // namespace isg

@@ -27,6 +27,8 @@ struct InstDesc {
   int64_t hyper_off;  // first hyper-edge (global id)
   int32_t n_hyper;    // hyper-edges of this instance
   int32_t max_deg;    // largest CSR row length
+  int32_t lat_L;      // side of a recognised periodic hypercubic lattice, else 0
+  int32_t lat_d;      // its dimension (2 or 3), else 0
 };
 
 // Everything a kernel needs to read an instance set.
@@ -43,6 +45,17 @@ struct DevGraph {
   const void *hJ;           // [total_edges] int8_t or float
   const int32_t *order;     // [total_spins] local spins sorted by (colour, index)
   const int32_t *cls;       // class pointers per instance (ncls + 1 each)
+  // Periodic lattices, per colour-order position v (global index spin_off + v):
+  //   meta bits 0-5   entry k of the site's CSR row wraps around the boundary
+  //        bits 8-25  direction of entry k (3 bits each: 0 +x, 1 -x, 2 +y, 3 -y, 4 +z, 5 -z)
+  //        bits 26-31 entry k has a negative coupling
+  //   Jpos[k * nsp + spin_off + v] = coupling of entry k (int8_t or float)
+  const uint32_t *meta;
+  const void *Jpos;
+  //   latinfo[spin_off + v]: bit d = the neighbour in direction d (0 +x, 1 -x,
+  //   2 +y, 3 -y, 4 +z, 5 -z) wraps around; bit 8 + d = its coupling is negative
+  const uint16_t *latinfo;
+  int64_t nsp;              // total spins (stride of Jpos)
   int32_t dtype;            // ISING_I8 / ISING_F32
 };
 
@@ -102,6 +115,11 @@ struct ising_handle {
   int32_t *d_order = nullptr;
   int32_t *d_cls = nullptr;
   float *d_Jdense = nullptr;
+  uint32_t *d_meta = nullptr;
+  uint16_t *d_latinfo = nullptr;
+  bool all_lattice = false;  // every instance is a recognised periodic lattice
+  void *d_Jpos = nullptr;
+  bool any_lattice = false;
 
   // scratch and per-call state, grown on demand
   void *d_scratch = nullptr;

@@ -1,9 +1,835 @@
-// sweep.cu — large-instance sweeps (filled in below).
-#include "internal.h"
+// sweep.cu — large instances (too big for one CTA's shared memory): every
+// colour class is one launch over the whole GPU; a sweep is the sequence of
+// class launches plus small bookkeeping launches, and chunks of sweeps are
+// captured once into a CUDA graph and replayed until every replica is done.
+//
+// Same method and semantics as the tile kernels (García & Markov, Sec. IV:
+// improving single-spin moves, repeated sweeps to a 1-flip minimum, random
+// restarts, best kept; incremental FP32 field updates for float couplings with
+// an FP64 refresh).  State lives in global memory: spin words sw[g][n] (bit l =
+// replica 32g + l), flip masks fm[g][n], best words bw[g][n], FP32 fields
+// F[g][position][LPS] stored in colour-class order so a class reads them
+// contiguously.  LPS (lanes per spin) = 32, 16 or 8 replicas share one warp
+// visit; with LPS < 32 a warp visits 32/LPS spins at once.
+//
+// Periodic lattices use the compact per-site metadata (DevGraph::meta/Jpos)
+// instead of the CSR: 4 bytes of neighbour directions and coupling signs plus
+// the couplings in class order, all read contiguously.
+#include <cfloat>
+#include <cstdio>
+#include <cstdlib>
+
+#include "device_common.cuh"
 
 namespace isg {
-cudaError_t launch_sweep(ising_handle *, const ising_search_params *, int32_t, cudaStream_t) {
-  return cudaErrorNotSupported;
+
+namespace {
+
+constexpr int kST = 256;  // threads per CTA
+
+struct GroupState {
+  uint32_t lane_valid, active, convround, any, upd, start;
+  int32_t k, d, done, round_end, final_pass, pad;
+  int32_t total[32], minima[32];
+  double best[32], E[32];
+};
+
+struct SweepArgs {
+  DevGraph g;
+  InstDesc I;
+  int32_t b, R, G, LPS;
+  int32_t max_sweeps, restarts, budget, refresh, sequential, lattice;
+  uint64_t seed;
+  uint32_t *sw, *fm, *bw;
+  float *F;
+  GroupState *gs;
+  double *partial;  // [grid_e][G][32]
+  int32_t grid_e;
+  unsigned int *counter;
+  int32_t *all_done;
+  unsigned long long *stats;
+  int8_t *spins;
+  double *energy;
+  int32_t *energy_i32;
+  int32_t *minima;
+};
+
+__device__ __forceinline__ int lat_nbr(int j, uint32_t meta, int k, int L) {
+  const int dir = (meta >> (8 + 3 * k)) & 7;
+  const int a = dir >> 1;
+  const int stride = a == 0 ? 1 : (a == 1 ? L : L * L);
+  int off = (dir & 1) ? -stride : stride;
+  if ((meta >> k) & 1u) off += (dir & 1) ? L * stride : -L * stride;
+  return j + off;
 }
-void sweep_free(ising_handle *) {}
+
+__global__ void sweep_init(SweepArgs A) {
+  const int g = threadIdx.x;
+  if (g < A.G) {
+    GroupState &S = A.gs[g];
+    const int rem = A.R - 32 * g;
+    const int lanes = rem >= A.LPS ? A.LPS : rem;
+    S.lane_valid = lanes >= 32 ? 0xffffffffu : ((1u << lanes) - 1u);
+    S.start = S.lane_valid;
+    S.active = S.lane_valid;
+    S.convround = S.any = S.upd = 0;
+    S.k = 0;
+    S.d = 0;
+    S.done = 0;
+    S.round_end = 0;
+    S.final_pass = 0;
+    for (int r = 0; r < 32; ++r) {
+      S.total[r] = 0;
+      S.minima[r] = 0;
+      S.best[r] = DBL_MAX;
+      S.E[r] = 0.0;
+    }
+    atomicAdd(A.stats + 3, (unsigned long long)__popc(S.start));
+  }
+  if (threadIdx.x == 0) {
+    *A.counter = 0;
+    *A.all_done = 0;
+  }
+}
+
+// One colour class of one sweep.  MODE 0 int lanes, 1 FP32 lanes, 2 multi-spin coded.
+template <int MODE, int LPS, bool LAT>
+__global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
+  __shared__ uint32_t s_any[32];
+  __shared__ unsigned long long s_red[kST / 32];
+  const DevGraph &G = A.g;
+  const InstDesc &I = A.I;
+  const int n = I.n;
+  const int tid = threadIdx.x, lane = threadIdx.x & 31;
+  if (tid < 32) s_any[tid] = 0;
+  __syncthreads();
+  int c0, c1;
+  if (A.sequential) {
+    c0 = c;
+    c1 = c + 1;
+  } else {
+    c0 = __ldg(G.cls + I.cls_off + c);
+    c1 = __ldg(G.cls + I.cls_off + c + 1);
+  }
+  const int cs = c1 - c0;
+  unsigned long long my_flips = 0;
+  constexpr uint32_t lmask = LPS == 32 ? 0xffffffffu : ((1u << LPS) - 1u);
+  const int L = I.lat_L;
+
+  if (MODE == 2) {
+    const int8_t *hi = reinterpret_cast<const int8_t *>(G.h);
+    const int8_t *Ji = reinterpret_cast<const int8_t *>(G.J);
+    const int64_t items = (int64_t)A.G * cs;
+    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + tid; it < items; it += (int64_t)gridDim.x * blockDim.x) {
+      const int g = (int)(it / cs);
+      const int v = c0 + (int)(it % cs);
+      const uint32_t active = A.gs[g].active;
+      if (!active) continue;
+      const int j = A.sequential ? v : __ldg(G.order + I.spin_off + v);
+      const int64_t gj = I.spin_off + j;
+      const uint32_t *swg = A.sw + (size_t)g * n;
+      const uint32_t wj = swg[j];
+      uint32_t q0 = 0, q1 = 0, q2 = 0, q3 = 0;
+      int deg;
+      if (LAT) {
+        const uint32_t meta = __ldg(G.meta + I.spin_off + v);
+        deg = 2 * I.lat_d;
+        for (int k = 0; k < deg; ++k) {
+          const int i = lat_nbr(j, meta, k, L);
+          uint32_t x = wj ^ swg[i] ^ (((meta >> (26 + k)) & 1u) ? 0xffffffffu : 0u);
+          uint32_t cy = q0 & x;
+          q0 ^= x;
+          x = cy;
+          cy = q1 & x;
+          q1 ^= x;
+          x = cy;
+          cy = q2 & x;
+          q2 ^= x;
+          q3 ^= cy;
+        }
+      } else {
+        const uint32_t k0 = __ldg(G.row + gj), k1 = __ldg(G.row + gj + 1);
+        deg = (int)(k1 - k0);
+        for (uint32_t kk = k0; kk < k1; ++kk) {
+          uint32_t x = wj ^ swg[__ldg(G.col + kk)] ^ (__ldg(Ji + kk) < 0 ? 0xffffffffu : 0u);
+          uint32_t cy = q0 & x;
+          q0 ^= x;
+          x = cy;
+          cy = q1 & x;
+          q1 ^= x;
+          x = cy;
+          cy = q2 & x;
+          q2 ^= x;
+          q3 ^= cy;
+        }
+      }
+      const int hv = __ldg(hi + gj);
+      uint32_t flip;
+      auto ge = [&](int t) -> uint32_t {
+        if (t <= 0) return 0xffffffffu;
+        if (t > 15) return 0u;
+        uint32_t gt = 0, eq = 0xffffffffu;
+        const uint32_t qq[4] = {q0, q1, q2, q3};
+#pragma unroll
+        for (int p = 3; p >= 0; --p) {
+          const uint32_t tb = ((t >> p) & 1) ? 0xffffffffu : 0u;
+          gt |= eq & qq[p] & ~tb;
+          eq &= ~(qq[p] ^ tb);
+        }
+        return gt | eq;
+      };
+      if (hv == 0) {
+        flip = ge(deg / 2 + 1);
+      } else {
+        const uint32_t plus = hv > 0 ? wj : ~wj;
+        flip = (ge((deg + 1) / 2 + 1) & plus) | (ge(deg >= 1 ? (deg - 1) / 2 + 1 : 0) & ~plus);
+      }
+      flip &= active & lmask;
+      if (flip) {
+        A.sw[(size_t)g * n + j] = wj ^ flip;
+        atomicOr(&s_any[g], flip);
+        my_flips += __popc(flip);
+      }
+    }
+  } else {
+    constexpr int SPW = 32 / LPS;
+    const int sub = lane / LPS, ln = lane % LPS;
+    const int witems_per_g = (cs + SPW - 1) / SPW;
+    const int64_t witems = (int64_t)A.G * witems_per_g;
+    const int64_t wstride = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t wi = (int64_t)blockIdx.x * (blockDim.x / 32) + (tid >> 5); wi < witems; wi += wstride) {
+      const int g = (int)(wi / witems_per_g);
+      const int v = c0 + (int)(wi % witems_per_g) * SPW + sub;
+      const GroupState &S = A.gs[g];
+      const uint32_t active = S.active;
+      if (!active) continue;  // warp-uniform: g is uniform in the warp
+      const bool valid = v < c1;
+      const int j = valid ? (A.sequential ? v : __ldg(G.order + I.spin_off + v)) : 0;
+      const int64_t gj = I.spin_off + j;
+      const uint32_t *swg = A.sw + (size_t)g * n;
+      const uint32_t *fmg = A.fm + (size_t)g * n;
+      const uint32_t wj = valid ? swg[j] : 0u;
+      const bool up = (wj >> ln) & 1u;
+      bool flip = false;
+      if (valid) {
+        const uint32_t meta = LAT ? __ldg(G.meta + I.spin_off + v) : 0u;
+        const uint32_t k0 = LAT ? 0u : __ldg(G.row + gj);
+        const uint32_t k1 = LAT ? (uint32_t)(2 * I.lat_d) : __ldg(G.row + gj + 1);
+        const uint32_t e0 = __ldg(G.inc_ptr + gj), e1 = __ldg(G.inc_ptr + gj + 1);
+        if (MODE == 0) {
+          int f = __ldg(reinterpret_cast<const int8_t *>(G.h) + gj);
+          for (uint32_t kk = k0; kk < k1; ++kk) {
+            int i, w;
+            if (LAT) {
+              i = lat_nbr(j, meta, (int)kk, L);
+              w = __ldg(reinterpret_cast<const int8_t *>(G.Jpos) + (int64_t)kk * G.nsp + I.spin_off + v);
+            } else {
+              i = __ldg(G.col + kk);
+              w = __ldg(reinterpret_cast<const int8_t *>(G.J) + kk);
+            }
+            f += ((swg[i] >> ln) & 1u) ? w : -w;
+          }
+          for (uint32_t q = e0; q < e1; ++q) {
+            const int e = __ldg(G.inc_edge + q);
+            uint32_t neg = 0;
+            for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
+              const int mm = __ldg(G.hmem + m);
+              if (mm != j) neg ^= ~(swg[mm] >> ln) & 1u;
+            }
+            const int w = __ldg(reinterpret_cast<const int8_t *>(G.hJ) + e);
+            f += neg ? -w : w;
+          }
+          flip = up ? (f < 0) : (f > 0);
+        } else {
+          const int d = S.d;
+          const bool refresh = (d == 0) || (A.refresh > 0 && d % A.refresh == 0);
+          float *Fp = A.F + ((size_t)g * n + v) * LPS + ln;
+          const float *hJ = reinterpret_cast<const float *>(G.hJ);
+          float f;
+          if (refresh) {
+            double acc = (double)__ldg(reinterpret_cast<const float *>(G.h) + gj);
+            for (uint32_t kk = k0; kk < k1; ++kk) {
+              int i;
+              double w;
+              if (LAT) {
+                i = lat_nbr(j, meta, (int)kk, L);
+                w = (double)__ldg(reinterpret_cast<const float *>(G.Jpos) + (int64_t)kk * G.nsp + I.spin_off + v);
+              } else {
+                i = __ldg(G.col + kk);
+                w = (double)__ldg(reinterpret_cast<const float *>(G.J) + kk);
+              }
+              acc = __dadd_rn(acc, ((swg[i] >> ln) & 1u) ? w : -w);
+            }
+            for (uint32_t q = e0; q < e1; ++q) {
+              const int e = __ldg(G.inc_edge + q);
+              uint32_t neg = 0;
+              for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
+                const int mm = __ldg(G.hmem + m);
+                if (mm != j) neg ^= ~(swg[mm] >> ln) & 1u;
+              }
+              const double w = (double)__ldg(hJ + e);
+              acc = __dadd_rn(acc, neg ? -w : w);
+            }
+            f = __double2float_rn(acc);
+            *Fp = f;
+          } else {
+            f = *Fp;
+            bool changed = false;
+            for (uint32_t kk = k0; kk < k1; ++kk) {
+              int i;
+              if (LAT) i = lat_nbr(j, meta, (int)kk, L);
+              else i = __ldg(G.col + kk);
+              if ((fmg[i] >> ln) & 1u) {
+                float w2;
+                if (LAT)
+                  w2 = 2.0f * __ldg(reinterpret_cast<const float *>(G.Jpos) + (int64_t)kk * G.nsp + I.spin_off + v);
+                else
+                  w2 = 2.0f * __ldg(reinterpret_cast<const float *>(G.J) + kk);
+                f = __fadd_rn(f, ((swg[i] >> ln) & 1u) ? w2 : -w2);
+                changed = true;
+              }
+            }
+            for (uint32_t q = e0; q < e1; ++q) {
+              const int e = __ldg(G.inc_edge + q);
+              uint32_t neg = 0, par = 0;
+              for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
+                const int mm = __ldg(G.hmem + m);
+                if (mm != j) {
+                  neg ^= ~(swg[mm] >> ln) & 1u;
+                  par ^= (fmg[mm] >> ln) & 1u;
+                }
+              }
+              if (par) {
+                const float w2 = 2.0f * __ldg(hJ + e);
+                f = __fadd_rn(f, neg ? -w2 : w2);
+                changed = true;
+              }
+            }
+            if (changed) *Fp = f;
+          }
+          flip = up ? (f < 0.0f) : (f > 0.0f);
+        }
+        flip = flip && ((active >> ln) & 1u);
+      }
+      const uint32_t m = __ballot_sync(0xffffffffu, flip);
+      const uint32_t seg = (m >> (sub * LPS)) & lmask;
+      if (valid && ln == 0) {
+        if (seg) A.sw[(size_t)g * n + j] = wj ^ seg;
+        if (MODE == 1) {
+          if (seg || A.fm[(size_t)g * n + j]) A.fm[(size_t)g * n + j] = seg;
+        }
+        if (seg) atomicOr(&s_any[g], seg);
+      }
+      my_flips += flip ? 1 : 0;
+    }
+  }
+  __syncthreads();
+  if (tid < A.G && s_any[tid]) atomicOr(&A.gs[tid].any, s_any[tid]);
+  my_flips = block_sum(my_flips, s_red);
+  if (tid == 0 && my_flips) atomicAdd(A.stats + 1, my_flips);
+}
+
+// End of a sweep: per group, which lanes converged, which descents ended.
+__global__ void sweep_end(SweepArgs A) {
+  const int g = threadIdx.x;
+  if (g >= A.G) return;
+  GroupState &S = A.gs[g];
+  S.start = 0;
+  S.upd = 0;
+  const uint32_t active = S.active;
+  if (!active) return;
+  const uint32_t any = S.any;
+  S.any = 0;
+  uint32_t ended = 0;
+  for (int r = 0; r < 32; ++r)
+    if ((active >> r) & 1u) {
+      S.total[r] += 1;
+      if (A.budget > 0 && S.total[r] >= A.budget) ended |= 1u << r;
+    }
+  const uint32_t conv = active & ~any;
+  ended |= conv;
+  S.d += 1;
+  if (S.d >= A.max_sweeps) ended |= active;
+  atomicAdd(A.stats + 4, (unsigned long long)__popc(active));
+  atomicAdd(A.stats + 0, (unsigned long long)__popc(active) * (unsigned long long)A.I.n);
+  atomicAdd(A.stats + 2, (unsigned long long)__popc(conv));
+  S.convround |= conv;
+  S.active = active & ~ended;
+  if (!S.active) S.round_end = 1;
+}
+
+// Energies of the lanes whose round ended (all lanes of the group at once,
+// lane-parallel, FP64 or exact int64), then - in the last CTA to finish - the
+// round's bookkeeping: minima, best energies, the next descent's lanes.
+template <bool FLOAT, int LPS, bool LAT>
+__global__ void __launch_bounds__(kST) sweep_energy(SweepArgs A) {
+  __shared__ double s_red[kST / 32][32];
+  __shared__ bool s_last;
+  const DevGraph &G = A.g;
+  const InstDesc &I = A.I;
+  const int n = I.n, L = I.lat_L;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  bool any = false;
+  for (int g = 0; g < A.G; ++g) any = any || A.gs[g].round_end || A.gs[g].final_pass;
+  if (!any) return;
+  constexpr int SPW = 32 / LPS;
+  const int sub = lane / LPS, ln = lane % LPS;
+  for (int g = 0; g < A.G; ++g) {
+    const GroupState &S = A.gs[g];
+    double accd = 0.0;
+    long long acci = 0;
+    if (S.round_end || S.final_pass) {
+      const uint32_t *swg = A.sw + (size_t)g * n;
+      const int64_t wtot = (n + SPW - 1) / SPW;
+      for (int64_t wi = (int64_t)blockIdx.x * nw + warp; wi < wtot; wi += (int64_t)gridDim.x * nw) {
+        const int v = (int)(wi * SPW + sub);
+        if (v >= n) continue;
+        const int j = (LAT && !A.sequential) ? __ldg(G.order + I.spin_off + v) : v;
+        const int64_t gj = I.spin_off + j;
+        const uint32_t bj = (swg[j] >> ln) & 1u;
+        const uint32_t meta = LAT ? __ldg(G.meta + I.spin_off + v) : 0u;
+        const uint32_t k0 = LAT ? 0u : __ldg(G.row + gj);
+        const uint32_t k1 = LAT ? (uint32_t)(2 * I.lat_d) : __ldg(G.row + gj + 1);
+        if (FLOAT) {
+          double e = (double)__ldg(reinterpret_cast<const float *>(G.h) + gj);
+          e = bj ? e : -e;
+          for (uint32_t kk = k0; kk < k1; ++kk) {
+            int i;
+            double w;
+            if (LAT) {
+              i = lat_nbr(j, meta, (int)kk, L);
+              w = (double)__ldg(reinterpret_cast<const float *>(G.Jpos) + (int64_t)kk * G.nsp + I.spin_off + v);
+            } else {
+              i = __ldg(G.col + kk);
+              w = (double)__ldg(reinterpret_cast<const float *>(G.J) + kk);
+            }
+            if (i > j) e += (((swg[i] >> ln) & 1u) ^ bj) ? -w : w;
+          }
+          accd -= e;
+        } else {
+          const int hv = __ldg(reinterpret_cast<const int8_t *>(G.h) + gj);
+          int e = bj ? hv : -hv;
+          for (uint32_t kk = k0; kk < k1; ++kk) {
+            int i, w;
+            if (LAT) {
+              i = lat_nbr(j, meta, (int)kk, L);
+              w = __ldg(reinterpret_cast<const int8_t *>(G.Jpos) + (int64_t)kk * G.nsp + I.spin_off + v);
+            } else {
+              i = __ldg(G.col + kk);
+              w = __ldg(reinterpret_cast<const int8_t *>(G.J) + kk);
+            }
+            if (i > j) e += (((swg[i] >> ln) & 1u) ^ bj) ? -w : w;
+          }
+          acci -= e;
+        }
+      }
+      // hyper-edges (CSR instances only)
+      for (int64_t wi = (int64_t)blockIdx.x * nw + warp; wi < (I.n_hyper + SPW - 1) / SPW;
+           wi += (int64_t)gridDim.x * nw) {
+        const int e = (int)(wi * SPW + sub);
+        if (e >= I.n_hyper) continue;
+        const int64_t ge = I.hyper_off + e;
+        uint32_t neg = 0;
+        for (uint32_t q = __ldg(G.hptr + ge), qe = __ldg(G.hptr + ge + 1); q < qe; ++q)
+          neg ^= ~(swg[__ldg(G.hmem + q)] >> ln) & 1u;
+        if (FLOAT) {
+          const double w = (double)__ldg(reinterpret_cast<const float *>(G.hJ) + ge);
+          accd -= neg ? -w : w;
+        } else {
+          const int w = __ldg(reinterpret_cast<const int8_t *>(G.hJ) + ge);
+          acci -= neg ? -w : w;
+        }
+      }
+    }
+    // lanes of the SPW sub-warps hold different spins of the same replica: fold them
+    if (FLOAT) {
+      for (int o = LPS; o < 32; o <<= 1) accd += __shfl_xor_sync(0xffffffffu, accd, o);
+    } else {
+      for (int o = LPS; o < 32; o <<= 1) acci += __shfl_xor_sync(0xffffffffu, acci, o);
+    }
+    __syncthreads();
+    s_red[warp][lane] = FLOAT ? accd : (double)acci;
+    __syncthreads();
+    if (warp == 0) {
+      double a = s_red[0][lane];
+      for (int w = 1; w < nw; ++w) a += s_red[w][lane];
+      A.partial[((size_t)blockIdx.x * A.G + g) * 32 + lane] = a;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(A.counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // last CTA: totals in CTA order, then per-group bookkeeping
+  for (int g = 0; g < A.G; ++g) {
+    GroupState &S = A.gs[g];
+    if (!(S.round_end || S.final_pass)) continue;
+    if (warp == 0) {
+      double a = 0.0;
+      for (int cta = 0; cta < (int)gridDim.x; ++cta) a += A.partial[((size_t)cta * A.G + g) * 32 + lane];
+      S.E[lane] = a;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      if (S.final_pass) {
+        S.final_pass = 0;
+      } else {
+        uint32_t upd = 0;
+        const uint32_t cr = S.convround;
+        for (int r = 0; r < 32; ++r)
+          if ((cr >> r) & 1u) {
+            S.minima[r] += 1;
+            if (S.E[r] < S.best[r]) {
+              S.best[r] = S.E[r];
+              upd |= 1u << r;
+            }
+          }
+        S.upd = upd;
+        S.k += 1;
+        uint32_t start = 0;
+        if (S.k < A.restarts)
+          for (int r = 0; r < 32; ++r)
+            if (((S.lane_valid >> r) & 1u) && (A.budget <= 0 || S.total[r] < A.budget)) start |= 1u << r;
+        S.start = start;
+        S.active = start;
+        S.convround = 0;
+        S.d = 0;
+        S.round_end = 0;
+        if (!start) S.done = 1;
+        atomicAdd(A.stats + 3, (unsigned long long)__popc(start));
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    int all = 1;
+    for (int g = 0; g < A.G; ++g) all = all && A.gs[g].done;
+    *A.all_done = all;
+    *A.counter = 0;
+  }
+}
+
+// Best-state copies and random starts decided by the last bookkeeping pass.
+// One warp owns a block of 128 sites: it first copies the improved lanes'
+// current words into the best-state words, then draws the new starts for the
+// same sites, so the copy never sees a new start.
+template <int LPS>
+__global__ void __launch_bounds__(kST) sweep_restart(SweepArgs A) {
+  const int n = A.I.n;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int g = 0; g < A.G; ++g) {
+    const GroupState &S = A.gs[g];
+    const uint32_t upd = S.upd, start = S.start;
+    if (!(upd | start)) continue;
+    const int nwb = (n + 127) / 128;
+    uint32_t *swg = A.sw + (size_t)g * n;
+    uint32_t *bwg = A.bw + (size_t)g * n;
+    uint32_t *fmg = A.fm + (size_t)g * n;
+    for (int w = blockIdx.x * nw + warp; w < nwb; w += gridDim.x * nw) {
+      if (upd)
+        for (int t = lane; t < 128; t += 32) {
+          const int i = w * 128 + t;
+          if (i < n) bwg[i] = (bwg[i] & ~upd) | (swg[i] & upd);
+        }
+      __syncwarp();
+      if (start) {
+        const uint4 x = start_bits(A.seed, (uint32_t)w, (uint32_t)(32 * g + lane), (uint32_t)S.k, (uint32_t)A.b);
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t xw = word_of(x, q);
+          for (int u = 0; u < 32; ++u) {
+            const int i = w * 128 + q * 32 + u;
+            if (i >= n) break;
+            const uint32_t m = __ballot_sync(0xffffffffu, (xw >> u) & 1u);
+            if (lane == 0) {
+              swg[i] = (swg[i] & ~start) | (m & start);
+              fmg[i] &= ~start;
+            }
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+__global__ void sweep_mark_final(SweepArgs A) {
+  const int g = threadIdx.x;
+  if (g >= A.G) return;
+  GroupState &S = A.gs[g];
+  uint32_t need = 0;
+  for (int r = 0; r < 32; ++r)
+    if (((S.lane_valid >> r) & 1u) && S.minima[r] == 0) need |= 1u << r;
+  S.final_pass = need ? 1 : 0;
+  if (threadIdx.x == 0) *A.counter = 0;
+}
+
+__global__ void sweep_output(SweepArgs A) {
+  const int n = A.I.n;
+  const int64_t tot = (int64_t)A.R * n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / n), i = (int)(t % n);
+    const int g = r / 32, l = r % 32;
+    const GroupState &S = A.gs[g];
+    const uint32_t w = S.minima[l] > 0 ? A.bw[(size_t)g * n + i] : A.sw[(size_t)g * n + i];
+    A.spins[(int64_t)A.R * A.I.spin_off + t] = ((w >> l) & 1u) ? 1 : -1;
+  }
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < A.R) {
+    const int g = (int)t / 32, l = (int)t % 32;
+    const GroupState &S = A.gs[g];
+    const double e = S.minima[l] > 0 ? S.best[l] : S.E[l];
+    const int64_t o = (int64_t)A.b * A.R + t;
+    A.energy[o] = e;
+    if (A.energy_i32) A.energy_i32[o] = (int32_t)e;
+    if (A.minima) A.minima[o] = S.minima[l];
+  }
+}
+
+struct SweepState {
+  size_t bytes = 0;
+  void *mem = nullptr;
+  int32_t *h_done = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+
+std::map<const ising_handle *, SweepState> &sweep_states() {
+  static std::map<const ising_handle *, SweepState> m;
+  return m;
+}
+
+// ISING_SWEEP_DEBUG=1: launch without graphs, synchronise and report after
+// every launch (diagnostics only).
+bool sweep_debug() {
+  static const int on = [] {
+    const char *v = std::getenv("ISING_SWEEP_DEBUG");
+    return v && v[0] == '1' ? 1 : 0;
+  }();
+  return on != 0;
+}
+
+void debug_step(const char *what, int c, cudaStream_t s) {
+  if (!sweep_debug()) return;
+  const cudaError_t e1 = cudaGetLastError();
+  const cudaError_t e2 = cudaStreamSynchronize(s);
+  std::fprintf(stderr, "[sweep] %s %d: launch=%s sync=%s\n", what, c, cudaGetErrorString(e1), cudaGetErrorString(e2));
+  std::fflush(stderr);
+}
+
+template <int MODE, int LPS, bool LAT>
+void enqueue_visit(const SweepArgs &A, int c, int grid, cudaStream_t s) {
+  sweep_visit<MODE, LPS, LAT><<<grid, kST, 0, s>>>(A, c);
+  debug_step("visit", c, s);
+}
+
+template <int LPS, bool LAT>
+void enqueue_sweep(const SweepArgs &A, int mode, int ncls, int grid_v, cudaStream_t s) {
+  for (int c = 0; c < ncls; ++c) {
+    if (mode == 0) enqueue_visit<0, LPS, LAT>(A, c, grid_v, s);
+    else if (mode == 1) enqueue_visit<1, LPS, LAT>(A, c, grid_v, s);
+    else enqueue_visit<2, LPS, LAT>(A, c, grid_v, s);
+  }
+  sweep_end<<<1, 32, 0, s>>>(A);
+  debug_step("end", 0, s);
+  if (mode == 1) sweep_energy<true, LPS, LAT><<<A.grid_e, kST, 0, s>>>(A);
+  else sweep_energy<false, LPS, LAT><<<A.grid_e, kST, 0, s>>>(A);
+  debug_step("energy", 0, s);
+  sweep_restart<LPS><<<A.grid_e, kST, 0, s>>>(A);
+  debug_step("restart", 0, s);
+}
+
+// Load every kernel of this configuration before any graph capture, so the
+// capture never triggers module loading.
+template <int LPS, bool LAT>
+cudaError_t preload(int mode) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaSuccess;
+  if (mode == 0) e = cudaFuncGetAttributes(&fa, sweep_visit<0, LPS, LAT>);
+  else if (mode == 1) e = cudaFuncGetAttributes(&fa, sweep_visit<1, LPS, LAT>);
+  else e = cudaFuncGetAttributes(&fa, sweep_visit<2, LPS, LAT>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, sweep_end);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, sweep_energy<true, LPS, LAT>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, sweep_energy<false, LPS, LAT>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, sweep_restart<LPS>);
+  return e;
+}
+
+template <int LPS, bool LAT>
+cudaError_t run_instance(ising_handle *h, SweepArgs A, int mode, cudaStream_t s) {
+  SweepState &S = sweep_states()[h];
+  const InstDesc &I = A.I;
+  const int ncls = A.sequential ? I.n : I.ncls;
+  int maxcls = 1;
+  if (A.sequential) maxcls = 1;
+  else
+    for (int c = 0; c < I.ncls; ++c)
+      maxcls = std::max(maxcls, h->h_cls[I.cls_off + c + 1] - h->h_cls[I.cls_off + c]);
+  const int64_t items = mode == 2 ? (int64_t)A.G * maxcls : (int64_t)A.G * ((maxcls + 32 / LPS - 1) / (32 / LPS)) * 32;
+  const int grid_v = (int)std::max<int64_t>(1, std::min<int64_t>((items + kST - 1) / kST, (int64_t)h->sm_count * 8));
+  if (sweep_debug())
+    std::fprintf(stderr, "[sweep] n=%d ncls=%d G=%d LPS=%d mode=%d grid_v=%d grid_e=%d lattice=%d seq=%d\n", I.n,
+                 ncls, A.G, LPS, mode, grid_v, A.grid_e, A.lattice, A.sequential);
+  cudaError_t e0 = preload<LPS, LAT>(mode);
+  if (e0 != cudaSuccess) return e0;
+  sweep_init<<<1, 32, 0, s>>>(A);
+  debug_step("init", 0, s);
+  sweep_restart<LPS><<<A.grid_e, kST, 0, s>>>(A);
+  debug_step("restart0", 0, s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // Capture a chunk of sweeps once and replay it until every group is done.
+  // A graph holds at most kMaxNodes launches; when one sweep alone needs more
+  // (many colour classes, e.g. the sequential schedule) sweeps are launched
+  // directly instead.
+  constexpr int kMaxNodes = 512;
+  const int per_sweep = ncls + 3;
+  const bool use_graph = per_sweep <= kMaxNodes && !sweep_debug();
+  const int chunk = use_graph ? std::max(1, std::min(16, kMaxNodes / per_sweep)) : 1;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cs = nullptr;
+  // the first sweep runs with direct launches, the rest from the graph
+  enqueue_sweep<LPS, LAT>(A, mode, ncls, grid_v, s);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (use_graph) {
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      for (int k = 0; k < chunk; ++k) enqueue_sweep<LPS, LAT>(A, mode, ncls, grid_v, cs);
+      e = cudaStreamEndCapture(cs, &graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaStreamDestroy(cs);
+      return e;
+    }
+  }
+  // upper bound on the sweeps any group can need
+  int64_t max_sweeps_total = (int64_t)A.restarts * A.max_sweeps + A.restarts;
+  if (A.budget > 0) max_sweeps_total = std::min<int64_t>(max_sweeps_total, (int64_t)A.R * A.budget + A.max_sweeps);
+  const int64_t max_chunks = max_sweeps_total / chunk + 2;
+  int64_t launched = 0;
+  for (;;) {
+    if (use_graph) {
+      if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) break;
+    } else {
+      enqueue_sweep<LPS, LAT>(A, mode, ncls, grid_v, s);
+      if ((e = cudaGetLastError()) != cudaSuccess) break;
+    }
+    cudaMemcpyAsync(S.h_done + (launched & 1), A.all_done, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    cudaEventRecord(S.ev[launched & 1], s);
+    ++launched;
+    if (sweep_debug()) std::fprintf(stderr, "[sweep] chunk %lld queued\n", (long long)launched);
+    if (launched >= 2) {
+      // look one chunk behind so the GPU always has queued work
+      cudaEventSynchronize(S.ev[launched & 1]);
+      if (S.h_done[launched & 1]) break;
+    }
+    if (launched >= max_chunks) break;
+  }
+  if (use_graph) {
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+  }
+  if (e != cudaSuccess) return e;
+  // energies of the final states of replicas that never converged
+  sweep_mark_final<<<1, 32, 0, s>>>(A);
+  if (mode == 1) sweep_energy<true, LPS, LAT><<<A.grid_e, kST, 0, s>>>(A);
+  else sweep_energy<false, LPS, LAT><<<A.grid_e, kST, 0, s>>>(A);
+  const int64_t tot = (int64_t)A.R * I.n;
+  sweep_output<<<(int)std::min<int64_t>((tot + kST - 1) / kST, (int64_t)h->sm_count * 16), kST, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+void sweep_free(ising_handle *h) {
+  auto &m = sweep_states();
+  auto it = m.find(h);
+  if (it == m.end()) return;
+  cudaFree(it->second.mem);
+  if (it->second.h_done) cudaFreeHost(it->second.h_done);
+  for (auto &e : it->second.ev)
+    if (e) cudaEventDestroy(e);
+  m.erase(it);
+}
+
+cudaError_t launch_sweep(ising_handle *h, const ising_search_params *p, int32_t R, int8_t *spins, double *E,
+                         int32_t *E32, int32_t *minima, const uint64_t *seeds_host, cudaStream_t s) {
+  SweepState &S = sweep_states()[h];
+  const int LPS = R > 16 ? 32 : (R > 8 ? 16 : 8);
+  const int G = (R + 31) / 32;
+  if (LPS < 32 && R > LPS) return cudaErrorInvalidValue;
+  const bool fl = h->dtype == ISING_F32;
+  const int mode = fl ? 1 : (h->msc_ok ? 2 : 0);
+  const int grid_e = h->sm_count * 4;
+  // scratch: sw, fm, bw [G][nmax]; F [G][nmax][LPS]; gs [G]; partial [grid_e][G][32]; counter; done
+  const size_t words = (size_t)G * h->nmax;
+  auto up256 = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t need = 3 * up256(words * 4) + (fl ? up256(words * LPS * 4) : 0) + up256(G * sizeof(GroupState)) +
+                      up256((size_t)grid_e * G * 32 * 8) + 2 * 256;
+  cudaError_t e;
+  if (need > S.bytes) {
+    cudaFree(S.mem);
+    S.mem = nullptr;
+    S.bytes = 0;
+    if ((e = cudaMalloc(&S.mem, need)) != cudaSuccess) return e;
+    S.bytes = need;
+  }
+  if (!S.h_done && (e = cudaMallocHost(&S.h_done, 2 * sizeof(int32_t))) != cudaSuccess) return e;
+  for (auto &ev : S.ev)
+    if (!ev && (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+  char *base = (char *)S.mem;
+  auto take = [&](size_t bytes) {
+    char *p0 = base;
+    base += (bytes + 255) / 256 * 256;
+    return (void *)p0;
+  };
+  SweepArgs A;
+  A.g = h->graph();
+  A.R = R;
+  A.G = G;
+  A.LPS = LPS;
+  A.max_sweeps = p->max_sweeps;
+  A.restarts = p->restarts;
+  A.budget = p->sweep_budget;
+  A.refresh = p->refresh_every;
+  A.sequential = p->schedule == ISING_SCHED_SEQUENTIAL ? 1 : 0;
+  A.sw = (uint32_t *)take(words * 4);
+  A.fm = (uint32_t *)take(words * 4);
+  A.bw = (uint32_t *)take(words * 4);
+  A.F = fl ? (float *)take(words * LPS * 4) : nullptr;
+  A.gs = (GroupState *)take(G * sizeof(GroupState));
+  A.grid_e = grid_e;
+  A.partial = (double *)take((size_t)grid_e * G * 32 * 8);
+  A.counter = (unsigned int *)take(64);
+  A.all_done = (int32_t *)take(64);
+  A.stats = h->d_stats;
+  A.spins = spins;
+  A.energy = E;
+  A.energy_i32 = E32;
+  A.minima = minima;
+  for (int32_t b = 0; b < h->n_inst; ++b) {
+    A.I = h->inst[b];
+    A.b = b;
+    A.seed = seeds_host[b];
+    A.lattice = (A.I.lat_d > 0 && !A.sequential) ? 1 : 0;
+    if ((e = cudaMemsetAsync(A.fm, 0, words * 4, s)) != cudaSuccess) return e;
+    if (A.lattice) {
+      if (LPS == 32) e = run_instance<32, true>(h, A, mode, s);
+      else if (LPS == 16) e = run_instance<16, true>(h, A, mode, s);
+      else e = run_instance<8, true>(h, A, mode, s);
+    } else {
+      if (LPS == 32) e = run_instance<32, false>(h, A, mode, s);
+      else if (LPS == 16) e = run_instance<16, false>(h, A, mode, s);
+      else e = run_instance<8, false>(h, A, mode, s);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 }  // namespace isg

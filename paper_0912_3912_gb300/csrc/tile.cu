@@ -19,7 +19,9 @@
 //   MODE 2  multi-spin coding for J in {-1,+1}, h in {-1,0,+1}: one thread per
 //           spin evaluates all 32 replicas with bitwise logic (unsatisfied-bond
 //           masks counted in a bit-sliced adder, compared with the per-field
-//           thresholds).
+//           thresholds);
+//   MODE 3  the same on periodic 2-d/3-d lattices, with neighbours computed
+//           from the lattice geometry and the field folded into the count.
 // Replicas of a tile run their descents in lockstep rounds: descent k of every
 // lane starts together; a lane whose descent ended waits (masked) until the
 // round ends.  Each replica's own sequence of states is exactly the one its
@@ -32,64 +34,146 @@ namespace isg {
 
 namespace {
 
-// Energy of replica lane r of the tile (Eq. 1 + Eq. 6), FP64 (exact for
-// integer couplings), summed over the whole block in a fixed order.
+// Energies of all 32 replica lanes of the tile at once (Eq. 1 + Eq. 6): one
+// warp per spin, lane = replica, FP64 (float couplings) or exact int64 (integer
+// couplings).  Each pair is counted at its smaller index, each hyper-edge once.
+// Per-lane sums are added over warps in ascending order (deterministic) and
+// written to E[32].
 template <bool FLOAT>
-__device__ double tile_lane_energy(const DevGraph &G, const InstDesc &I, const uint32_t *sw, int r,
-                                   double *redd, long long *redi) {
-  const int n = I.n;
-  if (FLOAT) {
-    const float *Jf = reinterpret_cast<const float *>(G.J);
-    const float *hf = reinterpret_cast<const float *>(G.h);
-    const float *hJ = reinterpret_cast<const float *>(G.hJ);
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const int64_t gi = I.spin_off + i;
-      const double si = ((sw[i] >> r) & 1u) ? 1.0 : -1.0;
-      double e = (double)__ldg(hf + gi) * si;
-      for (uint32_t k = __ldg(G.row + gi), ke = __ldg(G.row + gi + 1); k < ke; ++k) {
+__device__ void tile_energy_lanes(const DevGraph &G, const InstDesc &I, const uint32_t *sw, double *red,
+                                  double *E) {
+  const int n = I.n, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double accd = 0.0;
+  long long acci = 0;
+  for (int i = warp; i < n; i += nw) {
+    const int64_t gi = I.spin_off + i;
+    const uint32_t bi = (sw[i] >> lane) & 1u;
+    const uint32_t k0 = __ldg(G.row + gi), k1 = __ldg(G.row + gi + 1);
+    if (FLOAT) {
+      const float *Jf = reinterpret_cast<const float *>(G.J);
+      const double si = bi ? 1.0 : -1.0;
+      double e = (double)__ldg(reinterpret_cast<const float *>(G.h) + gi) * si;
+      for (uint32_t k = k0; k < k1; ++k) {
         const int j = __ldg(G.col + k);
-        if (j > i) e += (double)__ldg(Jf + k) * si * (((sw[j] >> r) & 1u) ? 1.0 : -1.0);
+        if (j > i) {
+          const double w = (double)__ldg(Jf + k);
+          e += (((sw[j] >> lane) & 1u) ^ bi) ? -w : w;
+        }
       }
-      acc -= e;
-    }
-    for (int e = threadIdx.x; e < I.n_hyper; e += blockDim.x) {
-      const int64_t ge = I.hyper_off + e;
-      uint32_t neg = 0;
-      for (uint32_t q = __ldg(G.hptr + ge), qe = __ldg(G.hptr + ge + 1); q < qe; ++q)
-        neg ^= ~(sw[__ldg(G.hmem + q)] >> r) & 1u;
-      const double p = neg ? -1.0 : 1.0;
-      acc -= (double)__ldg(hJ + ge) * p;
-    }
-    return block_sum(acc, redd);
-  } else {
-    const int8_t *Ji = reinterpret_cast<const int8_t *>(G.J);
-    const int8_t *hi = reinterpret_cast<const int8_t *>(G.h);
-    const int8_t *hJ = reinterpret_cast<const int8_t *>(G.hJ);
-    long long acc = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const int64_t gi = I.spin_off + i;
-      const uint32_t bi = (sw[i] >> r) & 1u;
-      int e = bi ? (int)__ldg(hi + gi) : -(int)__ldg(hi + gi);
-      for (uint32_t k = __ldg(G.row + gi), ke = __ldg(G.row + gi + 1); k < ke; ++k) {
+      accd -= e;
+    } else {
+      const int8_t *Ji = reinterpret_cast<const int8_t *>(G.J);
+      const int hv = __ldg(reinterpret_cast<const int8_t *>(G.h) + gi);
+      int e = bi ? hv : -hv;
+      for (uint32_t k = k0; k < k1; ++k) {
         const int j = __ldg(G.col + k);
         if (j > i) {
           const int w = __ldg(Ji + k);
-          e += ((((sw[j] >> r) & 1u) ^ bi) ? -w : w);
+          e += (((sw[j] >> lane) & 1u) ^ bi) ? -w : w;
         }
       }
-      acc -= e;
+      acci -= e;
     }
-    for (int e = threadIdx.x; e < I.n_hyper; e += blockDim.x) {
-      const int64_t ge = I.hyper_off + e;
-      uint32_t neg = 0;
-      for (uint32_t q = __ldg(G.hptr + ge), qe = __ldg(G.hptr + ge + 1); q < qe; ++q)
-        neg ^= ~(sw[__ldg(G.hmem + q)] >> r) & 1u;
-      const int w = __ldg(hJ + ge);
-      acc -= neg ? -w : w;
-    }
-    return (double)block_sum(acc, redi);
   }
+  for (int e = warp; e < I.n_hyper; e += nw) {
+    const int64_t ge = I.hyper_off + e;
+    uint32_t neg = 0;
+    for (uint32_t q = __ldg(G.hptr + ge), qe = __ldg(G.hptr + ge + 1); q < qe; ++q)
+      neg ^= ~(sw[__ldg(G.hmem + q)] >> lane) & 1u;
+    if (FLOAT) {
+      const double w = (double)__ldg(reinterpret_cast<const float *>(G.hJ) + ge);
+      accd -= neg ? -w : w;
+    } else {
+      const int w = __ldg(reinterpret_cast<const int8_t *>(G.hJ) + ge);
+      acci -= neg ? -w : w;
+    }
+  }
+  __syncthreads();
+  if (FLOAT) red[warp * 32 + lane] = accd;
+  else reinterpret_cast<long long *>(red)[warp * 32 + lane] = acci;
+  __syncthreads();
+  if (warp == 0) {
+    if (FLOAT) {
+      double a = red[lane];
+      for (int w = 1; w < nw; ++w) a += red[w * 32 + lane];
+      E[lane] = a;
+    } else {
+      const long long *ri = reinterpret_cast<const long long *>(red);
+      long long a = ri[lane];
+      for (int w = 1; w < nw; ++w) a += ri[w * 32 + lane];
+      E[lane] = (double)a;
+    }
+  }
+  __syncthreads();
+}
+
+// Energies of all 32 lanes for a +/-1 periodic lattice with |h| <= 1 (the
+// multi-spin coded lattice path): E = 2 U - (n d + #{h != 0}), U = the lane's
+// number of unsatisfied bonds and fields.  Each thread adds, per site, the
+// unsatisfied masks of its forward bonds (+x, +y, +z) and of its field into a
+// bit-sliced per-lane counter; ballots then total each counter bit over a
+// warp, and warps are added in shared memory.  Exact integers.
+__device__ void tile_energy_lattice(const DevGraph &G, const InstDesc &I, const uint32_t *sw, int *cnt,
+                                    double *E) {
+  constexpr int Q = 14;  // counter depth: up to 2^14 - 1 per lane and thread
+  const int n = I.n, L = I.lat_L, D = I.lat_d, lane = threadIdx.x & 31;
+  const int stride[3] = {1, L, L * L};
+  uint32_t acc[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) acc[q] = 0u;
+  int nz = 0;
+  if (threadIdx.x < 32) cnt[threadIdx.x] = 0;
+  if (threadIdx.x == 32) cnt[32] = 0;
+  __syncthreads();
+  for (int v = threadIdx.x; v < n; v += blockDim.x) {
+    const int j = __ldg(G.order + I.spin_off + v);
+    const uint32_t info = __ldg(G.latinfo + I.spin_off + v);
+    const int hv = __ldg(reinterpret_cast<const int8_t *>(G.h) + I.spin_off + j);
+    const uint32_t wj = sw[j];
+    uint32_t f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      f[a] = 0u;
+      if (a < D) {
+        const int d = 2 * a;  // forward direction along axis a
+        const int nb = j + stride[a] - (((info >> d) & 1u) ? L * stride[a] : 0);
+        f[a] = wj ^ sw[nb] ^ (((info >> (8 + d)) & 1u) ? 0xffffffffu : 0u);
+      }
+    }
+    const uint32_t uf = hv == 0 ? 0u : (hv > 0 ? ~wj : wj);
+    nz += hv != 0;
+    // compress the four masks into weights 1, 2, 4 and add them to the counter
+    const uint32_t s1 = f[0] ^ f[1] ^ f[2], c1 = (f[0] & f[1]) | (f[0] & f[2]) | (f[1] & f[2]);
+    const uint32_t s2 = s1 ^ uf, c2 = s1 & uf;
+    const uint32_t t1 = c1 ^ c2, t2 = c1 & c2;
+    uint32_t cy = acc[0] & s2;
+    acc[0] ^= s2;
+    const uint32_t x1 = acc[1] ^ t1 ^ cy;
+    cy = (acc[1] & t1) | (acc[1] & cy) | (t1 & cy);
+    acc[1] = x1;
+    const uint32_t x2 = acc[2] ^ t2 ^ cy;
+    cy = (acc[2] & t2) | (acc[2] & cy) | (t2 & cy);
+    acc[2] = x2;
+#pragma unroll
+    for (int q = 3; q < Q; ++q) {
+      const uint32_t c = acc[q] & cy;
+      acc[q] ^= cy;
+      cy = c;
+    }
+  }
+  long long mine = 0;
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+    for (int r = 0; r < 32; ++r) {
+      const int c = __popc(__ballot_sync(0xffffffffu, (acc[q] >> r) & 1u));
+      if (lane == r) mine += (long long)c << q;
+    }
+  nz = warp_sum(nz);
+  atomicAdd(&cnt[lane], (int)mine);
+  if (lane == 0) atomicAdd(&cnt[32], nz);
+  __syncthreads();
+  if (threadIdx.x < 32) E[threadIdx.x] = 2.0 * (double)cnt[threadIdx.x] - (double)n * D - (double)cnt[32];
+  __syncthreads();
 }
 
 // u >= t for a bit-sliced 4-bit count (c0 least significant), t a per-thread value.
@@ -114,11 +198,11 @@ template <int MODE>
 __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *__restrict__ Aptr) {
   extern __shared__ uint32_t smem[];
   __shared__ int s_tile;
-  __shared__ uint32_t s_any, s_active, s_conv, s_upd;
+  __shared__ uint32_t s_any, s_active, s_convround, s_upd;
   __shared__ int32_t s_total[32], s_minima[32];
-  __shared__ double s_best[32];
-  __shared__ double s_redd[32];
-  __shared__ long long s_redi[32];
+  __shared__ double s_best[32], s_E[32];
+  __shared__ double s_red[(kTileThreads / 32) * 32];
+  __shared__ int s_cnt[33];
 
   const TileArgs &A = *Aptr;
   const DevGraph G = A.g;
@@ -156,6 +240,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *_
           for (int r = 0; r < 32; ++r)
             if (((lane_valid >> r) & 1u) && (A.budget <= 0 || s_total[r] < A.budget)) start |= 1u << r;
         s_active = start;
+        s_convround = 0;
         my_desc += __popc(start);
       }
       __syncthreads();
@@ -168,14 +253,15 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *_
         const uint4 x = start_bits(seed, (uint32_t)w, (uint32_t)(32 * g + lane), (uint32_t)k, (uint32_t)b);
         for (int q = 0; q < 4; ++q) {
           const uint32_t xw = word_of(x, q);
+          uint32_t mine = 0;
           for (int u = 0; u < 32; ++u) {
-            const int i = w * 128 + q * 32 + u;
-            if (i >= n) break;
             const uint32_t m = __ballot_sync(0xffffffffu, (xw >> u) & 1u);
-            if (lane == 0) {
-              sw[i] = (sw[i] & ~active) | (m & active);
-              if (MODE == 1) fm[i] &= ~active;
-            }
+            if (lane == u) mine = m;
+          }
+          const int i = w * 128 + q * 32 + lane;
+          if (i < n) {
+            sw[i] = (sw[i] & ~active) | (mine & active);
+            if (MODE == 1) fm[i] &= ~active;
           }
         }
       }
@@ -194,7 +280,45 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *_
             c0 = __ldg(G.cls + I.cls_off + c);
             c1 = __ldg(G.cls + I.cls_off + c + 1);
           }
-          if (MODE == 2) {
+          if (MODE == 3) {
+            // +/-1 periodic lattice, |h| <= 1: the field counts as one more
+            // bond, so every site flips when at least deg/2 + 1 of its bonds and
+            // field are unsatisfied (3-d: majority of three carries; 2-d: >= 3).
+            const int L = I.lat_L, D = I.lat_d;
+            const int stride[3] = {1, L, L * L};
+            for (int v = c0 + tid; v < c1; v += blockDim.x) {
+              const int j = __ldg(G.order + I.spin_off + v);
+              const uint32_t info = __ldg(G.latinfo + I.spin_off + v);
+              const int hv = __ldg(reinterpret_cast<const int8_t *>(G.h) + I.spin_off + j);
+              const uint32_t wj = sw[j];
+              uint32_t x[6];
+#pragma unroll
+              for (int d = 0; d < 6; ++d) {
+                x[d] = 0u;
+                if (d < 2 * D) {
+                  const int a = d >> 1, st = stride[a];
+                  int nb = (d & 1) ? j - st : j + st;
+                  if ((info >> d) & 1u) nb += (d & 1) ? L * st : -L * st;
+                  x[d] = wj ^ sw[nb] ^ (((info >> (8 + d)) & 1u) ? 0xffffffffu : 0u);
+                }
+              }
+              const uint32_t uf = hv == 0 ? 0u : (hv > 0 ? ~wj : wj);
+              uint32_t flip;
+              const uint32_t s1 = x[0] ^ x[1] ^ x[2], c1 = (x[0] & x[1]) | (x[0] & x[2]) | (x[1] & x[2]);
+              if (D == 3) {
+                const uint32_t s2 = x[3] ^ x[4] ^ x[5], c2 = (x[3] & x[4]) | (x[3] & x[5]) | (x[4] & x[5]);
+                const uint32_t c3 = (s1 & s2) | (s1 & uf) | (s2 & uf);
+                flip = (c1 & c2) | (c1 & c3) | (c2 & c3);  // count >= 4
+              } else {
+                const uint32_t s2 = x[3] ^ uf ^ s1, c2 = (x[3] & uf) | (x[3] & s1) | (uf & s1);
+                flip = (c1 & c2) | ((c1 | c2) & s2);  // count >= 3
+              }
+              flip &= active;
+              sw[j] = wj ^ flip;
+              anyf |= flip;
+              my_flips += __popc(flip);
+            }
+          } else if (MODE == 2) {
             const int8_t *Ji = reinterpret_cast<const int8_t *>(G.J);
             const int8_t *hi = reinterpret_cast<const int8_t *>(G.h);
             for (int v = c0 + tid; v < c1; v += blockDim.x) {
@@ -344,29 +468,36 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *_
           my_sweeps += __popc(active);
           my_evals += (unsigned long long)__popc(active) * (unsigned long long)n;
           my_minima += __popc(conv);
-          s_conv = conv;
-          s_upd = 0;
+          s_convround |= conv;
           s_active = active & ~ended;
         }
         __syncthreads();
-        uint32_t conv = s_conv;
-        while (conv) {
-          const int r = __ffs(conv) - 1;
-          conv &= conv - 1;
-          const double E = tile_lane_energy<MODE == 1>(G, I, sw, r, s_redd, s_redi);
-          if (tid == 0) {
-            s_minima[r] += 1;
-            if (E < s_best[r]) {
-              s_best[r] = E;
-              s_upd |= 1u << r;
+        active = s_active;
+        if (!active) {
+          // Round over: converged lanes have been frozen since their last sweep,
+          // so all of them are scored in one lane-parallel pass.
+          const uint32_t cr = s_convround;
+          if (cr) {
+            if (MODE == 3) tile_energy_lattice(G, I, sw, s_cnt, s_E);
+            else tile_energy_lanes<MODE == 1>(G, I, sw, s_red, s_E);
+            if (tid == 0) {
+              uint32_t upd = 0;
+              for (int r = 0; r < 32; ++r)
+                if ((cr >> r) & 1u) {
+                  s_minima[r] += 1;
+                  if (s_E[r] < s_best[r]) {
+                    s_best[r] = s_E[r];
+                    upd |= 1u << r;
+                  }
+                }
+              s_upd = upd;
             }
+            __syncthreads();
+            const uint32_t upd = s_upd;
+            if (upd)
+              for (int i = tid; i < n; i += blockDim.x) bw[i] = (bw[i] & ~upd) | (sw[i] & upd);
           }
         }
-        __syncthreads();
-        const uint32_t upd = s_upd;
-        if (upd)
-          for (int i = tid; i < n; i += blockDim.x) bw[i] = (bw[i] & ~upd) | (sw[i] & upd);
-        active = s_active;
         __syncthreads();
       }
     }
@@ -375,12 +506,10 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *_
     uint32_t has_best = 0;
     for (int r = 0; r < 32; ++r)
       if (s_minima[r] > 0) has_best |= 1u << r;
-    uint32_t need = lane_valid & ~has_best;
-    while (need) {
-      const int r = __ffs(need) - 1;
-      need &= need - 1;
-      const double E = tile_lane_energy<MODE == 1>(G, I, sw, r, s_redd, s_redi);
-      if (tid == 0) s_best[r] = E;
+    if (lane_valid & ~has_best) {
+      if (MODE == 3) tile_energy_lattice(G, I, sw, s_cnt, s_E);
+      else tile_energy_lanes<MODE == 1>(G, I, sw, s_red, s_E);
+      if (tid < 32 && !((has_best >> tid) & 1u)) s_best[tid] = s_E[tid];
     }
     __syncthreads();
     const int64_t out_base = (int64_t)A.R * I.spin_off + (int64_t)(32 * g) * n;
@@ -399,7 +528,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *_
   }
 
   // work counters
-  my_flips = block_sum<unsigned long long>(my_flips, reinterpret_cast<unsigned long long *>(s_redi));
+  my_flips = block_sum<unsigned long long>(my_flips, reinterpret_cast<unsigned long long *>(s_red));
   if (tid == 0) {
     atomicAdd(A.stats + 0, my_evals);
     atomicAdd(A.stats + 1, my_flips);
@@ -410,7 +539,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *_
 }
 
 size_t tile_smem_bytes(int mode, int nmax) {
-  return (size_t)(mode == 2 ? 1 : 2) * (size_t)nmax * sizeof(uint32_t);
+  return (size_t)(mode >= 2 ? 1 : 2) * (size_t)nmax * sizeof(uint32_t);
 }
 
 int tile_max_ctas_per_sm(int mode, size_t smem) {
@@ -422,9 +551,12 @@ int tile_max_ctas_per_sm(int mode, size_t smem) {
   } else if (mode == 1) {
     e = cudaFuncSetAttribute(tile_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, tile_kernel<1>, kTileThreads, smem);
-  } else {
+  } else if (mode == 2) {
     e = cudaFuncSetAttribute(tile_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, tile_kernel<2>, kTileThreads, smem);
+  } else {
+    e = cudaFuncSetAttribute(tile_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, tile_kernel<3>, kTileThreads, smem);
   }
   return e == cudaSuccess ? blocks : 0;
 }
@@ -437,9 +569,12 @@ cudaError_t launch_tile(ising_handle *h, int mode, int grid, size_t smem, cudaSt
   } else if (mode == 1) {
     e = cudaFuncSetAttribute(tile_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) tile_kernel<1><<<grid, kTileThreads, smem, s>>>(h->d_tile_args);
-  } else {
+  } else if (mode == 2) {
     e = cudaFuncSetAttribute(tile_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) tile_kernel<2><<<grid, kTileThreads, smem, s>>>(h->d_tile_args);
+  } else {
+    e = cudaFuncSetAttribute(tile_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) tile_kernel<3><<<grid, kTileThreads, smem, s>>>(h->d_tile_args);
   }
   if (e != cudaSuccess) return e;
   return cudaGetLastError();

@@ -91,6 +91,20 @@ def test_3d_pmJ_with_fields_ragged_replicas(kernel):
     _compare([inst], [77], 37, True, max_sweeps=100, restarts=3, kernel=kernel)
 
 
+@pytest.mark.parametrize("seed", [4, 5])
+def test_msc_on_general_pm1_graph(seed):
+    # +/-1 couplings, h in {-1,0,1}, irregular degrees: the generic multi-spin coded evaluator
+    inst = W.random_graph(500, 4.0, seed, dtype="i8", int_range=1)
+    assert set(np.unique(inst.J)) <= {-1, 1} and np.max(np.diff(inst.row_ptr)) <= 15
+    _compare([inst], [seed], 70, True, max_sweeps=200, restarts=3, kernel=isg.KERNEL_MSC)
+
+
+def test_msc_lattice_2d_and_3d_with_fields():
+    for dims in [(14, 14), (10, 10, 10), (6, 8, 10)]:
+        inst = W.lattice(dims, periodic=True, couplings="pm1", fields="pm1_0", seed=len(dims))
+        _compare([inst], [len(dims)], 45, True, max_sweeps=300, restarts=4, kernel=isg.KERNEL_MSC)
+
+
 @pytest.mark.parametrize("seed,kernel", [(1, isg.KERNEL_TILE), (2, isg.KERNEL_TILE), (3, isg.KERNEL_PLAIN)])
 def test_random_integer_graph_with_hyperedges(seed, kernel):
     inst = W.random_graph(300, 5.0, seed, dtype="i8", n_hyper=40, hyper_order=(2, 3, 4))
@@ -172,4 +186,63 @@ def test_msc_rejected_for_float_and_large_fields():
     inst = W.random_graph(64, 3.0, 2, dtype="i8", int_range=3)
     h = isg.Handle([inst])
     assert h.plan_kernel(32) == isg.KERNEL_TILE
+    h.close()
+
+
+# ----------------------------------------------------------- large-instance sweep family
+@pytest.mark.parametrize("R", [64, 16, 5])
+def test_sweep_family_pmJ_lattice_msc(R):
+    inst = W.lattice((10, 10, 10), periodic=True, couplings="pm1", fields="pm1_0", seed=21)
+    _compare([inst], [321], R, True, max_sweeps=100, restarts=3, kernel=isg.KERNEL_SWEEP)
+
+
+def test_sweep_family_int_lattice_lanes():
+    inst = W.lattice((12, 12), periodic=True, couplings="pm1", seed=22)
+    inst.J = (inst.J * 2).astype(np.int8)  # |J| = 2: not multi-spin codable, integer lanes
+    _compare([inst], [5], 40, True, max_sweeps=200, restarts=2, kernel=isg.KERNEL_SWEEP)
+
+
+@pytest.mark.parametrize("R,refresh", [(16, 16), (32, 4), (8, 0)])
+def test_sweep_family_gauss_lattice_fp32(R, refresh):
+    inst = W.lattice((12, 12, 12), periodic=True, couplings="gauss", seed=23)
+    _compare([inst], [77], R, False, max_sweeps=1000, restarts=1 << 20, sweep_budget=60,
+             refresh_every=refresh, kernel=isg.KERNEL_SWEEP)
+
+
+def test_sweep_family_csr_with_hyperedges():
+    inst = W.random_graph(700, 4.0, 24, dtype="f32", n_hyper=50, hyper_order=(3, 4))
+    _compare([inst], [9], 20, False, max_sweeps=500, restarts=3, refresh_every=8, kernel=isg.KERNEL_SWEEP)
+
+
+def test_sweep_family_sequential_schedule():
+    inst = W.random_graph(200, 4.0, 25, dtype="i8", n_hyper=10, hyper_order=(3,))
+    _compare([inst], [3], 12, True, max_sweeps=300, restarts=2, schedule=isg.SCHED_SEQUENTIAL,
+             kernel=isg.KERNEL_SWEEP)
+
+
+# ----------------------------------------------------------- dense SK on tensor cores
+def test_dense_sk_tensor_core_path():
+    """BF16 hi+lo fields with FP32 accumulation: results are checked against the
+    FP64 oracle on what is unique (energies of the returned states) and on the
+    1-flip local-minimum property within the stated field error bound."""
+    inst = W.sk(384, seed=5)
+    R = 96
+    h = isg.Handle([inst])
+    assert h.plan_kernel(R) == isg.KERNEL_DENSE_TC
+    res = h.local_search([17], R, max_sweeps=500, restarts=2, kernel=isg.KERNEL_DENSE_TC)
+    torch.cuda.synchronize()
+    sp = res.spins.view(R, inst.n).cpu().numpy()
+    E = res.energy.view(R).cpu().numpy()
+    oi = oracle.OracleInstance(inst)
+    Eo = oracle.energies(oi, sp)
+    rel = np.abs(E - Eo) / np.abs(Eo)
+    assert rel.max() <= 1e-6, rel.max()
+    for r in range(R):
+        f = oracle.local_fields(oi, sp[r])
+        assert np.all(sp[r] * f >= -1e-4)
+    # same schedule and seeds in FP64: energies reached agree on average
+    _, Eo64, _, _ = oracle.descent(oi, 17, 0, R, max_sweeps=500, restarts=2, schedule=oracle.SCHED_SEQUENTIAL,
+                                   mode=oracle.MODE_F64)
+    assert abs(np.mean(E) - np.mean(Eo64)) <= 0.02 * abs(np.mean(Eo64))
+    assert res.stats["minima"] == 2 * R
     h.close()
