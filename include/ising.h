@@ -202,6 +202,29 @@ int32_t ising_plan_kernel(ising_handle *h, int32_t replicas, const ising_search_
 ising_status ising_autotune(ising_handle *h, int32_t replicas, const ising_search_params *p,
                             int32_t *chosen, cudaStream_t stream);
 
+/* Allocation-free energy evaluation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory - for example a
+ * framework whose pool allocator owns the whole device, or code that must not
+ * trigger the device-wide synchronisation a cudaMalloc implies - and so can
+ * use neither ising_create nor ising_energy's on-demand scratch.  It computes
+ * the same energies as ising_energy (pairs and fields of Eq. 1; no
+ * hyper-edges) from the caller's own DEVICE buffers: row_ptr_dev int64 [n+1],
+ * col_dev int32, J_dev (int8_t or float per dtype, symmetric CSR as for
+ * ising_create, not re-validated here), h_dev [n] or NULL, spins_dev int8
+ * [replicas][n]; energy_dev double [replicas] out.  It allocates nothing: its
+ * scratch is a fixed array of ISING_NOALLOC_MAX_PARTIALS doubles (512 KiB)
+ * that every device loading the library holds until the process exits, so it
+ * returns ISING_ERR_UNSUPPORTED when ceil(n / 4096) * replicas exceeds that
+ * limit.  The first call on a device looks up that array's address (with the
+ * device current) and should come before any stream capture on that device.
+ * All calls share the array: calls that overlap on the GPU race and must be
+ * ordered by the caller.                                                       */
+#define ISING_NOALLOC_MAX_PARTIALS 65536
+ising_status ising_energy_noalloc(int32_t n, const int64_t *row_ptr_dev, const int32_t *col_dev,
+                                  const void *J_dev, const void *h_dev, ising_dtype dtype,
+                                  const int8_t *spins_dev, int32_t replicas, double *energy_dev,
+                                  cudaStream_t stream);
+
 /* Free everything the handle owns.  ising_destroy(NULL) returns ISING_OK.      */
 ising_status ising_destroy(ising_handle *h);
 

@@ -78,6 +78,8 @@ def lib():
             L.ising_autotune.restype = i32
             L.ising_destroy.argtypes = [vp]
             L.ising_destroy.restype = i32
+            L.ising_energy_noalloc.argtypes = [i32, vp, vp, vp, vp, i32, vp, i32, vp, vp]
+            L.ising_energy_noalloc.restype = i32
             L.ising_status_string.argtypes = [i32]
             L.ising_status_string.restype = C.c_char_p
             _lib = L
@@ -85,7 +87,7 @@ def lib():
 
 
 EXPORTED = ("ising_create", "ising_energy", "ising_local_search", "ising_plan_kernel",
-            "ising_autotune", "ising_destroy", "ising_status_string")
+            "ising_autotune", "ising_destroy", "ising_status_string", "ising_energy_noalloc")
 
 
 def _check(code: int, where: str):
@@ -229,6 +231,23 @@ class Handle:
             self.close()
         except Exception:
             pass
+
+
+def energy_noalloc(row_ptr, col, J, h, spins, replicas: int, energy, stream=None) -> int:
+    """ising_energy_noalloc on caller-owned device tensors (argument marshalling only).
+
+    row_ptr int64 [n+1], col int32, J int8/float32, h (same dtype) or None,
+    spins int8 [replicas, n], energy float64 [replicas] (written).  Returns the
+    status code (0 = ok).
+    """
+    import torch
+    n = row_ptr.numel() - 1
+    dt = I8 if J.dtype == torch.int8 else F32
+    s = stream if stream is not None else torch.cuda.current_stream(spins.device)
+    return lib().ising_energy_noalloc(
+        n, C.c_void_p(row_ptr.data_ptr()), C.c_void_p(col.data_ptr()), C.c_void_p(J.data_ptr()),
+        None if h is None else C.c_void_p(h.data_ptr()), dt, C.c_void_p(spins.data_ptr()), replicas,
+        C.c_void_p(energy.data_ptr()), C.c_void_p(s.cuda_stream))
 
 
 def status_string(code: int) -> str:
