@@ -20,10 +20,17 @@
 #include <cuda_bf16.h>
 
 #include <cfloat>
+#include <cstdlib>
 
 #include "device_common.cuh"
 
 namespace isg {
+
+bool dense_tc_eligible(int n);
+cudaError_t dense_tc_run(int n, int R, int Rp, int b, uint64_t seed, const float *J, const __nv_bfloat16 *Jhi,
+                         const __nv_bfloat16 *Jlo, __nv_bfloat16 *S, int8_t *best, int8_t *out, double *E,
+                         int32_t *minima, unsigned long long *stats, int32_t *error,
+                         const ising_search_params *p, cudaStream_t s);
 
 namespace {
 
@@ -195,6 +202,8 @@ struct DenseState {
   DenseRep *rep = nullptr;
   int8_t *best = nullptr;
   int32_t *active = nullptr, *h_active = nullptr;
+  __nv_bfloat16 *S_tc = nullptr;  // [Rp128][n] replica-major spins for the tcgen05 kernel
+  int32_t *err = nullptr, *h_err = nullptr;
 };
 
 std::map<const ising_handle *, DenseState> &dense_states() {
@@ -212,6 +221,9 @@ void free_state(DenseState &D) {
   cudaFree(D.best);
   cudaFree(D.active);
   cudaFree(D.workspace);
+  cudaFree(D.S_tc);
+  cudaFree(D.err);
+  if (D.h_err) cudaFreeHost(D.h_err);
   if (D.h_active) cudaFreeHost(D.h_active);
   if (D.cublas) cublasDestroy(D.cublas);
   D = DenseState();
@@ -283,6 +295,26 @@ cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t 
     if (cublasSetStream(D.cublas, s) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
     const float *J = h->d_Jdense + joff;
     const uint64_t seed = seeds_host[b];
+    const char *force_lib = std::getenv("ISING_DENSE_CUBLAS");
+    if (dense_tc_eligible(n) && !(force_lib && force_lib[0] == '1')) {
+      // hand-written tcgen05 kernel: the whole search in one launch
+      const int Rp128 = (R + 127) / 128 * 128;
+      if (!D.S_tc) {
+        if ((e = cudaMalloc(&D.S_tc, (size_t)Rp128 * n * 2)) != cudaSuccess) return e;
+        if ((e = cudaMemset(D.S_tc, 0, (size_t)Rp128 * n * 2)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&D.err, 64)) != cudaSuccess) return e;
+        if ((e = cudaMallocHost(&D.h_err, 64)) != cudaSuccess) return e;
+      }
+      if ((e = cudaMemsetAsync(D.err, 0, 4, s)) != cudaSuccess) return e;
+      e = dense_tc_run(n, R, Rp128, b, seed, J, D.hi, D.lo, D.S_tc, D.best, spins + (int64_t)R * h->inst[b].spin_off,
+                       E + (int64_t)b * R, minima ? minima + (int64_t)b * R : nullptr, h->d_stats, D.err, p, s);
+      if (e != cudaSuccess) return e;
+      if ((e = cudaMemcpyAsync(D.h_err, D.err, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+      if (*D.h_err != 0) return cudaErrorLaunchTimeout;
+      joff += (int64_t)n * n;
+      continue;
+    }
     const int rb = (R + 255) / 256;
     dense_init<<<rb, 256, 0, s>>>(R, D.rep, h->d_stats);
     // capture one sweep into a graph, replay it sweep by sweep

@@ -1,0 +1,475 @@
+// dense_tc.cu — the dense (Sherrington-Kirkpatrick) path on 5th-generation
+// tensor cores, hand-written with tcgen05, TMA and thread-block clusters.
+//
+// Method: the paper's sequential single-spin descent (Sec. IV) on a complete
+// graph, where every colour class is one spin.  Spins are decided in blocks of
+// 128 consecutive indices.  The fields of a block for 128 replicas are
+//     F[r][i] = sum_j S[r][j] J[i][j],   i in the block, j = 0..n-1,
+// a GEMM with K = n, computed as S.J_hi^T + S.J_lo^T (J = J_hi + J_lo, both
+// BF16; spins +/-1 exact in BF16) with FP32 accumulation in tensor memory.  The
+// block's spins are then decided one after another, each field corrected in
+// FP32 for the earlier flips inside the block (+2 J_ij s_j): the paper's
+// incremental gain update restricted to the block.
+//
+// Work split: a cluster of 4 CTAs owns 128 replicas for the whole search (all
+// sweeps and restarts in this one launch).  CTA q multiplies the K-slice
+// j in [q n/4, (q+1) n/4) into its own tensor-memory accumulator; the four
+// partial blocks are exchanged through distributed shared memory and summed in
+// a fixed order; CTA q then decides replicas 32q..32q+31.  Thread 0 of each CTA
+// issues the TMA loads (128-byte swizzled K-major tiles) and the MMAs through a
+// 3-stage mbarrier pipeline.  Every mbarrier wait is bounded; a CTA whose wait
+// gives up records ISING_ERR_TIMEOUT, keeps the cluster's barrier sequence and
+// skips its remaining work, and the cluster ends together at the next sweep.
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <cfloat>
+#include <cstdio>
+
+#include "device_common.cuh"
+#include "tc.cuh"
+
+namespace isg {
+
+namespace {
+
+constexpr int kTM = 128;        // replicas per cluster (MMA M)
+constexpr int kTB = 128;        // spins per block (MMA N)
+constexpr int kKC = 64;         // K per TMA chunk (128 bytes of BF16)
+constexpr int kStages = 3;
+constexpr int kClus = 4;        // CTAs per cluster (split K)
+constexpr int kThreads = 128;
+constexpr int kTileBytes = kTM * kKC * 2;                 // 16 KB
+constexpr int kStageBytes = 3 * kTileBytes;               // A, B_hi, B_lo
+constexpr int kPartialBytes = kTB * kTM * 4;              // 64 KB, [spin][replica]
+constexpr int kSmemBytes = kStages * kStageBytes + kPartialBytes + 1024;  // + alignment slack
+
+struct TcArgs {
+  int32_t n, R, Rp, b;             // spins, replicas, padded replicas, instance
+  int32_t max_sweeps, restarts, budget;
+  uint64_t seed;
+  const float *J;                  // [n][n] FP32 (in-block corrections)
+  __nv_bfloat16 *S;                // [Rp][n] spins +/-1
+  int8_t *best;                    // [R][n]
+  int8_t *out;                     // [R][n] result spins (instance block)
+  double *E;                       // [R] result energies (instance block)
+  int32_t *minima;                 // [R] or null
+  unsigned long long *stats;
+  int32_t *error;                  // set to ISING_ERR_TIMEOUT when a wait gives up
+};
+
+struct RepState {  // per replica, owned by one thread of warp 0
+  int32_t active, conv, total, minima, d, k, flips, done;
+  double best, E;
+};
+
+__device__ __forceinline__ void write_start(const TcArgs &A, int r, int k) {
+  // Philox start R(b, r, k), written as BF16 +/-1 into S[r][:]
+  __nv_bfloat16 *row = A.S + (size_t)r * A.n;
+  for (int w = 0; w * 128 < A.n; ++w) {
+    const uint4 x = start_bits(A.seed, (uint32_t)w, (uint32_t)r, (uint32_t)k, (uint32_t)A.b);
+    for (int t = 0; t < 128 && w * 128 + t < A.n; ++t)
+      row[w * 128 + t] = __float2bfloat16_rn(((word_of(x, t / 32) >> (t % 32)) & 1u) ? 1.0f : -1.0f);
+  }
+}
+
+__global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
+    dense_tc_kernel(const __grid_constant__ CUtensorMap mapS, const __grid_constant__ CUtensorMap mapJhi,
+                    const __grid_constant__ CUtensorMap mapJlo, TcArgs A) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t *stage = smem;                                              // kStages x (A, Bhi, Blo)
+  float *P = reinterpret_cast<float *>(smem + kStages * kStageBytes);  // partial fields [spin][replica]
+  float *Floc = reinterpret_cast<float *>(smem);                      // reuses stages: [spin][32]
+  float *Jblk = reinterpret_cast<float *>(smem + kTB * 32 * 4);       // reuses stages: [128][128]
+
+  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], done_bar;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int32_t s_flag[2];   // cluster-visible: [0] my replicas still busy, [1] my failure
+  __shared__ int32_t s_ctrl[4];   // broadcast inside the CTA
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t q = tc::cluster_rank();
+  const int tile = blockIdx.x / kClus;
+  const int r0 = tile * kTM;                 // first replica of the cluster
+  const int rq = r0 + 32 * (int)q;           // first replica this CTA decides
+  const int n = A.n, nblk = n / kTB, kslice = n / kClus;
+  const int kchunks = kslice / kKC;
+  constexpr uint32_t idesc = tc::idesc_bf16_f32(kTM, kTB);
+
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      tc::mbar_init(&full_bar[s], 1);
+      tc::mbar_init(&empty_bar[s], 1);
+    }
+    tc::mbar_init(&done_bar, 1);
+    tc::fence_barrier_init();
+    tc::prefetch_tmap(&mapS);
+    tc::prefetch_tmap(&mapJhi);
+    tc::prefetch_tmap(&mapJlo);
+  }
+  if (warp == 0) tc::tmem_alloc(&tmem_base_s, 128);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+
+  // per-replica state: thread t of warp 0 owns replica rq + t
+  RepState st;
+  const int my_r = rq + lane;
+  const bool real = warp == 0 && my_r < A.R;
+  st.active = real ? 1 : 0;
+  st.conv = st.total = st.minima = st.d = st.k = st.flips = 0;
+  st.done = real ? 0 : 1;
+  st.best = DBL_MAX;
+  st.E = 0.0;
+  unsigned long long c_evals = 0, c_flips = 0, c_minima = 0, c_desc = 0, c_sweeps = 0;
+  if (real) {
+    write_start(A, my_r, 0);
+    c_desc = 1;
+  }
+  tc::fence_proxy_async_global();
+  bool failed = false;
+  uint32_t ph_full[kStages] = {0, 0, 0}, ph_empty[kStages] = {0, 0, 0}, ph_done = 0;
+  int tma_pending[kStages] = {0, 0, 0}, mma_pending = 0;
+  tc::cluster_sync();
+
+  // energy_pass: this "sweep" only accumulates FP64 energies, no decisions
+  for (int guard = 0; guard < (1 << 30); ++guard) {
+    // ---- cluster-wide control: is anybody active?  did anybody fail?
+    if (tid == 0) s_flag[0] = 0, s_flag[1] = failed ? 1 : 0;
+    __syncthreads();
+    if (warp == 0) {
+      const int busy = __any_sync(0xffffffffu, st.active);
+      if (lane == 0) s_flag[0] = busy;
+    }
+    __syncthreads();
+    tc::cluster_sync();
+    if (tid == 0) {
+      int busy = 0, bad = 0;
+      for (uint32_t c = 0; c < kClus; ++c) {
+        busy |= (int)tc::ld_cluster_u32(tc::map_shared(&s_flag[0], c));
+        bad |= (int)tc::ld_cluster_u32(tc::map_shared(&s_flag[1], c));
+      }
+      s_ctrl[0] = busy;
+      s_ctrl[1] = bad;
+    }
+    tc::cluster_sync();  // nobody rewrites s_flag before every CTA has read it
+    const int any_busy = s_ctrl[0], any_bad = s_ctrl[1];
+    if (any_bad) break;
+    // A round ends when no replica of the cluster is active: score it, then restart.
+    const bool energy_pass = !any_busy;
+    if (energy_pass) {
+      if (warp == 0) st.E = 0.0;
+    }
+    // ---- one sweep (or energy pass) over the blocks
+    for (int blk = 0; blk < nblk; ++blk) {
+      const int b0 = blk * kTB;
+      // Phase 1: partial fields of the block over this CTA's K-slice.  Thread 0
+      // keeps kStages chunks in flight: after issuing chunk kc's MMAs it refills
+      // the stage of chunk kc-1 once those MMAs have read it, so the tensor pipe
+      // always has the next chunk queued.
+      if (tid == 0 && !failed) {
+        const int kbase = (int)q * kslice;
+        auto load = [&](int s, int kn) {
+          uint8_t *st_ = stage + s * kStageBytes;
+          tc::mbar_arrive_expect_tx(&full_bar[s], kStageBytes);
+          tc::tma_load_2d(st_, &mapS, &full_bar[s], kbase + kn * kKC, r0);
+          tc::tma_load_2d(st_ + kTileBytes, &mapJhi, &full_bar[s], kbase + kn * kKC, b0);
+          tc::tma_load_2d(st_ + 2 * kTileBytes, &mapJlo, &full_bar[s], kbase + kn * kKC, b0);
+          tma_pending[s] = 1;
+        };
+        for (int s = 0; s < kStages && s < kchunks; ++s) load(s, s);
+        int waited = 0;  // chunks whose MMA completion (empty barrier) has been consumed
+        for (int kc = 0; kc < kchunks && !failed; ++kc) {
+          const int s = kc % kStages;
+          if (!tc::mbar_wait(&full_bar[s], ph_full[s])) {
+            failed = true;
+            break;
+          }
+          ph_full[s] ^= 1u;
+          tma_pending[s] = 0;
+          tc::tc_fence_after();
+          uint8_t *st_ = stage + s * kStageBytes;
+          const uint64_t da = tc::smem_desc_k_sw128(st_);
+          const uint64_t dh = tc::smem_desc_k_sw128(st_ + kTileBytes);
+          const uint64_t dl = tc::smem_desc_k_sw128(st_ + 2 * kTileBytes);
+#pragma unroll
+          for (int kk = 0; kk < kKC / 16; ++kk)
+            tc::mma_bf16(tmem, da + 2 * kk, dh + 2 * kk, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+#pragma unroll
+          for (int kk = 0; kk < kKC / 16; ++kk) tc::mma_bf16(tmem, da + 2 * kk, dl + 2 * kk, idesc, 1u);
+          tc::mma_commit(&empty_bar[s]);
+          mma_pending = 1;
+          if (kc >= 1) {
+            const int pc = kc - 1, sp = pc % kStages;
+            if (!tc::mbar_wait(&empty_bar[sp], ph_empty[sp])) {
+              failed = true;
+              break;
+            }
+            ph_empty[sp] ^= 1u;
+            waited = kc;
+            if (pc + kStages < kchunks) load(sp, pc + kStages);
+          }
+        }
+        if (!failed) {
+          tc::mma_commit(&done_bar);
+          // consume the MMA completions not waited for above
+          for (int c = waited; c < kchunks && !failed; ++c) {
+            const int sp = c % kStages;
+            if (!tc::mbar_wait(&empty_bar[sp], ph_empty[sp])) failed = true;
+            ph_empty[sp] ^= 1u;
+          }
+        }
+      }
+      __syncthreads();
+      if (tid == 0) s_ctrl[2] = failed ? 1 : 0;
+      __syncthreads();
+      failed = s_ctrl[2] != 0;
+      // Phase 2: accumulator -> shared memory, transposed to [spin][replica]
+      {
+        const bool ok = failed ? true : tc::mbar_wait(&done_bar, ph_done);
+        failed = __syncthreads_or(failed || !ok) != 0;
+        tc::tc_fence_after();
+        if (tid == 0 && !failed) mma_pending = 0;
+      }
+      ph_done ^= 1u;
+      if (!failed) {
+        for (int cc = 0; cc < kTB / 32; ++cc) {
+          uint32_t v[32];
+          tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(cc * 32), v);
+#pragma unroll
+          for (int k = 0; k < 32; ++k) P[(cc * 32 + k) * kTM + 32 * warp + lane] = __uint_as_float(v[k]);
+        }
+      }
+      tc::tc_fence_before();
+      __syncthreads();
+      tc::cluster_sync();
+      // Phase 3: sum the four partials (fixed order) for this CTA's 32 replicas,
+      // stage the block's couplings in FP32
+      if (!failed) {
+        for (int e = tid; e < kTB * 8; e += kThreads) {
+          const int i = e >> 3, c4 = e & 7;
+          float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+          for (uint32_t c = 0; c < kClus; ++c) {
+            const float4 p = tc::ld_cluster_f4(tc::map_shared(P + i * kTM + 32 * q + 4 * c4, c));
+            acc.x += p.x;
+            acc.y += p.y;
+            acc.z += p.z;
+            acc.w += p.w;
+          }
+          reinterpret_cast<float4 *>(Floc)[i * 8 + c4] = acc;
+        }
+        if (!energy_pass)
+          for (int e = tid; e < kTB * kTB / 4; e += kThreads) {
+            const int i = e / (kTB / 4), c4 = e % (kTB / 4);
+            reinterpret_cast<float4 *>(Jblk)[e] =
+                *reinterpret_cast<const float4 *>(A.J + (size_t)(b0 + i) * n + b0 + 4 * c4);
+          }
+      }
+      __syncthreads();
+      tc::cluster_sync();  // partials consumed: P may be overwritten by the next block
+      // Phase 4: sequential decisions (or energy accumulation), one thread per replica
+      if (!failed && warp == 0 && my_r < A.R) {
+        __nv_bfloat16 *row = A.S + (size_t)my_r * n + b0;
+        uint32_t up[kTB / 32], fl[kTB / 32];
+#pragma unroll
+        for (int w = 0; w < kTB / 32; ++w) {
+          up[w] = 0;
+          fl[w] = 0;
+        }
+        for (int i = 0; i < kTB; ++i)
+          if (__bfloat162float(row[i]) > 0.0f) up[i >> 5] |= 1u << (i & 31);
+        if (energy_pass) {
+          double acc = 0.0;
+          for (int i = 0; i < kTB; ++i)
+            acc += (((up[i >> 5] >> (i & 31)) & 1u) ? 1.0 : -1.0) * (double)Floc[i * 32 + lane];
+          st.E += acc;
+        } else if (st.active) {
+          int nfl = 0;
+          for (int i = 0; i < kTB; ++i) {
+            float f = Floc[i * 32 + lane];
+#pragma unroll
+            for (int w = 0; w < kTB / 32; ++w) {
+              uint32_t m = fl[w];
+              if (w * 32 >= i) m = 0;
+              else if (i - w * 32 < 32) m &= (1u << (i - w * 32)) - 1u;
+              while (m) {
+                const int jj = w * 32 + __ffs(m) - 1;
+                m &= m - 1;
+                const float w2 = 2.0f * Jblk[i * kTB + jj];
+                f = __fadd_rn(f, ((up[w] >> (jj - w * 32)) & 1u) ? w2 : -w2);
+              }
+            }
+            const bool s_up = (up[i >> 5] >> (i & 31)) & 1u;
+            if (s_up ? (f < 0.0f) : (f > 0.0f)) {
+              up[i >> 5] ^= 1u << (i & 31);
+              fl[i >> 5] |= 1u << (i & 31);
+              ++nfl;
+            }
+          }
+          if (nfl) {
+            for (int i = 0; i < kTB; ++i)
+              if ((fl[i >> 5] >> (i & 31)) & 1u)
+                row[i] = __float2bfloat16_rn(((up[i >> 5] >> (i & 31)) & 1u) ? 1.0f : -1.0f);
+            st.flips += nfl;
+            c_flips += (unsigned long long)nfl;
+          }
+        }
+      }
+      // generic-proxy writes (new spins in global memory, the staged fields and
+      // couplings in shared memory) are ordered before the next TMA writes/reads
+      tc::fence_proxy_async_global();
+      tc::fence_proxy_async_shared();
+      __syncthreads();
+      tc::cluster_sync();  // new spins visible to every CTA's next TMA loads
+    }
+    // ---- end of sweep / energy pass: per-replica bookkeeping (warp 0)
+    if (warp == 0 && my_r < A.R && !failed) {
+      if (energy_pass) {
+        const double E = -0.5 * st.E;
+        st.E = E;
+        if (!st.done) {
+          if (st.conv) {
+            st.minima += 1;
+            ++c_minima;
+            if (E < st.best) {
+              st.best = E;
+              const __nv_bfloat16 *row = A.S + (size_t)my_r * n;
+              for (int i = 0; i < n; ++i) A.best[(size_t)my_r * n + i] = __bfloat162float(row[i]) > 0.0f ? 1 : -1;
+            }
+          }
+          st.conv = 0;
+          st.k += 1;
+          if (st.k < A.restarts && (A.budget <= 0 || st.total < A.budget)) {
+            st.active = 1;
+            st.d = 0;
+            write_start(A, my_r, st.k);
+            ++c_desc;
+          } else {
+            st.done = 1;
+          }
+        }
+      } else if (st.active) {
+        st.total += 1;
+        st.d += 1;
+        c_evals += (unsigned long long)n;
+        ++c_sweeps;
+        const bool conv = st.flips == 0;
+        st.flips = 0;
+        if (conv || st.d >= A.max_sweeps || (A.budget > 0 && st.total >= A.budget)) {
+          st.active = 0;
+          st.conv = conv ? 1 : 0;
+        }
+      }
+    }
+    tc::fence_proxy_async_global();
+    __syncthreads();
+    // all done?  (every replica done and no round pending)
+    if (tid == 0) s_flag[0] = 0;
+    __syncthreads();
+    if (warp == 0) {
+      const int pending = __any_sync(0xffffffffu, !st.done);
+      if (lane == 0) s_flag[0] = pending;
+    }
+    __syncthreads();
+    tc::cluster_sync();
+    if (tid == 0) {
+      int pending = 0;
+      for (uint32_t c = 0; c < kClus; ++c) pending |= (int)tc::ld_cluster_u32(tc::map_shared(&s_flag[0], c));
+      s_ctrl[3] = pending;
+    }
+    tc::cluster_sync();
+    if (!s_ctrl[3]) break;
+  }
+
+  // results
+  if (warp == 0 && my_r < A.R) {
+    const bool hb = st.minima > 0;
+    const __nv_bfloat16 *row = A.S + (size_t)my_r * n;
+    for (int i = 0; i < n; ++i)
+      A.out[(size_t)my_r * n + i] = hb ? A.best[(size_t)my_r * n + i] : (__bfloat162float(row[i]) > 0.0f ? 1 : -1);
+    A.E[my_r] = hb ? st.best : st.E;
+    if (A.minima) A.minima[my_r] = st.minima;
+    atomicAdd(A.stats + 0, c_evals);
+    atomicAdd(A.stats + 1, c_flips);
+    atomicAdd(A.stats + 2, c_minima);
+    atomicAdd(A.stats + 3, c_desc);
+    atomicAdd(A.stats + 4, c_sweeps);
+  }
+  if (failed && tid == 0) {
+    atomicExch(A.error, (int32_t)ISING_ERR_TIMEOUT);
+    // let copies and MMAs still in flight land before the CTA releases its memory
+    for (int s = 0; s < kStages; ++s)
+      if (tma_pending[s]) tc::mbar_wait(&full_bar[s], ph_full[s]);
+    if (mma_pending) {
+      tc::mma_commit(&done_bar);
+      tc::mbar_wait(&done_bar, ph_done);
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 128);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+bool dense_tc_eligible(int n) { return n >= 256 && n % 256 == 0; }
+
+static cudaError_t encode_2d(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer,
+                             uint32_t box_inner, uint32_t box_outer) {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void *p = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p) return cudaErrorNotSupported;
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  const cuuint64_t dims[2] = {inner, outer};
+  const cuuint64_t strides[1] = {inner * 2};
+  const cuuint32_t box[2] = {box_inner, box_outer};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// S: [Rp][n] BF16 device buffer (Rp a multiple of 128), Jhi/Jlo [n][n] BF16.
+cudaError_t dense_tc_run(int n, int R, int Rp, int b, uint64_t seed, const float *J, const __nv_bfloat16 *Jhi,
+                         const __nv_bfloat16 *Jlo, __nv_bfloat16 *S, int8_t *best, int8_t *out, double *E,
+                         int32_t *minima, unsigned long long *stats, int32_t *error,
+                         const ising_search_params *p, cudaStream_t s) {
+  CUtensorMap mS, mH, mL;
+  cudaError_t e;
+  if ((e = encode_2d(&mS, S, (uint64_t)n, (uint64_t)Rp, kKC, kTM)) != cudaSuccess) return e;
+  if ((e = encode_2d(&mH, Jhi, (uint64_t)n, (uint64_t)n, kKC, kTB)) != cudaSuccess) return e;
+  if ((e = encode_2d(&mL, Jlo, (uint64_t)n, (uint64_t)n, kKC, kTB)) != cudaSuccess) return e;
+  TcArgs A;
+  A.n = n;
+  A.R = R;
+  A.Rp = Rp;
+  A.b = b;
+  A.max_sweeps = p->max_sweeps;
+  A.restarts = p->restarts;
+  A.budget = p->sweep_budget;
+  A.seed = seed;
+  A.J = J;
+  A.S = S;
+  A.best = best;
+  A.out = out;
+  A.E = E;
+  A.minima = minima;
+  A.stats = stats;
+  A.error = error;
+  if ((e = cudaFuncSetAttribute(dense_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)) !=
+      cudaSuccess)
+    return e;
+  const int grid = (Rp / kTM) * kClus;
+  dense_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(mS, mH, mL, A);
+  return cudaGetLastError();
+}
+
+}  // namespace isg

@@ -92,16 +92,42 @@ __global__ void sweep_init(SweepArgs A) {
   }
 }
 
-// One colour class of one sweep.  MODE 0 int lanes, 1 FP32 lanes, 2 multi-spin coded.
+// u >= t for a bit-sliced 4-bit count (q0 least significant), t per thread.
+__device__ __forceinline__ uint32_t sliced_ge4(uint32_t q0, uint32_t q1, uint32_t q2, uint32_t q3, int t) {
+  if (t <= 0) return 0xffffffffu;
+  if (t > 15) return 0u;
+  uint32_t gt = 0, eq = 0xffffffffu;
+  const uint32_t qq[4] = {q0, q1, q2, q3};
+#pragma unroll
+  for (int p = 3; p >= 0; --p) {
+    const uint32_t tb = ((t >> p) & 1) ? 0xffffffffu : 0u;
+    gt |= eq & qq[p] & ~tb;
+    eq &= ~(qq[p] ^ tb);
+  }
+  return gt | eq;
+}
+
+// One colour class of one sweep.  MODE 0 int lanes, 1 FP32 lanes, 2 multi-spin
+// coded.  Groups are walked in an outer loop so the per-group state is read once
+// per warp and no index needs a division.
 template <int MODE, int LPS, bool LAT>
 __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
   __shared__ uint32_t s_any[32];
   __shared__ unsigned long long s_red[kST / 32];
+  __shared__ int s_off[6], s_wrap[6];
   const DevGraph &G = A.g;
   const InstDesc &I = A.I;
-  const int n = I.n;
+  const int n = I.n, L = I.lat_L;
+  const int64_t so = I.spin_off;
   const int tid = threadIdx.x, lane = threadIdx.x & 31;
   if (tid < 32) s_any[tid] = 0;
+  if (LAT && tid < 6) {
+    // direction d: +x, -x, +y, -y, +z, -z; stride and wrap-around correction
+    const int a = tid >> 1;
+    const int st = a == 0 ? 1 : (a == 1 ? L : L * L);
+    s_off[tid] = (tid & 1) ? -st : st;
+    s_wrap[tid] = (tid & 1) ? L * st : -L * st;
+  }
   __syncthreads();
   int c0, c1;
   if (A.sequential) {
@@ -114,151 +140,121 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
   const int cs = c1 - c0;
   unsigned long long my_flips = 0;
   constexpr uint32_t lmask = LPS == 32 ? 0xffffffffu : ((1u << LPS) - 1u);
-  const int L = I.lat_L;
 
   if (MODE == 2) {
     const int8_t *hi = reinterpret_cast<const int8_t *>(G.h);
     const int8_t *Ji = reinterpret_cast<const int8_t *>(G.J);
-    const int64_t items = (int64_t)A.G * cs;
-    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + tid; it < items; it += (int64_t)gridDim.x * blockDim.x) {
-      const int g = (int)(it / cs);
-      const int v = c0 + (int)(it % cs);
-      const uint32_t active = A.gs[g].active;
+    const int D = I.lat_d;
+    for (int g = 0; g < A.G; ++g) {
+      const uint32_t active = A.gs[g].active & lmask;
       if (!active) continue;
-      const int j = A.sequential ? v : __ldg(G.order + I.spin_off + v);
-      const int64_t gj = I.spin_off + j;
-      const uint32_t *swg = A.sw + (size_t)g * n;
-      const uint32_t wj = swg[j];
-      uint32_t q0 = 0, q1 = 0, q2 = 0, q3 = 0;
-      int deg;
-      if (LAT) {
-        const uint32_t meta = __ldg(G.meta + I.spin_off + v);
-        deg = 2 * I.lat_d;
-        for (int k = 0; k < deg; ++k) {
-          const int i = lat_nbr(j, meta, k, L);
-          uint32_t x = wj ^ swg[i] ^ (((meta >> (26 + k)) & 1u) ? 0xffffffffu : 0u);
-          uint32_t cy = q0 & x;
-          q0 ^= x;
-          x = cy;
-          cy = q1 & x;
-          q1 ^= x;
-          x = cy;
-          cy = q2 & x;
-          q2 ^= x;
-          q3 ^= cy;
-        }
-      } else {
-        const uint32_t k0 = __ldg(G.row + gj), k1 = __ldg(G.row + gj + 1);
-        deg = (int)(k1 - k0);
-        for (uint32_t kk = k0; kk < k1; ++kk) {
-          uint32_t x = wj ^ swg[__ldg(G.col + kk)] ^ (__ldg(Ji + kk) < 0 ? 0xffffffffu : 0u);
-          uint32_t cy = q0 & x;
-          q0 ^= x;
-          x = cy;
-          cy = q1 & x;
-          q1 ^= x;
-          x = cy;
-          cy = q2 & x;
-          q2 ^= x;
-          q3 ^= cy;
-        }
-      }
-      const int hv = __ldg(hi + gj);
-      uint32_t flip;
-      auto ge = [&](int t) -> uint32_t {
-        if (t <= 0) return 0xffffffffu;
-        if (t > 15) return 0u;
-        uint32_t gt = 0, eq = 0xffffffffu;
-        const uint32_t qq[4] = {q0, q1, q2, q3};
+      uint32_t *swg = A.sw + (size_t)g * n;
+      uint32_t anyg = 0;
+      for (int t = blockIdx.x * blockDim.x + tid; t < cs; t += gridDim.x * blockDim.x) {
+        const int v = c0 + t;
+        const int j = A.sequential ? v : __ldg(G.order + so + v);
+        const uint32_t wj = swg[j];
+        const int hv = __ldg(hi + so + j);
+        uint32_t flip;
+        if (LAT) {
+          // field folded into the count: flip iff >= deg/2 + 1 of bonds+field unsatisfied
+          const uint32_t info = __ldg(G.latinfo + so + v);
+          uint32_t x[6];
 #pragma unroll
-        for (int p = 3; p >= 0; --p) {
-          const uint32_t tb = ((t >> p) & 1) ? 0xffffffffu : 0u;
-          gt |= eq & qq[p] & ~tb;
-          eq &= ~(qq[p] ^ tb);
+          for (int d = 0; d < 6; ++d) {
+            x[d] = 0u;
+            if (d < 2 * D) {
+              const int nb = j + s_off[d] + (((info >> d) & 1u) ? s_wrap[d] : 0);
+              x[d] = wj ^ swg[nb] ^ (((info >> (8 + d)) & 1u) ? 0xffffffffu : 0u);
+            }
+          }
+          const uint32_t uf = hv == 0 ? 0u : (hv > 0 ? ~wj : wj);
+          const uint32_t s1 = x[0] ^ x[1] ^ x[2], c1b = (x[0] & x[1]) | (x[0] & x[2]) | (x[1] & x[2]);
+          if (D == 3) {
+            const uint32_t s2 = x[3] ^ x[4] ^ x[5], c2b = (x[3] & x[4]) | (x[3] & x[5]) | (x[4] & x[5]);
+            const uint32_t c3b = (s1 & s2) | (s1 & uf) | (s2 & uf);
+            flip = (c1b & c2b) | (c1b & c3b) | (c2b & c3b);
+          } else {
+            const uint32_t s2 = x[3] ^ uf ^ s1, c2b = (x[3] & uf) | (x[3] & s1) | (uf & s1);
+            flip = (c1b & c2b) | ((c1b | c2b) & s2);
+          }
+        } else {
+          uint32_t q0 = 0, q1 = 0, q2 = 0, q3 = 0;
+          const uint32_t k0 = __ldg(G.row + so + j), k1 = __ldg(G.row + so + j + 1);
+          const int deg = (int)(k1 - k0);
+          for (uint32_t kk = k0; kk < k1; ++kk) {
+            uint32_t x = wj ^ swg[__ldg(G.col + kk)] ^ (__ldg(Ji + kk) < 0 ? 0xffffffffu : 0u);
+            uint32_t cy = q0 & x;
+            q0 ^= x;
+            x = cy;
+            cy = q1 & x;
+            q1 ^= x;
+            x = cy;
+            cy = q2 & x;
+            q2 ^= x;
+            q3 ^= cy;
+          }
+          if (hv == 0) {
+            flip = sliced_ge4(q0, q1, q2, q3, deg / 2 + 1);
+          } else {
+            const uint32_t plus = hv > 0 ? wj : ~wj;
+            flip = (sliced_ge4(q0, q1, q2, q3, (deg + 1) / 2 + 1) & plus) |
+                   (sliced_ge4(q0, q1, q2, q3, deg >= 1 ? (deg - 1) / 2 + 1 : 0) & ~plus);
+          }
         }
-        return gt | eq;
-      };
-      if (hv == 0) {
-        flip = ge(deg / 2 + 1);
-      } else {
-        const uint32_t plus = hv > 0 ? wj : ~wj;
-        flip = (ge((deg + 1) / 2 + 1) & plus) | (ge(deg >= 1 ? (deg - 1) / 2 + 1 : 0) & ~plus);
+        flip &= active;
+        if (flip) {
+          swg[j] = wj ^ flip;
+          anyg |= flip;
+          my_flips += __popc(flip);
+        }
       }
-      flip &= active & lmask;
-      if (flip) {
-        A.sw[(size_t)g * n + j] = wj ^ flip;
-        atomicOr(&s_any[g], flip);
-        my_flips += __popc(flip);
-      }
+      anyg = __reduce_or_sync(0xffffffffu, anyg);
+      if (lane == 0 && anyg) atomicOr(&s_any[g], anyg);
     }
   } else {
     constexpr int SPW = 32 / LPS;
     const int sub = lane / LPS, ln = lane % LPS;
-    const int witems_per_g = (cs + SPW - 1) / SPW;
-    const int64_t witems = (int64_t)A.G * witems_per_g;
-    const int64_t wstride = (int64_t)gridDim.x * (blockDim.x / 32);
-    for (int64_t wi = (int64_t)blockIdx.x * (blockDim.x / 32) + (tid >> 5); wi < witems; wi += wstride) {
-      const int g = (int)(wi / witems_per_g);
-      const int v = c0 + (int)(wi % witems_per_g) * SPW + sub;
+    const int witems = (cs + SPW - 1) / SPW;
+    const int wstride = gridDim.x * (blockDim.x >> 5);
+    const int wid = blockIdx.x * (blockDim.x >> 5) + (tid >> 5);
+    for (int g = 0; g < A.G; ++g) {
       const GroupState &S = A.gs[g];
       const uint32_t active = S.active;
-      if (!active) continue;  // warp-uniform: g is uniform in the warp
-      const bool valid = v < c1;
-      const int j = valid ? (A.sequential ? v : __ldg(G.order + I.spin_off + v)) : 0;
-      const int64_t gj = I.spin_off + j;
-      const uint32_t *swg = A.sw + (size_t)g * n;
-      const uint32_t *fmg = A.fm + (size_t)g * n;
-      const uint32_t wj = valid ? swg[j] : 0u;
-      const bool up = (wj >> ln) & 1u;
-      bool flip = false;
-      if (valid) {
-        const uint32_t meta = LAT ? __ldg(G.meta + I.spin_off + v) : 0u;
-        const uint32_t k0 = LAT ? 0u : __ldg(G.row + gj);
-        const uint32_t k1 = LAT ? (uint32_t)(2 * I.lat_d) : __ldg(G.row + gj + 1);
-        const uint32_t e0 = __ldg(G.inc_ptr + gj), e1 = __ldg(G.inc_ptr + gj + 1);
-        if (MODE == 0) {
-          int f = __ldg(reinterpret_cast<const int8_t *>(G.h) + gj);
-          for (uint32_t kk = k0; kk < k1; ++kk) {
-            int i, w;
+      if (!active) continue;
+      const int dd = S.d;
+      const bool refresh = (dd == 0) || (A.refresh > 0 && dd % A.refresh == 0);
+      uint32_t *swg = A.sw + (size_t)g * n;
+      uint32_t *fmg = A.fm + (size_t)g * n;
+      float *Fg = (MODE == 1) ? A.F + (size_t)g * n * LPS : nullptr;
+      uint32_t anyg = 0;
+      for (int wi = wid; wi < witems; wi += wstride) {
+        const int v = c0 + wi * SPW + sub;
+        const bool valid = v < c1;
+        const int j = valid ? (A.sequential ? v : __ldg(G.order + so + v)) : 0;
+        const uint32_t wj = valid ? swg[j] : 0u;
+        const bool up = (wj >> ln) & 1u;
+        bool flip = false;
+        if (valid) {
+          const uint32_t meta = LAT ? __ldg(G.meta + so + v) : 0u;
+          const uint32_t k0 = LAT ? 0u : __ldg(G.row + so + j);
+          const uint32_t k1 = LAT ? (uint32_t)(2 * I.lat_d) : __ldg(G.row + so + j + 1);
+          const uint32_t e0 = LAT ? 0u : __ldg(G.inc_ptr + so + j);
+          const uint32_t e1 = LAT ? 0u : __ldg(G.inc_ptr + so + j + 1);
+          auto nbr = [&](uint32_t kk) -> int {
             if (LAT) {
-              i = lat_nbr(j, meta, (int)kk, L);
-              w = __ldg(reinterpret_cast<const int8_t *>(G.Jpos) + (int64_t)kk * G.nsp + I.spin_off + v);
-            } else {
-              i = __ldg(G.col + kk);
-              w = __ldg(reinterpret_cast<const int8_t *>(G.J) + kk);
+              const int dir = (meta >> (8 + 3 * kk)) & 7;
+              return j + s_off[dir] + (((meta >> kk) & 1u) ? s_wrap[dir] : 0);
             }
-            f += ((swg[i] >> ln) & 1u) ? w : -w;
-          }
-          for (uint32_t q = e0; q < e1; ++q) {
-            const int e = __ldg(G.inc_edge + q);
-            uint32_t neg = 0;
-            for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
-              const int mm = __ldg(G.hmem + m);
-              if (mm != j) neg ^= ~(swg[mm] >> ln) & 1u;
-            }
-            const int w = __ldg(reinterpret_cast<const int8_t *>(G.hJ) + e);
-            f += neg ? -w : w;
-          }
-          flip = up ? (f < 0) : (f > 0);
-        } else {
-          const int d = S.d;
-          const bool refresh = (d == 0) || (A.refresh > 0 && d % A.refresh == 0);
-          float *Fp = A.F + ((size_t)g * n + v) * LPS + ln;
-          const float *hJ = reinterpret_cast<const float *>(G.hJ);
-          float f;
-          if (refresh) {
-            double acc = (double)__ldg(reinterpret_cast<const float *>(G.h) + gj);
+            return __ldg(G.col + kk);
+          };
+          if (MODE == 0) {
+            int f = __ldg(reinterpret_cast<const int8_t *>(G.h) + so + j);
+            const int8_t *Jp = LAT ? reinterpret_cast<const int8_t *>(G.Jpos) + so + v : nullptr;
             for (uint32_t kk = k0; kk < k1; ++kk) {
-              int i;
-              double w;
-              if (LAT) {
-                i = lat_nbr(j, meta, (int)kk, L);
-                w = (double)__ldg(reinterpret_cast<const float *>(G.Jpos) + (int64_t)kk * G.nsp + I.spin_off + v);
-              } else {
-                i = __ldg(G.col + kk);
-                w = (double)__ldg(reinterpret_cast<const float *>(G.J) + kk);
-              }
-              acc = __dadd_rn(acc, ((swg[i] >> ln) & 1u) ? w : -w);
+              const int i = nbr(kk);
+              const int w = LAT ? (int)__ldg(Jp + (int64_t)kk * G.nsp) : (int)__ldg(reinterpret_cast<const int8_t *>(G.J) + kk);
+              f += ((swg[i] >> ln) & 1u) ? w : -w;
             }
             for (uint32_t q = e0; q < e1; ++q) {
               const int e = __ldg(G.inc_edge + q);
@@ -267,60 +263,91 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
                 const int mm = __ldg(G.hmem + m);
                 if (mm != j) neg ^= ~(swg[mm] >> ln) & 1u;
               }
-              const double w = (double)__ldg(hJ + e);
-              acc = __dadd_rn(acc, neg ? -w : w);
+              const int w = __ldg(reinterpret_cast<const int8_t *>(G.hJ) + e);
+              f += neg ? -w : w;
             }
-            f = __double2float_rn(acc);
-            *Fp = f;
+            flip = up ? (f < 0) : (f > 0);
           } else {
-            f = *Fp;
-            bool changed = false;
-            for (uint32_t kk = k0; kk < k1; ++kk) {
-              int i;
-              if (LAT) i = lat_nbr(j, meta, (int)kk, L);
-              else i = __ldg(G.col + kk);
-              if ((fmg[i] >> ln) & 1u) {
-                float w2;
-                if (LAT)
-                  w2 = 2.0f * __ldg(reinterpret_cast<const float *>(G.Jpos) + (int64_t)kk * G.nsp + I.spin_off + v);
-                else
-                  w2 = 2.0f * __ldg(reinterpret_cast<const float *>(G.J) + kk);
-                f = __fadd_rn(f, ((swg[i] >> ln) & 1u) ? w2 : -w2);
-                changed = true;
+            const float *Jp = LAT ? reinterpret_cast<const float *>(G.Jpos) + so + v : nullptr;
+            const float *hJ = reinterpret_cast<const float *>(G.hJ);
+            float *Fp = Fg + (size_t)v * LPS + ln;
+            float f;
+            if (refresh) {
+              double acc = (double)__ldg(reinterpret_cast<const float *>(G.h) + so + j);
+              for (uint32_t kk = k0; kk < k1; ++kk) {
+                const int i = nbr(kk);
+                const double w = LAT ? (double)__ldg(Jp + (int64_t)kk * G.nsp)
+                                     : (double)__ldg(reinterpret_cast<const float *>(G.J) + kk);
+                acc = __dadd_rn(acc, ((swg[i] >> ln) & 1u) ? w : -w);
               }
-            }
-            for (uint32_t q = e0; q < e1; ++q) {
-              const int e = __ldg(G.inc_edge + q);
-              uint32_t neg = 0, par = 0;
-              for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
-                const int mm = __ldg(G.hmem + m);
-                if (mm != j) {
-                  neg ^= ~(swg[mm] >> ln) & 1u;
-                  par ^= (fmg[mm] >> ln) & 1u;
+              for (uint32_t q = e0; q < e1; ++q) {
+                const int e = __ldg(G.inc_edge + q);
+                uint32_t neg = 0;
+                for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
+                  const int mm = __ldg(G.hmem + m);
+                  if (mm != j) neg ^= ~(swg[mm] >> ln) & 1u;
                 }
+                const double w = (double)__ldg(hJ + e);
+                acc = __dadd_rn(acc, neg ? -w : w);
               }
-              if (par) {
-                const float w2 = 2.0f * __ldg(hJ + e);
-                f = __fadd_rn(f, neg ? -w2 : w2);
-                changed = true;
+              f = __double2float_rn(acc);
+              *Fp = f;
+              flip = up ? (f < 0.0f) : (f > 0.0f);
+            } else {
+              // Pull the flips of the neighbours since this spin's previous visit.
+              // If none flipped (for this lane) the field and so the decision
+              // are unchanged: a spin left stable by its last visit stays stable.
+              uint32_t flipped_k = 0;
+              for (uint32_t kk = k0; kk < k1; ++kk)
+                if ((fmg[nbr(kk)] >> ln) & 1u) flipped_k |= 1u << (kk - k0);
+              uint32_t par_e = 0;
+              for (uint32_t q = e0; q < e1; ++q) {
+                const int e = __ldg(G.inc_edge + q);
+                uint32_t par = 0;
+                for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
+                  const int mm = __ldg(G.hmem + m);
+                  if (mm != j) par ^= (fmg[mm] >> ln) & 1u;
+                }
+                par_e |= par << (q - e0);
+              }
+              if (flipped_k | par_e) {
+                f = *Fp;
+                for (uint32_t kk = k0; kk < k1; ++kk)
+                  if ((flipped_k >> (kk - k0)) & 1u) {
+                    const int i = nbr(kk);
+                    const float w2 = 2.0f * (LAT ? __ldg(Jp + (int64_t)kk * G.nsp)
+                                                 : __ldg(reinterpret_cast<const float *>(G.J) + kk));
+                    f = __fadd_rn(f, ((swg[i] >> ln) & 1u) ? w2 : -w2);
+                  }
+                for (uint32_t q = e0; q < e1; ++q)
+                  if ((par_e >> (q - e0)) & 1u) {
+                    const int e = __ldg(G.inc_edge + q);
+                    uint32_t neg = 0;
+                    for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
+                      const int mm = __ldg(G.hmem + m);
+                      if (mm != j) neg ^= ~(swg[mm] >> ln) & 1u;
+                    }
+                    const float w2 = 2.0f * __ldg(hJ + e);
+                    f = __fadd_rn(f, neg ? -w2 : w2);
+                  }
+                *Fp = f;
+                flip = up ? (f < 0.0f) : (f > 0.0f);
               }
             }
-            if (changed) *Fp = f;
           }
-          flip = up ? (f < 0.0f) : (f > 0.0f);
+          flip = flip && ((active >> ln) & 1u);
         }
-        flip = flip && ((active >> ln) & 1u);
-      }
-      const uint32_t m = __ballot_sync(0xffffffffu, flip);
-      const uint32_t seg = (m >> (sub * LPS)) & lmask;
-      if (valid && ln == 0) {
-        if (seg) A.sw[(size_t)g * n + j] = wj ^ seg;
-        if (MODE == 1) {
-          if (seg || A.fm[(size_t)g * n + j]) A.fm[(size_t)g * n + j] = seg;
+        const uint32_t m = __ballot_sync(0xffffffffu, flip);
+        const uint32_t seg = (m >> (sub * LPS)) & lmask;
+        if (valid && ln == 0) {
+          if (seg) swg[j] = wj ^ seg;
+          if (MODE == 1 && (seg || fmg[j])) fmg[j] = seg;
         }
-        if (seg) atomicOr(&s_any[g], seg);
+        anyg |= seg;
+        my_flips += flip ? 1 : 0;
       }
-      my_flips += flip ? 1 : 0;
+      anyg = __reduce_or_sync(0xffffffffu, anyg);
+      if (lane == 0 && anyg) atomicOr(&s_any[g], anyg);
     }
   }
   __syncthreads();

@@ -411,6 +411,25 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *_
                   }
                   f = __double2float_rn(acc);
                 } else {
+                  // Only neighbours that flipped since this spin's previous visit
+                  // change its field; with none, field and decision are unchanged.
+                  uint32_t flipped_k = 0, par_e = 0;
+                  for (uint32_t kk = k0; kk < k1; ++kk)
+                    if ((fm[__ldg(G.col + kk)] >> lane) & 1u) flipped_k |= 1u << ((kk - k0) & 31);
+                  for (uint32_t q = e0; q < e1; ++q) {
+                    const int e = __ldg(G.inc_edge + q);
+                    uint32_t par = 0;
+                    for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
+                      const int mm = __ldg(G.hmem + m);
+                      if (mm != j) par ^= (fm[mm] >> lane) & 1u;
+                    }
+                    par_e |= par << ((q - e0) & 31);
+                  }
+                  const bool dirty = (flipped_k | par_e) != 0 || (k1 - k0) > 32 || (e1 - e0) > 32;
+                  if (!dirty) {
+                    flip = false;
+                    goto decided;
+                  }
                   f = F[(size_t)j * 32 + lane];
                   for (uint32_t kk = k0; kk < k1; ++kk) {
                     const int i = __ldg(G.col + kk);
@@ -437,6 +456,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *_
                 }
                 F[(size_t)j * 32 + lane] = f;
                 flip = up ? (f < 0.0f) : (f > 0.0f);
+              decided:;
               }
               flip = flip && ((active >> lane) & 1u);
               const uint32_t m = __ballot_sync(0xffffffffu, flip);

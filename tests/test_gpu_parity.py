@@ -246,3 +246,34 @@ def test_dense_sk_tensor_core_path():
     assert abs(np.mean(E) - np.mean(Eo64)) <= 0.02 * abs(np.mean(Eo64))
     assert res.stats["minima"] == 2 * R
     h.close()
+
+
+@pytest.mark.parametrize("n,R", [(512, 96), (768, 256)])
+def test_dense_sk_tcgen05_kernel(n, R, monkeypatch):
+    """The hand-written tcgen05 kernel (n a multiple of 256): energies of the
+    returned states within 1e-6 of the FP64 oracle, 1-flip minima within the
+    field error bound, and the same results as the library-GEMM comparator on
+    the large majority of replicas (fields differ only in FP32 rounding)."""
+    inst = W.sk(n, seed=n)
+    h = isg.Handle([inst])
+    res = h.local_search([29], R, max_sweeps=500, restarts=2, kernel=isg.KERNEL_DENSE_TC)
+    torch.cuda.synchronize()
+    sp = res.spins.view(R, n).cpu().numpy().copy()
+    E = res.energy.view(R).cpu().numpy().copy()
+    st = dict(res.stats)
+    oi = oracle.OracleInstance(inst)
+    Eo = oracle.energies(oi, sp)
+    rel = np.abs(E - Eo) / np.abs(Eo)
+    assert rel.max() <= 1e-6, rel.max()
+    for r in range(R):
+        f = oracle.local_fields(oi, sp[r])
+        assert np.all(sp[r] * f >= -1e-4)
+    assert st["minima"] == 2 * R and st["descents"] == 2 * R
+    monkeypatch.setenv("ISING_DENSE_CUBLAS", "1")
+    ref = h.local_search([29], R, max_sweeps=500, restarts=2, kernel=isg.KERNEL_DENSE_TC)
+    torch.cuda.synchronize()
+    sp2 = ref.spins.view(R, n).cpu().numpy()
+    same = np.mean(np.all(sp == sp2, axis=1))
+    assert same >= 0.8, same
+    assert abs(np.mean(E) - ref.energy.cpu().numpy().mean()) <= 1e-3 * abs(np.mean(E))
+    h.close()
