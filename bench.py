@@ -36,8 +36,9 @@ METRIC = "spin-flip evals/s, minima/s on 1 GB300: batched/mixed vs plain at equa
 UNIT = "flip_evals/s"
 
 
-def make_workload(name: str):
-    """(instances, replicas, search kwargs, description)."""
+def make_workload(name: str, instances: int = 0, sk_n: int = 0):
+    """(instances, replicas, search kwargs, description).  `instances` (c3) and
+    `sk_n` (c4) shrink the workload for profiling captures."""
     if name == "c1":
         inst = W.lattice((16, 16), periodic=True, couplings="pm1", seed=W.config_seed(0))
         return [inst], 64, dict(max_sweeps=1000, restarts=10), "16x16 periodic +/-J lattice, 64 replicas, 10 restarts"
@@ -46,11 +47,11 @@ def make_workload(name: str):
         return [inst], 1024, dict(max_sweeps=100, restarts=10), \
             "32^3 periodic +/-J lattice, h in {-1,0,1}, 1024 replicas, <=100 sweeps/descent, 10 restarts"
     if name == "c3":
-        insts = W.chimera_batch(4096, 4, 16, seed=W.config_seed(2))
+        insts = W.chimera_batch(instances or 4096, 4, 16, seed=W.config_seed(2))
         return insts, 32, dict(max_sweeps=1000, restarts=1, refresh_every=16), \
             "4096 K4,4 cell grids (side 4..16), Gaussian J,h + one 3-spin coupling per cell, 32 replicas"
     if name == "c4":
-        inst = W.sk(4096, seed=W.config_seed(3))
+        inst = W.sk(sk_n or 4096, seed=W.config_seed(3))
         return [inst], 4096, dict(max_sweeps=1000, restarts=1, refresh_every=16, schedule=1), \
             "dense SK N=4096, 4096 replicas, sequential schedule"
     if name == "c5":
@@ -157,6 +158,23 @@ def oracle_sample(name, insts, R, kw, budget_s=10.0):
     return evals / dt, minima / dt, desc, dt
 
 
+# ----------------------------------------------------------------------------- multi-rank
+def job_totals(t_local, evals_local, minima_local, dist=None, device=None):
+    """Whole-job figures: the slowest rank's time, the work of all ranks summed.
+
+    Replicas are independent, so each rank runs its own replicas (its own seeds)
+    with no data-path collective; only these two reductions cross ranks.
+    """
+    if dist is None:
+        return t_local, evals_local, minima_local
+    import torch
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    w = torch.tensor([float(evals_local), float(minima_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(w[0].item()), float(w[1].item())
+
+
 # ----------------------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
@@ -169,12 +187,26 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    # smaller variants of a workload, for profiler captures
+    ap.add_argument("--replicas", type=int, default=0)
+    ap.add_argument("--restarts", type=int, default=0)
+    ap.add_argument("--sweep-budget", type=int, default=-1)
+    ap.add_argument("--instances", type=int, default=0)
+    ap.add_argument("--sk-n", type=int, default=0)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    insts, R, kw, desc = make_workload(args.workload)
+    insts, R, kw, desc = make_workload(args.workload, args.instances, args.sk_n)
+    if args.replicas:
+        R = args.replicas
+    if args.restarts:
+        kw["restarts"] = args.restarts
+    if args.sweep_budget >= 0:
+        kw["sweep_budget"] = args.sweep_budget
+    if args.replicas or args.restarts or args.sweep_budget >= 0 or args.instances or args.sk_n:
+        desc += f" [reduced: replicas={R}, {kw}]"
 
     if args.impl == "reference":
         if rank != 0:
@@ -243,13 +275,8 @@ def main():
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = [a.elapsed_time(b) for a, b in ev_pairs]
-    t_total = sum(ms) / 1e3
-    if dist is not None:
-        t = torch.tensor([t_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
-    evals_job = st["flip_evals"] * args.steps * world
-    minima_job = st["minima"] * args.steps * world
+    t_total, evals_job, minima_job = job_totals(sum(ms) / 1e3, st["flip_evals"] * args.steps,
+                                                st["minima"] * args.steps, dist, dev)
     value = evals_job / t_total
 
     # end to end: host seeds in, host results out (pinned), through the C ABI
@@ -268,30 +295,42 @@ def main():
         e2e_ms.append(a.elapsed_time(b))
     e2e_value = st["flip_evals"] * len(e2e_ms) / (sum(e2e_ms) / 1e3)
 
-    # roofline of the dominant kernel (the whole step is one kernel launch for tile/MSC)
+    # roofline of the dominant kernel
     hbm, bf16, bf16s, peak_src = measured_peaks()
-    n_launch_per_step = 1
-    roof = roofline(args.workload, chosen, insts, R, st, t_total / args.steps, clk, hbm, bf16s, peak_src)
+    n_launch_per_step = st.get("launches", 1)
+    eff_kernel = chosen
+    if chosen == isg.KERNEL_MSC or (chosen == isg.KERNEL_SWEEP and insts[0].dtype == "i8"):
+        eff_kernel = 2 if chosen == isg.KERNEL_MSC else 3
+    roof = roofline(args.workload, eff_kernel, insts, R, st, t_total / args.steps, clk, hbm, bf16s, peak_src)
+    st = {k: v for k, v in st.items() if k != "launches"}
 
     # equal-energy comparison with the plain comparator kernel
     plain = None
     if not args.no_plain and chosen != isg.KERNEL_PLAIN:
+        comparator = isg.KERNEL_PLAIN
+        if chosen == isg.KERNEL_DENSE_TC:
+            # dense: the straightforward blocked version with library GEMMs
+            os.environ["ISING_DENSE_CUBLAS"] = "1"
+            comparator = isg.KERNEL_DENSE_TC
         try:
-            pr = h.local_search(seeds, R, kernel=isg.KERNEL_PLAIN, stats=True, **kw)
+            pr = h.local_search(seeds, R, kernel=comparator, stats=True, **kw)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            pr = h.local_search(seeds, R, kernel=isg.KERNEL_PLAIN, stats=True, **kw)
+            pr = h.local_search(seeds, R, kernel=comparator, stats=True, **kw)
             b.record(stream)
             torch.cuda.synchronize()
             pms = a.elapsed_time(b)
             same = bool(torch.equal(pr.energy, E)) if insts[0].dtype == "i8" else float(
                 (pr.energy - E).abs().max().item())
-            plain = {"value": pr.stats["flip_evals"] / (pms / 1e3), "unit": UNIT, "ms_per_step": pms,
+            plain = {"kind": "cublas_blocked" if chosen == isg.KERNEL_DENSE_TC else "plain",
+                     "value": pr.stats["flip_evals"] / (pms / 1e3), "unit": UNIT, "ms_per_step": pms,
                      "energy_match": same, "speedup": value / (pr.stats["flip_evals"] / (pms / 1e3))}
-        except Exception as ex:  # plain kernel not available for this workload
+        except Exception as ex:  # comparator not available for this workload
             plain = {"unavailable": str(ex)}
+        finally:
+            os.environ.pop("ISING_DENSE_CUBLAS", None)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -314,7 +353,7 @@ def main():
             "work_per_step": st,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * len(insts),
                     "d2h_bytes_per_step": R * total_spins + 8 * R * len(insts)},
-            "gpu_launches": n_launch_per_step * args.steps,
+            "gpu_launches": int(n_launch_per_step) * args.steps,
             "clocks": clk,
             "roofline": roof,
             "plain": plain,
@@ -327,27 +366,42 @@ def main():
 
 
 def roofline(name, kernel, insts, R, st, step_s, clk, hbm, bf16s, src):
-    """Roofline of the step's dominant kernel (derivations in the design doc)."""
+    """Roofline of the step's dominant kernel.  The algorithmic work per unit is
+    the method's own (not the kernel's instruction count); the design doc derives each
+    figure.  The time is the whole step measured with CUDA events, so `achieved`
+    is a lower bound for the dominant kernel alone."""
     sm_count = 152
     mhz = (clk or {}).get("sm_mhz") or 2070.0
-    if kernel == 2:  # multi-spin coded tile: ALU/issue bound
-        # 22 integer/logic lane-operations per (spin, 32-replica word) visit for degree 6
-        deg = insts[0].nnz / insts[0].n if insts[0].row_ptr is not None else 6
-        ops_per_word = 3 * deg + 4
-        words = st["flip_evals"] / 32.0
-        achieved = words * ops_per_word / step_s / 1e12
+    inst = insts[0]
+    deg = sum(i.nnz for i in insts) / max(1, sum(i.n for i in insts)) if inst.row_ptr is not None else inst.n - 1
+    lattice = inst.meta.get("kind") == "lattice" and inst.meta.get("periodic") and len(set(inst.meta["dims"])) == 1
+    msc = inst.dtype == "i8" and inst.hyper_ptr is None and np.all(np.abs(inst.J) == 1) and (
+        inst.h is None or np.all(np.abs(inst.h) <= 1))
+    if msc and kernel in (2, 3):
+        # integer/logic lane-operations per (spin, replica word): per bond one
+        # unsatisfied-mask op, one for the field, about one adder op per input,
+        # the flip mask and the word update: 2 deg + 4
+        lanes = 32 if kernel == 2 else (32 if R > 16 else (16 if R > 8 else 8))
+        ops = 2 * deg + 4
+        words = st["flip_evals"] / lanes
+        achieved = words * ops / step_s / 1e12
         peak = sm_count * 128 * mhz * 1e6 / 1e12
-        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": None, "peak_source": f"152 SMs x 128 int lanes x {mhz:.0f} MHz (median under load)",
-                "ops_per_word": ops_per_word}
-    # lane-per-replica tile and sweep kernels: bytes moved per visit
-    evals = st["flip_evals"]
-    fl = insts[0].dtype == "f32"
-    deg = sum(i.nnz for i in insts) / sum(i.n for i in insts)
-    per_visit = (8.0 if fl else 0.0) + (deg * 8.0 + 8.0) / 32.0 + 0.25
-    achieved = evals * per_visit / step_s / 1e9
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlane-ops/s", "frac": achieved / peak,
+                "traffic": None, "ops_per_word": ops, "replicas_per_word": lanes,
+                "peak_source": f"derived: {sm_count} SMs x 128 integer lanes x {mhz:.0f} MHz (median SM clock under load)"}
+    if kernel == 4:
+        n = inst.n
+        flops = (st["sweeps"] + st["descents"]) * 4.0 * n * n
+        achieved = flops / step_s / 1e12
+        return {"bound": "tensor", "achieved": achieved, "peak": bf16s, "unit": "TFLOP/s", "frac": achieved / bf16s,
+                "traffic": None, "flops_per_replica_sweep": 4.0 * n * n,
+                "peak_source": f"{src} bf16 sustained (MEASURED_PEAKS.json)"}
+    # incremental method in HBM terms: per visit a 4-byte field read and 1/8 byte of
+    # spin; per accepted flip deg x (8 bytes coupling + index, 8 bytes field update)
+    byts = st["flip_evals"] * 4.125 + st["flips"] * deg * 16.0
+    achieved = byts / step_s / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": None, "peak_source": src, "bytes_per_eval": per_visit}
+            "traffic": None, "bytes_per_step": byts, "peak_source": f"{src} copy bandwidth (MEASURED_PEAKS.json)"}
 
 
 if __name__ == "__main__":

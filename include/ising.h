@@ -160,9 +160,10 @@ typedef struct {
  * flip_evals = spins visited (one gain computed and decided per visit),
  * flips = accepted moves, minima = converged descents, descents = descents run,
  * sweeps = sweeps run.  They depend only on the method's semantics, not on the
- * kernel that ran it.                                                          */
+ * kernel that ran it.  launches = this library's kernel launches the call
+ * enqueued (kernel nodes of replayed graphs included; library GEMMs not).      */
 typedef struct {
-  uint64_t flip_evals, flips, minima, descents, sweeps;
+  uint64_t flip_evals, flips, minima, descents, sweeps, launches;
 } ising_stats;
 
 typedef struct ising_handle ising_handle;

@@ -49,7 +49,7 @@ class _Params(C.Structure):
 
 class _Stats(C.Structure):
     _fields_ = [("flip_evals", C.c_uint64), ("flips", C.c_uint64), ("minima", C.c_uint64),
-                ("descents", C.c_uint64), ("sweeps", C.c_uint64)]
+                ("descents", C.c_uint64), ("sweeps", C.c_uint64), ("launches", C.c_uint64)]
 
 
 _lib = None

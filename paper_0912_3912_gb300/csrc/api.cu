@@ -2,6 +2,8 @@
 // colouring, planning, dispatch to the kernel families, status strings.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <vector>
@@ -268,6 +270,7 @@ void free_handle(ising_handle *h) {
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (h->h_stats_pinned) cudaFreeHost(h->h_stats_pinned);
+  if (h->tile_exec) cudaGraphExecDestroy(h->tile_exec);
   cudaSetDevice(cur);
   delete h;
 }
@@ -320,6 +323,28 @@ int32_t resolve_kernel(ising_handle *h, int32_t R, const ising_search_params *p)
   }
 }
 
+// Cluster split of the multi-spin-coded lattice path: worth it when the tiles
+// alone would leave most SMs idle.  Every instance must split into P
+// power-of-two chunks of at least 1024 sites (whole Philox blocks).
+int msc_cluster_size(const ising_handle *h, int32_t R, const ising_search_params *p) {
+  if (!h->msc_ok || !h->all_lattice || p->schedule != ISING_SCHED_COLOUR) return 0;
+  if (getenv("ISING_NO_CLUSTER")) return 0;
+  const int64_t tiles = (int64_t)h->n_inst * ((R + 31) / 32);
+  for (int P : {4, 2}) {
+    if (tiles * P > 2 * (int64_t)h->sm_count) continue;
+    bool ok = true;
+    int d = -1;
+    for (const auto &I : h->inst) {
+      const int csz = I.n / P;
+      if (I.n % P || csz < 1024 || (csz & (csz - 1)) || csz % 128) ok = false;
+      if (d >= 0 && I.lat_d != d) ok = false;
+      d = I.lat_d;
+    }
+    if (ok) return P;
+  }
+  return 0;
+}
+
 ising_status run_tile(ising_handle *h, int mode, int32_t R, const ising_search_params *p, int8_t *spins,
                       double *E, int32_t *E32, int32_t *minima, cudaStream_t s) {
   // tiles: (instance, 32-replica group), largest instances first
@@ -337,6 +362,36 @@ ising_status run_tile(ising_handle *h, int mode, int32_t R, const ising_search_p
     if (upload(&h->d_tiles, tiles) != cudaSuccess) return ISING_ERR_CUDA;
     h->n_tiles = (int32_t)tiles.size();
     h->tiles_R = R;
+  }
+  const int P = mode == 3 ? msc_cluster_size(h, R, p) : 0;
+  if (P > 0) {
+    const size_t bw_bytes = (size_t)h->n_tiles * h->nmax * sizeof(uint32_t);
+    ising_status st = ensure_scratch(h, bw_bytes + 256);
+    if (st != ISING_OK) return st;
+    TileArgs a;
+    a.g = h->graph();
+    a.tiles = h->d_tiles;
+    a.n_tiles = h->n_tiles;
+    a.queue = h->d_queue;
+    a.R = R;
+    a.max_sweeps = p->max_sweeps;
+    a.restarts = p->restarts;
+    a.budget = p->sweep_budget;
+    a.refresh = p->refresh_every;
+    a.sequential = 0;
+    a.seeds = h->d_seeds;
+    a.F = nullptr;
+    a.bw = (uint32_t *)h->d_scratch;
+    a.nmax = h->nmax;
+    a.spins = spins;
+    a.energy = E;
+    a.energy_i32 = E32;
+    a.minima = minima;
+    a.stats = h->d_stats;
+    CUDA_OK(cudaMemcpyAsync(h->d_tile_args, &a, sizeof(a), cudaMemcpyHostToDevice, s));
+    CUDA_OK(launch_msc_cluster(h, h->n_tiles, P, h->nmax / P, h->inst[0].lat_d, s));
+    h->launches += 1;
+    return ISING_OK;
   }
   const size_t smem = tile_smem_bytes(mode, h->nmax);
   int per_sm = tile_max_ctas_per_sm(mode, smem);
@@ -367,9 +422,90 @@ ising_status run_tile(ising_handle *h, int mode, int32_t R, const ising_search_p
   a.minima = minima;
   a.stats = h->d_stats;
   CUDA_OK(cudaMemcpyAsync(h->d_tile_args, &a, sizeof(a), cudaMemcpyHostToDevice, s));
-  CUDA_OK(cudaMemsetAsync(h->d_queue, 0, sizeof(int32_t), s));
-  CUDA_OK(launch_tile(h, mode, grid, smem, s));
+  // The launch sequence reads its arguments from device memory, so one captured
+  // graph serves every call with the same mode, grid and shared memory.
+  if (!h->tile_exec || h->tile_exec_key[0] != mode || h->tile_exec_key[1] != grid ||
+      h->tile_exec_key[2] != (int32_t)smem) {
+    if (h->tile_exec) cudaGraphExecDestroy(h->tile_exec);
+    h->tile_exec = nullptr;
+    cudaStream_t cs;
+    CUDA_OK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaMemsetAsync(h->d_queue, 0, sizeof(int32_t), cs);
+      launch_tile(h, mode, grid, smem, cs);
+      e = cudaStreamEndCapture(cs, &g);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->tile_exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+      h->tile_exec = nullptr;
+      return ISING_ERR_CUDA;
+    }
+    h->tile_exec_key[0] = mode;
+    h->tile_exec_key[1] = grid;
+    h->tile_exec_key[2] = (int32_t)smem;
+  }
+  CUDA_OK(cudaGraphLaunch(h->tile_exec, s));
+  h->launches += 1;
   return ISING_OK;
+}
+
+// ---------------------------------------------------------------- tuning cache
+// Decisions are keyed by the GPU name and an instance class (dtype, instance
+// count, largest instance, lattice / multi-spin eligibility, replicas,
+// schedule).  With ISING_TUNE_CACHE=<file> they persist across processes as
+// lines of a small JSON object: {"key": family, ...}.
+std::string tune_key(const ising_handle *h, int32_t R, const ising_search_params *p) {
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, h->device);
+  char buf[512];
+  snprintf(buf, sizeof buf, "%s|dt%d|b%d|n%d|lat%d|msc%d|dense%d|R%d|sched%d|refresh%d", prop.name, h->dtype,
+           h->n_inst, h->nmax, h->all_lattice ? 1 : 0, h->msc_ok ? 1 : 0, h->dense ? 1 : 0, R, (int)p->schedule,
+           p->refresh_every);
+  return buf;
+}
+
+std::map<std::string, int32_t> read_tune_file(const char *path) {
+  std::map<std::string, int32_t> m;
+  FILE *f = path ? fopen(path, "r") : nullptr;
+  if (!f) return m;
+  char line[1024];
+  while (fgets(line, sizeof line, f)) {
+    char *a = strchr(line, '"');
+    if (!a) continue;
+    char *b = strchr(a + 1, '"');
+    if (!b) continue;
+    char *c = strchr(b, ':');
+    if (!c) continue;
+    m[std::string(a + 1, b)] = (int32_t)strtol(c + 1, nullptr, 10);
+  }
+  fclose(f);
+  return m;
+}
+
+int32_t tune_cache_lookup(const std::string &key) {
+  const char *path = getenv("ISING_TUNE_CACHE");
+  if (!path) return -1;
+  auto m = read_tune_file(path);
+  auto it = m.find(key);
+  return it == m.end() ? -1 : it->second;
+}
+
+void tune_cache_store(const std::string &key, int32_t fam) {
+  const char *path = getenv("ISING_TUNE_CACHE");
+  if (!path) return;
+  auto m = read_tune_file(path);
+  m[key] = fam;
+  FILE *f = fopen(path, "w");
+  if (!f) return;
+  fprintf(f, "{\n");
+  size_t i = 0;
+  for (auto &kv : m) fprintf(f, "  \"%s\": %d%s\n", kv.first.c_str(), kv.second, ++i < m.size() ? "," : "");
+  fprintf(f, "}\n");
+  fclose(f);
 }
 
 }  // namespace
@@ -610,6 +746,7 @@ ising_status ising_local_search(ising_handle *h, const uint64_t *seeds, int32_t 
   cudaGetDevice(&cur);
   if (cur != h->device) cudaSetDevice(h->device);
   st = ISING_OK;
+  h->launches = 0;
   do {
     if (cudaMemcpyAsync(h->d_seeds, seeds, sizeof(uint64_t) * h->n_inst, cudaMemcpyHostToDevice, stream) !=
             cudaSuccess ||
@@ -657,6 +794,7 @@ ising_status ising_local_search(ising_handle *h, const uint64_t *seeds, int32_t 
       stats->minima = h->h_stats_pinned[2];
       stats->descents = h->h_stats_pinned[3];
       stats->sweeps = h->h_stats_pinned[4];
+      stats->launches = h->launches;
     }
   }
   if (cur != h->device) cudaSetDevice(cur);
@@ -665,11 +803,68 @@ ising_status ising_local_search(ising_handle *h, const uint64_t *seeds, int32_t 
 
 ising_status ising_autotune(ising_handle *h, int32_t replicas, const ising_search_params *p, int32_t *chosen,
                             cudaStream_t stream) {
-  (void)stream;
   if (!h || !p || replicas < 1) return ISING_ERR_INVALID_ARG;
-  int32_t k = resolve_kernel(h, replicas, p);
-  if (k < 0) return (ising_status)(-k);
-  if (chosen) *chosen = k;
+  ising_status st = validate_params(p);
+  if (st != ISING_OK) return st;
+  const std::string key = tune_key(h, replicas, p);
+  // a cached decision for this GPU and instance class?
+  int32_t cached = tune_cache_lookup(key);
+  if (cached > 0) {
+    ising_search_params q = *p;
+    q.kernel = (ising_kernel)cached;
+    if (resolve_kernel(h, replicas, &q) == cached) {
+      h->tuned[replicas] = cached;
+      if (chosen) *chosen = cached;
+      return ISING_OK;
+    }
+  }
+  // time every eligible family on this handle with these parameters
+  const int32_t families[] = {ISING_KERNEL_MSC, ISING_KERNEL_TILE, ISING_KERNEL_SWEEP, ISING_KERNEL_DENSE_TC};
+  int8_t *spins = nullptr;
+  double *E = nullptr;
+  int32_t *mins = nullptr;
+  if (cudaMalloc(&spins, (size_t)replicas * h->total_spins) != cudaSuccess ||
+      cudaMalloc(&E, sizeof(double) * replicas * h->n_inst) != cudaSuccess ||
+      cudaMalloc(&mins, sizeof(int32_t) * replicas * h->n_inst) != cudaSuccess) {
+    cudaFree(spins);
+    cudaFree(E);
+    cudaFree(mins);
+    return ISING_ERR_OOM;
+  }
+  std::vector<uint64_t> seeds(h->n_inst);
+  for (int32_t b = 0; b < h->n_inst; ++b) seeds[b] = 0x9E3779B97F4A7C15ull * (uint64_t)(b + 1);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int32_t best_k = -1;
+  float best_ms = 0.0f;
+  h->tuned.erase(replicas);
+  for (int32_t fam : families) {
+    ising_search_params q = *p;
+    q.kernel = (ising_kernel)fam;
+    if (resolve_kernel(h, replicas, &q) != fam) continue;
+    ising_stats s1;
+    if (ising_local_search(h, seeds.data(), replicas, &q, spins, E, nullptr, mins, &s1, stream) != ISING_OK) continue;
+    cudaEventRecord(e0, stream);
+    ising_status r = ising_local_search(h, seeds.data(), replicas, &q, spins, E, nullptr, mins, nullptr, stream);
+    cudaEventRecord(e1, stream);
+    if (r != ISING_OK || cudaEventSynchronize(e1) != cudaSuccess) continue;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (best_k < 0 || ms < best_ms) {
+      best_k = fam;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(spins);
+  cudaFree(E);
+  cudaFree(mins);
+  if (best_k < 0) return ISING_ERR_UNSUPPORTED;
+  h->tuned[replicas] = best_k;
+  tune_cache_store(key, best_k);
+  if (chosen) *chosen = best_k;
   return ISING_OK;
 }
 

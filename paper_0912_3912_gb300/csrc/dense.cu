@@ -309,6 +309,7 @@ cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t 
       e = dense_tc_run(n, R, Rp128, b, seed, J, D.hi, D.lo, D.S_tc, D.best, spins + (int64_t)R * h->inst[b].spin_off,
                        E + (int64_t)b * R, minima ? minima + (int64_t)b * R : nullptr, h->d_stats, D.err, p, s);
       if (e != cudaSuccess) return e;
+      h->launches += 1;
       if ((e = cudaMemcpyAsync(D.h_err, D.err, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
       if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
       if (*D.h_err != 0) return cudaErrorLaunchTimeout;
@@ -349,6 +350,7 @@ cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t 
       // one descent round: sweep until no replica is active
       for (int sw = 0;; ++sw) {
         if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) break;
+        h->launches += 2 + (n + kDB - 1) / kDB;
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
         if (*D.h_active == 0) break;
       }

@@ -42,7 +42,9 @@ constexpr int kThreads = 128;
 constexpr int kTileBytes = kTM * kKC * 2;                 // 16 KB
 constexpr int kStageBytes = 3 * kTileBytes;               // A, B_hi, B_lo
 constexpr int kPartialBytes = kTB * kTM * 4;              // 64 KB, [spin][replica]
-constexpr int kSmemBytes = kStages * kStageBytes + kPartialBytes + 1024;  // + alignment slack
+constexpr int kMaxN = 4096;                                 // spins whose bits fit in shared memory
+constexpr int kSbitsBytes = 32 * (kMaxN / 32) * 4;          // this CTA's 32 replicas, 1 bit per spin
+constexpr int kSmemBytes = kStages * kStageBytes + kPartialBytes + kSbitsBytes + 1024;  // + alignment slack
 
 struct TcArgs {
   int32_t n, R, Rp, b;             // spins, replicas, padded replicas, instance
@@ -63,11 +65,12 @@ struct RepState {  // per replica, owned by one thread of warp 0
   double best, E;
 };
 
-__device__ __forceinline__ void write_start(const TcArgs &A, int r, int k) {
-  // Philox start R(b, r, k), written as BF16 +/-1 into S[r][:]
+__device__ __forceinline__ void write_start(const TcArgs &A, int r, int k, uint32_t *bits) {
+  // Philox start R(b, r, k), written as BF16 +/-1 into S[r][:] and as bits
   __nv_bfloat16 *row = A.S + (size_t)r * A.n;
   for (int w = 0; w * 128 < A.n; ++w) {
     const uint4 x = start_bits(A.seed, (uint32_t)w, (uint32_t)r, (uint32_t)k, (uint32_t)A.b);
+    for (int q = 0; q < 4; ++q) bits[w * 4 + q] = word_of(x, q);
     for (int t = 0; t < 128 && w * 128 + t < A.n; ++t)
       row[w * 128 + t] = __float2bfloat16_rn(((word_of(x, t / 32) >> (t % 32)) & 1u) ? 1.0f : -1.0f);
   }
@@ -82,11 +85,15 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
   float *P = reinterpret_cast<float *>(smem + kStages * kStageBytes);  // partial fields [spin][replica]
   float *Floc = reinterpret_cast<float *>(smem);                      // reuses stages: [spin][32]
   float *Jblk = reinterpret_cast<float *>(smem + kTB * 32 * 4);       // reuses stages: [128][128]
+  float *fvs = reinterpret_cast<float *>(smem + kTB * 32 * 4 + kTB * kTB * 4);  // reuses stages: [32][128 threads]
+  uint32_t *sbits = reinterpret_cast<uint32_t *>(smem + kStages * kStageBytes + kPartialBytes);  // [32][n/32]
 
   __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], done_bar;
   __shared__ uint32_t tmem_base_s;
   __shared__ int32_t s_flag[2];   // cluster-visible: [0] my replicas still busy, [1] my failure
   __shared__ int32_t s_ctrl[4];   // broadcast inside the CTA
+  __shared__ int32_t s_act[32], s_nfl[32];
+  __shared__ double s_en[32];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t q = tc::cluster_rank();
@@ -124,8 +131,9 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
   st.best = DBL_MAX;
   st.E = 0.0;
   unsigned long long c_evals = 0, c_flips = 0, c_minima = 0, c_desc = 0, c_sweeps = 0;
+  const int nw32 = n / 32;
   if (real) {
-    write_start(A, my_r, 0);
+    write_start(A, my_r, 0, sbits + lane * nw32);
     c_desc = 1;
   }
   tc::fence_proxy_async_global();
@@ -269,52 +277,95 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
       }
       __syncthreads();
       tc::cluster_sync();  // partials consumed: P may be overwritten by the next block
-      // Phase 4: sequential decisions (or energy accumulation), one thread per replica
-      if (!failed && warp == 0 && my_r < A.R) {
-        __nv_bfloat16 *row = A.S + (size_t)my_r * n + b0;
-        uint32_t up[kTB / 32], fl[kTB / 32];
-#pragma unroll
-        for (int w = 0; w < kTB / 32; ++w) {
-          up[w] = 0;
-          fl[w] = 0;
+      // Phase 4: sequential decisions (or energy accumulation).  Four threads per
+      // replica: replica rl = tid / 4, and sub-lane ql = tid % 4 keeps the running
+      // fields of the block's spins i = 4m + ql in registers.  Spins are decided
+      // in order i = 0..127 by their owner; each flip is broadcast to the quad,
+      // which adds 2 J_ij s_j to the fields of the later spins (same FP32 order
+      // as visiting them one by one).
+      if (warp == 0) s_act[lane] = (my_r < A.R && !failed) ? st.active : 0;
+      __syncthreads();
+      {
+        const int rl = tid >> 2, ql = tid & 3;
+        const int rr = rq + rl;
+        const bool valid_r = rr < A.R && !failed;
+        uint32_t *mybits = sbits + rl * nw32 + (b0 >> 5);
+        uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;  // the block's 128 spins of replica rl (1 = +1)
+        if (valid_r) {
+          w0 = mybits[0];
+          w1 = mybits[1];
+          w2 = mybits[2];
+          w3 = mybits[3];
         }
-        for (int i = 0; i < kTB; ++i)
-          if (__bfloat162float(row[i]) > 0.0f) up[i >> 5] |= 1u << (i & 31);
+        auto bit = [&](int i) -> uint32_t {
+          const uint32_t w = i < 64 ? (i < 32 ? w0 : w1) : (i < 96 ? w2 : w3);
+          return (w >> (i & 31)) & 1u;
+        };
+        float *myf = fvs + tid;  // running fields of spins 4m + ql at myf[m * kThreads]
+        for (int m = 0; m < kTB / 4; ++m) myf[m * kThreads] = valid_r ? Floc[(4 * m + ql) * 32 + rl] : 0.0f;
         if (energy_pass) {
           double acc = 0.0;
-          for (int i = 0; i < kTB; ++i)
-            acc += (((up[i >> 5] >> (i & 31)) & 1u) ? 1.0 : -1.0) * (double)Floc[i * 32 + lane];
-          st.E += acc;
-        } else if (st.active) {
+          for (int m = 0; m < kTB / 4; ++m) acc += (bit(4 * m + ql) ? 1.0 : -1.0) * (double)myf[m * kThreads];
+          acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+          acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+          if (ql == 0) s_en[rl] = valid_r ? acc : 0.0;
+        } else {
+          const bool act = valid_r && s_act[rl] != 0;
           int nfl = 0;
-          for (int i = 0; i < kTB; ++i) {
-            float f = Floc[i * 32 + lane];
+          uint32_t f0 = 0, f1 = 0, f2 = 0, f3 = 0;  // flipped in this block
+          const int qbase = lane & ~3;
+          for (int m = 0; m < kTB / 4; ++m) {
 #pragma unroll
-            for (int w = 0; w < kTB / 32; ++w) {
-              uint32_t m = fl[w];
-              if (w * 32 >= i) m = 0;
-              else if (i - w * 32 < 32) m &= (1u << (i - w * 32)) - 1u;
-              while (m) {
-                const int jj = w * 32 + __ffs(m) - 1;
-                m &= m - 1;
-                const float w2 = 2.0f * Jblk[i * kTB + jj];
-                f = __fadd_rn(f, ((up[w] >> (jj - w * 32)) & 1u) ? w2 : -w2);
+            for (int owner = 0; owner < 4; ++owner) {
+              const int i = 4 * m + owner;
+              const uint32_t s_up = bit(i);
+              int dec = 0;
+              if (ql == owner && act) {
+                const float f = myf[m * kThreads];
+                dec = s_up ? (f < 0.0f) : (f > 0.0f);
+              }
+              if (__shfl_sync(0xffffffffu, dec, qbase | owner)) {
+                const uint32_t msk = 1u << (i & 31);
+                if (i < 32) { w0 ^= msk; f0 |= msk; }
+                else if (i < 64) { w1 ^= msk; f1 |= msk; }
+                else if (i < 96) { w2 ^= msk; f2 |= msk; }
+                else { w3 ^= msk; f3 |= msk; }
+                if (ql == owner) ++nfl;
+                const float sgn = s_up ? -2.0f : 2.0f;  // 2 s_i with the new spin
+                const float *Jrow = Jblk + i * kTB;   // J symmetric: row i = column i
+                for (int mm = m; mm < kTB / 4; ++mm) {
+                  const int ip = 4 * mm + ql;
+                  if (ip > i) myf[mm * kThreads] = __fadd_rn(myf[mm * kThreads], sgn * Jrow[ip]);
+                }
               }
             }
-            const bool s_up = (up[i >> 5] >> (i & 31)) & 1u;
-            if (s_up ? (f < 0.0f) : (f > 0.0f)) {
-              up[i >> 5] ^= 1u << (i & 31);
-              fl[i >> 5] |= 1u << (i & 31);
-              ++nfl;
+          }
+          if (f0 | f1 | f2 | f3) {
+            if (ql == 0) {
+              mybits[0] = w0;
+              mybits[1] = w1;
+              mybits[2] = w2;
+              mybits[3] = w3;
+            }
+            __nv_bfloat16 *row = A.S + (size_t)rr * n + b0;
+            for (int m = 0; m < kTB / 4; ++m) {
+              const int i = 4 * m + ql;
+              const uint32_t fw = i < 64 ? (i < 32 ? f0 : f1) : (i < 96 ? f2 : f3);
+              if ((fw >> (i & 31)) & 1u) row[i] = __float2bfloat16_rn(bit(i) ? 1.0f : -1.0f);
             }
           }
-          if (nfl) {
-            for (int i = 0; i < kTB; ++i)
-              if ((fl[i >> 5] >> (i & 31)) & 1u)
-                row[i] = __float2bfloat16_rn(((up[i >> 5] >> (i & 31)) & 1u) ? 1.0f : -1.0f);
-            st.flips += nfl;
-            c_flips += (unsigned long long)nfl;
-          }
+          nfl += __shfl_xor_sync(0xffffffffu, nfl, 1);
+          nfl += __shfl_xor_sync(0xffffffffu, nfl, 2);
+          if (ql == 0) s_nfl[rl] = act ? nfl : 0;
+        }
+      }
+      __syncthreads();
+      if (warp == 0 && my_r < A.R && !failed) {
+        if (energy_pass) {
+          st.E += s_en[lane];
+        } else {
+          st.flips += s_nfl[lane];
+          c_flips += (unsigned long long)s_nfl[lane];
         }
       }
       // generic-proxy writes (new spins in global memory, the staged fields and
@@ -344,7 +395,7 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
           if (st.k < A.restarts && (A.budget <= 0 || st.total < A.budget)) {
             st.active = 1;
             st.d = 0;
-            write_start(A, my_r, st.k);
+            write_start(A, my_r, st.k, sbits + lane * nw32);
             ++c_desc;
           } else {
             st.done = 1;
@@ -415,7 +466,7 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
 }  // namespace
 
 // ---------------------------------------------------------------- host side
-bool dense_tc_eligible(int n) { return n >= 256 && n % 256 == 0; }
+bool dense_tc_eligible(int n) { return n >= 256 && n % 256 == 0 && n <= kMaxN; }
 
 static cudaError_t encode_2d(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer,
                              uint32_t box_inner, uint32_t box_outer) {

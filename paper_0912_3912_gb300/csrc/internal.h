@@ -141,7 +141,12 @@ struct ising_handle {
 
   // tuned kernel family per replica count (autotuner cache)
   std::map<int32_t, int32_t> tuned;
+  // the tile path's launch sequence (queue reset + persistent kernel) captured
+  // once per (mode, grid, shared memory) and replayed
+  cudaGraphExec_t tile_exec = nullptr;
+  int32_t tile_exec_key[3] = {-1, -1, -1};
   ising_status latched = ISING_OK;
+  uint64_t launches = 0;  // kernel launches enqueued by the current call
   isg::DevGraph graph() const;
 };
 
@@ -153,4 +158,6 @@ int tile_max_ctas_per_sm(int mode, size_t smem);
 cudaError_t launch_energy(ising_handle *h, const int8_t *spins, int32_t R, double *E,
                           int32_t *E32, cudaStream_t s);
 void energy_plan_free(ising_handle *h);
+size_t msc_cluster_smem(int csz);
+cudaError_t launch_msc_cluster(ising_handle *h, int n_tiles, int P, int csz_max, int D, cudaStream_t s);
 }  // namespace isg

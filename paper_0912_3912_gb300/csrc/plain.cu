@@ -307,6 +307,7 @@ cudaError_t launch_plain(ising_handle *h, const ising_search_params *p, int32_t 
     const int ncls = seq ? I.n : I.ncls;
     plain_reset<<<rb, kPT, 0, s>>>(P.rep, R);
     for (int sweep = 0;; ++sweep) {
+      h->launches += 5 + ncls;
       plain_start<<<nb, kPT, 0, s>>>(G, I, R, b, seeds_host[b], P.s, P.fm, P.rep);
       plain_start_done<<<rb, kPT, 0, s>>>(P.rep, R, h->d_stats);
       for (int c = 0; c < ncls; ++c) {

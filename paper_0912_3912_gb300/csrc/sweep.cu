@@ -41,6 +41,7 @@ struct SweepArgs {
   int32_t max_sweeps, restarts, budget, refresh, sequential, lattice;
   uint64_t seed;
   uint32_t *sw, *fm, *bw;
+  uint32_t *pend;  // [g][n]: lanes in which some neighbour flipped since the spin's last visit
   float *F;
   GroupState *gs;
   double *partial;  // [grid_e][G][32]
@@ -148,11 +149,16 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
     for (int g = 0; g < A.G; ++g) {
       const uint32_t active = A.gs[g].active & lmask;
       if (!active) continue;
+      const bool fresh = A.gs[g].d == 0;
       uint32_t *swg = A.sw + (size_t)g * n;
+      uint32_t *pendg = A.pend + (size_t)g * n;
       uint32_t anyg = 0;
       for (int t = blockIdx.x * blockDim.x + tid; t < cs; t += gridDim.x * blockDim.x) {
         const int v = c0 + t;
         const int j = A.sequential ? v : __ldg(G.order + so + v);
+        const uint32_t pj = pendg[j];
+        if (!fresh && !(pj & active)) continue;  // no neighbour flipped: still stable
+        if (pj) pendg[j] = 0u;
         const uint32_t wj = swg[j];
         const int hv = __ldg(hi + so + j);
         uint32_t flip;
@@ -207,6 +213,14 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
           swg[j] = wj ^ flip;
           anyg |= flip;
           my_flips += __popc(flip);
+          if (LAT) {
+            const uint32_t info = __ldg(G.latinfo + so + v);
+            for (int d = 0; d < 2 * D; ++d)
+              atomicOr(&pendg[j + s_off[d] + (((info >> d) & 1u) ? s_wrap[d] : 0)], flip);
+          } else {
+            for (uint32_t kk = __ldg(G.row + so + j), k1 = __ldg(G.row + so + j + 1); kk < k1; ++kk)
+              atomicOr(&pendg[__ldg(G.col + kk)], flip);
+          }
         }
       }
       anyg = __reduce_or_sync(0xffffffffu, anyg);
@@ -226,16 +240,23 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
       const bool refresh = (dd == 0) || (A.refresh > 0 && dd % A.refresh == 0);
       uint32_t *swg = A.sw + (size_t)g * n;
       uint32_t *fmg = A.fm + (size_t)g * n;
+      uint32_t *pendg = A.pend + (size_t)g * n;
       float *Fg = (MODE == 1) ? A.F + (size_t)g * n * LPS : nullptr;
+      const bool fresh = MODE == 1 ? refresh : dd == 0;  // every spin is evaluated
       uint32_t anyg = 0;
       for (int wi = wid; wi < witems; wi += wstride) {
         const int v = c0 + wi * SPW + sub;
         const bool valid = v < c1;
         const int j = valid ? (A.sequential ? v : __ldg(G.order + so + v)) : 0;
+        // Only a spin with a neighbour that flipped since its last visit can
+        // change its decision (its field is otherwise unchanged and it was left
+        // stable); the pending mask, pushed by flipping neighbours, says which lanes.
+        const uint32_t pj = valid ? pendg[j] : 0u;
+        const bool need = valid && (fresh || ((pj >> ln) & 1u));
         const uint32_t wj = valid ? swg[j] : 0u;
         const bool up = (wj >> ln) & 1u;
         bool flip = false;
-        if (valid) {
+        if (need) {
           const uint32_t meta = LAT ? __ldg(G.meta + so + v) : 0u;
           const uint32_t k0 = LAT ? 0u : __ldg(G.row + so + j);
           const uint32_t k1 = LAT ? (uint32_t)(2 * I.lat_d) : __ldg(G.row + so + j + 1);
@@ -340,7 +361,28 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
         const uint32_t m = __ballot_sync(0xffffffffu, flip);
         const uint32_t seg = (m >> (sub * LPS)) & lmask;
         if (valid && ln == 0) {
-          if (seg) swg[j] = wj ^ seg;
+          if (pj) pendg[j] = 0u;
+          if (seg) {
+            swg[j] = wj ^ seg;
+            // tell the neighbours (and hyper-edge co-members) which lanes flipped
+            if (LAT) {
+              const uint32_t meta = __ldg(G.meta + so + v);
+              for (int kk = 0; kk < 2 * I.lat_d; ++kk) {
+                const int dir = (meta >> (8 + 3 * kk)) & 7;
+                atomicOr(&pendg[j + s_off[dir] + (((meta >> kk) & 1u) ? s_wrap[dir] : 0)], seg);
+              }
+            } else {
+              for (uint32_t kk = __ldg(G.row + so + j), k1 = __ldg(G.row + so + j + 1); kk < k1; ++kk)
+                atomicOr(&pendg[__ldg(G.col + kk)], seg);
+              for (uint32_t q = __ldg(G.inc_ptr + so + j), q1 = __ldg(G.inc_ptr + so + j + 1); q < q1; ++q) {
+                const int e = __ldg(G.inc_edge + q);
+                for (uint32_t mm = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); mm < me; ++mm) {
+                  const int o = __ldg(G.hmem + mm);
+                  if (o != j) atomicOr(&pendg[o], seg);
+                }
+              }
+            }
+          }
           if (MODE == 1 && (seg || fmg[j])) fmg[j] = seg;
         }
         anyg |= seg;
@@ -702,6 +744,7 @@ cudaError_t run_instance(ising_handle *h, SweepArgs A, int mode, cudaStream_t s)
   sweep_init<<<1, 32, 0, s>>>(A);
   debug_step("init", 0, s);
   sweep_restart<LPS><<<A.grid_e, kST, 0, s>>>(A);
+  h->launches += 2;
   debug_step("restart0", 0, s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -718,6 +761,7 @@ cudaError_t run_instance(ising_handle *h, SweepArgs A, int mode, cudaStream_t s)
   cudaStream_t cs = nullptr;
   // the first sweep runs with direct launches, the rest from the graph
   enqueue_sweep<LPS, LAT>(A, mode, ncls, grid_v, s);
+  h->launches += per_sweep;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (use_graph) {
     if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return e;
@@ -739,6 +783,7 @@ cudaError_t run_instance(ising_handle *h, SweepArgs A, int mode, cudaStream_t s)
   const int64_t max_chunks = max_sweeps_total / chunk + 2;
   int64_t launched = 0;
   for (;;) {
+    h->launches += (uint64_t)chunk * per_sweep;
     if (use_graph) {
       if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) break;
     } else {
@@ -764,6 +809,7 @@ cudaError_t run_instance(ising_handle *h, SweepArgs A, int mode, cudaStream_t s)
   if (e != cudaSuccess) return e;
   // energies of the final states of replicas that never converged
   sweep_mark_final<<<1, 32, 0, s>>>(A);
+  h->launches += 3;
   if (mode == 1) sweep_energy<true, LPS, LAT><<<A.grid_e, kST, 0, s>>>(A);
   else sweep_energy<false, LPS, LAT><<<A.grid_e, kST, 0, s>>>(A);
   const int64_t tot = (int64_t)A.R * I.n;
@@ -796,7 +842,7 @@ cudaError_t launch_sweep(ising_handle *h, const ising_search_params *p, int32_t 
   // scratch: sw, fm, bw [G][nmax]; F [G][nmax][LPS]; gs [G]; partial [grid_e][G][32]; counter; done
   const size_t words = (size_t)G * h->nmax;
   auto up256 = [](size_t b) { return (b + 255) / 256 * 256; };
-  const size_t need = 3 * up256(words * 4) + (fl ? up256(words * LPS * 4) : 0) + up256(G * sizeof(GroupState)) +
+  const size_t need = 4 * up256(words * 4) + (fl ? up256(words * LPS * 4) : 0) + up256(G * sizeof(GroupState)) +
                       up256((size_t)grid_e * G * 32 * 8) + 2 * 256;
   cudaError_t e;
   if (need > S.bytes) {
@@ -828,6 +874,7 @@ cudaError_t launch_sweep(ising_handle *h, const ising_search_params *p, int32_t 
   A.sw = (uint32_t *)take(words * 4);
   A.fm = (uint32_t *)take(words * 4);
   A.bw = (uint32_t *)take(words * 4);
+  A.pend = (uint32_t *)take(words * 4);
   A.F = fl ? (float *)take(words * LPS * 4) : nullptr;
   A.gs = (GroupState *)take(G * sizeof(GroupState));
   A.grid_e = grid_e;
@@ -845,6 +892,7 @@ cudaError_t launch_sweep(ising_handle *h, const ising_search_params *p, int32_t 
     A.seed = seeds_host[b];
     A.lattice = (A.I.lat_d > 0 && !A.sequential) ? 1 : 0;
     if ((e = cudaMemsetAsync(A.fm, 0, words * 4, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(A.pend, 0, words * 4, s)) != cudaSuccess) return e;
     if (A.lattice) {
       if (LPS == 32) e = run_instance<32, true>(h, A, mode, s);
       else if (LPS == 16) e = run_instance<16, true>(h, A, mode, s);

@@ -210,6 +210,9 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *_
   const int nmax = A.nmax;
   uint32_t *sw = smem;
   uint32_t *fm = smem + nmax;
+  // pending bits: spin i's bit is set when a neighbour flipped (in any lane)
+  // since i's last visit; a spin without it keeps its field and stays stable
+  uint32_t *pb = smem + (MODE >= 2 ? 1 : 2) * nmax;
   uint32_t *bw = A.bw + (size_t)blockIdx.x * nmax;
   float *F = A.F ? A.F + (size_t)blockIdx.x * nmax * 32 : nullptr;
   unsigned long long my_flips = 0, my_evals = 0, my_sweeps = 0, my_minima = 0, my_desc = 0;
@@ -269,6 +272,12 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *_
 
       for (int d = 0; active; ++d) {
         const bool refresh = (d == 0) || (A.refresh > 0 && d % A.refresh == 0);
+        const bool fresh = MODE == 1 ? refresh : d == 0;  // every spin is evaluated
+        auto pending = [&](int j) -> bool { return fresh || ((pb[j >> 5] >> (j & 31)) & 1u); };
+        auto clear_pending = [&](int j) {
+          if ((pb[j >> 5] >> (j & 31)) & 1u) atomicAnd(&pb[j >> 5], ~(1u << (j & 31)));
+        };
+        auto mark = [&](int i) { atomicOr(&pb[i >> 5], 1u << (i & 31)); };
         if (tid == 0) s_any = 0;
         uint32_t anyf = 0;
         for (int c = 0; c < ncls; ++c) {
@@ -288,6 +297,8 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *_
             const int stride[3] = {1, L, L * L};
             for (int v = c0 + tid; v < c1; v += blockDim.x) {
               const int j = __ldg(G.order + I.spin_off + v);
+              if (!pending(j)) continue;
+              clear_pending(j);
               const uint32_t info = __ldg(G.latinfo + I.spin_off + v);
               const int hv = __ldg(reinterpret_cast<const int8_t *>(G.h) + I.spin_off + j);
               const uint32_t wj = sw[j];
@@ -314,6 +325,13 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *_
                 flip = (c1 & c2) | ((c1 | c2) & s2);  // count >= 3
               }
               flip &= active;
+              if (flip)
+                for (int d = 0; d < 2 * D; ++d) {
+                  const int a = d >> 1, st = stride[a];
+                  int nb = (d & 1) ? j - st : j + st;
+                  if ((info >> d) & 1u) nb += (d & 1) ? L * st : -L * st;
+                  mark(nb);
+                }
               sw[j] = wj ^ flip;
               anyf |= flip;
               my_flips += __popc(flip);
@@ -323,6 +341,8 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *_
             const int8_t *hi = reinterpret_cast<const int8_t *>(G.h);
             for (int v = c0 + tid; v < c1; v += blockDim.x) {
               const int j = A.sequential ? v : __ldg(G.order + I.spin_off + v);
+              if (!pending(j)) continue;
+              clear_pending(j);
               const int64_t gj = I.spin_off + j;
               const uint32_t wj = sw[j];
               uint32_t c0b = 0, c1b = 0, c2b = 0, c3b = 0;
@@ -355,6 +375,8 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *_
                        (sliced_ge(c0b, c1b, c2b, c3b, tm) & ~plus);
               }
               flip &= active;
+              if (flip)
+                for (uint32_t kk = k0; kk < k1; ++kk) mark(__ldg(G.col + kk));
               sw[j] = wj ^ flip;
               anyf |= flip;
               my_flips += __popc(flip);
@@ -362,6 +384,10 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *_
           } else {
             for (int v = c0 + warp; v < c1; v += nwarps) {
               const int j = A.sequential ? v : __ldg(G.order + I.spin_off + v);
+              if (!pending(j)) {  // warp-uniform; the visit flips nothing
+                if (MODE == 1 && lane == 0 && fm[j]) fm[j] = 0u;
+                continue;
+              }
               const int64_t gj = I.spin_off + j;
               const uint32_t wj = sw[j];
               const bool up = (wj >> lane) & 1u;
@@ -461,8 +487,19 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *_
               flip = flip && ((active >> lane) & 1u);
               const uint32_t m = __ballot_sync(0xffffffffu, flip);
               if (lane == 0) {
+                clear_pending(j);
                 sw[j] = wj ^ m;
                 if (MODE == 1) fm[j] = m;
+                if (m) {
+                  for (uint32_t kk = k0; kk < k1; ++kk) mark(__ldg(G.col + kk));
+                  for (uint32_t q = e0; q < e1; ++q) {
+                    const int e = __ldg(G.inc_edge + q);
+                    for (uint32_t mm = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); mm < me; ++mm) {
+                      const int o = __ldg(G.hmem + mm);
+                      if (o != j) mark(o);
+                    }
+                  }
+                }
               }
               anyf |= m;
               my_flips += flip ? 1 : 0;
@@ -559,7 +596,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *_
 }
 
 size_t tile_smem_bytes(int mode, int nmax) {
-  return (size_t)(mode >= 2 ? 1 : 2) * (size_t)nmax * sizeof(uint32_t);
+  return (size_t)(mode >= 2 ? 1 : 2) * (size_t)nmax * sizeof(uint32_t) + (size_t)((nmax + 31) / 32) * sizeof(uint32_t);
 }
 
 int tile_max_ctas_per_sm(int mode, size_t smem) {
@@ -581,22 +618,13 @@ int tile_max_ctas_per_sm(int mode, size_t smem) {
   return e == cudaSuccess ? blocks : 0;
 }
 
+// Launch only: the shared-memory attribute was set by tile_max_ctas_per_sm, so
+// this is a plain stream operation and can be captured into a graph.
 cudaError_t launch_tile(ising_handle *h, int mode, int grid, size_t smem, cudaStream_t s) {
-  cudaError_t e = cudaSuccess;
-  if (mode == 0) {
-    e = cudaFuncSetAttribute(tile_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) tile_kernel<0><<<grid, kTileThreads, smem, s>>>(h->d_tile_args);
-  } else if (mode == 1) {
-    e = cudaFuncSetAttribute(tile_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) tile_kernel<1><<<grid, kTileThreads, smem, s>>>(h->d_tile_args);
-  } else if (mode == 2) {
-    e = cudaFuncSetAttribute(tile_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) tile_kernel<2><<<grid, kTileThreads, smem, s>>>(h->d_tile_args);
-  } else {
-    e = cudaFuncSetAttribute(tile_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) tile_kernel<3><<<grid, kTileThreads, smem, s>>>(h->d_tile_args);
-  }
-  if (e != cudaSuccess) return e;
+  if (mode == 0) tile_kernel<0><<<grid, kTileThreads, smem, s>>>(h->d_tile_args);
+  else if (mode == 1) tile_kernel<1><<<grid, kTileThreads, smem, s>>>(h->d_tile_args);
+  else if (mode == 2) tile_kernel<2><<<grid, kTileThreads, smem, s>>>(h->d_tile_args);
+  else tile_kernel<3><<<grid, kTileThreads, smem, s>>>(h->d_tile_args);
   return cudaGetLastError();
 }
 

@@ -63,7 +63,8 @@ def _compare(insts, seeds, R, exact_energy, **kw):
             assert np.array_equal(g[b][1], o[b][1])
         else:
             np.testing.assert_allclose(g[b][1], o[b][1], rtol=1e-9, atol=1e-9)
-    assert gst == ost
+    assert {k: gst[k] for k in ost} == ost
+    assert gst["launches"] >= 1
     if e32 is not None:
         assert np.array_equal(e32.ravel(), np.concatenate([x[1] for x in o]).astype(np.int32))
     return g, o
@@ -277,3 +278,39 @@ def test_dense_sk_tcgen05_kernel(n, R, monkeypatch):
     assert same >= 0.8, same
     assert abs(np.mean(E) - ref.energy.cpu().numpy().mean()) <= 1e-3 * abs(np.mean(E))
     h.close()
+
+
+def test_autotuner_picks_an_eligible_family_and_results_do_not_depend_on_it(tmp_path, monkeypatch):
+    monkeypatch.setenv("ISING_TUNE_CACHE", str(tmp_path / "tune.json"))
+    inst = W.lattice((12, 12, 12), periodic=True, couplings="pm1", fields="pm1_0", seed=31)
+    R = 64
+    h = isg.Handle([inst])
+    kw = dict(max_sweeps=100, restarts=3)
+    fam = h.autotune(R, **kw)
+    assert fam in (isg.KERNEL_MSC, isg.KERNEL_TILE, isg.KERNEL_SWEEP)
+    assert h.plan_kernel(R, **kw) == fam
+    assert (tmp_path / "tune.json").exists()
+    outs = []
+    for k in (isg.KERNEL_AUTO, isg.KERNEL_MSC, isg.KERNEL_TILE, isg.KERNEL_SWEEP):
+        r = h.local_search([8], R, kernel=k, **kw)
+        torch.cuda.synchronize()
+        outs.append((r.spins.cpu().numpy().copy(), r.energy.cpu().numpy().copy(), r.stats))
+    for o in outs[1:]:
+        assert np.array_equal(o[0], outs[0][0]) and np.array_equal(o[1], outs[0][1])
+        assert {k: v for k, v in o[2].items() if k != "launches"} == {
+            k: v for k, v in outs[0][2].items() if k != "launches"}
+    h.close()
+    # a fresh handle of the same class reads the decision from the cache file
+    h2 = isg.Handle([inst])
+    assert h2.autotune(R, **kw) == fam
+    h2.close()
+
+
+@pytest.mark.parametrize("dims,R", [((16, 16, 16), 70), ((64, 64), 40)])
+def test_msc_lattice_cluster_split(dims, R):
+    """Lattices whose replica groups are few are split over a 4-CTA cluster
+    (distributed shared memory for the slab-boundary neighbours)."""
+    inst = W.lattice(dims, periodic=True, couplings="pm1", fields="pm1_0", seed=sum(dims))
+    _compare([inst], [sum(dims)], R, True, max_sweeps=200, restarts=4, kernel=isg.KERNEL_MSC)
+    _compare([inst], [sum(dims) + 1], R, True, max_sweeps=3, restarts=1000, sweep_budget=17,
+             kernel=isg.KERNEL_MSC)
