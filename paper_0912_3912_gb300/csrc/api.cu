@@ -73,6 +73,35 @@ struct HostInst {
   int32_t lat_L = 0, lat_d = 0;
 };
 
+// Unit (biased exponent) for exact fixed-point energies of an FP32 instance.
+// Every nonzero coupling and field is then an integer multiple M << (e - ebase)
+// of 2^(ebase - 150) with a 24-bit M; with a spread of at most 38 every term
+// fits below 2^62, and the high halves of up to 2^22 terms stay below 2^53 so
+// the final conversion to FP64 rounds once.  Returns -1 when that does not hold
+// (subnormal values, a wider spread or more terms).
+int32_t energy_base_exponent(const HostInst &I) {
+  int emin = 256, emax = -1;
+  bool sub = false;
+  auto see = [&](float v) {
+    uint32_t b;
+    std::memcpy(&b, &v, 4);
+    b &= 0x7fffffffu;
+    if (!b) return;
+    const int e = (int)(b >> 23);
+    if (e == 0 || e == 255) sub = true;
+    emin = std::min(emin, e);
+    emax = std::max(emax, e);
+  };
+  for (float v : I.Jf) see(v);
+  for (float v : I.hf) see(v);
+  for (float v : I.hJf) see(v);
+  if (sub) return -1;
+  if (emax < 0) return 1;  // all zero
+  const int64_t terms = (int64_t)I.col.size() / 2 + I.n + (int64_t)I.hJf.size();
+  if (emax - emin > 38 || terms >= (int64_t)1 << 22) return -1;
+  return emin;
+}
+
 // Recognise a periodic hypercubic lattice (side L >= 3, d = 2 or 3, spin index
 // x0 + L*x1 + L^2*x2) from the CSR structure alone.
 void detect_lattice(HostInst &I) {
@@ -327,7 +356,7 @@ int32_t resolve_kernel(ising_handle *h, int32_t R, const ising_search_params *p)
 // alone would leave most SMs idle.  Every instance must split into P
 // power-of-two chunks of at least 1024 sites (whole Philox blocks).
 int msc_cluster_size(const ising_handle *h, int32_t R, const ising_search_params *p) {
-  if (!h->msc_ok || !h->all_lattice || p->schedule != ISING_SCHED_COLOUR) return 0;
+  if (!h->msc_ok || !h->all_lattice || !h->lat_parity || p->schedule != ISING_SCHED_COLOUR) return 0;
   if (getenv("ISING_NO_CLUSTER")) return 0;
   const int64_t tiles = (int64_t)h->n_inst * ((R + 31) / 32);
   for (int P : {4, 2}) {
@@ -574,6 +603,8 @@ ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
     D.max_deg = I.max_deg;
     D.lat_L = I.lat_L;
     D.lat_d = I.lat_d;
+    D.ebase = fl ? energy_base_exponent(I) : -1;
+    D.pad_ = 0;
     h->any_lattice = h->any_lattice || I.lat_d > 0;
     h->all_lattice = (b == 0 ? true : h->all_lattice) && I.lat_d > 0;
     h->nmax = std::max(h->nmax, I.n);
@@ -648,13 +679,21 @@ ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
     std::vector<uint16_t> latinfo(nsp, 0);
     std::vector<float> Jpf(fl ? 6 * nsp : 0, 0.0f);
     std::vector<int8_t> Jpi(fl ? 0 : 6 * nsp, 0);
+    h->lat_parity = h->all_lattice;
     for (auto &ls : lat_sites) {
       const HostInst &I = hin[ls.first];
       const InstDesc &D = inst[ls.first];
       if (I.lat_d == 0) continue;
       const int32_t L = I.lat_L;
+      if (D.ncls != 2) h->lat_parity = false;
       for (int32_t v = 0; v < I.n; ++v) {
         const int32_t j = ls.second[v];
+        if (h->lat_parity) {
+          int par = 0;
+          for (int32_t a = 0, r = j; a < I.lat_d; ++a, r /= L) par += r % L;
+          const int c = v < h->h_cls[D.cls_off + 1] - h->h_cls[D.cls_off] ? 0 : 1;
+          if ((par & 1) != c) h->lat_parity = false;
+        }
         uint32_t m = 0;
         int kk = 0;
         for (int64_t k = I.row[j]; k < I.row[j + 1]; ++k, ++kk) {

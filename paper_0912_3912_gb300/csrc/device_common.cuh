@@ -36,6 +36,65 @@ __device__ __forceinline__ uint32_t word_of(const uint4 &x, int t) {
   return t == 0 ? x.x : (t == 1 ? x.y : (t == 2 ? x.z : x.w));
 }
 
+// ---- exact field refresh without FP64 arithmetic ------------------------
+// A refresh is defined as a sequential FP64 sum of FP32 terms (field, then the
+// couplings) rounded once to FP32.  When every partial sum of that sequence is
+// exactly representable in FP64 the sequence never rounds, and the result is
+// the round-to-nearest FP32 value of the exact sum.  With e the biased
+// exponents of the nonzero terms this holds when min e >= 24 (no subnormals),
+// max e <= 200 and k terms of at most 24 + (max e - min e) bits sum below 2^53.
+// The exact sum is then formed in 64-bit fixed point with unit 2^(emin - 150).
+struct XRange {
+  int emin = 256, emax = -1, k = 0;
+};
+
+__device__ __forceinline__ void xr_see(XRange &r, float w) {
+  const uint32_t a = __float_as_uint(w) & 0x7fffffffu;
+  r.k += 1;
+  if (a) {
+    const int e = (int)(a >> 23);
+    r.emin = min(r.emin, e);
+    r.emax = max(r.emax, e);
+  }
+}
+
+__device__ __forceinline__ bool xr_exact(const XRange &r) {
+  if (r.emax < 0) return true;  // every term is zero
+  const int lg = 32 - __clz(r.k);  // 2^lg > k
+  return r.emin >= 24 && r.emax <= 200 && (r.emax - r.emin) + 24 + lg <= 53;
+}
+
+// w as a signed integer multiple of 2^(unit - 150); needs unit <= e(w) <= unit + 38.
+__device__ __forceinline__ int64_t xr_term(float w, int unit) {
+  const uint32_t b = __float_as_uint(w), a = b & 0x7fffffffu;
+  if (!a) return 0;
+  const int64_t t = (int64_t)((a & 0x7fffffu) | 0x800000u) << ((int)(a >> 23) - unit);
+  return (b >> 31) ? -t : t;
+}
+
+// RN32(s * 2^(unit - 150)) for |s| <= 2^53, unit >= 24: the integer is
+// rounded once to FP32 and scaled by an exact power of two.
+__device__ __forceinline__ float xr_round(int64_t s, int unit) {
+  return __ll2float_rn(s) * __int_as_float((unit - 23) << 23);
+}
+
+// ---- exact energies ------------------------------------------------------
+// Energy terms as integers t (unit 2^(ebase - 150), |t| < 2^62) accumulated as
+// a signed high part (t >> 32) and an unsigned low part (t & 0xffffffff):
+// integer sums, so the total does not depend on the order of the additions.
+__device__ __forceinline__ void xe_add(long long &hi, unsigned long long &lo, int64_t t) {
+  hi += (long long)(t >> 32);
+  lo += (unsigned long long)(uint32_t)t;
+}
+
+// Round the exact total hi * 2^32 + lo (times the unit) once to FP64.
+__device__ __forceinline__ double xe_value(long long hi, unsigned long long lo, int ebase) {
+  hi += (long long)(lo >> 32);
+  lo &= 0xffffffffull;
+  const double v = __fma_rn((double)hi, 4294967296.0, (double)lo);
+  return v * __longlong_as_double((long long)(ebase - 150 + 1023) << 52);
+}
+
 template <class T>
 __device__ __forceinline__ T ldg_val(const void *p, int64_t i) {
   return __ldg(reinterpret_cast<const T *>(p) + i);

@@ -29,6 +29,11 @@ struct InstDesc {
   int32_t max_deg;    // largest CSR row length
   int32_t lat_L;      // side of a recognised periodic hypercubic lattice, else 0
   int32_t lat_d;      // its dimension (2 or 3), else 0
+  // FP32 couplings: biased exponent of the smallest nonzero |J|, |h|, |J_e|
+  // when the energy can be summed exactly in 64-bit fixed point with that
+  // unit (see xe_term), else -1 (FP64 sums instead)
+  int32_t ebase;
+  int32_t pad_;
 };
 
 // Everything a kernel needs to read an instance set.
@@ -118,6 +123,7 @@ struct ising_handle {
   uint32_t *d_meta = nullptr;
   uint16_t *d_latinfo = nullptr;
   bool all_lattice = false;  // every instance is a recognised periodic lattice
+  bool lat_parity = false;   // ... coloured by site parity: class c = {x + y + z = c mod 2}
   void *d_Jpos = nullptr;
   bool any_lattice = false;
 

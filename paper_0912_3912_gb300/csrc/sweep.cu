@@ -44,7 +44,7 @@ struct SweepArgs {
   uint32_t *pend;  // [g][n]: lanes in which some neighbour flipped since the spin's last visit
   float *F;
   GroupState *gs;
-  double *partial;  // [grid_e][G][32]
+  double *partial;  // [2][grid_e][G][32]: FP64 sums, or fixed-point high and low halves
   int32_t grid_e;
   unsigned int *counter;
   int32_t *all_done;
@@ -63,6 +63,13 @@ __device__ __forceinline__ int lat_nbr(int j, uint32_t meta, int k, int L) {
   if ((meta >> k) & 1u) off += (dir & 1) ? L * stride : -L * stride;
   return j + off;
 }
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __global__ void sweep_init(SweepArgs A) {
   const int g = threadIdx.x;
@@ -113,6 +120,8 @@ __device__ __forceinline__ uint32_t sliced_ge4(uint32_t q0, uint32_t q1, uint32_
 // per warp and no index needs a division.
 template <int MODE, int LPS, bool LAT>
 __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
+  // FP32 lattice path: the stored fields of the 32 positions of a warp step
+  __shared__ __align__(16) float s_F[(MODE == 1 && LAT) ? (kST / 32) * 32 * LPS : 1];
   __shared__ uint32_t s_any[32];
   __shared__ unsigned long long s_red[kST / 32];
   __shared__ int s_off[6], s_wrap[6];
@@ -156,15 +165,16 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
       for (int t = blockIdx.x * blockDim.x + tid; t < cs; t += gridDim.x * blockDim.x) {
         const int v = c0 + t;
         const int j = A.sequential ? v : __ldg(G.order + so + v);
+        // everything indexed by the site itself is read in one round trip
         const uint32_t pj = pendg[j];
-        if (!fresh && !(pj & active)) continue;  // no neighbour flipped: still stable
-        if (pj) pendg[j] = 0u;
         const uint32_t wj = swg[j];
         const int hv = __ldg(hi + so + j);
+        const uint32_t info = LAT ? __ldg(G.latinfo + so + v) : 0u;
+        if (!fresh && !(pj & active)) continue;  // no neighbour flipped: still stable
+        if (pj) pendg[j] = 0u;
         uint32_t flip;
         if (LAT) {
           // field folded into the count: flip iff >= deg/2 + 1 of bonds+field unsatisfied
-          const uint32_t info = __ldg(G.latinfo + so + v);
           uint32_t x[6];
 #pragma unroll
           for (int d = 0; d < 6; ++d) {
@@ -214,7 +224,6 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
           anyg |= flip;
           my_flips += __popc(flip);
           if (LAT) {
-            const uint32_t info = __ldg(G.latinfo + so + v);
             for (int d = 0; d < 2 * D; ++d)
               atomicOr(&pendg[j + s_off[d] + (((info >> d) & 1u) ? s_wrap[d] : 0)], flip);
           } else {
@@ -227,11 +236,16 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
       if (lane == 0 && anyg) atomicOr(&s_any[g], anyg);
     }
   } else {
+    // Lane paths.  A warp takes 32 consecutive class positions at a time: one
+    // coalesced pass reads their pending masks and ballots the positions that
+    // must be evaluated; those are then visited SPW at a time (LPS lanes =
+    // replicas each), with all loads of one visit independent of each other.
     constexpr int SPW = 32 / LPS;
     const int sub = lane / LPS, ln = lane % LPS;
-    const int witems = (cs + SPW - 1) / SPW;
-    const int wstride = gridDim.x * (blockDim.x >> 5);
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
     const int wid = blockIdx.x * (blockDim.x >> 5) + (tid >> 5);
+    const float *Jf = reinterpret_cast<const float *>(G.J);
+    const float *hJf = reinterpret_cast<const float *>(G.hJ);
     for (int g = 0; g < A.G; ++g) {
       const GroupState &S = A.gs[g];
       const uint32_t active = S.active;
@@ -244,62 +258,210 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
       float *Fg = (MODE == 1) ? A.F + (size_t)g * n * LPS : nullptr;
       const bool fresh = MODE == 1 ? refresh : dd == 0;  // every spin is evaluated
       uint32_t anyg = 0;
-      for (int wi = wid; wi < witems; wi += wstride) {
-        const int v = c0 + wi * SPW + sub;
-        const bool valid = v < c1;
-        const int j = valid ? (A.sequential ? v : __ldg(G.order + so + v)) : 0;
+      if constexpr (MODE == 1 && LAT) {
+        // Periodic lattice, FP32 fields.  Lane = position for every read a
+        // visit needs (its word, the neighbour words, their flip masks, the
+        // couplings, the field, and - staged into shared memory - the stored
+        // fields of all LPS lanes), so a warp step costs one round trip to
+        // memory; the per-replica visits then take the values by shuffle.
+        const int D2 = 2 * I.lat_d;
+        const float *Jp0 = reinterpret_cast<const float *>(G.Jpos) + so;
+        const float *hf = reinterpret_cast<const float *>(G.h) + so;
+        float *sF = s_F + (tid >> 5) * 32 * LPS;
+        auto nb_of = [&](int jj, uint32_t mm, int kk) -> int {
+          const int dir = (mm >> (8 + 3 * kk)) & 7;
+          return jj + s_off[dir] + (((mm >> kk) & 1u) ? s_wrap[dir] : 0);
+        };
+        for (int base = wid * 32; base < cs; base += nwarps * 32) {
+          const int v1 = c0 + base + lane;
+          const bool valid1 = v1 < c1;
+          const int j1 = valid1 ? __ldg(G.order + so + v1) : 0;
+          const uint32_t p1 = valid1 ? pendg[j1] : 0u;
+          const uint32_t meta1 = valid1 ? __ldg(G.meta + so + v1) : 0u;
+          const bool need1 = valid1 && (refresh || (p1 & active) != 0u);
+          if (valid1 && p1) pendg[j1] = 0u;
+          if (valid1 && !need1 && fmg[j1]) fmg[j1] = 0u;  // no flips at this visit
+          uint32_t todo = __ballot_sync(0xffffffffu, need1);
+          if (!todo) continue;
+          uint32_t wj1 = 0u, sn1[6], fn1[6];
+          float jw1[6], hj1 = 0.0f;
+#pragma unroll
+          for (int kk = 0; kk < 6; ++kk) {
+            sn1[kk] = 0u;
+            fn1[kk] = 0u;
+            jw1[kk] = 0.0f;
+          }
+          if (need1) {
+            wj1 = swg[j1];
+#pragma unroll
+            for (int kk = 0; kk < 6; ++kk)
+              if (kk < D2) {
+                const int i = nb_of(j1, meta1, kk);
+                sn1[kk] = swg[i];
+                if (!refresh) fn1[kk] = fmg[i];
+                jw1[kk] = __ldg(Jp0 + (int64_t)kk * G.nsp + v1);
+              }
+            if (refresh) {
+              hj1 = __ldg(hf + j1);
+            } else {
+#pragma unroll
+              for (int q = 0; q < LPS / 4; ++q) cp_async16(sF + lane * LPS + 4 * q, Fg + (size_t)v1 * LPS + 4 * q);
+            }
+          }
+          if (!refresh) cp_async_wait_all();
+          __syncwarp();
+          while (todo) {
+            uint32_t t = todo;
+            for (int q = 0; q < sub; ++q) t &= t - 1u;
+            const int src = t ? __ffs(t) - 1 : 31;
+            const bool valid = t != 0u;
+            for (int q = 0; q < SPW; ++q) todo &= todo - 1u;
+            const int v = __shfl_sync(0xffffffffu, v1, src);
+            const int j = __shfl_sync(0xffffffffu, j1, src);
+            const uint32_t pj = __shfl_sync(0xffffffffu, p1, src);
+            const uint32_t meta = __shfl_sync(0xffffffffu, meta1, src);
+            const uint32_t wj = __shfl_sync(0xffffffffu, wj1, src);
+            uint32_t sn[6], fn[6];
+            float jw[6];
+#pragma unroll
+            for (int kk = 0; kk < 6; ++kk) {
+              sn[kk] = 0u;
+              fn[kk] = 0u;
+              jw[kk] = 0.0f;
+              if (kk < D2) {
+                sn[kk] = __shfl_sync(0xffffffffu, sn1[kk], src);
+                jw[kk] = __shfl_sync(0xffffffffu, jw1[kk], src);
+                if (!refresh) fn[kk] = __shfl_sync(0xffffffffu, fn1[kk], src);
+              }
+            }
+            const float hj = __shfl_sync(0xffffffffu, hj1, src);
+            const bool need = valid && (refresh || ((pj >> ln) & 1u));
+            const bool up = (wj >> ln) & 1u;
+            bool flip = false;
+            if (need) {
+              float *Fp = Fg + (size_t)v * LPS + ln;
+              float f;
+              if (refresh) {
+                // from scratch: the FP64 sum rounded to FP32, formed exactly in
+                // fixed point when the exponent range allows it
+                XRange xr;
+                xr_see(xr, hj);
+#pragma unroll
+                for (int kk = 0; kk < 6; ++kk)
+                  if (kk < D2) xr_see(xr, jw[kk]);
+                if (xr_exact(xr)) {
+                  const int u = xr.emax < 0 ? 24 : xr.emin;
+                  int64_t acc = xr_term(hj, u);
+#pragma unroll
+                  for (int kk = 0; kk < 6; ++kk)
+                    if (kk < D2) {
+                      const int64_t tt = xr_term(jw[kk], u);
+                      acc += ((sn[kk] >> ln) & 1u) ? tt : -tt;
+                    }
+                  f = xr_round(acc, u);
+                } else {
+                  double acc = (double)hj;
+#pragma unroll
+                  for (int kk = 0; kk < 6; ++kk)
+                    if (kk < D2) acc = __dadd_rn(acc, ((sn[kk] >> ln) & 1u) ? (double)jw[kk] : -(double)jw[kk]);
+                  f = __double2float_rn(acc);
+                }
+                *Fp = f;
+                flip = up ? (f < 0.0f) : (f > 0.0f);
+              } else {
+                // the flips of the neighbours since this spin's previous visit, in
+                // CSR order; with none the field and the decision are unchanged
+                f = sF[src * LPS + ln];
+                bool dirty = false;
+#pragma unroll
+                for (int kk = 0; kk < 6; ++kk)
+                  if (kk < D2 && ((fn[kk] >> ln) & 1u)) {
+                    const float w2 = 2.0f * jw[kk];
+                    f = __fadd_rn(f, ((sn[kk] >> ln) & 1u) ? w2 : -w2);
+                    dirty = true;
+                  }
+                if (dirty) {
+                  *Fp = f;
+                  flip = up ? (f < 0.0f) : (f > 0.0f);
+                }
+              }
+              flip = flip && ((active >> ln) & 1u);
+            }
+            const uint32_t m = __ballot_sync(0xffffffffu, flip);
+            const uint32_t seg = (m >> (sub * LPS)) & lmask;
+            if (valid && ln == 0) {
+              if (seg) {
+                swg[j] = wj ^ seg;
+                for (int kk = 0; kk < D2; ++kk) atomicOr(&pendg[nb_of(j, meta, kk)], seg);
+              }
+              if (seg || fmg[j]) fmg[j] = seg;
+            }
+            anyg |= seg;
+            my_flips += flip ? 1 : 0;
+          }
+          __syncwarp();  // the staged fields are read before the next step overwrites them
+        }
+      } else
+      for (int base = wid * 32; base < cs; base += nwarps * 32) {
+        const int v1 = c0 + base + lane;
+        const bool valid1 = v1 < c1;
+        const int j1 = valid1 ? (A.sequential ? v1 : __ldg(G.order + so + v1)) : 0;
+        const uint32_t p1 = valid1 ? pendg[j1] : 0u;
+        const uint32_t meta1 = (LAT && valid1) ? __ldg(G.meta + so + v1) : 0u;
         // Only a spin with a neighbour that flipped since its last visit can
         // change its decision (its field is otherwise unchanged and it was left
-        // stable); the pending mask, pushed by flipping neighbours, says which lanes.
-        const uint32_t pj = valid ? pendg[j] : 0u;
-        const bool need = valid && (fresh || ((pj >> ln) & 1u));
-        const uint32_t wj = valid ? swg[j] : 0u;
-        const bool up = (wj >> ln) & 1u;
-        bool flip = false;
-        if (need) {
-          const uint32_t meta = LAT ? __ldg(G.meta + so + v) : 0u;
-          const uint32_t k0 = LAT ? 0u : __ldg(G.row + so + j);
-          const uint32_t k1 = LAT ? (uint32_t)(2 * I.lat_d) : __ldg(G.row + so + j + 1);
-          const uint32_t e0 = LAT ? 0u : __ldg(G.inc_ptr + so + j);
-          const uint32_t e1 = LAT ? 0u : __ldg(G.inc_ptr + so + j + 1);
-          auto nbr = [&](uint32_t kk) -> int {
-            if (LAT) {
-              const int dir = (meta >> (8 + 3 * kk)) & 7;
-              return j + s_off[dir] + (((meta >> kk) & 1u) ? s_wrap[dir] : 0);
-            }
-            return __ldg(G.col + kk);
-          };
-          if (MODE == 0) {
-            int f = __ldg(reinterpret_cast<const int8_t *>(G.h) + so + j);
-            const int8_t *Jp = LAT ? reinterpret_cast<const int8_t *>(G.Jpos) + so + v : nullptr;
-            for (uint32_t kk = k0; kk < k1; ++kk) {
-              const int i = nbr(kk);
-              const int w = LAT ? (int)__ldg(Jp + (int64_t)kk * G.nsp) : (int)__ldg(reinterpret_cast<const int8_t *>(G.J) + kk);
-              f += ((swg[i] >> ln) & 1u) ? w : -w;
-            }
-            for (uint32_t q = e0; q < e1; ++q) {
-              const int e = __ldg(G.inc_edge + q);
-              uint32_t neg = 0;
-              for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
-                const int mm = __ldg(G.hmem + m);
-                if (mm != j) neg ^= ~(swg[mm] >> ln) & 1u;
+        // stable); the pending mask, pushed by flipping neighbours, says which
+        // lanes.  The class is an independent set, so nothing pushes into it now.
+        const bool need1 = valid1 && (fresh || (p1 & active) != 0u);
+        if (valid1 && p1) pendg[j1] = 0u;
+        if (MODE == 1 && valid1 && !need1 && !refresh && fmg[j1]) fmg[j1] = 0u;  // no flips at this visit
+        uint32_t todo = __ballot_sync(0xffffffffu, need1);
+        while (todo) {
+          uint32_t t = todo;
+          for (int q = 0; q < sub; ++q) t &= t - 1u;
+          const int src = t ? __ffs(t) - 1 : 31;
+          const bool valid = t != 0u;
+          for (int q = 0; q < SPW; ++q) todo &= todo - 1u;
+          const int v = __shfl_sync(0xffffffffu, v1, src);
+          const int j = __shfl_sync(0xffffffffu, j1, src);
+          const uint32_t pj = __shfl_sync(0xffffffffu, p1, src);
+          const uint32_t meta = __shfl_sync(0xffffffffu, meta1, src);
+          const bool need = valid && (fresh || ((pj >> ln) & 1u));
+          const uint32_t wj = valid ? swg[j] : 0u;
+          const bool up = (wj >> ln) & 1u;
+          bool flip = false;
+          if (need) {
+            const uint32_t k0 = LAT ? 0u : __ldg(G.row + so + j);
+            const uint32_t k1 = LAT ? (uint32_t)(2 * I.lat_d) : __ldg(G.row + so + j + 1);
+            const uint32_t e0 = LAT ? 0u : __ldg(G.inc_ptr + so + j);
+            const uint32_t e1 = LAT ? 0u : __ldg(G.inc_ptr + so + j + 1);
+            auto nbr = [&](uint32_t kk) -> int {
+              if (LAT) {
+                const int dir = (meta >> (8 + 3 * kk)) & 7;
+                return j + s_off[dir] + (((meta >> kk) & 1u) ? s_wrap[dir] : 0);
               }
-              const int w = __ldg(reinterpret_cast<const int8_t *>(G.hJ) + e);
-              f += neg ? -w : w;
-            }
-            flip = up ? (f < 0) : (f > 0);
-          } else {
-            const float *Jp = LAT ? reinterpret_cast<const float *>(G.Jpos) + so + v : nullptr;
-            const float *hJ = reinterpret_cast<const float *>(G.hJ);
-            float *Fp = Fg + (size_t)v * LPS + ln;
-            float f;
-            if (refresh) {
-              double acc = (double)__ldg(reinterpret_cast<const float *>(G.h) + so + j);
-              for (uint32_t kk = k0; kk < k1; ++kk) {
-                const int i = nbr(kk);
-                const double w = LAT ? (double)__ldg(Jp + (int64_t)kk * G.nsp)
-                                     : (double)__ldg(reinterpret_cast<const float *>(G.J) + kk);
-                acc = __dadd_rn(acc, ((swg[i] >> ln) & 1u) ? w : -w);
+              return __ldg(G.col + kk);
+            };
+            if (MODE == 0) {
+              int f = __ldg(reinterpret_cast<const int8_t *>(G.h) + so + j);
+              const int8_t *Jp = LAT ? reinterpret_cast<const int8_t *>(G.Jpos) + so + v : nullptr;
+              if (LAT) {
+                uint32_t sn[6];
+                int wv[6];
+#pragma unroll
+                for (int kk = 0; kk < 6; ++kk)
+                  if (kk < (int)k1) {
+                    sn[kk] = swg[nbr(kk)];
+                    wv[kk] = __ldg(Jp + (int64_t)kk * G.nsp);
+                  }
+#pragma unroll
+                for (int kk = 0; kk < 6; ++kk)
+                  if (kk < (int)k1) f += ((sn[kk] >> ln) & 1u) ? wv[kk] : -wv[kk];
+              } else {
+                for (uint32_t kk = k0; kk < k1; ++kk) {
+                  const int w = (int)__ldg(reinterpret_cast<const int8_t *>(G.J) + kk);
+                  f += ((swg[nbr(kk)] >> ln) & 1u) ? w : -w;
+                }
               }
               for (uint32_t q = e0; q < e1; ++q) {
                 const int e = __ldg(G.inc_edge + q);
@@ -308,85 +470,169 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
                   const int mm = __ldg(G.hmem + m);
                   if (mm != j) neg ^= ~(swg[mm] >> ln) & 1u;
                 }
-                const double w = (double)__ldg(hJ + e);
-                acc = __dadd_rn(acc, neg ? -w : w);
+                const int w = __ldg(reinterpret_cast<const int8_t *>(G.hJ) + e);
+                f += neg ? -w : w;
               }
-              f = __double2float_rn(acc);
-              *Fp = f;
-              flip = up ? (f < 0.0f) : (f > 0.0f);
+              flip = up ? (f < 0) : (f > 0);
             } else {
-              // Pull the flips of the neighbours since this spin's previous visit.
-              // If none flipped (for this lane) the field and so the decision
-              // are unchanged: a spin left stable by its last visit stays stable.
-              uint32_t flipped_k = 0;
-              for (uint32_t kk = k0; kk < k1; ++kk)
-                if ((fmg[nbr(kk)] >> ln) & 1u) flipped_k |= 1u << (kk - k0);
-              uint32_t par_e = 0;
-              for (uint32_t q = e0; q < e1; ++q) {
-                const int e = __ldg(G.inc_edge + q);
-                uint32_t par = 0;
-                for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
-                  const int mm = __ldg(G.hmem + m);
-                  if (mm != j) par ^= (fmg[mm] >> ln) & 1u;
-                }
-                par_e |= par << (q - e0);
-              }
-              if (flipped_k | par_e) {
-                f = *Fp;
-                for (uint32_t kk = k0; kk < k1; ++kk)
-                  if ((flipped_k >> (kk - k0)) & 1u) {
-                    const int i = nbr(kk);
-                    const float w2 = 2.0f * (LAT ? __ldg(Jp + (int64_t)kk * G.nsp)
-                                                 : __ldg(reinterpret_cast<const float *>(G.J) + kk));
-                    f = __fadd_rn(f, ((swg[i] >> ln) & 1u) ? w2 : -w2);
-                  }
-                for (uint32_t q = e0; q < e1; ++q)
-                  if ((par_e >> (q - e0)) & 1u) {
-                    const int e = __ldg(G.inc_edge + q);
-                    uint32_t neg = 0;
-                    for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
-                      const int mm = __ldg(G.hmem + m);
-                      if (mm != j) neg ^= ~(swg[mm] >> ln) & 1u;
+              const float *Jp = LAT ? reinterpret_cast<const float *>(G.Jpos) + so + v : nullptr;
+              float *Fp = Fg + (size_t)v * LPS + ln;
+              auto coup = [&](uint32_t kk) -> float {
+                return LAT ? __ldg(Jp + (int64_t)kk * G.nsp) : __ldg(Jf + kk);
+              };
+              float f;
+              if (refresh) {
+                // from scratch: the FP64 sum rounded to FP32, formed exactly in
+                // fixed point when the exponent range allows it
+                const float hj = __ldg(reinterpret_cast<const float *>(G.h) + so + j);
+                float jw[6];
+                uint32_t sn[6];
+                XRange xr;
+                xr_see(xr, hj);
+                if (LAT) {
+#pragma unroll
+                  for (int kk = 0; kk < 6; ++kk)
+                    if (kk < (int)k1) {
+                      jw[kk] = coup(kk);
+                      sn[kk] = swg[nbr(kk)];
+                      xr_see(xr, jw[kk]);
                     }
-                    const float w2 = 2.0f * __ldg(hJ + e);
-                    f = __fadd_rn(f, neg ? -w2 : w2);
+                } else {
+                  for (uint32_t kk = k0; kk < k1; ++kk) xr_see(xr, coup(kk));
+                  for (uint32_t q = e0; q < e1; ++q) xr_see(xr, __ldg(hJf + __ldg(G.inc_edge + q)));
+                }
+                auto hyper_neg = [&](int e) -> uint32_t {
+                  uint32_t neg = 0;
+                  for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
+                    const int mm = __ldg(G.hmem + m);
+                    if (mm != j) neg ^= ~(swg[mm] >> ln) & 1u;
                   }
+                  return neg;
+                };
+                if (xr_exact(xr)) {
+                  const int u = xr.emax < 0 ? 24 : xr.emin;
+                  int64_t acc = xr_term(hj, u);
+                  if (LAT) {
+#pragma unroll
+                    for (int kk = 0; kk < 6; ++kk)
+                      if (kk < (int)k1) {
+                        const int64_t tt = xr_term(jw[kk], u);
+                        acc += ((sn[kk] >> ln) & 1u) ? tt : -tt;
+                      }
+                  } else {
+                    for (uint32_t kk = k0; kk < k1; ++kk) {
+                      const int64_t tt = xr_term(coup(kk), u);
+                      acc += ((swg[nbr(kk)] >> ln) & 1u) ? tt : -tt;
+                    }
+                  }
+                  for (uint32_t q = e0; q < e1; ++q) {
+                    const int e = __ldg(G.inc_edge + q);
+                    const int64_t tt = xr_term(__ldg(hJf + e), u);
+                    acc += hyper_neg(e) ? -tt : tt;
+                  }
+                  f = xr_round(acc, u);
+                } else {
+                  double acc = (double)hj;
+                  for (uint32_t kk = k0; kk < k1; ++kk) {
+                    const double w = (double)coup(kk);
+                    acc = __dadd_rn(acc, ((swg[nbr(kk)] >> ln) & 1u) ? w : -w);
+                  }
+                  for (uint32_t q = e0; q < e1; ++q) {
+                    const int e = __ldg(G.inc_edge + q);
+                    const double w = (double)__ldg(hJf + e);
+                    acc = __dadd_rn(acc, hyper_neg(e) ? -w : w);
+                  }
+                  f = __double2float_rn(acc);
+                }
                 *Fp = f;
                 flip = up ? (f < 0.0f) : (f > 0.0f);
-              }
-            }
-          }
-          flip = flip && ((active >> ln) & 1u);
-        }
-        const uint32_t m = __ballot_sync(0xffffffffu, flip);
-        const uint32_t seg = (m >> (sub * LPS)) & lmask;
-        if (valid && ln == 0) {
-          if (pj) pendg[j] = 0u;
-          if (seg) {
-            swg[j] = wj ^ seg;
-            // tell the neighbours (and hyper-edge co-members) which lanes flipped
-            if (LAT) {
-              const uint32_t meta = __ldg(G.meta + so + v);
-              for (int kk = 0; kk < 2 * I.lat_d; ++kk) {
-                const int dir = (meta >> (8 + 3 * kk)) & 7;
-                atomicOr(&pendg[j + s_off[dir] + (((meta >> kk) & 1u) ? s_wrap[dir] : 0)], seg);
-              }
-            } else {
-              for (uint32_t kk = __ldg(G.row + so + j), k1 = __ldg(G.row + so + j + 1); kk < k1; ++kk)
-                atomicOr(&pendg[__ldg(G.col + kk)], seg);
-              for (uint32_t q = __ldg(G.inc_ptr + so + j), q1 = __ldg(G.inc_ptr + so + j + 1); q < q1; ++q) {
-                const int e = __ldg(G.inc_edge + q);
-                for (uint32_t mm = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); mm < me; ++mm) {
-                  const int o = __ldg(G.hmem + mm);
-                  if (o != j) atomicOr(&pendg[o], seg);
+              } else {
+                // Pull the flips of the neighbours since this spin's previous
+                // visit (CSR order, then hyper-edges ascending).  If none flipped
+                // for this lane the field and so the decision are unchanged.
+                f = *Fp;
+                bool dirty = false;
+                if (LAT) {
+                  uint32_t fn[6], sn[6];
+                  float jw[6];
+#pragma unroll
+                  for (int kk = 0; kk < 6; ++kk)
+                    if (kk < (int)k1) {
+                      const int i = nbr(kk);
+                      fn[kk] = fmg[i];
+                      sn[kk] = swg[i];
+                      jw[kk] = coup(kk);
+                    }
+#pragma unroll
+                  for (int kk = 0; kk < 6; ++kk)
+                    if (kk < (int)k1 && ((fn[kk] >> ln) & 1u)) {
+                      const float w2 = 2.0f * jw[kk];
+                      f = __fadd_rn(f, ((sn[kk] >> ln) & 1u) ? w2 : -w2);
+                      dirty = true;
+                    }
+                } else {
+                  for (uint32_t kk = k0; kk < k1; ++kk) {
+                    const int i = nbr(kk);
+                    if ((fmg[i] >> ln) & 1u) {
+                      const float w2 = 2.0f * coup(kk);
+                      f = __fadd_rn(f, ((swg[i] >> ln) & 1u) ? w2 : -w2);
+                      dirty = true;
+                    }
+                  }
+                  for (uint32_t q = e0; q < e1; ++q) {
+                    const int e = __ldg(G.inc_edge + q);
+                    uint32_t neg = 0, par = 0;
+                    for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
+                      const int mm = __ldg(G.hmem + m);
+                      if (mm != j) {
+                        const uint32_t x = swg[mm];
+                        neg ^= ~(x >> ln) & 1u;
+                        par ^= (fmg[mm] >> ln) & 1u;
+                      }
+                    }
+                    if (par) {
+                      const float w2 = 2.0f * __ldg(hJf + e);
+                      f = __fadd_rn(f, neg ? -w2 : w2);
+                      dirty = true;
+                    }
+                  }
+                }
+                if (dirty) {
+                  *Fp = f;
+                  flip = up ? (f < 0.0f) : (f > 0.0f);
                 }
               }
             }
+            flip = flip && ((active >> ln) & 1u);
           }
-          if (MODE == 1 && (seg || fmg[j])) fmg[j] = seg;
+          const uint32_t m = __ballot_sync(0xffffffffu, flip);
+          const uint32_t seg = (m >> (sub * LPS)) & lmask;
+          if (valid && ln == 0) {
+            if (seg) {
+              swg[j] = wj ^ seg;
+              // tell the neighbours (and hyper-edge co-members) which lanes flipped
+              if (LAT) {
+                for (int kk = 0; kk < 2 * I.lat_d; ++kk) {
+                  const int dir = (meta >> (8 + 3 * kk)) & 7;
+                  atomicOr(&pendg[j + s_off[dir] + (((meta >> kk) & 1u) ? s_wrap[dir] : 0)], seg);
+                }
+              } else {
+                for (uint32_t kk = __ldg(G.row + so + j), k1 = __ldg(G.row + so + j + 1); kk < k1; ++kk)
+                  atomicOr(&pendg[__ldg(G.col + kk)], seg);
+                for (uint32_t q = __ldg(G.inc_ptr + so + j), q1 = __ldg(G.inc_ptr + so + j + 1); q < q1; ++q) {
+                  const int e = __ldg(G.inc_edge + q);
+                  for (uint32_t mm = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); mm < me; ++mm) {
+                    const int o = __ldg(G.hmem + mm);
+                    if (o != j) atomicOr(&pendg[o], seg);
+                  }
+                }
+              }
+            }
+            if (MODE == 1 && (seg || fmg[j])) fmg[j] = seg;
+          }
+          anyg |= seg;
+          my_flips += flip ? 1 : 0;
         }
-        anyg |= seg;
-        my_flips += flip ? 1 : 0;
       }
       anyg = __reduce_or_sync(0xffffffffu, anyg);
       if (lane == 0 && anyg) atomicOr(&s_any[g], anyg);
@@ -428,8 +674,10 @@ __global__ void sweep_end(SweepArgs A) {
 }
 
 // Energies of the lanes whose round ended (all lanes of the group at once,
-// lane-parallel, FP64 or exact int64), then - in the last CTA to finish - the
-// round's bookkeeping: minima, best energies, the next descent's lanes.
+// lane-parallel; exact int64 for integer couplings, exact 64-bit fixed point
+// for FP32 couplings when InstDesc::ebase >= 0, else FP64), then - in the last
+// CTA to finish - the round's bookkeeping: minima, best energies, the next
+// descent's lanes.  Per-CTA partials are added in CTA order (deterministic).
 template <bool FLOAT, int LPS, bool LAT>
 __global__ void __launch_bounds__(kST) sweep_energy(SweepArgs A) {
   __shared__ double s_red[kST / 32][32];
@@ -438,6 +686,9 @@ __global__ void __launch_bounds__(kST) sweep_energy(SweepArgs A) {
   const InstDesc &I = A.I;
   const int n = I.n, L = I.lat_L;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int ub = I.ebase;
+  const bool fx = FLOAT && ub >= 0;
+  const size_t half = (size_t)A.grid_e * A.G * 32;
   bool any = false;
   for (int g = 0; g < A.G; ++g) any = any || A.gs[g].round_end || A.gs[g].final_pass;
   if (!any) return;
@@ -447,34 +698,55 @@ __global__ void __launch_bounds__(kST) sweep_energy(SweepArgs A) {
     const GroupState &S = A.gs[g];
     double accd = 0.0;
     long long acci = 0;
+    unsigned long long accl = 0;
     if (S.round_end || S.final_pass) {
       const uint32_t *swg = A.sw + (size_t)g * n;
-      const int64_t wtot = (n + SPW - 1) / SPW;
-      for (int64_t wi = (int64_t)blockIdx.x * nw + warp; wi < wtot; wi += (int64_t)gridDim.x * nw) {
-        const int v = (int)(wi * SPW + sub);
+      // 32 positions per warp step: one coalesced read of their site indices
+      // and lattice metadata, then SPW sites at a time, several steps unrolled
+      // so that their neighbour reads are in flight together
+      for (int base = (blockIdx.x * nw + warp) * 32; base < n; base += gridDim.x * nw * 32) {
+        const int v1 = base + lane;
+        const int j1 = v1 < n ? ((LAT && !A.sequential) ? __ldg(G.order + I.spin_off + v1) : v1) : 0;
+        const uint32_t meta1 = (LAT && v1 < n) ? __ldg(G.meta + I.spin_off + v1) : 0u;
+#pragma unroll 4
+      for (int st = 0; st < 32 / SPW; ++st) {
+        const int src = st * SPW + sub;
+        const int v = base + src;
+        const int j = __shfl_sync(0xffffffffu, j1, src);
+        const uint32_t meta = __shfl_sync(0xffffffffu, meta1, src);
         if (v >= n) continue;
-        const int j = (LAT && !A.sequential) ? __ldg(G.order + I.spin_off + v) : v;
         const int64_t gj = I.spin_off + j;
         const uint32_t bj = (swg[j] >> ln) & 1u;
-        const uint32_t meta = LAT ? __ldg(G.meta + I.spin_off + v) : 0u;
         const uint32_t k0 = LAT ? 0u : __ldg(G.row + gj);
         const uint32_t k1 = LAT ? (uint32_t)(2 * I.lat_d) : __ldg(G.row + gj + 1);
         if (FLOAT) {
-          double e = (double)__ldg(reinterpret_cast<const float *>(G.h) + gj);
-          e = bj ? e : -e;
+          const float hv = __ldg(reinterpret_cast<const float *>(G.h) + gj);
+          double e = bj ? (double)hv : -(double)hv;
+          if (fx) {
+            const int64_t th = xr_term(hv, ub);
+            xe_add(acci, accl, bj ? -th : th);
+          }
           for (uint32_t kk = k0; kk < k1; ++kk) {
             int i;
-            double w;
+            float w;
             if (LAT) {
               i = lat_nbr(j, meta, (int)kk, L);
-              w = (double)__ldg(reinterpret_cast<const float *>(G.Jpos) + (int64_t)kk * G.nsp + I.spin_off + v);
+              w = __ldg(reinterpret_cast<const float *>(G.Jpos) + (int64_t)kk * G.nsp + I.spin_off + v);
             } else {
               i = __ldg(G.col + kk);
-              w = (double)__ldg(reinterpret_cast<const float *>(G.J) + kk);
+              w = __ldg(reinterpret_cast<const float *>(G.J) + kk);
             }
-            if (i > j) e += (((swg[i] >> ln) & 1u) ^ bj) ? -w : w;
+            if (i > j) {
+              const bool differ = ((swg[i] >> ln) & 1u) ^ bj;
+              if (fx) {
+                const int64_t t = xr_term(w, ub);
+                xe_add(acci, accl, differ ? t : -t);
+              } else {
+                e += differ ? -(double)w : (double)w;
+              }
+            }
           }
-          accd -= e;
+          if (!fx) accd -= e;
         } else {
           const int hv = __ldg(reinterpret_cast<const int8_t *>(G.h) + gj);
           int e = bj ? hv : -hv;
@@ -492,6 +764,7 @@ __global__ void __launch_bounds__(kST) sweep_energy(SweepArgs A) {
           acci -= e;
         }
       }
+      }
       // hyper-edges (CSR instances only)
       for (int64_t wi = (int64_t)blockIdx.x * nw + warp; wi < (I.n_hyper + SPW - 1) / SPW;
            wi += (int64_t)gridDim.x * nw) {
@@ -502,8 +775,13 @@ __global__ void __launch_bounds__(kST) sweep_energy(SweepArgs A) {
         for (uint32_t q = __ldg(G.hptr + ge), qe = __ldg(G.hptr + ge + 1); q < qe; ++q)
           neg ^= ~(swg[__ldg(G.hmem + q)] >> ln) & 1u;
         if (FLOAT) {
-          const double w = (double)__ldg(reinterpret_cast<const float *>(G.hJ) + ge);
-          accd -= neg ? -w : w;
+          const float w = __ldg(reinterpret_cast<const float *>(G.hJ) + ge);
+          if (fx) {
+            const int64_t t = xr_term(w, ub);
+            xe_add(acci, accl, neg ? t : -t);
+          } else {
+            accd -= neg ? -(double)w : (double)w;
+          }
         } else {
           const int w = __ldg(reinterpret_cast<const int8_t *>(G.hJ) + ge);
           acci -= neg ? -w : w;
@@ -511,19 +789,39 @@ __global__ void __launch_bounds__(kST) sweep_energy(SweepArgs A) {
       }
     }
     // lanes of the SPW sub-warps hold different spins of the same replica: fold them
-    if (FLOAT) {
-      for (int o = LPS; o < 32; o <<= 1) accd += __shfl_xor_sync(0xffffffffu, accd, o);
-    } else {
-      for (int o = LPS; o < 32; o <<= 1) acci += __shfl_xor_sync(0xffffffffu, acci, o);
+    for (int o = LPS; o < 32; o <<= 1) {
+      accd += __shfl_xor_sync(0xffffffffu, accd, o);
+      acci += __shfl_xor_sync(0xffffffffu, acci, o);
+      accl += __shfl_xor_sync(0xffffffffu, accl, o);
     }
+    const bool dbl = FLOAT && !fx;
+    long long *ri = reinterpret_cast<long long *>(&s_red[0][0]);
     __syncthreads();
-    s_red[warp][lane] = FLOAT ? accd : (double)acci;
+    if (dbl) s_red[warp][lane] = accd;
+    else ri[warp * 32 + lane] = acci;
     __syncthreads();
     if (warp == 0) {
-      double a = s_red[0][lane];
-      for (int w = 1; w < nw; ++w) a += s_red[w][lane];
-      A.partial[((size_t)blockIdx.x * A.G + g) * 32 + lane] = a;
+      double a = 0.0;
+      long long b = 0;
+      for (int w = 0; w < nw; ++w) {
+        if (dbl) a = w == 0 ? s_red[0][lane] : a + s_red[w][lane];
+        else b += ri[w * 32 + lane];
+      }
+      const size_t o = ((size_t)blockIdx.x * A.G + g) * 32 + lane;
+      if (dbl) A.partial[o] = a;
+      else reinterpret_cast<long long *>(A.partial)[o] = b;
     }
+    if (fx) {
+      __syncthreads();
+      reinterpret_cast<unsigned long long *>(ri)[warp * 32 + lane] = accl;
+      __syncthreads();
+      if (warp == 0) {
+        unsigned long long b = 0;
+        for (int w = 0; w < nw; ++w) b += reinterpret_cast<unsigned long long *>(ri)[w * 32 + lane];
+        reinterpret_cast<unsigned long long *>(A.partial)[half + ((size_t)blockIdx.x * A.G + g) * 32 + lane] = b;
+      }
+    }
+    __syncthreads();
   }
   __threadfence();
   __syncthreads();
@@ -536,9 +834,20 @@ __global__ void __launch_bounds__(kST) sweep_energy(SweepArgs A) {
     GroupState &S = A.gs[g];
     if (!(S.round_end || S.final_pass)) continue;
     if (warp == 0) {
-      double a = 0.0;
-      for (int cta = 0; cta < (int)gridDim.x; ++cta) a += A.partial[((size_t)cta * A.G + g) * 32 + lane];
-      S.E[lane] = a;
+      if (FLOAT && !fx) {
+        double a = 0.0;
+        for (int cta = 0; cta < (int)gridDim.x; ++cta) a += A.partial[((size_t)cta * A.G + g) * 32 + lane];
+        S.E[lane] = a;
+      } else {
+        long long hi = 0;
+        unsigned long long lo = 0;
+        for (int cta = 0; cta < (int)gridDim.x; ++cta) {
+          const size_t o = ((size_t)cta * A.G + g) * 32 + lane;
+          hi += reinterpret_cast<const long long *>(A.partial)[o];
+          if (fx) lo += reinterpret_cast<const unsigned long long *>(A.partial)[half + o];
+        }
+        S.E[lane] = fx ? xe_value(hi, lo, ub) : (double)hi;
+      }
     }
     __syncthreads();
     if (tid == 0) {
@@ -839,11 +1148,11 @@ cudaError_t launch_sweep(ising_handle *h, const ising_search_params *p, int32_t 
   const bool fl = h->dtype == ISING_F32;
   const int mode = fl ? 1 : (h->msc_ok ? 2 : 0);
   const int grid_e = h->sm_count * 4;
-  // scratch: sw, fm, bw [G][nmax]; F [G][nmax][LPS]; gs [G]; partial [grid_e][G][32]; counter; done
+  // scratch: sw, fm, bw, pend [G][nmax]; F [G][nmax][LPS]; gs [G]; partial [2][grid_e][G][32]; counter; done
   const size_t words = (size_t)G * h->nmax;
   auto up256 = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t need = 4 * up256(words * 4) + (fl ? up256(words * LPS * 4) : 0) + up256(G * sizeof(GroupState)) +
-                      up256((size_t)grid_e * G * 32 * 8) + 2 * 256;
+                      up256((size_t)grid_e * G * 32 * 16) + 2 * 256;
   cudaError_t e;
   if (need > S.bytes) {
     cudaFree(S.mem);
@@ -878,7 +1187,7 @@ cudaError_t launch_sweep(ising_handle *h, const ising_search_params *p, int32_t 
   A.F = fl ? (float *)take(words * LPS * 4) : nullptr;
   A.gs = (GroupState *)take(G * sizeof(GroupState));
   A.grid_e = grid_e;
-  A.partial = (double *)take((size_t)grid_e * G * 32 * 8);
+  A.partial = (double *)take((size_t)grid_e * G * 32 * 16);  // FP64 sums, or fixed-point high | low halves
   A.counter = (unsigned int *)take(64);
   A.all_done = (int32_t *)take(64);
   A.stats = h->d_stats;

@@ -35,32 +35,48 @@ namespace isg {
 namespace {
 
 // Energies of all 32 replica lanes of the tile at once (Eq. 1 + Eq. 6): one
-// warp per spin, lane = replica, FP64 (float couplings) or exact int64 (integer
-// couplings).  Each pair is counted at its smaller index, each hyper-edge once.
-// Per-lane sums are added over warps in ascending order (deterministic) and
-// written to E[32].
+// warp per spin, lane = replica.  Integer couplings sum exactly in int64;
+// FP32 couplings sum exactly in 64-bit fixed point when the instance allows it
+// (InstDesc::ebase >= 0; one final rounding to FP64), else in FP64 with warps
+// added in ascending order.  Each pair is counted at its smaller index, each
+// hyper-edge once.  Every path is deterministic; the result goes to E[32].
 template <bool FLOAT>
 __device__ void tile_energy_lanes(const DevGraph &G, const InstDesc &I, const uint32_t *sw, double *red,
                                   double *E) {
   const int n = I.n, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int ub = I.ebase;
+  const bool fx = FLOAT && ub >= 0;
   double accd = 0.0;
   long long acci = 0;
+  unsigned long long accl = 0;
   for (int i = warp; i < n; i += nw) {
     const int64_t gi = I.spin_off + i;
     const uint32_t bi = (sw[i] >> lane) & 1u;
     const uint32_t k0 = __ldg(G.row + gi), k1 = __ldg(G.row + gi + 1);
     if (FLOAT) {
       const float *Jf = reinterpret_cast<const float *>(G.J);
-      const double si = bi ? 1.0 : -1.0;
-      double e = (double)__ldg(reinterpret_cast<const float *>(G.h) + gi) * si;
-      for (uint32_t k = k0; k < k1; ++k) {
-        const int j = __ldg(G.col + k);
-        if (j > i) {
-          const double w = (double)__ldg(Jf + k);
-          e += (((sw[j] >> lane) & 1u) ^ bi) ? -w : w;
+      const float hv = __ldg(reinterpret_cast<const float *>(G.h) + gi);
+      if (fx) {
+        const int64_t th = xr_term(hv, ub);
+        xe_add(acci, accl, bi ? -th : th);
+        for (uint32_t k = k0; k < k1; ++k) {
+          const int j = __ldg(G.col + k);
+          if (j > i) {
+            const int64_t t = xr_term(__ldg(Jf + k), ub);
+            xe_add(acci, accl, (((sw[j] >> lane) & 1u) ^ bi) ? t : -t);
+          }
         }
+      } else {
+        double e = bi ? (double)hv : -(double)hv;
+        for (uint32_t k = k0; k < k1; ++k) {
+          const int j = __ldg(G.col + k);
+          if (j > i) {
+            const double w = (double)__ldg(Jf + k);
+            e += (((sw[j] >> lane) & 1u) ^ bi) ? -w : w;
+          }
+        }
+        accd -= e;
       }
-      accd -= e;
     } else {
       const int8_t *Ji = reinterpret_cast<const int8_t *>(G.J);
       const int hv = __ldg(reinterpret_cast<const int8_t *>(G.h) + gi);
@@ -81,27 +97,42 @@ __device__ void tile_energy_lanes(const DevGraph &G, const InstDesc &I, const ui
     for (uint32_t q = __ldg(G.hptr + ge), qe = __ldg(G.hptr + ge + 1); q < qe; ++q)
       neg ^= ~(sw[__ldg(G.hmem + q)] >> lane) & 1u;
     if (FLOAT) {
-      const double w = (double)__ldg(reinterpret_cast<const float *>(G.hJ) + ge);
-      accd -= neg ? -w : w;
+      const float w = __ldg(reinterpret_cast<const float *>(G.hJ) + ge);
+      if (fx) {
+        const int64_t t = xr_term(w, ub);
+        xe_add(acci, accl, neg ? t : -t);
+      } else {
+        accd -= neg ? -(double)w : (double)w;
+      }
     } else {
       const int w = __ldg(reinterpret_cast<const int8_t *>(G.hJ) + ge);
       acci -= neg ? -w : w;
     }
   }
+  long long *ri = reinterpret_cast<long long *>(red);
   __syncthreads();
-  if (FLOAT) red[warp * 32 + lane] = accd;
-  else reinterpret_cast<long long *>(red)[warp * 32 + lane] = acci;
+  if (FLOAT && !fx) red[warp * 32 + lane] = accd;
+  else ri[warp * 32 + lane] = acci;
   __syncthreads();
+  long long hi = 0;
   if (warp == 0) {
-    if (FLOAT) {
+    if (FLOAT && !fx) {
       double a = red[lane];
       for (int w = 1; w < nw; ++w) a += red[w * 32 + lane];
       E[lane] = a;
     } else {
-      const long long *ri = reinterpret_cast<const long long *>(red);
-      long long a = ri[lane];
-      for (int w = 1; w < nw; ++w) a += ri[w * 32 + lane];
-      E[lane] = (double)a;
+      for (int w = 0; w < nw; ++w) hi += ri[w * 32 + lane];
+      if (!FLOAT) E[lane] = (double)hi;
+    }
+  }
+  if (fx) {
+    __syncthreads();
+    reinterpret_cast<unsigned long long *>(red)[warp * 32 + lane] = accl;
+    __syncthreads();
+    if (warp == 0) {
+      unsigned long long lo = 0;
+      for (int w = 0; w < nw; ++w) lo += reinterpret_cast<unsigned long long *>(red)[w * 32 + lane];
+      E[lane] = xe_value(hi, lo, ub);
     }
   }
   __syncthreads();
@@ -419,23 +450,48 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *_
                 const float *hJ = reinterpret_cast<const float *>(G.hJ);
                 float f;
                 if (refresh) {
-                  double acc = (double)__ldg(reinterpret_cast<const float *>(G.h) + gj);
-                  for (uint32_t kk = k0; kk < k1; ++kk) {
-                    const int i = __ldg(G.col + kk);
-                    const double w = (double)__ldg(Jf + kk);
-                    acc = __dadd_rn(acc, ((sw[i] >> lane) & 1u) ? w : -w);
-                  }
-                  for (uint32_t q = e0; q < e1; ++q) {
-                    const int e = __ldg(G.inc_edge + q);
-                    uint32_t neg = 0;
-                    for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
-                      const int mm = __ldg(G.hmem + m);
-                      if (mm != j) neg ^= ~(sw[mm] >> lane) & 1u;
+                  const float hj = __ldg(reinterpret_cast<const float *>(G.h) + gj);
+                  XRange xr;
+                  xr_see(xr, hj);
+                  for (uint32_t kk = k0; kk < k1; ++kk) xr_see(xr, __ldg(Jf + kk));
+                  for (uint32_t q = e0; q < e1; ++q) xr_see(xr, __ldg(hJ + __ldg(G.inc_edge + q)));
+                  if (xr_exact(xr)) {
+                    const int u = xr.emax < 0 ? 24 : xr.emin;
+                    int64_t acc = xr_term(hj, u);
+                    for (uint32_t kk = k0; kk < k1; ++kk) {
+                      const int64_t t = xr_term(__ldg(Jf + kk), u);
+                      acc += ((sw[__ldg(G.col + kk)] >> lane) & 1u) ? t : -t;
                     }
-                    const double w = (double)__ldg(hJ + e);
-                    acc = __dadd_rn(acc, neg ? -w : w);
+                    for (uint32_t q = e0; q < e1; ++q) {
+                      const int e = __ldg(G.inc_edge + q);
+                      uint32_t neg = 0;
+                      for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
+                        const int mm = __ldg(G.hmem + m);
+                        if (mm != j) neg ^= ~(sw[mm] >> lane) & 1u;
+                      }
+                      const int64_t t = xr_term(__ldg(hJ + e), u);
+                      acc += neg ? -t : t;
+                    }
+                    f = xr_round(acc, u);
+                  } else {
+                    double acc = (double)hj;
+                    for (uint32_t kk = k0; kk < k1; ++kk) {
+                      const int i = __ldg(G.col + kk);
+                      const double w = (double)__ldg(Jf + kk);
+                      acc = __dadd_rn(acc, ((sw[i] >> lane) & 1u) ? w : -w);
+                    }
+                    for (uint32_t q = e0; q < e1; ++q) {
+                      const int e = __ldg(G.inc_edge + q);
+                      uint32_t neg = 0;
+                      for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
+                        const int mm = __ldg(G.hmem + m);
+                        if (mm != j) neg ^= ~(sw[mm] >> lane) & 1u;
+                      }
+                      const double w = (double)__ldg(hJ + e);
+                      acc = __dadd_rn(acc, neg ? -w : w);
+                    }
+                    f = __double2float_rn(acc);
                   }
-                  f = __double2float_rn(acc);
                 } else {
                   // Only neighbours that flipped since this spin's previous visit
                   // change its field; with none, field and decision are unchanged.

@@ -221,6 +221,41 @@ def test_sweep_family_sequential_schedule():
              kernel=isg.KERNEL_SWEEP)
 
 
+# ----------------------------------------------------------- FP32 exponent ranges
+def _exp_spread(inst, lo, hi):
+    """Scale each coupling pair, field and hyper-edge by 2^e, e in [lo, hi),
+    symmetric in the pair, so values span about hi - lo binades."""
+    n = inst.n
+    rows = np.repeat(np.arange(n), np.diff(inst.row_ptr))
+    a = np.minimum(rows, inst.col.astype(np.int64))
+    b = np.maximum(rows, inst.col.astype(np.int64))
+    e = (a * 7919 + b * 104729) % (hi - lo) + lo
+    inst.J = (inst.J.astype(np.float64) * np.exp2(e)).astype(np.float32)
+    if inst.h is not None:
+        eh = (np.arange(n) * 15485863) % (hi - lo) + lo
+        inst.h = (inst.h.astype(np.float64) * np.exp2(eh)).astype(np.float32)
+    if inst.hyper_J is not None:
+        ee = (np.arange(inst.n_hyper) * 32452843) % (hi - lo) + lo
+        inst.hyper_J = (inst.hyper_J.astype(np.float64) * np.exp2(ee)).astype(np.float32)
+    return inst
+
+
+# A refresh sums in fixed point when a spin's terms span few enough binades and
+# in FP64 otherwise; energies likewise per instance.  Both sides of each switch:
+@pytest.mark.parametrize("lo,hi", [(-12, 8), (-45, 25)])
+@pytest.mark.parametrize("kernel", [isg.KERNEL_TILE, isg.KERNEL_SWEEP])
+def test_fp32_exponent_range_graph(lo, hi, kernel):
+    inst = _exp_spread(W.random_graph(300, 5.0, 31, dtype="f32", n_hyper=25, hyper_order=(3,)), lo, hi)
+    _compare([inst], [4321], 24, False, max_sweeps=400, restarts=3, refresh_every=3, kernel=kernel)
+
+
+@pytest.mark.parametrize("lo,hi", [(-20, 4), (-50, 30)])
+def test_fp32_exponent_range_lattice_sweep(lo, hi):
+    inst = _exp_spread(W.lattice((10, 10, 10), periodic=True, couplings="gauss", fields="gauss", seed=32), lo, hi)
+    _compare([inst], [99], 16, False, max_sweeps=1000, restarts=1 << 20, sweep_budget=40,
+             refresh_every=5, kernel=isg.KERNEL_SWEEP)
+
+
 # ----------------------------------------------------------- dense SK on tensor cores
 def test_dense_sk_tensor_core_path():
     """BF16 hi+lo fields with FP32 accumulation: results are checked against the
@@ -306,7 +341,7 @@ def test_autotuner_picks_an_eligible_family_and_results_do_not_depend_on_it(tmp_
     h2.close()
 
 
-@pytest.mark.parametrize("dims,R", [((16, 16, 16), 70), ((64, 64), 40)])
+@pytest.mark.parametrize("dims,R", [((16, 16, 16), 70), ((64, 64), 40), ((32, 32, 32), 40), ((128, 128), 33)])
 def test_msc_lattice_cluster_split(dims, R):
     """Lattices whose replica groups are few are split over a 4-CTA cluster
     (distributed shared memory for the slab-boundary neighbours)."""
@@ -314,3 +349,10 @@ def test_msc_lattice_cluster_split(dims, R):
     _compare([inst], [sum(dims)], R, True, max_sweeps=200, restarts=4, kernel=isg.KERNEL_MSC)
     _compare([inst], [sum(dims) + 1], R, True, max_sweeps=3, restarts=1000, sweep_budget=17,
              kernel=isg.KERNEL_MSC)
+
+
+def test_msc_lattice_cluster_mixed_sizes():
+    """Instances of different sides in one cluster launch (per-tile slab sizes)."""
+    insts = [W.lattice((32, 32, 32), periodic=True, couplings="pm1", fields="pm1_0", seed=41),
+             W.lattice((16, 16, 16), periodic=True, couplings="pm1", seed=42)]
+    _compare(insts, [41, 42], 45, True, max_sweeps=200, restarts=3, kernel=isg.KERNEL_MSC)
