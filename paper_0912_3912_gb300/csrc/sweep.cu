@@ -120,8 +120,8 @@ __device__ __forceinline__ uint32_t sliced_ge4(uint32_t q0, uint32_t q1, uint32_
 // per warp and no index needs a division.
 template <int MODE, int LPS, bool LAT>
 __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
-  // FP32 lattice path: the stored fields of the 32 positions of a warp step
-  __shared__ __align__(16) float s_F[(MODE == 1 && LAT) ? (kST / 32) * 32 * LPS : 1];
+  // FP32 lattice path: per-warp staging of (48 LPS + 640) words (dynamic)
+  extern __shared__ __align__(16) uint32_t s_dyn[];
   __shared__ uint32_t s_any[32];
   __shared__ unsigned long long s_red[kST / 32];
   __shared__ int s_off[6], s_wrap[6];
@@ -261,13 +261,20 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
       if constexpr (MODE == 1 && LAT) {
         // Periodic lattice, FP32 fields.  Lane = position for every read a
         // visit needs (its word, the neighbour words, their flip masks, the
-        // couplings, the field, and - staged into shared memory - the stored
-        // fields of all LPS lanes), so a warp step costs one round trip to
-        // memory; the per-replica visits then take the values by shuffle.
+        // couplings, the field), so a warp step costs one round trip to memory.
+        // Refresh sweeps evaluate every (site, replica) pair: SPW sites at a
+        // time, LPS lanes each, values taken by shuffle.  Other sweeps evaluate
+        // only the pairs with a pending bit: the positions stage their reads and
+        // stored fields in shared memory, the pairs are listed, and all 32 lanes
+        // work through the list; the flips are then applied per position.
         const int D2 = 2 * I.lat_d;
         const float *Jp0 = reinterpret_cast<const float *>(G.Jpos) + so;
         const float *hf = reinterpret_cast<const float *>(G.h) + so;
-        float *sF = s_F + (tid >> 5) * 32 * LPS;
+        uint32_t *wsm = s_dyn + (tid >> 5) * (48 * LPS + 640);
+        float *sF = reinterpret_cast<float *>(wsm);                 // [32][LPS] stored fields
+        uint32_t *sP = wsm + 32 * LPS;                              // [19][32]: word, nbr words, nbr flips, couplings
+        uint16_t *sL = reinterpret_cast<uint16_t *>(sP + 19 * 32);  // [32 LPS] pending pairs (position << 5 | lane)
+        uint32_t *sSeg = sP + 19 * 32 + 16 * LPS;                   // [32] flips per position
         auto nb_of = [&](int jj, uint32_t mm, int kk) -> int {
           const int dir = (mm >> (8 + 3 * kk)) & 7;
           return jj + s_off[dir] + (((mm >> kk) & 1u) ? s_wrap[dir] : 0);
@@ -278,17 +285,90 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
           const int j1 = valid1 ? __ldg(G.order + so + v1) : 0;
           const uint32_t p1 = valid1 ? pendg[j1] : 0u;
           const uint32_t meta1 = valid1 ? __ldg(G.meta + so + v1) : 0u;
+          const uint32_t fm1 = valid1 ? fmg[j1] : 0u;
           const bool need1 = valid1 && (refresh || (p1 & active) != 0u);
           if (valid1 && p1) pendg[j1] = 0u;
-          if (valid1 && !need1 && fmg[j1]) fmg[j1] = 0u;  // no flips at this visit
+          if (valid1 && !need1 && fm1) fmg[j1] = 0u;  // no flips at this visit
           uint32_t todo = __ballot_sync(0xffffffffu, need1);
           if (!todo) continue;
-          uint32_t wj1 = 0u, sn1[6], fn1[6];
+          if (!refresh) {
+            const uint32_t pm = need1 ? (p1 & active) : 0u;
+            uint32_t wj1 = 0u;
+            if (need1) {
+              wj1 = swg[j1];
+              sP[lane] = wj1;
+#pragma unroll
+              for (int kk = 0; kk < 6; ++kk)
+                if (kk < D2) {
+                  const int i = nb_of(j1, meta1, kk);
+                  sP[(1 + kk) * 32 + lane] = swg[i];
+                  sP[(7 + kk) * 32 + lane] = fmg[i];
+                  sP[(13 + kk) * 32 + lane] = __float_as_uint(__ldg(Jp0 + (int64_t)kk * G.nsp + v1));
+                }
+#pragma unroll
+              for (int q = 0; q < LPS / 4; ++q) cp_async16(sF + lane * LPS + 4 * q, Fg + (size_t)v1 * LPS + 4 * q);
+            }
+            sSeg[lane] = 0u;
+            // list the pending pairs: exclusive prefix of the per-position counts
+            const int cnt = __popc(pm);
+            int inc = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const int y = __shfl_up_sync(0xffffffffu, inc, o);
+              if (lane >= o) inc += y;
+            }
+            const int total = __shfl_sync(0xffffffffu, inc, 31);
+            {
+              uint32_t m = pm;
+              int o = inc - cnt;
+              while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1u;
+                sL[o++] = (uint16_t)((lane << 5) | b);
+              }
+            }
+            cp_async_wait_all();
+            __syncwarp();
+            // the flips of the neighbours since this spin's previous visit, in CSR
+            // order; with none the field and the decision are unchanged
+            for (int t = lane; t < total; t += 32) {
+              const uint32_t e = sL[t];
+              const int pos = (int)(e >> 5), l = (int)(e & 31u);
+              float f = sF[pos * LPS + l];
+              bool dirty = false;
+#pragma unroll
+              for (int kk = 0; kk < 6; ++kk)
+                if (kk < D2 && ((sP[(7 + kk) * 32 + pos] >> l) & 1u)) {
+                  const float w2 = 2.0f * __uint_as_float(sP[(13 + kk) * 32 + pos]);
+                  f = __fadd_rn(f, ((sP[(1 + kk) * 32 + pos] >> l) & 1u) ? w2 : -w2);
+                  dirty = true;
+                }
+              if (dirty) {
+                Fg[(size_t)(c0 + base + pos) * LPS + l] = f;
+                const bool up = (sP[pos] >> l) & 1u;
+                if (up ? (f < 0.0f) : (f > 0.0f)) atomicOr(&sSeg[pos], 1u << l);
+              }
+            }
+            __syncwarp();
+            const uint32_t seg = need1 ? sSeg[lane] : 0u;
+            if (need1) {
+              if (seg) {
+                swg[j1] = wj1 ^ seg;
+                for (int kk = 0; kk < D2; ++kk) atomicOr(&pendg[nb_of(j1, meta1, kk)], seg);
+              }
+              if (seg || fm1) fmg[j1] = seg;
+            }
+            anyg |= seg;
+            my_flips += __popc(seg);
+            __syncwarp();  // staging read before the next batch overwrites it
+            continue;
+          }
+          // refresh sweep: every pair of every position
+          uint32_t wj1 = 0u, sn1[6];
           float jw1[6], hj1 = 0.0f;
 #pragma unroll
           for (int kk = 0; kk < 6; ++kk) {
             sn1[kk] = 0u;
-            fn1[kk] = 0u;
             jw1[kk] = 0.0f;
           }
           if (need1) {
@@ -296,20 +376,11 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
 #pragma unroll
             for (int kk = 0; kk < 6; ++kk)
               if (kk < D2) {
-                const int i = nb_of(j1, meta1, kk);
-                sn1[kk] = swg[i];
-                if (!refresh) fn1[kk] = fmg[i];
+                sn1[kk] = swg[nb_of(j1, meta1, kk)];
                 jw1[kk] = __ldg(Jp0 + (int64_t)kk * G.nsp + v1);
               }
-            if (refresh) {
-              hj1 = __ldg(hf + j1);
-            } else {
-#pragma unroll
-              for (int q = 0; q < LPS / 4; ++q) cp_async16(sF + lane * LPS + 4 * q, Fg + (size_t)v1 * LPS + 4 * q);
-            }
+            hj1 = __ldg(hf + j1);
           }
-          if (!refresh) cp_async_wait_all();
-          __syncwarp();
           while (todo) {
             uint32_t t = todo;
             for (int q = 0; q < sub; ++q) t &= t - 1u;
@@ -318,74 +389,51 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
             for (int q = 0; q < SPW; ++q) todo &= todo - 1u;
             const int v = __shfl_sync(0xffffffffu, v1, src);
             const int j = __shfl_sync(0xffffffffu, j1, src);
-            const uint32_t pj = __shfl_sync(0xffffffffu, p1, src);
             const uint32_t meta = __shfl_sync(0xffffffffu, meta1, src);
             const uint32_t wj = __shfl_sync(0xffffffffu, wj1, src);
-            uint32_t sn[6], fn[6];
+            const uint32_t fmj = __shfl_sync(0xffffffffu, fm1, src);
+            uint32_t sn[6];
             float jw[6];
 #pragma unroll
             for (int kk = 0; kk < 6; ++kk) {
               sn[kk] = 0u;
-              fn[kk] = 0u;
               jw[kk] = 0.0f;
               if (kk < D2) {
                 sn[kk] = __shfl_sync(0xffffffffu, sn1[kk], src);
                 jw[kk] = __shfl_sync(0xffffffffu, jw1[kk], src);
-                if (!refresh) fn[kk] = __shfl_sync(0xffffffffu, fn1[kk], src);
               }
             }
             const float hj = __shfl_sync(0xffffffffu, hj1, src);
-            const bool need = valid && (refresh || ((pj >> ln) & 1u));
             const bool up = (wj >> ln) & 1u;
             bool flip = false;
-            if (need) {
-              float *Fp = Fg + (size_t)v * LPS + ln;
+            if (valid) {
+              // from scratch: the FP64 sum rounded to FP32, formed exactly in
+              // fixed point when the exponent range allows it
               float f;
-              if (refresh) {
-                // from scratch: the FP64 sum rounded to FP32, formed exactly in
-                // fixed point when the exponent range allows it
-                XRange xr;
-                xr_see(xr, hj);
+              XRange xr;
+              xr_see(xr, hj);
+#pragma unroll
+              for (int kk = 0; kk < 6; ++kk)
+                if (kk < D2) xr_see(xr, jw[kk]);
+              if (xr_exact(xr)) {
+                const int u = xr.emax < 0 ? 24 : xr.emin;
+                int64_t acc = xr_term(hj, u);
 #pragma unroll
                 for (int kk = 0; kk < 6; ++kk)
-                  if (kk < D2) xr_see(xr, jw[kk]);
-                if (xr_exact(xr)) {
-                  const int u = xr.emax < 0 ? 24 : xr.emin;
-                  int64_t acc = xr_term(hj, u);
-#pragma unroll
-                  for (int kk = 0; kk < 6; ++kk)
-                    if (kk < D2) {
-                      const int64_t tt = xr_term(jw[kk], u);
-                      acc += ((sn[kk] >> ln) & 1u) ? tt : -tt;
-                    }
-                  f = xr_round(acc, u);
-                } else {
-                  double acc = (double)hj;
-#pragma unroll
-                  for (int kk = 0; kk < 6; ++kk)
-                    if (kk < D2) acc = __dadd_rn(acc, ((sn[kk] >> ln) & 1u) ? (double)jw[kk] : -(double)jw[kk]);
-                  f = __double2float_rn(acc);
-                }
-                *Fp = f;
-                flip = up ? (f < 0.0f) : (f > 0.0f);
-              } else {
-                // the flips of the neighbours since this spin's previous visit, in
-                // CSR order; with none the field and the decision are unchanged
-                f = sF[src * LPS + ln];
-                bool dirty = false;
-#pragma unroll
-                for (int kk = 0; kk < 6; ++kk)
-                  if (kk < D2 && ((fn[kk] >> ln) & 1u)) {
-                    const float w2 = 2.0f * jw[kk];
-                    f = __fadd_rn(f, ((sn[kk] >> ln) & 1u) ? w2 : -w2);
-                    dirty = true;
+                  if (kk < D2) {
+                    const int64_t tt = xr_term(jw[kk], u);
+                    acc += ((sn[kk] >> ln) & 1u) ? tt : -tt;
                   }
-                if (dirty) {
-                  *Fp = f;
-                  flip = up ? (f < 0.0f) : (f > 0.0f);
-                }
+                f = xr_round(acc, u);
+              } else {
+                double acc = (double)hj;
+#pragma unroll
+                for (int kk = 0; kk < 6; ++kk)
+                  if (kk < D2) acc = __dadd_rn(acc, ((sn[kk] >> ln) & 1u) ? (double)jw[kk] : -(double)jw[kk]);
+                f = __double2float_rn(acc);
               }
-              flip = flip && ((active >> ln) & 1u);
+              Fg[(size_t)v * LPS + ln] = f;
+              flip = (up ? (f < 0.0f) : (f > 0.0f)) && ((active >> ln) & 1u);
             }
             const uint32_t m = __ballot_sync(0xffffffffu, flip);
             const uint32_t seg = (m >> (sub * LPS)) & lmask;
@@ -394,12 +442,11 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
                 swg[j] = wj ^ seg;
                 for (int kk = 0; kk < D2; ++kk) atomicOr(&pendg[nb_of(j, meta, kk)], seg);
               }
-              if (seg || fmg[j]) fmg[j] = seg;
+              if (seg || fmj) fmg[j] = seg;
             }
             anyg |= seg;
             my_flips += flip ? 1 : 0;
           }
-          __syncwarp();  // the staged fields are read before the next step overwrites them
         }
       } else
       for (int base = wid * 32; base < cs; base += nwarps * 32) {
@@ -681,6 +728,7 @@ __global__ void sweep_end(SweepArgs A) {
 template <bool FLOAT, int LPS, bool LAT>
 __global__ void __launch_bounds__(kST) sweep_energy(SweepArgs A) {
   __shared__ double s_red[kST / 32][32];
+  __shared__ __align__(8) uint32_t s_stage[LAT ? (kST / 32) * 704 : 1];
   __shared__ bool s_last;
   const DevGraph &G = A.g;
   const InstDesc &I = A.I;
@@ -701,69 +749,155 @@ __global__ void __launch_bounds__(kST) sweep_energy(SweepArgs A) {
     unsigned long long accl = 0;
     if (S.round_end || S.final_pass) {
       const uint32_t *swg = A.sw + (size_t)g * n;
-      // 32 positions per warp step: one coalesced read of their site indices
-      // and lattice metadata, then SPW sites at a time, several steps unrolled
-      // so that their neighbour reads are in flight together
-      for (int base = (blockIdx.x * nw + warp) * 32; base < n; base += gridDim.x * nw * 32) {
-        const int v1 = base + lane;
-        const int j1 = v1 < n ? ((LAT && !A.sequential) ? __ldg(G.order + I.spin_off + v1) : v1) : 0;
-        const uint32_t meta1 = (LAT && v1 < n) ? __ldg(G.meta + I.spin_off + v1) : 0u;
-#pragma unroll 4
-      for (int st = 0; st < 32 / SPW; ++st) {
-        const int src = st * SPW + sub;
-        const int v = base + src;
-        const int j = __shfl_sync(0xffffffffu, j1, src);
-        const uint32_t meta = __shfl_sync(0xffffffffu, meta1, src);
-        if (v >= n) continue;
-        const int64_t gj = I.spin_off + j;
-        const uint32_t bj = (swg[j] >> ln) & 1u;
-        const uint32_t k0 = LAT ? 0u : __ldg(G.row + gj);
-        const uint32_t k1 = LAT ? (uint32_t)(2 * I.lat_d) : __ldg(G.row + gj + 1);
-        if (FLOAT) {
-          const float hv = __ldg(reinterpret_cast<const float *>(G.h) + gj);
-          double e = bj ? (double)hv : -(double)hv;
-          if (fx) {
-            const int64_t th = xr_term(hv, ub);
-            xe_add(acci, accl, bj ? -th : th);
-          }
-          for (uint32_t kk = k0; kk < k1; ++kk) {
-            int i;
-            float w;
-            if (LAT) {
-              i = lat_nbr(j, meta, (int)kk, L);
-              w = __ldg(reinterpret_cast<const float *>(G.Jpos) + (int64_t)kk * G.nsp + I.spin_off + v);
+      if constexpr (LAT) {
+        // Lattice: lane = position stages the position's word, its forward
+        // neighbours' words (those with a larger index, so each bond counts
+        // once) and its terms - fixed-point integers, FP32 values or integers -
+        // in shared memory in one round trip; the per-replica steps then read
+        // shared memory only.
+        uint32_t *sW = s_stage + warp * 704;      // [32] words
+        uint32_t *sN = sW + 32;                   // [6][32] forward neighbour words
+        uint32_t *sT = sW + 224;                  // [7][32] x 2: terms (kk 0..5, field)
+        uint32_t *sM = sW + 672;                  // [32] forward mask
+        for (int base = (blockIdx.x * nw + warp) * 32; base < n; base += gridDim.x * nw * 32) {
+          const int v1 = base + lane;
+          if (v1 < n) {
+            const int j1 = __ldg(G.order + I.spin_off + v1);
+            const uint32_t meta1 = __ldg(G.meta + I.spin_off + v1);
+            sW[lane] = swg[j1];
+            uint32_t fwd = 0u;
+#pragma unroll
+            for (int kk = 0; kk < 6; ++kk)
+              if (kk < 2 * I.lat_d) {
+                const int i = lat_nbr(j1, meta1, kk, L);
+                if (i > j1) {
+                  fwd |= 1u << kk;
+                  sN[kk * 32 + lane] = swg[i];
+                  const int64_t jp = (int64_t)kk * G.nsp + I.spin_off + v1;
+                  int64_t t;
+                  if (FLOAT) {
+                    const float w = __ldg(reinterpret_cast<const float *>(G.Jpos) + jp);
+                    t = fx ? xr_term(w, ub) : (int64_t)__float_as_uint(w);
+                  } else {
+                    t = __ldg(reinterpret_cast<const int8_t *>(G.Jpos) + jp);
+                  }
+                  reinterpret_cast<int64_t *>(sT)[kk * 32 + lane] = t;
+                }
+              }
+            int64_t th;
+            if (FLOAT) {
+              const float hv = __ldg(reinterpret_cast<const float *>(G.h) + I.spin_off + j1);
+              th = fx ? xr_term(hv, ub) : (int64_t)__float_as_uint(hv);
             } else {
-              i = __ldg(G.col + kk);
-              w = __ldg(reinterpret_cast<const float *>(G.J) + kk);
+              th = __ldg(reinterpret_cast<const int8_t *>(G.h) + I.spin_off + j1);
             }
-            if (i > j) {
-              const bool differ = ((swg[i] >> ln) & 1u) ^ bj;
-              if (fx) {
-                const int64_t t = xr_term(w, ub);
-                xe_add(acci, accl, differ ? t : -t);
+            reinterpret_cast<int64_t *>(sT)[6 * 32 + lane] = th;
+            sM[lane] = fwd;
+          }
+          __syncwarp();
+          const int cnt = min(32, n - base);
+          for (int src = sub; src < cnt; src += SPW) {
+            const uint32_t bj = (sW[src] >> ln) & 1u;
+            const uint32_t fwd = sM[src];
+            const int64_t *T = reinterpret_cast<const int64_t *>(sT);
+            if (FLOAT && fx) {
+              const int64_t th = T[6 * 32 + src];
+              xe_add(acci, accl, bj ? -th : th);
+#pragma unroll
+              for (int kk = 0; kk < 6; ++kk)
+                if ((fwd >> kk) & 1u) {
+                  const int64_t t = T[kk * 32 + src];
+                  xe_add(acci, accl, (((sN[kk * 32 + src] >> ln) & 1u) ^ bj) ? t : -t);
+                }
+            } else if (FLOAT) {
+              const double hv = (double)__uint_as_float((uint32_t)T[6 * 32 + src]);
+              double e = bj ? hv : -hv;
+#pragma unroll
+              for (int kk = 0; kk < 6; ++kk)
+                if ((fwd >> kk) & 1u) {
+                  const double w = (double)__uint_as_float((uint32_t)T[kk * 32 + src]);
+                  e += (((sN[kk * 32 + src] >> ln) & 1u) ^ bj) ? -w : w;
+                }
+              accd -= e;
+            } else {
+              const int hv = (int)T[6 * 32 + src];
+              int e = bj ? hv : -hv;
+#pragma unroll
+              for (int kk = 0; kk < 6; ++kk)
+                if ((fwd >> kk) & 1u) {
+                  const int w = (int)T[kk * 32 + src];
+                  e += (((sN[kk * 32 + src] >> ln) & 1u) ^ bj) ? -w : w;
+                }
+              acci -= e;
+            }
+          }
+          __syncwarp();
+        }
+      } else {
+      // 32 positions per warp step: one coalesced read of their site indices
+        // and lattice metadata, then SPW sites at a time, several steps unrolled
+        // so that their neighbour reads are in flight together
+        for (int base = (blockIdx.x * nw + warp) * 32; base < n; base += gridDim.x * nw * 32) {
+          const int v1 = base + lane;
+          const int j1 = v1 < n ? ((LAT && !A.sequential) ? __ldg(G.order + I.spin_off + v1) : v1) : 0;
+          const uint32_t meta1 = (LAT && v1 < n) ? __ldg(G.meta + I.spin_off + v1) : 0u;
+  #pragma unroll 4
+        for (int st = 0; st < 32 / SPW; ++st) {
+          const int src = st * SPW + sub;
+          const int v = base + src;
+          const int j = __shfl_sync(0xffffffffu, j1, src);
+          const uint32_t meta = __shfl_sync(0xffffffffu, meta1, src);
+          if (v >= n) continue;
+          const int64_t gj = I.spin_off + j;
+          const uint32_t bj = (swg[j] >> ln) & 1u;
+          const uint32_t k0 = LAT ? 0u : __ldg(G.row + gj);
+          const uint32_t k1 = LAT ? (uint32_t)(2 * I.lat_d) : __ldg(G.row + gj + 1);
+          if (FLOAT) {
+            const float hv = __ldg(reinterpret_cast<const float *>(G.h) + gj);
+            double e = bj ? (double)hv : -(double)hv;
+            if (fx) {
+              const int64_t th = xr_term(hv, ub);
+              xe_add(acci, accl, bj ? -th : th);
+            }
+            for (uint32_t kk = k0; kk < k1; ++kk) {
+              int i;
+              float w;
+              if (LAT) {
+                i = lat_nbr(j, meta, (int)kk, L);
+                w = __ldg(reinterpret_cast<const float *>(G.Jpos) + (int64_t)kk * G.nsp + I.spin_off + v);
               } else {
-                e += differ ? -(double)w : (double)w;
+                i = __ldg(G.col + kk);
+                w = __ldg(reinterpret_cast<const float *>(G.J) + kk);
+              }
+              if (i > j) {
+                const bool differ = ((swg[i] >> ln) & 1u) ^ bj;
+                if (fx) {
+                  const int64_t t = xr_term(w, ub);
+                  xe_add(acci, accl, differ ? t : -t);
+                } else {
+                  e += differ ? -(double)w : (double)w;
+                }
               }
             }
-          }
-          if (!fx) accd -= e;
-        } else {
-          const int hv = __ldg(reinterpret_cast<const int8_t *>(G.h) + gj);
-          int e = bj ? hv : -hv;
-          for (uint32_t kk = k0; kk < k1; ++kk) {
-            int i, w;
-            if (LAT) {
-              i = lat_nbr(j, meta, (int)kk, L);
-              w = __ldg(reinterpret_cast<const int8_t *>(G.Jpos) + (int64_t)kk * G.nsp + I.spin_off + v);
-            } else {
-              i = __ldg(G.col + kk);
-              w = __ldg(reinterpret_cast<const int8_t *>(G.J) + kk);
+            if (!fx) accd -= e;
+          } else {
+            const int hv = __ldg(reinterpret_cast<const int8_t *>(G.h) + gj);
+            int e = bj ? hv : -hv;
+            for (uint32_t kk = k0; kk < k1; ++kk) {
+              int i, w;
+              if (LAT) {
+                i = lat_nbr(j, meta, (int)kk, L);
+                w = __ldg(reinterpret_cast<const int8_t *>(G.Jpos) + (int64_t)kk * G.nsp + I.spin_off + v);
+              } else {
+                i = __ldg(G.col + kk);
+                w = __ldg(reinterpret_cast<const int8_t *>(G.J) + kk);
+              }
+              if (i > j) e += (((swg[i] >> ln) & 1u) ^ bj) ? -w : w;
             }
-            if (i > j) e += (((swg[i] >> ln) & 1u) ^ bj) ? -w : w;
+            acci -= e;
           }
-          acci -= e;
         }
-      }
+        }
       }
       // hyper-edges (CSR instances only)
       for (int64_t wi = (int64_t)blockIdx.x * nw + warp; wi < (I.n_hyper + SPW - 1) / SPW;
@@ -913,17 +1047,23 @@ __global__ void __launch_bounds__(kST) sweep_restart(SweepArgs A) {
         }
       __syncwarp();
       if (start) {
+        // lane l draws replica 32g + l's bits; ballots transpose them so that
+        // lane u ends up with the word of site 128w + 32q + u
         const uint4 x = start_bits(A.seed, (uint32_t)w, (uint32_t)(32 * g + lane), (uint32_t)S.k, (uint32_t)A.b);
+#pragma unroll
         for (int q = 0; q < 4; ++q) {
           const uint32_t xw = word_of(x, q);
+          uint32_t mine = 0;
+#pragma unroll
           for (int u = 0; u < 32; ++u) {
-            const int i = w * 128 + q * 32 + u;
-            if (i >= n) break;
             const uint32_t m = __ballot_sync(0xffffffffu, (xw >> u) & 1u);
-            if (lane == 0) {
-              swg[i] = (swg[i] & ~start) | (m & start);
-              fmg[i] &= ~start;
-            }
+            if (lane == u) mine = m;
+          }
+          const int i = w * 128 + q * 32 + lane;
+          if (i < n) {
+            swg[i] = (swg[i] & ~start) | (mine & start);
+            const uint32_t f = fmg[i];
+            if (f & start) fmg[i] = f & ~start;
           }
         }
       }
@@ -995,9 +1135,13 @@ void debug_step(const char *what, int c, cudaStream_t s) {
   std::fflush(stderr);
 }
 
+constexpr size_t visit_smem(int mode, int lps, bool lat) {
+  return (mode == 1 && lat) ? (size_t)(kST / 32) * (48 * lps + 640) * 4 : 0;
+}
+
 template <int MODE, int LPS, bool LAT>
 void enqueue_visit(const SweepArgs &A, int c, int grid, cudaStream_t s) {
-  sweep_visit<MODE, LPS, LAT><<<grid, kST, 0, s>>>(A, c);
+  sweep_visit<MODE, LPS, LAT><<<grid, kST, visit_smem(MODE, LPS, LAT), s>>>(A, c);
   debug_step("visit", c, s);
 }
 
@@ -1024,7 +1168,11 @@ cudaError_t preload(int mode) {
   cudaFuncAttributes fa;
   cudaError_t e = cudaSuccess;
   if (mode == 0) e = cudaFuncGetAttributes(&fa, sweep_visit<0, LPS, LAT>);
-  else if (mode == 1) e = cudaFuncGetAttributes(&fa, sweep_visit<1, LPS, LAT>);
+  else if (mode == 1) {
+    e = cudaFuncSetAttribute(sweep_visit<1, LPS, LAT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)visit_smem(1, LPS, LAT));
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, sweep_visit<1, LPS, LAT>);
+  }
   else e = cudaFuncGetAttributes(&fa, sweep_visit<2, LPS, LAT>);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, sweep_end);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, sweep_energy<true, LPS, LAT>);
