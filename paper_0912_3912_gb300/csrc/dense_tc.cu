@@ -38,7 +38,8 @@ constexpr int kTB = 128;        // spins per block (MMA N)
 constexpr int kKC = 64;         // K per TMA chunk (128 bytes of BF16)
 constexpr int kStages = 3;
 constexpr int kClus = 4;        // CTAs per cluster (split K)
-constexpr int kThreads = 128;
+constexpr int kThreads = 1024;  // one warp per decided replica (32 per CTA)
+constexpr int kFl = kTB + 1;    // padded row of the block fields [replica][spin]
 constexpr int kTileBytes = kTM * kKC * 2;                 // 16 KB
 constexpr int kStageBytes = 3 * kTileBytes;               // A, B_hi, B_lo
 constexpr int kPartialBytes = kTB * kTM * 4;              // 64 KB, [spin][replica]
@@ -65,10 +66,11 @@ struct RepState {  // per replica, owned by one thread of warp 0
   double best, E;
 };
 
-__device__ __forceinline__ void write_start(const TcArgs &A, int r, int k, uint32_t *bits) {
-  // Philox start R(b, r, k), written as BF16 +/-1 into S[r][:] and as bits
+// Philox start R(b, r, k) of replica r, written as BF16 +/-1 into S[r][:] and
+// as bits; warp-cooperative, lane l handles the 128-spin blocks l, l + 32, ...
+__device__ __forceinline__ void write_start_warp(const TcArgs &A, int r, int k, uint32_t *bits, int lane) {
   __nv_bfloat16 *row = A.S + (size_t)r * A.n;
-  for (int w = 0; w * 128 < A.n; ++w) {
+  for (int w = lane; w * 128 < A.n; w += 32) {
     const uint4 x = start_bits(A.seed, (uint32_t)w, (uint32_t)r, (uint32_t)k, (uint32_t)A.b);
     for (int q = 0; q < 4; ++q) bits[w * 4 + q] = word_of(x, q);
     for (int t = 0; t < 128 && w * 128 + t < A.n; ++t)
@@ -83,16 +85,15 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t *stage = smem;                                              // kStages x (A, Bhi, Blo)
   float *P = reinterpret_cast<float *>(smem + kStages * kStageBytes);  // partial fields [spin][replica]
-  float *Floc = reinterpret_cast<float *>(smem);                      // reuses stages: [spin][32]
-  float *Jblk = reinterpret_cast<float *>(smem + kTB * 32 * 4);       // reuses stages: [128][128]
-  float *fvs = reinterpret_cast<float *>(smem + kTB * 32 * 4 + kTB * kTB * 4);  // reuses stages: [32][128 threads]
+  float *Floc = reinterpret_cast<float *>(smem);                      // reuses stages: [32 replicas][kFl]
+  float *Jblk = reinterpret_cast<float *>(smem + 32 * kFl * 4 + 128); // reuses stages: [128][128]
   uint32_t *sbits = reinterpret_cast<uint32_t *>(smem + kStages * kStageBytes + kPartialBytes);  // [32][n/32]
 
   __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], done_bar;
   __shared__ uint32_t tmem_base_s;
   __shared__ int32_t s_flag[2];   // cluster-visible: [0] my replicas still busy, [1] my failure
   __shared__ int32_t s_ctrl[4];   // broadcast inside the CTA
-  __shared__ int32_t s_act[32], s_nfl[32];
+  __shared__ int32_t s_act[32], s_nfl[32], s_rst[32], s_cpy[32];
   __shared__ double s_en[32];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -132,10 +133,8 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
   st.E = 0.0;
   unsigned long long c_evals = 0, c_flips = 0, c_minima = 0, c_desc = 0, c_sweeps = 0;
   const int nw32 = n / 32;
-  if (real) {
-    write_start(A, my_r, 0, sbits + lane * nw32);
-    c_desc = 1;
-  }
+  if (rq + warp < A.R) write_start_warp(A, rq + warp, 0, sbits + warp * nw32, lane);
+  if (real) c_desc = 1;
   tc::fence_proxy_async_global();
   bool failed = false;
   uint32_t ph_full[kStages] = {0, 0, 0}, ph_empty[kStages] = {0, 0, 0}, ph_done = 0;
@@ -242,13 +241,14 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
         if (tid == 0 && !failed) mma_pending = 0;
       }
       ph_done ^= 1u;
-      if (!failed) {
-        for (int cc = 0; cc < kTB / 32; ++cc) {
-          uint32_t v[32];
-          tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(cc * 32), v);
+      if (!failed && warp < 16) {
+        // warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its lane quarter)
+        // and accumulator columns 32 (w / 4) .. + 31
+        const int lq = warp & 3, cc = warp >> 2;
+        uint32_t v[32];
+        tc::tmem_ld32(tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(cc * 32), v);
 #pragma unroll
-          for (int k = 0; k < 32; ++k) P[(cc * 32 + k) * kTM + 32 * warp + lane] = __uint_as_float(v[k]);
-        }
+        for (int k = 0; k < 32; ++k) P[(cc * 32 + k) * kTM + 32 * lq + lane] = __uint_as_float(v[k]);
       }
       tc::tc_fence_before();
       __syncthreads();
@@ -266,7 +266,10 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
             acc.z += p.z;
             acc.w += p.w;
           }
-          reinterpret_cast<float4 *>(Floc)[i * 8 + c4] = acc;
+          Floc[(4 * c4 + 0) * kFl + i] = acc.x;
+          Floc[(4 * c4 + 1) * kFl + i] = acc.y;
+          Floc[(4 * c4 + 2) * kFl + i] = acc.z;
+          Floc[(4 * c4 + 3) * kFl + i] = acc.w;
         }
         if (!energy_pass)
           for (int e = tid; e < kTB * kTB / 4; e += kThreads) {
@@ -277,86 +280,72 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
       }
       __syncthreads();
       tc::cluster_sync();  // partials consumed: P may be overwritten by the next block
-      // Phase 4: sequential decisions (or energy accumulation).  Four threads per
-      // replica: replica rl = tid / 4, and sub-lane ql = tid % 4 keeps the running
-      // fields of the block's spins i = 4m + ql in registers.  Spins are decided
-      // in order i = 0..127 by their owner; each flip is broadcast to the quad,
-      // which adds 2 J_ij s_j to the fields of the later spins (same FP32 order
-      // as visiting them one by one).
+      // Phase 4: sequential decisions (or energy accumulation).  Warp w decides
+      // replica rq + w; lane l keeps the fields of spins 32q + l (q = 0..3) in
+      // registers.  Spins are decided in index order; between two flips no field
+      // changes, so the warp ballots every current decision of a quarter and
+      // jumps to the first flipping spin at or after the current one, flips it,
+      // adds 2 J_ij s_j to the fields of the later spins (in flip order, the same
+      // FP32 order as visiting them one by one) and continues after it.
       if (warp == 0) s_act[lane] = (my_r < A.R && !failed) ? st.active : 0;
       __syncthreads();
       {
-        const int rl = tid >> 2, ql = tid & 3;
-        const int rr = rq + rl;
+        const int rr = rq + warp;
         const bool valid_r = rr < A.R && !failed;
-        uint32_t *mybits = sbits + rl * nw32 + (b0 >> 5);
-        uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;  // the block's 128 spins of replica rl (1 = +1)
-        if (valid_r) {
-          w0 = mybits[0];
-          w1 = mybits[1];
-          w2 = mybits[2];
-          w3 = mybits[3];
+        uint32_t *mybits = sbits + warp * nw32 + (b0 >> 5);
+        uint32_t wq[4] = {0u, 0u, 0u, 0u};  // the block's 128 spins of replica rr (1 = +1)
+        float f[4];
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+          if (valid_r) wq[qq] = mybits[qq];
+          f[qq] = valid_r ? Floc[warp * kFl + 32 * qq + lane] : 0.0f;
         }
-        auto bit = [&](int i) -> uint32_t {
-          const uint32_t w = i < 64 ? (i < 32 ? w0 : w1) : (i < 96 ? w2 : w3);
-          return (w >> (i & 31)) & 1u;
-        };
-        float *myf = fvs + tid;  // running fields of spins 4m + ql at myf[m * kThreads]
-        for (int m = 0; m < kTB / 4; ++m) myf[m * kThreads] = valid_r ? Floc[(4 * m + ql) * 32 + rl] : 0.0f;
         if (energy_pass) {
           double acc = 0.0;
-          for (int m = 0; m < kTB / 4; ++m) acc += (bit(4 * m + ql) ? 1.0 : -1.0) * (double)myf[m * kThreads];
-          acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-          acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-          if (ql == 0) s_en[rl] = valid_r ? acc : 0.0;
-        } else {
-          const bool act = valid_r && s_act[rl] != 0;
-          int nfl = 0;
-          uint32_t f0 = 0, f1 = 0, f2 = 0, f3 = 0;  // flipped in this block
-          const int qbase = lane & ~3;
-          for (int m = 0; m < kTB / 4; ++m) {
 #pragma unroll
-            for (int owner = 0; owner < 4; ++owner) {
-              const int i = 4 * m + owner;
-              const uint32_t s_up = bit(i);
-              int dec = 0;
-              if (ql == owner && act) {
-                const float f = myf[m * kThreads];
-                dec = s_up ? (f < 0.0f) : (f > 0.0f);
-              }
-              if (__shfl_sync(0xffffffffu, dec, qbase | owner)) {
-                const uint32_t msk = 1u << (i & 31);
-                if (i < 32) { w0 ^= msk; f0 |= msk; }
-                else if (i < 64) { w1 ^= msk; f1 |= msk; }
-                else if (i < 96) { w2 ^= msk; f2 |= msk; }
-                else { w3 ^= msk; f3 |= msk; }
-                if (ql == owner) ++nfl;
+          for (int qq = 0; qq < 4; ++qq) acc += (((wq[qq] >> lane) & 1u) ? 1.0 : -1.0) * (double)f[qq];
+          acc = warp_sum(acc);
+          if (lane == 0) s_en[warp] = valid_r ? acc : 0.0;
+        } else {
+          const bool act = valid_r && s_act[warp] != 0;
+          int nfl = 0;
+          uint32_t fl[4] = {0u, 0u, 0u, 0u};
+          if (act) {
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+              uint32_t from = 0xffffffffu;  // lanes not yet decided in this quarter
+              for (;;) {
+                const bool up = (wq[qq] >> lane) & 1u;
+                const bool dec = up ? (f[qq] < 0.0f) : (f[qq] > 0.0f);
+                const uint32_t m = __ballot_sync(0xffffffffu, dec) & from;
+                if (!m) break;
+                const int li = __ffs(m) - 1, i = 32 * qq + li;
+                const bool s_up = (wq[qq] >> li) & 1u;
+                wq[qq] ^= 1u << li;
+                fl[qq] |= 1u << li;
+                ++nfl;
                 const float sgn = s_up ? -2.0f : 2.0f;  // 2 s_i with the new spin
-                const float *Jrow = Jblk + i * kTB;   // J symmetric: row i = column i
-                for (int mm = m; mm < kTB / 4; ++mm) {
-                  const int ip = 4 * mm + ql;
-                  if (ip > i) myf[mm * kThreads] = __fadd_rn(myf[mm * kThreads], sgn * Jrow[ip]);
+                const float *Jrow = Jblk + i * kTB;     // J symmetric: row i = column i
+#pragma unroll
+                for (int q2 = qq; q2 < 4; ++q2) {
+                  const int jj = 32 * q2 + lane;
+                  if (jj > i) f[q2] = __fadd_rn(f[q2], sgn * Jrow[jj]);
                 }
+                from = li == 31 ? 0u : (0xffffffffu << (li + 1));
               }
             }
           }
-          if (f0 | f1 | f2 | f3) {
-            if (ql == 0) {
-              mybits[0] = w0;
-              mybits[1] = w1;
-              mybits[2] = w2;
-              mybits[3] = w3;
+          if (nfl) {
+            if (lane == 0) {
+#pragma unroll
+              for (int qq = 0; qq < 4; ++qq) mybits[qq] = wq[qq];
             }
             __nv_bfloat16 *row = A.S + (size_t)rr * n + b0;
-            for (int m = 0; m < kTB / 4; ++m) {
-              const int i = 4 * m + ql;
-              const uint32_t fw = i < 64 ? (i < 32 ? f0 : f1) : (i < 96 ? f2 : f3);
-              if ((fw >> (i & 31)) & 1u) row[i] = __float2bfloat16_rn(bit(i) ? 1.0f : -1.0f);
-            }
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq)
+              if ((fl[qq] >> lane) & 1u) row[32 * qq + lane] = __float2bfloat16_rn(((wq[qq] >> lane) & 1u) ? 1.0f : -1.0f);
           }
-          nfl += __shfl_xor_sync(0xffffffffu, nfl, 1);
-          nfl += __shfl_xor_sync(0xffffffffu, nfl, 2);
-          if (ql == 0) s_nfl[rl] = act ? nfl : 0;
+          if (lane == 0) s_nfl[warp] = act ? nfl : 0;
         }
       }
       __syncthreads();
@@ -375,7 +364,12 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
       __syncthreads();
       tc::cluster_sync();  // new spins visible to every CTA's next TMA loads
     }
-    // ---- end of sweep / energy pass: per-replica bookkeeping (warp 0)
+    // ---- end of sweep / energy pass: per-replica bookkeeping (warp 0); best
+    // copies and new starts are then written by the replica's own warp
+    if (warp == 0) {
+      s_cpy[lane] = 0;
+      s_rst[lane] = -1;
+    }
     if (warp == 0 && my_r < A.R && !failed) {
       if (energy_pass) {
         const double E = -0.5 * st.E;
@@ -386,8 +380,7 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
             ++c_minima;
             if (E < st.best) {
               st.best = E;
-              const __nv_bfloat16 *row = A.S + (size_t)my_r * n;
-              for (int i = 0; i < n; ++i) A.best[(size_t)my_r * n + i] = __bfloat162float(row[i]) > 0.0f ? 1 : -1;
+              s_cpy[lane] = 1;
             }
           }
           st.conv = 0;
@@ -395,7 +388,7 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
           if (st.k < A.restarts && (A.budget <= 0 || st.total < A.budget)) {
             st.active = 1;
             st.d = 0;
-            write_start(A, my_r, st.k, sbits + lane * nw32);
+            s_rst[lane] = st.k;
             ++c_desc;
           } else {
             st.done = 1;
@@ -413,6 +406,16 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
           st.conv = conv ? 1 : 0;
         }
       }
+    }
+    __syncthreads();
+    if (energy_pass && rq + warp < A.R && !failed) {
+      const int rr = rq + warp;
+      if (s_cpy[warp]) {
+        const __nv_bfloat16 *row = A.S + (size_t)rr * n;
+        for (int i = lane; i < n; i += 32) A.best[(size_t)rr * n + i] = __bfloat162float(row[i]) > 0.0f ? 1 : -1;
+      }
+      __syncwarp();
+      if (s_rst[warp] >= 0) write_start_warp(A, rr, s_rst[warp], sbits + warp * nw32, lane);
     }
     tc::fence_proxy_async_global();
     __syncthreads();
@@ -435,11 +438,17 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
   }
 
   // results
+  if (warp == 0) s_cpy[lane] = (my_r < A.R && st.minima > 0) ? 1 : 0;
+  __syncthreads();
+  if (rq + warp < A.R) {
+    const int rr = rq + warp;
+    const bool hb = s_cpy[warp] != 0;
+    const __nv_bfloat16 *row = A.S + (size_t)rr * n;
+    for (int i = lane; i < n; i += 32)
+      A.out[(size_t)rr * n + i] = hb ? A.best[(size_t)rr * n + i] : (__bfloat162float(row[i]) > 0.0f ? 1 : -1);
+  }
   if (warp == 0 && my_r < A.R) {
     const bool hb = st.minima > 0;
-    const __nv_bfloat16 *row = A.S + (size_t)my_r * n;
-    for (int i = 0; i < n; ++i)
-      A.out[(size_t)my_r * n + i] = hb ? A.best[(size_t)my_r * n + i] : (__bfloat162float(row[i]) > 0.0f ? 1 : -1);
     A.E[my_r] = hb ? st.best : st.E;
     if (A.minima) A.minima[my_r] = st.minima;
     atomicAdd(A.stats + 0, c_evals);
