@@ -359,7 +359,9 @@ int msc_cluster_size(const ising_handle *h, int32_t R, const ising_search_params
   if (!h->msc_ok || !h->all_lattice || !h->lat_parity || p->schedule != ISING_SCHED_COLOUR) return 0;
   if (getenv("ISING_NO_CLUSTER")) return 0;
   const int64_t tiles = (int64_t)h->n_inst * ((R + 31) / 32);
-  for (int P : {4, 2}) {
+  const char *force = getenv("ISING_CLUSTER_P");  // diagnostics: restrict to one cluster size
+  for (int P : {8, 4, 2}) {
+    if (force && atoi(force) != P) continue;
     if (tiles * P > 2 * (int64_t)h->sm_count) continue;
     bool ok = true;
     int d = -1;
@@ -369,6 +371,13 @@ int msc_cluster_size(const ising_handle *h, int32_t R, const ising_search_params
       if (d >= 0 && I.lat_d != d) ok = false;
       d = I.lat_d;
     }
+    // Clusters of 8 (256-thread CTAs) only when every CTA gets an SM of its own
+    // and all clusters are resident at once: few replica groups, each spread
+    // wider.  With more groups, 4-CTA clusters of 512 threads measured faster.
+    if (ok && P == 8 &&
+        (tiles * P > (int64_t)h->sm_count ||
+         msc_cluster_max_active(const_cast<ising_handle *>(h), (int)tiles, P, h->nmax / P, d) < tiles))
+      ok = false;
     if (ok) return P;
   }
   return 0;
@@ -823,17 +832,19 @@ ising_status ising_local_search(ising_handle *h, const uint64_t *seeds, int32_t 
     }
   } while (0);
   if (st == ISING_OK && stats) {
-    if (cudaMemcpyAsync(h->h_stats_pinned, h->d_stats, sizeof(unsigned long long) * 5, cudaMemcpyDeviceToHost,
+    if (cudaMemcpyAsync(h->h_stats_pinned, h->d_stats, sizeof(unsigned long long) * 7, cudaMemcpyDeviceToHost,
                         stream) != cudaSuccess ||
         cudaStreamSynchronize(stream) != cudaSuccess) {
       st = ISING_ERR_CUDA;
+    } else if (h->h_stats_pinned[6]) {
+      st = ISING_ERR_TIMEOUT;  // a device-side sweep loop reached its bound
     } else {
       stats->flip_evals = h->h_stats_pinned[0];
       stats->flips = h->h_stats_pinned[1];
       stats->minima = h->h_stats_pinned[2];
       stats->descents = h->h_stats_pinned[3];
       stats->sweeps = h->h_stats_pinned[4];
-      stats->launches = h->launches;
+      stats->launches = h->launches + h->h_stats_pinned[5];  // host launches + kernels of device-side loops
     }
   }
   if (cur != h->device) cudaSetDevice(cur);

@@ -166,4 +166,5 @@ cudaError_t launch_energy(ising_handle *h, const int8_t *spins, int32_t R, doubl
 void energy_plan_free(ising_handle *h);
 size_t msc_cluster_smem(int csz);
 cudaError_t launch_msc_cluster(ising_handle *h, int n_tiles, int P, int csz_max, int D, cudaStream_t s);
+int msc_cluster_max_active(ising_handle *h, int n_tiles, int P, int csz_max, int D);
 }  // namespace isg

@@ -30,14 +30,15 @@ namespace isg {
 
 namespace {
 
-constexpr int kCT = 512;
+// CTA sizes: 512 threads (one CTA per SM) for clusters of 2 or 4 CTAs, 256
+// threads (two CTAs per SM) for clusters of 8
 
 __device__ __forceinline__ void st_cluster_u32(uint32_t addr, uint32_t v) {
   asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
 
-template <int D>
-__global__ void __launch_bounds__(kCT, 1) msc_cluster_kernel(const TileArgs *__restrict__ Aptr, int P) {
+template <int D, int NT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) msc_cluster_kernel(const TileArgs *__restrict__ Aptr, int P) {
   extern __shared__ uint32_t smem[];
   __shared__ uint32_t s_any[2], s_active, s_convround, s_upd;
   __shared__ int32_t s_total[32], s_minima[32];
@@ -361,7 +362,7 @@ __global__ void __launch_bounds__(kCT, 1) msc_cluster_kernel(const TileArgs *__r
     atomicAdd(A.stats + 3, my_desc);
     atomicAdd(A.stats + 4, my_sweeps);
   }
-  __shared__ unsigned long long s_fl[kCT / 32];
+  __shared__ unsigned long long s_fl[NT / 32];
   my_flips = block_sum(my_flips, s_fl);
   if (tid == 0) atomicAdd(A.stats + 1, my_flips);
   tc::cluster_sync();  // no CTA leaves while peers may still read its shared memory
@@ -371,11 +372,22 @@ __global__ void __launch_bounds__(kCT, 1) msc_cluster_kernel(const TileArgs *__r
 
 size_t msc_cluster_smem(int csz) { return (size_t)csz * 4 + (size_t)(csz / 64) * 2 * 4 + (size_t)csz; }
 
-cudaError_t launch_msc_cluster(ising_handle *h, int n_tiles, int P, int csz_max, int D, cudaStream_t s) {
+template <int D, int NT>
+cudaError_t launch_cfg(cudaLaunchConfig_t &cfg, const TileArgs *args, int P, size_t smem, int *max_active) {
+  cudaError_t e = cudaFuncSetAttribute(msc_cluster_kernel<D, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (max_active) return cudaOccupancyMaxActiveClusters(max_active, msc_cluster_kernel<D, NT>, &cfg);
+  return cudaLaunchKernelEx(&cfg, msc_cluster_kernel<D, NT>, args, P);
+}
+
+// Launch (max_active == nullptr) or report how many clusters can be resident at once.
+cudaError_t msc_cluster_launch_or_query(ising_handle *h, int n_tiles, int P, int csz_max, int D, cudaStream_t s,
+                                        int *max_active) {
   const size_t smem = msc_cluster_smem(csz_max);
+  const int nt = P == 8 ? 256 : 512;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(n_tiles * P);
-  cfg.blockDim = dim3(kCT);
+  cfg.blockDim = dim3(nt);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -385,15 +397,22 @@ cudaError_t launch_msc_cluster(ising_handle *h, int n_tiles, int P, int csz_max,
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e;
-  if (D == 3) {
-    e = cudaFuncSetAttribute(msc_cluster_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, msc_cluster_kernel<3>, (const TileArgs *)h->d_tile_args, P);
-  } else {
-    e = cudaFuncSetAttribute(msc_cluster_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, msc_cluster_kernel<2>, (const TileArgs *)h->d_tile_args, P);
+  const TileArgs *args = (const TileArgs *)h->d_tile_args;
+  if (D == 3) return nt == 256 ? launch_cfg<3, 256>(cfg, args, P, smem, max_active) : launch_cfg<3, 512>(cfg, args, P, smem, max_active);
+  return nt == 256 ? launch_cfg<2, 256>(cfg, args, P, smem, max_active) : launch_cfg<2, 512>(cfg, args, P, smem, max_active);
+}
+
+cudaError_t launch_msc_cluster(ising_handle *h, int n_tiles, int P, int csz_max, int D, cudaStream_t s) {
+  return msc_cluster_launch_or_query(h, n_tiles, P, csz_max, D, s, nullptr);
+}
+
+int msc_cluster_max_active(ising_handle *h, int n_tiles, int P, int csz_max, int D) {
+  int m = 0;
+  if (msc_cluster_launch_or_query(h, n_tiles, P, csz_max, D, nullptr, &m) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
   }
-  return e;
+  return m;
 }
 
 }  // namespace isg

@@ -18,6 +18,8 @@
 #include <cfloat>
 #include <cstdio>
 #include <cstdlib>
+#include <map>
+#include <string>
 
 #include "device_common.cuh"
 
@@ -48,6 +50,7 @@ struct SweepArgs {
   int32_t grid_e;
   unsigned int *counter;
   int32_t *all_done;
+  unsigned long long *iters;  // sweeps run by the device-side loop
   unsigned long long *stats;
   int8_t *spins;
   double *energy;
@@ -97,6 +100,7 @@ __global__ void sweep_init(SweepArgs A) {
   if (threadIdx.x == 0) {
     *A.counter = 0;
     *A.all_done = 0;
+    *A.iters = 0;
   }
 }
 
@@ -692,32 +696,52 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
 }
 
 // End of a sweep: per group, which lanes converged, which descents ended.
-__global__ void sweep_end(SweepArgs A) {
+// Inside the device-side loop (cond != 0) it also sets the loop condition `hw`
+// to 0 once every group is done or after `bound` sweeps (then stats[6] = 1
+// reports that the bound was hit), and counts the loop's kernels in stats[5].
+__global__ void sweep_end(SweepArgs A, cudaGraphConditionalHandle hw, int cond, long long bound, int nvis) {
+  __shared__ int s_done;
   const int g = threadIdx.x;
-  if (g >= A.G) return;
-  GroupState &S = A.gs[g];
-  S.start = 0;
-  S.upd = 0;
-  const uint32_t active = S.active;
-  if (!active) return;
-  const uint32_t any = S.any;
-  S.any = 0;
-  uint32_t ended = 0;
-  for (int r = 0; r < 32; ++r)
-    if ((active >> r) & 1u) {
-      S.total[r] += 1;
-      if (A.budget > 0 && S.total[r] >= A.budget) ended |= 1u << r;
+  if (g == 0) s_done = 1;
+  __syncthreads();
+  if (g < A.G) {
+    GroupState &S = A.gs[g];
+    S.start = 0;
+    S.upd = 0;
+    const uint32_t active = S.active;
+    if (active) {
+      const uint32_t any = S.any;
+      S.any = 0;
+      uint32_t ended = 0;
+      for (int r = 0; r < 32; ++r)
+        if ((active >> r) & 1u) {
+          S.total[r] += 1;
+          if (A.budget > 0 && S.total[r] >= A.budget) ended |= 1u << r;
+        }
+      const uint32_t conv = active & ~any;
+      ended |= conv;
+      S.d += 1;
+      if (S.d >= A.max_sweeps) ended |= active;
+      atomicAdd(A.stats + 4, (unsigned long long)__popc(active));
+      atomicAdd(A.stats + 0, (unsigned long long)__popc(active) * (unsigned long long)A.I.n);
+      atomicAdd(A.stats + 2, (unsigned long long)__popc(conv));
+      S.convround |= conv;
+      S.active = active & ~ended;
+      if (!S.active) S.round_end = 1;
     }
-  const uint32_t conv = active & ~any;
-  ended |= conv;
-  S.d += 1;
-  if (S.d >= A.max_sweeps) ended |= active;
-  atomicAdd(A.stats + 4, (unsigned long long)__popc(active));
-  atomicAdd(A.stats + 0, (unsigned long long)__popc(active) * (unsigned long long)A.I.n);
-  atomicAdd(A.stats + 2, (unsigned long long)__popc(conv));
-  S.convround |= conv;
-  S.active = active & ~ended;
-  if (!S.active) S.round_end = 1;
+    if (!S.done) atomicAnd(&s_done, 0);
+  }
+  __syncthreads();
+  if (cond && g == 0) {
+    atomicAdd(A.stats + 5, (unsigned long long)(nvis + 3));  // kernels of this sweep
+    const unsigned long long it = ++*A.iters;
+    bool stop = s_done != 0;
+    if ((long long)it > bound) {
+      stop = true;
+      A.stats[6] = 1ull;
+    }
+    if (stop) cudaGraphSetConditional(hw, 0u);
+  }
 }
 
 // Energies of the lanes whose round ended (all lanes of the group at once,
@@ -1105,11 +1129,17 @@ __global__ void sweep_output(SweepArgs A) {
   }
 }
 
+struct SweepGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
 struct SweepState {
   size_t bytes = 0;
   void *mem = nullptr;
   int32_t *h_done = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
+  std::map<std::string, SweepGraph> graphs;  // instantiated device-side loops by configuration
 };
 
 std::map<const ising_handle *, SweepState> &sweep_states() {
@@ -1146,19 +1176,41 @@ void enqueue_visit(const SweepArgs &A, int c, int grid, cudaStream_t s) {
 }
 
 template <int LPS, bool LAT>
+void enqueue_round_end(const SweepArgs &A, int mode, cudaStream_t s) {
+  if (mode == 1) sweep_energy<true, LPS, LAT><<<A.grid_e, kST, 0, s>>>(A);
+  else sweep_energy<false, LPS, LAT><<<A.grid_e, kST, 0, s>>>(A);
+  debug_step("energy", 0, s);
+  sweep_restart<LPS><<<A.grid_e, kST, 0, s>>>(A);
+  debug_step("restart", 0, s);
+}
+
+template <int LPS, bool LAT>
 void enqueue_sweep(const SweepArgs &A, int mode, int ncls, int grid_v, cudaStream_t s) {
   for (int c = 0; c < ncls; ++c) {
     if (mode == 0) enqueue_visit<0, LPS, LAT>(A, c, grid_v, s);
     else if (mode == 1) enqueue_visit<1, LPS, LAT>(A, c, grid_v, s);
     else enqueue_visit<2, LPS, LAT>(A, c, grid_v, s);
   }
-  sweep_end<<<1, 32, 0, s>>>(A);
+  sweep_end<<<1, 32, 0, s>>>(A, 0, 0, 0, 0);
   debug_step("end", 0, s);
-  if (mode == 1) sweep_energy<true, LPS, LAT><<<A.grid_e, kST, 0, s>>>(A);
-  else sweep_energy<false, LPS, LAT><<<A.grid_e, kST, 0, s>>>(A);
-  debug_step("energy", 0, s);
-  sweep_restart<LPS><<<A.grid_e, kST, 0, s>>>(A);
-  debug_step("restart", 0, s);
+  enqueue_round_end<LPS, LAT>(A, mode, s);
+}
+
+// One sweep inside the device-side loop: the class visits, the end-of-sweep
+// bookkeeping (which clears the loop condition once every group is done), the
+// energy pass and the restarts (both return at once when no round ended).
+// Measured on GB300, an IF node around the last two cost more per sweep than the
+// two early-returning launches it saves.
+template <int LPS, bool LAT>
+void capture_sweep(const SweepArgs &A, int mode, int ncls, int grid_v, cudaStream_t s,
+                   cudaGraphConditionalHandle hw, long long bound) {
+  for (int c = 0; c < ncls; ++c) {
+    if (mode == 0) enqueue_visit<0, LPS, LAT>(A, c, grid_v, s);
+    else if (mode == 1) enqueue_visit<1, LPS, LAT>(A, c, grid_v, s);
+    else enqueue_visit<2, LPS, LAT>(A, c, grid_v, s);
+  }
+  sweep_end<<<1, 32, 0, s>>>(A, hw, 1, bound, ncls);
+  enqueue_round_end<LPS, LAT>(A, mode, s);
 }
 
 // Load every kernel of this configuration before any graph capture, so the
@@ -1205,63 +1257,83 @@ cudaError_t run_instance(ising_handle *h, SweepArgs A, int mode, cudaStream_t s)
   debug_step("restart0", 0, s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  // Capture a chunk of sweeps once and replay it until every group is done.
-  // A graph holds at most kMaxNodes launches; when one sweep alone needs more
-  // (many colour classes, e.g. the sequential schedule) sweeps are launched
-  // directly instead.
+  // upper bound on the sweeps any group can need
+  int64_t max_sweeps_total = (int64_t)A.restarts * A.max_sweeps + A.restarts;
+  if (A.budget > 0) max_sweeps_total = std::min<int64_t>(max_sweeps_total, (int64_t)A.R * A.budget + A.max_sweeps);
+  // After one sweep of direct launches, the sweeps run as a device-side loop: a
+  // CUDA graph whose WHILE node replays a chunk of sweeps until sweep_end finds
+  // every group done (or the bound above is reached), each sweep's energy pass
+  // and restarts behind an IF node.  No host polling; the call stays
+  // asynchronous.  A graph holds at most kMaxNodes launches per chunk; when one
+  // sweep alone needs more (many colour classes, e.g. the sequential schedule)
+  // chunks of direct launches are polled from the host instead.
   constexpr int kMaxNodes = 512;
   const int per_sweep = ncls + 3;
   const bool use_graph = per_sweep <= kMaxNodes && !sweep_debug();
   const int chunk = use_graph ? std::max(1, std::min(16, kMaxNodes / per_sweep)) : 1;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  cudaStream_t cs = nullptr;
-  // the first sweep runs with direct launches, the rest from the graph
   enqueue_sweep<LPS, LAT>(A, mode, ncls, grid_v, s);
   h->launches += per_sweep;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (use_graph) {
-    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return e;
-    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-      for (int k = 0; k < chunk; ++k) enqueue_sweep<LPS, LAT>(A, mode, ncls, grid_v, cs);
-      e = cudaStreamEndCapture(cs, &graph);
+    std::string key(reinterpret_cast<const char *>(&A), sizeof(A));
+    key += std::to_string(mode) + "/" + std::to_string(grid_v) + "/" + std::to_string(chunk);
+    auto it = S.graphs.find(key);
+    if (it == S.graphs.end()) {
+      SweepGraph sg;
+      cudaStream_t cs = nullptr;
+      cudaGraphConditionalHandle hw;
+      cudaGraphNodeParams wp = {};
+      cudaGraphNode_t wn;
+      e = cudaGraphCreate(&sg.graph, 0);
+      if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hw, sg.graph, 1, cudaGraphCondAssignDefault);
+      if (e == cudaSuccess) {
+        wp.type = cudaGraphNodeTypeConditional;
+        wp.conditional.handle = hw;
+        wp.conditional.type = cudaGraphCondTypeWhile;
+        wp.conditional.size = 1;
+        e = cudaGraphAddNode(&wn, sg.graph, nullptr, nullptr, 0, &wp);
+      }
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+      if (e == cudaSuccess)
+        e = cudaStreamBeginCaptureToGraph(cs, wp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        const long long bound = (long long)max_sweeps_total + 2 * chunk + 2;
+        for (int k = 0; k < chunk; ++k) capture_sweep<LPS, LAT>(A, mode, ncls, grid_v, cs, hw, bound);
+        e = cudaGetLastError();
+        cudaGraph_t body = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &body);
+        if (e == cudaSuccess) e = e2;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&sg.exec, sg.graph, 0);
+      if (cs) cudaStreamDestroy(cs);
+      if (e != cudaSuccess) {
+        if (sg.graph) cudaGraphDestroy(sg.graph);
+        cudaGetLastError();
+        return e;
+      }
+      it = S.graphs.emplace(key, sg).first;
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-    if (e != cudaSuccess) {
-      if (graph) cudaGraphDestroy(graph);
-      cudaStreamDestroy(cs);
-      return e;
-    }
-  }
-  // upper bound on the sweeps any group can need
-  int64_t max_sweeps_total = (int64_t)A.restarts * A.max_sweeps + A.restarts;
-  if (A.budget > 0) max_sweeps_total = std::min<int64_t>(max_sweeps_total, (int64_t)A.R * A.budget + A.max_sweeps);
-  const int64_t max_chunks = max_sweeps_total / chunk + 2;
-  int64_t launched = 0;
-  for (;;) {
-    h->launches += (uint64_t)chunk * per_sweep;
-    if (use_graph) {
-      if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) break;
-    } else {
+    // kernels run inside the loop are counted on the device (stats slot 5)
+    e = cudaGraphLaunch(it->second.exec, s);
+  } else {
+    const int64_t max_chunks = max_sweeps_total + 2;
+    int64_t launched = 0;
+    for (;;) {
+      h->launches += per_sweep;
       enqueue_sweep<LPS, LAT>(A, mode, ncls, grid_v, s);
       if ((e = cudaGetLastError()) != cudaSuccess) break;
+      cudaMemcpyAsync(S.h_done + (launched & 1), A.all_done, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+      cudaEventRecord(S.ev[launched & 1], s);
+      ++launched;
+      if (sweep_debug()) std::fprintf(stderr, "[sweep] chunk %lld queued\n", (long long)launched);
+      if (launched >= 2) {
+        // look one chunk behind so the GPU always has queued work
+        cudaEventSynchronize(S.ev[launched & 1]);
+        if (S.h_done[launched & 1]) break;
+      }
+      if (launched >= max_chunks) break;
     }
-    cudaMemcpyAsync(S.h_done + (launched & 1), A.all_done, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-    cudaEventRecord(S.ev[launched & 1], s);
-    ++launched;
-    if (sweep_debug()) std::fprintf(stderr, "[sweep] chunk %lld queued\n", (long long)launched);
-    if (launched >= 2) {
-      // look one chunk behind so the GPU always has queued work
-      cudaEventSynchronize(S.ev[launched & 1]);
-      if (S.h_done[launched & 1]) break;
-    }
-    if (launched >= max_chunks) break;
-  }
-  if (use_graph) {
-    cudaGraphExecDestroy(exec);
-    cudaGraphDestroy(graph);
-    cudaStreamDestroy(cs);
   }
   if (e != cudaSuccess) return e;
   // energies of the final states of replicas that never converged
@@ -1280,6 +1352,10 @@ void sweep_free(ising_handle *h) {
   auto &m = sweep_states();
   auto it = m.find(h);
   if (it == m.end()) return;
+  for (auto &kv : it->second.graphs) {
+    cudaGraphExecDestroy(kv.second.exec);
+    cudaGraphDestroy(kv.second.graph);
+  }
   cudaFree(it->second.mem);
   if (it->second.h_done) cudaFreeHost(it->second.h_done);
   for (auto &e : it->second.ev)
@@ -1300,7 +1376,7 @@ cudaError_t launch_sweep(ising_handle *h, const ising_search_params *p, int32_t 
   const size_t words = (size_t)G * h->nmax;
   auto up256 = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t need = 4 * up256(words * 4) + (fl ? up256(words * LPS * 4) : 0) + up256(G * sizeof(GroupState)) +
-                      up256((size_t)grid_e * G * 32 * 16) + 2 * 256;
+                      up256((size_t)grid_e * G * 32 * 16) + 3 * 256;
   cudaError_t e;
   if (need > S.bytes) {
     cudaFree(S.mem);
@@ -1338,6 +1414,7 @@ cudaError_t launch_sweep(ising_handle *h, const ising_search_params *p, int32_t 
   A.partial = (double *)take((size_t)grid_e * G * 32 * 16);  // FP64 sums, or fixed-point high | low halves
   A.counter = (unsigned int *)take(64);
   A.all_done = (int32_t *)take(64);
+  A.iters = (unsigned long long *)take(64);
   A.stats = h->d_stats;
   A.spins = spins;
   A.energy = E;
