@@ -367,73 +367,70 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
             __syncwarp();  // staging read before the next batch overwrites it
             continue;
           }
-          // refresh sweep: every pair of every position
-          uint32_t wj1 = 0u, sn1[6];
-          float jw1[6], hj1 = 0.0f;
-#pragma unroll
-          for (int kk = 0; kk < 6; ++kk) {
-            sn1[kk] = 0u;
-            jw1[kk] = 0.0f;
-          }
+          // refresh sweep: every pair of every position.  The position lane forms
+          // the site's terms once - fixed-point integers when the sum is exact,
+          // else the FP32 values for the FP64 path - and stages them with the
+          // neighbour words; the per-replica steps read shared memory only.
+          uint32_t *sW = wsm;                                        // [32] words
+          uint32_t *sN = wsm + 32;                                   // [6][32] neighbour words
+          int64_t *sT = reinterpret_cast<int64_t *>(wsm + 224);      // [7][32] terms (kk 0..5, field)
+          int32_t *sU = reinterpret_cast<int32_t *>(wsm + 672);      // [32] unit exponent, -1: FP64 path
           if (need1) {
-            wj1 = swg[j1];
+            sW[lane] = swg[j1];
+            const float hj = __ldg(hf + j1);
+            float jw[6];
+            XRange xr;
+            xr_see(xr, hj);
+#pragma unroll
+            for (int kk = 0; kk < 6; ++kk) {
+              jw[kk] = 0.0f;
+              if (kk < D2) {
+                sN[kk * 32 + lane] = swg[nb_of(j1, meta1, kk)];
+                jw[kk] = __ldg(Jp0 + (int64_t)kk * G.nsp + v1);
+                xr_see(xr, jw[kk]);
+              }
+            }
+            const bool ex = xr_exact(xr);
+            const int u = xr.emax < 0 ? 24 : xr.emin;
+            sU[lane] = ex ? u : -1;
+            sT[6 * 32 + lane] = ex ? xr_term(hj, u) : (int64_t)__float_as_uint(hj);
 #pragma unroll
             for (int kk = 0; kk < 6; ++kk)
-              if (kk < D2) {
-                sn1[kk] = swg[nb_of(j1, meta1, kk)];
-                jw1[kk] = __ldg(Jp0 + (int64_t)kk * G.nsp + v1);
-              }
-            hj1 = __ldg(hf + j1);
+              if (kk < D2) sT[kk * 32 + lane] = ex ? xr_term(jw[kk], u) : (int64_t)__float_as_uint(jw[kk]);
           }
+          __syncwarp();
           while (todo) {
             uint32_t t = todo;
             for (int q = 0; q < sub; ++q) t &= t - 1u;
             const int src = t ? __ffs(t) - 1 : 31;
             const bool valid = t != 0u;
             for (int q = 0; q < SPW; ++q) todo &= todo - 1u;
-            const int v = __shfl_sync(0xffffffffu, v1, src);
-            const int j = __shfl_sync(0xffffffffu, j1, src);
-            const uint32_t meta = __shfl_sync(0xffffffffu, meta1, src);
-            const uint32_t wj = __shfl_sync(0xffffffffu, wj1, src);
-            const uint32_t fmj = __shfl_sync(0xffffffffu, fm1, src);
-            uint32_t sn[6];
-            float jw[6];
-#pragma unroll
-            for (int kk = 0; kk < 6; ++kk) {
-              sn[kk] = 0u;
-              jw[kk] = 0.0f;
-              if (kk < D2) {
-                sn[kk] = __shfl_sync(0xffffffffu, sn1[kk], src);
-                jw[kk] = __shfl_sync(0xffffffffu, jw1[kk], src);
-              }
-            }
-            const float hj = __shfl_sync(0xffffffffu, hj1, src);
+            const int v = c0 + base + src;
+            const uint32_t wj = sW[src];
             const bool up = (wj >> ln) & 1u;
             bool flip = false;
             if (valid) {
-              // from scratch: the FP64 sum rounded to FP32, formed exactly in
-              // fixed point when the exponent range allows it
+              // from scratch: the FP64 sum rounded to FP32 (exact fixed point when
+              // the exponent range allows it, else FP64)
               float f;
-              XRange xr;
-              xr_see(xr, hj);
-#pragma unroll
-              for (int kk = 0; kk < 6; ++kk)
-                if (kk < D2) xr_see(xr, jw[kk]);
-              if (xr_exact(xr)) {
-                const int u = xr.emax < 0 ? 24 : xr.emin;
-                int64_t acc = xr_term(hj, u);
+              const int u = sU[src];
+              if (u >= 0) {
+                int64_t acc = sT[6 * 32 + src];
 #pragma unroll
                 for (int kk = 0; kk < 6; ++kk)
                   if (kk < D2) {
-                    const int64_t tt = xr_term(jw[kk], u);
-                    acc += ((sn[kk] >> ln) & 1u) ? tt : -tt;
+                    const int64_t tt = sT[kk * 32 + src];
+                    acc += ((sN[kk * 32 + src] >> ln) & 1u) ? tt : -tt;
                   }
                 f = xr_round(acc, u);
               } else {
-                double acc = (double)hj;
+                double acc = (double)__uint_as_float((uint32_t)sT[6 * 32 + src]);
 #pragma unroll
                 for (int kk = 0; kk < 6; ++kk)
-                  if (kk < D2) acc = __dadd_rn(acc, ((sn[kk] >> ln) & 1u) ? (double)jw[kk] : -(double)jw[kk]);
+                  if (kk < D2) {
+                    const double w = (double)__uint_as_float((uint32_t)sT[kk * 32 + src]);
+                    acc = __dadd_rn(acc, ((sN[kk * 32 + src] >> ln) & 1u) ? w : -w);
+                  }
                 f = __double2float_rn(acc);
               }
               Fg[(size_t)v * LPS + ln] = f;
@@ -442,15 +439,18 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
             const uint32_t m = __ballot_sync(0xffffffffu, flip);
             const uint32_t seg = (m >> (sub * LPS)) & lmask;
             if (valid && ln == 0) {
+              const int j = __ldg(G.order + so + v);
+              const uint32_t meta = __ldg(G.meta + so + v);
               if (seg) {
                 swg[j] = wj ^ seg;
                 for (int kk = 0; kk < D2; ++kk) atomicOr(&pendg[nb_of(j, meta, kk)], seg);
               }
-              if (seg || fmj) fmg[j] = seg;
+              if (seg || fmg[j]) fmg[j] = seg;
             }
             anyg |= seg;
             my_flips += flip ? 1 : 0;
           }
+          __syncwarp();  // staging read before the next batch overwrites it
         }
       } else
       for (int base = wid * 32; base < cs; base += nwarps * 32) {
