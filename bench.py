@@ -22,6 +22,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -78,7 +79,9 @@ class ClockSampler:
 
     def __init__(self, gpu_index: int):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples (summarised into the JSON line); ISING_BENCH_CLOCKS_DIR keeps them
+        self.path = os.path.join(os.environ.get("ISING_BENCH_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"clocks_{os.getpid()}.csv")
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
@@ -322,8 +325,15 @@ def main():
             b.record(stream)
             torch.cuda.synchronize()
             pms = a.elapsed_time(b)
-            same = bool(torch.equal(pr.energy, E)) if insts[0].dtype == "i8" else float(
-                (pr.energy - E).abs().max().item())
+            if insts[0].dtype == "i8":
+                same = bool(torch.equal(pr.energy, E))  # integer couplings: identical results
+            else:
+                # float couplings: the comparator's rounding differs where its field
+                # arithmetic does; report how the energies reached compare
+                m1, m2 = float(E.mean().item()), float(pr.energy.mean().item())
+                same = {"max_abs_diff": float((pr.energy - E).abs().max().item()), "mean_energy": m1,
+                        "comparator_mean_energy": m2, "rel_mean_diff": abs(m1 - m2) / max(abs(m2), 1e-300),
+                        "identical_replicas": float((pr.energy == E).double().mean().item())}
             plain = {"kind": "cublas_blocked" if chosen == isg.KERNEL_DENSE_TC else "plain",
                      "value": pr.stats["flip_evals"] / (pms / 1e3), "unit": UNIT, "ms_per_step": pms,
                      "energy_match": same, "speedup": value / (pr.stats["flip_evals"] / (pms / 1e3))}
@@ -367,9 +377,9 @@ def main():
 
 def roofline(name, kernel, insts, R, st, step_s, clk, hbm, bf16s, src):
     """Roofline of the step's dominant kernel.  The algorithmic work per unit is
-    the method's own (not the kernel's instruction count); the design doc derives each
-    figure.  The time is the whole step measured with CUDA events, so `achieved`
-    is a lower bound for the dominant kernel alone."""
+    the method's own (not the kernel's instruction count).  The time is the whole
+    step measured with CUDA events, so `achieved` is a lower bound for the
+    dominant kernel alone."""
     sm_count = 152
     mhz = (clk or {}).get("sm_mhz") or 2070.0
     inst = insts[0]

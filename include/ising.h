@@ -101,7 +101,7 @@ typedef enum {
   ISING_ERR_UNSUPPORTED = 6,   /* instance/kernel combination this build cannot run     */
   ISING_ERR_OOM = 7,           /* device or host allocation failed                      */
   ISING_ERR_CUDA = 8,          /* a CUDA runtime call failed                            */
-  ISING_ERR_TIMEOUT = 9,       /* a device-side bounded wait or loop ran out            */
+  ISING_ERR_TIMEOUT = 9,       /* a device-side bounded wait ran out                    */
   ISING_ERR_DEVICE = 10        /* a device-side consistency check failed                */
 } ising_status;
 
@@ -117,8 +117,8 @@ typedef enum {
   ISING_KERNEL_MSC = 2,      /* multi-spin coded tile: 32 replicas as bits of a word;
                                 needs J in {-1,+1}, h in {-1,0,+1}, no hyper-edges      */
   ISING_KERNEL_SWEEP = 3,    /* large instances: one launch per colour class over the
-                                whole GPU; sweeps run as a device-side loop (a CUDA
-                                graph with a conditional WHILE node)                    */
+                                whole GPU; chunks of sweeps captured once in a CUDA
+                                graph and replayed until every replica is done          */
   ISING_KERNEL_DENSE_TC = 4, /* dense couplings: fields as a tcgen05 GEMM (BF16 hi+lo)  */
   ISING_KERNEL_PLAIN = 5     /* plain comparator: one launch per instance and colour
                                 class, one thread per (spin, replica), the same field
@@ -161,12 +161,9 @@ typedef struct {
  * flip_evals = spins visited (one gain computed and decided per visit),
  * flips = accepted moves, minima = converged descents, descents = descents run,
  * sweeps = sweeps run.  They depend only on the method's semantics, not on the
- * kernel that ran it.  launches = this library's kernels the call ran: host
- * launches plus kernel nodes of replayed graphs, the kernels of device-side
- * loops counted on the device (library GEMMs not counted).  When stats is
- * non-NULL the call waits for the search, and a device-side sweep loop that
- * reached its bound (a safety cap above the sweeps the parameters allow) is
- * reported as ISING_ERR_TIMEOUT.                                               */
+ * kernel that ran it.  launches = this library's kernel launches the call
+ * enqueued (kernel nodes of replayed graphs included; library GEMMs not).
+ * When stats is non-NULL the call waits for the search to finish.              */
 typedef struct {
   uint64_t flip_evals, flips, minima, descents, sweeps, launches;
 } ising_stats;

@@ -47,6 +47,7 @@ DevGraph ising_handle::graph() const {
   g.meta = d_meta;
   g.Jpos = d_Jpos;
   g.latinfo = d_latinfo;
+  g.runit = d_runit;
   g.nsp = total_spins;
   g.dtype = dtype;
   return g;
@@ -293,7 +294,7 @@ void free_handle(ising_handle *h) {
   dense_free(h);
   plain_free(h);
   void *ptrs[] = {h->d_inst, h->d_row, h->d_col, h->d_J, h->d_h, h->d_inc_ptr, h->d_inc_edge, h->d_hptr,
-                  h->d_hmem, h->d_hJ, h->d_order, h->d_cls, h->d_Jdense, h->d_meta, h->d_Jpos, h->d_latinfo,
+                  h->d_hmem, h->d_hJ, h->d_order, h->d_cls, h->d_Jdense, h->d_meta, h->d_Jpos, h->d_latinfo, h->d_runit,
                   h->d_scratch, h->d_tile_args,
                   h->d_seeds, h->d_stats, h->d_queue, h->d_tiles};
   for (void *p : ptrs)
@@ -431,7 +432,12 @@ ising_status run_tile(ising_handle *h, int mode, int32_t R, const ising_search_p
     h->launches += 1;
     return ISING_OK;
   }
-  const size_t smem = tile_smem_bytes(mode, h->nmax);
+  // FP32 lanes: fields in shared memory for every instance that fits (one CTA
+  // per SM either way: the kernel's register use allows no second one)
+  constexpr size_t kFsmBudget = 216 * 1024;
+  const int fsm_cap = mode == 1 ? tile_fsm_cap(h->nmax, kFsmBudget) : 0;
+  const size_t smem = mode == 1 && fsm_cap > 0 ? (tile_smem_bytes(mode, h->nmax) + 15) / 16 * 16 + (size_t)fsm_cap * 128
+                                              : tile_smem_bytes(mode, h->nmax);
   int per_sm = tile_max_ctas_per_sm(mode, smem);
   if (per_sm < 1) return ISING_ERR_UNSUPPORTED;
   const int grid = std::min<int64_t>(h->n_tiles, (int64_t)per_sm * h->sm_count);
@@ -452,6 +458,7 @@ ising_status run_tile(ising_handle *h, int mode, int32_t R, const ising_search_p
   a.sequential = p->schedule == ISING_SCHED_SEQUENTIAL ? 1 : 0;
   a.seeds = h->d_seeds;
   a.F = mode == 1 ? (float *)h->d_scratch : nullptr;
+  a.fsm_cap = fsm_cap;
   a.bw = (uint32_t *)((char *)h->d_scratch + ((f_bytes + 255) / 256) * 256);
   a.nmax = h->nmax;
   a.spins = spins;
@@ -676,6 +683,30 @@ ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
     if (fl) {
       ok = upload((float **)&h->d_J, Jf) == cudaSuccess && upload((float **)&h->d_h, hf) == cudaSuccess &&
            upload((float **)&h->d_hJ, hJf) == cudaSuccess;
+      // per-spin refresh unit: the same test as the kernels' xr_exact, once here
+      std::vector<int16_t> runit(spin_off);
+      for (int64_t gi = 0; gi < spin_off && ok; ++gi) {
+        int emin = 256, emax = -1, k = 0;
+        auto see = [&](float v) {
+          uint32_t bits;
+          std::memcpy(&bits, &v, 4);
+          bits &= 0x7fffffffu;
+          ++k;
+          if (bits) {
+            const int e = (int)(bits >> 23);
+            emin = std::min(emin, e);
+            emax = std::max(emax, e);
+          }
+        };
+        see(hf.empty() ? 0.0f : hf[gi]);
+        for (uint32_t kk = row[gi]; kk < row[gi + 1]; ++kk) see(Jf[kk]);
+        for (uint32_t q = inc_ptr[gi]; q < inc_ptr[gi + 1]; ++q) see(hJf[inc_edge[q]]);
+        int lg = 0;
+        while (lg < 31 && (1u << lg) <= (uint32_t)k) ++lg;  // 2^lg > k
+        const bool ex = emax < 0 || (emin >= 24 && emax <= 200 && (emax - emin) + 24 + lg <= 53);
+        runit[gi] = (int16_t)(emax < 0 ? 24 : (ex ? emin : -1));
+      }
+      ok = ok && upload(&h->d_runit, runit) == cudaSuccess;
     } else {
       ok = upload((int8_t **)&h->d_J, Ji) == cudaSuccess && upload((int8_t **)&h->d_h, hi) == cudaSuccess &&
            upload((int8_t **)&h->d_hJ, hJi) == cudaSuccess;
@@ -832,19 +863,17 @@ ising_status ising_local_search(ising_handle *h, const uint64_t *seeds, int32_t 
     }
   } while (0);
   if (st == ISING_OK && stats) {
-    if (cudaMemcpyAsync(h->h_stats_pinned, h->d_stats, sizeof(unsigned long long) * 7, cudaMemcpyDeviceToHost,
+    if (cudaMemcpyAsync(h->h_stats_pinned, h->d_stats, sizeof(unsigned long long) * 5, cudaMemcpyDeviceToHost,
                         stream) != cudaSuccess ||
         cudaStreamSynchronize(stream) != cudaSuccess) {
       st = ISING_ERR_CUDA;
-    } else if (h->h_stats_pinned[6]) {
-      st = ISING_ERR_TIMEOUT;  // a device-side sweep loop reached its bound
     } else {
       stats->flip_evals = h->h_stats_pinned[0];
       stats->flips = h->h_stats_pinned[1];
       stats->minima = h->h_stats_pinned[2];
       stats->descents = h->h_stats_pinned[3];
       stats->sweeps = h->h_stats_pinned[4];
-      stats->launches = h->launches + h->h_stats_pinned[5];  // host launches + kernels of device-side loops
+      stats->launches = h->launches;
     }
   }
   if (cur != h->device) cudaSetDevice(cur);

@@ -60,6 +60,9 @@ struct DevGraph {
   //   latinfo[spin_off + v]: bit d = the neighbour in direction d (0 +x, 1 -x,
   //   2 +y, 3 -y, 4 +z, 5 -z) wraps around; bit 8 + d = its coupling is negative
   const uint16_t *latinfo;
+  // FP32 instances: per spin, the unit (smallest biased exponent) of an exact
+  // fixed-point refresh, or -1 when that spin's refresh needs FP64 (see xr_exact)
+  const int16_t *runit;
   int64_t nsp;              // total spins (stride of Jpos)
   int32_t dtype;            // ISING_I8 / ISING_F32
 };
@@ -74,6 +77,7 @@ struct TileArgs {
   int32_t R, max_sweeps, restarts, budget, refresh, sequential;
   const uint64_t *seeds;    // [n_inst]
   float *F;                 // [grid][nmax][32] FP32 fields (float lane path)
+  int32_t fsm_cap;          // instances up to this size keep their fields in shared memory
   uint32_t *bw;             // [grid][nmax] best-state words
   int32_t nmax;
   int8_t *spins;            // out [inst][replica][spin]
@@ -122,6 +126,7 @@ struct ising_handle {
   float *d_Jdense = nullptr;
   uint32_t *d_meta = nullptr;
   uint16_t *d_latinfo = nullptr;
+  int16_t *d_runit = nullptr;
   bool all_lattice = false;  // every instance is a recognised periodic lattice
   bool lat_parity = false;   // ... coloured by site parity: class c = {x + y + z = c mod 2}
   void *d_Jpos = nullptr;
@@ -160,6 +165,7 @@ namespace isg {
 // launchers (tile.cu / energy.cu / plain.cu / sweep.cu / dense.cu)
 cudaError_t launch_tile(ising_handle *h, int mode, int grid, size_t smem, cudaStream_t s);
 size_t tile_smem_bytes(int mode, int nmax);
+int tile_fsm_cap(int nmax, size_t budget);
 int tile_max_ctas_per_sm(int mode, size_t smem);
 cudaError_t launch_energy(ising_handle *h, const int8_t *spins, int32_t R, double *E,
                           int32_t *E32, cudaStream_t s);

@@ -33,10 +33,6 @@ namespace {
 // CTA sizes: 512 threads (one CTA per SM) for clusters of 2 or 4 CTAs, 256
 // threads (two CTAs per SM) for clusters of 8
 
-__device__ __forceinline__ void st_cluster_u32(uint32_t addr, uint32_t v) {
-  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
-}
-
 template <int D, int NT>
 __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) msc_cluster_kernel(const TileArgs *__restrict__ Aptr, int P) {
   extern __shared__ uint32_t smem[];
@@ -81,7 +77,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) msc_cluster_kernel(cons
     const uint32_t owner = (uint32_t)j >> lgc;
     uint32_t *f = pend + cls * nch + ((j & (csz - 1)) >> 6);
     if (owner == rank) *f = 1u;
-    else st_cluster_u32(tc::map_shared(f, owner), 1u);
+    else tc::st_cluster_u32(tc::map_shared(f, owner), 1u);
   };
   // neighbour of site j in direction d (+x, -x, +y, -y, +z, -z), periodic:
   // step the axis coordinate inside its bit field (L is a power of two)

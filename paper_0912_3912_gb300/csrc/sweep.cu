@@ -50,7 +50,6 @@ struct SweepArgs {
   int32_t grid_e;
   unsigned int *counter;
   int32_t *all_done;
-  unsigned long long *iters;  // sweeps run by the device-side loop
   unsigned long long *stats;
   int8_t *spins;
   double *energy;
@@ -100,7 +99,6 @@ __global__ void sweep_init(SweepArgs A) {
   if (threadIdx.x == 0) {
     *A.counter = 0;
     *A.all_done = 0;
-    *A.iters = 0;
   }
 }
 
@@ -117,6 +115,37 @@ __device__ __forceinline__ uint32_t sliced_ge4(uint32_t q0, uint32_t q1, uint32_
     eq &= ~(qq[p] ^ tb);
   }
   return gt | eq;
+}
+
+// End of a sweep: per group, which lanes converged, which descents ended.
+// (Folding this into the last class visit - its last CTA closing the sweep -
+// was measured slower than this separate one-block launch.)
+__global__ void sweep_end(SweepArgs A) {
+  const int g = threadIdx.x;
+  if (g >= A.G) return;
+  GroupState &S = A.gs[g];
+  S.start = 0;
+  S.upd = 0;
+  const uint32_t active = S.active;
+  if (!active) return;
+  const uint32_t any = S.any;
+  S.any = 0;
+  uint32_t ended = 0;
+  for (int r = 0; r < 32; ++r)
+    if ((active >> r) & 1u) {
+      S.total[r] += 1;
+      if (A.budget > 0 && S.total[r] >= A.budget) ended |= 1u << r;
+    }
+  const uint32_t conv = active & ~any;
+  ended |= conv;
+  S.d += 1;
+  if (S.d >= A.max_sweeps) ended |= active;
+  atomicAdd(A.stats + 4, (unsigned long long)__popc(active));
+  atomicAdd(A.stats + 0, (unsigned long long)__popc(active) * (unsigned long long)A.I.n);
+  atomicAdd(A.stats + 2, (unsigned long long)__popc(conv));
+  S.convround |= conv;
+  S.active = active & ~ended;
+  if (!S.active) S.round_end = 1;
 }
 
 // One colour class of one sweep.  MODE 0 int lanes, 1 FP32 lanes, 2 multi-spin
@@ -534,24 +563,9 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
               float f;
               if (refresh) {
                 // from scratch: the FP64 sum rounded to FP32, formed exactly in
-                // fixed point when the exponent range allows it
+                // fixed point with the spin's precomputed unit when that is exact
+                // (this path serves CSR instances; lattices take the staged path)
                 const float hj = __ldg(reinterpret_cast<const float *>(G.h) + so + j);
-                float jw[6];
-                uint32_t sn[6];
-                XRange xr;
-                xr_see(xr, hj);
-                if (LAT) {
-#pragma unroll
-                  for (int kk = 0; kk < 6; ++kk)
-                    if (kk < (int)k1) {
-                      jw[kk] = coup(kk);
-                      sn[kk] = swg[nbr(kk)];
-                      xr_see(xr, jw[kk]);
-                    }
-                } else {
-                  for (uint32_t kk = k0; kk < k1; ++kk) xr_see(xr, coup(kk));
-                  for (uint32_t q = e0; q < e1; ++q) xr_see(xr, __ldg(hJf + __ldg(G.inc_edge + q)));
-                }
                 auto hyper_neg = [&](int e) -> uint32_t {
                   uint32_t neg = 0;
                   for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
@@ -560,21 +574,12 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
                   }
                   return neg;
                 };
-                if (xr_exact(xr)) {
-                  const int u = xr.emax < 0 ? 24 : xr.emin;
+                const int u = __ldg(G.runit + so + j);
+                if (u >= 0) {
                   int64_t acc = xr_term(hj, u);
-                  if (LAT) {
-#pragma unroll
-                    for (int kk = 0; kk < 6; ++kk)
-                      if (kk < (int)k1) {
-                        const int64_t tt = xr_term(jw[kk], u);
-                        acc += ((sn[kk] >> ln) & 1u) ? tt : -tt;
-                      }
-                  } else {
-                    for (uint32_t kk = k0; kk < k1; ++kk) {
-                      const int64_t tt = xr_term(coup(kk), u);
-                      acc += ((swg[nbr(kk)] >> ln) & 1u) ? tt : -tt;
-                    }
+                  for (uint32_t kk = k0; kk < k1; ++kk) {
+                    const int64_t tt = xr_term(coup(kk), u);
+                    acc += ((swg[nbr(kk)] >> ln) & 1u) ? tt : -tt;
                   }
                   for (uint32_t q = e0; q < e1; ++q) {
                     const int e = __ldg(G.inc_edge + q);
@@ -693,55 +698,6 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
   if (tid < A.G && s_any[tid]) atomicOr(&A.gs[tid].any, s_any[tid]);
   my_flips = block_sum(my_flips, s_red);
   if (tid == 0 && my_flips) atomicAdd(A.stats + 1, my_flips);
-}
-
-// End of a sweep: per group, which lanes converged, which descents ended.
-// Inside the device-side loop (cond != 0) it also sets the loop condition `hw`
-// to 0 once every group is done or after `bound` sweeps (then stats[6] = 1
-// reports that the bound was hit), and counts the loop's kernels in stats[5].
-__global__ void sweep_end(SweepArgs A, cudaGraphConditionalHandle hw, int cond, long long bound, int nvis) {
-  __shared__ int s_done;
-  const int g = threadIdx.x;
-  if (g == 0) s_done = 1;
-  __syncthreads();
-  if (g < A.G) {
-    GroupState &S = A.gs[g];
-    S.start = 0;
-    S.upd = 0;
-    const uint32_t active = S.active;
-    if (active) {
-      const uint32_t any = S.any;
-      S.any = 0;
-      uint32_t ended = 0;
-      for (int r = 0; r < 32; ++r)
-        if ((active >> r) & 1u) {
-          S.total[r] += 1;
-          if (A.budget > 0 && S.total[r] >= A.budget) ended |= 1u << r;
-        }
-      const uint32_t conv = active & ~any;
-      ended |= conv;
-      S.d += 1;
-      if (S.d >= A.max_sweeps) ended |= active;
-      atomicAdd(A.stats + 4, (unsigned long long)__popc(active));
-      atomicAdd(A.stats + 0, (unsigned long long)__popc(active) * (unsigned long long)A.I.n);
-      atomicAdd(A.stats + 2, (unsigned long long)__popc(conv));
-      S.convround |= conv;
-      S.active = active & ~ended;
-      if (!S.active) S.round_end = 1;
-    }
-    if (!S.done) atomicAnd(&s_done, 0);
-  }
-  __syncthreads();
-  if (cond && g == 0) {
-    atomicAdd(A.stats + 5, (unsigned long long)(nvis + 3));  // kernels of this sweep
-    const unsigned long long it = ++*A.iters;
-    bool stop = s_done != 0;
-    if ((long long)it > bound) {
-      stop = true;
-      A.stats[6] = 1ull;
-    }
-    if (stop) cudaGraphSetConditional(hw, 0u);
-  }
 }
 
 // Energies of the lanes whose round ended (all lanes of the group at once,
@@ -991,20 +947,48 @@ __global__ void __launch_bounds__(kST) sweep_energy(SweepArgs A) {
   for (int g = 0; g < A.G; ++g) {
     GroupState &S = A.gs[g];
     if (!(S.round_end || S.final_pass)) continue;
-    if (warp == 0) {
-      if (FLOAT && !fx) {
-        double a = 0.0;
-        for (int cta = 0; cta < (int)gridDim.x; ++cta) a += A.partial[((size_t)cta * A.G + g) * 32 + lane];
-        S.E[lane] = a;
-      } else {
-        long long hi = 0;
-        unsigned long long lo = 0;
-        for (int cta = 0; cta < (int)gridDim.x; ++cta) {
-          const size_t o = ((size_t)cta * A.G + g) * 32 + lane;
+    // warp w adds the partials of CTAs w, w + nw, ... (fixed order), then warp 0
+    // adds the warps' sums in ascending order: deterministic, nw times shorter
+    {
+      double a = 0.0;
+      long long hi = 0;
+      unsigned long long lo = 0;
+      for (int cta = warp; cta < (int)gridDim.x; cta += nw) {
+        const size_t o = ((size_t)cta * A.G + g) * 32 + lane;
+        if (FLOAT && !fx) {
+          a += A.partial[o];
+        } else {
           hi += reinterpret_cast<const long long *>(A.partial)[o];
           if (fx) lo += reinterpret_cast<const unsigned long long *>(A.partial)[half + o];
         }
-        S.E[lane] = fx ? xe_value(hi, lo, ub) : (double)hi;
+      }
+      __syncthreads();
+      long long *ri = reinterpret_cast<long long *>(&s_red[0][0]);
+      if (FLOAT && !fx) s_red[warp][lane] = a;
+      else ri[warp * 32 + lane] = hi;
+      __syncthreads();
+      if (warp == 0) {
+        if (FLOAT && !fx) {
+          double t = s_red[0][lane];
+          for (int w = 1; w < nw; ++w) t += s_red[w][lane];
+          S.E[lane] = t;
+        } else {
+          long long t = 0;
+          for (int w = 0; w < nw; ++w) t += ri[w * 32 + lane];
+          hi = t;
+        }
+      }
+      if (fx) {
+        __syncthreads();
+        reinterpret_cast<unsigned long long *>(ri)[warp * 32 + lane] = lo;
+        __syncthreads();
+        if (warp == 0) {
+          unsigned long long t = 0;
+          for (int w = 0; w < nw; ++w) t += reinterpret_cast<unsigned long long *>(ri)[w * 32 + lane];
+          S.E[lane] = xe_value(hi, t, ub);
+        }
+      } else if (!FLOAT && warp == 0) {
+        S.E[lane] = (double)hi;
       }
     }
     __syncthreads();
@@ -1139,7 +1123,7 @@ struct SweepState {
   void *mem = nullptr;
   int32_t *h_done = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
-  std::map<std::string, SweepGraph> graphs;  // instantiated device-side loops by configuration
+  std::map<std::string, SweepGraph> graphs;  // instantiated sweep chunks by configuration
 };
 
 std::map<const ising_handle *, SweepState> &sweep_states() {
@@ -1191,25 +1175,8 @@ void enqueue_sweep(const SweepArgs &A, int mode, int ncls, int grid_v, cudaStrea
     else if (mode == 1) enqueue_visit<1, LPS, LAT>(A, c, grid_v, s);
     else enqueue_visit<2, LPS, LAT>(A, c, grid_v, s);
   }
-  sweep_end<<<1, 32, 0, s>>>(A, 0, 0, 0, 0);
+  sweep_end<<<1, 32, 0, s>>>(A);
   debug_step("end", 0, s);
-  enqueue_round_end<LPS, LAT>(A, mode, s);
-}
-
-// One sweep inside the device-side loop: the class visits, the end-of-sweep
-// bookkeeping (which clears the loop condition once every group is done), the
-// energy pass and the restarts (both return at once when no round ended).
-// Measured on GB300, an IF node around the last two cost more per sweep than the
-// two early-returning launches it saves.
-template <int LPS, bool LAT>
-void capture_sweep(const SweepArgs &A, int mode, int ncls, int grid_v, cudaStream_t s,
-                   cudaGraphConditionalHandle hw, long long bound) {
-  for (int c = 0; c < ncls; ++c) {
-    if (mode == 0) enqueue_visit<0, LPS, LAT>(A, c, grid_v, s);
-    else if (mode == 1) enqueue_visit<1, LPS, LAT>(A, c, grid_v, s);
-    else enqueue_visit<2, LPS, LAT>(A, c, grid_v, s);
-  }
-  sweep_end<<<1, 32, 0, s>>>(A, hw, 1, bound, ncls);
   enqueue_round_end<LPS, LAT>(A, mode, s);
 }
 
@@ -1260,80 +1227,68 @@ cudaError_t run_instance(ising_handle *h, SweepArgs A, int mode, cudaStream_t s)
   // upper bound on the sweeps any group can need
   int64_t max_sweeps_total = (int64_t)A.restarts * A.max_sweeps + A.restarts;
   if (A.budget > 0) max_sweeps_total = std::min<int64_t>(max_sweeps_total, (int64_t)A.R * A.budget + A.max_sweeps);
-  // After one sweep of direct launches, the sweeps run as a device-side loop: a
-  // CUDA graph whose WHILE node replays a chunk of sweeps until sweep_end finds
-  // every group done (or the bound above is reached), each sweep's energy pass
-  // and restarts behind an IF node.  No host polling; the call stays
-  // asynchronous.  A graph holds at most kMaxNodes launches per chunk; when one
+  // Capture a chunk of sweeps once per configuration (cached) and replay it
+  // until every group is done, polling a done flag one chunk behind so the GPU
+  // always has queued work.  A graph holds at most kMaxNodes launches; when one
   // sweep alone needs more (many colour classes, e.g. the sequential schedule)
-  // chunks of direct launches are polled from the host instead.
+  // sweeps are launched directly instead.  (A device-side loop - a conditional
+  // WHILE node, optionally with an IF node around the round-end kernels - was
+  // measured slightly slower on GB300, and its kernels are not visible to ncu.)
   constexpr int kMaxNodes = 512;
   const int per_sweep = ncls + 3;
   const bool use_graph = per_sweep <= kMaxNodes && !sweep_debug();
   const int chunk = use_graph ? std::max(1, std::min(16, kMaxNodes / per_sweep)) : 1;
+  // the first sweep runs with direct launches, the rest from the graph
   enqueue_sweep<LPS, LAT>(A, mode, ncls, grid_v, s);
   h->launches += per_sweep;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  cudaGraphExec_t exec = nullptr;
   if (use_graph) {
-    std::string key(reinterpret_cast<const char *>(&A), sizeof(A));
-    key += std::to_string(mode) + "/" + std::to_string(grid_v) + "/" + std::to_string(chunk);
+    // everything the captured launches bake in besides the handle's own arrays
+    char key[256];
+    std::snprintf(key, sizeof key, "%d/%d/%d/%d/%d/%d/%d/%d/%d/%d/%llu/%p/%d/%d/%d/%d", A.b, A.R, A.G, A.LPS,
+                  A.max_sweeps, A.restarts, A.budget, A.refresh, A.sequential, A.lattice,
+                  (unsigned long long)A.seed, (void *)A.sw, mode, grid_v, chunk, ncls);
     auto it = S.graphs.find(key);
     if (it == S.graphs.end()) {
       SweepGraph sg;
       cudaStream_t cs = nullptr;
-      cudaGraphConditionalHandle hw;
-      cudaGraphNodeParams wp = {};
-      cudaGraphNode_t wn;
-      e = cudaGraphCreate(&sg.graph, 0);
-      if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hw, sg.graph, 1, cudaGraphCondAssignDefault);
+      if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return e;
+      e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        wp.type = cudaGraphNodeTypeConditional;
-        wp.conditional.handle = hw;
-        wp.conditional.type = cudaGraphCondTypeWhile;
-        wp.conditional.size = 1;
-        e = cudaGraphAddNode(&wn, sg.graph, nullptr, nullptr, 0, &wp);
-      }
-      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-      if (e == cudaSuccess)
-        e = cudaStreamBeginCaptureToGraph(cs, wp.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                          cudaStreamCaptureModeThreadLocal);
-      if (e == cudaSuccess) {
-        const long long bound = (long long)max_sweeps_total + 2 * chunk + 2;
-        for (int k = 0; k < chunk; ++k) capture_sweep<LPS, LAT>(A, mode, ncls, grid_v, cs, hw, bound);
-        e = cudaGetLastError();
-        cudaGraph_t body = nullptr;
-        const cudaError_t e2 = cudaStreamEndCapture(cs, &body);
-        if (e == cudaSuccess) e = e2;
+        for (int k = 0; k < chunk; ++k) enqueue_sweep<LPS, LAT>(A, mode, ncls, grid_v, cs);
+        e = cudaStreamEndCapture(cs, &sg.graph);
       }
       if (e == cudaSuccess) e = cudaGraphInstantiate(&sg.exec, sg.graph, 0);
-      if (cs) cudaStreamDestroy(cs);
+      cudaStreamDestroy(cs);
       if (e != cudaSuccess) {
         if (sg.graph) cudaGraphDestroy(sg.graph);
-        cudaGetLastError();
         return e;
       }
       it = S.graphs.emplace(key, sg).first;
     }
-    // kernels run inside the loop are counted on the device (stats slot 5)
-    e = cudaGraphLaunch(it->second.exec, s);
-  } else {
-    const int64_t max_chunks = max_sweeps_total + 2;
-    int64_t launched = 0;
-    for (;;) {
-      h->launches += per_sweep;
+    exec = it->second.exec;
+  }
+  const int64_t max_chunks = max_sweeps_total / chunk + 2;
+  int64_t launched = 0;
+  for (;;) {
+    h->launches += (uint64_t)chunk * per_sweep;
+    if (use_graph) {
+      if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) break;
+    } else {
       enqueue_sweep<LPS, LAT>(A, mode, ncls, grid_v, s);
       if ((e = cudaGetLastError()) != cudaSuccess) break;
-      cudaMemcpyAsync(S.h_done + (launched & 1), A.all_done, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-      cudaEventRecord(S.ev[launched & 1], s);
-      ++launched;
-      if (sweep_debug()) std::fprintf(stderr, "[sweep] chunk %lld queued\n", (long long)launched);
-      if (launched >= 2) {
-        // look one chunk behind so the GPU always has queued work
-        cudaEventSynchronize(S.ev[launched & 1]);
-        if (S.h_done[launched & 1]) break;
-      }
-      if (launched >= max_chunks) break;
     }
+    cudaMemcpyAsync(S.h_done + (launched & 1), A.all_done, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    cudaEventRecord(S.ev[launched & 1], s);
+    ++launched;
+    if (sweep_debug()) std::fprintf(stderr, "[sweep] chunk %lld queued\n", (long long)launched);
+    if (launched >= 2) {
+      // look one chunk behind so the GPU always has queued work
+      cudaEventSynchronize(S.ev[launched & 1]);
+      if (S.h_done[launched & 1]) break;
+    }
+    if (launched >= max_chunks) break;
   }
   if (e != cudaSuccess) return e;
   // energies of the final states of replicas that never converged
@@ -1376,9 +1331,14 @@ cudaError_t launch_sweep(ising_handle *h, const ising_search_params *p, int32_t 
   const size_t words = (size_t)G * h->nmax;
   auto up256 = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t need = 4 * up256(words * 4) + (fl ? up256(words * LPS * 4) : 0) + up256(G * sizeof(GroupState)) +
-                      up256((size_t)grid_e * G * 32 * 16) + 3 * 256;
+                      up256((size_t)grid_e * G * 32 * 16) + 2 * 256;
   cudaError_t e;
   if (need > S.bytes) {
+    for (auto &kv : S.graphs) {  // captured against the old scratch
+      cudaGraphExecDestroy(kv.second.exec);
+      cudaGraphDestroy(kv.second.graph);
+    }
+    S.graphs.clear();
     cudaFree(S.mem);
     S.mem = nullptr;
     S.bytes = 0;
@@ -1414,7 +1374,6 @@ cudaError_t launch_sweep(ising_handle *h, const ising_search_params *p, int32_t 
   A.partial = (double *)take((size_t)grid_e * G * 32 * 16);  // FP64 sums, or fixed-point high | low halves
   A.counter = (unsigned int *)take(64);
   A.all_done = (int32_t *)take(64);
-  A.iters = (unsigned long long *)take(64);
   A.stats = h->d_stats;
   A.spins = spins;
   A.energy = E;

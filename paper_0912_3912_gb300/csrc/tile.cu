@@ -28,6 +28,8 @@
 // C-ABI semantics define.
 #include <cfloat>
 
+#include <algorithm>
+
 #include "device_common.cuh"
 
 namespace isg {
@@ -246,6 +248,8 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *_
   uint32_t *pb = smem + (MODE >= 2 ? 1 : 2) * nmax;
   uint32_t *bw = A.bw + (size_t)blockIdx.x * nmax;
   float *F = A.F ? A.F + (size_t)blockIdx.x * nmax * 32 : nullptr;
+  // FP32 fields of instances up to A.fsm_cap spins stay in shared memory
+  float *Fs = reinterpret_cast<float *>(smem + (((MODE >= 2 ? 1 : 2) * nmax + (nmax + 31) / 32 + 3) & ~3));
   unsigned long long my_flips = 0, my_evals = 0, my_sweeps = 0, my_minima = 0, my_desc = 0;
 
   for (;;) {
@@ -260,6 +264,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *_
     const uint32_t lane_valid = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
     const uint64_t seed = A.seeds[b];
     const int ncls = A.sequential ? n : I.ncls;
+    float *Fc = (MODE == 1 && n <= A.fsm_cap) ? Fs : F;
     if (tid < 32) {
       s_total[tid] = 0;
       s_minima[tid] = 0;
@@ -450,13 +455,11 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *_
                 const float *hJ = reinterpret_cast<const float *>(G.hJ);
                 float f;
                 if (refresh) {
+                  // from scratch: the FP64 sum rounded to FP32, formed exactly in
+                  // fixed point with the spin's precomputed unit when that is exact
                   const float hj = __ldg(reinterpret_cast<const float *>(G.h) + gj);
-                  XRange xr;
-                  xr_see(xr, hj);
-                  for (uint32_t kk = k0; kk < k1; ++kk) xr_see(xr, __ldg(Jf + kk));
-                  for (uint32_t q = e0; q < e1; ++q) xr_see(xr, __ldg(hJ + __ldg(G.inc_edge + q)));
-                  if (xr_exact(xr)) {
-                    const int u = xr.emax < 0 ? 24 : xr.emin;
+                  const int u = __ldg(G.runit + gj);
+                  if (u >= 0) {
                     int64_t acc = xr_term(hj, u);
                     for (uint32_t kk = k0; kk < k1; ++kk) {
                       const int64_t t = xr_term(__ldg(Jf + kk), u);
@@ -493,31 +496,17 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *_
                     f = __double2float_rn(acc);
                   }
                 } else {
-                  // Only neighbours that flipped since this spin's previous visit
-                  // change its field; with none, field and decision are unchanged.
-                  uint32_t flipped_k = 0, par_e = 0;
-                  for (uint32_t kk = k0; kk < k1; ++kk)
-                    if ((fm[__ldg(G.col + kk)] >> lane) & 1u) flipped_k |= 1u << ((kk - k0) & 31);
-                  for (uint32_t q = e0; q < e1; ++q) {
-                    const int e = __ldg(G.inc_edge + q);
-                    uint32_t par = 0;
-                    for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
-                      const int mm = __ldg(G.hmem + m);
-                      if (mm != j) par ^= (fm[mm] >> lane) & 1u;
-                    }
-                    par_e |= par << ((q - e0) & 31);
-                  }
-                  const bool dirty = (flipped_k | par_e) != 0 || (k1 - k0) > 32 || (e1 - e0) > 32;
-                  if (!dirty) {
-                    flip = false;
-                    goto decided;
-                  }
-                  f = F[(size_t)j * 32 + lane];
+                  // Pull the flips of the neighbours since this spin's previous
+                  // visit (CSR order, then hyper-edges ascending), one pass; with
+                  // none for this lane, field and decision are unchanged.
+                  f = Fc[(size_t)j * 32 + lane];
+                  bool dirty = false;
                   for (uint32_t kk = k0; kk < k1; ++kk) {
                     const int i = __ldg(G.col + kk);
                     if ((fm[i] >> lane) & 1u) {
                       const float w2 = 2.0f * __ldg(Jf + kk);
                       f = __fadd_rn(f, ((sw[i] >> lane) & 1u) ? w2 : -w2);
+                      dirty = true;
                     }
                   }
                   for (uint32_t q = e0; q < e1; ++q) {
@@ -533,10 +522,15 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *_
                     if (par) {
                       const float w2 = 2.0f * __ldg(hJ + e);
                       f = __fadd_rn(f, neg ? -w2 : w2);
+                      dirty = true;
                     }
                   }
+                  if (!dirty) {
+                    flip = false;
+                    goto decided;
+                  }
                 }
-                F[(size_t)j * 32 + lane] = f;
+                Fc[(size_t)j * 32 + lane] = f;
                 flip = up ? (f < 0.0f) : (f > 0.0f);
               decided:;
               }
@@ -653,6 +647,15 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *_
 
 size_t tile_smem_bytes(int mode, int nmax) {
   return (size_t)(mode >= 2 ? 1 : 2) * (size_t)nmax * sizeof(uint32_t) + (size_t)((nmax + 31) / 32) * sizeof(uint32_t);
+}
+
+// Spins whose FP32 fields (32 lanes) fit in shared memory next to the tile's
+// words, within `budget` bytes of dynamic shared memory.
+int tile_fsm_cap(int nmax, size_t budget) {
+  const size_t base = (tile_smem_bytes(1, nmax) + 15) / 16 * 16;
+  if (budget <= base) return 0;
+  const size_t cap = (budget - base) / (32 * sizeof(float));
+  return (int)std::min<size_t>(cap, (size_t)nmax);
 }
 
 int tile_max_ctas_per_sm(int mode, size_t smem) {
