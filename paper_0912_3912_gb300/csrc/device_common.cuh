@@ -95,6 +95,47 @@ __device__ __forceinline__ double xe_value(long long hi, unsigned long long lo, 
   return v * __longlong_as_double((long long)(ebase - 150 + 1023) << 52);
 }
 
+// 32 x 32 bit transpose across a warp: lane i holds row i (bit c = column c);
+// returns column `lane` (bit i = row i's bit `lane`).  Five exchange stages,
+// each swapping the off-diagonal halves of 2j x 2j blocks between lanes i and i^j.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t v, int lane) {
+  const uint32_t m[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int j = 16 >> s;
+    const uint32_t t = __shfl_xor_sync(0xffffffffu, v, j);
+    v = (lane & j) ? ((v & ~m[s]) | ((t & ~m[s]) >> j)) : ((v & m[s]) | ((t & m[s]) << j));
+  }
+  return v;
+}
+
+// Warp total of bit-sliced per-lane counters: plane q of every lane holds bit
+// q of 32 counters (one per bit position r).  A butterfly of bit-sliced adds
+// leaves every lane with the warp-wide sums (Q + 5 planes); lane r then reads
+// counter r's total from bit r of each plane.
+template <int Q>
+__device__ __forceinline__ long long warp_sliced_total(const uint32_t (&acc)[Q], int lane) {
+  uint32_t w[Q + 5];
+#pragma unroll
+  for (int q = 0; q < Q + 5; ++q) w[q] = q < Q ? acc[q] : 0u;
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int j = 16 >> s;
+    uint32_t carry = 0u;
+#pragma unroll
+    for (int q = 0; q < Q + 5; ++q) {
+      const uint32_t o = __shfl_xor_sync(0xffffffffu, w[q], j);
+      const uint32_t x = w[q];
+      w[q] = x ^ o ^ carry;
+      carry = (x & o) | (x & carry) | (o & carry);
+    }
+  }
+  long long total = 0;
+#pragma unroll
+  for (int q = 0; q < Q + 5; ++q) total += (long long)((w[q] >> lane) & 1u) << q;
+  return total;
+}
+
 template <class T>
 __device__ __forceinline__ T ldg_val(const void *p, int64_t i) {
   return __ldg(reinterpret_cast<const T *>(p) + i);

@@ -168,13 +168,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) msc_cluster_kernel(cons
         cy = c;
       }
     }
-    long long mine = 0;
-#pragma unroll
-    for (int q = 0; q < Q; ++q)
-      for (int r = 0; r < 32; ++r) {
-        const int c = __popc(__ballot_sync(0xffffffffu, (acc[q] >> r) & 1u));
-        if (lane == r) mine += (long long)c << q;
-      }
+    const long long mine = warp_sliced_total<Q>(acc, lane);  // lane r: replica r's warp total
     nz = warp_sum(nz);
     atomicAdd(&s_cnt[lane], (int)mine);
     if (lane == 0) atomicAdd(&s_cnt[32], nz);
@@ -210,11 +204,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) msc_cluster_kernel(cons
       const uint4 x = start_bits(seed, (uint32_t)w, (uint32_t)(32 * g + lane), (uint32_t)k, (uint32_t)b);
       for (int q = 0; q < 4; ++q) {
         const uint32_t xw = word_of(x, q);
-        uint32_t mine = 0;
-        for (int u = 0; u < 32; ++u) {
-          const uint32_t m = __ballot_sync(0xffffffffu, (xw >> u) & 1u);
-          if (lane == u) mine = m;
-        }
+        const uint32_t mine = warp_transpose32(xw, lane);  // lane u: site u's word
         const int o = w * 128 + q * 32 + lane - lo;
         sw[o] = (sw[o] & ~active) | (mine & active);
       }

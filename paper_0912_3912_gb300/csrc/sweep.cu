@@ -1055,18 +1055,13 @@ __global__ void __launch_bounds__(kST) sweep_restart(SweepArgs A) {
         }
       __syncwarp();
       if (start) {
-        // lane l draws replica 32g + l's bits; ballots transpose them so that
-        // lane u ends up with the word of site 128w + 32q + u
+        // lane l draws replica 32g + l's bits; a warp transpose hands lane u
+        // the word of site 128w + 32q + u
         const uint4 x = start_bits(A.seed, (uint32_t)w, (uint32_t)(32 * g + lane), (uint32_t)S.k, (uint32_t)A.b);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const uint32_t xw = word_of(x, q);
-          uint32_t mine = 0;
-#pragma unroll
-          for (int u = 0; u < 32; ++u) {
-            const uint32_t m = __ballot_sync(0xffffffffu, (xw >> u) & 1u);
-            if (lane == u) mine = m;
-          }
+          const uint32_t mine = warp_transpose32(xw, lane);  // lane u: site u's word
           const int i = w * 128 + q * 32 + lane;
           if (i < n) {
             swg[i] = (swg[i] & ~start) | (mine & start);

@@ -144,8 +144,8 @@ __device__ void tile_energy_lanes(const DevGraph &G, const InstDesc &I, const ui
 // multi-spin coded lattice path): E = 2 U - (n d + #{h != 0}), U = the lane's
 // number of unsatisfied bonds and fields.  Each thread adds, per site, the
 // unsatisfied masks of its forward bonds (+x, +y, +z) and of its field into a
-// bit-sliced per-lane counter; ballots then total each counter bit over a
-// warp, and warps are added in shared memory.  Exact integers.
+// bit-sliced per-lane counter; a butterfly of bit-sliced adds totals the
+// counters over the warp, and warps are added in shared memory.  Exact integers.
 __device__ void tile_energy_lattice(const DevGraph &G, const InstDesc &I, const uint32_t *sw, int *cnt,
                                     double *E) {
   constexpr int Q = 14;  // counter depth: up to 2^14 - 1 per lane and thread
@@ -194,13 +194,7 @@ __device__ void tile_energy_lattice(const DevGraph &G, const InstDesc &I, const 
       cy = c;
     }
   }
-  long long mine = 0;
-#pragma unroll
-  for (int q = 0; q < Q; ++q)
-    for (int r = 0; r < 32; ++r) {
-      const int c = __popc(__ballot_sync(0xffffffffu, (acc[q] >> r) & 1u));
-      if (lane == r) mine += (long long)c << q;
-    }
+  const long long mine = warp_sliced_total<Q>(acc, lane);  // lane r: replica r's warp total
   nz = warp_sum(nz);
   atomicAdd(&cnt[lane], (int)mine);
   if (lane == 0) atomicAdd(&cnt[32], nz);
@@ -287,16 +281,12 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_kernel(const TileArgs *_
       if (!active) break;
 
       // Random starts for the lanes beginning descent k (Sec. IV); a warp
-      // transposes 32 replicas x 128 spins with ballots.
+      // transposes 32 replicas x 128 spins with shuffle exchanges.
       for (int w = warp; w * 128 < n; w += nwarps) {
         const uint4 x = start_bits(seed, (uint32_t)w, (uint32_t)(32 * g + lane), (uint32_t)k, (uint32_t)b);
         for (int q = 0; q < 4; ++q) {
           const uint32_t xw = word_of(x, q);
-          uint32_t mine = 0;
-          for (int u = 0; u < 32; ++u) {
-            const uint32_t m = __ballot_sync(0xffffffffu, (xw >> u) & 1u);
-            if (lane == u) mine = m;
-          }
+          const uint32_t mine = warp_transpose32(xw, lane);  // lane u: site u's word
           const int i = w * 128 + q * 32 + lane;
           if (i < n) {
             sw[i] = (sw[i] & ~active) | (mine & active);
