@@ -372,9 +372,9 @@ int msc_cluster_size(const ising_handle *h, int32_t R, const ising_search_params
       if (d >= 0 && I.lat_d != d) ok = false;
       d = I.lat_d;
     }
-    // Clusters of 8 (256-thread CTAs) only when every CTA gets an SM of its own
-    // and all clusters are resident at once: few replica groups, each spread
-    // wider.  With more groups, 4-CTA clusters of 512 threads measured faster.
+    // Clusters of 8 only when every CTA gets an SM of its own and all clusters
+    // are resident at once: few replica groups, each spread wider.  With more
+    // groups, 4-CTA clusters measured faster than two 8-CTA clusters per SM set.
     if (ok && P == 8 &&
         (tiles * P > (int64_t)h->sm_count ||
          msc_cluster_max_active(const_cast<ising_handle *>(h), (int)tiles, P, h->nmax / P, d) < tiles))

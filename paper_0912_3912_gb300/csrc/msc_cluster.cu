@@ -30,11 +30,12 @@ namespace isg {
 
 namespace {
 
-// CTA sizes: 512 threads (one CTA per SM) for clusters of 2 or 4 CTAs, 256
-// threads (two CTAs per SM) for clusters of 8
+// CTAs of 512 threads, one per SM (two per SM at 64 registers, in clusters of
+// 8, measured slower on the 32^3 lattice)
+constexpr int kCT = 512;
 
-template <int D, int NT>
-__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) msc_cluster_kernel(const TileArgs *__restrict__ Aptr, int P) {
+template <int D>
+__global__ void __launch_bounds__(kCT, 1) msc_cluster_kernel(const TileArgs *__restrict__ Aptr, int P) {
   extern __shared__ uint32_t smem[];
   __shared__ uint32_t s_any[2], s_active, s_convround, s_upd;
   __shared__ int32_t s_total[32], s_minima[32];
@@ -348,7 +349,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) msc_cluster_kernel(cons
     atomicAdd(A.stats + 3, my_desc);
     atomicAdd(A.stats + 4, my_sweeps);
   }
-  __shared__ unsigned long long s_fl[NT / 32];
+  __shared__ unsigned long long s_fl[kCT / 32];
   my_flips = block_sum(my_flips, s_fl);
   if (tid == 0) atomicAdd(A.stats + 1, my_flips);
   tc::cluster_sync();  // no CTA leaves while peers may still read its shared memory
@@ -358,22 +359,23 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) msc_cluster_kernel(cons
 
 size_t msc_cluster_smem(int csz) { return (size_t)csz * 4 + (size_t)(csz / 64) * 2 * 4 + (size_t)csz; }
 
-template <int D, int NT>
+template <int D>
 cudaError_t launch_cfg(cudaLaunchConfig_t &cfg, const TileArgs *args, int P, size_t smem, int *max_active) {
-  cudaError_t e = cudaFuncSetAttribute(msc_cluster_kernel<D, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = msc_cluster_kernel<D>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if (max_active) return cudaOccupancyMaxActiveClusters(max_active, msc_cluster_kernel<D, NT>, &cfg);
-  return cudaLaunchKernelEx(&cfg, msc_cluster_kernel<D, NT>, args, P);
+  if (max_active) return cudaOccupancyMaxActiveClusters(max_active, kern, &cfg);
+  return cudaLaunchKernelEx(&cfg, kern, args, P);
 }
 
 // Launch (max_active == nullptr) or report how many clusters can be resident at once.
 cudaError_t msc_cluster_launch_or_query(ising_handle *h, int n_tiles, int P, int csz_max, int D, cudaStream_t s,
                                         int *max_active) {
   const size_t smem = msc_cluster_smem(csz_max);
-  const int nt = P == 8 ? 256 : 512;
+
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(n_tiles * P);
-  cfg.blockDim = dim3(nt);
+  cfg.blockDim = dim3(kCT);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -384,8 +386,7 @@ cudaError_t msc_cluster_launch_or_query(ising_handle *h, int n_tiles, int P, int
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   const TileArgs *args = (const TileArgs *)h->d_tile_args;
-  if (D == 3) return nt == 256 ? launch_cfg<3, 256>(cfg, args, P, smem, max_active) : launch_cfg<3, 512>(cfg, args, P, smem, max_active);
-  return nt == 256 ? launch_cfg<2, 256>(cfg, args, P, smem, max_active) : launch_cfg<2, 512>(cfg, args, P, smem, max_active);
+  return D == 3 ? launch_cfg<3>(cfg, args, P, smem, max_active) : launch_cfg<2>(cfg, args, P, smem, max_active);
 }
 
 cudaError_t launch_msc_cluster(ising_handle *h, int n_tiles, int P, int csz_max, int D, cudaStream_t s) {
