@@ -434,7 +434,7 @@ ising_status run_tile(ising_handle *h, int mode, int32_t R, const ising_search_p
   }
   // FP32 lanes: fields in shared memory for every instance that fits, within a
   // budget that still lets two CTAs share an SM (the kernel is built for two)
-  constexpr size_t kFsmBudget = 100 * 1024;
+  constexpr size_t kFsmBudget = 48 * 1024;
   const int fsm_cap = mode == 1 ? tile_fsm_cap(h->nmax, kFsmBudget) : 0;
   const size_t smem = mode == 1 && fsm_cap > 0 ? (tile_smem_bytes(mode, h->nmax) + 15) / 16 * 16 + (size_t)fsm_cap * 128
                                               : tile_smem_bytes(mode, h->nmax);

@@ -14,7 +14,7 @@
 
 namespace isg {
 
-constexpr int kTileThreads = 512;   // threads per tile CTA (16 warps)
+constexpr int kTileThreads = 256;   // threads per tile CTA (8 warps)
 constexpr int kSweepThreads = 256;  // threads per CTA of the large-instance sweeps
 
 // One instance as the kernels see it.  Spin, edge and class arrays of all

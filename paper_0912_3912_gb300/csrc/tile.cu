@@ -222,7 +222,7 @@ __device__ __forceinline__ uint32_t sliced_ge(uint32_t c0, uint32_t c1, uint32_t
 }  // namespace
 
 template <int MODE>
-__global__ void __launch_bounds__(kTileThreads, MODE == 3 ? 1 : 2) tile_kernel(const TileArgs *__restrict__ Aptr) {
+__global__ void __launch_bounds__(kTileThreads, MODE == 3 ? 2 : 4) tile_kernel(const TileArgs *__restrict__ Aptr) {
   extern __shared__ uint32_t smem[];
   __shared__ int s_tile;
   __shared__ uint32_t s_any, s_active, s_convround, s_upd;
