@@ -176,6 +176,24 @@ __global__ void dense_init(int32_t R, DenseRep *rep, unsigned long long *stats) 
   atomicAdd(stats + 3, 1ull);
 }
 
+// Returned energies, recomputed from the returned spins with the FP32
+// couplings: F = S J by an FP32 GEMM (library), then E_r = -1/2 sum_i s_i F_ri
+// in FP64, one warp per replica in a fixed order.  The search's own energies
+// come from its BF16 hi+lo fields, whose error grows with n.
+__global__ void dense_spins_f32(const int8_t *s, float *Sf, int64_t count) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
+    Sf[t] = (float)s[t];
+}
+
+__global__ void dense_energy_from_fields(const int8_t *s, const float *F, int32_t n, int32_t R, double *E) {
+  const int r = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (r >= R) return;
+  double acc = 0.0;
+  for (int i = lane; i < n; i += 32) acc += (double)s[(int64_t)r * n + i] * (double)F[(int64_t)r * n + i];
+  acc = warp_sum(acc);
+  if (lane == 0) E[r] = -0.5 * acc;
+}
+
 __global__ void dense_output(int32_t n, int32_t R, int32_t Rp, int32_t b, int64_t spin_off, const __nv_bfloat16 *S,
                              const int8_t *best, const DenseRep *rep, int8_t *out, double *E, int32_t *minima) {
   const int64_t tot = (int64_t)R * n;
@@ -204,6 +222,7 @@ struct DenseState {
   int32_t *active = nullptr, *h_active = nullptr;
   __nv_bfloat16 *S_tc = nullptr;  // [Rp128][n] replica-major spins for the tcgen05 kernel
   int32_t *err = nullptr, *h_err = nullptr;
+  float *Sx = nullptr, *Fx = nullptr;  // [R][n] returned spins and their FP32 fields
 };
 
 std::map<const ising_handle *, DenseState> &dense_states() {
@@ -223,6 +242,8 @@ void free_state(DenseState &D) {
   cudaFree(D.workspace);
   cudaFree(D.S_tc);
   cudaFree(D.err);
+  cudaFree(D.Sx);
+  cudaFree(D.Fx);
   if (D.h_err) cudaFreeHost(D.h_err);
   if (D.h_active) cudaFreeHost(D.h_active);
   if (D.cublas) cublasDestroy(D.cublas);
@@ -242,6 +263,26 @@ bool fields(DenseState &D, int b0, int cnt, float *out) {
   if (gemm(D, D.Rp, cnt, n, D.S, D.Rp, D.hi + (int64_t)b0 * n, n, out, D.Rp, 0.0f) != CUBLAS_STATUS_SUCCESS)
     return false;
   return gemm(D, D.Rp, cnt, n, D.S, D.Rp, D.lo + (int64_t)b0 * n, n, out, D.Rp, 1.0f) == CUBLAS_STATUS_SUCCESS;
+}
+
+cudaError_t exact_energies(DenseState &D, ising_handle *h, int n, int R, const float *J, const int8_t *out,
+                           double *E, cudaStream_t s) {
+  cudaError_t e;
+  if (!D.Sx) {  // sized for D.Rp >= R replicas; freed with the state when n or Rp changes
+    if ((e = cudaMalloc(&D.Sx, (size_t)D.Rp * n * sizeof(float))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&D.Fx, (size_t)D.Rp * n * sizeof(float))) != cudaSuccess) return e;
+  }
+  const int64_t tot = (int64_t)R * n;
+  dense_spins_f32<<<(int)std::min<int64_t>((tot + 255) / 256, (int64_t)h->sm_count * 16), 256, 0, s>>>(out, D.Sx, tot);
+  // column-major view: F^T (n x R) = J (n x n, symmetric) . S^T (n x R); FP32 compute, no TF32
+  const float one = 1.0f, zero = 0.0f;
+  if (cublasSetStream(D.cublas, s) != CUBLAS_STATUS_SUCCESS ||
+      cublasGemmEx(D.cublas, CUBLAS_OP_N, CUBLAS_OP_N, n, R, n, &one, J, CUDA_R_32F, n, D.Sx, CUDA_R_32F, n, &zero,
+                   D.Fx, CUDA_R_32F, n, CUBLAS_COMPUTE_32F_PEDANTIC, CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
+    return cudaErrorUnknown;
+  dense_energy_from_fields<<<(R * 32 + 255) / 256, 256, 0, s>>>(out, D.Fx, n, R, E);
+  h->launches += 2;
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -313,6 +354,9 @@ cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t 
       if ((e = cudaMemcpyAsync(D.h_err, D.err, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
       if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
       if (*D.h_err != 0) return cudaErrorLaunchTimeout;
+      if ((e = exact_energies(D, h, n, R, J, spins + (int64_t)R * h->inst[b].spin_off, E + (int64_t)b * R, s)) !=
+          cudaSuccess)
+        return e;
       joff += (int64_t)n * n;
       continue;
     }
@@ -373,6 +417,9 @@ cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t 
     dense_output<<<(int)std::min<int64_t>((tot + 255) / 256, (int64_t)h->sm_count * 16), 256, 0, s>>>(
         n, R, Rp, b, h->inst[b].spin_off, D.S, D.best, D.rep, spins, E, minima);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = exact_energies(D, h, n, R, J, spins + (int64_t)R * h->inst[b].spin_off, E + (int64_t)b * R, s)) !=
+        cudaSuccess)
+      return e;
     joff += (int64_t)n * n;
   }
   return cudaSuccess;
