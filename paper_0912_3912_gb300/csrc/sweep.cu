@@ -1164,7 +1164,7 @@ void enqueue_round_end(const SweepArgs &A, int mode, cudaStream_t s) {
 }
 
 template <int LPS, bool LAT>
-void enqueue_sweep(const SweepArgs &A, int mode, int ncls, int grid_v, cudaStream_t s) {
+void enqueue_sweep(const SweepArgs &A, int mode, int ncls, int grid_v, cudaStream_t s, bool round_end = true) {
   for (int c = 0; c < ncls; ++c) {
     if (mode == 0) enqueue_visit<0, LPS, LAT>(A, c, grid_v, s);
     else if (mode == 1) enqueue_visit<1, LPS, LAT>(A, c, grid_v, s);
@@ -1172,7 +1172,7 @@ void enqueue_sweep(const SweepArgs &A, int mode, int ncls, int grid_v, cudaStrea
   }
   sweep_end<<<1, 32, 0, s>>>(A);
   debug_step("end", 0, s);
-  enqueue_round_end<LPS, LAT>(A, mode, s);
+  if (round_end) enqueue_round_end<LPS, LAT>(A, mode, s);
 }
 
 // Load every kernel of this configuration before any graph capture, so the
@@ -1220,8 +1220,10 @@ cudaError_t run_instance(ising_handle *h, SweepArgs A, int mode, cudaStream_t s)
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // upper bound on the sweeps any group can need
-  int64_t max_sweeps_total = (int64_t)A.restarts * A.max_sweeps + A.restarts;
-  if (A.budget > 0) max_sweeps_total = std::min<int64_t>(max_sweeps_total, (int64_t)A.R * A.budget + A.max_sweeps);
+  // (each round may wait one sweep for its round-end kernels)
+  int64_t max_sweeps_total = (int64_t)A.restarts * (A.max_sweeps + 2) + A.restarts;
+  if (A.budget > 0)
+    max_sweeps_total = std::min<int64_t>(max_sweeps_total, (int64_t)A.R * A.budget * 2 + A.max_sweeps + 2);
   // Capture a chunk of sweeps once per configuration (cached) and replay it
   // until every group is done, polling a done flag one chunk behind so the GPU
   // always has queued work.  A graph holds at most kMaxNodes launches; when one
@@ -1251,7 +1253,11 @@ cudaError_t run_instance(ising_handle *h, SweepArgs A, int mode, cudaStream_t s)
       if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return e;
       e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        for (int k = 0; k < chunk; ++k) enqueue_sweep<LPS, LAT>(A, mode, ncls, grid_v, cs);
+        // The round-end kernels (energy pass, restarts) follow every second
+        // sweep: a group whose round ended has no active lane, so the sweep in
+        // between visits nothing for it and counts nothing; it only waits.
+        for (int k = 0; k < chunk; ++k)
+          enqueue_sweep<LPS, LAT>(A, mode, ncls, grid_v, cs, (k & 1) || chunk == 1);
         e = cudaStreamEndCapture(cs, &sg.graph);
       }
       if (e == cudaSuccess) e = cudaGraphInstantiate(&sg.exec, sg.graph, 0);
@@ -1267,7 +1273,8 @@ cudaError_t run_instance(ising_handle *h, SweepArgs A, int mode, cudaStream_t s)
   const int64_t max_chunks = max_sweeps_total / chunk + 2;
   int64_t launched = 0;
   for (;;) {
-    h->launches += (uint64_t)chunk * per_sweep;
+    // sweeps k = 0, 2, 4, ... of a captured chunk have no round-end kernels
+    h->launches += (uint64_t)chunk * per_sweep - (use_graph && chunk > 1 ? (uint64_t)((chunk + 1) / 2) * 2 : 0);
     if (use_graph) {
       if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) break;
     } else {
