@@ -1,5 +1,8 @@
 // dense.cu — fully connected instances (Sherrington-Kirkpatrick): the
-// sequential schedule with fields computed on tensor cores.
+// sequential schedule with fields computed on tensor cores.  Dispatches to the
+// hand-written tcgen05 kernel (dense_tc.cu) where it applies; the block search
+// below, with its GEMMs in cuBLAS, is the comparator and the fallback for
+// other sizes.
 //
 // For a complete graph every colour class is one spin, so descent is the
 // paper's one-move-at-a-time order (Sec. IV).  Spins are visited in blocks of
@@ -10,12 +13,12 @@
 // exact in BF16, accumulated in FP32 (two GEMMs into one FP32 result).  Inside
 // the block the spins are then decided one after another, each field corrected
 // in FP32 for the block's own earlier flips (+2 J_ij s_j per flipped j), the
-// incremental gain update of the paper restricted to the block.  Energies of
-// converged replicas are -1/2 sum_i s_i f_i summed in FP64 over fields from one
-// full-size GEMM.  These fields carry the BF16-split and FP32 accumulation
-// error, so decisions within about 1e-4 of zero and energies within about
-// 1e-7 relative may differ from an FP64 computation; the tests state and check
-// both bounds.
+// incremental gain update of the paper restricted to the block.  During the
+// search, energies (which decide the best state kept) are -1/2 sum_i s_i f_i in
+// FP64 over those fields; they carry the BF16-split and FP32 accumulation
+// error, so decisions within about 1e-4 of zero may differ from an FP64
+// computation.  The returned energies are recomputed from the returned spins
+// with the FP32 couplings (FP32 GEMM, FP64 sums), within ~1e-8 relative.
 #include <cublas_v2.h>
 #include <cuda_bf16.h>
 

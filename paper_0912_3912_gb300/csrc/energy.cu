@@ -2,8 +2,7 @@
 // Eq. 6), int8 spins [instance][replica][spin].  Two passes with a fixed
 // summation order: blocks of kChunk spins (and a proportional share of the
 // hyper-edges) write partial sums; a second kernel adds them in order.
-// FP64 for float couplings (the only FP64 step besides the field refresh);
-// exact int64 for integer couplings.
+// FP64 for float couplings; exact int64 for integer couplings.
 #include "device_common.cuh"
 
 namespace isg {

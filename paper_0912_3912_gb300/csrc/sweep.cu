@@ -1,13 +1,16 @@
 // sweep.cu — large instances (too big for one CTA's shared memory): every
 // colour class is one launch over the whole GPU; a sweep is the sequence of
-// class launches plus small bookkeeping launches, and chunks of sweeps are
-// captured once into a CUDA graph and replayed until every replica is done.
+// class launches plus a one-block end-of-sweep launch, with the round-end
+// kernels (energy pass, restarts) after every second sweep; chunks of sweeps
+// are captured once into a CUDA graph (cached) and replayed until every replica
+// is done, the host polling a done flag one chunk behind.
 //
 // Same method and semantics as the tile kernels (García & Markov, Sec. IV:
 // improving single-spin moves, repeated sweeps to a 1-flip minimum, random
 // restarts, best kept; incremental FP32 field updates for float couplings with
-// an FP64 refresh).  State lives in global memory: spin words sw[g][n] (bit l =
-// replica 32g + l), flip masks fm[g][n], best words bw[g][n], FP32 fields
+// an exact refresh).  State lives in global memory: spin words sw[g][n] (bit l =
+// replica 32g + l), flip masks fm[g][n], pending masks pend[g][n] (lanes with a
+// neighbour that flipped since the spin's last visit), best words bw[g][n], FP32 fields
 // F[g][position][LPS] stored in colour-class order so a class reads them
 // contiguously.  LPS (lanes per spin) = 32, 16 or 8 replicas share one warp
 // visit; with LPS < 32 a warp visits 32/LPS spins at once.

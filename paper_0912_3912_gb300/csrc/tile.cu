@@ -1,21 +1,23 @@
-// tile.cu — persistent tile kernels: one CTA works on one (instance,
-// 32-replica group) tile at a time, pulled from a work queue, with the
-// instance's spins bit-packed in shared memory (bit r of word i = replica r of
-// spin i is +1).
+// tile.cu — persistent tile kernels: one CTA (256 threads; four per SM, two for
+// the lattice mode) works on one (instance, 32-replica group) tile at a time,
+// pulled from a work queue largest first, with the instance's spins bit-packed
+// in shared memory (bit r of word i = replica r of spin i is +1).
 //
 // Method (García & Markov, Sec. IV): single-spin moves taken when their gain
 // -2 s_i f_i is positive, whole sweeps repeated until no move is taken (a 1-flip
 // local minimum), independent random starts, the best result kept.  Colour
 // classes are independent sets, so all spins of a class decide at once.
 //
-// Three evaluators share the sweep/restart machinery:
+// Four evaluators share the sweep/restart machinery:
 //   MODE 0  integer couplings, one warp per spin, lane = replica, exact int32
 //           fields recomputed from the neighbours' bits at each visit;
 //   MODE 1  FP32 couplings, one warp per spin, lane = replica, FP32 fields kept
 //           per (spin, replica) and updated at each visit from the neighbours
 //           that flipped since the previous visit (the paper's incremental gain
-//           update), with an FP64 from-scratch refresh at descent sweeps
-//           d % refresh == 0 (always d == 0);
+//           update), with a from-scratch refresh at descent sweeps
+//           d % refresh == 0 (always d == 0): the FP64 sum rounded to FP32,
+//           formed exactly in fixed point when that is exact (runit >= 0);
+//           fields of instances that fit stay in shared memory;
 //   MODE 2  multi-spin coding for J in {-1,+1}, h in {-1,0,+1}: one thread per
 //           spin evaluates all 32 replicas with bitwise logic (unsatisfied-bond
 //           masks counted in a bit-sliced adder, compared with the per-field
