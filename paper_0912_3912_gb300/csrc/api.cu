@@ -592,7 +592,7 @@ ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
   cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
   h->n_inst = n_instances;
   h->dtype = dtype;
-  h->dense = dense;
+  h->dense = dense && !hyper;  // hyper-edges on a dense instance: the CSR paths take it
   h->msc_ok = msc;
   h->has_hyper = hyper;
   h->abs_energy_bound = absb;

@@ -25,24 +25,21 @@
 #include <cfloat>
 #include <cstdlib>
 
+#include "dense.cuh"
 #include "device_common.cuh"
 
 namespace isg {
 
 bool dense_tc_eligible(int n);
-cudaError_t dense_tc_run(int n, int R, int Rp, int b, uint64_t seed, const float *J, const __nv_bfloat16 *Jhi,
-                         const __nv_bfloat16 *Jlo, __nv_bfloat16 *S, int8_t *best, int8_t *out, double *E,
-                         int32_t *minima, unsigned long long *stats, int32_t *error,
+cudaError_t dense_tc_run(int n, int R, int Rp, int b, uint64_t seed, const float *J, const float *h,
+                         const __nv_bfloat16 *Jhi, const __nv_bfloat16 *Jlo, __nv_bfloat16 *S, float *Fx,
+                         DenseRep *rep, int sweeps_a, unsigned long long *stats, int32_t *error,
                          const ising_search_params *p, cudaStream_t s);
 
 namespace {
 
-constexpr int kDB = 128;  // spins per block
-
-struct DenseRep {
-  int32_t active, conv, total, minima, d, k, flips, pad;
-  double best, E;
-};
+constexpr int kDB = 128;          // spins per block
+constexpr int kTcSweepsA = 6;     // tensor-core sweeps per round before the per-replica continuation
 
 __global__ void dense_split(const float *J, __nv_bfloat16 *hi, __nv_bfloat16 *lo, int64_t nn) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (int64_t)gridDim.x * blockDim.x) {
@@ -69,8 +66,8 @@ __global__ void dense_start(int32_t n, int32_t R, int32_t Rp, uint64_t seed, int
 
 // In-block sequential decisions, one thread per replica.
 __global__ void __launch_bounds__(256) dense_decide(int32_t n, int32_t R, int32_t Rp, int32_t b0, int32_t bsz,
-                                                    const float *__restrict__ J, const float *__restrict__ F,
-                                                    __nv_bfloat16 *S, DenseRep *rep) {
+                                                    const float *__restrict__ J, const float *__restrict__ hf,
+                                                    const float *__restrict__ F, __nv_bfloat16 *S, DenseRep *rep) {
   extern __shared__ float sJ[];  // [kDB][kDB] block of J
   for (int t = threadIdx.x; t < bsz * bsz; t += blockDim.x) {
     const int a = t / bsz, c = t % bsz;
@@ -84,7 +81,7 @@ __global__ void __launch_bounds__(256) dense_decide(int32_t n, int32_t R, int32_
   for (int q = 0; q < kDB / 32; ++q) flipped[q] = up[q] = 0;
   int nflip = 0;
   for (int i = 0; i < bsz; ++i) {
-    float f = F[(int64_t)i * Rp + r];
+    float f = F[(int64_t)i * Rp + r] + hf[b0 + i];
     const bool s_up = __bfloat162float(S[(int64_t)(b0 + i) * Rp + r]) > 0.0f;
 #pragma unroll
     for (int q = 0; q < kDB / 32; ++q) {
@@ -132,13 +129,16 @@ __global__ void dense_end(int32_t R, int32_t n, int32_t max_sweeps, int32_t budg
   }
 }
 
-// E_r = -1/2 sum_i s_ir F_ir in FP64; then best-state bookkeeping for the round.
-__global__ void dense_energy(int32_t n, int32_t R, int32_t Rp, const __nv_bfloat16 *S, const float *Ff, DenseRep *rep,
-                             int8_t *best, int32_t final_pass) {
+// E_r = -1/2 sum_i s_ir (F_ir + 2 h_i) in FP64 (F without h); then best-state
+// bookkeeping for the round.
+__global__ void dense_energy(int32_t n, int32_t R, int32_t Rp, const __nv_bfloat16 *S, const float *Ff,
+                             const float *hf, DenseRep *rep, int8_t *best, int32_t final_pass) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= R) return;
   double acc = 0.0;
-  for (int i = 0; i < n; ++i) acc += (double)__bfloat162float(S[(int64_t)i * Rp + r]) * (double)Ff[(int64_t)i * Rp + r];
+  for (int i = 0; i < n; ++i)
+    acc += (double)__bfloat162float(S[(int64_t)i * Rp + r]) *
+           ((double)Ff[(int64_t)i * Rp + r] + 2.0 * (double)hf[i]);
   const double E = -0.5 * acc;
   DenseRep &p = rep[r];
   p.E = E;
@@ -172,7 +172,8 @@ __global__ void dense_init(int32_t R, DenseRep *rep, unsigned long long *stats) 
   if (r >= R) return;
   DenseRep p;
   p.active = 1;
-  p.conv = p.total = p.minima = p.d = p.k = p.flips = p.pad = 0;
+  p.conv = p.total = p.minima = p.d = p.k = p.flips = 0;
+  p.round = 1;
   p.best = DBL_MAX;
   p.E = 0.0;
   rep[r] = p;
@@ -180,19 +181,21 @@ __global__ void dense_init(int32_t R, DenseRep *rep, unsigned long long *stats) 
 }
 
 // Returned energies, recomputed from the returned spins with the FP32
-// couplings: F = S J by an FP32 GEMM (library), then E_r = -1/2 sum_i s_i F_ri
-// in FP64, one warp per replica in a fixed order.  The search's own energies
+// couplings: F = S J by an FP32 GEMM (library), then
+// E_r = -1/2 sum_i s_i (F_ri + 2 h_i) in FP64, one warp per replica in a fixed order.  The search's own energies
 // come from its BF16 hi+lo fields, whose error grows with n.
 __global__ void dense_spins_f32(const int8_t *s, float *Sf, int64_t count) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
     Sf[t] = (float)s[t];
 }
 
-__global__ void dense_energy_from_fields(const int8_t *s, const float *F, int32_t n, int32_t R, double *E) {
+__global__ void dense_energy_from_fields(const int8_t *s, const float *F, const float *hf, int32_t n, int32_t R,
+                                         double *E) {
   const int r = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (r >= R) return;
-  double acc = 0.0;
-  for (int i = lane; i < n; i += 32) acc += (double)s[(int64_t)r * n + i] * (double)F[(int64_t)r * n + i];
+  double acc = 0.0;  // sum_i s_i (F_i + 2 h_i), F without h: E = -1/2 acc
+  for (int i = lane; i < n; i += 32)
+    acc += (double)s[(int64_t)r * n + i] * ((double)F[(int64_t)r * n + i] + 2.0 * (double)hf[i]);
   acc = warp_sum(acc);
   if (lane == 0) E[r] = -0.5 * acc;
 }
@@ -213,6 +216,61 @@ __global__ void dense_output(int32_t n, int32_t R, int32_t Rp, int32_t b, int64_
   }
 }
 
+// End of a round of the tensor-core path, one warp per replica (S replica-major,
+// [Rp][n]): count a converged descent, keep its state if it is the best so far
+// (strictly lower energy; ties keep the earlier), then start the next restart
+// unless the restarts or the sweep budget are used up.
+__global__ void dense_round_end(int32_t n, int32_t R, int32_t restarts, int32_t budget, const __nv_bfloat16 *S,
+                                DenseRep *rep, int8_t *best, int32_t *active_count, unsigned long long *stats) {
+  const int r = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (r >= R) return;
+  int copy = 0;
+  if (lane == 0) {
+    DenseRep p = rep[r];
+    if (p.round) {
+      p.round = 0;
+      if (p.conv) {
+        p.minima += 1;
+        atomicAdd(stats + 2, 1ull);
+        if (p.E < p.best) {
+          p.best = p.E;
+          copy = 1;
+        }
+      }
+      p.conv = 0;
+      p.k += 1;
+      if (p.k < restarts && (budget <= 0 || p.total < budget)) {
+        p.active = 1;
+        p.d = 0;
+        p.round = 1;
+        atomicAdd(active_count, 1);
+        atomicAdd(stats + 3, 1ull);
+      }
+      rep[r] = p;
+    }
+  }
+  copy = __shfl_sync(0xffffffffu, copy, 0);
+  if (copy)
+    for (int i = lane; i < n; i += 32)
+      best[(int64_t)r * n + i] = __bfloat162float(S[(int64_t)r * n + i]) > 0.0f ? 1 : -1;
+}
+
+// Results of the tensor-core path: the best converged state, else the final one.
+__global__ void dense_tc_output(int32_t n, int32_t R, const __nv_bfloat16 *S, const int8_t *best,
+                                const DenseRep *rep, int8_t *out, double *E, int32_t *minima) {
+  const int64_t tot = (int64_t)R * n;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / n);
+    out[t] = rep[r].minima > 0 ? best[t] : (__bfloat162float(S[t]) > 0.0f ? 1 : -1);
+  }
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < R) {
+    const DenseRep &p = rep[t];
+    E[t] = p.minima > 0 ? p.best : p.E;
+    if (minima) minima[t] = p.minima;
+  }
+}
+
 struct DenseState {
   cublasHandle_t cublas = nullptr;
   void *workspace = nullptr;
@@ -225,6 +283,7 @@ struct DenseState {
   int32_t *active = nullptr, *h_active = nullptr;
   __nv_bfloat16 *S_tc = nullptr;  // [Rp128][n] replica-major spins for the tcgen05 kernel
   int32_t *err = nullptr, *h_err = nullptr;
+  int32_t *counter = nullptr;          // work counter of the per-replica continuation
   float *Sx = nullptr, *Fx = nullptr;  // [R][n] returned spins and their FP32 fields
 };
 
@@ -245,6 +304,7 @@ void free_state(DenseState &D) {
   cudaFree(D.workspace);
   cudaFree(D.S_tc);
   cudaFree(D.err);
+  cudaFree(D.counter);
   cudaFree(D.Sx);
   cudaFree(D.Fx);
   if (D.h_err) cudaFreeHost(D.h_err);
@@ -268,8 +328,8 @@ bool fields(DenseState &D, int b0, int cnt, float *out) {
   return gemm(D, D.Rp, cnt, n, D.S, D.Rp, D.lo + (int64_t)b0 * n, n, out, D.Rp, 1.0f) == CUBLAS_STATUS_SUCCESS;
 }
 
-cudaError_t exact_energies(DenseState &D, ising_handle *h, int n, int R, const float *J, const int8_t *out,
-                           double *E, cudaStream_t s) {
+cudaError_t exact_energies(DenseState &D, ising_handle *h, int n, int R, const float *J, const float *hf,
+                           const int8_t *out, double *E, cudaStream_t s) {
   cudaError_t e;
   if (!D.Sx) {  // sized for D.Rp >= R replicas; freed with the state when n or Rp changes
     if ((e = cudaMalloc(&D.Sx, (size_t)D.Rp * n * sizeof(float))) != cudaSuccess) return e;
@@ -283,7 +343,7 @@ cudaError_t exact_energies(DenseState &D, ising_handle *h, int n, int R, const f
       cublasGemmEx(D.cublas, CUBLAS_OP_N, CUBLAS_OP_N, n, R, n, &one, J, CUDA_R_32F, n, D.Sx, CUDA_R_32F, n, &zero,
                    D.Fx, CUDA_R_32F, n, CUBLAS_COMPUTE_32F_PEDANTIC, CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
     return cudaErrorUnknown;
-  dense_energy_from_fields<<<(R * 32 + 255) / 256, 256, 0, s>>>(out, D.Fx, n, R, E);
+  dense_energy_from_fields<<<(R * 32 + 255) / 256, 256, 0, s>>>(out, D.Fx, hf, n, R, E);
   h->launches += 2;
   return cudaGetLastError();
 }
@@ -340,26 +400,55 @@ cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t 
     const float *J = h->d_Jdense + joff;
     const uint64_t seed = seeds_host[b];
     const char *force_lib = std::getenv("ISING_DENSE_CUBLAS");
+    const float *hf = reinterpret_cast<const float *>(h->d_h) + h->inst[b].spin_off;
     if (dense_tc_eligible(n) && !(force_lib && force_lib[0] == '1')) {
-      // hand-written tcgen05 kernel: the whole search in one launch
+      // Rounds of: the first sweeps of every replica's descent on tensor cores
+      // (hand-written tcgen05 kernel), then each replica on its own until its
+      // descent ends (incremental updates, CUDA cores), then the round's
+      // bookkeeping.  The host reads one count per round.
       const int Rp128 = (R + 127) / 128 * 128;
       if (!D.S_tc) {
         if ((e = cudaMalloc(&D.S_tc, (size_t)Rp128 * n * 2)) != cudaSuccess) return e;
         if ((e = cudaMemset(D.S_tc, 0, (size_t)Rp128 * n * 2)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&D.err, 64)) != cudaSuccess) return e;
         if ((e = cudaMallocHost(&D.h_err, 64)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&D.counter, 64)) != cudaSuccess) return e;
       }
+      if (!D.Sx) {  // [Rp][n] FP32: exported fields here, returned-energy GEMM operands afterwards
+        if ((e = cudaMalloc(&D.Sx, (size_t)D.Rp * n * sizeof(float))) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&D.Fx, (size_t)D.Rp * n * sizeof(float))) != cudaSuccess) return e;
+      }
+      int sweeps_a = kTcSweepsA;
+      if (const char *v = std::getenv("ISING_DENSE_TC_SWEEPS")) sweeps_a = std::max(0, std::atoi(v));
       if ((e = cudaMemsetAsync(D.err, 0, 4, s)) != cudaSuccess) return e;
-      e = dense_tc_run(n, R, Rp128, b, seed, J, D.hi, D.lo, D.S_tc, D.best, spins + (int64_t)R * h->inst[b].spin_off,
-                       E + (int64_t)b * R, minima ? minima + (int64_t)b * R : nullptr, h->d_stats, D.err, p, s);
-      if (e != cudaSuccess) return e;
+      const int rb = (R + 255) / 256, wb = (R * 32 + 255) / 256;
+      dense_init<<<rb, 256, 0, s>>>(R, D.rep, h->d_stats);
       h->launches += 1;
-      if ((e = cudaMemcpyAsync(D.h_err, D.err, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
-      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-      if (*D.h_err != 0) return cudaErrorLaunchTimeout;
-      if ((e = exact_energies(D, h, n, R, J, spins + (int64_t)R * h->inst[b].spin_off, E + (int64_t)b * R, s)) !=
-          cudaSuccess)
-        return e;
+      for (;;) {
+        e = dense_tc_run(n, R, Rp128, b, seed, J, hf, D.hi, D.lo, D.S_tc, D.Fx, D.rep, sweeps_a, h->d_stats, D.err,
+                         p, s);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(D.counter, 0, 4, s)) != cudaSuccess) return e;
+        e = dense_push_run(n, R, p->max_sweeps, p->sweep_budget, J, hf, D.Fx, D.S_tc, D.rep, D.counter, h->d_stats,
+                           h->sm_count, s);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(D.active, 0, 4, s)) != cudaSuccess) return e;
+        dense_round_end<<<wb, 256, 0, s>>>(n, R, p->restarts, p->sweep_budget, D.S_tc, D.rep, D.best, D.active,
+                                           h->d_stats);
+        h->launches += 3;
+        if ((e = cudaMemcpyAsync(D.h_active, D.active, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(D.h_err, D.err, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+        if (*D.h_err != 0) return cudaErrorLaunchTimeout;
+        if (*D.h_active == 0) break;
+      }
+      int8_t *outb = spins + (int64_t)R * h->inst[b].spin_off;
+      const int64_t tot = (int64_t)R * n;
+      dense_tc_output<<<(int)std::min<int64_t>((tot + 255) / 256, (int64_t)h->sm_count * 16), 256, 0, s>>>(
+          n, R, D.S_tc, D.best, D.rep, outb, E + (int64_t)b * R, minima ? minima + (int64_t)b * R : nullptr);
+      h->launches += 1;
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if ((e = exact_energies(D, h, n, R, J, hf, outb, E + (int64_t)b * R, s)) != cudaSuccess) return e;
       joff += (int64_t)n * n;
       continue;
     }
@@ -378,7 +467,7 @@ cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t 
       for (int b0 = 0; b0 < n && ok; b0 += kDB) {
         const int cnt = std::min(kDB, n - b0);
         ok = fields(D, b0, cnt, D.F);
-        dense_decide<<<rb, 256, kDB * kDB * sizeof(float), cs>>>(n, R, Rp, b0, cnt, J, D.F, D.S, D.rep);
+        dense_decide<<<rb, 256, kDB * kDB * sizeof(float), cs>>>(n, R, Rp, b0, cnt, J, hf, D.F, D.S, D.rep);
       }
       cudaMemsetAsync(D.active, 0, 4, cs);
       dense_end<<<rb, 256, 0, cs>>>(R, n, p->max_sweeps, p->sweep_budget, D.rep, D.active, h->d_stats);
@@ -403,7 +492,7 @@ cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t 
       }
       if (e != cudaSuccess) break;
       fields(D, 0, n, D.Ff);
-      dense_energy<<<rb, 256, 0, s>>>(n, R, Rp, D.S, D.Ff, D.rep, D.best, 0);
+      dense_energy<<<rb, 256, 0, s>>>(n, R, Rp, D.S, D.Ff, hf, D.rep, D.best, 0);
       cudaMemsetAsync(D.active, 0, 4, s);
       dense_next_round<<<rb, 256, 0, s>>>(R, p->restarts, p->sweep_budget, D.rep, D.active, h->d_stats);
       cudaMemcpyAsync(D.h_active, D.active, 4, cudaMemcpyDeviceToHost, s);
@@ -415,12 +504,12 @@ cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t 
     cudaStreamDestroy(cs);
     if (e != cudaSuccess) return e;
     // energies of replicas that never converged: their final states
-    dense_energy<<<rb, 256, 0, s>>>(n, R, Rp, D.S, D.Ff, D.rep, D.best, 1);
+    dense_energy<<<rb, 256, 0, s>>>(n, R, Rp, D.S, D.Ff, hf, D.rep, D.best, 1);
     const int64_t tot = (int64_t)R * n;
     dense_output<<<(int)std::min<int64_t>((tot + 255) / 256, (int64_t)h->sm_count * 16), 256, 0, s>>>(
         n, R, Rp, b, h->inst[b].spin_off, D.S, D.best, D.rep, spins, E, minima);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = exact_energies(D, h, n, R, J, spins + (int64_t)R * h->inst[b].spin_off, E + (int64_t)b * R, s)) !=
+    if ((e = exact_energies(D, h, n, R, J, hf, spins + (int64_t)R * h->inst[b].spin_off, E + (int64_t)b * R, s)) !=
         cudaSuccess)
       return e;
     joff += (int64_t)n * n;

@@ -11,21 +11,27 @@
 // FP32 for the earlier flips inside the block (+2 J_ij s_j): the paper's
 // incremental gain update restricted to the block.
 //
-// Work split: a cluster of 4 CTAs owns 128 replicas for the whole search (all
-// sweeps and restarts in this one launch).  CTA q multiplies the K-slice
+// Work split: a cluster of 4 CTAs owns 128 replicas for the first sweeps of a
+// round (one descent of every replica): the replicas start from their Philox
+// states together and sweep in lockstep.  CTA q multiplies the K-slice
 // j in [q n/4, (q+1) n/4) into its own tensor-memory accumulator; the four
 // partial blocks are exchanged through distributed shared memory and summed in
 // a fixed order; CTA q then decides replicas 32q..32q+31.  Thread 0 of each CTA
 // issues the TMA loads (128-byte swizzled K-major tiles) and the MMAs through a
-// 3-stage mbarrier pipeline.  Every mbarrier wait is bounded; a CTA whose wait
-// gives up records ISING_ERR_TIMEOUT, keeps the cluster's barrier sequence and
-// skips its remaining work, and the cluster ends together at the next sweep.
+// 3-stage mbarrier pipeline.  A last pass without decisions exports the full
+// field vectors of the replicas still descending, which dense_push.cu continues
+// one replica at a time: the first sweeps flip most spins (a GEMM per block is
+// then cheap per flip), the later ones few, and their number varies widely
+// between replicas.  Every mbarrier wait is bounded; a CTA whose wait gives up
+// records ISING_ERR_TIMEOUT, keeps the cluster's barrier sequence and skips its
+// remaining work, and the cluster ends together at the next sweep.
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include <cfloat>
 #include <cstdio>
 
+#include "dense.cuh"
 #include "device_common.cuh"
 #include "tc.cuh"
 
@@ -49,21 +55,16 @@ constexpr int kSmemBytes = kStages * kStageBytes + kPartialBytes + kSbitsBytes +
 
 struct TcArgs {
   int32_t n, R, Rp, b;             // spins, replicas, padded replicas, instance
-  int32_t max_sweeps, restarts, budget;
+  int32_t max_sweeps, budget;      // sweep cap per descent, sweep budget over descents (<= 0: none)
+  int32_t sweeps_a;                // decision sweeps of a round on tensor cores before the export
   uint64_t seed;
   const float *J;                  // [n][n] FP32 (in-block corrections)
+  const float *h;                  // [n] FP32 fields of the spins (zeros allowed)
   __nv_bfloat16 *S;                // [Rp][n] spins +/-1
-  int8_t *best;                    // [R][n]
-  int8_t *out;                     // [R][n] result spins (instance block)
-  double *E;                       // [R] result energies (instance block)
-  int32_t *minima;                 // [R] or null
+  float *Fx;                       // [R][n] exported fields (h included) of replicas still descending
+  DenseRep *rep;                   // [R] per-replica state, read at entry and written back
   unsigned long long *stats;
   int32_t *error;                  // set to ISING_ERR_TIMEOUT when a wait gives up
-};
-
-struct RepState {  // per replica, owned by one thread of warp 0
-  int32_t active, conv, total, minima, d, k, flips, done;
-  double best, E;
 };
 
 // Philox start R(b, r, k) of replica r, written as BF16 +/-1 into S[r][:] and
@@ -78,6 +79,12 @@ __device__ __forceinline__ void write_start_warp(const TcArgs &A, int r, int k, 
   }
 }
 
+// One round's first sweeps on tensor cores.  Every replica taking part starts
+// its descent (restart k) from its Philox state and sweeps in lockstep with the
+// cluster's other replicas for up to sweeps_a sweeps; a final pass then computes
+// every block's fields once more without decisions, giving the energy of each
+// replica's state and, for replicas still descending, their full field vectors
+// (exported to Fx for the per-replica continuation).
 __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
     dense_tc_kernel(const __grid_constant__ CUtensorMap mapS, const __grid_constant__ CUtensorMap mapJhi,
                     const __grid_constant__ CUtensorMap mapJlo, TcArgs A) {
@@ -93,7 +100,7 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
   __shared__ uint32_t tmem_base_s;
   __shared__ int32_t s_flag[2];   // cluster-visible: [0] my replicas still busy, [1] my failure
   __shared__ int32_t s_ctrl[4];   // broadcast inside the CTA
-  __shared__ int32_t s_act[32], s_nfl[32], s_rst[32], s_cpy[32];
+  __shared__ int32_t s_act[32], s_nfl[32], s_run[32];
   __shared__ double s_en[32];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -123,31 +130,48 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
   const uint32_t tmem = tmem_base_s;
 
   // per-replica state: thread t of warp 0 owns replica rq + t
-  RepState st;
   const int my_r = rq + lane;
   const bool real = warp == 0 && my_r < A.R;
-  st.active = real ? 1 : 0;
-  st.conv = st.total = st.minima = st.d = st.k = st.flips = 0;
-  st.done = real ? 0 : 1;
-  st.best = DBL_MAX;
-  st.E = 0.0;
-  unsigned long long c_evals = 0, c_flips = 0, c_minima = 0, c_desc = 0, c_sweeps = 0;
+  // the fields of DenseRep this kernel changes (static shared memory is nearly
+  // all taken by the stages, partials and spin bits)
+  struct TcRep {
+    int32_t active, conv, total, d, flips, round;
+    double E;
+  };
+  __shared__ TcRep s_rep[32];  // warp 0, lane l: replica rq + l
+  TcRep &st = s_rep[lane];
+  if (warp == 0) {
+    st.active = st.conv = st.total = st.d = st.flips = st.round = 0;
+    st.E = 0.0;
+    s_run[lane] = s_nfl[lane] = 0;
+    if (real) {
+      const DenseRep g = A.rep[my_r];
+      st.active = g.active;
+      st.conv = g.conv;
+      st.total = g.total;
+      st.d = g.d;
+      st.round = g.round;
+      st.E = g.E;
+      s_run[lane] = g.round;
+      s_nfl[lane] = g.k;
+    }
+  }
+  unsigned long long c_evals = 0, c_flips = 0, c_sweeps = 0;
   const int nw32 = n / 32;
-  if (rq + warp < A.R) write_start_warp(A, rq + warp, 0, sbits + warp * nw32, lane);
-  if (real) c_desc = 1;
+  __syncthreads();
+  if (rq + warp < A.R && s_run[warp]) write_start_warp(A, rq + warp, s_nfl[warp], sbits + warp * nw32, lane);
   tc::fence_proxy_async_global();
   bool failed = false;
   uint32_t ph_full[kStages] = {0, 0, 0}, ph_empty[kStages] = {0, 0, 0}, ph_done = 0;
   int tma_pending[kStages] = {0, 0, 0}, mma_pending = 0;
   tc::cluster_sync();
 
-  // energy_pass: this "sweep" only accumulates FP64 energies, no decisions
-  for (int guard = 0; guard < (1 << 30); ++guard) {
+  for (int sw = 0; sw <= A.sweeps_a; ++sw) {
     // ---- cluster-wide control: is anybody active?  did anybody fail?
     if (tid == 0) s_flag[0] = 0, s_flag[1] = failed ? 1 : 0;
     __syncthreads();
     if (warp == 0) {
-      const int busy = __any_sync(0xffffffffu, st.active);
+      const int busy = __any_sync(0xffffffffu, st.active != 0);
       if (lane == 0) s_flag[0] = busy;
     }
     __syncthreads();
@@ -164,12 +188,11 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
     tc::cluster_sync();  // nobody rewrites s_flag before every CTA has read it
     const int any_busy = s_ctrl[0], any_bad = s_ctrl[1];
     if (any_bad) break;
-    // A round ends when no replica of the cluster is active: score it, then restart.
-    const bool energy_pass = !any_busy;
-    if (energy_pass) {
-      if (warp == 0) st.E = 0.0;
-    }
-    // ---- one sweep (or energy pass) over the blocks
+    if (sw == 0 && !any_busy) break;  // no replica of the cluster takes part in this round
+    // the export pass: fields and energies of the current states, no decisions
+    const bool export_pass = !any_busy || sw == A.sweeps_a;
+    double e_acc = 0.0;  // warp 0: energy sums of the CTA's replicas over the blocks
+    // ---- one sweep (or the export pass) over the blocks
     for (int blk = 0; blk < nblk; ++blk) {
       const int b0 = blk * kTB;
       // Phase 1: partial fields of the block over this CTA's K-slice.  Thread 0
@@ -253,8 +276,8 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
       tc::tc_fence_before();
       __syncthreads();
       tc::cluster_sync();
-      // Phase 3: sum the four partials (fixed order) for this CTA's 32 replicas,
-      // stage the block's couplings in FP32
+      // Phase 3: sum the four partials (fixed order) and add h for this CTA's 32
+      // replicas, stage the block's couplings in FP32
       if (!failed) {
         for (int e = tid; e < kTB * 8; e += kThreads) {
           const int i = e >> 3, c4 = e & 7;
@@ -266,12 +289,13 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
             acc.z += p.z;
             acc.w += p.w;
           }
-          Floc[(4 * c4 + 0) * kFl + i] = acc.x;
-          Floc[(4 * c4 + 1) * kFl + i] = acc.y;
-          Floc[(4 * c4 + 2) * kFl + i] = acc.z;
-          Floc[(4 * c4 + 3) * kFl + i] = acc.w;
+          const float hv = __ldg(A.h + b0 + i);
+          Floc[(4 * c4 + 0) * kFl + i] = acc.x + hv;
+          Floc[(4 * c4 + 1) * kFl + i] = acc.y + hv;
+          Floc[(4 * c4 + 2) * kFl + i] = acc.z + hv;
+          Floc[(4 * c4 + 3) * kFl + i] = acc.w + hv;
         }
-        if (!energy_pass)
+        if (!export_pass)
           for (int e = tid; e < kTB * kTB / 4; e += kThreads) {
             const int i = e / (kTB / 4), c4 = e % (kTB / 4);
             reinterpret_cast<float4 *>(Jblk)[e] =
@@ -280,8 +304,8 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
       }
       __syncthreads();
       tc::cluster_sync();  // partials consumed: P may be overwritten by the next block
-      // Phase 4: sequential decisions (or energy accumulation).  Warp w decides
-      // replica rq + w; lane l keeps the fields of spins 32q + l (q = 0..3) in
+      // Phase 4: sequential decisions (or the export).  Warp w decides replica
+      // rq + w; lane l keeps the fields of spins 32q + l (q = 0..3) in
       // registers.  Spins are decided in index order; between two flips no field
       // changes, so the warp ballots every current decision of a quarter and
       // jumps to the first flipping spin at or after the current one, flips it,
@@ -300,12 +324,21 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
           if (valid_r) wq[qq] = mybits[qq];
           f[qq] = valid_r ? Floc[warp * kFl + 32 * qq + lane] : 0.0f;
         }
-        if (energy_pass) {
+        if (export_pass) {
+          // E = -1/2 sum_i s_i (f_i + h_i), f including h
           double acc = 0.0;
 #pragma unroll
-          for (int qq = 0; qq < 4; ++qq) acc += (((wq[qq] >> lane) & 1u) ? 1.0 : -1.0) * (double)f[qq];
+          for (int qq = 0; qq < 4; ++qq) {
+            const double v = (double)f[qq] + (double)__ldg(A.h + b0 + 32 * qq + lane);
+            acc += ((wq[qq] >> lane) & 1u) ? v : -v;
+          }
           acc = warp_sum(acc);
           if (lane == 0) s_en[warp] = valid_r ? acc : 0.0;
+          if (valid_r && s_act[warp]) {
+            float *dst = A.Fx + (size_t)rr * n + b0;
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) dst[32 * qq + lane] = f[qq];
+          }
         } else {
           const bool act = valid_r && s_act[warp] != 0;
           int nfl = 0;
@@ -350,8 +383,8 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
       }
       __syncthreads();
       if (warp == 0 && my_r < A.R && !failed) {
-        if (energy_pass) {
-          st.E += s_en[lane];
+        if (export_pass) {
+          e_acc += s_en[lane];
         } else {
           st.flips += s_nfl[lane];
           c_flips += (unsigned long long)s_nfl[lane];
@@ -364,98 +397,40 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
       __syncthreads();
       tc::cluster_sync();  // new spins visible to every CTA's next TMA loads
     }
-    // ---- end of sweep / energy pass: per-replica bookkeeping (warp 0); best
-    // copies and new starts are then written by the replica's own warp
-    if (warp == 0) {
-      s_cpy[lane] = 0;
-      s_rst[lane] = -1;
+    // (a CTA that failed keeps the cluster's barrier sequence; the control step
+    // of the next sweep ends the cluster together)
+    if (export_pass) {
+      if (real && st.round) st.E = -0.5 * e_acc;
+      break;
     }
-    if (warp == 0 && my_r < A.R && !failed) {
-      if (energy_pass) {
-        const double E = -0.5 * st.E;
-        st.E = E;
-        if (!st.done) {
-          if (st.conv) {
-            st.minima += 1;
-            ++c_minima;
-            if (E < st.best) {
-              st.best = E;
-              s_cpy[lane] = 1;
-            }
-          }
-          st.conv = 0;
-          st.k += 1;
-          if (st.k < A.restarts && (A.budget <= 0 || st.total < A.budget)) {
-            st.active = 1;
-            st.d = 0;
-            s_rst[lane] = st.k;
-            ++c_desc;
-          } else {
-            st.done = 1;
-          }
-        }
-      } else if (st.active) {
-        st.total += 1;
-        st.d += 1;
-        c_evals += (unsigned long long)n;
-        ++c_sweeps;
-        const bool conv = st.flips == 0;
-        st.flips = 0;
-        if (conv || st.d >= A.max_sweeps || (A.budget > 0 && st.total >= A.budget)) {
-          st.active = 0;
-          st.conv = conv ? 1 : 0;
-        }
+    // ---- end of sweep: per-replica bookkeeping (warp 0)
+    if (real && st.active) {
+      st.total += 1;
+      st.d += 1;
+      c_evals += (unsigned long long)n;
+      ++c_sweeps;
+      const bool conv = st.flips == 0;
+      st.flips = 0;
+      if (conv || st.d >= A.max_sweeps || (A.budget > 0 && st.total >= A.budget)) {
+        st.active = 0;
+        st.conv = conv ? 1 : 0;
       }
     }
-    __syncthreads();
-    if (energy_pass && rq + warp < A.R && !failed) {
-      const int rr = rq + warp;
-      if (s_cpy[warp]) {
-        const __nv_bfloat16 *row = A.S + (size_t)rr * n;
-        for (int i = lane; i < n; i += 32) A.best[(size_t)rr * n + i] = __bfloat162float(row[i]) > 0.0f ? 1 : -1;
-      }
-      __syncwarp();
-      if (s_rst[warp] >= 0) write_start_warp(A, rr, s_rst[warp], sbits + warp * nw32, lane);
-    }
-    tc::fence_proxy_async_global();
-    __syncthreads();
-    // all done?  (every replica done and no round pending)
-    if (tid == 0) s_flag[0] = 0;
-    __syncthreads();
-    if (warp == 0) {
-      const int pending = __any_sync(0xffffffffu, !st.done);
-      if (lane == 0) s_flag[0] = pending;
-    }
-    __syncthreads();
-    tc::cluster_sync();
-    if (tid == 0) {
-      int pending = 0;
-      for (uint32_t c = 0; c < kClus; ++c) pending |= (int)tc::ld_cluster_u32(tc::map_shared(&s_flag[0], c));
-      s_ctrl[3] = pending;
-    }
-    tc::cluster_sync();
-    if (!s_ctrl[3]) break;
   }
 
-  // results
-  if (warp == 0) s_cpy[lane] = (my_r < A.R && st.minima > 0) ? 1 : 0;
-  __syncthreads();
-  if (rq + warp < A.R) {
-    const int rr = rq + warp;
-    const bool hb = s_cpy[warp] != 0;
-    const __nv_bfloat16 *row = A.S + (size_t)rr * n;
-    for (int i = lane; i < n; i += 32)
-      A.out[(size_t)rr * n + i] = hb ? A.best[(size_t)rr * n + i] : (__bfloat162float(row[i]) > 0.0f ? 1 : -1);
-  }
-  if (warp == 0 && my_r < A.R) {
-    const bool hb = st.minima > 0;
-    A.E[my_r] = hb ? st.best : st.E;
-    if (A.minima) A.minima[my_r] = st.minima;
-    atomicAdd(A.stats + 0, c_evals);
-    atomicAdd(A.stats + 1, c_flips);
-    atomicAdd(A.stats + 2, c_minima);
-    atomicAdd(A.stats + 3, c_desc);
-    atomicAdd(A.stats + 4, c_sweeps);
+  if (real) {
+    DenseRep &g = A.rep[my_r];
+    g.active = st.active;
+    g.conv = st.conv;
+    g.total = st.total;
+    g.d = st.d;
+    g.flips = 0;
+    g.E = st.E;
+    if (c_sweeps) {
+      atomicAdd(A.stats + 0, c_evals);
+      atomicAdd(A.stats + 1, c_flips);
+      atomicAdd(A.stats + 4, c_sweeps);
+    }
   }
   if (failed && tid == 0) {
     atomicExch(A.error, (int32_t)ISING_ERR_TIMEOUT);
@@ -497,10 +472,12 @@ static cudaError_t encode_2d(CUtensorMap *map, const void *base, uint64_t inner,
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// S: [Rp][n] BF16 device buffer (Rp a multiple of 128), Jhi/Jlo [n][n] BF16.
-cudaError_t dense_tc_run(int n, int R, int Rp, int b, uint64_t seed, const float *J, const __nv_bfloat16 *Jhi,
-                         const __nv_bfloat16 *Jlo, __nv_bfloat16 *S, int8_t *best, int8_t *out, double *E,
-                         int32_t *minima, unsigned long long *stats, int32_t *error,
+// One round's tensor-core sweeps (see dense_tc_kernel).  S: [Rp][n] BF16 spins
+// (Rp a multiple of 128), Jhi/Jlo [n][n] BF16, J [n][n] FP32, h [n] FP32,
+// Fx [R][n] FP32 exported fields, rep [R] per-replica state.
+cudaError_t dense_tc_run(int n, int R, int Rp, int b, uint64_t seed, const float *J, const float *h,
+                         const __nv_bfloat16 *Jhi, const __nv_bfloat16 *Jlo, __nv_bfloat16 *S, float *Fx,
+                         DenseRep *rep, int sweeps_a, unsigned long long *stats, int32_t *error,
                          const ising_search_params *p, cudaStream_t s) {
   CUtensorMap mS, mH, mL;
   cudaError_t e;
@@ -513,15 +490,14 @@ cudaError_t dense_tc_run(int n, int R, int Rp, int b, uint64_t seed, const float
   A.Rp = Rp;
   A.b = b;
   A.max_sweeps = p->max_sweeps;
-  A.restarts = p->restarts;
   A.budget = p->sweep_budget;
+  A.sweeps_a = sweeps_a;
   A.seed = seed;
   A.J = J;
+  A.h = h;
   A.S = S;
-  A.best = best;
-  A.out = out;
-  A.E = E;
-  A.minima = minima;
+  A.Fx = Fx;
+  A.rep = rep;
   A.stats = stats;
   A.error = error;
   if ((e = cudaFuncSetAttribute(dense_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)) !=

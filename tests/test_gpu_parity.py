@@ -315,6 +315,97 @@ def test_dense_sk_tcgen05_kernel(n, R, monkeypatch):
     h.close()
 
 
+def _dense_checks(inst, res, R, tol=1e-4):
+    sp = res.spins.view(R, inst.n).cpu().numpy().copy()
+    E = res.energy.view(R).cpu().numpy().copy()
+    oi = oracle.OracleInstance(inst)
+    Eo = oracle.energies(oi, sp)
+    rel = np.abs(E - Eo) / np.maximum(np.abs(Eo), 1.0)
+    assert rel.max() <= 1e-6, rel.max()
+    m = res.minima.view(R).cpu().numpy()
+    for r in np.nonzero(m > 0)[0]:
+        f = oracle.local_fields(oi, sp[r])
+        assert np.all(sp[r] * f >= -tol), f"replica {r} is not a 1-flip minimum"
+    return sp, E, m
+
+
+def _sk_with_fields(n, seed, scale=0.3):
+    inst = W.sk(n, seed=seed)
+    inst.h = (np.random.default_rng(seed).standard_normal(n) * scale).astype(np.float32)
+    return inst
+
+
+@pytest.mark.parametrize("sweeps_a", ["0", "2", "1000"])
+def test_dense_tc_phases_and_fields(sweeps_a, monkeypatch):
+    """The tensor-core path with its first-sweeps/continuation split moved
+    (0: fields exported at once and every sweep continued per replica; 1000:
+    every sweep on tensor cores), on an instance with fields h and a replica
+    count that leaves a partial 128-replica cluster: energies of the returned
+    states, 1-flip minima, work counters, and agreement with the comparator."""
+    monkeypatch.setenv("ISING_DENSE_TC_SWEEPS", sweeps_a)
+    inst = _sk_with_fields(512, 77)
+    R = 160
+    h = isg.Handle([inst])
+    res = h.local_search([31], R, max_sweeps=500, restarts=3, kernel=isg.KERNEL_DENSE_TC)
+    torch.cuda.synchronize()
+    sp, E, m = _dense_checks(inst, res, R)
+    st = dict(res.stats)
+    assert st["minima"] == 3 * R and st["descents"] == 3 * R and np.all(m == 3)
+    assert st["flip_evals"] == st["sweeps"] * inst.n
+    monkeypatch.setenv("ISING_DENSE_CUBLAS", "1")
+    ref = h.local_search([31], R, max_sweeps=500, restarts=3, kernel=isg.KERNEL_DENSE_TC)
+    torch.cuda.synchronize()
+    sp2 = ref.spins.view(R, inst.n).cpu().numpy()
+    assert np.mean(np.all(sp == sp2, axis=1)) >= 0.8
+    assert dict(ref.stats)["minima"] == 3 * R
+    h.close()
+
+
+@pytest.mark.parametrize("sweeps_a", ["0", "4"])
+def test_dense_tc_sweep_cap_and_budget(sweeps_a, monkeypatch):
+    """Descents cut by the sweep cap (inside and after the tensor-core sweeps)
+    return their final states, counted as no minimum; a sweep budget ends every
+    replica after exactly that many sweeps over its restarts."""
+    monkeypatch.setenv("ISING_DENSE_TC_SWEEPS", sweeps_a)
+    inst = _sk_with_fields(256, 78, scale=0.1)
+    R = 64
+    h = isg.Handle([inst])
+    for cap in (1, 3, 6):
+        res = h.local_search([5], R, max_sweeps=cap, restarts=2, kernel=isg.KERNEL_DENSE_TC)
+        torch.cuda.synchronize()
+        sp, E, m = _dense_checks(inst, res, R)
+        st = dict(res.stats)
+        assert st["sweeps"] <= 2 * cap * R and st["descents"] == 2 * R
+        if cap == 1:  # one sweep from a random start never ends at a minimum
+            assert st["minima"] == 0 and np.all(m == 0) and st["sweeps"] == 2 * R
+    res = h.local_search([6], R, max_sweeps=1000, restarts=1 << 20, sweep_budget=37, kernel=isg.KERNEL_DENSE_TC)
+    torch.cuda.synchronize()
+    _dense_checks(inst, res, R)
+    st = dict(res.stats)
+    assert st["sweeps"] == 37 * R and st["minima"] >= R
+    h.close()
+
+
+def test_dense_instance_with_hyper_edges_takes_the_csr_path():
+    """Hyper-edges on a dense instance: the planner routes it to a CSR family,
+    whose results match the oracle's FP32 mirror."""
+    inst = _sk_with_fields(96, 79)
+    inst.hyper_ptr = np.array([0, 3, 5], dtype=np.int64)
+    inst.hyper_members = np.array([1, 7, 50, 3, 90], dtype=np.int32)
+    inst.hyper_J = np.array([0.4, -0.25], dtype=np.float32)
+    h = isg.Handle([inst])
+    assert h.plan_kernel(32) != isg.KERNEL_DENSE_TC
+    h.close()
+    h2 = isg.Handle([inst])
+    res = h2.local_search([3], 32, max_sweeps=200, restarts=2, refresh_every=16, schedule=1)
+    torch.cuda.synchronize()
+    s, Eo, mo, _ = oracle.descent(inst, 3, 0, 32, max_sweeps=200, restarts=2, refresh_every=16,
+                                  schedule=oracle.SCHED_SEQUENTIAL)
+    assert np.array_equal(h2.spins_of(res.spins, 0, 32).cpu().numpy(), s)
+    np.testing.assert_allclose(res.energy[0].cpu().numpy(), Eo, rtol=1e-9, atol=1e-9)
+    h2.close()
+
+
 def test_autotuner_picks_an_eligible_family_and_results_do_not_depend_on_it(tmp_path, monkeypatch):
     monkeypatch.setenv("ISING_TUNE_CACHE", str(tmp_path / "tune.json"))
     inst = W.lattice((12, 12, 12), periodic=True, couplings="pm1", fields="pm1_0", seed=31)
