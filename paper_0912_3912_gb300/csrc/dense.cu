@@ -39,7 +39,7 @@ cudaError_t dense_tc_run(int n, int R, int Rp, int b, uint64_t seed, const float
 namespace {
 
 constexpr int kDB = 128;          // spins per block
-constexpr int kTcSweepsA = 6;     // tensor-core sweeps per round before the per-replica continuation
+constexpr int kTcSweepsA = 3;     // tensor-core sweeps per round before the per-replica continuation
 
 __global__ void dense_split(const float *J, __nv_bfloat16 *hi, __nv_bfloat16 *lo, int64_t nn) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (int64_t)gridDim.x * blockDim.x) {

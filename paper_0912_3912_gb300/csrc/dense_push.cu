@@ -1,18 +1,17 @@
 // dense_push.cu — the late part of a dense descent: the paper's incremental
-// gain update (Sec. IV), one warp per replica on CUDA cores.
+// gain update (Sec. IV), one CTA per replica on CUDA cores.
 //
 // After the first sweeps of a descent on tensor cores (dense_tc.cu) most
 // replicas flip few spins per sweep, and the number of sweeps a replica needs
 // varies widely (for SK n = 4096, from about 20 to over 100).  Recomputing a
 // block's fields as a GEMM costs the same whether one spin or a hundred flip,
 // and in lockstep every replica pays for the slowest one.  Here each replica
-// proceeds on its own: its FP32 fields f_i = h_i + sum_j J_ij s_j live in
-// shared memory, a sweep visits the spins in index order (sequential
-// schedule), and a flip of spin i adds 2 J_ij s_i (s_i the new value) to every
-// field f_j, reading row i of J (row i = column i, J symmetric; J_ii = 0 leaves
-// f_i unchanged).  Fields change only at flips, so the warp evaluates 128
-// spins at once (four 32-spin ballots) and jumps to the first spin that flips;
-// the spins it passes over keep their decisions, as in a one-by-one visit.
+// proceeds on its own (one CTA of 128 threads): its FP32 fields
+// f_i = h_i + sum_j J_ij s_j live in registers (32 per thread at n = 4096), a
+// sweep visits the spins in index order (sequential schedule), and a flip of
+// spin i adds 2 J_ij s_i (s_i the new value) to every field f_j, reading row i
+// of J (row i = column i, J symmetric; J_ii = 0 leaves f_i unchanged).  Per
+// flip only the coupling row moves through the memory system.
 //
 // A replica leaves when a sweep flips nothing (a 1-flip minimum), or at the
 // descent's sweep cap or the sweep budget.  It then records its energy
@@ -30,8 +29,9 @@ namespace isg {
 
 namespace {
 
-constexpr int kMaxWarps = 16;
-constexpr int kBatch = 8;  // coupling-row float4 loads in flight per lane
+constexpr int kThreads = 128;  // one CTA per replica
+constexpr int kSlots = 8;      // most float4 field slots per thread: n <= 4 * kThreads * kSlots = 4096
+constexpr int kNone = 0x7fffffff;
 
 struct PushArgs {
   int32_t n, R, max_sweeps, budget;
@@ -44,95 +44,124 @@ struct PushArgs {
   unsigned long long *stats;
 };
 
-// f_j += c J_ij for all j; c = +/-2, so c J_ij is exact and each field sees one
-// rounding, as when its update is added on its own.
-__device__ __forceinline__ void push_row(float *F, const float *__restrict__ Jrow, float c, int n, int lane) {
-  const float4 *J4 = reinterpret_cast<const float4 *>(Jrow);
-  float4 *F4 = reinterpret_cast<float4 *>(F);
-  const int n4 = n >> 2;  // a multiple of 32 * kBatch when n % 1024 == 0; tail handled below
-  int t = lane;
-  for (; t + 32 * (kBatch - 1) < n4; t += 32 * kBatch) {
-    float4 j[kBatch];
+// Layout: thread t holds, in slot k, the fields and spins of the four spins
+// j = 4 (t + kThreads k) + e, e = 0..3, so slot k of the CTA covers the
+// 512-spin group [512 k, 512 k + 512) in order of (t, e), and a coupling row is
+// read as one coalesced float4 per thread and slot.
+//
+// A sweep visits the groups in order.  In a group every thread evaluates its
+// own four spins (those after the last flip), the CTA takes the first one in
+// index order that flips (the minimum over the threads, exchanged through
+// shared memory at one barrier), and if there is one, every thread adds
+// c J_ij to its fields (c = 2 s_i after the flip: exact, so each field sees one
+// rounding) and the group is evaluated again after spin i.  The spins it
+// passes over keep their decisions, as in a one-by-one visit, because fields
+// change only at flips.
+//
+// NS = slots per thread (groups); GUARD: n is not 512 NS, so the last group is
+// partial and spins j >= n are masked out.
+template <int NS, bool GUARD>
+__global__ void __launch_bounds__(kThreads, 6) dense_push_kernel(PushArgs A) {
+  __shared__ int s_r;
+  __shared__ int s_min[2][kThreads / 32];
+  __shared__ double s_e[kThreads / 32];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int n = A.n;
+  // valid bit 4 k + e: spin 4 (t + kThreads k) + e exists
+  uint32_t valid = 0xffffffffu;
+  if (GUARD) {
+    valid = 0;
 #pragma unroll
-    for (int u = 0; u < kBatch; ++u) j[u] = __ldg(J4 + t + 32 * u);
+    for (int k = 0; k < NS; ++k)
 #pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
-      float4 f = F4[t + 32 * u];
-      f.x = __fmaf_rn(c, j[u].x, f.x);
-      f.y = __fmaf_rn(c, j[u].y, f.y);
-      f.z = __fmaf_rn(c, j[u].z, f.z);
-      f.w = __fmaf_rn(c, j[u].w, f.w);
-      F4[t + 32 * u] = f;
-    }
+      for (int e = 0; e < 4; ++e)
+        if (4 * (t + kThreads * k) + e < n) valid |= 1u << (4 * k + e);
   }
-  for (; t < n4; t += 32) {
-    const float4 j = __ldg(J4 + t);
-    float4 f = F4[t];
-    f.x = __fmaf_rn(c, j.x, f.x);
-    f.y = __fmaf_rn(c, j.y, f.y);
-    f.z = __fmaf_rn(c, j.z, f.z);
-    f.w = __fmaf_rn(c, j.w, f.w);
-    F4[t] = f;
-  }
-}
-
-__global__ void __launch_bounds__(kMaxWarps * 32) dense_push_kernel(PushArgs A) {
-  extern __shared__ float4 smem4[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int n = A.n, nw = n >> 5;
-  float *F = reinterpret_cast<float *>(smem4) + (size_t)warp * (n + nw);  // n fields, then nw spin words
-  uint32_t *bits = reinterpret_cast<uint32_t *>(F + n);
-  unsigned long long c_evals = 0, c_flips = 0, c_sweeps = 0;
+  uint32_t c_sweeps = 0;  // flip evaluations = c_sweeps * n
+  unsigned long long c_flips = 0;
+  int par = 0;  // s_min buffer in use (alternates, so one barrier per exchange suffices)
   for (;;) {
-    int r = 0;
-    if (lane == 0) r = atomicAdd(A.counter, 1);
-    r = __shfl_sync(0xffffffffu, r, 0);
+    if (t == 0) s_r = atomicAdd(A.counter, 1);
+    __syncthreads();
+    const int r = s_r;
+    __syncthreads();  // s_r is rewritten only after every thread has read it
     if (r >= A.R) break;
     DenseRep st = A.rep[r];
     if (!st.active) continue;
-    const float4 *src = reinterpret_cast<const float4 *>(A.F + (size_t)r * n);
-    for (int t = lane; t < (n >> 2); t += 32) reinterpret_cast<float4 *>(F)[t] = src[t];
+    float4 f[NS];
+    uint32_t sb = 0;  // bit 4 k + e: spin 4 (t + kThreads k) + e is +1
+    const float4 *F4 = reinterpret_cast<const float4 *>(A.F + (size_t)r * n);
     __nv_bfloat16 *row = A.S + (size_t)r * n;
-    for (int w = 0; w < nw; ++w) {
-      const uint32_t m = __ballot_sync(0xffffffffu, __bfloat162float(row[32 * w + lane]) > 0.0f);
-      if (lane == 0) bits[w] = m;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      const int j = 4 * (t + kThreads * k);
+      f[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (!GUARD || j < n) {
+        f[k] = F4[t + kThreads * k];
+        const uint2 sv = *reinterpret_cast<const uint2 *>(row + j);  // four BF16 spins
+        // spin e is the BF16 in half e of (sv.x, sv.y); sign bit clear: +1
+        const uint32_t nx = ~sv.x, ny = ~sv.y;
+        const uint32_t up4 = ((nx >> 15) & 1u) | ((nx >> 30) & 2u) | (((ny >> 15) & 1u) << 2) | (((ny >> 31) & 1u) << 3);
+        sb |= up4 << (4 * k);
+      }
     }
-    __syncwarp();
+    sb &= valid;
     for (;;) {  // sweeps
       int nfl = 0;
-      int pos = 0;  // next spin to decide
-      while (pos < n) {
-        const int w0 = pos >> 5;
-        uint32_t mm[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int w = w0 + q;
-          bool dec = false;
-          if (w < nw) {
-            const float f = F[32 * w + lane];
-            dec = ((bits[w] >> lane) & 1u) ? (f < 0.0f) : (f > 0.0f);
+      for (int g = 0; g < NS; ++g) {
+        const int j0 = 4 * (t + kThreads * g);
+        int from = 512 * g;  // first spin of the group still to decide
+        for (;;) {
+          // this thread's first flipping spin of group g at or after `from`:
+          // spin e flips iff its field is nonzero with the sign of its spin
+          // (s_e = +1 and f_e < 0, or s_e = -1 and f_e > 0)
+          const uint32_t upm = (sb >> (4 * g)) & 0xFu;
+          const uint32_t ux = __float_as_uint(f[g].x), uy = __float_as_uint(f[g].y);
+          const uint32_t uz = __float_as_uint(f[g].z), uw = __float_as_uint(f[g].w);
+          const uint32_t sgn = (ux >> 31) | ((uy >> 30) & 2u) | ((uz >> 29) & 4u) | ((uw >> 28) & 8u);
+          const uint32_t nz = ((ux << 1) != 0u ? 1u : 0u) | ((uy << 1) != 0u ? 2u : 0u) |
+                              ((uz << 1) != 0u ? 4u : 0u) | ((uw << 1) != 0u ? 8u : 0u);
+          const int lim = min(max(from - j0, 0), 4);
+          const uint32_t dec = ~(sgn ^ upm) & nz & (0xFu << lim) & (valid >> (4 * g));
+          int cand = kNone;
+          if (dec & 0xFu) {
+            const int e = __ffs(dec) - 1;
+            cand = 2 * (j0 + e) + (int)((upm >> e) & 1u);
           }
-          mm[q] = __ballot_sync(0xffffffffu, dec);
+          // CTA minimum: warp minimum by ballot, then the four warps' minima
+          const uint32_t m = __ballot_sync(0xffffffffu, cand != kNone);
+          const int wmin = m ? __shfl_sync(0xffffffffu, cand, __ffs(m) - 1) : kNone;
+          if (lane == 0) s_min[par][warp] = wmin;
+          __syncthreads();
+          int best = s_min[par][0];
+#pragma unroll
+          for (int w = 1; w < kThreads / 32; ++w) best = min(best, s_min[par][w]);
+          par ^= 1;
+          if (best == kNone) break;
+          const int i = best >> 1;
+          const float c = (best & 1) ? -2.0f : 2.0f;  // 2 s_i after the flip
+          // the owner flips its bit (i lies in group g); everyone adds c J_ij to its fields
+          if (((i >> 2) & (kThreads - 1)) == t) sb ^= 1u << (4 * g + (i & 3));
+          const float4 *J4 = reinterpret_cast<const float4 *>(A.J + (size_t)i * n);
+          float4 jv[NS];
+#pragma unroll
+          for (int k = 0; k < NS; ++k)
+            if (!GUARD || 4 * (t + kThreads * k) < n) jv[k] = __ldg(J4 + t + kThreads * k);
+#pragma unroll
+          for (int k = 0; k < NS; ++k)
+            if (!GUARD || 4 * (t + kThreads * k) < n) {
+              f[k].x = __fmaf_rn(c, jv[k].x, f[k].x);
+              f[k].y = __fmaf_rn(c, jv[k].y, f[k].y);
+              f[k].z = __fmaf_rn(c, jv[k].z, f[k].z);
+              f[k].w = __fmaf_rn(c, jv[k].w, f[k].w);
+            }
+          ++nfl;
+          from = i + 1;
         }
-        mm[0] &= 0xffffffffu << (pos & 31);
-        int q = 0;
-        while (q < 4 && !mm[q]) ++q;
-        if (q == 4) {
-          pos = 32 * (w0 + 4);
-          continue;
-        }
-        const int w = w0 + q, li = __ffs(mm[q]) - 1, i = 32 * w + li;
-        const bool was_up = (bits[w] >> li) & 1u;
-        __syncwarp();
-        if (lane == 0) bits[w] ^= 1u << li;
-        push_row(F, A.J + (size_t)i * n, was_up ? -2.0f : 2.0f, n, lane);
-        __syncwarp();
-        ++nfl;
-        pos = i + 1;
       }
       st.d += 1;
       st.total += 1;
-      c_evals += (unsigned long long)n;
       c_sweeps += 1;
       c_flips += (unsigned long long)nfl;
       if (nfl == 0 || st.d >= A.max_sweeps || (A.budget > 0 && st.total >= A.budget)) {
@@ -141,24 +170,57 @@ __global__ void __launch_bounds__(kMaxWarps * 32) dense_push_kernel(PushArgs A) 
         break;
       }
     }
+    // E = -1/2 sum_i s_i (f_i + h_i): per-thread sums, then warps, then the CTA
+    // in a fixed order; spins written back
     double acc = 0.0;
-    for (int i = lane; i < n; i += 32) {
-      const bool up = (bits[i >> 5] >> lane) & 1u;
-      const double v = (double)F[i] + (double)__ldg(A.h + i);
-      acc += up ? v : -v;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      const int j = 4 * (t + kThreads * k);
+      if (!GUARD || j < n) {
+        const float4 hv = *reinterpret_cast<const float4 *>(A.h + j);
+        const float fv[4] = {f[k].x, f[k].y, f[k].z, f[k].w}, hh[4] = {hv.x, hv.y, hv.z, hv.w};
+        uint32_t w[2] = {0u, 0u};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const bool up = (sb >> (4 * k + e)) & 1u;
+          const double v = (double)fv[e] + (double)hh[e];
+          acc += up ? v : -v;
+          w[e >> 1] |= (uint32_t)(up ? 0x3F80u : 0xBF80u) << (16 * (e & 1));  // BF16 +1 / -1
+        }
+        *reinterpret_cast<uint2 *>(row + j) = make_uint2(w[0], w[1]);
+      }
     }
     acc = warp_sum(acc);
-    st.E = -0.5 * acc;
-    for (int i = lane; i < n; i += 32)
-      row[i] = __float2bfloat16_rn(((bits[i >> 5] >> lane) & 1u) ? 1.0f : -1.0f);
-    if (lane == 0) A.rep[r] = st;
-    __syncwarp();
+    if (lane == 0) s_e[warp] = acc;
+    __syncthreads();
+    if (t == 0) {
+      double e = 0.0;
+      for (int w = 0; w < kThreads / 32; ++w) e += s_e[w];
+      st.E = -0.5 * e;
+      A.rep[r] = st;
+    }
   }
-  if (lane == 0 && c_sweeps) {
-    atomicAdd(A.stats + 0, c_evals);
+  if (t == 0 && c_sweeps) {
+    atomicAdd(A.stats + 0, (unsigned long long)c_sweeps * (unsigned long long)n);
     atomicAdd(A.stats + 1, c_flips);
-    atomicAdd(A.stats + 4, c_sweeps);
+    atomicAdd(A.stats + 4, (unsigned long long)c_sweeps);
   }
+}
+
+template <int NS, bool GUARD>
+cudaError_t launch_push(const PushArgs &A, int sm_count, cudaStream_t s) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense_push_kernel<NS, GUARD>, kThreads, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int grid = std::max(1, std::min(sm_count * per_sm, A.R));
+  dense_push_kernel<NS, GUARD><<<grid, kThreads, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+template <int NS>
+cudaError_t launch_push_ns(const PushArgs &A, int sm_count, cudaStream_t s) {
+  return A.n == 4 * kThreads * NS ? launch_push<NS, false>(A, sm_count, s) : launch_push<NS, true>(A, sm_count, s);
 }
 
 }  // namespace
@@ -166,23 +228,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) dense_push_kernel(PushArgs A) 
 cudaError_t dense_push_run(int n, int R, int max_sweeps, int budget, const float *J, const float *h, const float *F,
                            __nv_bfloat16 *S, DenseRep *rep, int32_t *counter, unsigned long long *stats, int sm_count,
                            cudaStream_t s) {
-  if (n % 32 != 0 || n < 32) return cudaErrorInvalidValue;
-  const size_t per_warp = (size_t)(n + n / 32) * sizeof(float);
-  int dev = 0, smem_max = 0;
-  cudaError_t e;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-  if ((e = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
-  const int warps = (int)std::min<size_t>(kMaxWarps, (size_t)smem_max / per_warp);
-  if (warps < 1) return cudaErrorInvalidValue;
-  const size_t smem = per_warp * warps;
-  if ((e = cudaFuncSetAttribute(dense_push_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-      cudaSuccess)
-    return e;
-  int per_sm = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense_push_kernel, warps * 32, smem)) !=
-      cudaSuccess)
-    return e;
-  const int grid = std::max(1, std::min(sm_count * std::max(per_sm, 1), (R + warps - 1) / warps));
+  // whole float4 groups, 16-byte aligned rows, fields in registers: n % 4 == 0, n <= 4096
+  if (n % 4 != 0 || n < 4 || n > 4 * kThreads * kSlots) return cudaErrorInvalidValue;
   PushArgs A;
   A.n = n;
   A.R = R;
@@ -195,8 +242,16 @@ cudaError_t dense_push_run(int n, int R, int max_sweeps, int budget, const float
   A.rep = rep;
   A.counter = counter;
   A.stats = stats;
-  dense_push_kernel<<<grid, warps * 32, smem, s>>>(A);
-  return cudaGetLastError();
+  switch ((n + 4 * kThreads - 1) / (4 * kThreads)) {
+    case 1: return launch_push_ns<1>(A, sm_count, s);
+    case 2: return launch_push_ns<2>(A, sm_count, s);
+    case 3: return launch_push_ns<3>(A, sm_count, s);
+    case 4: return launch_push_ns<4>(A, sm_count, s);
+    case 5: return launch_push_ns<5>(A, sm_count, s);
+    case 6: return launch_push_ns<6>(A, sm_count, s);
+    case 7: return launch_push_ns<7>(A, sm_count, s);
+    default: return launch_push_ns<8>(A, sm_count, s);
+  }
 }
 
 }  // namespace isg
