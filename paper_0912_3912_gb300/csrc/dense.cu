@@ -24,6 +24,7 @@
 
 #include <cfloat>
 #include <cstdlib>
+#include <cstring>
 
 #include "dense.cuh"
 #include "device_common.cuh"
@@ -337,11 +338,21 @@ cudaError_t exact_energies(DenseState &D, ising_handle *h, int n, int R, const f
   }
   const int64_t tot = (int64_t)R * n;
   dense_spins_f32<<<(int)std::min<int64_t>((tot + 255) / 256, (int64_t)h->sm_count * 16), 256, 0, s>>>(out, D.Sx, tot);
-  // column-major view: F^T (n x R) = J (n x n, symmetric) . S^T (n x R); FP32 compute, no TF32
+  // column-major view: F^T (n x R) = J (n x n, symmetric) . S^T (n x R).  FP32
+  // accuracy: by default the library's BF16x9 emulation of FP32 on tensor cores
+  // (each operand split exactly into three BF16 terms), else plain FP32 SIMT
+  // (ISING_DENSE_ENERGY_GEMM=fp32); never TF32.
+  static const bool simt = [] {
+    const char *v = std::getenv("ISING_DENSE_ENERGY_GEMM");
+    return v && std::strcmp(v, "fp32") == 0;
+  }();
   const float one = 1.0f, zero = 0.0f;
-  if (cublasSetStream(D.cublas, s) != CUBLAS_STATUS_SUCCESS ||
-      cublasGemmEx(D.cublas, CUBLAS_OP_N, CUBLAS_OP_N, n, R, n, &one, J, CUDA_R_32F, n, D.Sx, CUDA_R_32F, n, &zero,
-                   D.Fx, CUDA_R_32F, n, CUBLAS_COMPUTE_32F_PEDANTIC, CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
+  if (cublasSetStream(D.cublas, s) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+  if (!simt && cublasSetEmulationStrategy(D.cublas, CUBLAS_EMULATION_STRATEGY_EAGER) != CUBLAS_STATUS_SUCCESS)
+    return cudaErrorUnknown;
+  if (cublasGemmEx(D.cublas, CUBLAS_OP_N, CUBLAS_OP_N, n, R, n, &one, J, CUDA_R_32F, n, D.Sx, CUDA_R_32F, n, &zero,
+                   D.Fx, CUDA_R_32F, n, simt ? CUBLAS_COMPUTE_32F_PEDANTIC : CUBLAS_COMPUTE_32F_EMULATED_16BFX9,
+                   CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
     return cudaErrorUnknown;
   dense_energy_from_fields<<<(R * 32 + 255) / 256, 256, 0, s>>>(out, D.Fx, hf, n, R, E);
   h->launches += 2;
