@@ -266,6 +266,7 @@ def main():
     if dist is not None:
         dist.barrier()
     clocks = ClockSampler(dev.index)
+    h.set_timing(True)            # per-kernel CUDA events inside the library, over the timed steps
     torch.cuda.synchronize()
     ev_pairs = []
     for _ in range(args.steps):
@@ -277,6 +278,8 @@ def main():
         ev_pairs.append((a, b))
     torch.cuda.synchronize()
     clk = clocks.stop()
+    ktimes = h.kernel_times()
+    h.set_timing(False)
     ms = [a.elapsed_time(b) for a, b in ev_pairs]
     t_total, evals_job, minima_job = job_totals(sum(ms) / 1e3, st["flip_evals"] * args.steps,
                                                 st["minima"] * args.steps, dist, dev)
@@ -304,7 +307,8 @@ def main():
     eff_kernel = chosen
     if chosen == isg.KERNEL_MSC or (chosen == isg.KERNEL_SWEEP and insts[0].dtype == "i8"):
         eff_kernel = 2 if chosen == isg.KERNEL_MSC else 3
-    roof = roofline(args.workload, eff_kernel, insts, R, st, t_total / args.steps, clk, hbm, bf16s, peak_src)
+    roof = roofline(args.workload, eff_kernel, insts, R, st, t_total / args.steps, clk, hbm, bf16s, peak_src,
+                    ktimes, args.steps)
     st = {k: v for k, v in st.items() if k != "launches"}
 
     # equal-energy comparison with the plain comparator kernel
@@ -375,11 +379,32 @@ def main():
         dist.destroy_process_group()
 
 
-def roofline(name, kernel, insts, R, st, step_s, clk, hbm, bf16s, src):
-    """Roofline of the step's dominant kernel.  The algorithmic work per unit is
-    the method's own (not the kernel's instruction count).  The time is the whole
-    step measured with CUDA events, so `achieved` is a lower bound for the
-    dominant kernel alone."""
+def roofline(name, kernel, insts, R, st, step_s, clk, hbm, bf16s, src, ktimes=None, steps=1):
+    """Roofline of the step's main kernel.  The algorithmic work per unit is the
+    method's own (not the kernel's instruction count).  The time is that
+    kernel's device time over the timed steps, from the CUDA events the library
+    records around its launches (ising_set_timing); where none were recorded,
+    the whole step's time (a lower bound for the kernel alone)."""
+    out = _roofline(name, kernel, insts, R, st, step_s, clk, hbm, bf16s, src)
+    kname = out.get("kernel")
+    if kname == "tile_kernel" and ktimes and kname not in ktimes and "msc_cluster_kernel" in ktimes:
+        kname = out["kernel"] = "msc_cluster_kernel"  # the lattice tiles split over CTA clusters
+    if ktimes and kname in ktimes and ktimes[kname][0] > 0:
+        k_s = ktimes[kname][0] / 1e3 / steps
+        scale = step_s / k_s
+        out["achieved"] *= scale
+        out["frac"] *= scale
+        out["time_basis"] = f"{kname}: CUDA events around its launches, {ktimes[kname][1] // max(1, steps)} per step"
+        out["kernel_ms_per_step"] = k_s * 1e3
+        out["kernel_share_of_step"] = k_s / step_s
+    else:
+        out["time_basis"] = "whole step (CUDA events)"
+    if ktimes:
+        out["kernels_ms_per_step"] = {k: v[0] / steps for k, v in ktimes.items()}
+    return out
+
+
+def _roofline(name, kernel, insts, R, st, step_s, clk, hbm, bf16s, src):
     sm_count = 152
     mhz = (clk or {}).get("sm_mhz") or 2070.0
     inst = insts[0]
@@ -396,8 +421,9 @@ def roofline(name, kernel, insts, R, st, step_s, clk, hbm, bf16s, src):
         words = st["flip_evals"] / lanes
         achieved = words * ops / step_s / 1e12
         peak = sm_count * 128 * mhz * 1e6 / 1e12
+        kname = "sweep_chunk" if kernel == 3 else "tile_kernel"
         return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlane-ops/s", "frac": achieved / peak,
-                "traffic": None, "ops_per_word": ops, "replicas_per_word": lanes,
+                "traffic": None, "kernel": kname, "ops_per_word": ops, "replicas_per_word": lanes,
                 "peak_source": f"derived: {sm_count} SMs x 128 integer lanes x {mhz:.0f} MHz (median SM clock under load)"}
     if kernel == 4:
         # Tensor-core work actually done: each descent's first sweeps (the
@@ -417,7 +443,8 @@ def roofline(name, kernel, insts, R, st, step_s, clk, hbm, bf16s, src):
     byts = st["flip_evals"] * 4.125 + st["flips"] * deg * 16.0
     achieved = byts / step_s / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": None, "bytes_per_step": byts, "peak_source": f"{src} copy bandwidth (MEASURED_PEAKS.json)"}
+            "traffic": None, "kernel": "sweep_chunk" if kernel == 3 else "tile_kernel", "bytes_per_step": byts,
+            "peak_source": f"{src} copy bandwidth (MEASURED_PEAKS.json)"}
 
 
 if __name__ == "__main__":

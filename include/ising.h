@@ -228,6 +228,25 @@ ising_status ising_energy_noalloc(int32_t n, const int64_t *row_ptr_dev, const i
                                   const int8_t *spins_dev, int32_t replicas, double *energy_dev,
                                   cudaStream_t stream);
 
+/* Device timing of the kernels a search runs, for measurement.
+ * ising_set_timing(h, 1) opens a timing window (clearing the previous one);
+ * while it is open every ising_local_search call records a pair of CUDA events
+ * on its stream around each of its main kernel launches (a family's main
+ * kernel, or a graph of them: "tile_kernel", "msc_cluster_kernel",
+ * "sweep_chunk", "dense_tc_kernel", "dense_push_kernel", "dense_energy_gemm",
+ * "plain_path").  ising_set_timing(h, 0) stops recording.
+ * ising_kernel_times waits for the recorded events and writes up to cap
+ * entries {name, total ms, launches} summed over the window, in order of first
+ * launch; it returns the number of distinct names (which may exceed cap), or
+ * a negative ising_status.  name points to a static string of the library.    */
+typedef struct {
+  const char *name;
+  double ms;
+  int32_t launches;
+} ising_kernel_time;
+ising_status ising_set_timing(ising_handle *h, int32_t enable);
+int32_t ising_kernel_times(ising_handle *h, ising_kernel_time *out, int32_t cap);
+
 /* Free everything the handle owns.  ising_destroy(NULL) returns ISING_OK.      */
 ising_status ising_destroy(ising_handle *h);
 

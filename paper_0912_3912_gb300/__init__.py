@@ -52,6 +52,10 @@ class _Stats(C.Structure):
                 ("descents", C.c_uint64), ("sweeps", C.c_uint64), ("launches", C.c_uint64)]
 
 
+class _KTime(C.Structure):
+    _fields_ = [("name", C.c_char_p), ("ms", C.c_double), ("launches", C.c_int32)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -80,6 +84,10 @@ def lib():
             L.ising_destroy.restype = i32
             L.ising_energy_noalloc.argtypes = [i32, vp, vp, vp, vp, i32, vp, i32, vp, vp]
             L.ising_energy_noalloc.restype = i32
+            L.ising_set_timing.argtypes = [vp, i32]
+            L.ising_set_timing.restype = i32
+            L.ising_kernel_times.argtypes = [vp, vp, i32]
+            L.ising_kernel_times.restype = i32
             L.ising_status_string.argtypes = [i32]
             L.ising_status_string.restype = C.c_char_p
             _lib = L
@@ -87,7 +95,8 @@ def lib():
 
 
 EXPORTED = ("ising_create", "ising_energy", "ising_local_search", "ising_plan_kernel",
-            "ising_autotune", "ising_destroy", "ising_status_string", "ising_energy_noalloc")
+            "ising_autotune", "ising_destroy", "ising_status_string", "ising_energy_noalloc",
+            "ising_set_timing", "ising_kernel_times")
 
 
 def _check(code: int, where: str):
@@ -215,6 +224,18 @@ class Handle:
         _check(lib().ising_autotune(self._h, replicas, C.byref(p), C.byref(ch), self._stream(stream)),
                "ising_autotune")
         return ch.value
+
+    def set_timing(self, enable: bool) -> None:
+        """Open (and clear) or close the device-timing window (ising_set_timing)."""
+        _check(lib().ising_set_timing(self._h, 1 if enable else 0), "ising_set_timing")
+
+    def kernel_times(self) -> dict:
+        """{kernel name: (total ms, launches)} over the timing window."""
+        buf = (_KTime * 16)()
+        k = lib().ising_kernel_times(self._h, buf, 16)
+        if k < 0:
+            raise IsingError(-k, "ising_kernel_times")
+        return {buf[i].name.decode(): (buf[i].ms, int(buf[i].launches)) for i in range(min(k, 16))}
 
     def spins_of(self, result_spins, b: int, replicas: int):
         """View of instance b's block as [replicas, n_b]."""

@@ -289,6 +289,10 @@ void free_handle(ising_handle *h) {
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(h->device);
+  for (auto &t : h->ktimers) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
   energy_plan_free(h);
   sweep_free(h);
   dense_free(h);
@@ -428,7 +432,9 @@ ising_status run_tile(ising_handle *h, int mode, int32_t R, const ising_search_p
     a.minima = minima;
     a.stats = h->d_stats;
     CUDA_OK(cudaMemcpyAsync(h->d_tile_args, &a, sizeof(a), cudaMemcpyHostToDevice, s));
+    kt_begin(h, "msc_cluster_kernel", s);
     CUDA_OK(launch_msc_cluster(h, h->n_tiles, P, h->nmax / P, h->inst[0].lat_d, s));
+    kt_end(h, s);
     h->launches += 1;
     return ISING_OK;
   }
@@ -493,7 +499,9 @@ ising_status run_tile(ising_handle *h, int mode, int32_t R, const ising_search_p
     h->tile_exec_key[1] = grid;
     h->tile_exec_key[2] = (int32_t)smem;
   }
+  kt_begin(h, "tile_kernel", s);
   CUDA_OK(cudaGraphLaunch(h->tile_exec, s));
+  kt_end(h, s);
   h->launches += 1;
   return ISING_OK;
 }
@@ -554,6 +562,31 @@ void tune_cache_store(const std::string &key, int32_t fam) {
 }
 
 }  // namespace
+
+namespace isg {
+
+void kt_begin(ising_handle *h, const char *name, cudaStream_t s) {
+  if (!h->timing) return;
+  if (h->kt_used == h->ktimers.size()) {
+    ising_handle::KTimer t{name, nullptr, nullptr};
+    if (cudaEventCreate(&t.a) != cudaSuccess) return;
+    if (cudaEventCreate(&t.b) != cudaSuccess) {
+      cudaEventDestroy(t.a);
+      return;
+    }
+    h->ktimers.push_back(t);
+  }
+  h->ktimers[h->kt_used].name = name;
+  cudaEventRecord(h->ktimers[h->kt_used].a, s);
+}
+
+void kt_end(ising_handle *h, cudaStream_t s) {
+  if (!h->timing || h->kt_used == h->ktimers.size()) return;  // (begin could not create its events)
+  cudaEventRecord(h->ktimers[h->kt_used].b, s);
+  ++h->kt_used;
+}
+
+}  // namespace isg
 
 extern "C" {
 
@@ -853,9 +886,11 @@ ising_status ising_local_search(ising_handle *h, const uint64_t *seeds, int32_t 
           st = ISING_ERR_CUDA;
         break;
       case ISING_KERNEL_PLAIN:
+        kt_begin(h, "plain_path", stream);
         if (launch_plain(h, p, replicas, spins_dev, energy_dev, energy_i32_dev, minima_dev, seeds, stream) !=
             cudaSuccess)
           st = ISING_ERR_CUDA;
+        kt_end(h, stream);
         break;
       default:
         st = ISING_ERR_UNSUPPORTED;
@@ -950,6 +985,33 @@ ising_status ising_autotune(ising_handle *h, int32_t replicas, const ising_searc
 ising_status ising_destroy(ising_handle *h) {
   free_handle(h);
   return ISING_OK;
+}
+
+ising_status ising_set_timing(ising_handle *h, int32_t enable) {
+  if (!h) return ISING_ERR_INVALID_ARG;
+  if (enable && h->kt_used && cudaEventSynchronize(h->ktimers[h->kt_used - 1].b) != cudaSuccess)
+    return ISING_ERR_CUDA;
+  h->timing = enable != 0;
+  if (enable) h->kt_used = 0;
+  return ISING_OK;
+}
+
+int32_t ising_kernel_times(ising_handle *h, ising_kernel_time *out, int32_t cap) {
+  if (!h || cap < 0 || (cap > 0 && !out)) return -(int32_t)ISING_ERR_INVALID_ARG;
+  std::vector<ising_kernel_time> acc;
+  for (size_t i = 0; i < h->kt_used; ++i) {
+    const auto &t = h->ktimers[i];
+    float ms = 0.0f;
+    if (cudaEventSynchronize(t.b) != cudaSuccess || cudaEventElapsedTime(&ms, t.a, t.b) != cudaSuccess)
+      return -(int32_t)ISING_ERR_CUDA;
+    size_t k = 0;
+    while (k < acc.size() && std::strcmp(acc[k].name, t.name) != 0) ++k;
+    if (k == acc.size()) acc.push_back(ising_kernel_time{t.name, 0.0, 0});
+    acc[k].ms += (double)ms;
+    acc[k].launches += 1;
+  }
+  for (size_t k = 0; k < acc.size() && (int32_t)k < cap; ++k) out[k] = acc[k];
+  return (int32_t)acc.size();
 }
 
 const char *ising_status_string(ising_status s) {

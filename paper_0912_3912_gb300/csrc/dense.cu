@@ -436,12 +436,16 @@ cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t 
       dense_init<<<rb, 256, 0, s>>>(R, D.rep, h->d_stats);
       h->launches += 1;
       for (;;) {
+        kt_begin(h, "dense_tc_kernel", s);
         e = dense_tc_run(n, R, Rp128, b, seed, J, hf, D.hi, D.lo, D.S_tc, D.Fx, D.rep, sweeps_a, h->d_stats, D.err,
                          p, s);
+        kt_end(h, s);
         if (e != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(D.counter, 0, 4, s)) != cudaSuccess) return e;
+        kt_begin(h, "dense_push_kernel", s);
         e = dense_push_run(n, R, p->max_sweeps, p->sweep_budget, J, hf, D.Fx, D.S_tc, D.rep, D.counter, h->d_stats,
                            h->sm_count, s);
+        kt_end(h, s);
         if (e != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(D.active, 0, 4, s)) != cudaSuccess) return e;
         dense_round_end<<<wb, 256, 0, s>>>(n, R, p->restarts, p->sweep_budget, D.S_tc, D.rep, D.best, D.active,
@@ -459,7 +463,10 @@ cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t 
           n, R, D.S_tc, D.best, D.rep, outb, E + (int64_t)b * R, minima ? minima + (int64_t)b * R : nullptr);
       h->launches += 1;
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      if ((e = exact_energies(D, h, n, R, J, hf, outb, E + (int64_t)b * R, s)) != cudaSuccess) return e;
+      kt_begin(h, "dense_energy_gemm", s);
+      e = exact_energies(D, h, n, R, J, hf, outb, E + (int64_t)b * R, s);
+      kt_end(h, s);
+      if (e != cudaSuccess) return e;
       joff += (int64_t)n * n;
       continue;
     }

@@ -158,10 +158,22 @@ struct ising_handle {
   int32_t tile_exec_key[3] = {-1, -1, -1};
   ising_status latched = ISING_OK;
   uint64_t launches = 0;  // kernel launches enqueued by the current call
+  // Optional device timing (ising_set_timing): CUDA events recorded on the
+  // call's stream around each main kernel launch (or graph of launches).
+  struct KTimer {
+    const char *name;
+    cudaEvent_t a, b;
+  };
+  bool timing = false;
+  std::vector<KTimer> ktimers;
+  size_t kt_used = 0;
   isg::DevGraph graph() const;
 };
 
 namespace isg {
+// device timing around a launch (no-ops unless timing is on); name: a static string
+void kt_begin(ising_handle *h, const char *name, cudaStream_t s);
+void kt_end(ising_handle *h, cudaStream_t s);
 // launchers (tile.cu / energy.cu / plain.cu / sweep.cu / dense.cu)
 cudaError_t launch_tile(ising_handle *h, int mode, int grid, size_t smem, cudaStream_t s);
 size_t tile_smem_bytes(int mode, int nmax);

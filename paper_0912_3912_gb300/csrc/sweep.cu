@@ -1278,12 +1278,14 @@ cudaError_t run_instance(ising_handle *h, SweepArgs A, int mode, cudaStream_t s)
   for (;;) {
     // sweeps k = 0, 2, 4, ... of a captured chunk have no round-end kernels
     h->launches += (uint64_t)chunk * per_sweep - (use_graph && chunk > 1 ? (uint64_t)((chunk + 1) / 2) * 2 : 0);
+    kt_begin(h, "sweep_chunk", s);
     if (use_graph) {
       if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) break;
     } else {
       enqueue_sweep<LPS, LAT>(A, mode, ncls, grid_v, s);
       if ((e = cudaGetLastError()) != cudaSuccess) break;
     }
+    kt_end(h, s);
     cudaMemcpyAsync(S.h_done + (launched & 1), A.all_done, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     cudaEventRecord(S.ev[launched & 1], s);
     ++launched;

@@ -447,3 +447,35 @@ def test_msc_lattice_cluster_mixed_sizes():
     insts = [W.lattice((32, 32, 32), periodic=True, couplings="pm1", fields="pm1_0", seed=41),
              W.lattice((16, 16, 16), periodic=True, couplings="pm1", seed=42)]
     _compare(insts, [41, 42], 45, True, max_sweeps=200, restarts=3, kernel=isg.KERNEL_MSC)
+
+
+def test_kernel_timing_window():
+    """ising_set_timing / ising_kernel_times: names of the kernels a family ran,
+    positive device times, one timed group per launch, nothing recorded once
+    the window is closed, and results unchanged by the events."""
+    inst = W.sk(512, seed=90)
+    R = 128
+    h = isg.Handle([inst])
+    ref = h.local_search([4], R, max_sweeps=200, kernel=isg.KERNEL_DENSE_TC)
+    torch.cuda.synchronize()
+    sp_ref = ref.spins.cpu().numpy().copy()
+    h.set_timing(True)
+    for _ in range(2):
+        res = h.local_search([4], R, max_sweeps=200, kernel=isg.KERNEL_DENSE_TC)
+    kt = h.kernel_times()
+    h.set_timing(False)
+    assert np.array_equal(res.spins.cpu().numpy(), sp_ref)
+    assert set(kt) == {"dense_tc_kernel", "dense_push_kernel", "dense_energy_gemm"}, kt
+    for name, (ms, launches) in kt.items():
+        assert ms > 0.0 and launches == 2, (name, ms, launches)
+    h.local_search([4], R, max_sweeps=200, kernel=isg.KERNEL_DENSE_TC)
+    assert h.kernel_times() == kt or all(h.kernel_times()[k][1] == 2 for k in kt)
+    h.close()
+    lat = W.lattice((12, 12, 12), periodic=True, couplings="pm1", seed=91)
+    h2 = isg.Handle([lat])
+    h2.set_timing(True)
+    h2.local_search([5], 64, max_sweeps=100, restarts=2, kernel=isg.KERNEL_SWEEP)
+    h2.local_search([5], 64, max_sweeps=100, restarts=2, kernel=isg.KERNEL_TILE)
+    kt2 = h2.kernel_times()
+    assert kt2["sweep_chunk"][1] >= 1 and kt2["tile_kernel"][1] == 1
+    h2.close()

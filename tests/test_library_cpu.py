@@ -41,6 +41,12 @@ def test_library_exports_every_declared_function(isg):
     assert set(names) == set(isg.EXPORTED)
 
 
+def test_timing_entry_points_reject_a_null_handle(isg):
+    L = isg.lib()
+    assert L.ising_set_timing(None, 1) == 1          # ISING_ERR_INVALID_ARG
+    assert L.ising_kernel_times(None, None, 0) == -1
+
+
 def test_status_strings(isg):
     assert isg.status_string(0) == "ok"
     assert "symmetric" in isg.status_string(2)
