@@ -1,8 +1,11 @@
 // dense.cu — fully connected instances (Sherrington-Kirkpatrick): the
-// sequential schedule with fields computed on tensor cores.  Dispatches to the
-// hand-written tcgen05 kernel (dense_tc.cu) where it applies; the block search
-// below, with its GEMMs in cuBLAS, is the comparator and the fallback for
-// other sizes.
+// sequential schedule with fields computed on tensor cores.  Where the
+// hand-written kernels apply (n a multiple of 256, at most 4096) a round of the
+// search is: the first sweeps of every replica's descent in lockstep on tcgen05
+// (dense_tc.cu), each replica's remaining sweeps as incremental gain updates
+// (dense_push.cu), then the round's bookkeeping (best state, next restart).
+// The block search below, with its GEMMs in cuBLAS, is the comparator and the
+// path for other sizes.
 //
 // For a complete graph every colour class is one spin, so descent is the
 // paper's one-move-at-a-time order (Sec. IV).  Spins are visited in blocks of
