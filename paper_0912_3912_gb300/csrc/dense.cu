@@ -35,7 +35,8 @@
 namespace isg {
 
 bool dense_tc_eligible(int n);
-cudaError_t dense_tc_run(int n, int R, int Rp, int b, uint64_t seed, const float *J, const float *h,
+int dense_tc_padded(int n);
+cudaError_t dense_tc_run(int n, int n_eval, int R, int Rp, int b, uint64_t seed, const float *J, const float *h,
                          const __nv_bfloat16 *Jhi, const __nv_bfloat16 *Jlo, __nv_bfloat16 *S, float *Fx,
                          DenseRep *rep, int sweeps_a, unsigned long long *stats, int32_t *error,
                          const ising_search_params *p, cudaStream_t s);
@@ -44,6 +45,22 @@ namespace {
 
 constexpr int kDB = 128;          // spins per block
 constexpr int kTcSweepsA = 3;     // tensor-core sweeps per round before the per-replica continuation
+
+// Zero-padded copies for the tensor-core path: J [n][n] -> Jp [np][np] FP32 and
+// its BF16 split, h [n] -> hp [np].
+__global__ void dense_pad_split(const float *J, const float *h, int32_t n, int32_t np, float *Jp, float *hp,
+                                __nv_bfloat16 *hi, __nv_bfloat16 *lo) {
+  const int64_t nn = (int64_t)np * np;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / np), j = (int)(t % np);
+    const float w = (i < n && j < n) ? J[(int64_t)i * n + j] : 0.0f;
+    if (Jp) Jp[t] = w;
+    const __nv_bfloat16 a = __float2bfloat16_rn(w);
+    hi[t] = a;
+    lo[t] = __float2bfloat16_rn(w - __bfloat162float(a));
+    if (hp && t < np) hp[t] = t < n ? h[t] : 0.0f;
+  }
+}
 
 __global__ void dense_split(const float *J, __nv_bfloat16 *hi, __nv_bfloat16 *lo, int64_t nn) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (int64_t)gridDim.x * blockDim.x) {
@@ -224,8 +241,9 @@ __global__ void dense_output(int32_t n, int32_t R, int32_t Rp, int32_t b, int64_
 // [Rp][n]): count a converged descent, keep its state if it is the best so far
 // (strictly lower energy; ties keep the earlier), then start the next restart
 // unless the restarts or the sweep budget are used up.
-__global__ void dense_round_end(int32_t n, int32_t R, int32_t restarts, int32_t budget, const __nv_bfloat16 *S,
-                                DenseRep *rep, int8_t *best, int32_t *active_count, unsigned long long *stats) {
+__global__ void dense_round_end(int32_t n, int32_t np, int32_t R, int32_t restarts, int32_t budget,
+                                const __nv_bfloat16 *S, DenseRep *rep, int8_t *best, int32_t *active_count,
+                                unsigned long long *stats) {
   const int r = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (r >= R) return;
   int copy = 0;
@@ -256,16 +274,17 @@ __global__ void dense_round_end(int32_t n, int32_t R, int32_t restarts, int32_t 
   copy = __shfl_sync(0xffffffffu, copy, 0);
   if (copy)
     for (int i = lane; i < n; i += 32)
-      best[(int64_t)r * n + i] = __bfloat162float(S[(int64_t)r * n + i]) > 0.0f ? 1 : -1;
+      best[(int64_t)r * n + i] = __bfloat162float(S[(int64_t)r * np + i]) > 0.0f ? 1 : -1;
 }
 
-// Results of the tensor-core path: the best converged state, else the final one.
-__global__ void dense_tc_output(int32_t n, int32_t R, const __nv_bfloat16 *S, const int8_t *best,
+// Results of the tensor-core path: the best converged state, else the final one
+// (S rows of np spins, the first n the instance's).
+__global__ void dense_tc_output(int32_t n, int32_t np, int32_t R, const __nv_bfloat16 *S, const int8_t *best,
                                 const DenseRep *rep, int8_t *out, double *E, int32_t *minima) {
   const int64_t tot = (int64_t)R * n;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(t / n);
-    out[t] = rep[r].minima > 0 ? best[t] : (__bfloat162float(S[t]) > 0.0f ? 1 : -1);
+    const int r = (int)(t / n), i = (int)(t % n);
+    out[t] = rep[r].minima > 0 ? best[t] : (__bfloat162float(S[(int64_t)r * np + i]) > 0.0f ? 1 : -1);
   }
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < R) {
@@ -285,7 +304,13 @@ struct DenseState {
   DenseRep *rep = nullptr;
   int8_t *best = nullptr;
   int32_t *active = nullptr, *h_active = nullptr;
-  __nv_bfloat16 *S_tc = nullptr;  // [Rp128][n] replica-major spins for the tcgen05 kernel
+  __nv_bfloat16 *S_tc = nullptr;  // [Rp128][np] replica-major spins for the tcgen05 kernel
+  // tensor-core path with n padded to np (a multiple of 256): own copies of J
+  // (FP32 and BF16 split) and h when np != n, else the unpadded ones
+  int32_t np = 0;
+  float *Jp = nullptr, *hp = nullptr;
+  __nv_bfloat16 *tc_hi = nullptr, *tc_lo = nullptr;
+  int64_t fx_floats = 0;  // capacity of Sx and Fx
   int32_t *err = nullptr, *h_err = nullptr;
   int32_t *counter = nullptr;          // work counter of the per-replica continuation
   float *Sx = nullptr, *Fx = nullptr;  // [R][n] returned spins and their FP32 fields
@@ -311,6 +336,12 @@ void free_state(DenseState &D) {
   cudaFree(D.counter);
   cudaFree(D.Sx);
   cudaFree(D.Fx);
+  if (D.np != D.n) {  // the padded copies are owned only when padding was needed
+    cudaFree(D.Jp);
+    cudaFree(D.hp);
+    cudaFree(D.tc_hi);
+    cudaFree(D.tc_lo);
+  }
   if (D.h_err) cudaFreeHost(D.h_err);
   if (D.h_active) cudaFreeHost(D.h_active);
   if (D.cublas) cublasDestroy(D.cublas);
@@ -332,13 +363,24 @@ bool fields(DenseState &D, int b0, int cnt, float *out) {
   return gemm(D, D.Rp, cnt, n, D.S, D.Rp, D.lo + (int64_t)b0 * n, n, out, D.Rp, 1.0f) == CUBLAS_STATUS_SUCCESS;
 }
 
+// Sx and Fx hold at least `floats` floats each (freed with the state).
+cudaError_t ensure_fx(DenseState &D, int64_t floats) {
+  if (D.fx_floats >= floats) return cudaSuccess;
+  cudaFree(D.Sx);
+  cudaFree(D.Fx);
+  D.Sx = D.Fx = nullptr;
+  D.fx_floats = 0;
+  cudaError_t e;
+  if ((e = cudaMalloc(&D.Sx, (size_t)floats * sizeof(float))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&D.Fx, (size_t)floats * sizeof(float))) != cudaSuccess) return e;
+  D.fx_floats = floats;
+  return cudaSuccess;
+}
+
 cudaError_t exact_energies(DenseState &D, ising_handle *h, int n, int R, const float *J, const float *hf,
                            const int8_t *out, double *E, cudaStream_t s) {
   cudaError_t e;
-  if (!D.Sx) {  // sized for D.Rp >= R replicas; freed with the state when n or Rp changes
-    if ((e = cudaMalloc(&D.Sx, (size_t)D.Rp * n * sizeof(float))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&D.Fx, (size_t)D.Rp * n * sizeof(float))) != cudaSuccess) return e;
-  }
+  if ((e = ensure_fx(D, (int64_t)D.Rp * n)) != cudaSuccess) return e;
   const int64_t tot = (int64_t)R * n;
   dense_spins_f32<<<(int)std::min<int64_t>((tot + 255) / 256, (int64_t)h->sm_count * 16), 256, 0, s>>>(out, D.Sx, tot);
   // column-major view: F^T (n x R) = J (n x n, symmetric) . S^T (n x R).  FP32
@@ -421,17 +463,30 @@ cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t 
       // descent ends (incremental updates, CUDA cores), then the round's
       // bookkeeping.  The host reads one count per round.
       const int Rp128 = (R + 127) / 128 * 128;
+      const int np = dense_tc_padded(n);
       if (!D.S_tc) {
-        if ((e = cudaMalloc(&D.S_tc, (size_t)Rp128 * n * 2)) != cudaSuccess) return e;
-        if ((e = cudaMemset(D.S_tc, 0, (size_t)Rp128 * n * 2)) != cudaSuccess) return e;
+        D.np = np;
+        if (np == n) {
+          D.Jp = const_cast<float *>(J);
+          D.hp = const_cast<float *>(hf);
+          D.tc_hi = D.hi;
+          D.tc_lo = D.lo;
+        } else {
+          if ((e = cudaMalloc(&D.Jp, (size_t)np * np * 4)) != cudaSuccess) return e;
+          if ((e = cudaMalloc(&D.hp, (size_t)np * 4)) != cudaSuccess) return e;
+          if ((e = cudaMalloc(&D.tc_hi, (size_t)np * np * 2)) != cudaSuccess) return e;
+          if ((e = cudaMalloc(&D.tc_lo, (size_t)np * np * 2)) != cudaSuccess) return e;
+          dense_pad_split<<<h->sm_count * 8, 256, 0, s>>>(J, hf, n, np, D.Jp, D.hp, D.tc_hi, D.tc_lo);
+          h->launches += 1;
+        }
+        if ((e = cudaMalloc(&D.S_tc, (size_t)Rp128 * np * 2)) != cudaSuccess) return e;
+        if ((e = cudaMemset(D.S_tc, 0, (size_t)Rp128 * np * 2)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&D.err, 64)) != cudaSuccess) return e;
         if ((e = cudaMallocHost(&D.h_err, 64)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&D.counter, 64)) != cudaSuccess) return e;
       }
-      if (!D.Sx) {  // [Rp][n] FP32: exported fields here, returned-energy GEMM operands afterwards
-        if ((e = cudaMalloc(&D.Sx, (size_t)D.Rp * n * sizeof(float))) != cudaSuccess) return e;
-        if ((e = cudaMalloc(&D.Fx, (size_t)D.Rp * n * sizeof(float))) != cudaSuccess) return e;
-      }
+      // [R][np] FP32: exported fields here, returned-energy GEMM operands afterwards
+      if ((e = ensure_fx(D, (int64_t)std::max(D.Rp, R) * np)) != cudaSuccess) return e;
       int sweeps_a = kTcSweepsA;
       if (const char *v = std::getenv("ISING_DENSE_TC_SWEEPS")) sweeps_a = std::max(0, std::atoi(v));
       if ((e = cudaMemsetAsync(D.err, 0, 4, s)) != cudaSuccess) return e;
@@ -440,19 +495,19 @@ cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t 
       h->launches += 1;
       for (;;) {
         kt_begin(h, "dense_tc_kernel", s);
-        e = dense_tc_run(n, R, Rp128, b, seed, J, hf, D.hi, D.lo, D.S_tc, D.Fx, D.rep, sweeps_a, h->d_stats, D.err,
-                         p, s);
+        e = dense_tc_run(np, n, R, Rp128, b, seed, D.Jp, D.hp, D.tc_hi, D.tc_lo, D.S_tc, D.Fx, D.rep, sweeps_a,
+                         h->d_stats, D.err, p, s);
         kt_end(h, s);
         if (e != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(D.counter, 0, 4, s)) != cudaSuccess) return e;
         kt_begin(h, "dense_push_kernel", s);
-        e = dense_push_run(n, R, p->max_sweeps, p->sweep_budget, J, hf, D.Fx, D.S_tc, D.rep, D.counter, h->d_stats,
-                           h->sm_count, s);
+        e = dense_push_run(np, n, R, p->max_sweeps, p->sweep_budget, D.Jp, D.hp, D.Fx, D.S_tc, D.rep, D.counter,
+                           h->d_stats, h->sm_count, s);
         kt_end(h, s);
         if (e != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(D.active, 0, 4, s)) != cudaSuccess) return e;
-        dense_round_end<<<wb, 256, 0, s>>>(n, R, p->restarts, p->sweep_budget, D.S_tc, D.rep, D.best, D.active,
-                                           h->d_stats);
+        dense_round_end<<<wb, 256, 0, s>>>(n, np, R, p->restarts, p->sweep_budget, D.S_tc, D.rep, D.best,
+                                           D.active, h->d_stats);
         h->launches += 3;
         if ((e = cudaMemcpyAsync(D.h_active, D.active, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
         if ((e = cudaMemcpyAsync(D.h_err, D.err, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
@@ -463,7 +518,7 @@ cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t 
       int8_t *outb = spins + (int64_t)R * h->inst[b].spin_off;
       const int64_t tot = (int64_t)R * n;
       dense_tc_output<<<(int)std::min<int64_t>((tot + 255) / 256, (int64_t)h->sm_count * 16), 256, 0, s>>>(
-          n, R, D.S_tc, D.best, D.rep, outb, E + (int64_t)b * R, minima ? minima + (int64_t)b * R : nullptr);
+          n, np, R, D.S_tc, D.best, D.rep, outb, E + (int64_t)b * R, minima ? minima + (int64_t)b * R : nullptr);
       h->launches += 1;
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       kt_begin(h, "dense_energy_gemm", s);

@@ -24,13 +24,15 @@ struct DenseRep {
   double E;         // energy of the current state, as the search computes it
 };
 
-// Fields of the dense instances that leave the tensor-core sweeps still
-// descending are continued by dense_push_run: one warp per replica, fields in
-// shared memory, one coupling-row update per flip.
+// Replicas of a dense instance that leave the tensor-core sweeps still
+// descending are continued by dense_push_run: one CTA per replica, fields in
+// registers, one coupling-row update per flip.
 //   J [n][n] FP32, h [n] FP32 (zeros allowed), F [R][n] fields (h included),
-//   S [Rp][n] BF16 spins (rows of the replicas it finishes are rewritten).
-cudaError_t dense_push_run(int n, int R, int max_sweeps, int budget, const float *J, const float *h, const float *F,
-                           __nv_bfloat16 *S, DenseRep *rep, int32_t *counter, unsigned long long *stats, int sm_count,
-                           cudaStream_t s);
+//   S [Rp][n] BF16 spins (rows of the replicas it finishes are rewritten);
+//   n <= 4096, a multiple of 4 (padded; n_eval = the instance's own spins,
+//   for the work counters).
+cudaError_t dense_push_run(int n, int n_eval, int R, int max_sweeps, int budget, const float *J, const float *h,
+                           const float *F, __nv_bfloat16 *S, DenseRep *rep, int32_t *counter,
+                           unsigned long long *stats, int sm_count, cudaStream_t s);
 
 }  // namespace isg

@@ -34,7 +34,7 @@ constexpr int kSlots = 8;      // most float4 field slots per thread: n <= 4 * k
 constexpr int kNone = 0x7fffffff;
 
 struct PushArgs {
-  int32_t n, R, max_sweeps, budget;
+  int32_t n, n_eval, R, max_sweeps, budget;  // n: row length (padded); n_eval: the instance's spins
   const float *J;      // [n][n]
   const float *h;      // [n]
   const float *F;      // [R][n] fields at entry
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kThreads, 6) dense_push_kernel(PushArgs A) {
     }
   }
   if (t == 0 && c_sweeps) {
-    atomicAdd(A.stats + 0, (unsigned long long)c_sweeps * (unsigned long long)n);
+    atomicAdd(A.stats + 0, (unsigned long long)c_sweeps * (unsigned long long)A.n_eval);
     atomicAdd(A.stats + 1, c_flips);
     atomicAdd(A.stats + 4, (unsigned long long)c_sweeps);
   }
@@ -225,13 +225,14 @@ cudaError_t launch_push_ns(const PushArgs &A, int sm_count, cudaStream_t s) {
 
 }  // namespace
 
-cudaError_t dense_push_run(int n, int R, int max_sweeps, int budget, const float *J, const float *h, const float *F,
-                           __nv_bfloat16 *S, DenseRep *rep, int32_t *counter, unsigned long long *stats, int sm_count,
-                           cudaStream_t s) {
+cudaError_t dense_push_run(int n, int n_eval, int R, int max_sweeps, int budget, const float *J, const float *h,
+                           const float *F, __nv_bfloat16 *S, DenseRep *rep, int32_t *counter,
+                           unsigned long long *stats, int sm_count, cudaStream_t s) {
   // whole float4 groups, 16-byte aligned rows, fields in registers: n % 4 == 0, n <= 4096
   if (n % 4 != 0 || n < 4 || n > 4 * kThreads * kSlots) return cudaErrorInvalidValue;
   PushArgs A;
   A.n = n;
+  A.n_eval = n_eval;
   A.R = R;
   A.max_sweeps = max_sweeps;
   A.budget = budget;

@@ -54,7 +54,8 @@ constexpr int kSbitsBytes = 32 * (kMaxN / 32) * 4;          // this CTA's 32 rep
 constexpr int kSmemBytes = kStages * kStageBytes + kPartialBytes + kSbitsBytes + 1024;  // + alignment slack
 
 struct TcArgs {
-  int32_t n, R, Rp, b;             // spins, replicas, padded replicas, instance
+  int32_t n, R, Rp, b;             // spins (padded to a multiple of 256), replicas, padded replicas, instance
+  int32_t n_eval;                  // the instance's own spins (work counters)
   int32_t max_sweeps, budget;      // sweep cap per descent, sweep budget over descents (<= 0: none)
   int32_t sweeps_a;                // decision sweeps of a round on tensor cores before the export
   uint64_t seed;
@@ -407,7 +408,7 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
     if (real && st.active) {
       st.total += 1;
       st.d += 1;
-      c_evals += (unsigned long long)n;
+      c_evals += (unsigned long long)A.n_eval;
       ++c_sweeps;
       const bool conv = st.flips == 0;
       st.flips = 0;
@@ -450,7 +451,11 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
 }  // namespace
 
 // ---------------------------------------------------------------- host side
-bool dense_tc_eligible(int n) { return n >= 256 && n % 256 == 0 && n <= kMaxN; }
+// Any n up to kMaxN: smaller or ragged instances run zero-padded to a multiple
+// of 256 (padded spins have no couplings and no field, so they never flip and
+// add nothing to an energy).
+bool dense_tc_eligible(int n) { return n >= 1 && n <= kMaxN; }
+int dense_tc_padded(int n) { return (n + 255) / 256 * 256; }
 
 static cudaError_t encode_2d(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer,
                              uint32_t box_inner, uint32_t box_outer) {
@@ -472,10 +477,11 @@ static cudaError_t encode_2d(CUtensorMap *map, const void *base, uint64_t inner,
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// One round's tensor-core sweeps (see dense_tc_kernel).  S: [Rp][n] BF16 spins
-// (Rp a multiple of 128), Jhi/Jlo [n][n] BF16, J [n][n] FP32, h [n] FP32,
-// Fx [R][n] FP32 exported fields, rep [R] per-replica state.
-cudaError_t dense_tc_run(int n, int R, int Rp, int b, uint64_t seed, const float *J, const float *h,
+// One round's tensor-core sweeps (see dense_tc_kernel).  n a multiple of 256
+// (n_eval <= n the instance's own spins); S: [Rp][n] BF16 spins (Rp a multiple
+// of 128), Jhi/Jlo [n][n] BF16, J [n][n] FP32, h [n] FP32, Fx [R][n] FP32
+// exported fields, rep [R] per-replica state.
+cudaError_t dense_tc_run(int n, int n_eval, int R, int Rp, int b, uint64_t seed, const float *J, const float *h,
                          const __nv_bfloat16 *Jhi, const __nv_bfloat16 *Jlo, __nv_bfloat16 *S, float *Fx,
                          DenseRep *rep, int sweeps_a, unsigned long long *stats, int32_t *error,
                          const ising_search_params *p, cudaStream_t s) {
@@ -485,7 +491,9 @@ cudaError_t dense_tc_run(int n, int R, int Rp, int b, uint64_t seed, const float
   if ((e = encode_2d(&mH, Jhi, (uint64_t)n, (uint64_t)n, kKC, kTB)) != cudaSuccess) return e;
   if ((e = encode_2d(&mL, Jlo, (uint64_t)n, (uint64_t)n, kKC, kTB)) != cudaSuccess) return e;
   TcArgs A;
+  if (n % 256 != 0 || n > kMaxN || n_eval > n) return cudaErrorInvalidValue;
   A.n = n;
+  A.n_eval = n_eval;
   A.R = R;
   A.Rp = Rp;
   A.b = b;

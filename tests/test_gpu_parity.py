@@ -361,6 +361,29 @@ def test_dense_tc_phases_and_fields(sweeps_a, monkeypatch):
     h.close()
 
 
+@pytest.mark.parametrize("n", [1, 37, 300, 1000])
+def test_dense_tc_padded_sizes(n, monkeypatch):
+    """Sizes that are not a multiple of 256 run zero-padded on the hand-written
+    kernels: energies of the returned states, 1-flip minima, exact work
+    counters (the instance's own spins), and agreement with the comparator."""
+    inst = _sk_with_fields(n, 100 + n)
+    R = 130
+    h = isg.Handle([inst])
+    assert h.plan_kernel(R) == isg.KERNEL_DENSE_TC
+    res = h.local_search([11], R, max_sweeps=500, restarts=2, kernel=isg.KERNEL_DENSE_TC)
+    torch.cuda.synchronize()
+    sp, E, m = _dense_checks(inst, res, R)
+    st = dict(res.stats)
+    assert st["minima"] == 2 * R and st["descents"] == 2 * R and np.all(m == 2)
+    assert st["flip_evals"] == st["sweeps"] * n
+    monkeypatch.setenv("ISING_DENSE_CUBLAS", "1")
+    ref = h.local_search([11], R, max_sweeps=500, restarts=2, kernel=isg.KERNEL_DENSE_TC)
+    torch.cuda.synchronize()
+    sp2 = ref.spins.view(R, n).cpu().numpy()
+    assert np.mean(np.all(sp == sp2, axis=1)) >= 0.8
+    h.close()
+
+
 @pytest.mark.parametrize("sweeps_a", ["0", "4"])
 def test_dense_tc_sweep_cap_and_budget(sweeps_a, monkeypatch):
     """Descents cut by the sweep cap (inside and after the tensor-core sweeps)
