@@ -407,6 +407,8 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
           uint32_t *sN = wsm + 32;                                   // [6][32] neighbour words
           int64_t *sT = reinterpret_cast<int64_t *>(wsm + 224);      // [7][32] terms (kk 0..5, field)
           int32_t *sU = reinterpret_cast<int32_t *>(wsm + 672);      // [32] unit exponent, -1: FP64 path
+          uint32_t *sG = wsm + 704;                                  // [32] flips per position
+          sG[lane] = 0u;
           if (need1) {
             sW[lane] = swg[j1];
             const float hj = __ldg(hf + j1);
@@ -470,17 +472,21 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
             }
             const uint32_t m = __ballot_sync(0xffffffffu, flip);
             const uint32_t seg = (m >> (sub * LPS)) & lmask;
-            if (valid && ln == 0) {
-              const int j = __ldg(G.order + so + v);
-              const uint32_t meta = __ldg(G.meta + so + v);
-              if (seg) {
-                swg[j] = wj ^ seg;
-                for (int kk = 0; kk < D2; ++kk) atomicOr(&pendg[nb_of(j, meta, kk)], seg);
-              }
-              if (seg || fmg[j]) fmg[j] = seg;
-            }
+            if (valid && ln == 0) sG[src] = seg;
             anyg |= seg;
-            my_flips += flip ? 1 : 0;
+          }
+          __syncwarp();
+          // the flips are applied per position, all 32 lanes at once (words of
+          // this class, pending marks of the other class, flip masks: nothing the
+          // steps above read)
+          if (need1) {
+            const uint32_t seg = sG[lane];
+            if (seg) {
+              swg[j1] = sW[lane] ^ seg;
+              for (int kk = 0; kk < D2; ++kk) atomicOr(&pendg[nb_of(j1, meta1, kk)], seg);
+            }
+            if (seg || fm1) fmg[j1] = seg;
+            my_flips += __popc(seg);
           }
           __syncwarp();  // staging read before the next batch overwrites it
         }
