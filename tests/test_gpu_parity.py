@@ -384,6 +384,33 @@ def test_dense_tc_padded_sizes(n, monkeypatch):
     h.close()
 
 
+def test_dense_batch_of_instances():
+    """Several dense instances in one handle (sizes with and without padding,
+    one with fields): each block of results checked on its own instance, and
+    the same results when the batch is searched again."""
+    insts = [_sk_with_fields(256, 120, scale=0.0), _sk_with_fields(384, 121), _sk_with_fields(1000, 122)]
+    R = 64
+    h = isg.Handle(insts)
+    res = h.local_search([1, 2, 3], R, max_sweeps=400, restarts=2, kernel=isg.KERNEL_DENSE_TC)
+    torch.cuda.synchronize()
+    first = res.spins.cpu().numpy().copy()
+    st = dict(res.stats)
+    assert st["minima"] == 2 * R * len(insts)
+    for b, inst in enumerate(insts):
+        sp = h.spins_of(res.spins, b, R).cpu().numpy()
+        E = res.energy[b].cpu().numpy()
+        oi = oracle.OracleInstance(inst)
+        Eo = oracle.energies(oi, sp)
+        assert np.max(np.abs(E - Eo) / np.maximum(np.abs(Eo), 1.0)) <= 1e-6
+        for r in range(R):
+            f = oracle.local_fields(oi, sp[r])
+            assert np.all(sp[r] * f >= -1e-4)
+    again = h.local_search([1, 2, 3], R, max_sweeps=400, restarts=2, kernel=isg.KERNEL_DENSE_TC)
+    torch.cuda.synchronize()
+    assert np.array_equal(again.spins.cpu().numpy(), first)
+    h.close()
+
+
 @pytest.mark.parametrize("sweeps_a", ["0", "4"])
 def test_dense_tc_sweep_cap_and_budget(sweeps_a, monkeypatch):
     """Descents cut by the sweep cap (inside and after the tensor-core sweeps)
