@@ -276,8 +276,19 @@ ising_status load_desc(const ising_instance_desc &d, ising_dtype dtype, HostInst
   return ISING_OK;
 }
 
+// Host-side fault injection for tests (ISING_FAULT): "alloc:k" makes the k-th
+// device upload of ising_create fail ("alloc" = the first); "launch" makes
+// ising_local_search fail as a failed launch would; "device_timeout" (read by
+// the dense tensor-core path) makes one CTA's bounded wait run out.
+bool fault_is(const char *what) {
+  const char *f = std::getenv("ISING_FAULT");
+  return f && std::strncmp(f, what, std::strlen(what)) == 0;
+}
+int g_alloc_countdown = 0;  // allocations left before the injected failure (0: none)
+
 template <class T>
 cudaError_t upload(T **dst, const std::vector<T> &src) {
+  if (g_alloc_countdown > 0 && --g_alloc_countdown == 0) return cudaErrorMemoryAllocation;
   cudaError_t e = cudaMalloc((void **)dst, std::max<size_t>(1, src.size()) * sizeof(T));
   if (e != cudaSuccess) return e;
   if (!src.empty()) e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
@@ -591,6 +602,11 @@ void kt_end(ising_handle *h, cudaStream_t s) {
 extern "C" {
 
 ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances, ising_handle **out) {
+  g_alloc_countdown = 0;
+  if (fault_is("alloc")) {
+    const char *f = std::getenv("ISING_FAULT");
+    g_alloc_countdown = f[5] == ':' ? std::max(1, std::atoi(f + 6)) : 1;
+  }
   if (!out) return ISING_ERR_INVALID_ARG;
   *out = nullptr;
   if (!descs || n_instances < 1) return ISING_ERR_INVALID_ARG;
@@ -866,6 +882,10 @@ ising_status ising_local_search(ising_handle *h, const uint64_t *seeds, int32_t 
       st = ISING_ERR_CUDA;
       break;
     }
+    if (fault_is("launch")) {  // injected: as if the family's launch had failed
+      st = ISING_ERR_CUDA;
+      break;
+    }
     switch (kernel) {
       case ISING_KERNEL_TILE:
         st = run_tile(h, h->dtype == ISING_F32 ? 1 : 0, replicas, p, spins_dev, energy_dev, energy_i32_dev,
@@ -880,11 +900,13 @@ ising_status ising_local_search(ising_handle *h, const uint64_t *seeds, int32_t 
             cudaSuccess)
           st = ISING_ERR_CUDA;
         break;
-      case ISING_KERNEL_DENSE_TC:
-        if (launch_dense(h, p, replicas, spins_dev, energy_dev, energy_i32_dev, minima_dev, seeds, stream) !=
-            cudaSuccess)
-          st = ISING_ERR_CUDA;
+      case ISING_KERNEL_DENSE_TC: {
+        const cudaError_t e = launch_dense(h, p, replicas, spins_dev, energy_dev, energy_i32_dev, minima_dev, seeds,
+                                           stream);
+        if (e == cudaErrorLaunchTimeout) st = ISING_ERR_TIMEOUT;  // a bounded device wait gave up
+        else if (e != cudaSuccess) st = ISING_ERR_CUDA;
         break;
+      }
       case ISING_KERNEL_PLAIN:
         kt_begin(h, "plain_path", stream);
         if (launch_plain(h, p, replicas, spins_dev, energy_dev, energy_i32_dev, minima_dev, seeds, stream) !=

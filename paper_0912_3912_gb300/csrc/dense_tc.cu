@@ -30,6 +30,8 @@
 
 #include <cfloat>
 #include <cstdio>
+#include <cstdlib>
+#include <cstring>
 
 #include "dense.cuh"
 #include "device_common.cuh"
@@ -66,6 +68,8 @@ struct TcArgs {
   DenseRep *rep;                   // [R] per-replica state, read at entry and written back
   unsigned long long *stats;
   int32_t *error;                  // set to ISING_ERR_TIMEOUT when a wait gives up
+  int32_t stall_test;              // nonzero: CTA 0 waits, with a short limit, on a barrier nothing
+                                   // completes (exercises the failure path in tests)
 };
 
 // Philox start R(b, r, k) of replica r, written as BF16 +/-1 into S[r][:] and
@@ -97,7 +101,7 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
   float *Jblk = reinterpret_cast<float *>(smem + 32 * kFl * 4 + 128); // reuses stages: [128][128]
   uint32_t *sbits = reinterpret_cast<uint32_t *>(smem + kStages * kStageBytes + kPartialBytes);  // [32][n/32]
 
-  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], done_bar;
+  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], done_bar, drain_bar, stall_bar;
   __shared__ uint32_t tmem_base_s;
   __shared__ int32_t s_flag[2];   // cluster-visible: [0] my replicas still busy, [1] my failure
   __shared__ int32_t s_ctrl[4];   // broadcast inside the CTA
@@ -119,6 +123,8 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
       tc::mbar_init(&empty_bar[s], 1);
     }
     tc::mbar_init(&done_bar, 1);
+    tc::mbar_init(&drain_bar, 1);
+    tc::mbar_init(&stall_bar, 1);
     tc::fence_barrier_init();
     tc::prefetch_tmap(&mapS);
     tc::prefetch_tmap(&mapJhi);
@@ -211,6 +217,8 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
           tma_pending[s] = 1;
         };
         for (int s = 0; s < kStages && s < kchunks; ++s) load(s, s);
+        if (A.stall_test && blockIdx.x == 0 && sw == 0 && blk == 0 && !tc::mbar_wait(&stall_bar, 0, 20000))
+          failed = true;  // nothing arrives on stall_bar: the wait gives up after 20 us
         int waited = 0;  // chunks whose MMA completion (empty barrier) has been consumed
         for (int kc = 0; kc < kchunks && !failed; ++kc) {
           const int s = kc % kStages;
@@ -438,9 +446,9 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
     // let copies and MMAs still in flight land before the CTA releases its memory
     for (int s = 0; s < kStages; ++s)
       if (tma_pending[s]) tc::mbar_wait(&full_bar[s], ph_full[s]);
-    if (mma_pending) {
-      tc::mma_commit(&done_bar);
-      tc::mbar_wait(&done_bar, ph_done);
+    if (mma_pending) {  // a barrier of its own: done_bar's phase may not match after a failure
+      tc::mma_commit(&drain_bar);
+      tc::mbar_wait(&drain_bar, 0);
     }
   }
   tc::tc_fence_before();
@@ -508,6 +516,10 @@ cudaError_t dense_tc_run(int n, int n_eval, int R, int Rp, int b, uint64_t seed,
   A.rep = rep;
   A.stats = stats;
   A.error = error;
+  {
+    const char *f = std::getenv("ISING_FAULT");
+    A.stall_test = (f && std::strcmp(f, "device_timeout") == 0) ? 1 : 0;
+  }
   if ((e = cudaFuncSetAttribute(dense_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)) !=
       cudaSuccess)
     return e;
