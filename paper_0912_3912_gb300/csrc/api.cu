@@ -8,6 +8,8 @@
 #include <numeric>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 
 namespace isg {
@@ -576,6 +578,15 @@ void tune_cache_store(const std::string &key, int32_t fam) {
 
 namespace isg {
 
+// An NVTX range for the duration of a C-ABI call (visible to profilers that
+// record NVTX; a no-op otherwise).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 void kt_begin(ising_handle *h, const char *name, cudaStream_t s) {
   if (!h->timing) return;
   if (h->kt_used == h->ktimers.size()) {
@@ -602,6 +613,7 @@ void kt_end(ising_handle *h, cudaStream_t s) {
 extern "C" {
 
 ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances, ising_handle **out) {
+  const NvtxRange nvtx_range("ising_create");
   g_alloc_countdown = 0;
   if (fault_is("alloc")) {
     const char *f = std::getenv("ISING_FAULT");
@@ -830,6 +842,7 @@ ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
 
 ising_status ising_energy(ising_handle *h, const int8_t *spins_dev, int32_t replicas, double *energy_dev,
                           int32_t *energy_i32_dev, cudaStream_t stream) {
+  const NvtxRange nvtx_range("ising_energy");
   if (!h || !spins_dev || !energy_dev || replicas < 1) return ISING_ERR_INVALID_ARG;
   if (h->latched != ISING_OK) {
     ising_status l = h->latched;
@@ -857,6 +870,7 @@ ising_status ising_local_search(ising_handle *h, const uint64_t *seeds, int32_t 
                                 const ising_search_params *p, int8_t *spins_dev, double *energy_dev,
                                 int32_t *energy_i32_dev, int32_t *minima_dev, ising_stats *stats,
                                 cudaStream_t stream) {
+  const NvtxRange nvtx_range("ising_local_search");
   if (!h || !seeds || replicas < 1 || !spins_dev || !energy_dev) return ISING_ERR_INVALID_ARG;
   ising_status st = validate_params(p);
   if (st != ISING_OK) return st;
@@ -939,6 +953,7 @@ ising_status ising_local_search(ising_handle *h, const uint64_t *seeds, int32_t 
 
 ising_status ising_autotune(ising_handle *h, int32_t replicas, const ising_search_params *p, int32_t *chosen,
                             cudaStream_t stream) {
+  const NvtxRange nvtx_range("ising_autotune");
   if (!h || !p || replicas < 1) return ISING_ERR_INVALID_ARG;
   ising_status st = validate_params(p);
   if (st != ISING_OK) return st;
