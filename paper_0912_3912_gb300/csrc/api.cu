@@ -386,6 +386,7 @@ int msc_cluster_size(const ising_handle *h, int32_t R, const ising_search_params
     for (const auto &I : h->inst) {
       const int csz = I.n / P;
       if (I.n % P || csz < 1024 || (csz & (csz - 1)) || csz % 128) ok = false;
+      if (msc_cluster_smem(csz) + 4096 > 232448) ok = false;  // dynamic + static shared memory of a CTA
       if (d >= 0 && I.lat_d != d) ok = false;
       d = I.lat_d;
     }

@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(kCT, 1) msc_cluster_kernel(const TileArgs *__r
   uint32_t *sw = smem;                                          // words of sites lo .. lo + csz - 1
   uint32_t *pend = smem + csz;                                  // [2][nch] pending flags
   uint8_t *tab = reinterpret_cast<uint8_t *>(smem + csz + 2 * nch);  // [csz]: neg bits 0..5, h != 0, h > 0
-  uint32_t *bw = A.bw + (size_t)tile * A.nmax;
+  uint32_t *bw = smem + csz + 2 * nch + csz / 4;                      // [csz]: best words of my sites
   const int rem = A.R - 32 * g;
   const uint32_t lane_valid = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
   const uint64_t seed = A.seeds[b];
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(kCT, 1) msc_cluster_kernel(const TileArgs *__r
           __syncthreads();
           const uint32_t upd = s_upd;
           if (upd)
-            for (int o = tid; o < csz; o += blockDim.x) bw[lo + o] = (bw[lo + o] & ~upd) | (sw[o] & upd);
+            for (int o = tid; o < csz; o += blockDim.x) bw[o] = (bw[o] & ~upd) | (sw[o] & upd);
         }
         // stale pending flags are harmless: the next descent's first sweep
         // visits every chunk and resets them
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(kCT, 1) msc_cluster_kernel(const TileArgs *__r
   __syncthreads();
   const int64_t out_base = (int64_t)A.R * I.spin_off + (int64_t)(32 * g) * n;
   for (int o = tid; o < csz; o += blockDim.x) {
-    const uint32_t wv = (bw[lo + o] & has_best) | (sw[o] & ~has_best);
+    const uint32_t wv = (bw[o] & has_best) | (sw[o] & ~has_best);
     for (int r = 0; r < 32; ++r)
       if ((lane_valid >> r) & 1u) A.spins[out_base + (int64_t)r * n + lo + o] = ((wv >> r) & 1u) ? 1 : -1;
   }
@@ -357,7 +357,8 @@ __global__ void __launch_bounds__(kCT, 1) msc_cluster_kernel(const TileArgs *__r
 
 }  // namespace
 
-size_t msc_cluster_smem(int csz) { return (size_t)csz * 4 + (size_t)(csz / 64) * 2 * 4 + (size_t)csz; }
+// words, pending flags, per-site bytes, best words
+size_t msc_cluster_smem(int csz) { return (size_t)csz * 4 + (size_t)(csz / 64) * 2 * 4 + (size_t)csz + (size_t)csz * 4; }
 
 template <int D>
 cudaError_t launch_cfg(cudaLaunchConfig_t &cfg, const TileArgs *args, int P, size_t smem, int *max_active) {
