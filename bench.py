@@ -379,6 +379,21 @@ def main():
         dist.destroy_process_group()
 
 
+def ncu_traffic(workload, kernel):
+    """DRAM bytes per launch of `kernel` for `workload` from the committed ncu
+    summary (read + write), or None when it holds no line for them."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "dram_traffic.txt")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    for line in lines:
+        f = line.split()
+        if len(f) >= 4 and f[0] == workload and f[1] == kernel and f[2].isdigit() and f[3].isdigit():
+            return int(f[2]) + int(f[3])
+    return None
+
+
 def roofline(name, kernel, insts, R, st, step_s, clk, hbm, bf16s, src, ktimes=None, steps=1):
     """Roofline of the step's main kernel.  The algorithmic work per unit is the
     method's own (not the kernel's instruction count).  The time is that
@@ -401,6 +416,10 @@ def roofline(name, kernel, insts, R, st, step_s, clk, hbm, bf16s, src, ktimes=No
         out["time_basis"] = "whole step (CUDA events)"
     if ktimes:
         out["kernels_ms_per_step"] = {k: v[0] / steps for k, v in ktimes.items()}
+    tr = ncu_traffic(name, out.get("kernel"))
+    if tr is not None:
+        out["traffic"] = tr
+        out["traffic_unit"] = "DRAM bytes per launch (ncu, committed summary)"
     return out
 
 
