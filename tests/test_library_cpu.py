@@ -41,6 +41,29 @@ def test_library_exports_every_declared_function(isg):
     assert set(names) == set(isg.EXPORTED)
 
 
+def test_product_path_fails_loudly_without_the_library():
+    """No fallback: with the shared library absent, creating a handle raises."""
+    import subprocess
+    import sys
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "import paper_0912_3912_gb300 as m, workloads as W\n"
+        "m.LIB_PATH = '/nonexistent/libising_gb300.so'\n"
+        "m._lib = None\n"
+        "try:\n"
+        "    m.lib()\n"
+        "except RuntimeError as e:\n"
+        "    print('raised:', 'missing' in str(e))\n"
+        "try:\n"
+        "    m.Handle([W.lattice((4, 4), periodic=True, couplings='pm1', seed=1)])\n"
+        "    print('handle created')\n"
+        "except RuntimeError:\n"
+        "    pass\n"
+    ) % ROOT
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert "raised: True" in r.stdout and "handle created" not in r.stdout, (r.stdout, r.stderr)
+
+
 def test_timing_entry_points_reject_a_null_handle(isg):
     L = isg.lib()
     assert L.ising_set_timing(None, 1) == 1          # ISING_ERR_INVALID_ARG
