@@ -233,13 +233,32 @@ ising_status ising_energy_noalloc(int32_t n, const int64_t *row_ptr_dev, const i
                                   const int8_t *spins_dev, int32_t replicas, double *energy_dev,
                                   cudaStream_t stream);
 
+/* The paper's pass-based search with hill climbing (Sec. IV, Fig. 3), for
+ * instances of at most 4096 spins (else ISING_ERR_UNSUPPORTED).  Per replica,
+ * `restarts` starts (Philox, counter layout as for ising_local_search, restart
+ * index k = 0 .. restarts-1); from each start, passes: every spin moves once
+ * per pass in best-gain order (largest -2 s_i f_i among the spins not yet
+ * moved, ties to the lowest index; moves with negative gain included), the
+ * pass is cut back to its earliest strictly lowest-energy prefix, and passes
+ * repeat while one lowers the energy strictly (float couplings: by more than
+ * 1e-9 (1 + |E|)); max_passes > 0 caps the passes per start (0: no cap).  Gains
+ * and energies in FP64 (exact for integer couplings).  Per replica the result
+ * is the lowest-energy start (ties keep the earlier).
+ * spins_dev, energy_dev: as for ising_local_search; passes_dev: device int32
+ * [instance][replica] passes summed over the starts, or NULL.  stats (nullable;
+ * the call then waits): descents = starts, sweeps = passes, flips and
+ * flip_evals = moves applied (n per pass), minima = 0.                        */
+ising_status ising_fm_search(ising_handle *h, const uint64_t *seeds, int32_t replicas, int32_t restarts,
+                             int32_t max_passes, int8_t *spins_dev, double *energy_dev, int32_t *passes_dev,
+                             ising_stats *stats, cudaStream_t stream);
+
 /* Device timing of the kernels a search runs, for measurement.
  * ising_set_timing(h, 1) opens a timing window (clearing the previous one);
  * while it is open every ising_local_search call records a pair of CUDA events
  * on its stream around each of its main kernel launches (a family's main
  * kernel, or a graph of them: "tile_kernel", "msc_cluster_kernel",
  * "sweep_chunk", "dense_tc_kernel", "dense_push_kernel", "dense_energy_gemm",
- * "plain_path").  ising_set_timing(h, 0) stops recording.
+ * "plain_path", "fm_kernel").  ising_set_timing(h, 0) stops recording.
  * ising_kernel_times waits for the recorded events and writes up to cap
  * entries {name, total ms, launches} summed over the window, in order of first
  * launch; it returns the number of distinct names (which may exceed cap), or

@@ -84,6 +84,8 @@ def lib():
             L.ising_destroy.restype = i32
             L.ising_energy_noalloc.argtypes = [i32, vp, vp, vp, vp, i32, vp, i32, vp, vp]
             L.ising_energy_noalloc.restype = i32
+            L.ising_fm_search.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
+            L.ising_fm_search.restype = i32
             L.ising_set_timing.argtypes = [vp, i32]
             L.ising_set_timing.restype = i32
             L.ising_kernel_times.argtypes = [vp, vp, i32]
@@ -96,7 +98,7 @@ def lib():
 
 EXPORTED = ("ising_create", "ising_energy", "ising_local_search", "ising_plan_kernel",
             "ising_autotune", "ising_destroy", "ising_status_string", "ising_energy_noalloc",
-            "ising_set_timing", "ising_kernel_times")
+            "ising_set_timing", "ising_kernel_times", "ising_fm_search")
 
 
 def _check(code: int, where: str):
@@ -210,6 +212,22 @@ class Handle:
         if stats:
             sd = {k: int(getattr(st, k)) for k, _ in _Stats._fields_}
         return SearchResult(spins, E, E32, minima, sd)
+
+    def fm_search(self, seeds, replicas: int, *, restarts=1, max_passes=0, stream=None, stats=True):
+        """The paper's pass-based search with hill climbing (ising_fm_search).
+        Returns (spins [total], energy [instances, replicas], passes, stats)."""
+        torch = self._torch
+        seeds = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64).reshape(self.n_inst))
+        spins = torch.empty(replicas * self.total_spins, dtype=torch.int8, device=self.device)
+        E = torch.empty((self.n_inst, replicas), dtype=torch.float64, device=self.device)
+        passes = torch.empty((self.n_inst, replicas), dtype=torch.int32, device=self.device)
+        st = _Stats()
+        _check(lib().ising_fm_search(
+            self._h, C.c_void_p(seeds.ctypes.data), replicas, restarts, max_passes, C.c_void_p(spins.data_ptr()),
+            C.c_void_p(E.data_ptr()), C.c_void_p(passes.data_ptr()), C.byref(st) if stats else None,
+            self._stream(stream)), "ising_fm_search")
+        sd = {k: int(getattr(st, k)) for k, _ in _Stats._fields_} if stats else None
+        return spins, E, passes, sd
 
     def plan_kernel(self, replicas: int, **kw) -> int:
         p = self.params(**kw)

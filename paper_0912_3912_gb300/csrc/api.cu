@@ -308,6 +308,7 @@ void free_handle(ising_handle *h) {
   }
   energy_plan_free(h);
   sweep_free(h);
+  fm_free(h);
   dense_free(h);
   plain_free(h);
   void *ptrs[] = {h->d_inst, h->d_row, h->d_col, h->d_J, h->d_h, h->d_inc_ptr, h->d_inc_edge, h->d_hptr,
@@ -1023,6 +1024,54 @@ ising_status ising_autotune(ising_handle *h, int32_t replicas, const ising_searc
 ising_status ising_destroy(ising_handle *h) {
   free_handle(h);
   return ISING_OK;
+}
+
+ising_status ising_fm_search(ising_handle *h, const uint64_t *seeds, int32_t replicas, int32_t restarts,
+                             int32_t max_passes, int8_t *spins_dev, double *energy_dev, int32_t *passes_dev,
+                             ising_stats *stats, cudaStream_t stream) {
+  const NvtxRange nvtx_range("ising_fm_search");
+  if (!h || !seeds || replicas < 1 || restarts < 1 || max_passes < 0 || !spins_dev || !energy_dev)
+    return ISING_ERR_INVALID_ARG;
+  if (h->latched != ISING_OK) {
+    ising_status l = h->latched;
+    h->latched = ISING_OK;
+    return l;
+  }
+  if (h->nmax > fm_max_spins()) return ISING_ERR_UNSUPPORTED;
+  if ((int64_t)replicas * h->n_inst > 0x7fffffffLL) return ISING_ERR_UNSUPPORTED;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != h->device) cudaSetDevice(h->device);
+  ising_status st = ISING_OK;
+  h->launches = 0;
+  if (fault_is("launch")) {
+    st = ISING_ERR_CUDA;
+  } else if (cudaMemcpyAsync(h->d_seeds, seeds, sizeof(uint64_t) * h->n_inst, cudaMemcpyHostToDevice, stream) !=
+                 cudaSuccess ||
+             cudaMemsetAsync(h->d_stats, 0, sizeof(unsigned long long) * 8, stream) != cudaSuccess) {
+    st = ISING_ERR_CUDA;
+  } else {
+    kt_begin(h, "fm_kernel", stream);
+    if (launch_fm(h, replicas, restarts, max_passes, spins_dev, energy_dev, passes_dev, stream) != cudaSuccess)
+      st = ISING_ERR_CUDA;
+    kt_end(h, stream);
+  }
+  if (st == ISING_OK && stats) {
+    if (cudaMemcpyAsync(h->h_stats_pinned, h->d_stats, sizeof(unsigned long long) * 5, cudaMemcpyDeviceToHost,
+                        stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess) {
+      st = ISING_ERR_CUDA;
+    } else {
+      stats->flip_evals = h->h_stats_pinned[0];
+      stats->flips = h->h_stats_pinned[1];
+      stats->minima = h->h_stats_pinned[2];
+      stats->descents = h->h_stats_pinned[3];
+      stats->sweeps = h->h_stats_pinned[4];
+      stats->launches = h->launches;
+    }
+  }
+  if (cur != h->device) cudaSetDevice(cur);
+  return st;
 }
 
 ising_status ising_set_timing(ising_handle *h, int32_t enable) {

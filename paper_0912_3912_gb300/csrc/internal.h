@@ -184,5 +184,10 @@ cudaError_t launch_energy(ising_handle *h, const int8_t *spins, int32_t R, doubl
 void energy_plan_free(ising_handle *h);
 size_t msc_cluster_smem(int csz);
 cudaError_t launch_msc_cluster(ising_handle *h, int n_tiles, int P, int csz_max, int D, cudaStream_t s);
+// the pass-based search (fm.cu)
+int fm_max_spins();
+cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_passes, int8_t *spins, double *E,
+                      int32_t *passes, cudaStream_t s);
+void fm_free(ising_handle *h);
 int msc_cluster_max_active(ising_handle *h, int n_tiles, int P, int csz_max, int D);
 }  // namespace isg

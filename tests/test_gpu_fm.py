@@ -1,0 +1,117 @@
+"""The pass-based search with hill climbing (Sec. IV, Fig. 3) on the GPU
+against the oracle's heap implementation (Fig. 4), move for move: the same
+starts, the same passes, the same results.  Integer couplings: spins,
+energies and pass counts exactly equal.  Float couplings: spins and pass
+counts equal, energies within 1e-9 relative (the oracle sums energies with
+compensation, the kernel in plain FP64; the improvement margin of a pass
+absorbs that difference)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+isg = pytest.importorskip("paper_0912_3912_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_0912_3912_gb300 import build as B
+    B.build()
+    oracle.build()
+
+
+def _oracle_fm(inst, seed, b, R, restarts):
+    spins, energies, passes = [], [], []
+    for r in range(R):
+        best_E, best_s, tp = np.inf, None, 0
+        for k in range(restarts):
+            s, E, p = oracle.fm_search(inst, oracle.random_start(inst.n, seed, b, r, k))
+            tp += p
+            if E < best_E:
+                best_E, best_s = E, s
+        spins.append(best_s)
+        energies.append(best_E)
+        passes.append(tp)
+    return np.array(spins), np.array(energies), np.array(passes)
+
+
+def _compare(insts, R, restarts, exact):
+    seeds = [W.replica_seed(W.splitmix64(0xF00 + b)) for b in range(len(insts))]
+    h = isg.Handle(insts)
+    sp, E, P, st = h.fm_search(seeds, R, restarts=restarts)
+    torch.cuda.synchronize()
+    total_passes = 0
+    for b, inst in enumerate(insts):
+        s_o, E_o, p_o = _oracle_fm(inst, seeds[b], b, R, restarts)
+        s_g = h.spins_of(sp, b, R).cpu().numpy()
+        assert np.array_equal(s_g, s_o), f"spins differ for instance {b}"
+        assert np.array_equal(P[b].cpu().numpy(), p_o), f"pass counts differ for instance {b}"
+        if exact:
+            assert np.array_equal(E[b].cpu().numpy(), E_o)
+        else:
+            np.testing.assert_allclose(E[b].cpu().numpy(), E_o, rtol=1e-9, atol=1e-9)
+        total_passes += int(p_o.sum())
+    assert st["descents"] == len(insts) * R * restarts
+    assert st["sweeps"] == total_passes
+    h.close()
+
+
+def test_fm_integer_graph_with_hyperedges():
+    inst = W.random_graph(300, 4.0, 71, dtype="i8", n_hyper=25, hyper_order=(3, 4))
+    _compare([inst], 16, 3, True)
+
+
+def test_fm_pm_lattice_with_fields():
+    inst = W.lattice((16, 16), periodic=True, couplings="pm1", fields="pm1_0", seed=72)
+    _compare([inst], 32, 2, True)
+
+
+def test_fm_float_graph_with_hyperedges():
+    inst = W.random_graph(200, 5.0, 73, dtype="f32", n_hyper=20, hyper_order=(3,))
+    _compare([inst], 16, 2, False)
+
+
+def test_fm_uneven_integer_batch():
+    insts = [W.random_graph(n, 3.0, 80 + n, dtype="i8", n_hyper=n // 20, hyper_order=(3,))
+             for n in (1, 5, 100, 700)]
+    _compare(insts, 8, 2, True)
+
+
+def test_fm_chimera_2048_float():
+    inst = W.chimera(16, seed=74)
+    _compare([inst], 4, 1, False)
+
+
+def test_fm_dense_sk():
+    inst = W.sk(128, seed=75)
+    _compare([inst], 8, 2, False)
+
+
+def test_fm_reaches_lower_energies_than_greedy_descent():
+    """Same starts: the passes with hill climbing end no higher than the first
+    1-flip minimum (a pass only keeps a strictly better prefix), and lower on
+    average."""
+    inst = W.lattice((32, 32), periodic=True, couplings="gauss", seed=76)
+    R, seed = 64, 77
+    h = isg.Handle([inst])
+    _, E_fm, _, _ = h.fm_search([seed], R, restarts=1)
+    res = h.local_search([seed], R, max_sweeps=1000, restarts=1, refresh_every=1, schedule=isg.SCHED_SEQUENTIAL)
+    torch.cuda.synchronize()
+    e_fm, e_gd = E_fm[0].cpu().numpy(), res.energy[0].cpu().numpy()
+    assert e_fm.mean() < e_gd.mean()
+    h.close()
+
+
+def test_fm_rejects_instances_beyond_its_size():
+    inst = W.lattice((72, 72), periodic=True, couplings="pm1", seed=78)  # 5184 spins
+    h = isg.Handle([inst])
+    with pytest.raises(isg.IsingError) as ei:
+        h.fm_search([1], 4)
+    assert ei.value.code == 6  # ISING_ERR_UNSUPPORTED
+    h.close()
