@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <cstdlib>
 #include <map>
 #include <vector>
 
@@ -39,13 +40,14 @@ constexpr int kFmMaxSpins = 4096;
 
 struct FmArgs {
   DevGraph g;
-  int32_t n_items, R, restarts, max_passes, is_float;
+  int32_t n_work, R_out, restarts, max_passes, is_float;
+  int32_t split;              // 1: one start per work unit (work = item * restarts + start)
   const int2 *items;          // (instance, replica), largest instances first
   const uint64_t *seeds;      // [instances]
   int32_t *queue;
-  int8_t *spins;              // [instance block: R x n] results
-  double *energy;             // [instance][replica]
-  int32_t *passes;            // [instance][replica] or null
+  int8_t *spins;              // [instance block: R_out x n] results
+  double *energy;             // [instance][R_out]
+  int32_t *passes;            // [instance][R_out] or null
   unsigned long long *stats;
 };
 
@@ -83,7 +85,7 @@ __device__ __forceinline__ unsigned long long gain_key(double f, int8_t s) {
 
 // E (Eq. 1 extended by Eq. 6) by one warp: pairs once (j > i), fields,
 // hyper-edges; lane partial sums, then the warp sum (a fixed order)
-__device__ double fm_energy(const DevGraph &G, const InstDesc &I, bool fl, const int8_t *s, int lane) {
+__device__ __forceinline__ double fm_energy(const DevGraph &G, const InstDesc &I, bool fl, const int8_t *s, int lane) {
   double acc = 0.0;
   for (int i = lane; i < I.n; i += 32) {
     const int64_t gi = I.spin_off + i;
@@ -101,13 +103,71 @@ __device__ double fm_energy(const DevGraph &G, const InstDesc &I, bool fl, const
   return warp_sum(acc);
 }
 
-// bytes of shared memory one warp needs for an instance of n spins
+// bytes of shared memory one warp needs for an instance of n spins:
+// fields (FP64), block maxima (key, index), lock and dirty bits, the pass's
+// moves (16-bit), spins and the best spins over the starts
 __host__ __device__ constexpr size_t fm_warp_bytes(int n) {
-  return (size_t)n * 8 + (size_t)n * 4 + (size_t)((n + 31) / 32) * 4 + (size_t)n * 2 + 16;
+  return (size_t)n * 12 + (size_t)((n + 31) / 32) * 14 + 16;
 }
 
-// One warp per (instance, replica): no CTA barriers on the per-move path.
-__global__ void __launch_bounds__(kFT) fm_kernel(FmArgs A, int nmax) {
+// The warp's maximum of (key, index) pairs: the largest key, among equal keys
+// the lowest index.  Every lane receives it.  Keys of real gains are never 0
+// (see gain_key), so key 0 marks "no candidate".
+struct KeyIdx {
+  unsigned long long key;
+  int idx;
+};
+__device__ __forceinline__ KeyIdx warp_argmax(unsigned long long key, int idx) {
+  const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
+  const unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
+  const unsigned mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
+  const int mi = __reduce_min_sync(0xffffffffu, (hi == mhi && lo == mlo) ? idx : 0x7fffffff);
+  return {((unsigned long long)mhi << 32) | mlo, mi};
+}
+
+// Per-warp state of one search, carved out of the warp's shared memory.
+struct FmState {
+  double *f;                // [n] fields
+  unsigned long long *bkey; // [nb] largest unlocked gain key of each 32-spin block (0: none)
+  uint32_t *lock;           // [nb] spins moved in this pass
+  uint32_t *dirty;          // [4] blocks whose maximum must be recomputed
+  int16_t *moves;           // [n] the pass's moves in order
+  int16_t *bidx;            // [nb] the spin of each block maximum (lowest of equal keys)
+  int8_t *s, *sb;           // [n] spins, best spins over the starts
+  int n, nb;
+};
+__device__ __forceinline__ FmState fm_state(uint8_t *base, int n) {
+  FmState S;
+  S.n = n;
+  S.nb = (n + 31) / 32;
+  S.f = reinterpret_cast<double *>(base);
+  S.bkey = reinterpret_cast<unsigned long long *>(S.f + n);
+  S.lock = reinterpret_cast<uint32_t *>(S.bkey + S.nb);
+  S.dirty = S.lock + S.nb;
+  S.moves = reinterpret_cast<int16_t *>(S.dirty + 4);
+  S.bidx = S.moves + n;
+  S.s = reinterpret_cast<int8_t *>(S.bidx + S.nb);
+  S.sb = S.s + n;
+  return S;
+}
+
+// block j's maximum over its unlocked spins, one lane per spin
+__device__ __forceinline__ void block_max(const FmState &S, int j, int lane) {
+  const int i = (j << 5) + lane;
+  unsigned long long key = 0ull;
+  if (i < S.n && !((S.lock[j] >> lane) & 1u)) key = gain_key(S.f[i], S.s[i]);
+  const KeyIdx m = warp_argmax(key, i);
+  if (lane == 0) {
+    S.bkey[j] = m.key;
+    S.bidx[j] = (int16_t)m.idx;
+  }
+}
+
+// One warp per search (instance, replica, a range of starts): no CTA barriers
+// on the per-move path.  The move's spin is the maximum over the cached block
+// maxima; a move recomputes only the blocks it touched (the moved spin's and
+// those of the spins whose fields changed).
+__global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
   extern __shared__ __align__(16) uint8_t fm_smem[];
   const DevGraph &G = A.g;
   const bool fl = A.is_float != 0;
@@ -115,23 +175,25 @@ __global__ void __launch_bounds__(kFT) fm_kernel(FmArgs A, int nmax) {
   uint8_t *base = fm_smem + (size_t)warp * ((fm_warp_bytes(nmax) + 15) & ~(size_t)15);
   unsigned long long c_moves = 0, c_passes = 0, c_starts = 0;
   for (;;) {
-    int it = 0;
-    if (lane == 0) it = atomicAdd(A.queue, 1);
-    it = __shfl_sync(0xffffffffu, it, 0);
-    if (it >= A.n_items) break;
+    int w = 0;
+    if (lane == 0) w = atomicAdd(A.queue, 1);
+    w = __shfl_sync(0xffffffffu, w, 0);
+    if (w >= A.n_work) break;
+    // split starts: one start per work unit, results to slot r * restarts + k
+    const int it = A.split ? w / A.restarts : w;
+    const int k0 = A.split ? w % A.restarts : 0, k1 = A.split ? k0 + 1 : A.restarts;
     const int b = A.items[it].x, r = A.items[it].y;
+    const int slot = A.split ? r * A.restarts + k0 : r;
     const InstDesc I = G.inst[b];
     const int n = I.n;
     const int64_t so = I.spin_off;
-    double *f = reinterpret_cast<double *>(base);                          // [n] fields
-    int32_t *moves = reinterpret_cast<int32_t *>(f + n);                  // [n] moves of the pass
-    uint32_t *lock = reinterpret_cast<uint32_t *>(moves + n);             // [n/32] moved in this pass
-    int8_t *s = reinterpret_cast<int8_t *>(lock + (n + 31) / 32);         // [n] spins
-    int8_t *sb = s + n;                                                   // [n] best over the starts
+    const FmState S = fm_state(base, n);
+    double *f = S.f;
+    int8_t *s = S.s;
     const uint64_t seed = A.seeds[b];
-    double E_all = DBL_MAX;  // lane 0's copy is used
+    double E_all = DBL_MAX;
     int total_passes = 0;
-    for (int k = 0; k < A.restarts; ++k) {
+    for (int k = k0; k < k1; ++k) {
       for (int i = lane; i < n; i += 32) {
         const uint4 x = start_bits(seed, (uint32_t)(i >> 7), (uint32_t)r, (uint32_t)k, (uint32_t)b);
         s[i] = ((word_of(x, (i & 127) >> 5) >> (i & 31)) & 1u) ? 1 : -1;
@@ -153,32 +215,26 @@ __global__ void __launch_bounds__(kFT) fm_kernel(FmArgs A, int nmax) {
           }
           f[i] = acc;
         }
-        for (int w = lane; w < (n + 31) / 32; w += 32) lock[w] = 0u;
+        for (int j = lane; j < S.nb; j += 32) S.lock[j] = 0u;
+        if (lane < 4) S.dirty[lane] = 0u;
+        __syncwarp();
+        for (int j = 0; j < S.nb; ++j) block_max(S, j, lane);
         __syncwarp();
         double Ecur = Estar, Ebest = Estar;  // lane 0's copies are used
         int best_prefix = 0;
         for (int step = 0; step < n; ++step) {
-          // the largest gain among unlocked spins, ties to the lowest index
+          // the largest gain among unlocked spins, ties to the lowest index:
+          // blocks in ascending order per lane, then across lanes
           unsigned long long bk = 0ull;
           int bi = 0x7fffffff;
-          for (int i = lane; i < n; i += 32) {
-            if ((lock[i >> 5] >> lane) & 1u) continue;  // i & 31 == lane
-            const unsigned long long key = gain_key(f[i], s[i]);
-            if (bi == 0x7fffffff || key > bk) {  // ascending i: the first of equal keys stays
+          for (int j = lane; j < S.nb; j += 32) {
+            const unsigned long long key = S.bkey[j];
+            if (key > bk) {
               bk = key;
-              bi = i;
+              bi = S.bidx[j];
             }
           }
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (oi != 0x7fffffff && (bi == 0x7fffffff || ok > bk || (ok == bk && oi < bi))) {
-              bk = ok;
-              bi = oi;
-            }
-          }
-          const int i = bi;  // every lane holds the same winner
+          const int i = warp_argmax(bk, bi).idx;
           if (lane == 0) {
             const double gain = -2.0 * (double)s[i] * f[i];
             Ecur -= gain;  // apply the move
@@ -186,8 +242,9 @@ __global__ void __launch_bounds__(kFT) fm_kernel(FmArgs A, int nmax) {
               Ebest = Ecur;
               best_prefix = step + 1;
             }
-            moves[step] = i;
-            lock[i >> 5] |= 1u << (i & 31);
+            S.moves[step] = (int16_t)i;
+            S.lock[i >> 5] |= 1u << (i & 31);
+            S.dirty[i >> 10] |= 1u << ((i >> 5) & 31);
             s[i] = (int8_t)-s[i];
           }
           __syncwarp();
@@ -195,8 +252,11 @@ __global__ void __launch_bounds__(kFT) fm_kernel(FmArgs A, int nmax) {
           // then the hyper-edges in order (one lane: shared members possible)
           const double si2 = 2.0 * (double)s[i];
           const int64_t gi = so + i;
-          for (uint32_t kk = __ldg(G.row + gi) + lane, ke = __ldg(G.row + gi + 1); kk < ke; kk += 32)
-            f[__ldg(G.col + kk)] += coupling(G, fl, kk) * si2;
+          for (uint32_t kk = __ldg(G.row + gi) + lane, ke = __ldg(G.row + gi + 1); kk < ke; kk += 32) {
+            const int c = __ldg(G.col + kk);
+            f[c] += coupling(G, fl, kk) * si2;
+            atomicOr(S.dirty + (c >> 10), 1u << ((c >> 5) & 31));
+          }
           const uint32_t u0 = __ldg(G.inc_ptr + gi), u1 = __ldg(G.inc_ptr + gi + 1);
           if (u0 < u1) {
             __syncwarp();
@@ -206,15 +266,29 @@ __global__ void __launch_bounds__(kFT) fm_kernel(FmArgs A, int nmax) {
                 const double w2 = 2.0 * coupling_e(G, fl, e);
                 for (uint32_t q = __ldg(G.hptr + e), qe = __ldg(G.hptr + e + 1); q < qe; ++q) {
                   const int m = __ldg(G.hmem + q);
-                  if (m != i) f[m] += w2 * hyper_prod(G, e, s, m);
+                  if (m != i) {
+                    f[m] += w2 * hyper_prod(G, e, s, m);
+                    S.dirty[m >> 10] |= 1u << ((m >> 5) & 31);
+                  }
                 }
               }
           }
           __syncwarp();
+          for (int dw = 0; dw < (S.nb + 31) / 32; ++dw) {
+            unsigned d = S.dirty[dw];
+            while (d) {
+              const int jb = __ffs(d) - 1;
+              d &= d - 1u;
+              block_max(S, (dw << 5) + jb, lane);
+            }
+          }
+          __syncwarp();
+          if (lane < 4) S.dirty[lane] = 0u;
+          __syncwarp();
         }
         // roll back to the best prefix (each spin moved once: distinct entries)
         const int bp = __shfl_sync(0xffffffffu, best_prefix, 0);
-        for (int st = bp + lane; st < n; st += 32) s[moves[st]] = (int8_t)-s[moves[st]];
+        for (int st = bp + lane; st < n; st += 32) s[S.moves[st]] = (int8_t)-s[S.moves[st]];
         __syncwarp();
         const double Enew = fm_energy(G, I, fl, s, lane);
         const double margin = fl ? 1e-9 * (1.0 + fabs(Estar)) : 0.0;
@@ -226,7 +300,7 @@ __global__ void __launch_bounds__(kFT) fm_kernel(FmArgs A, int nmax) {
         if (Enew < Estar - margin) {
           Estar = Enew;  // pass cap reached after an improving pass: keep it
         } else {
-          for (int st = lane; st < bp; st += 32) s[moves[st]] = (int8_t)-s[moves[st]];
+          for (int st = lane; st < bp; st += 32) s[S.moves[st]] = (int8_t)-s[S.moves[st]];
           __syncwarp();
         }
         break;
@@ -237,15 +311,15 @@ __global__ void __launch_bounds__(kFT) fm_kernel(FmArgs A, int nmax) {
       // keep the best start (strictly lower energy; ties keep the earlier)
       if (Estar < E_all) {
         E_all = Estar;
-        for (int i = lane; i < n; i += 32) sb[i] = s[i];
+        for (int i = lane; i < n; i += 32) S.sb[i] = s[i];
       }
       __syncwarp();
     }
-    int8_t *out = A.spins + (int64_t)A.R * so + (int64_t)r * n;
-    for (int i = lane; i < n; i += 32) out[i] = sb[i];
+    int8_t *out = A.spins + (int64_t)A.R_out * so + (int64_t)slot * n;
+    for (int i = lane; i < n; i += 32) out[i] = S.sb[i];
     if (lane == 0) {
-      A.energy[(int64_t)b * A.R + r] = E_all;
-      if (A.passes) A.passes[(int64_t)b * A.R + r] = total_passes;
+      A.energy[(int64_t)b * A.R_out + slot] = E_all;
+      if (A.passes) A.passes[(int64_t)b * A.R_out + slot] = total_passes;
     }
     __syncwarp();
   }
@@ -257,29 +331,85 @@ __global__ void __launch_bounds__(kFT) fm_kernel(FmArgs A, int nmax) {
   }
 }
 
-// device (instance, replica) lists per handle, kept across calls
-std::map<const ising_handle *, std::pair<int2 *, int64_t>> &fm_items() {
-  static std::map<const ising_handle *, std::pair<int2 *, int64_t>> m;
+// After split starts: per (instance, replica) the best start (strictly lower
+// energy, ties keep the earlier start), its spins, and the pass count summed
+// over the starts.  One warp per (instance, replica).
+__global__ void fm_best_start_kernel(const InstDesc *inst, int32_t n_inst, int32_t R, int32_t restarts,
+                                     const int8_t *spins_k, const double *E_k, const int32_t *passes_k,
+                                     int8_t *spins, double *E, int32_t *passes) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (wid >= (int64_t)n_inst * R) return;
+  const int b = (int)(wid / R), r = (int)(wid % R);
+  const InstDesc I = inst[b];
+  const int64_t base = (int64_t)b * R * restarts + (int64_t)r * restarts;
+  int best = 0;
+  double Eb = E_k[base];
+  int tp = passes_k ? passes_k[base] : 0;
+  for (int k = 1; k < restarts; ++k) {
+    const double e = E_k[base + k];
+    if (e < Eb) {
+      Eb = e;
+      best = k;
+    }
+    if (passes_k) tp += passes_k[base + k];
+  }
+  const int8_t *src = spins_k + (int64_t)R * restarts * I.spin_off + ((int64_t)r * restarts + best) * I.n;
+  int8_t *dst = spins + (int64_t)R * I.spin_off + (int64_t)r * I.n;
+  for (int i = lane; i < I.n; i += 32) dst[i] = src[i];
+  if (lane == 0) {
+    E[(int64_t)b * R + r] = Eb;
+    if (passes) passes[(int64_t)b * R + r] = tp;
+  }
+}
+
+// device buffers per handle, kept across calls: the (instance, replica)
+// list and, for split starts, every start's result
+struct FmBufs {
+  int2 *items = nullptr;
+  int64_t n_items = 0;
+  void *scratch = nullptr;
+  size_t scratch_bytes = 0;
+};
+std::map<const ising_handle *, FmBufs> &fm_bufs() {
+  static std::map<const ising_handle *, FmBufs> m;
   return m;
 }
+
+cudaError_t grow(void **p, size_t &have, size_t need) {
+  if (have >= need) return cudaSuccess;
+  cudaFree(*p);
+  *p = nullptr;
+  have = 0;
+  const cudaError_t e = cudaMalloc(p, need);
+  if (e == cudaSuccess) have = need;
+  return e;
+}
+
+constexpr size_t kSplitScratchMax = size_t(1) << 30;  // bytes of per-start results at most
 
 }  // namespace
 
 int fm_max_spins() { return kFmMaxSpins; }
 
-// One launch over every (instance, replica).  seeds: device [instances].
+// One launch over every (instance, replica), plus a selection launch when the
+// starts run in parallel.  seeds: device [instances].
 cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_passes, int8_t *spins, double *E,
                       int32_t *passes, cudaStream_t s) {
   const int64_t n_items = (int64_t)h->n_inst * R;
   if (n_items > 0x7fffffff) return cudaErrorInvalidValue;
-  auto &slot = fm_items()[h];
+  FmBufs &B = fm_bufs()[h];
   cudaError_t e;
-  if (slot.second < n_items) {
-    cudaFree(slot.first);
-    slot.first = nullptr;
-    slot.second = 0;
-    if ((e = cudaMalloc(&slot.first, (size_t)n_items * sizeof(int2))) != cudaSuccess) return e;
-    slot.second = n_items;
+  if (B.n_items < n_items) {
+    size_t have = 0;
+    void *p = B.items;
+    if ((e = grow(&p, have, (size_t)n_items * sizeof(int2))) != cudaSuccess) {
+      B.items = nullptr;
+      B.n_items = 0;
+      return e;
+    }
+    B.items = static_cast<int2 *>(p);
+    B.n_items = n_items;
   }
   std::vector<int32_t> ord(h->n_inst);
   for (int32_t b = 0; b < h->n_inst; ++b) ord[b] = b;
@@ -288,26 +418,13 @@ cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_
   items.reserve((size_t)n_items);
   for (int32_t b : ord)
     for (int32_t r = 0; r < R; ++r) items.push_back(make_int2(b, r));
-  if ((e = cudaMemcpyAsync(slot.first, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, s)) !=
+  if ((e = cudaMemcpyAsync(B.items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, s)) !=
       cudaSuccess)
     return e;
   if ((e = cudaMemsetAsync(h->d_queue, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
-  FmArgs A;
-  A.g = h->graph();
-  A.n_items = (int32_t)n_items;
-  A.R = R;
-  A.restarts = restarts;
-  A.max_passes = max_passes;
-  A.is_float = h->dtype == ISING_F32 ? 1 : 0;
-  A.items = slot.first;
-  A.seeds = h->d_seeds;
-  A.queue = h->d_queue;
-  A.spins = spins;
-  A.energy = E;
-  A.passes = passes;
-  A.stats = h->d_stats;
+
   const int nmax = h->nmax;
-  // warps per CTA (one replica each) as shared memory allows
+  // warps per CTA (one search each) as shared memory allows
   const size_t per_warp = (fm_warp_bytes(nmax) + 15) & ~(size_t)15;
   int smem_optin = 0;
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
@@ -318,18 +435,61 @@ cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_
   int per_sm = 0;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fm_kernel, warps * 32, smem)) != cudaSuccess)
     return e;
-  const int64_t ctas_needed = (n_items + warps - 1) / warps;
+  const int64_t resident = (int64_t)h->sm_count * std::max(per_sm, 1) * warps;
+
+  // Starts run in parallel (one per warp, the best chosen afterwards) when
+  // the searches alone would leave the GPU underfilled.
+  const size_t sp_bytes = ((size_t)R * restarts * h->total_spins + 15) & ~(size_t)15;
+  const size_t e_bytes = (size_t)n_items * restarts * sizeof(double);
+  const size_t p_bytes = (size_t)n_items * restarts * sizeof(int32_t);
+  // ISING_FM_SPLIT=0 / 1 overrides the choice (both give the same results).
+  const char *force = std::getenv("ISING_FM_SPLIT");
+  const bool want = force && *force ? std::atoi(force) != 0 : n_items < 4 * resident;
+  const bool split = want && restarts > 1 && (int64_t)n_items * restarts <= 0x7fffffff &&
+                     sp_bytes + e_bytes + p_bytes <= kSplitScratchMax;
+  int8_t *sp_k = nullptr;
+  double *E_k = nullptr;
+  int32_t *P_k = nullptr;
+  if (split) {
+    if ((e = grow(&B.scratch, B.scratch_bytes, sp_bytes + e_bytes + p_bytes)) != cudaSuccess) return e;
+    sp_k = static_cast<int8_t *>(B.scratch);
+    E_k = reinterpret_cast<double *>(sp_k + sp_bytes);
+    P_k = reinterpret_cast<int32_t *>(E_k + (size_t)n_items * restarts);
+  }
+
+  FmArgs A;
+  A.g = h->graph();
+  A.n_work = (int32_t)(split ? n_items * restarts : n_items);
+  A.R_out = split ? R * restarts : R;
+  A.restarts = restarts;
+  A.max_passes = max_passes;
+  A.is_float = h->dtype == ISING_F32 ? 1 : 0;
+  A.split = split ? 1 : 0;
+  A.items = B.items;
+  A.seeds = h->d_seeds;
+  A.queue = h->d_queue;
+  A.spins = split ? sp_k : spins;
+  A.energy = split ? E_k : E;
+  A.passes = split ? P_k : passes;
+  A.stats = h->d_stats;
+  const int64_t ctas_needed = ((int64_t)A.n_work + warps - 1) / warps;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->sm_count * std::max(per_sm, 1), ctas_needed));
   fm_kernel<<<grid, warps * 32, smem, s>>>(A, nmax);
+  h->launches += 1;
+  if ((e = cudaGetLastError()) != cudaSuccess || !split) return e;
+  const int64_t threads = n_items * 32;
+  fm_best_start_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(h->d_inst, h->n_inst, R, restarts, sp_k,
+                                                                         E_k, P_k, spins, E, passes);
   h->launches += 1;
   return cudaGetLastError();
 }
 
 void fm_free(ising_handle *h) {
-  auto &m = fm_items();
+  auto &m = fm_bufs();
   auto it = m.find(h);
   if (it == m.end()) return;
-  cudaFree(it->second.first);
+  cudaFree(it->second.items);
+  cudaFree(it->second.scratch);
   m.erase(it);
 }
 

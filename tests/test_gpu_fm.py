@@ -115,3 +115,22 @@ def test_fm_rejects_instances_beyond_its_size():
         h.fm_search([1], 4)
     assert ei.value.code == 6  # ISING_ERR_UNSUPPORTED
     h.close()
+
+
+@pytest.mark.parametrize("dtype", ["i8", "f32"])
+def test_fm_parallel_and_sequential_starts_agree(monkeypatch, dtype):
+    """Starts run one per warp (the best chosen by a second launch) or one
+    after another in a warp: identical spins, energies and pass counts."""
+    insts = [W.random_graph(n, 4.0, 90 + n, dtype=dtype, n_hyper=n // 25, hyper_order=(3,)) for n in (64, 333, 1500)]
+    seeds = [11, 12, 13]
+    out = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("ISING_FM_SPLIT", mode)
+        h = isg.Handle(insts)
+        sp, E, P, st = h.fm_search(seeds, 24, restarts=4)
+        torch.cuda.synchronize()
+        out[mode] = (sp.cpu().numpy(), E.cpu().numpy(), P.cpu().numpy(), st["descents"], st["sweeps"])
+        h.close()
+    for a, b in zip(out["0"], out["1"]):
+        assert np.array_equal(a, b)
+    assert out["0"][3] == 3 * 24 * 4
