@@ -460,7 +460,7 @@ def run_fm(args, insts, R, kw, desc):
                "sample": f"{n_runs} oracle searches (first starts of this workload), {moves} moves, {dt:.1f} s"}
     line = {"metric": "pass-based search (Sec. IV, Fig. 3) moves/s on 1 GB300", "value": value, "unit": "moves/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 gains",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64 (FP64-exact instances) or f64",
             "data": "synthetic (seeded generators)",
             "config": {"workload": args.workload, "method": "fm", "description": desc, "replicas": R,
                        "restarts": restarts, "instances": len(insts),

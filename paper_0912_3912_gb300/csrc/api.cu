@@ -105,6 +105,28 @@ int32_t energy_base_exponent(const HostInst &I) {
   return emin;
 }
 
+// InstDesc::fx53: with unit u (2^(ebase - 150), or 1 for int8), the sum of
+// |term| / u over every coupling (both CSR directions), field and hyper-edge
+// coupling bounds every field, twice every gain and every energy; below 2^53
+// all of them, and every partial sum on the way, are exact in FP64.
+int32_t fp64_exact(const HostInst &I, bool fl, int32_t ebase) {
+  if (!fl) return 1;  // |terms| <= 127 and far fewer than 2^45 of them
+  if (ebase < 0) return 0;
+  unsigned __int128 sum = 0;
+  auto add = [&](float v) {
+    uint32_t b;
+    std::memcpy(&b, &v, 4);
+    b &= 0x7fffffffu;
+    if (!b) return;
+    const int e = (int)(b >> 23);
+    sum += (unsigned __int128)((b & 0x7fffffu) | 0x800000u) << (e - ebase);
+  };
+  for (float v : I.Jf) add(v);
+  for (float v : I.hf) add(v);
+  for (float v : I.hJf) add(v);
+  return 2 * sum < ((unsigned __int128)1 << 53) ? 1 : 0;
+}
+
 // Recognise a periodic hypercubic lattice (side L >= 3, d = 2 or 3, spin index
 // x0 + L*x1 + L^2*x2) from the CSR structure alone.
 void detect_lattice(HostInst &I) {
@@ -683,7 +705,7 @@ ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
     D.lat_L = I.lat_L;
     D.lat_d = I.lat_d;
     D.ebase = fl ? energy_base_exponent(I) : -1;
-    D.pad_ = 0;
+    D.fx53 = fp64_exact(I, fl, D.ebase);
     h->any_lattice = h->any_lattice || I.lat_d > 0;
     h->all_lattice = (b == 0 ? true : h->all_lattice) && I.lat_d > 0;
     h->nmax = std::max(h->nmax, I.n);

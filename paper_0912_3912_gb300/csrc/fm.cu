@@ -26,6 +26,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <map>
+#include <type_traits>
 #include <vector>
 
 #include "device_common.cuh"
@@ -81,6 +82,60 @@ __device__ __forceinline__ unsigned long long gain_key(double f, int8_t s) {
   if (s > 0) b ^= 0x8000000000000000ull;  // the gain has the sign of -s f
   if ((b << 1) == 0ull) b = 0ull;          // -0 -> +0
   return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// ---- the same search in exact integers ----------------------------------
+// When every field, gain and energy value of an instance is an integer
+// multiple of a unit u (2^(ebase - 150) for FP32 couplings, 1 for int8) below
+// 2^53 in magnitude (InstDesc::fx53), FP64 computes all of them without
+// rounding; the search then runs on 64-bit integers in units of u and gives
+// bit-identical results with no FP64 arithmetic on the per-move path.
+
+// spin product of hyper-edge e except `skip` (-1: all), as +1 or -1
+__device__ __forceinline__ int hyper_sign(const DevGraph &G, int64_t e, const int8_t *s, int skip) {
+  int neg = 0;
+  for (uint32_t q = __ldg(G.hptr + e), qe = __ldg(G.hptr + e + 1); q < qe; ++q) {
+    const int m = __ldg(G.hmem + q);
+    if (m != skip) neg ^= s[m] < 0;
+  }
+  return neg ? -1 : 1;
+}
+
+// coupling or field k of array p in units of u
+__device__ __forceinline__ long long fx_of(const void *p, bool fl, int64_t k, int unit) {
+  return fl ? (long long)xr_term(__ldg(reinterpret_cast<const float *>(p) + k), unit)
+            : (long long)__ldg(reinterpret_cast<const int8_t *>(p) + k);
+}
+
+// order-preserving key of the gain -2 s f (|gain| < 2^54: never key 0)
+__device__ __forceinline__ unsigned long long gain_key_fx(long long f, int8_t s) {
+  const long long g = s > 0 ? -2 * f : 2 * f;
+  return (unsigned long long)g ^ 0x8000000000000000ull;
+}
+
+// E in units of u by one warp (integer sums: the order does not matter)
+__device__ __forceinline__ long long fm_energy_fx(const DevGraph &G, const InstDesc &I, bool fl, const int8_t *s,
+                                                  int lane, int unit) {
+  long long acc = 0;
+  for (int i = lane; i < I.n; i += 32) {
+    const int64_t gi = I.spin_off + i;
+    const int8_t si = s[i];
+    for (uint32_t k = __ldg(G.row + gi), ke = __ldg(G.row + gi + 1); k < ke; ++k) {
+      const int j = __ldg(G.col + k);
+      if (j > i) {
+        const long long t = fx_of(G.J, fl, k, unit);
+        acc -= (si == s[j]) ? t : -t;
+      }
+    }
+    const long long th = fx_of(G.h, fl, gi, unit);
+    acc -= si > 0 ? th : -th;
+  }
+  for (int e = lane; e < I.n_hyper; e += 32) {
+    const int64_t ge = I.hyper_off + e;
+    const long long t = fx_of(G.hJ, fl, ge, unit);
+    acc -= hyper_sign(G, ge, s, -1) > 0 ? t : -t;
+  }
+  return warp_sum(acc);
 }
 
 // E (Eq. 1 extended by Eq. 6) by one warp: pairs once (j > i), fields,
@@ -152,10 +207,16 @@ __device__ __forceinline__ FmState fm_state(uint8_t *base, int n) {
 }
 
 // block j's maximum over its unlocked spins, one lane per spin
+template <bool FX>
 __device__ __forceinline__ void block_max(const FmState &S, int j, int lane) {
   const int i = (j << 5) + lane;
   unsigned long long key = 0ull;
-  if (i < S.n && !((S.lock[j] >> lane) & 1u)) key = gain_key(S.f[i], S.s[i]);
+  if (i < S.n && !((S.lock[j] >> lane) & 1u)) {
+    if constexpr (FX)
+      key = gain_key_fx(reinterpret_cast<const long long *>(S.f)[i], S.s[i]);
+    else
+      key = gain_key(S.f[i], S.s[i]);
+  }
   const KeyIdx m = warp_argmax(key, i);
   if (lane == 0) {
     S.bkey[j] = m.key;
@@ -166,8 +227,11 @@ __device__ __forceinline__ void block_max(const FmState &S, int j, int lane) {
 // One warp per search (instance, replica, a range of starts): no CTA barriers
 // on the per-move path.  The move's spin is the maximum over the cached block
 // maxima; a move recomputes only the blocks it touched (the moved spin's and
-// those of the spins whose fields changed).
+// those of the spins whose fields changed).  FX: exact integer arithmetic in
+// units of u (instances with InstDesc::fx53 set), else FP64.
+template <bool FX>
 __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
+  using T = std::conditional_t<FX, long long, double>;
   extern __shared__ __align__(16) uint8_t fm_smem[];
   const DevGraph &G = A.g;
   const bool fl = A.is_float != 0;
@@ -187,10 +251,23 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
     const InstDesc I = G.inst[b];
     const int n = I.n;
     const int64_t so = I.spin_off;
+    const int unit = I.ebase;  // FX with FP32 couplings: u = 2^(unit - 150)
+    const double scale = (FX && fl) ? __longlong_as_double((long long)(unit - 150 + 1023) << 52) : 1.0;
     const FmState S = fm_state(base, n);
-    double *f = S.f;
+    T *f = reinterpret_cast<T *>(S.f);
     int8_t *s = S.s;
     const uint64_t seed = A.seeds[b];
+    // E of the current spins: FP64 (the same value in every lane), and in FX
+    // also the integer it is exactly
+    auto energy = [&](long long &Ei) -> double {
+      if constexpr (FX) {
+        Ei = fm_energy_fx(G, I, fl, s, lane, unit);
+        return (double)Ei * scale;
+      } else {
+        Ei = 0;
+        return fm_energy(G, I, fl, s, lane);
+      }
+    };
     double E_all = DBL_MAX;
     int total_passes = 0;
     for (int k = k0; k < k1; ++k) {
@@ -199,28 +276,48 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
         s[i] = ((word_of(x, (i & 127) >> 5) >> (i & 31)) & 1u) ? 1 : -1;
       }
       __syncwarp();
-      double Estar = fm_energy(G, I, fl, s, lane);  // the same value in every lane
+      long long EstarI;
+      double Estar = energy(EstarI);
       int passes = 0;
       for (;;) {
         ++passes;
         // fields: h, the CSR row in order, then the hyper-edges in ascending order
         for (int i = lane; i < n; i += 32) {
           const int64_t gi = so + i;
-          double acc = field_h(G, fl, gi);
-          for (uint32_t kk = __ldg(G.row + gi), ke = __ldg(G.row + gi + 1); kk < ke; ++kk)
-            acc += coupling(G, fl, kk) * (double)s[__ldg(G.col + kk)];
-          for (uint32_t u = __ldg(G.inc_ptr + gi), ue = __ldg(G.inc_ptr + gi + 1); u < ue; ++u) {
-            const int64_t e = __ldg(G.inc_edge + u);
-            acc += coupling_e(G, fl, e) * hyper_prod(G, e, s, i);
+          if constexpr (FX) {
+            long long acc = fx_of(G.h, fl, gi, unit);
+            for (uint32_t kk = __ldg(G.row + gi), ke = __ldg(G.row + gi + 1); kk < ke; ++kk) {
+              const long long t = fx_of(G.J, fl, kk, unit);
+              acc += s[__ldg(G.col + kk)] > 0 ? t : -t;
+            }
+            for (uint32_t u = __ldg(G.inc_ptr + gi), ue = __ldg(G.inc_ptr + gi + 1); u < ue; ++u) {
+              const int64_t e = __ldg(G.inc_edge + u);
+              const long long t = fx_of(G.hJ, fl, e, unit);
+              acc += hyper_sign(G, e, s, i) > 0 ? t : -t;
+            }
+            f[i] = acc;
+          } else {
+            double acc = field_h(G, fl, gi);
+            for (uint32_t kk = __ldg(G.row + gi), ke = __ldg(G.row + gi + 1); kk < ke; ++kk)
+              acc += coupling(G, fl, kk) * (double)s[__ldg(G.col + kk)];
+            for (uint32_t u = __ldg(G.inc_ptr + gi), ue = __ldg(G.inc_ptr + gi + 1); u < ue; ++u) {
+              const int64_t e = __ldg(G.inc_edge + u);
+              acc += coupling_e(G, fl, e) * hyper_prod(G, e, s, i);
+            }
+            f[i] = acc;
           }
-          f[i] = acc;
         }
         for (int j = lane; j < S.nb; j += 32) S.lock[j] = 0u;
         if (lane < 4) S.dirty[lane] = 0u;
         __syncwarp();
-        for (int j = 0; j < S.nb; ++j) block_max(S, j, lane);
+        for (int j = 0; j < S.nb; ++j) block_max<FX>(S, j, lane);
         __syncwarp();
-        double Ecur = Estar, Ebest = Estar;  // lane 0's copies are used
+        T Ecur, Ebest;  // lane 0's copies are used
+        if constexpr (FX)
+          Ecur = EstarI;
+        else
+          Ecur = Estar;
+        Ebest = Ecur;
         int best_prefix = 0;
         for (int step = 0; step < n; ++step) {
           // the largest gain among unlocked spins, ties to the lowest index:
@@ -236,7 +333,11 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
           }
           const int i = warp_argmax(bk, bi).idx;
           if (lane == 0) {
-            const double gain = -2.0 * (double)s[i] * f[i];
+            T gain;
+            if constexpr (FX)
+              gain = s[i] > 0 ? -2 * f[i] : 2 * f[i];
+            else
+              gain = -2.0 * (double)s[i] * f[i];
             Ecur -= gain;  // apply the move
             if (Ecur < Ebest) {
               Ebest = Ecur;
@@ -250,11 +351,16 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
           __syncwarp();
           // neighbours' fields: the CSR row (distinct columns, one lane each),
           // then the hyper-edges in order (one lane: shared members possible)
-          const double si2 = 2.0 * (double)s[i];
+          const int8_t snew = s[i];
           const int64_t gi = so + i;
           for (uint32_t kk = __ldg(G.row + gi) + lane, ke = __ldg(G.row + gi + 1); kk < ke; kk += 32) {
             const int c = __ldg(G.col + kk);
-            f[c] += coupling(G, fl, kk) * si2;
+            if constexpr (FX) {
+              const long long t2 = 2 * fx_of(G.J, fl, kk, unit);
+              f[c] += snew > 0 ? t2 : -t2;
+            } else {
+              f[c] += coupling(G, fl, kk) * (2.0 * (double)snew);
+            }
             atomicOr(S.dirty + (c >> 10), 1u << ((c >> 5) & 31));
           }
           const uint32_t u0 = __ldg(G.inc_ptr + gi), u1 = __ldg(G.inc_ptr + gi + 1);
@@ -263,12 +369,23 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
             if (lane == 0)
               for (uint32_t u = u0; u < u1; ++u) {
                 const int64_t e = __ldg(G.inc_edge + u);
-                const double w2 = 2.0 * coupling_e(G, fl, e);
-                for (uint32_t q = __ldg(G.hptr + e), qe = __ldg(G.hptr + e + 1); q < qe; ++q) {
-                  const int m = __ldg(G.hmem + q);
-                  if (m != i) {
-                    f[m] += w2 * hyper_prod(G, e, s, m);
-                    S.dirty[m >> 10] |= 1u << ((m >> 5) & 31);
+                if constexpr (FX) {
+                  const long long w2 = 2 * fx_of(G.hJ, fl, e, unit);
+                  for (uint32_t q = __ldg(G.hptr + e), qe = __ldg(G.hptr + e + 1); q < qe; ++q) {
+                    const int m = __ldg(G.hmem + q);
+                    if (m != i) {
+                      f[m] += hyper_sign(G, e, s, m) > 0 ? w2 : -w2;
+                      S.dirty[m >> 10] |= 1u << ((m >> 5) & 31);
+                    }
+                  }
+                } else {
+                  const double w2 = 2.0 * coupling_e(G, fl, e);
+                  for (uint32_t q = __ldg(G.hptr + e), qe = __ldg(G.hptr + e + 1); q < qe; ++q) {
+                    const int m = __ldg(G.hmem + q);
+                    if (m != i) {
+                      f[m] += w2 * hyper_prod(G, e, s, m);
+                      S.dirty[m >> 10] |= 1u << ((m >> 5) & 31);
+                    }
                   }
                 }
               }
@@ -279,7 +396,7 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
             while (d) {
               const int jb = __ffs(d) - 1;
               d &= d - 1u;
-              block_max(S, (dw << 5) + jb, lane);
+              block_max<FX>(S, (dw << 5) + jb, lane);
             }
           }
           __syncwarp();
@@ -290,11 +407,13 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
         const int bp = __shfl_sync(0xffffffffu, best_prefix, 0);
         for (int st = bp + lane; st < n; st += 32) s[S.moves[st]] = (int8_t)-s[S.moves[st]];
         __syncwarp();
-        const double Enew = fm_energy(G, I, fl, s, lane);
+        long long EnewI;
+        const double Enew = energy(EnewI);
         const double margin = fl ? 1e-9 * (1.0 + fabs(Estar)) : 0.0;
         c_moves += (unsigned long long)n;
         if (Enew < Estar - margin && (A.max_passes <= 0 || passes < A.max_passes)) {
           Estar = Enew;
+          EstarI = EnewI;
           continue;
         }
         if (Enew < Estar - margin) {
@@ -364,10 +483,12 @@ __global__ void fm_best_start_kernel(const InstDesc *inst, int32_t n_inst, int32
 }
 
 // device buffers per handle, kept across calls: the (instance, replica)
-// list and, for split starts, every start's result
+// list, the work-queue counters and, for split starts, every start's result
 struct FmBufs {
   int2 *items = nullptr;
-  int64_t n_items = 0;
+  size_t items_bytes = 0;
+  int32_t *queues = nullptr;
+  size_t queues_bytes = 0;
   void *scratch = nullptr;
   size_t scratch_bytes = 0;
 };
@@ -376,69 +497,99 @@ std::map<const ising_handle *, FmBufs> &fm_bufs() {
   return m;
 }
 
-cudaError_t grow(void **p, size_t &have, size_t need) {
+template <typename P>
+cudaError_t grow(P *&p, size_t &have, size_t need) {
   if (have >= need) return cudaSuccess;
-  cudaFree(*p);
-  *p = nullptr;
+  cudaFree(p);
+  p = nullptr;
   have = 0;
-  const cudaError_t e = cudaMalloc(p, need);
-  if (e == cudaSuccess) have = need;
+  void *q = nullptr;
+  const cudaError_t e = cudaMalloc(&q, need);
+  if (e != cudaSuccess) return e;
+  p = static_cast<P *>(q);
+  have = need;
   return e;
 }
 
 constexpr size_t kSplitScratchMax = size_t(1) << 30;  // bytes of per-start results at most
 
+// One launch group: instances of one arithmetic (FX or FP64) whose size falls
+// in (lo, hi], so that each warp's shared memory is sized for hi.
+struct FmPart {
+  bool fx;
+  int nmax;
+  int64_t first, count;  // range of the item list
+};
+
+template <bool FX>
+cudaError_t fm_shape(const ising_handle *h, int nmax, int &warps, size_t &smem, int &per_sm) {
+  const size_t per_warp = (fm_warp_bytes(nmax) + 15) & ~(size_t)15;
+  int smem_optin = 0;
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  warps = (int)std::max<size_t>(1, std::min<size_t>(kFW, (size_t)smem_optin / per_warp));
+  smem = per_warp * warps;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(fm_kernel<FX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+      cudaSuccess)
+    return e;
+  per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fm_kernel<FX>, warps * 32, smem)) != cudaSuccess)
+    return e;
+  per_sm = std::max(per_sm, 1);
+  return cudaSuccess;
+}
+
 }  // namespace
 
 int fm_max_spins() { return kFmMaxSpins; }
 
-// One launch over every (instance, replica), plus a selection launch when the
-// starts run in parallel.  seeds: device [instances].
+// Launches over every (instance, replica): one per group of instances of like
+// arithmetic and size, plus a selection launch when the starts run in
+// parallel.  seeds: device [instances].
 cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_passes, int8_t *spins, double *E,
                       int32_t *passes, cudaStream_t s) {
   const int64_t n_items = (int64_t)h->n_inst * R;
   if (n_items > 0x7fffffff) return cudaErrorInvalidValue;
   FmBufs &B = fm_bufs()[h];
   cudaError_t e;
-  if (B.n_items < n_items) {
-    size_t have = 0;
-    void *p = B.items;
-    if ((e = grow(&p, have, (size_t)n_items * sizeof(int2))) != cudaSuccess) {
-      B.items = nullptr;
-      B.n_items = 0;
-      return e;
-    }
-    B.items = static_cast<int2 *>(p);
-    B.n_items = n_items;
-  }
+  // groups: exact-integer instances first, then FP64; within each, size
+  // classes (0, 256], (256, 512], ... (2048, 4096], largest first
+  auto cls = [](int n) {
+    int c = 0;
+    while (c < 4 && n > (256 << c)) ++c;
+    return c;
+  };
   std::vector<int32_t> ord(h->n_inst);
   for (int32_t b = 0; b < h->n_inst; ++b) ord[b] = b;
-  std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) { return h->inst[a].n > h->inst[c].n; });
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) {
+    const InstDesc &x = h->inst[a], &y = h->inst[c];
+    if (x.fx53 != y.fx53) return x.fx53 > y.fx53;
+    return x.n > y.n;
+  });
   std::vector<int2> items;
+  std::vector<FmPart> parts;
   items.reserve((size_t)n_items);
-  for (int32_t b : ord)
+  for (int32_t b : ord) {
+    const InstDesc &D = h->inst[b];
+    const bool fx = D.fx53 != 0;
+    if (parts.empty() || parts.back().fx != fx || cls(parts.back().nmax) != cls(D.n))
+      parts.push_back({fx, D.n, (int64_t)items.size(), 0});
     for (int32_t r = 0; r < R; ++r) items.push_back(make_int2(b, r));
+    parts.back().count += R;
+  }
+  if ((e = grow(B.items, B.items_bytes, (size_t)n_items * sizeof(int2))) != cudaSuccess) return e;
+  if ((e = grow(B.queues, B.queues_bytes, parts.size() * sizeof(int32_t))) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(B.items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, s)) !=
       cudaSuccess)
     return e;
-  if ((e = cudaMemsetAsync(h->d_queue, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
-
-  const int nmax = h->nmax;
-  // warps per CTA (one search each) as shared memory allows
-  const size_t per_warp = (fm_warp_bytes(nmax) + 15) & ~(size_t)15;
-  int smem_optin = 0;
-  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-  const int warps = (int)std::max<size_t>(1, std::min<size_t>(kFW, (size_t)smem_optin / per_warp));
-  const size_t smem = per_warp * warps;
-  if ((e = cudaFuncSetAttribute(fm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-    return e;
-  int per_sm = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fm_kernel, warps * 32, smem)) != cudaSuccess)
-    return e;
-  const int64_t resident = (int64_t)h->sm_count * std::max(per_sm, 1) * warps;
+  if ((e = cudaMemsetAsync(B.queues, 0, parts.size() * sizeof(int32_t), s)) != cudaSuccess) return e;
 
   // Starts run in parallel (one per warp, the best chosen afterwards) when
   // the searches alone would leave the GPU underfilled.
+  int warps0 = 0, per_sm0 = 0;
+  size_t smem0 = 0;
+  if ((e = fm_shape<true>(h, h->nmax, warps0, smem0, per_sm0)) != cudaSuccess) return e;
+  const int64_t resident = (int64_t)h->sm_count * per_sm0 * warps0;
   const size_t sp_bytes = ((size_t)R * restarts * h->total_spins + 15) & ~(size_t)15;
   const size_t e_bytes = (size_t)n_items * restarts * sizeof(double);
   const size_t p_bytes = (size_t)n_items * restarts * sizeof(int32_t);
@@ -451,32 +602,44 @@ cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_
   double *E_k = nullptr;
   int32_t *P_k = nullptr;
   if (split) {
-    if ((e = grow(&B.scratch, B.scratch_bytes, sp_bytes + e_bytes + p_bytes)) != cudaSuccess) return e;
+    if ((e = grow(B.scratch, B.scratch_bytes, sp_bytes + e_bytes + p_bytes)) != cudaSuccess) return e;
     sp_k = static_cast<int8_t *>(B.scratch);
     E_k = reinterpret_cast<double *>(sp_k + sp_bytes);
     P_k = reinterpret_cast<int32_t *>(E_k + (size_t)n_items * restarts);
   }
 
-  FmArgs A;
-  A.g = h->graph();
-  A.n_work = (int32_t)(split ? n_items * restarts : n_items);
-  A.R_out = split ? R * restarts : R;
-  A.restarts = restarts;
-  A.max_passes = max_passes;
-  A.is_float = h->dtype == ISING_F32 ? 1 : 0;
-  A.split = split ? 1 : 0;
-  A.items = B.items;
-  A.seeds = h->d_seeds;
-  A.queue = h->d_queue;
-  A.spins = split ? sp_k : spins;
-  A.energy = split ? E_k : E;
-  A.passes = split ? P_k : passes;
-  A.stats = h->d_stats;
-  const int64_t ctas_needed = ((int64_t)A.n_work + warps - 1) / warps;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->sm_count * std::max(per_sm, 1), ctas_needed));
-  fm_kernel<<<grid, warps * 32, smem, s>>>(A, nmax);
-  h->launches += 1;
-  if ((e = cudaGetLastError()) != cudaSuccess || !split) return e;
+  for (size_t q = 0; q < parts.size(); ++q) {
+    const FmPart &P = parts[q];
+    const int nmax = P.nmax;  // the group's largest instance
+    int warps = 0, per_sm = 0;
+    size_t smem = 0;
+    e = P.fx ? fm_shape<true>(h, nmax, warps, smem, per_sm) : fm_shape<false>(h, nmax, warps, smem, per_sm);
+    if (e != cudaSuccess) return e;
+    FmArgs A;
+    A.g = h->graph();
+    A.n_work = (int32_t)(split ? P.count * restarts : P.count);
+    A.R_out = split ? R * restarts : R;
+    A.restarts = restarts;
+    A.max_passes = max_passes;
+    A.is_float = h->dtype == ISING_F32 ? 1 : 0;
+    A.split = split ? 1 : 0;
+    A.items = B.items + P.first;
+    A.seeds = h->d_seeds;
+    A.queue = B.queues + q;
+    A.spins = split ? sp_k : spins;
+    A.energy = split ? E_k : E;
+    A.passes = split ? P_k : passes;
+    A.stats = h->d_stats;
+    const int64_t ctas_needed = ((int64_t)A.n_work + warps - 1) / warps;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->sm_count * per_sm, ctas_needed));
+    if (P.fx)
+      fm_kernel<true><<<grid, warps * 32, smem, s>>>(A, nmax);
+    else
+      fm_kernel<false><<<grid, warps * 32, smem, s>>>(A, nmax);
+    h->launches += 1;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (!split) return cudaSuccess;
   const int64_t threads = n_items * 32;
   fm_best_start_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(h->d_inst, h->n_inst, R, restarts, sp_k,
                                                                          E_k, P_k, spins, E, passes);
@@ -489,6 +652,7 @@ void fm_free(ising_handle *h) {
   auto it = m.find(h);
   if (it == m.end()) return;
   cudaFree(it->second.items);
+  cudaFree(it->second.queues);
   cudaFree(it->second.scratch);
   m.erase(it);
 }

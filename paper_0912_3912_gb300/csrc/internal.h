@@ -33,7 +33,10 @@ struct InstDesc {
   // when the energy can be summed exactly in 64-bit fixed point with that
   // unit (see xe_term), else -1 (FP64 sums instead)
   int32_t ebase;
-  int32_t pad_;
+  // 1 when every field, gain and energy value of the instance is an integer
+  // multiple of the unit (2^(ebase - 150) for FP32 couplings, 1 for int8)
+  // below 2^53 in magnitude, so FP64 arithmetic on them is exact
+  int32_t fx53;
 };
 
 // Everything a kernel needs to read an instance set.

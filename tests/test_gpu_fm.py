@@ -4,7 +4,11 @@ starts, the same passes, the same results.  Integer couplings: spins,
 energies and pass counts exactly equal.  Float couplings: spins and pass
 counts equal, energies within 1e-9 relative (the oracle sums energies with
 compensation, the kernel in plain FP64; the improvement margin of a pass
-absorbs that difference)."""
+absorbs that difference).  Instances whose fields and energies FP64 computes
+exactly run in 64-bit integers on the GPU; one test mixes such an instance
+with one whose couplings span too many binary orders for that (FP64 path)."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -134,3 +138,24 @@ def test_fm_parallel_and_sequential_starts_agree(monkeypatch, dtype):
     for a, b in zip(out["0"], out["1"]):
         assert np.array_equal(a, b)
     assert out["0"][3] == 3 * 24 * 4
+
+
+def _wide_spread(inst, scale=2.0 ** -60):
+    """A copy with one coupling pair scaled far below the rest: the couplings
+    then span more than 38 binary orders, so the integer form does not apply
+    and the kernel keeps FP64."""
+    J = inst.J.copy()
+    i = int(np.nonzero(np.diff(inst.row_ptr) > 0)[0][0])
+    k = int(inst.row_ptr[i])
+    j = int(inst.col[k])
+    J[k] = np.float32(J[k] * scale)
+    lo, hi = int(inst.row_ptr[j]), int(inst.row_ptr[j + 1])
+    kk = lo + int(np.nonzero(inst.col[lo:hi] == i)[0][0])
+    J[kk] = J[k]
+    return dataclasses.replace(inst, J=J)
+
+
+def test_fm_float_exact_and_fp64_instances_in_one_batch():
+    a = W.random_graph(300, 4.0, 91, dtype="f32", n_hyper=15, hyper_order=(3,))
+    b = _wide_spread(W.random_graph(260, 4.0, 92, dtype="f32", n_hyper=12, hyper_order=(3, 4)))
+    _compare([a, b], 12, 2, False)
