@@ -752,6 +752,41 @@ ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
   row.push_back((uint32_t)nnz_off);
   inc_ptr.push_back((uint32_t)inc_edge.size());
   hptr.push_back((uint32_t)mem_off);
+  std::vector<int16_t> runit;
+  if (fl) {
+    // per-spin refresh unit: the same test as the kernels' xr_exact, once here
+    runit.assign(spin_off, 0);
+    for (int64_t gi = 0; gi < spin_off; ++gi) {
+      int emin = 256, emax = -1, k = 0;
+      auto see = [&](float v) {
+        uint32_t bits;
+        std::memcpy(&bits, &v, 4);
+        bits &= 0x7fffffffu;
+        ++k;
+        if (bits) {
+          const int e = (int)(bits >> 23);
+          emin = std::min(emin, e);
+          emax = std::max(emax, e);
+        }
+      };
+      see(hf.empty() ? 0.0f : hf[gi]);
+      for (uint32_t kk = row[gi]; kk < row[gi + 1]; ++kk) see(Jf[kk]);
+      for (uint32_t q = inc_ptr[gi]; q < inc_ptr[gi + 1]; ++q) see(hJf[inc_edge[q]]);
+      int lg = 0;
+      while (lg < 31 && (1u << lg) <= (uint32_t)k) ++lg;  // 2^lg > k
+      const bool ex = emax < 0 || (emin >= 24 && emax <= 200 && (emax - emin) + 24 + lg <= 53);
+      runit[gi] = (int16_t)(emax < 0 ? 24 : (ex ? emin : -1));
+    }
+    // InstDesc::fx53 = 2: fields exact in FP64 spin by spin (every spin has a
+    // refresh unit), though not the energy as one integer sum
+    for (int32_t b = 0; b < n_instances; ++b) {
+      InstDesc &D = inst[b];
+      if (D.fx53) continue;
+      bool all = true;
+      for (int64_t gi = D.spin_off; gi < D.spin_off + D.n && all; ++gi) all = runit[gi] >= 0;
+      if (all) D.fx53 = 2;
+    }
+  }
   h->inst = inst;
   h->h_cls = cls;
   h->total_spins = spin_off;
@@ -768,29 +803,6 @@ ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
     if (fl) {
       ok = upload((float **)&h->d_J, Jf) == cudaSuccess && upload((float **)&h->d_h, hf) == cudaSuccess &&
            upload((float **)&h->d_hJ, hJf) == cudaSuccess;
-      // per-spin refresh unit: the same test as the kernels' xr_exact, once here
-      std::vector<int16_t> runit(spin_off);
-      for (int64_t gi = 0; gi < spin_off && ok; ++gi) {
-        int emin = 256, emax = -1, k = 0;
-        auto see = [&](float v) {
-          uint32_t bits;
-          std::memcpy(&bits, &v, 4);
-          bits &= 0x7fffffffu;
-          ++k;
-          if (bits) {
-            const int e = (int)(bits >> 23);
-            emin = std::min(emin, e);
-            emax = std::max(emax, e);
-          }
-        };
-        see(hf.empty() ? 0.0f : hf[gi]);
-        for (uint32_t kk = row[gi]; kk < row[gi + 1]; ++kk) see(Jf[kk]);
-        for (uint32_t q = inc_ptr[gi]; q < inc_ptr[gi + 1]; ++q) see(hJf[inc_edge[q]]);
-        int lg = 0;
-        while (lg < 31 && (1u << lg) <= (uint32_t)k) ++lg;  // 2^lg > k
-        const bool ex = emax < 0 || (emin >= 24 && emax <= 200 && (emax - emin) + 24 + lg <= 53);
-        runit[gi] = (int16_t)(emax < 0 ? 24 : (ex ? emin : -1));
-      }
       ok = ok && upload(&h->d_runit, runit) == cudaSuccess;
     } else {
       ok = upload((int8_t **)&h->d_J, Ji) == cudaSuccess && upload((int8_t **)&h->d_h, hi) == cudaSuccess &&

@@ -38,6 +38,9 @@ namespace {
 constexpr int kFT = 256;           // threads per CTA
 constexpr int kFW = kFT / 32;
 constexpr int kFmMaxSpins = 4096;
+// arithmetic of a search (InstDesc::fx53): FP64 as defined; int64 in one unit
+// per instance; int64 fields in per-spin units with FP64 energies
+constexpr int kFp64 = 0, kFx = 1, kFxSpin = 2;
 
 struct FmArgs {
   DevGraph g;
@@ -113,6 +116,18 @@ __device__ __forceinline__ unsigned long long gain_key_fx(long long f, int8_t s)
   return (unsigned long long)g ^ 0x8000000000000000ull;
 }
 
+// v * 2^(unit - 150) as an FP64 value, built from its bits (|v| < 2^53:
+// exact, no rounding), for fields held in per-spin units
+__device__ __forceinline__ double fx_double(long long v, int unit) {
+  if (v == 0) return 0.0;
+  const unsigned long long sign = v < 0 ? 0x8000000000000000ull : 0ull;
+  const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+  const int lz = __clzll((long long)a);
+  const unsigned long long mant = (a << (lz + 1)) >> 12;  // the bits below the leading one
+  const unsigned long long ex = (unsigned long long)(63 - lz + unit - 150 + 1023);
+  return __longlong_as_double((long long)(sign | (ex << 52) | mant));
+}
+
 // E in units of u by one warp (integer sums: the order does not matter)
 __device__ __forceinline__ long long fm_energy_fx(const DevGraph &G, const InstDesc &I, bool fl, const int8_t *s,
                                                   int lane, int unit) {
@@ -159,10 +174,11 @@ __device__ __forceinline__ double fm_energy(const DevGraph &G, const InstDesc &I
 }
 
 // bytes of shared memory one warp needs for an instance of n spins:
-// fields (FP64), block maxima (key, index), lock and dirty bits, the pass's
-// moves (16-bit), spins and the best spins over the starts
+// fields (FP64 or int64), block maxima (key, index), lock and dirty bits, the
+// pass's moves (16-bit), spins, the best spins over the starts and the
+// spins' field units
 __host__ __device__ constexpr size_t fm_warp_bytes(int n) {
-  return (size_t)n * 12 + (size_t)((n + 31) / 32) * 14 + 16;
+  return (size_t)n * 13 + (size_t)((n + 31) / 32) * 14 + 16;
 }
 
 // The warp's maximum of (key, index) pairs: the largest key, among equal keys
@@ -189,6 +205,7 @@ struct FmState {
   int16_t *moves;           // [n] the pass's moves in order
   int16_t *bidx;            // [nb] the spin of each block maximum (lowest of equal keys)
   int8_t *s, *sb;           // [n] spins, best spins over the starts
+  uint8_t *un;              // [n] each spin's field unit (per-spin integer form)
   int n, nb;
 };
 __device__ __forceinline__ FmState fm_state(uint8_t *base, int n) {
@@ -203,17 +220,20 @@ __device__ __forceinline__ FmState fm_state(uint8_t *base, int n) {
   S.bidx = S.moves + n;
   S.s = reinterpret_cast<int8_t *>(S.bidx + S.nb);
   S.sb = S.s + n;
+  S.un = reinterpret_cast<uint8_t *>(S.sb + n);
   return S;
 }
 
 // block j's maximum over its unlocked spins, one lane per spin
-template <bool FX>
+template <int M>
 __device__ __forceinline__ void block_max(const FmState &S, int j, int lane) {
   const int i = (j << 5) + lane;
   unsigned long long key = 0ull;
   if (i < S.n && !((S.lock[j] >> lane) & 1u)) {
-    if constexpr (FX)
+    if constexpr (M == kFx)
       key = gain_key_fx(reinterpret_cast<const long long *>(S.f)[i], S.s[i]);
+    else if constexpr (M == kFxSpin)
+      key = gain_key(fx_double(reinterpret_cast<const long long *>(S.f)[i], S.un[i]), S.s[i]);
     else
       key = gain_key(S.f[i], S.s[i]);
   }
@@ -227,11 +247,14 @@ __device__ __forceinline__ void block_max(const FmState &S, int j, int lane) {
 // One warp per search (instance, replica, a range of starts): no CTA barriers
 // on the per-move path.  The move's spin is the maximum over the cached block
 // maxima; a move recomputes only the blocks it touched (the moved spin's and
-// those of the spins whose fields changed).  FX: exact integer arithmetic in
-// units of u (instances with InstDesc::fx53 set), else FP64.
-template <bool FX>
+// those of the spins whose fields changed).  M: the arithmetic (kFp64, kFx,
+// kFxSpin); every form computes the same values as FP64 in the definition's
+// order, so all give identical moves.
+template <int M>
 __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
-  using T = std::conditional_t<FX, long long, double>;
+  constexpr bool INT = M != kFp64;
+  using T = std::conditional_t<INT, long long, double>;       // fields
+  using TE = std::conditional_t<M == kFx, long long, double>;  // running energy
   extern __shared__ __align__(16) uint8_t fm_smem[];
   const DevGraph &G = A.g;
   const bool fl = A.is_float != 0;
@@ -251,16 +274,23 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
     const InstDesc I = G.inst[b];
     const int n = I.n;
     const int64_t so = I.spin_off;
-    const int unit = I.ebase;  // FX with FP32 couplings: u = 2^(unit - 150)
-    const double scale = (FX && fl) ? __longlong_as_double((long long)(unit - 150 + 1023) << 52) : 1.0;
+    const int unit = I.ebase;  // kFx with FP32 couplings: u = 2^(unit - 150)
+    const double scale = (M == kFx && fl) ? __longlong_as_double((long long)(unit - 150 + 1023) << 52) : 1.0;
     const FmState S = fm_state(base, n);
     T *f = reinterpret_cast<T *>(S.f);
     int8_t *s = S.s;
+    if constexpr (M == kFxSpin)
+      for (int i = lane; i < n; i += 32) S.un[i] = (uint8_t)__ldg(G.runit + so + i);
+    // spin i's unit in the integer forms
+    auto unit_of = [&](int i) -> int {
+      if constexpr (M == kFxSpin) return S.un[i];
+      return unit;
+    };
     const uint64_t seed = A.seeds[b];
-    // E of the current spins: FP64 (the same value in every lane), and in FX
-    // also the integer it is exactly
+    // E of the current spins in FP64 (the same value in every lane); kFx also
+    // returns the integer it is exactly
     auto energy = [&](long long &Ei) -> double {
-      if constexpr (FX) {
+      if constexpr (M == kFx) {
         Ei = fm_energy_fx(G, I, fl, s, lane, unit);
         return (double)Ei * scale;
       } else {
@@ -284,15 +314,16 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
         // fields: h, the CSR row in order, then the hyper-edges in ascending order
         for (int i = lane; i < n; i += 32) {
           const int64_t gi = so + i;
-          if constexpr (FX) {
-            long long acc = fx_of(G.h, fl, gi, unit);
+          if constexpr (INT) {
+            const int ui = unit_of(i);
+            long long acc = fx_of(G.h, fl, gi, ui);
             for (uint32_t kk = __ldg(G.row + gi), ke = __ldg(G.row + gi + 1); kk < ke; ++kk) {
-              const long long t = fx_of(G.J, fl, kk, unit);
+              const long long t = fx_of(G.J, fl, kk, ui);
               acc += s[__ldg(G.col + kk)] > 0 ? t : -t;
             }
             for (uint32_t u = __ldg(G.inc_ptr + gi), ue = __ldg(G.inc_ptr + gi + 1); u < ue; ++u) {
               const int64_t e = __ldg(G.inc_edge + u);
-              const long long t = fx_of(G.hJ, fl, e, unit);
+              const long long t = fx_of(G.hJ, fl, e, ui);
               acc += hyper_sign(G, e, s, i) > 0 ? t : -t;
             }
             f[i] = acc;
@@ -310,10 +341,10 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
         for (int j = lane; j < S.nb; j += 32) S.lock[j] = 0u;
         if (lane < 4) S.dirty[lane] = 0u;
         __syncwarp();
-        for (int j = 0; j < S.nb; ++j) block_max<FX>(S, j, lane);
+        for (int j = 0; j < S.nb; ++j) block_max<M>(S, j, lane);
         __syncwarp();
-        T Ecur, Ebest;  // lane 0's copies are used
-        if constexpr (FX)
+        TE Ecur, Ebest;  // lane 0's copies are used
+        if constexpr (M == kFx)
           Ecur = EstarI;
         else
           Ecur = Estar;
@@ -333,9 +364,11 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
           }
           const int i = warp_argmax(bk, bi).idx;
           if (lane == 0) {
-            T gain;
-            if constexpr (FX)
+            TE gain;
+            if constexpr (M == kFx)
               gain = s[i] > 0 ? -2 * f[i] : 2 * f[i];
+            else if constexpr (M == kFxSpin)
+              gain = -2.0 * (double)s[i] * fx_double(f[i], S.un[i]);
             else
               gain = -2.0 * (double)s[i] * f[i];
             Ecur -= gain;  // apply the move
@@ -350,13 +383,14 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
           }
           __syncwarp();
           // neighbours' fields: the CSR row (distinct columns, one lane each),
-          // then the hyper-edges in order (one lane: shared members possible)
+          // then the hyper-edges in order, each by its members in parallel
+          // (distinct within an edge)
           const int8_t snew = s[i];
           const int64_t gi = so + i;
           for (uint32_t kk = __ldg(G.row + gi) + lane, ke = __ldg(G.row + gi + 1); kk < ke; kk += 32) {
             const int c = __ldg(G.col + kk);
-            if constexpr (FX) {
-              const long long t2 = 2 * fx_of(G.J, fl, kk, unit);
+            if constexpr (INT) {
+              const long long t2 = 2 * fx_of(G.J, fl, kk, unit_of(c));
               f[c] += snew > 0 ? t2 : -t2;
             } else {
               f[c] += coupling(G, fl, kk) * (2.0 * (double)snew);
@@ -364,31 +398,26 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
             atomicOr(S.dirty + (c >> 10), 1u << ((c >> 5) & 31));
           }
           const uint32_t u0 = __ldg(G.inc_ptr + gi), u1 = __ldg(G.inc_ptr + gi + 1);
-          if (u0 < u1) {
+          for (uint32_t u = u0; u < u1; ++u) {
             __syncwarp();
-            if (lane == 0)
-              for (uint32_t u = u0; u < u1; ++u) {
-                const int64_t e = __ldg(G.inc_edge + u);
-                if constexpr (FX) {
-                  const long long w2 = 2 * fx_of(G.hJ, fl, e, unit);
-                  for (uint32_t q = __ldg(G.hptr + e), qe = __ldg(G.hptr + e + 1); q < qe; ++q) {
-                    const int m = __ldg(G.hmem + q);
-                    if (m != i) {
-                      f[m] += hyper_sign(G, e, s, m) > 0 ? w2 : -w2;
-                      S.dirty[m >> 10] |= 1u << ((m >> 5) & 31);
-                    }
-                  }
-                } else {
-                  const double w2 = 2.0 * coupling_e(G, fl, e);
-                  for (uint32_t q = __ldg(G.hptr + e), qe = __ldg(G.hptr + e + 1); q < qe; ++q) {
-                    const int m = __ldg(G.hmem + q);
-                    if (m != i) {
-                      f[m] += w2 * hyper_prod(G, e, s, m);
-                      S.dirty[m >> 10] |= 1u << ((m >> 5) & 31);
-                    }
-                  }
-                }
+            const int64_t e = __ldg(G.inc_edge + u);
+            const uint32_t q0 = __ldg(G.hptr + e), q1 = __ldg(G.hptr + e + 1);
+            int neg = 0;  // parity of the members' negative spins
+            for (uint32_t q = q0 + lane; q < q1; q += 32) neg ^= s[__ldg(G.hmem + q)] < 0;
+            const int par = __popc(__ballot_sync(0xffffffffu, neg)) & 1;
+            for (uint32_t q = q0 + lane; q < q1; q += 32) {
+              const int m = __ldg(G.hmem + q);
+              if (m == i) continue;
+              const bool minus = par ^ (s[m] < 0);  // the other members' product is -1
+              if constexpr (INT) {
+                const long long w2 = 2 * fx_of(G.hJ, fl, e, unit_of(m));
+                f[m] += minus ? -w2 : w2;
+              } else {
+                const double w2 = 2.0 * coupling_e(G, fl, e);
+                f[m] += w2 * (minus ? -1.0 : 1.0);
               }
+              atomicOr(S.dirty + (m >> 10), 1u << ((m >> 5) & 31));
+            }
           }
           __syncwarp();
           for (int dw = 0; dw < (S.nb + 31) / 32; ++dw) {
@@ -396,7 +425,7 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
             while (d) {
               const int jb = __ffs(d) - 1;
               d &= d - 1u;
-              block_max<FX>(S, (dw << 5) + jb, lane);
+              block_max<M>(S, (dw << 5) + jb, lane);
             }
           }
           __syncwarp();
@@ -491,6 +520,10 @@ struct FmBufs {
   size_t queues_bytes = 0;
   void *scratch = nullptr;
   size_t scratch_bytes = 0;
+  // side streams for overlapping the groups' launches, with fork/join events
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
 };
 std::map<const ising_handle *, FmBufs> &fm_bufs() {
   static std::map<const ising_handle *, FmBufs> m;
@@ -512,16 +545,40 @@ cudaError_t grow(P *&p, size_t &have, size_t need) {
 }
 
 constexpr size_t kSplitScratchMax = size_t(1) << 30;  // bytes of per-start results at most
+constexpr int kSideStreams = 4;
+
+cudaError_t ensure_side(FmBufs &B) {
+  if (!B.side.empty()) return cudaSuccess;
+  cudaError_t e = cudaEventCreateWithFlags(&B.fork, cudaEventDisableTiming);
+  for (int j = 0; j < kSideStreams && e == cudaSuccess; ++j) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) break;
+    B.side.push_back(st);
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) break;
+    B.join.push_back(ev);
+  }
+  if (e != cudaSuccess || (int)B.join.size() != kSideStreams) {
+    for (cudaStream_t st : B.side) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : B.join) cudaEventDestroy(ev);
+    if (B.fork) cudaEventDestroy(B.fork);
+    B.side.clear();
+    B.join.clear();
+    B.fork = nullptr;
+    return e != cudaSuccess ? e : cudaErrorUnknown;
+  }
+  return cudaSuccess;
+}
 
 // One launch group: instances of one arithmetic (FX or FP64) whose size falls
 // in (lo, hi], so that each warp's shared memory is sized for hi.
 struct FmPart {
-  bool fx;
+  int mode;  // kFp64 / kFx / kFxSpin
   int nmax;
   int64_t first, count;  // range of the item list
 };
 
-template <bool FX>
+template <int M>
 cudaError_t fm_shape(const ising_handle *h, int nmax, int &warps, size_t &smem, int &per_sm) {
   const size_t per_warp = (fm_warp_bytes(nmax) + 15) & ~(size_t)15;
   int smem_optin = 0;
@@ -529,11 +586,11 @@ cudaError_t fm_shape(const ising_handle *h, int nmax, int &warps, size_t &smem, 
   warps = (int)std::max<size_t>(1, std::min<size_t>(kFW, (size_t)smem_optin / per_warp));
   smem = per_warp * warps;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(fm_kernel<FX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+  if ((e = cudaFuncSetAttribute(fm_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
       cudaSuccess)
     return e;
   per_sm = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fm_kernel<FX>, warps * 32, smem)) != cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fm_kernel<M>, warps * 32, smem)) != cudaSuccess)
     return e;
   per_sm = std::max(per_sm, 1);
   return cudaSuccess;
@@ -552,8 +609,9 @@ cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_
   if (n_items > 0x7fffffff) return cudaErrorInvalidValue;
   FmBufs &B = fm_bufs()[h];
   cudaError_t e;
-  // groups: exact-integer instances first, then FP64; within each, size
-  // classes (0, 256], (256, 512], ... (2048, 4096], largest first
+  // groups: one-unit integer instances, per-spin-unit ones, then FP64;
+  // within each, size classes (0, 256], (256, 512], ... (2048, 4096],
+  // largest first
   auto cls = [](int n) {
     int c = 0;
     while (c < 4 && n > (256 << c)) ++c;
@@ -563,7 +621,8 @@ cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_
   for (int32_t b = 0; b < h->n_inst; ++b) ord[b] = b;
   std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) {
     const InstDesc &x = h->inst[a], &y = h->inst[c];
-    if (x.fx53 != y.fx53) return x.fx53 > y.fx53;
+    auto rank = [](int m) { return m == kFx ? 0 : (m == kFxSpin ? 1 : 2); };
+    if (x.fx53 != y.fx53) return rank(x.fx53) < rank(y.fx53);
     return x.n > y.n;
   });
   std::vector<int2> items;
@@ -571,9 +630,9 @@ cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_
   items.reserve((size_t)n_items);
   for (int32_t b : ord) {
     const InstDesc &D = h->inst[b];
-    const bool fx = D.fx53 != 0;
-    if (parts.empty() || parts.back().fx != fx || cls(parts.back().nmax) != cls(D.n))
-      parts.push_back({fx, D.n, (int64_t)items.size(), 0});
+    const int mode = D.fx53;
+    if (parts.empty() || parts.back().mode != mode || cls(parts.back().nmax) != cls(D.n))
+      parts.push_back({mode, D.n, (int64_t)items.size(), 0});
     for (int32_t r = 0; r < R; ++r) items.push_back(make_int2(b, r));
     parts.back().count += R;
   }
@@ -588,7 +647,7 @@ cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_
   // the searches alone would leave the GPU underfilled.
   int warps0 = 0, per_sm0 = 0;
   size_t smem0 = 0;
-  if ((e = fm_shape<true>(h, h->nmax, warps0, smem0, per_sm0)) != cudaSuccess) return e;
+  if ((e = fm_shape<kFx>(h, h->nmax, warps0, smem0, per_sm0)) != cudaSuccess) return e;
   const int64_t resident = (int64_t)h->sm_count * per_sm0 * warps0;
   const size_t sp_bytes = ((size_t)R * restarts * h->total_spins + 15) & ~(size_t)15;
   const size_t e_bytes = (size_t)n_items * restarts * sizeof(double);
@@ -608,13 +667,33 @@ cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_
     P_k = reinterpret_cast<int32_t *>(E_k + (size_t)n_items * restarts);
   }
 
-  for (size_t q = 0; q < parts.size(); ++q) {
+  // Groups launch largest size class first; with several groups they go to
+  // side streams (forked from and joined back into s), so that a group's
+  // CTAs take the SMs as the previous group's retire instead of waiting for
+  // its last search.
+  std::vector<size_t> order(parts.size());
+  for (size_t q = 0; q < parts.size(); ++q) order[q] = q;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](size_t a, size_t c) { return cls(parts[a].nmax) > cls(parts[c].nmax); });
+  const bool fan = parts.size() > 1;
+  if (fan) {
+    if ((e = ensure_side(B)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(B.fork, s)) != cudaSuccess) return e;
+    for (cudaStream_t st : B.side)
+      if ((e = cudaStreamWaitEvent(st, B.fork, 0)) != cudaSuccess) return e;
+  }
+  cudaError_t le = cudaSuccess;
+  for (size_t o = 0; o < order.size() && le == cudaSuccess; ++o) {
+    const size_t q = order[o];
     const FmPart &P = parts[q];
+    cudaStream_t ls = fan ? B.side[o % B.side.size()] : s;
     const int nmax = P.nmax;  // the group's largest instance
     int warps = 0, per_sm = 0;
     size_t smem = 0;
-    e = P.fx ? fm_shape<true>(h, nmax, warps, smem, per_sm) : fm_shape<false>(h, nmax, warps, smem, per_sm);
-    if (e != cudaSuccess) return e;
+    le = P.mode == kFx ? fm_shape<kFx>(h, nmax, warps, smem, per_sm)
+                       : (P.mode == kFxSpin ? fm_shape<kFxSpin>(h, nmax, warps, smem, per_sm)
+                                            : fm_shape<kFp64>(h, nmax, warps, smem, per_sm));
+    if (le != cudaSuccess) break;
     FmArgs A;
     A.g = h->graph();
     A.n_work = (int32_t)(split ? P.count * restarts : P.count);
@@ -632,13 +711,22 @@ cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_
     A.stats = h->d_stats;
     const int64_t ctas_needed = ((int64_t)A.n_work + warps - 1) / warps;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->sm_count * per_sm, ctas_needed));
-    if (P.fx)
-      fm_kernel<true><<<grid, warps * 32, smem, s>>>(A, nmax);
+    if (P.mode == kFx)
+      fm_kernel<kFx><<<grid, warps * 32, smem, ls>>>(A, nmax);
+    else if (P.mode == kFxSpin)
+      fm_kernel<kFxSpin><<<grid, warps * 32, smem, ls>>>(A, nmax);
     else
-      fm_kernel<false><<<grid, warps * 32, smem, s>>>(A, nmax);
+      fm_kernel<kFp64><<<grid, warps * 32, smem, ls>>>(A, nmax);
     h->launches += 1;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    le = cudaGetLastError();
   }
+  if (fan)  // join every side stream back into s, also after a failed launch
+    for (size_t j = 0; j < B.side.size(); ++j) {
+      cudaError_t je = cudaEventRecord(B.join[j], B.side[j]);
+      if (je == cudaSuccess) je = cudaStreamWaitEvent(s, B.join[j], 0);
+      if (le == cudaSuccess) le = je;
+    }
+  if (le != cudaSuccess) return le;
   if (!split) return cudaSuccess;
   const int64_t threads = n_items * 32;
   fm_best_start_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(h->d_inst, h->n_inst, R, restarts, sp_k,
@@ -654,6 +742,9 @@ void fm_free(ising_handle *h) {
   cudaFree(it->second.items);
   cudaFree(it->second.queues);
   cudaFree(it->second.scratch);
+  for (cudaStream_t st : it->second.side) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : it->second.join) cudaEventDestroy(ev);
+  if (it->second.fork) cudaEventDestroy(it->second.fork);
   m.erase(it);
 }
 

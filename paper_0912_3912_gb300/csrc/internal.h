@@ -33,9 +33,12 @@ struct InstDesc {
   // when the energy can be summed exactly in 64-bit fixed point with that
   // unit (see xe_term), else -1 (FP64 sums instead)
   int32_t ebase;
-  // 1 when every field, gain and energy value of the instance is an integer
-  // multiple of the unit (2^(ebase - 150) for FP32 couplings, 1 for int8)
-  // below 2^53 in magnitude, so FP64 arithmetic on them is exact
+  // Exactness of FP64 arithmetic on the instance's fields, gains and energies:
+  // 1 = every such value is an integer multiple of one unit (2^(ebase - 150)
+  //     for FP32 couplings, 1 for int8) below 2^53 in magnitude;
+  // 2 = (FP32) each spin's field values are multiples of that spin's refresh
+  //     unit (DevGraph::runit) below 2^53 units; energies are not covered;
+  // 0 = neither.
   int32_t fx53;
 };
 

@@ -6,7 +6,9 @@ counts equal, energies within 1e-9 relative (the oracle sums energies with
 compensation, the kernel in plain FP64; the improvement margin of a pass
 absorbs that difference).  Instances whose fields and energies FP64 computes
 exactly run in 64-bit integers on the GPU; one test mixes such an instance
-with one whose couplings span too many binary orders for that (FP64 path)."""
+with one whose couplings span too many binary orders for that (FP64 path);
+another has two components at scales 2^30 apart, so its fields are exact
+spin by spin but its energy is not one integer sum (per-spin integer path)."""
 import dataclasses
 
 import numpy as np
@@ -159,3 +161,26 @@ def test_fm_float_exact_and_fp64_instances_in_one_batch():
     a = W.random_graph(300, 4.0, 91, dtype="f32", n_hyper=15, hyper_order=(3,))
     b = _wide_spread(W.random_graph(260, 4.0, 92, dtype="f32", n_hyper=12, hyper_order=(3, 4)))
     _compare([a, b], 12, 2, False)
+
+
+def _two_scales(a, b, scale=2.0 ** -30):
+    """Block-diagonal union of two FP32 instances, the second scaled by
+    `scale`: each spin's terms stay within a narrow range of binary orders,
+    the instance's as a whole do not."""
+    n = a.n + b.n
+    row_ptr = np.concatenate([a.row_ptr, a.row_ptr[-1] + b.row_ptr[1:]]).astype(np.int64)
+    col = np.concatenate([a.col, b.col + a.n]).astype(np.int32)
+    J = np.concatenate([a.J, (b.J * scale).astype(np.float32)])
+    h = np.concatenate([a.h, (b.h * scale).astype(np.float32)])
+    hp = np.concatenate([a.hyper_ptr, a.hyper_ptr[-1] + b.hyper_ptr[1:]]).astype(np.int64)
+    hm = np.concatenate([a.hyper_members, b.hyper_members + a.n]).astype(np.int32)
+    hJ = np.concatenate([a.hyper_J, (b.hyper_J * scale).astype(np.float32)])
+    return W.Instance(n=n, row_ptr=row_ptr, col=col, J=J, h=h, hyper_ptr=hp, hyper_members=hm, hyper_J=hJ,
+                      dtype="f32")
+
+
+def test_fm_float_per_spin_exact_instance():
+    a = W.random_graph(180, 4.0, 93, dtype="f32", n_hyper=10, hyper_order=(3,))
+    b = W.random_graph(150, 4.0, 94, dtype="f32", n_hyper=8, hyper_order=(3, 4))
+    c = W.random_graph(120, 4.0, 95, dtype="f32", n_hyper=6, hyper_order=(3,))
+    _compare([_two_scales(a, b), c, _wide_spread(b)], 12, 2, False)
