@@ -173,12 +173,12 @@ __device__ __forceinline__ double fm_energy(const DevGraph &G, const InstDesc &I
   return warp_sum(acc);
 }
 
-// bytes of shared memory one warp needs for an instance of n spins:
-// fields (FP64 or int64), block maxima (key, index), lock and dirty bits, the
-// pass's moves (16-bit), spins, the best spins over the starts and the
-// spins' field units
-__host__ __device__ constexpr size_t fm_warp_bytes(int n) {
-  return (size_t)n * 13 + (size_t)((n + 31) / 32) * 14 + 16;
+// bytes of shared memory one warp needs for an instance of n spins in
+// arithmetic M: fields (FP64 or int64), block maxima (key, index), lock bits
+// and their snapshot at the best prefix, dirty bits, spins and, in per-spin
+// units, the spins' field units
+__host__ __device__ constexpr size_t fm_warp_bytes(int n, int M) {
+  return (size_t)n * (M == 2 ? 10 : 9) + (size_t)((n + 31) / 32) * 18 + 16;
 }
 
 // The warp's maximum of (key, index) pairs: the largest key, among equal keys
@@ -201,11 +201,11 @@ struct FmState {
   double *f;                // [n] fields
   unsigned long long *bkey; // [nb] largest unlocked gain key of each 32-spin block (0: none)
   uint32_t *lock;           // [nb] spins moved in this pass
+  uint32_t *best;           // [nb] spins moved up to the best prefix so far
   uint32_t *dirty;          // [4] blocks whose maximum must be recomputed
-  int16_t *moves;           // [n] the pass's moves in order
   int16_t *bidx;            // [nb] the spin of each block maximum (lowest of equal keys)
-  int8_t *s, *sb;           // [n] spins, best spins over the starts
-  uint8_t *un;              // [n] each spin's field unit (per-spin integer form)
+  int8_t *s;                // [n] spins
+  uint8_t *un;              // [n] each spin's field unit (per-spin integer form only)
   int n, nb;
 };
 __device__ __forceinline__ FmState fm_state(uint8_t *base, int n) {
@@ -215,12 +215,11 @@ __device__ __forceinline__ FmState fm_state(uint8_t *base, int n) {
   S.f = reinterpret_cast<double *>(base);
   S.bkey = reinterpret_cast<unsigned long long *>(S.f + n);
   S.lock = reinterpret_cast<uint32_t *>(S.bkey + S.nb);
-  S.dirty = S.lock + S.nb;
-  S.moves = reinterpret_cast<int16_t *>(S.dirty + 4);
-  S.bidx = S.moves + n;
+  S.best = S.lock + S.nb;
+  S.dirty = S.best + S.nb;
+  S.bidx = reinterpret_cast<int16_t *>(S.dirty + 4);
   S.s = reinterpret_cast<int8_t *>(S.bidx + S.nb);
-  S.sb = S.s + n;
-  S.un = reinterpret_cast<uint8_t *>(S.sb + n);
+  S.un = reinterpret_cast<uint8_t *>(S.s + n);
   return S;
 }
 
@@ -259,7 +258,7 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
   const DevGraph &G = A.g;
   const bool fl = A.is_float != 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint8_t *base = fm_smem + (size_t)warp * ((fm_warp_bytes(nmax) + 15) & ~(size_t)15);
+  uint8_t *base = fm_smem + (size_t)warp * ((fm_warp_bytes(nmax, M) + 15) & ~(size_t)15);
   unsigned long long c_moves = 0, c_passes = 0, c_starts = 0;
   for (;;) {
     int w = 0;
@@ -300,6 +299,7 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
     };
     double E_all = DBL_MAX;
     int total_passes = 0;
+    int8_t *out = A.spins + (int64_t)A.R_out * so + (int64_t)slot * n;
     for (int k = k0; k < k1; ++k) {
       for (int i = lane; i < n; i += 32) {
         const uint4 x = start_bits(seed, (uint32_t)(i >> 7), (uint32_t)r, (uint32_t)k, (uint32_t)b);
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
             f[i] = acc;
           }
         }
-        for (int j = lane; j < S.nb; j += 32) S.lock[j] = 0u;
+        for (int j = lane; j < S.nb; j += 32) S.lock[j] = S.best[j] = 0u;
         if (lane < 4) S.dirty[lane] = 0u;
         __syncwarp();
         for (int j = 0; j < S.nb; ++j) block_max<M>(S, j, lane);
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
         else
           Ecur = Estar;
         Ebest = Ecur;
-        int best_prefix = 0;
+        bool any_best = false;  // the pass found a prefix below its start
         for (int step = 0; step < n; ++step) {
           // the largest gain among unlocked spins, ties to the lowest index:
           // blocks in ascending order per lane, then across lanes
@@ -363,6 +363,7 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
             }
           }
           const int i = warp_argmax(bk, bi).idx;
+          bool new_best = false;
           if (lane == 0) {
             TE gain;
             if constexpr (M == kFx)
@@ -374,9 +375,8 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
             Ecur -= gain;  // apply the move
             if (Ecur < Ebest) {
               Ebest = Ecur;
-              best_prefix = step + 1;
+              new_best = true;
             }
-            S.moves[step] = (int16_t)i;
             S.lock[i >> 5] |= 1u << (i & 31);
             S.dirty[i >> 10] |= 1u << ((i >> 5) & 31);
             s[i] = (int8_t)-s[i];
@@ -419,6 +419,13 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
               atomicOr(S.dirty + (m >> 10), 1u << ((m >> 5) & 31));
             }
           }
+          // the earliest strictly lowest prefix so far ends here: remember
+          // which spins it moved (every spin moves once per pass, so the
+          // lock bits are that set)
+          if (__shfl_sync(0xffffffffu, (int)new_best, 0)) {
+            any_best = true;
+            for (int j = lane; j < S.nb; j += 32) S.best[j] = S.lock[j];
+          }
           __syncwarp();
           for (int dw = 0; dw < (S.nb + 31) / 32; ++dw) {
             unsigned d = S.dirty[dw];
@@ -432,9 +439,11 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
           if (lane < 4) S.dirty[lane] = 0u;
           __syncwarp();
         }
-        // roll back to the best prefix (each spin moved once: distinct entries)
-        const int bp = __shfl_sync(0xffffffffu, best_prefix, 0);
-        for (int st = bp + lane; st < n; st += 32) s[S.moves[st]] = (int8_t)-s[S.moves[st]];
+        // roll back to the best prefix: every spin moved once, so the spins
+        // outside that prefix's set are flipped back
+        __syncwarp();
+        for (int i = lane; i < n; i += 32)
+          if (!((S.best[i >> 5] >> (i & 31)) & 1u)) s[i] = (int8_t)-s[i];
         __syncwarp();
         long long EnewI;
         const double Enew = energy(EnewI);
@@ -447,8 +456,9 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
         }
         if (Enew < Estar - margin) {
           Estar = Enew;  // pass cap reached after an improving pass: keep it
-        } else {
-          for (int st = lane; st < bp; st += 32) s[S.moves[st]] = (int8_t)-s[S.moves[st]];
+        } else if (any_best) {  // back to the pass's start
+          for (int i = lane; i < n; i += 32)
+            if ((S.best[i >> 5] >> (i & 31)) & 1u) s[i] = (int8_t)-s[i];
           __syncwarp();
         }
         break;
@@ -459,12 +469,10 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
       // keep the best start (strictly lower energy; ties keep the earlier)
       if (Estar < E_all) {
         E_all = Estar;
-        for (int i = lane; i < n; i += 32) S.sb[i] = s[i];
+        for (int i = lane; i < n; i += 32) out[i] = s[i];
       }
       __syncwarp();
     }
-    int8_t *out = A.spins + (int64_t)A.R_out * so + (int64_t)slot * n;
-    for (int i = lane; i < n; i += 32) out[i] = S.sb[i];
     if (lane == 0) {
       A.energy[(int64_t)b * A.R_out + slot] = E_all;
       if (A.passes) A.passes[(int64_t)b * A.R_out + slot] = total_passes;
@@ -578,21 +586,31 @@ struct FmPart {
   int64_t first, count;  // range of the item list
 };
 
+// Warps per CTA (one search each) and CTAs per SM for instances of up to
+// nmax spins: the most searches per SM that shared memory and registers allow,
+// the larger CTA among equals.
 template <int M>
 cudaError_t fm_shape(const ising_handle *h, int nmax, int &warps, size_t &smem, int &per_sm) {
-  const size_t per_warp = (fm_warp_bytes(nmax) + 15) & ~(size_t)15;
+  const size_t per_warp = (fm_warp_bytes(nmax, M) + 15) & ~(size_t)15;
   int smem_optin = 0;
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-  warps = (int)std::max<size_t>(1, std::min<size_t>(kFW, (size_t)smem_optin / per_warp));
-  smem = per_warp * warps;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(fm_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-      cudaSuccess)
+  const int wmax = (int)std::max<size_t>(1, std::min<size_t>(kFW, (size_t)smem_optin / per_warp));
+  if ((e = cudaFuncSetAttribute(fm_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(per_warp * wmax))) != cudaSuccess)
     return e;
-  per_sm = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fm_kernel<M>, warps * 32, smem)) != cudaSuccess)
-    return e;
-  per_sm = std::max(per_sm, 1);
+  int best = -1;
+  for (int w = wmax; w >= 1; --w) {
+    int c = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, fm_kernel<M>, w * 32, per_warp * w)) != cudaSuccess)
+      return e;
+    if (c * w > best) {
+      best = c * w;
+      warps = w;
+      per_sm = std::max(c, 1);
+    }
+  }
+  smem = per_warp * warps;
   return cudaSuccess;
 }
 
