@@ -468,9 +468,10 @@ def run_fm(args, insts, R, kw, desc):
             "work_per_step": {k: v for k, v in st.items() if k != "launches"},
             "e2e": {"value": e2e_value, "unit": "moves/s", "h2d_bytes_per_step": 8 * len(insts),
                     "d2h_bytes_per_step": int(h_sp.numel() + 8 * h_E.numel())},
-            "gpu_launches": st.get("launches", 1), "clocks": clk,
+            "gpu_launches": st.get("launches", 1) * args.steps, "clocks": clk,
             "roofline": None,
-            "roofline_note": "a CTA per replica takes the best gain by one reduction per move: latency-bound; "
+            "roofline_note": "a warp per search, one dependent chain per move (block-maximum reductions, "
+                             "neighbour field updates): latency-bound, neither HBM nor an ALU pipe applies; "
                              "kernel ms per step: " + json.dumps({k: v[0] / args.steps for k, v in ktimes.items()}),
             "cpu_baseline": cpu}
     print(json.dumps(line))

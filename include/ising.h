@@ -242,8 +242,14 @@ ising_status ising_energy_noalloc(int32_t n, const int64_t *row_ptr_dev, const i
  * pass is cut back to its earliest strictly lowest-energy prefix, and passes
  * repeat while one lowers the energy strictly (float couplings: by more than
  * 1e-9 (1 + |E|)); max_passes > 0 caps the passes per start (0: no cap).  Gains
- * and energies in FP64 (exact for integer couplings).  Per replica the result
- * is the lowest-energy start (ties keep the earlier).
+ * and energies are the FP64 values of that definition (fields summed as h,
+ * then the CSR row in stored order, then the hyper-edges ascending); where FP64
+ * is exact on an instance the kernels compute them in integers, with the same
+ * results.  Per replica the result is the lowest-energy start (ties keep the
+ * earlier).  The work is ordered on `stream` (internal streams are forked from
+ * it and joined back before the call's last launch).  The handle keeps its
+ * scratch (item lists; with few replicas, every start's result, at most 1 GiB)
+ * until ising_destroy.
  * spins_dev, energy_dev: as for ising_local_search; passes_dev: device int32
  * [instance][replica] passes summed over the starts, or NULL.  stats (nullable;
  * the call then waits): descents = starts, sweeps = passes, flips and
