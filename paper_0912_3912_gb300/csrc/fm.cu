@@ -41,10 +41,12 @@ constexpr int kFmMaxSpins = 4096;
 // arithmetic of a search (InstDesc::fx53): FP64 as defined; int64 in one unit
 // per instance; int64 fields in per-spin units with FP64 energies
 constexpr int kFp64 = 0, kFx = 1, kFxSpin = 2;
+// a move that changes more fields than this recomputes every block maximum
+constexpr int kTouched = 64;
 
 struct FmArgs {
   DevGraph g;
-  int32_t n_work, R_out, restarts, max_passes, is_float;
+  int32_t n_work, R_out, restarts, max_passes;
   int32_t split;              // 1: one start per work unit (work = item * restarts + start)
   const int2 *items;          // (instance, replica), largest instances first
   const uint64_t *seeds;      // [instances]
@@ -178,7 +180,7 @@ __device__ __forceinline__ double fm_energy(const DevGraph &G, const InstDesc &I
 // and their snapshot at the best prefix, dirty bits, spins and, in per-spin
 // units, the spins' field units
 __host__ __device__ constexpr size_t fm_warp_bytes(int n, int M) {
-  return (size_t)n * (M == 2 ? 10 : 9) + (size_t)((n + 31) / 32) * 18 + 16;
+  return (size_t)n * (M == 2 ? 10 : 9) + (size_t)((n + 31) / 32) * 18 + 16 + 2 * 64;
 }
 
 // The warp's maximum of (key, index) pairs: the largest key, among equal keys
@@ -204,6 +206,7 @@ struct FmState {
   uint32_t *best;           // [nb] spins moved up to the best prefix so far
   uint32_t *dirty;          // [4] blocks whose maximum must be recomputed
   int16_t *bidx;            // [nb] the spin of each block maximum (lowest of equal keys)
+  int16_t *touched;         // [kTouched] spins whose fields the current move changed (-1: none)
   int8_t *s;                // [n] spins
   uint8_t *un;              // [n] each spin's field unit (per-spin integer form only)
   int n, nb;
@@ -218,9 +221,21 @@ __device__ __forceinline__ FmState fm_state(uint8_t *base, int n) {
   S.best = S.lock + S.nb;
   S.dirty = S.best + S.nb;
   S.bidx = reinterpret_cast<int16_t *>(S.dirty + 4);
-  S.s = reinterpret_cast<int8_t *>(S.bidx + S.nb);
+  S.touched = S.bidx + S.nb;
+  S.s = reinterpret_cast<int8_t *>(S.touched + kTouched);
   S.un = reinterpret_cast<uint8_t *>(S.s + n);
   return S;
+}
+
+// gain key of unlocked spin c in arithmetic M
+template <int M>
+__device__ __forceinline__ unsigned long long spin_key(const FmState &S, int c) {
+  if constexpr (M == kFx)
+    return gain_key_fx(reinterpret_cast<const long long *>(S.f)[c], S.s[c]);
+  else if constexpr (M == kFxSpin)
+    return gain_key(fx_double(reinterpret_cast<const long long *>(S.f)[c], S.un[c]), S.s[c]);
+  else
+    return gain_key(S.f[c], S.s[c]);
 }
 
 // block j's maximum over its unlocked spins, one lane per spin
@@ -228,14 +243,7 @@ template <int M>
 __device__ __forceinline__ void block_max(const FmState &S, int j, int lane) {
   const int i = (j << 5) + lane;
   unsigned long long key = 0ull;
-  if (i < S.n && !((S.lock[j] >> lane) & 1u)) {
-    if constexpr (M == kFx)
-      key = gain_key_fx(reinterpret_cast<const long long *>(S.f)[i], S.s[i]);
-    else if constexpr (M == kFxSpin)
-      key = gain_key(fx_double(reinterpret_cast<const long long *>(S.f)[i], S.un[i]), S.s[i]);
-    else
-      key = gain_key(S.f[i], S.s[i]);
-  }
+  if (i < S.n && !((S.lock[j] >> lane) & 1u)) key = spin_key<M>(S, i);
   const KeyIdx m = warp_argmax(key, i);
   if (lane == 0) {
     S.bkey[j] = m.key;
@@ -249,14 +257,14 @@ __device__ __forceinline__ void block_max(const FmState &S, int j, int lane) {
 // those of the spins whose fields changed).  M: the arithmetic (kFp64, kFx,
 // kFxSpin); every form computes the same values as FP64 in the definition's
 // order, so all give identical moves.
-template <int M>
+template <int M, bool FL>
 __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
   constexpr bool INT = M != kFp64;
   using T = std::conditional_t<INT, long long, double>;       // fields
   using TE = std::conditional_t<M == kFx, long long, double>;  // running energy
   extern __shared__ __align__(16) uint8_t fm_smem[];
   const DevGraph &G = A.g;
-  const bool fl = A.is_float != 0;
+  constexpr bool fl = FL;  // FP32 couplings (else int8)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint8_t *base = fm_smem + (size_t)warp * ((fm_warp_bytes(nmax, M) + 15) & ~(size_t)15);
   unsigned long long c_moves = 0, c_passes = 0, c_starts = 0;
@@ -378,16 +386,19 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
               new_best = true;
             }
             S.lock[i >> 5] |= 1u << (i & 31);
-            S.dirty[i >> 10] |= 1u << ((i >> 5) & 31);
+            S.dirty[i >> 10] |= 1u << ((i >> 5) & 31);  // its block lost its maximum
             s[i] = (int8_t)-s[i];
           }
           __syncwarp();
           // neighbours' fields: the CSR row (distinct columns, one lane each),
           // then the hyper-edges in order, each by its members in parallel
-          // (distinct within an edge)
+          // (distinct within an edge); every changed field's spin goes to
+          // the touched list (CSR entries first, then the edges' members)
           const int8_t snew = s[i];
           const int64_t gi = so + i;
-          for (uint32_t kk = __ldg(G.row + gi) + lane, ke = __ldg(G.row + gi + 1); kk < ke; kk += 32) {
+          const uint32_t r0 = __ldg(G.row + gi), r1 = __ldg(G.row + gi + 1);
+          const uint32_t u0 = __ldg(G.inc_ptr + gi), u1 = __ldg(G.inc_ptr + gi + 1);
+          for (uint32_t kk = r0 + lane; kk < r1; kk += 32) {
             const int c = __ldg(G.col + kk);
             if constexpr (INT) {
               const long long t2 = 2 * fx_of(G.J, fl, kk, unit_of(c));
@@ -395,9 +406,9 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
             } else {
               f[c] += coupling(G, fl, kk) * (2.0 * (double)snew);
             }
-            atomicOr(S.dirty + (c >> 10), 1u << ((c >> 5) & 31));
+            if (kk - r0 < (uint32_t)kTouched) S.touched[kk - r0] = (int16_t)c;
           }
-          const uint32_t u0 = __ldg(G.inc_ptr + gi), u1 = __ldg(G.inc_ptr + gi + 1);
+          uint32_t n_touched = r1 - r0;
           for (uint32_t u = u0; u < u1; ++u) {
             __syncwarp();
             const int64_t e = __ldg(G.inc_edge + u);
@@ -407,6 +418,8 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
             const int par = __popc(__ballot_sync(0xffffffffu, neg)) & 1;
             for (uint32_t q = q0 + lane; q < q1; q += 32) {
               const int m = __ldg(G.hmem + q);
+              const uint32_t slot_t = n_touched + (q - q0);
+              if (slot_t < (uint32_t)kTouched) S.touched[slot_t] = (int16_t)(m == i ? -1 : m);
               if (m == i) continue;
               const bool minus = par ^ (s[m] < 0);  // the other members' product is -1
               if constexpr (INT) {
@@ -416,8 +429,8 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
                 const double w2 = 2.0 * coupling_e(G, fl, e);
                 f[m] += w2 * (minus ? -1.0 : 1.0);
               }
-              atomicOr(S.dirty + (m >> 10), 1u << ((m >> 5) & 31));
             }
+            n_touched += q1 - q0;
           }
           // the earliest strictly lowest prefix so far ends here: remember
           // which spins it moved (every spin moves once per pass, so the
@@ -427,8 +440,53 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
             for (int j = lane; j < S.nb; j += 32) S.best[j] = S.lock[j];
           }
           __syncwarp();
+          // Block maxima after the move.  The moved spin's block is recomputed
+          // (its maximum is now locked).  A touched unlocked spin elsewhere
+          // either raises its block's maximum (applied one spin at a time, the
+          // larger key or on equal keys the lower index winning) or, when it
+          // was that maximum and its key fell, marks the block for a recompute.
+          // A move touching more than kTouched fields recomputes every block.
+          if (n_touched <= (uint32_t)kTouched) {
+            const int jm = i >> 5;
+            for (uint32_t t0 = 0; t0 < n_touched; t0 += 32) {  // at most two rounds
+              const uint32_t t = t0 + lane;
+              const int ct = t < n_touched ? S.touched[t] : -1;
+              unsigned long long kt = 0ull;
+              bool raise = false;
+              if (ct >= 0 && (ct >> 5) != jm && !((S.lock[ct >> 5] >> (ct & 31)) & 1u)) {
+                kt = spin_key<M>(S, ct);
+                const int jb = ct >> 5;
+                const unsigned long long ok = S.bkey[jb];
+                const int oi = S.bidx[jb];
+                if (oi == ct && kt < ok)
+                  atomicOr(S.dirty + (jb >> 5), 1u << (jb & 31));
+                else
+                  raise = oi == ct || kt > ok || (kt == ok && ct < oi);
+              }
+              // apply the raises one lane at a time against the current maximum
+              unsigned pend = __ballot_sync(0xffffffffu, raise);
+              while (pend) {
+                const int L = __ffs(pend) - 1;
+                pend &= pend - 1u;
+                if (lane == L) {
+                  const int jb = ct >> 5;
+                  const unsigned long long ok = S.bkey[jb];
+                  const int oi = S.bidx[jb];
+                  if (oi == ct ? kt >= ok : (kt > ok || (kt == ok && ct < oi))) {
+                    S.bkey[jb] = kt;
+                    S.bidx[jb] = (int16_t)ct;
+                  }
+                }
+                __syncwarp();
+              }
+            }
+          } else {
+            for (int dw = lane; dw < 4; dw += 32) S.dirty[dw] = 0xffffffffu;
+          }
+          __syncwarp();
           for (int dw = 0; dw < (S.nb + 31) / 32; ++dw) {
             unsigned d = S.dirty[dw];
+            if (dw == (S.nb - 1) >> 5 && (S.nb & 31)) d &= (1u << (S.nb & 31)) - 1u;
             while (d) {
               const int jb = __ffs(d) - 1;
               d &= d - 1u;
@@ -589,20 +647,20 @@ struct FmPart {
 // Warps per CTA (one search each) and CTAs per SM for instances of up to
 // nmax spins: the most searches per SM that shared memory and registers allow,
 // the larger CTA among equals.
-template <int M>
+template <int M, bool FL>
 cudaError_t fm_shape(const ising_handle *h, int nmax, int &warps, size_t &smem, int &per_sm) {
   const size_t per_warp = (fm_warp_bytes(nmax, M) + 15) & ~(size_t)15;
   int smem_optin = 0;
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
   cudaError_t e;
   const int wmax = (int)std::max<size_t>(1, std::min<size_t>(kFW, (size_t)smem_optin / per_warp));
-  if ((e = cudaFuncSetAttribute(fm_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if ((e = cudaFuncSetAttribute(fm_kernel<M, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(per_warp * wmax))) != cudaSuccess)
     return e;
   int best = -1;
   for (int w = wmax; w >= 1; --w) {
     int c = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, fm_kernel<M>, w * 32, per_warp * w)) != cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, fm_kernel<M, FL>, w * 32, per_warp * w)) != cudaSuccess)
       return e;
     if (c * w > best) {
       best = c * w;
@@ -665,7 +723,10 @@ cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_
   // the searches alone would leave the GPU underfilled.
   int warps0 = 0, per_sm0 = 0;
   size_t smem0 = 0;
-  if ((e = fm_shape<kFx>(h, h->nmax, warps0, smem0, per_sm0)) != cudaSuccess) return e;
+  const bool fl = h->dtype == ISING_F32;
+  if ((e = fl ? fm_shape<kFx, true>(h, h->nmax, warps0, smem0, per_sm0)
+              : fm_shape<kFx, false>(h, h->nmax, warps0, smem0, per_sm0)) != cudaSuccess)
+    return e;
   const int64_t resident = (int64_t)h->sm_count * per_sm0 * warps0;
   const size_t sp_bytes = ((size_t)R * restarts * h->total_spins + 15) & ~(size_t)15;
   const size_t e_bytes = (size_t)n_items * restarts * sizeof(double);
@@ -708,9 +769,11 @@ cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_
     const int nmax = P.nmax;  // the group's largest instance
     int warps = 0, per_sm = 0;
     size_t smem = 0;
-    le = P.mode == kFx ? fm_shape<kFx>(h, nmax, warps, smem, per_sm)
-                       : (P.mode == kFxSpin ? fm_shape<kFxSpin>(h, nmax, warps, smem, per_sm)
-                                            : fm_shape<kFp64>(h, nmax, warps, smem, per_sm));
+    // int8 couplings are always exact in one unit (mode kFx)
+    le = !fl ? fm_shape<kFx, false>(h, nmax, warps, smem, per_sm)
+             : P.mode == kFx ? fm_shape<kFx, true>(h, nmax, warps, smem, per_sm)
+             : P.mode == kFxSpin ? fm_shape<kFxSpin, true>(h, nmax, warps, smem, per_sm)
+                                 : fm_shape<kFp64, true>(h, nmax, warps, smem, per_sm);
     if (le != cudaSuccess) break;
     FmArgs A;
     A.g = h->graph();
@@ -718,7 +781,6 @@ cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_
     A.R_out = split ? R * restarts : R;
     A.restarts = restarts;
     A.max_passes = max_passes;
-    A.is_float = h->dtype == ISING_F32 ? 1 : 0;
     A.split = split ? 1 : 0;
     A.items = B.items + P.first;
     A.seeds = h->d_seeds;
@@ -729,12 +791,14 @@ cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_
     A.stats = h->d_stats;
     const int64_t ctas_needed = ((int64_t)A.n_work + warps - 1) / warps;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->sm_count * per_sm, ctas_needed));
-    if (P.mode == kFx)
-      fm_kernel<kFx><<<grid, warps * 32, smem, ls>>>(A, nmax);
+    if (!fl)
+      fm_kernel<kFx, false><<<grid, warps * 32, smem, ls>>>(A, nmax);
+    else if (P.mode == kFx)
+      fm_kernel<kFx, true><<<grid, warps * 32, smem, ls>>>(A, nmax);
     else if (P.mode == kFxSpin)
-      fm_kernel<kFxSpin><<<grid, warps * 32, smem, ls>>>(A, nmax);
+      fm_kernel<kFxSpin, true><<<grid, warps * 32, smem, ls>>>(A, nmax);
     else
-      fm_kernel<kFp64><<<grid, warps * 32, smem, ls>>>(A, nmax);
+      fm_kernel<kFp64, true><<<grid, warps * 32, smem, ls>>>(A, nmax);
     h->launches += 1;
     le = cudaGetLastError();
   }

@@ -184,3 +184,12 @@ def test_fm_float_per_spin_exact_instance():
     b = W.random_graph(150, 4.0, 94, dtype="f32", n_hyper=8, hyper_order=(3, 4))
     c = W.random_graph(120, 4.0, 95, dtype="f32", n_hyper=6, hyper_order=(3,))
     _compare([_two_scales(a, b), c, _wide_spread(b)], 12, 2, False)
+
+
+@pytest.mark.parametrize("dtype", ["i8", "f32"])
+def test_fm_denser_graph(dtype):
+    """Degrees around 30-60: a move's changed fields span one or two rounds of
+    the warp and, for the densest spins, more than the touched list holds (every
+    block maximum is then recomputed)."""
+    inst = W.random_graph(400, 46.0, 96, dtype=dtype, n_hyper=30, hyper_order=(3, 5))
+    _compare([inst], 8, 2, dtype == "i8")
