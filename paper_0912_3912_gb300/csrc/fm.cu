@@ -371,6 +371,11 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
             }
           }
           const int i = warp_argmax(bk, bi).idx;
+          // the moved spin's row and incidence bounds, loaded before its
+          // bookkeeping so that the loads overlap it
+          const int64_t gi = so + i;
+          const uint32_t r0 = __ldg(G.row + gi), r1 = __ldg(G.row + gi + 1);
+          const uint32_t u0 = __ldg(G.inc_ptr + gi), u1 = __ldg(G.inc_ptr + gi + 1);
           bool new_best = false;
           if (lane == 0) {
             TE gain;
@@ -395,9 +400,6 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
           // (distinct within an edge); every changed field's spin goes to
           // the touched list (CSR entries first, then the edges' members)
           const int8_t snew = s[i];
-          const int64_t gi = so + i;
-          const uint32_t r0 = __ldg(G.row + gi), r1 = __ldg(G.row + gi + 1);
-          const uint32_t u0 = __ldg(G.inc_ptr + gi), u1 = __ldg(G.inc_ptr + gi + 1);
           for (uint32_t kk = r0 + lane; kk < r1; kk += 32) {
             const int c = __ldg(G.col + kk);
             if constexpr (INT) {
