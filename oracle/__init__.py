@@ -226,3 +226,69 @@ def transfer_matrix(inst, rows, cols, periodic_rows, periodic_cols):
     if not ok.value:
         raise ValueError("instance is not a grid this routine accepts")
     return float(E)
+
+
+def window_instance(inst, s, members):
+    """The window check of Sec. V (branch and bound on a few dozen adjacent spins
+    with the rest of a local-search result held fixed), as an instance over the
+    spins `members` alone.  With every other spin fixed at `s`, Eq. 1 / Eq. 6
+    split into terms inside the window, terms with one window spin (added to
+    that spin's field: h_i plus J_ij s_j over fixed neighbours j, plus J_e times
+    the fixed members' product for a hyper-edge with one window member), terms
+    of hyper-edges with two or more window members (kept, coupling J_e times
+    the fixed members' product) and a constant.  Returns (sub-instance, const)
+    with E(state) = E_sub(state restricted to the window) + const.  Couplings
+    and fields must be integers (int8 instances) so that the folded fields are
+    exact."""
+    import workloads as W  # the Instance container only
+    if inst.dtype != "i8":
+        raise ValueError("window_instance folds fields exactly for int8 instances only")
+    members = [int(m) for m in members]
+    pos = {m: k for k, m in enumerate(members)}
+    s = np.asarray(s, dtype=np.int64)
+    nw = len(members)
+    h = np.zeros(nw, dtype=np.int64)
+    if inst.h is not None:
+        for m, k in pos.items():
+            h[k] = int(inst.h[m])
+    rows = [[] for _ in range(nw)]
+    for m, k in pos.items():
+        for q in range(int(inst.row_ptr[m]), int(inst.row_ptr[m + 1])):
+            j = int(inst.col[q])
+            Jv = int(inst.J[q])
+            if j in pos:
+                rows[k].append((pos[j], Jv))
+            else:
+                h[k] += Jv * s[j]
+    hp, hm, hJ = [0], [], []
+    if inst.hyper_ptr is not None:
+        for e in range(len(inst.hyper_ptr) - 1):
+            mem = [int(x) for x in inst.hyper_members[inst.hyper_ptr[e]:inst.hyper_ptr[e + 1]]]
+            inside = [pos[x] for x in mem if x in pos]
+            prod = 1
+            for x in mem:
+                if x not in pos:
+                    prod *= int(s[x])
+            Je = int(inst.hyper_J[e]) * prod
+            if len(inside) == 1:
+                h[inside[0]] += Je
+            elif len(inside) >= 2:
+                hm.extend(inside)
+                hp.append(len(hm))
+                hJ.append(Je)
+    if np.abs(h).max(initial=0) > 127:
+        raise ValueError("folded field outside int8")
+    row_ptr = np.zeros(nw + 1, dtype=np.int64)
+    col, J = [], []
+    for k in range(nw):
+        for j, Jv in sorted(rows[k]):
+            col.append(j)
+            J.append(Jv)
+        row_ptr[k + 1] = len(col)
+    sub = W.Instance(n=nw, row_ptr=row_ptr, col=np.array(col, dtype=np.int32), J=np.array(J, dtype=np.int8),
+                     h=h.astype(np.int8),
+                     hyper_ptr=np.array(hp, dtype=np.int64) if hJ else None,
+                     hyper_members=np.array(hm, dtype=np.int32) if hJ else None,
+                     hyper_J=np.array(hJ, dtype=np.int8) if hJ else None, dtype="i8")
+    const = energy(inst, s.astype(np.int8)) - energy(sub, s[members].astype(np.int8))
+    return sub, const
