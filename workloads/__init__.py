@@ -263,6 +263,77 @@ def random_graph(n: int, avg_degree: float, seed: int, dtype: str = "f32",
                     hyper_J=hJ, dtype=dtype, meta={"kind": "random"})
 
 
+def _poly_mul(a: dict, b: dict) -> dict:
+    """Product of multilinear polynomials in +/-1 spins (S_i^2 = 1): monomials
+    are frozensets of spin indices, multiplied by symmetric difference."""
+    out = {}
+    for ka, va in a.items():
+        for kb, vb in b.items():
+            k = ka ^ kb
+            out[k] = out.get(k, 0) + va * vb
+    return {k: v for k, v in out.items() if v}
+
+
+def factoring(N: int, n_x: int, n_y: int, hyper: bool = True) -> Instance:
+    """Factoring N as a hyper-Ising instance (Sec. VI, Eqs. 7-9).
+
+    x = 1 + sum_{i=1..n_x} 2^i b_i and y = 1 + sum_{j=1..n_y} 2^j c_j (odd
+    factors; bit 0 is fixed), bits b = (1 - S) / 2.  Spins: x's bits 1..n_x
+    first, then y's bits n_y..1 (the order of Fig. 7's N = 21 example).  The
+    objective f = (N - x y)^2 expanded in the spins (integer coefficients, terms
+    of up to four spins) becomes Eq. 6 with h_i = -c_i and J_e = -c_e, so that
+    E = f - c_0 and the ground states (E = -c_0) are the factorisations.  Pair
+    terms go to the CSR couplings, 3- and 4-spin terms to hyper-edges (left out
+    with hyper=False, the reduced model whose ground states need not factor N).
+    Couplings are FP32 and must be integers below 2^24 in magnitude (exact);
+    larger N raise ValueError.  meta holds N, n_x, n_y and c_0."""
+    n = n_x + n_y
+    x = {frozenset(): 1}
+    y = {frozenset(): 1}
+    for i in range(1, n_x + 1):  # 2^i b = 2^(i-1) (1 - S)
+        x[frozenset()] += 2 ** (i - 1)
+        x[frozenset([i - 1])] = -(2 ** (i - 1))
+    for k, j in enumerate(range(n_y, 0, -1)):
+        y[frozenset()] += 2 ** (j - 1)
+        y[frozenset([n_x + k])] = -(2 ** (j - 1))
+    g = {kk: -v for kk, v in _poly_mul(x, y).items()}
+    g[frozenset()] = g.get(frozenset(), 0) + N
+    f = _poly_mul({kk: v for kk, v in g.items() if v}, {kk: v for kk, v in g.items() if v})
+    c0 = f.pop(frozenset(), 0)
+    if any(abs(v) >= 1 << 24 for v in f.values()):
+        raise ValueError("coefficients beyond 2^24: not exact in FP32")
+    h = np.zeros(n, dtype=np.float32)
+    u, v, w, hm, hp, hJ = [], [], [], [], [0], []
+    for mono in sorted(f, key=lambda m: (len(m), sorted(m))):
+        c = f[mono]
+        idx = sorted(mono)
+        if len(idx) == 1:
+            h[idx[0]] = -c
+        elif len(idx) == 2:
+            u.append(idx[0])
+            v.append(idx[1])
+            w.append(-c)
+        elif hyper:
+            hm.extend(idx)
+            hp.append(len(hm))
+            hJ.append(-c)
+    row_ptr, col, J = csr_from_edges(n, np.array(u, dtype=np.int64), np.array(v, dtype=np.int64),
+                                     np.array(w, dtype=np.float32), "f32")
+    return Instance(n=n, row_ptr=row_ptr, col=col, J=J, h=h,
+                    hyper_ptr=np.array(hp, dtype=np.int64) if hJ else None,
+                    hyper_members=np.array(hm, dtype=np.int32) if hJ else None,
+                    hyper_J=np.array(hJ, dtype=np.float32) if hJ else None, dtype="f32",
+                    meta={"N": N, "n_x": n_x, "n_y": n_y, "c0": c0})
+
+
+def factoring_decode(inst: Instance, s) -> tuple:
+    """(x, y) of a spin configuration of a factoring instance."""
+    n_x, n_y = inst.meta["n_x"], inst.meta["n_y"]
+    x = 1 + sum(2 ** i * (1 - int(s[i - 1])) // 2 for i in range(1, n_x + 1))
+    y = 1 + sum(2 ** j * (1 - int(s[n_x + k])) // 2 for k, j in enumerate(range(n_y, 0, -1)))
+    return x, y
+
+
 def replica_seed(instance_seed: int) -> int:
     """Seed of the Philox random starts for an instance."""
     return splitmix64(instance_seed ^ 0xA5A5A5A5A5A5A5A5)
