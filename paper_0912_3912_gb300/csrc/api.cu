@@ -105,26 +105,27 @@ int32_t energy_base_exponent(const HostInst &I) {
   return emin;
 }
 
-// InstDesc::fx53: with unit u (2^(ebase - 150), or 1 for int8), the sum of
-// |term| / u over every coupling (both CSR directions), field and hyper-edge
-// coupling bounds every field, twice every gain and every energy; below 2^53
-// all of them, and every partial sum on the way, are exact in FP64.
+// InstDesc::fx53: with unit u (2^(ebase - 150), or 1 for int8), A = the sum
+// of |term| / u over the energy's terms (each pair once, fields, hyper-edge
+// couplings) bounds every energy, every field and every partial sum of either
+// (each is a signed sum of a subset of those terms); below 2^53 all of them
+// are exact in FP64, and the gains, twice a field, are too.
 int32_t fp64_exact(const HostInst &I, bool fl, int32_t ebase) {
   if (!fl) return 1;  // |terms| <= 127 and far fewer than 2^45 of them
   if (ebase < 0) return 0;
-  unsigned __int128 sum = 0;
-  auto add = [&](float v) {
+  auto units = [&](float v) -> unsigned __int128 {
     uint32_t b;
     std::memcpy(&b, &v, 4);
     b &= 0x7fffffffu;
-    if (!b) return;
+    if (!b) return 0;
     const int e = (int)(b >> 23);
-    sum += (unsigned __int128)((b & 0x7fffffu) | 0x800000u) << (e - ebase);
+    return (unsigned __int128)((b & 0x7fffffu) | 0x800000u) << (e - ebase);
   };
-  for (float v : I.Jf) add(v);
-  for (float v : I.hf) add(v);
-  for (float v : I.hJf) add(v);
-  return 2 * sum < ((unsigned __int128)1 << 53) ? 1 : 0;
+  unsigned __int128 pairs2 = 0, rest = 0;  // pairs2: both CSR directions, twice the pair sum
+  for (float v : I.Jf) pairs2 += units(v);
+  for (float v : I.hf) rest += units(v);
+  for (float v : I.hJf) rest += units(v);
+  return pairs2 / 2 + rest < ((unsigned __int128)1 << 53) ? 1 : 0;
 }
 
 // Recognise a periodic hypercubic lattice (side L >= 3, d = 2 or 3, spin index
