@@ -748,14 +748,18 @@ cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_
     P_k = reinterpret_cast<int32_t *>(E_k + (size_t)n_items * restarts);
   }
 
-  // Groups launch largest size class first; with several groups they go to
-  // side streams (forked from and joined back into s), so that a group's
-  // CTAs take the SMs as the previous group's retire instead of waiting for
-  // its last search.
+  // Groups launch largest size class first and, within a class, the group
+  // with fewer searches first: its CTAs take their SMs at once, and its
+  // searches (as long as the class's others) do not wait for the big group's
+  // persistent CTAs to retire.  With several groups they go to side streams
+  // (forked from and joined back into s), so that a group's CTAs take the SMs
+  // as the previous group's retire instead of waiting for its last search.
   std::vector<size_t> order(parts.size());
   for (size_t q = 0; q < parts.size(); ++q) order[q] = q;
-  std::stable_sort(order.begin(), order.end(),
-                   [&](size_t a, size_t c) { return cls(parts[a].nmax) > cls(parts[c].nmax); });
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t c) {
+    const int ca = cls(parts[a].nmax), cc = cls(parts[c].nmax);
+    return ca != cc ? ca > cc : parts[a].count < parts[c].count;
+  });
   const bool fan = parts.size() > 1;
   if (fan) {
     if ((e = ensure_side(B)) != cudaSuccess) return e;
