@@ -63,11 +63,16 @@ def make_workload(name: str, instances: int = 0, sk_n: int = 0):
         inst = W.lattice((100, 100, 100), periodic=True, couplings="pm1", seed=W.config_seed(4))
         return [inst], 16, dict(max_sweeps=1000, restarts=1 << 30, sweep_budget=1000), \
             "100^3 periodic +/-J lattice, 16 replicas, 1000-sweep budget with restarts"
+    if name == "l50":
+        # the size of the paper's 50x50 timing (ln^2 n random starts, Sec. V), for --method fm
+        inst = W.lattice((50, 50), periodic=True, couplings="gauss", seed=W.config_seed(6))
+        return [inst], 61, dict(max_sweeps=1000, restarts=1), \
+            "50x50 periodic Gaussian lattice, 61 = round(ln^2 2500) random starts"
     raise ValueError(name)
 
 
 def seeds_for(name: str, n_inst: int, rank: int):
-    base = W.config_seed(int(name[1]) - 1) + 1000003 * rank
+    base = W.config_seed(7 if name == "l50" else int(name[1]) - 1) + 1000003 * rank
     return [W.replica_seed(W.splitmix64(base + b)) for b in range(n_inst)]
 
 
