@@ -28,6 +28,9 @@
  *  Flipping spin i changes the energy by dE_i = 2 s_i f_i; the paper's gain is
  *  -dE_i (positive gain = lower energy).  A descent flips a spin iff dE_i < 0.
  *
+ *  Threads: calls on different handles may run concurrently on different host
+ *  threads; calls on one handle must not overlap.
+ *
  *  Schedules.  A sweep visits every spin once.
  *   - ISING_SCHED_COLOUR: colour classes c = 0..C-1 in ascending order; all
  *     spins of a class decide against the same state, then flip together.  A

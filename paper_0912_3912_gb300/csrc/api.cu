@@ -13,6 +13,13 @@
 #include "internal.h"
 
 namespace isg {
+std::mutex &state_mutex() {
+  static std::mutex m;
+  return m;
+}
+}  // namespace isg
+
+namespace isg {
 cudaError_t launch_plain(ising_handle *h, const ising_search_params *p, int32_t R, int8_t *spins, double *E,
                          int32_t *E32, int32_t *minima, const uint64_t *seeds_host, cudaStream_t s);
 cudaError_t launch_sweep(ising_handle *h, const ising_search_params *p, int32_t R, int8_t *spins, double *E,

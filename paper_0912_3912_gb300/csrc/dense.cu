@@ -411,6 +411,7 @@ bool dense_supported(const ising_handle *h, int32_t R) {
 }
 
 void dense_free(ising_handle *h) {
+  std::lock_guard<std::mutex> guard(state_mutex());
   auto &m = dense_states();
   auto it = m.find(h);
   if (it == m.end()) return;
@@ -421,7 +422,7 @@ void dense_free(ising_handle *h) {
 cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t R, int8_t *spins, double *E,
                          int32_t *E32, int32_t *minima, const uint64_t *seeds_host, cudaStream_t s) {
   (void)E32;
-  DenseState &D = dense_states()[h];
+  DenseState &D = locked_slot(dense_states(), h);
   cudaError_t e;
   const int Rp = (R + 7) / 8 * 8;
   int64_t joff = 0;

@@ -685,7 +685,7 @@ cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_
                       int32_t *passes, cudaStream_t s) {
   const int64_t n_items = (int64_t)h->n_inst * R;
   if (n_items > 0x7fffffff) return cudaErrorInvalidValue;
-  FmBufs &B = fm_bufs()[h];
+  FmBufs &B = locked_slot(fm_bufs(), h);
   cudaError_t e;
   // groups: one-unit integer instances, per-spin-unit ones, then FP64;
   // within each, size classes (0, 256], (256, 512], ... (2048, 4096],
@@ -824,6 +824,7 @@ cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_
 }
 
 void fm_free(ising_handle *h) {
+  std::lock_guard<std::mutex> guard(state_mutex());
   auto &m = fm_bufs();
   auto it = m.find(h);
   if (it == m.end()) return;

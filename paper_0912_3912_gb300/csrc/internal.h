@@ -6,6 +6,7 @@
 
 #include <cstdint>
 #include <map>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -177,6 +178,16 @@ struct ising_handle {
 };
 
 namespace isg {
+// Per-handle state of the launchers lives in maps keyed by handle; one mutex
+// guards their insertions and erasures, so that calls on different handles
+// may run on different threads (a handle's own state is used by one call at
+// a time; references into a std::map survive other keys' insertion and erasure).
+std::mutex &state_mutex();
+template <typename Map>
+typename Map::mapped_type &locked_slot(Map &m, const ising_handle *h) {
+  std::lock_guard<std::mutex> g(state_mutex());
+  return m[h];
+}
 // device timing around a launch (no-ops unless timing is on); name: a static string
 void kt_begin(ising_handle *h, const char *name, cudaStream_t s);
 void kt_end(ising_handle *h, cudaStream_t s);

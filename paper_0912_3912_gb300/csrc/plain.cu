@@ -259,6 +259,7 @@ std::map<const ising_handle *, PlainState> &plain_states() {
 }  // namespace
 
 void plain_free(ising_handle *h) {
+  std::lock_guard<std::mutex> guard(state_mutex());
   auto &m = plain_states();
   auto it = m.find(h);
   if (it == m.end()) return;
@@ -276,7 +277,7 @@ void plain_free(ising_handle *h) {
 // Runs the whole search for every instance, one instance after another.
 cudaError_t launch_plain(ising_handle *h, const ising_search_params *p, int32_t R, int8_t *spins, double *E,
                               int32_t *E32, int32_t *minima, const uint64_t *seeds_host, cudaStream_t s) {
-  PlainState &P = plain_states()[h];
+  PlainState &P = locked_slot(plain_states(), h);
   const size_t need = (size_t)R * h->nmax;
   cudaError_t e;
   if (need > P.cap_elems || R > P.cap_R) {

@@ -1206,7 +1206,7 @@ cudaError_t preload(int mode) {
 
 template <int LPS, bool LAT>
 cudaError_t run_instance(ising_handle *h, SweepArgs A, int mode, cudaStream_t s) {
-  SweepState &S = sweep_states()[h];
+  SweepState &S = locked_slot(sweep_states(), h);
   const InstDesc &I = A.I;
   const int ncls = A.sequential ? I.n : I.ncls;
   int maxcls = 1;
@@ -1317,6 +1317,7 @@ cudaError_t run_instance(ising_handle *h, SweepArgs A, int mode, cudaStream_t s)
 }  // namespace
 
 void sweep_free(ising_handle *h) {
+  std::lock_guard<std::mutex> guard(state_mutex());
   auto &m = sweep_states();
   auto it = m.find(h);
   if (it == m.end()) return;
@@ -1333,7 +1334,7 @@ void sweep_free(ising_handle *h) {
 
 cudaError_t launch_sweep(ising_handle *h, const ising_search_params *p, int32_t R, int8_t *spins, double *E,
                          int32_t *E32, int32_t *minima, const uint64_t *seeds_host, cudaStream_t s) {
-  SweepState &S = sweep_states()[h];
+  SweepState &S = locked_slot(sweep_states(), h);
   const int LPS = R > 16 ? 32 : (R > 8 ? 16 : 8);
   const int G = (R + 31) / 32;
   if (LPS < 32 && R > LPS) return cudaErrorInvalidValue;
