@@ -193,3 +193,32 @@ def test_fm_denser_graph(dtype):
     block maximum is then recomputed)."""
     inst = W.random_graph(400, 46.0, 96, dtype=dtype, n_hyper=30, hyper_order=(3, 5))
     _compare([inst], 8, 2, dtype == "i8")
+
+
+def test_two_handles_on_two_threads():
+    """Calls on different handles from different host threads give the same
+    results as the same calls made one after another."""
+    import threading
+    insts = [W.random_graph(500, 4.0, 97, dtype="f32", n_hyper=20, hyper_order=(3,)),
+             W.lattice((24, 24), periodic=True, couplings="pm1", seed=98)]
+
+    def run(inst, out, k):
+        h = isg.Handle([inst])
+        for _ in range(3):
+            sp, E, P, _ = h.fm_search([7 + k], 64, restarts=2)
+            res = h.local_search([7 + k], 64, max_sweeps=200, restarts=2)
+        torch.cuda.synchronize()
+        out[k] = (sp.cpu().numpy(), E.cpu().numpy(), res.spins.cpu().numpy(), res.energy.cpu().numpy())
+        h.close()
+
+    seq, par = {}, {}
+    for k, inst in enumerate(insts):
+        run(inst, seq, k)
+    threads = [threading.Thread(target=run, args=(inst, par, k)) for k, inst in enumerate(insts)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    for k in range(len(insts)):
+        for a, b in zip(seq[k], par[k]):
+            assert np.array_equal(a, b)
