@@ -327,6 +327,52 @@ def test_fm_passes_local_minimum_and_bruteforce(dtype, seed):
     assert hits >= 10
 
 
+def _fm_bruteforce(inst, s0):
+    """The passes of Fig. 3 with every gain taken as the difference of two full
+    energies (Eq. 1 / Eq. 6): no gain heap, no incremental gain updates.  The
+    largest gain among the unlocked spins moves (ties: lowest index), negative
+    gains included; the pass keeps its earliest prefix strictly below every
+    earlier energy (its start included); passes repeat while one improves."""
+    n = inst.n
+    s = np.array(s0, dtype=np.int8)
+    E = oracle.energy(inst, s)
+    passes = 0
+    while True:
+        passes += 1
+        cur, Ecur = s.copy(), E
+        locked = np.zeros(n, dtype=bool)
+        best_E, best_s = E, s.copy()
+        for _ in range(n):
+            cand = []
+            for i in range(n):
+                if not locked[i]:
+                    t = cur.copy()
+                    t[i] = -t[i]
+                    cand.append((-(Ecur - oracle.energy(inst, t)), i))
+            _, i = min(cand)
+            cur[i] = -cur[i]
+            locked[i] = True
+            Ecur = oracle.energy(inst, cur)
+            if Ecur < best_E:
+                best_E, best_s = Ecur, cur.copy()
+        if best_E < E:
+            s, E = best_s, best_E
+            continue
+        return s, E, passes
+
+
+@pytest.mark.parametrize("seed", [61, 62, 63, 64])
+def test_fm_passes_match_bruteforce_passes(seed):
+    """Integer instances (exact gains): the oracle's heap and incremental
+    updates make exactly the moves of the brute-force passes."""
+    inst = W.random_graph(13, 3.5, seed, dtype="i8", n_hyper=4, hyper_order=(3, 4), int_range=2)
+    for k in range(12):
+        s0 = oracle.random_start(inst.n, seed, 0, 0, k)
+        s_o, E_o, p_o = oracle.fm_search(inst, s0)
+        s_b, E_b, p_b = _fm_bruteforce(inst, s0)
+        assert np.array_equal(s_o, s_b) and E_o == E_b and p_o == p_b, (k, p_o, p_b, E_o, E_b)
+
+
 def test_fm_passes_beat_greedy_descent_on_average():
     inst = W.lattice((16, 16), periodic=True, couplings="gauss", seed=2)
     R = 16
