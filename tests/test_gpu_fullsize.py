@@ -112,3 +112,58 @@ def test_fullsize_lattice_100cubed(name, exact, tol):
     _check_sample(insts[0], 0, seeds[0], 1, kw, sp, E, m, exact)
     _check_properties(insts[0], sp, E, m, exact, tol)
     h.close()
+
+
+# --------------------------------------------------------------------------- pass-based search
+def _fm_full(name):
+    insts, R, kw, _ = bench.make_workload(name)
+    seeds = bench.seeds_for(name, len(insts), 0)
+    restarts = int(kw.get("restarts", 1))
+    h = isg.Handle(insts)
+    sp, E, P, st = h.fm_search(seeds, R, restarts=restarts)
+    torch.cuda.synchronize()
+    return insts, R, restarts, seeds, h, sp, E.cpu().numpy(), P.cpu().numpy(), st
+
+
+def _oracle_fm_best(inst, seed, b, r, restarts):
+    best, total = None, 0
+    for k in range(restarts):
+        s, Ek, p = oracle.fm_search(inst, oracle.random_start(inst.n, seed, b, r, k))
+        total += p
+        if best is None or Ek < best[1]:
+            best = (s, Ek)
+    return best[0], best[1], total
+
+
+def test_fm_c1_full_every_replica():
+    """16x16 +/-J, 64 replicas x 10 starts (starts in parallel, then the
+    best-start selection): every replica against the oracle."""
+    insts, R, restarts, seeds, h, sp, E, P, st = _fm_full("c1")
+    inst = insts[0]
+    s_all = h.spins_of(sp, 0, R).cpu().numpy()
+    for r in range(R):
+        s_o, E_o, p_o = _oracle_fm_best(inst, seeds[0], 0, r, restarts)
+        assert np.array_equal(s_all[r], s_o) and E[0, r] == E_o and P[0, r] == p_o, r
+    assert st["descents"] == R * restarts
+    h.close()
+
+
+def test_fm_c3_full_sampled_and_energies():
+    """4096 chimera instances x 32 replicas in one call: sampled searches
+    (largest, middle and smallest instances) against the oracle; on every
+    replica the returned energy is the oracle's energy of the returned spins."""
+    insts, R, restarts, seeds, h, sp, E, P, st = _fm_full("c3")
+    order = np.argsort([inst.n for inst in insts])
+    for b in (int(order[-1]), int(order[-2]), int(order[len(order) // 2]), int(order[0])):
+        s_all = h.spins_of(sp, b, R).cpu().numpy()
+        for r in (0, R - 1):
+            s_o, E_o, p_o = _oracle_fm_best(insts[b], seeds[b], b, r, restarts)
+            assert np.array_equal(s_all[r], s_o), (b, r)
+            assert P[b, r] == p_o
+            np.testing.assert_allclose(E[b, r], E_o, rtol=1e-9, atol=1e-9)
+    for b in range(0, len(insts), 97):
+        s_all = h.spins_of(sp, b, R).cpu().numpy()
+        Eo = oracle.energies(oracle.OracleInstance(insts[b]), s_all)
+        np.testing.assert_allclose(E[b], Eo, rtol=1e-9, atol=1e-9)
+    assert st["descents"] == len(insts) * R
+    h.close()
