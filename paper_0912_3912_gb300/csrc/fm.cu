@@ -547,6 +547,221 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
   }
 }
 
+// Small instances in the one-unit integer form (kFx, n <= 32 * kRegSlots):
+// lane l holds the fields, spin bits, lock bits and best-prefix bits of spins
+// l, l + 32, ... in registers.  A move's arg-max is each lane's maximum over
+// its own unlocked spins (registers only) and one warp reduction; the changed
+// fields travel through a 32-entry list in shared memory to the lanes that
+// hold them.  The spins are also kept in shared memory for the neighbour reads
+// of the per-pass field and energy sums.  Same moves as fm_kernel.
+constexpr int kRegSlots = 8;
+constexpr int kRegMaxSpins = 32 * kRegSlots;
+// per warp: fields staged at a pass's start, list deltas, spins, list spins
+constexpr size_t kRegWarpBytes = kRegMaxSpins * 8 + 32 * 8 + kRegMaxSpins + 32 * 4;
+
+template <bool FL>
+__global__ void __launch_bounds__(kFT, 2) fm_reg_kernel(FmArgs A) {
+  extern __shared__ __align__(16) uint8_t fm_smem[];
+  const DevGraph &G = A.g;
+  constexpr bool fl = FL;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint8_t *base = fm_smem + (size_t)warp * kRegWarpBytes;
+  long long *fsc = reinterpret_cast<long long *>(base);          // [kRegMaxSpins] fields at a pass's start
+  long long *ldv = fsc + kRegMaxSpins;                            // [32] field changes
+  int8_t *s = reinterpret_cast<int8_t *>(ldv + 32);               // [kRegMaxSpins] spins
+  int32_t *ldc = reinterpret_cast<int32_t *>(s + kRegMaxSpins);   // [32] the changed fields' spins
+  unsigned long long c_moves = 0, c_passes = 0, c_starts = 0;
+  for (;;) {
+    int w = 0;
+    if (lane == 0) w = atomicAdd(A.queue, 1);
+    w = __shfl_sync(0xffffffffu, w, 0);
+    if (w >= A.n_work) break;
+    const int it = A.split ? w / A.restarts : w;
+    const int k0 = A.split ? w % A.restarts : 0, k1 = A.split ? k0 + 1 : A.restarts;
+    const int b = A.items[it].x, r = A.items[it].y;
+    const int slot = A.split ? r * A.restarts + k0 : r;
+    const InstDesc I = G.inst[b];
+    const int n = I.n;
+    const int64_t so = I.spin_off;
+    const int unit = I.ebase;
+    const double scale = fl ? __longlong_as_double((long long)(unit - 150 + 1023) << 52) : 1.0;
+    uint32_t vm = 0;  // own slots that are spins of the instance
+#pragma unroll
+    for (int t = 0; t < kRegSlots; ++t)
+      if (lane + 32 * t < n) vm |= 1u << t;
+    const uint64_t seed = A.seeds[b];
+    int8_t *out = A.spins + (int64_t)A.R_out * so + (int64_t)slot * n;
+    double E_all = DBL_MAX;
+    int total_passes = 0;
+    for (int k = k0; k < k1; ++k) {
+      for (int i = lane; i < n; i += 32) {
+        const uint4 x = start_bits(seed, (uint32_t)(i >> 7), (uint32_t)r, (uint32_t)k, (uint32_t)b);
+        s[i] = ((word_of(x, (i & 127) >> 5) >> (i & 31)) & 1u) ? 1 : -1;
+      }
+      __syncwarp();
+      long long EstarI = fm_energy_fx(G, I, fl, s, lane, unit);
+      double Estar = (double)EstarI * scale;
+      int passes = 0;
+      for (;;) {
+        ++passes;
+        // own fields: h, the CSR row in order, then the hyper-edges ascending,
+        // staged in shared memory and then taken into registers
+        for (int i = lane; i < n; i += 32) {
+          const int64_t gi = so + i;
+          long long acc = fx_of(G.h, fl, gi, unit);
+          for (uint32_t kk = __ldg(G.row + gi), ke = __ldg(G.row + gi + 1); kk < ke; ++kk) {
+            const long long tj = fx_of(G.J, fl, kk, unit);
+            acc += s[__ldg(G.col + kk)] > 0 ? tj : -tj;
+          }
+          for (uint32_t u = __ldg(G.inc_ptr + gi), ue = __ldg(G.inc_ptr + gi + 1); u < ue; ++u) {
+            const int64_t e = __ldg(G.inc_edge + u);
+            const long long te = fx_of(G.hJ, fl, e, unit);
+            acc += hyper_sign(G, e, s, i) > 0 ? te : -te;
+          }
+          fsc[i] = acc;
+        }
+        __syncwarp();
+        long long fr[kRegSlots];
+        uint32_t sb = 0;  // own spins that are +1
+#pragma unroll
+        for (int t = 0; t < kRegSlots; ++t) {
+          const int i = lane + 32 * t;
+          fr[t] = i < n ? fsc[i] : 0;
+          if (i < n && s[i] > 0) sb |= 1u << t;
+        }
+        uint32_t lk = 0, bb = 0;  // own lock bits, own bits of the best prefix's spins
+        long long Ecur = EstarI, Ebest = EstarI;
+        bool any_best = false;
+        for (int step = 0; step < n; ++step) {
+          unsigned long long bk = 0ull;
+          int bi = 0x7fffffff;
+#pragma unroll
+          for (int t = 0; t < kRegSlots; ++t) {
+            if (((vm & ~lk) >> t) & 1u) {
+              const long long g = ((sb >> t) & 1u) ? -2 * fr[t] : 2 * fr[t];
+              const unsigned long long key = (unsigned long long)g ^ 0x8000000000000000ull;
+              if (key > bk) {  // ascending slots: the lower index keeps equal keys
+                bk = key;
+                bi = lane + 32 * t;
+              }
+            }
+          }
+          const KeyIdx m = warp_argmax(bk, bi);
+          const int i = m.idx;
+          Ecur -= (long long)(m.key ^ 0x8000000000000000ull);  // the move's gain
+          const bool new_best = Ecur < Ebest;
+          if (new_best) Ebest = Ecur;
+          const int8_t snew = (int8_t)-s[i];
+          if (lane == (i & 31)) {
+            lk |= 1u << (i >> 5);
+            sb ^= 1u << (i >> 5);
+          }
+          if (new_best) {
+            any_best = true;
+            bb = lk;
+          }
+          const int64_t gi = so + i;
+          const uint32_t r0 = __ldg(G.row + gi), r1 = __ldg(G.row + gi + 1);
+          const uint32_t u0 = __ldg(G.inc_ptr + gi), u1 = __ldg(G.inc_ptr + gi + 1);
+          __syncwarp();
+          if (lane == 0) s[i] = snew;
+          __syncwarp();
+          // CSR neighbours, 32 entries at a time through the list
+          for (uint32_t c0 = r0; c0 < r1; c0 += 32) {
+            const uint32_t kk = c0 + lane;
+            if (kk < r1) {
+              const long long t2 = 2 * fx_of(G.J, fl, kk, unit);
+              ldc[lane] = __ldg(G.col + kk);
+              ldv[lane] = snew > 0 ? t2 : -t2;
+            }
+            __syncwarp();
+            const int cnt = (int)min(32u, r1 - c0);
+            for (int q = 0; q < cnt; ++q) {
+              const int c = ldc[q];
+              const long long d = (c & 31) == lane ? ldv[q] : 0;
+              const int ts = c >> 5;
+#pragma unroll
+              for (int t = 0; t < kRegSlots; ++t) fr[t] += t == ts ? d : 0;
+            }
+            __syncwarp();
+          }
+          // hyper-edges in order, their members 32 at a time
+          for (uint32_t u = u0; u < u1; ++u) {
+            const int64_t e = __ldg(G.inc_edge + u);
+            const uint32_t q0 = __ldg(G.hptr + e), q1 = __ldg(G.hptr + e + 1);
+            int neg = 0;
+            for (uint32_t q = q0 + lane; q < q1; q += 32) neg ^= s[__ldg(G.hmem + q)] < 0;
+            const int par = __popc(__ballot_sync(0xffffffffu, neg)) & 1;
+            const long long w2 = 2 * fx_of(G.hJ, fl, e, unit);
+            for (uint32_t c0 = q0; c0 < q1; c0 += 32) {
+              const uint32_t q = c0 + lane;
+              if (q < q1) {
+                const int mm = __ldg(G.hmem + q);
+                const bool minus = par ^ (s[mm] < 0);
+                ldc[lane] = mm == i ? -1 : mm;
+                ldv[lane] = minus ? -w2 : w2;
+              }
+              __syncwarp();
+              const int cnt = (int)min(32u, q1 - c0);
+              for (int qq = 0; qq < cnt; ++qq) {
+                const int c = ldc[qq];
+                const long long d = c >= 0 && (c & 31) == lane ? ldv[qq] : 0;
+                const int ts = c >> 5;
+#pragma unroll
+                for (int t = 0; t < kRegSlots; ++t) fr[t] += t == ts ? d : 0;
+              }
+              __syncwarp();
+            }
+          }
+        }
+        // roll back to the best prefix: own spins outside its set flip back
+        const uint32_t back = vm & ~bb;
+#pragma unroll
+        for (int t = 0; t < kRegSlots; ++t)
+          if ((back >> t) & 1u) s[lane + 32 * t] = (int8_t)-s[lane + 32 * t];
+        __syncwarp();
+        const long long EnewI = fm_energy_fx(G, I, fl, s, lane, unit);
+        const double Enew = (double)EnewI * scale;
+        const double margin = fl ? 1e-9 * (1.0 + fabs(Estar)) : 0.0;
+        c_moves += (unsigned long long)n;
+        if (Enew < Estar - margin && (A.max_passes <= 0 || passes < A.max_passes)) {
+          Estar = Enew;
+          EstarI = EnewI;
+          continue;
+        }
+        if (Enew < Estar - margin) {
+          Estar = Enew;
+        } else if (any_best) {
+#pragma unroll
+          for (int t = 0; t < kRegSlots; ++t)
+            if (((vm & bb) >> t) & 1u) s[lane + 32 * t] = (int8_t)-s[lane + 32 * t];
+          __syncwarp();
+        }
+        break;
+      }
+      total_passes += passes;
+      c_passes += (unsigned long long)passes;
+      c_starts += 1;
+      if (Estar < E_all) {
+        E_all = Estar;
+        for (int i = lane; i < n; i += 32) out[i] = s[i];
+      }
+      __syncwarp();
+    }
+    if (lane == 0) {
+      A.energy[(int64_t)b * A.R_out + slot] = E_all;
+      if (A.passes) A.passes[(int64_t)b * A.R_out + slot] = total_passes;
+    }
+    __syncwarp();
+  }
+  if (lane == 0 && c_starts) {
+    atomicAdd(A.stats + 0, c_moves);
+    atomicAdd(A.stats + 1, c_moves);
+    atomicAdd(A.stats + 3, c_starts);
+    atomicAdd(A.stats + 4, c_passes);
+  }
+}
+
 // After split starts: per (instance, replica) the best start (strictly lower
 // energy, ties keep the earlier start), its spins, and the pass count summed
 // over the starts.  One warp per (instance, replica).
@@ -674,6 +889,29 @@ cudaError_t fm_shape(const ising_handle *h, int nmax, int &warps, size_t &smem, 
   return cudaSuccess;
 }
 
+// the register kernel's shape: 8 warps per CTA, as many CTAs per SM as fit
+template <bool FL>
+cudaError_t fm_reg_shape(const ising_handle *h, int &warps, size_t &smem, int &per_sm) {
+  (void)h;
+  warps = kFW;
+  smem = kRegWarpBytes * kFW;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(fm_reg_kernel<FL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+      cudaSuccess)
+    return e;
+  per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fm_reg_kernel<FL>, kFT, smem)) != cudaSuccess)
+    return e;
+  per_sm = std::max(per_sm, 1);
+  return cudaSuccess;
+}
+
+// ISING_FM_REG=0 keeps small instances on fm_kernel (both give the same results)
+bool fm_reg_off() {
+  const char *v = std::getenv("ISING_FM_REG");
+  return v && *v && std::atoi(v) == 0;
+}
+
 }  // namespace
 
 int fm_max_spins() { return kFmMaxSpins; }
@@ -775,8 +1013,10 @@ cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_
     const int nmax = P.nmax;  // the group's largest instance
     int warps = 0, per_sm = 0;
     size_t smem = 0;
+    const bool reg = P.mode == kFx && nmax <= kRegMaxSpins && !fm_reg_off();
     // int8 couplings are always exact in one unit (mode kFx)
-    le = !fl ? fm_shape<kFx, false>(h, nmax, warps, smem, per_sm)
+    le = reg ? (fl ? fm_reg_shape<true>(h, warps, smem, per_sm) : fm_reg_shape<false>(h, warps, smem, per_sm))
+       : !fl ? fm_shape<kFx, false>(h, nmax, warps, smem, per_sm)
              : P.mode == kFx ? fm_shape<kFx, true>(h, nmax, warps, smem, per_sm)
              : P.mode == kFxSpin ? fm_shape<kFxSpin, true>(h, nmax, warps, smem, per_sm)
                                  : fm_shape<kFp64, true>(h, nmax, warps, smem, per_sm);
@@ -797,7 +1037,11 @@ cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_
     A.stats = h->d_stats;
     const int64_t ctas_needed = ((int64_t)A.n_work + warps - 1) / warps;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->sm_count * per_sm, ctas_needed));
-    if (!fl)
+    if (reg && fl)
+      fm_reg_kernel<true><<<grid, warps * 32, smem, ls>>>(A);
+    else if (reg)
+      fm_reg_kernel<false><<<grid, warps * 32, smem, ls>>>(A);
+    else if (!fl)
       fm_kernel<kFx, false><<<grid, warps * 32, smem, ls>>>(A, nmax);
     else if (P.mode == kFx)
       fm_kernel<kFx, true><<<grid, warps * 32, smem, ls>>>(A, nmax);

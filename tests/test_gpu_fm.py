@@ -222,3 +222,33 @@ def test_two_handles_on_two_threads():
     for k in range(len(insts)):
         for a, b in zip(seq[k], par[k]):
             assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("dtype", ["i8", "f32"])
+def test_fm_register_kernel_matches_shared_memory_kernel(monkeypatch, dtype):
+    """Instances of up to 256 spins in the one-unit integer form run on the
+    register-resident kernel; ISING_FM_REG=0 keeps them on the shared-memory
+    kernel.  Identical spins, energies and pass counts, including a dense
+    instance (rows longer than a warp) and a hyper-edge with 40 members."""
+    insts = [W.random_graph(n, 4.0, 110 + n, dtype=dtype, n_hyper=n // 20, hyper_order=(3, 4)) for n in (7, 64, 200, 256)]
+    insts.append(W.random_graph(90, 50.0, 120, dtype=dtype))
+    big = W.random_graph(120, 3.0, 121, dtype=dtype)
+    hp = np.array([0, 40], dtype=np.int64)
+    hm = np.arange(0, 80, 2, dtype=np.int32)
+    hJ = np.array([1 if dtype == "i8" else 0.75], dtype=np.int8 if dtype == "i8" else np.float32)
+    insts.append(dataclasses.replace(big, hyper_ptr=hp, hyper_members=hm, hyper_J=hJ))
+    seeds = [31 + b for b in range(len(insts))]
+    out = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("ISING_FM_REG", mode)
+        h = isg.Handle(insts)
+        sp, E, P, st = h.fm_search(seeds, 12, restarts=3)
+        torch.cuda.synchronize()
+        out[mode] = (sp.cpu().numpy(), E.cpu().numpy(), P.cpu().numpy(), st["sweeps"])
+        h.close()
+    for a, b in zip(out["0"], out["1"]):
+        assert np.array_equal(a, b)
+    last = len(insts) - 1
+    _, E_o, p_o = _oracle_fm(insts[last], seeds[last], last, 12, 3)
+    assert np.array_equal(out["1"][2][last], p_o)
+    np.testing.assert_allclose(out["1"][1][last], E_o, rtol=1e-9, atol=1e-9)
