@@ -1,26 +1,30 @@
 // fm.cu — the paper's pass-based local search with hill climbing (Sec. IV,
 // Fig. 3) for instances of up to 4096 spins.
 //
-// One warp per search, as many per CTA as shared memory allows (fields in
-// FP64, the pass's move list, lock bits and spins of each warp's instance).
 // From each random start (Philox, the counter layout of ising_local_search)
-// the search runs passes.  A pass computes every spin's gain -2 s_i f_i
-// (FP64), then n times: takes the largest gain among the spins not yet moved
-// in this pass (ties to the lowest index), applies that move even when the gain
-// is negative (hill climbing), locks the spin, updates its neighbours' fields,
+// the search runs passes.  A pass computes every spin's gain -2 s_i f_i, then
+// n times: takes the largest gain among the spins not yet moved in this pass
+// (ties to the lowest index), applies that move even when the gain is
+// negative (hill climbing), locks the spin, updates its neighbours' fields,
 // and records the prefix whose running energy is strictly the lowest so far
 // (the earliest such prefix).  The pass is then rolled back to that prefix; a
 // new pass follows while the pass lowered the energy strictly (for float
 // couplings by more than 1e-9 relative, so FP64 rounding cannot fake an
-// improvement), else the pass's start is the result.  The paper keeps the
-// gains in a heap (Fig. 4); here the warp takes the maximum by shuffles at each
-// move (gains compared as order-preserving integers), which selects the same spin.
+// improvement), else the pass's start is the result.
 //
-// The arithmetic follows the definition in this order: fields are FP64 sums
-// of h_i, then the CSR row in stored order, then the incident hyper-edges in
-// ascending edge order; a move of spin i adds 2 J_ij s_i to the fields of its
-// CSR neighbours in row order and then each incident hyper-edge's term to its
-// other members.  Integer couplings are exact throughout.
+// The values are those of FP64 arithmetic in the definition's order: fields
+// summed as h_i, then the CSR row in stored order, then the incident
+// hyper-edges in ascending edge order; a move of spin i adds 2 J_ij s_i to its
+// CSR neighbours' fields and each incident hyper-edge's term to its other
+// members.  Where FP64 computes an instance's values exactly, the kernels hold
+// them as 64-bit integers (one unit per instance, or per spin), with the same
+// results and no FP64 on the per-move path.
+//
+// One warp per search.  The paper keeps the gains in a heap (Fig. 4);
+// fm_kernel keeps per-warp maxima of 32-spin blocks in shared memory and takes
+// the move's spin by warp reductions over them (gains compared as
+// order-preserving integers); fm_reg_kernel holds a small instance's fields in
+// the lanes' registers.  Both select the heap's spin.
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
