@@ -551,29 +551,29 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
   }
 }
 
-// Small instances in the one-unit integer form (kFx, n <= 32 * kRegSlots):
+// Small instances in the one-unit integer form (kFx, n <= 32 * S, S = 8 or 16):
 // lane l holds the fields, spin bits, lock bits and best-prefix bits of spins
 // l, l + 32, ... in registers.  A move's arg-max is each lane's maximum over
 // its own unlocked spins (registers only) and one warp reduction; the changed
 // fields travel through a 32-entry list in shared memory to the lanes that
 // hold them.  The spins are also kept in shared memory for the neighbour reads
 // of the per-pass field and energy sums.  Same moves as fm_kernel.
-constexpr int kRegSlots = 8;
-constexpr int kRegMaxSpins = 32 * kRegSlots;
+constexpr int kRegMaxSpins = 32 * 16;
 // per warp: fields staged at a pass's start, list deltas, spins, list spins
-constexpr size_t kRegWarpBytes = kRegMaxSpins * 8 + 32 * 8 + kRegMaxSpins + 32 * 4;
+__host__ __device__ constexpr size_t reg_warp_bytes(int S) { return (size_t)32 * S * 9 + 32 * 8 + 32 * 4; }
 
-template <bool FL>
-__global__ void __launch_bounds__(kFT, 2) fm_reg_kernel(FmArgs A) {
+template <bool FL, int S>
+__global__ void __launch_bounds__(kFT, S <= 8 ? 2 : 1) fm_reg_kernel(FmArgs A) {
+  constexpr int kRegSlots = S;
   extern __shared__ __align__(16) uint8_t fm_smem[];
   const DevGraph &G = A.g;
   constexpr bool fl = FL;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint8_t *base = fm_smem + (size_t)warp * kRegWarpBytes;
-  long long *fsc = reinterpret_cast<long long *>(base);          // [kRegMaxSpins] fields at a pass's start
-  long long *ldv = fsc + kRegMaxSpins;                            // [32] field changes
-  int8_t *s = reinterpret_cast<int8_t *>(ldv + 32);               // [kRegMaxSpins] spins
-  int32_t *ldc = reinterpret_cast<int32_t *>(s + kRegMaxSpins);   // [32] the changed fields' spins
+  uint8_t *base = fm_smem + (size_t)warp * reg_warp_bytes(S);
+  long long *fsc = reinterpret_cast<long long *>(base);  // [32 S] fields at a pass's start
+  long long *ldv = fsc + 32 * S;                          // [32] field changes
+  int8_t *s = reinterpret_cast<int8_t *>(ldv + 32);       // [32 S] spins
+  int32_t *ldc = reinterpret_cast<int32_t *>(s + 32 * S); // [32] the changed fields' spins
   unsigned long long c_moves = 0, c_passes = 0, c_starts = 0;
   for (;;) {
     int w = 0;
@@ -894,26 +894,32 @@ cudaError_t fm_shape(const ising_handle *h, int nmax, int &warps, size_t &smem, 
 }
 
 // the register kernel's shape: 8 warps per CTA, as many CTAs per SM as fit
-template <bool FL>
+template <bool FL, int S>
 cudaError_t fm_reg_shape(const ising_handle *h, int &warps, size_t &smem, int &per_sm) {
   (void)h;
   warps = kFW;
-  smem = kRegWarpBytes * kFW;
+  smem = reg_warp_bytes(S) * kFW;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(fm_reg_kernel<FL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+  if ((e = cudaFuncSetAttribute(fm_reg_kernel<FL, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
       cudaSuccess)
     return e;
   per_sm = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fm_reg_kernel<FL>, kFT, smem)) != cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fm_reg_kernel<FL, S>, kFT, smem)) !=
+      cudaSuccess)
     return e;
   per_sm = std::max(per_sm, 1);
   return cudaSuccess;
 }
 
-// ISING_FM_REG=0 keeps small instances on fm_kernel (both give the same results)
+// ISING_FM_REG=0 keeps small instances on fm_kernel, =1 puts them on the
+// register kernel whatever their number (both give the same results)
 bool fm_reg_off() {
   const char *v = std::getenv("ISING_FM_REG");
   return v && *v && std::atoi(v) == 0;
+}
+bool fm_reg_forced() {
+  const char *v = std::getenv("ISING_FM_REG");
+  return v && *v && std::atoi(v) == 1;
 }
 
 }  // namespace
@@ -1017,13 +1023,25 @@ cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_
     const int nmax = P.nmax;  // the group's largest instance
     int warps = 0, per_sm = 0;
     size_t smem = 0;
-    const bool reg = P.mode == kFx && nmax <= kRegMaxSpins && !fm_reg_off();
+    // Small one-unit instances take the register kernel when the group's
+    // searches fit in one wave of it (latency-bound); larger groups keep the
+    // shared-memory kernel, which holds more searches per SM.
+    const int64_t work = split ? P.count * restarts : P.count;
+    const bool reg8 = nmax <= 256;
+    bool reg = P.mode == kFx && nmax <= kRegMaxSpins && !fm_reg_off();
+    if (reg) {
+      le = fl ? (reg8 ? fm_reg_shape<true, 8>(h, warps, smem, per_sm) : fm_reg_shape<true, 16>(h, warps, smem, per_sm))
+              : (reg8 ? fm_reg_shape<false, 8>(h, warps, smem, per_sm)
+                      : fm_reg_shape<false, 16>(h, warps, smem, per_sm));
+      if (le != cudaSuccess) break;
+      reg = work <= (int64_t)h->sm_count * per_sm * warps || fm_reg_forced();
+    }
     // int8 couplings are always exact in one unit (mode kFx)
-    le = reg ? (fl ? fm_reg_shape<true>(h, warps, smem, per_sm) : fm_reg_shape<false>(h, warps, smem, per_sm))
-       : !fl ? fm_shape<kFx, false>(h, nmax, warps, smem, per_sm)
-             : P.mode == kFx ? fm_shape<kFx, true>(h, nmax, warps, smem, per_sm)
-             : P.mode == kFxSpin ? fm_shape<kFxSpin, true>(h, nmax, warps, smem, per_sm)
-                                 : fm_shape<kFp64, true>(h, nmax, warps, smem, per_sm);
+    if (!reg)
+      le = !fl ? fm_shape<kFx, false>(h, nmax, warps, smem, per_sm)
+               : P.mode == kFx ? fm_shape<kFx, true>(h, nmax, warps, smem, per_sm)
+               : P.mode == kFxSpin ? fm_shape<kFxSpin, true>(h, nmax, warps, smem, per_sm)
+                                   : fm_shape<kFp64, true>(h, nmax, warps, smem, per_sm);
     if (le != cudaSuccess) break;
     FmArgs A;
     A.g = h->graph();
@@ -1041,10 +1059,14 @@ cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_
     A.stats = h->d_stats;
     const int64_t ctas_needed = ((int64_t)A.n_work + warps - 1) / warps;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)h->sm_count * per_sm, ctas_needed));
-    if (reg && fl)
-      fm_reg_kernel<true><<<grid, warps * 32, smem, ls>>>(A);
+    if (reg && fl && reg8)
+      fm_reg_kernel<true, 8><<<grid, warps * 32, smem, ls>>>(A);
+    else if (reg && fl)
+      fm_reg_kernel<true, 16><<<grid, warps * 32, smem, ls>>>(A);
+    else if (reg && reg8)
+      fm_reg_kernel<false, 8><<<grid, warps * 32, smem, ls>>>(A);
     else if (reg)
-      fm_reg_kernel<false><<<grid, warps * 32, smem, ls>>>(A);
+      fm_reg_kernel<false, 16><<<grid, warps * 32, smem, ls>>>(A);
     else if (!fl)
       fm_kernel<kFx, false><<<grid, warps * 32, smem, ls>>>(A, nmax);
     else if (P.mode == kFx)

@@ -226,11 +226,13 @@ def test_two_handles_on_two_threads():
 
 @pytest.mark.parametrize("dtype", ["i8", "f32"])
 def test_fm_register_kernel_matches_shared_memory_kernel(monkeypatch, dtype):
-    """Instances of up to 256 spins in the one-unit integer form run on the
-    register-resident kernel; ISING_FM_REG=0 keeps them on the shared-memory
+    """Instances of up to 512 spins in the one-unit integer form run on the
+    register-resident kernel (8 or 16 spins per lane; ISING_FM_REG=1 whatever
+    the number of searches); ISING_FM_REG=0 keeps them on the shared-memory
     kernel.  Identical spins, energies and pass counts, including a dense
     instance (rows longer than a warp) and a hyper-edge with 40 members."""
-    insts = [W.random_graph(n, 4.0, 110 + n, dtype=dtype, n_hyper=n // 20, hyper_order=(3, 4)) for n in (7, 64, 200, 256)]
+    insts = [W.random_graph(n, 4.0, 110 + n, dtype=dtype, n_hyper=n // 20, hyper_order=(3, 4))
+             for n in (7, 64, 200, 256, 257, 400, 512)]
     insts.append(W.random_graph(90, 50.0, 120, dtype=dtype))
     big = W.random_graph(120, 3.0, 121, dtype=dtype)
     hp = np.array([0, 40], dtype=np.int64)
