@@ -218,6 +218,10 @@ def main():
     if args.replicas or args.restarts or args.sweep_budget >= 0 or args.instances or args.sk_n:
         desc += f" [reduced: replicas={R}, {kw}]"
 
+    if args.impl == "reference" and args.method == "fm":
+        if rank == 0:
+            run_fm_reference(args, insts, R, kw, desc)
+        return
     if args.impl == "reference":
         if rank != 0:
             return
@@ -481,6 +485,42 @@ def run_fm(args, insts, R, kw, desc):
             "cpu_baseline": cpu}
     print(json.dumps(line))
     h.close()
+
+
+def run_fm_reference(args, insts, R, kw, desc):
+    """The reference arm of --method fm: the oracle's pass-based search (heap,
+    one host core) on the first starts of the workload, each step a bounded
+    sample (about --cpu-seconds / steps of work), moves applied per second."""
+    import oracle
+    oracle.build()
+    seeds = seeds_for(args.workload, len(insts), 0)
+    restarts = int(kw.get("restarts", 1))
+    budget = max(args.cpu_seconds / max(args.steps + args.warmup, 1), 0.05)
+    units = [(b, r, k) for b in range(len(insts)) for r in range(R) for k in range(restarts)]
+    pos, rates, moves_all, runs_all, t_all = 0, [], 0, 0, 0.0
+    for step in range(args.warmup + args.steps):
+        moves, runs, t0 = 0, 0, time.perf_counter()
+        while time.perf_counter() - t0 < budget:
+            b, r, k = units[pos % len(units)]
+            pos += 1
+            _, _, p = oracle.fm_search(insts[b], oracle.random_start(insts[b].n, seeds[b], b, r, k))
+            moves += p * insts[b].n
+            runs += 1
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            rates.append(moves / dt)
+            moves_all, runs_all, t_all = moves_all + moves, runs_all + runs, t_all + dt
+    value = moves_all / t_all
+    sample = f"{runs_all} oracle searches (first starts of this workload, in order), {moves_all} moves, {t_all:.1f} s"
+    line = {"metric": "pass-based search (Sec. IV, Fig. 3) moves/s on 1 GB300", "value": value, "unit": "moves/s",
+            "impl": "reference", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 (oracle)",
+            "data": "synthetic (seeded generators)",
+            "config": {"workload": args.workload, "method": "fm", "description": desc, "replicas": R,
+                       "restarts": restarts, "instances": len(insts)},
+            "cpu_baseline": {"value": value, "unit": "moves/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "moves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
 
 
 def ncu_traffic(workload, kernel):
