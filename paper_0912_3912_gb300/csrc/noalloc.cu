@@ -84,19 +84,29 @@ __global__ void noalloc_finish(int32_t replicas, int32_t nchunks, const double *
   E[r] = acc;
 }
 
-// Device address of the scratch array for the current device, looked up once
-// per device (with that device current) and cached.
-cudaError_t scratch_address(double **out) {
+// Device address of the scratch array for the current device.  Outside stream
+// capture it is looked up on every call (cudaGetSymbolAddress allocates
+// nothing), so a context that was torn down and recreated - cudaDeviceReset, or
+// the primary context released and retained again - never leaves a stale
+// address behind.  While `stream` is capturing, the address recorded by the
+// last uncaptured call on this device is used instead (a lookup there could
+// load the module, which capture forbids).
+cudaError_t scratch_address(cudaStream_t stream, double **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kNaMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(stream, &cap);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_na_mutex);
-  if (!g_na_ptr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_partials);
     if (e != cudaSuccess) return e;
     g_na_ptr[dev] = static_cast<double *>(p);
+  } else if (!g_na_ptr[dev]) {
+    return cudaErrorStreamCaptureUnsupported;
   }
   *out = g_na_ptr[dev];
   return cudaSuccess;
@@ -110,12 +120,13 @@ extern "C" ising_status ising_energy_noalloc(int32_t n, const int64_t *row_ptr_d
                                              const int8_t *spins_dev, int32_t replicas, double *energy_dev,
                                              cudaStream_t stream) {
   using namespace isg;
-  if (n < 1 || replicas < 1 || !row_ptr_dev || !spins_dev || !energy_dev) return ISING_ERR_INVALID_ARG;
+  if (n < 1 || replicas < 1 || !row_ptr_dev || !col_dev || !J_dev || !spins_dev || !energy_dev)
+    return ISING_ERR_INVALID_ARG;
   if (dtype != ISING_I8 && dtype != ISING_F32) return ISING_ERR_INVALID_ARG;
   const int64_t nchunks = (n + kNaChunk - 1) / kNaChunk;
   if (nchunks * (int64_t)replicas > (int64_t)ISING_NOALLOC_MAX_PARTIALS) return ISING_ERR_UNSUPPORTED;
   double *partials = nullptr;
-  if (scratch_address(&partials) != cudaSuccess) return ISING_ERR_CUDA;
+  if (scratch_address(stream, &partials) != cudaSuccess) return ISING_ERR_CUDA;
   const int blocks = (int)(nchunks * replicas);
   if (dtype == ISING_F32)
     noalloc_partial<true><<<blocks, kNaThreads, 0, stream>>>(n, row_ptr_dev, col_dev, J_dev, h_dev, spins_dev,

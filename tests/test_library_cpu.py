@@ -146,3 +146,18 @@ def test_create_rejects_bad_arguments(isg):
     d, keep = _desc(isg, base)
     d.n = 0
     assert _create_code(isg, d) == 1
+
+
+def test_noalloc_rejects_null_pointers_before_any_device_work(isg):
+    """ising_energy_noalloc checks its required pointers and sizes on the host
+    and returns ISING_ERR_INVALID_ARG without touching a device."""
+    L = isg.lib()
+    fake = C.c_void_p(0x1000)  # never dereferenced: every call below fails its checks first
+    args = dict(n=4, row_ptr=fake, col=fake, J=fake, h=None, dt=0, spins=fake, R=1, E=fake)
+    cases = [dict(col=None), dict(J=None), dict(row_ptr=None), dict(spins=None), dict(E=None),
+             dict(n=0), dict(R=0), dict(dt=7)]
+    for c in cases:
+        a = {**args, **c}
+        code = L.ising_energy_noalloc(a["n"], a["row_ptr"], a["col"], a["J"], a["h"], a["dt"], a["spins"], a["R"],
+                                      a["E"], None)
+        assert code == 1, (c, code)
