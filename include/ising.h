@@ -155,6 +155,16 @@ typedef struct {
   ising_dtype dtype;
 } ising_instance_desc;
 
+/* Variant of the dense family (ISING_KERNEL_DENSE_TC). */
+typedef enum {
+  ISING_DENSE_OWN = 0,     /* the library's own kernels (n <= 4096)                  */
+  ISING_DENSE_LIBRARY = 1  /* comparator: 128-spin block decisions with the block
+                              fields from cuBLAS BF16 GEMMs (hi+lo), any n            */
+} ising_dense_variant;
+
+/* Search parameters.  The last three fields choose between implementations of
+ * one family; none changes what a search computes beyond the rounding noted
+ * for the dense family.  Zero-initialised, they take the library's defaults.   */
 typedef struct {
   int32_t max_sweeps;    /* >= 1, cap on sweeps per descent                          */
   int32_t restarts;      /* >= 1, descents per replica                               */
@@ -163,6 +173,15 @@ typedef struct {
                             0 = only at the first sweep of a descent                 */
   ising_schedule schedule;
   ising_kernel kernel;
+  int32_t dense_variant;       /* ising_dense_variant (dense family only)            */
+  int32_t dense_tensor_sweeps; /* ISING_DENSE_OWN: sweeps of each descent decided on
+                                  tensor cores before the per-replica continuation;
+                                  0 = default (3), < 0 = none (identical results
+                                  up to the dense family's rounding)                 */
+  int32_t cluster_ctas;        /* multi-spin-coded periodic lattices: CTAs per
+                                  cluster; 0 = automatic, 1 = no clusters, 2/4/8 =
+                                  only that size where eligible, else none (same
+                                  results either way)                                */
 } ising_search_params;
 
 /* Work counters of one ising_local_search call, summed over all replicas:
@@ -217,34 +236,55 @@ ising_status ising_autotune(ising_handle *h, int32_t replicas, const ising_searc
  * point exists for callers that cannot allocate device memory - for example a
  * framework whose pool allocator owns the whole device, or code that must not
  * trigger the device-wide synchronisation a cudaMalloc implies - and so can
- * use neither ising_create nor ising_energy's on-demand scratch.  It computes
- * the same energies as ising_energy (pairs and fields of Eq. 1; no
- * hyper-edges) from the caller's own DEVICE buffers: row_ptr_dev int64 [n+1],
- * col_dev int32, J_dev (int8_t or float per dtype, symmetric CSR as for
- * ising_create, not re-validated here), h_dev [n] or NULL, spins_dev int8
- * [replicas][n]; energy_dev double [replicas] out.  It allocates nothing: its
+ * use neither ising_create nor ising_energy's on-demand scratch.  It returns
+ * the same energies as ising_energy for instances with pair couplings and
+ * fields only (no hyper-edges): minus the sum over each coupled pair, counted
+ * once, of J_ij s_i s_j, minus the sum of h_i s_i.  Inputs are the caller's own
+ * DEVICE buffers: row_ptr_dev int64 [n+1], col_dev int32 and J_dev (int8_t or
+ * float per dtype) [row_ptr[n]], a symmetric CSR as for ising_create that is
+ * not re-validated here (all three required: an instance without couplings
+ * still passes valid device pointers), h_dev [n] or NULL (no fields),
+ * spins_dev int8 [replicas][n]; energy_dev double [replicas] out.  All buffers
+ * and `stream` belong to the current device.  It allocates nothing: its
  * scratch is a fixed array of ISING_NOALLOC_MAX_PARTIALS doubles (512 KiB)
  * that every device loading the library holds until the process exits, so it
  * returns ISING_ERR_UNSUPPORTED when ceil(n / 4096) * replicas exceeds that
- * limit.  The first call on a device looks up that array's address (with the
- * device current) and should come before any stream capture on that device.
- * All calls share the array: calls that overlap on the GPU race and must be
- * ordered by the caller.                                                       */
+ * limit, and ISING_ERR_INVALID_ARG for a NULL required pointer or a size
+ * below 1.  Outside stream capture every call looks up that array's address
+ * on the current device, so a device reset or a recreated context does not
+ * invalidate it; a call made while `stream` is capturing reuses the address
+ * of the last uncaptured call on that device, so at least one uncaptured call
+ * on the device (and none since a reset) must come before any capture, else
+ * the call returns ISING_ERR_CUDA.  All calls share the array: calls that
+ * overlap on the GPU race and must be ordered by the caller.                   */
 #define ISING_NOALLOC_MAX_PARTIALS 65536
 ising_status ising_energy_noalloc(int32_t n, const int64_t *row_ptr_dev, const int32_t *col_dev,
                                   const void *J_dev, const void *h_dev, ising_dtype dtype,
                                   const int8_t *spins_dev, int32_t replicas, double *energy_dev,
                                   cudaStream_t stream);
 
+/* Parameters of the pass-based search. */
+typedef struct {
+  int32_t restarts;    /* >= 1, random starts per replica                          */
+  int32_t max_passes;  /* >= 0, cap on passes per start; 0 = no cap                */
+  int32_t starts;      /* 0 = automatic; 1 = a replica's starts one after another
+                          in one warp; 2 = one start per warp, the best chosen
+                          afterwards (same results either way)                    */
+  int32_t reg_kernel;  /* instances of at most 512 spins in the one-unit integer
+                          form: 0 = automatic (registers when the searches fit one
+                          wave), 1 = always the register-resident kernel, -1 =
+                          always the shared-memory kernel (same results)          */
+} ising_fm_params;
+
 /* The paper's pass-based search with hill climbing (Sec. IV, Fig. 3), for
  * instances of at most 4096 spins (else ISING_ERR_UNSUPPORTED).  Per replica,
- * `restarts` starts (Philox, counter layout as for ising_local_search, restart
- * index k = 0 .. restarts-1); from each start, passes: every spin moves once
+ * p->restarts starts (Philox, counter layout as for ising_local_search, restart
+ * index k = 0 .. p->restarts-1); from each start, passes: every spin moves once
  * per pass in best-gain order (largest -2 s_i f_i among the spins not yet
  * moved, ties to the lowest index; moves with negative gain included), the
  * pass is cut back to its earliest strictly lowest-energy prefix, and passes
  * repeat while one lowers the energy strictly (float couplings: by more than
- * 1e-9 (1 + |E|)); max_passes > 0 caps the passes per start (0: no cap).  Gains
+ * 1e-9 (1 + |E|)); p->max_passes > 0 caps the passes per start (0: no cap).  Gains
  * and energies are the FP64 values of that definition (fields summed as h,
  * then the CSR row in stored order, then the hyper-edges ascending); where FP64
  * is exact on an instance the kernels compute them in integers, with the same
@@ -257,9 +297,9 @@ ising_status ising_energy_noalloc(int32_t n, const int64_t *row_ptr_dev, const i
  * [instance][replica] passes summed over the starts, or NULL.  stats (nullable;
  * the call then waits): descents = starts, sweeps = passes, flips and
  * flip_evals = moves applied (n per pass), minima = 0.                        */
-ising_status ising_fm_search(ising_handle *h, const uint64_t *seeds, int32_t replicas, int32_t restarts,
-                             int32_t max_passes, int8_t *spins_dev, double *energy_dev, int32_t *passes_dev,
-                             ising_stats *stats, cudaStream_t stream);
+ising_status ising_fm_search(ising_handle *h, const uint64_t *seeds, int32_t replicas, const ising_fm_params *p,
+                             int8_t *spins_dev, double *energy_dev, int32_t *passes_dev, ising_stats *stats,
+                             cudaStream_t stream);
 
 /* Device timing of the kernels a search runs, for measurement.
  * ising_set_timing(h, 1) opens a timing window (clearing the previous one);

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libising_gb300.so")
 I8, F32 = 0, 1
 SCHED_COLOUR, SCHED_SEQUENTIAL = 0, 1
 KERNEL_AUTO, KERNEL_TILE, KERNEL_MSC, KERNEL_SWEEP, KERNEL_DENSE_TC, KERNEL_PLAIN = range(6)
+DENSE_OWN, DENSE_LIBRARY = 0, 1
 KERNEL_NAMES = {KERNEL_AUTO: "auto", KERNEL_TILE: "tile", KERNEL_MSC: "msc", KERNEL_SWEEP: "sweep",
                 KERNEL_DENSE_TC: "dense_tc", KERNEL_PLAIN: "plain"}
 
@@ -44,7 +45,13 @@ class _Desc(C.Structure):
 
 class _Params(C.Structure):
     _fields_ = [("max_sweeps", C.c_int32), ("restarts", C.c_int32), ("sweep_budget", C.c_int32),
-                ("refresh_every", C.c_int32), ("schedule", C.c_int32), ("kernel", C.c_int32)]
+                ("refresh_every", C.c_int32), ("schedule", C.c_int32), ("kernel", C.c_int32),
+                ("dense_variant", C.c_int32), ("dense_tensor_sweeps", C.c_int32), ("cluster_ctas", C.c_int32)]
+
+
+class _FmParams(C.Structure):
+    _fields_ = [("restarts", C.c_int32), ("max_passes", C.c_int32), ("starts", C.c_int32),
+                ("reg_kernel", C.c_int32)]
 
 
 class _Stats(C.Structure):
@@ -84,7 +91,7 @@ def lib():
             L.ising_destroy.restype = i32
             L.ising_energy_noalloc.argtypes = [i32, vp, vp, vp, vp, i32, vp, i32, vp, vp]
             L.ising_energy_noalloc.restype = i32
-            L.ising_fm_search.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
+            L.ising_fm_search.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp]
             L.ising_fm_search.restype = i32
             L.ising_set_timing.argtypes = [vp, i32]
             L.ising_set_timing.restype = i32
@@ -168,8 +175,10 @@ class Handle:
 
     @staticmethod
     def params(max_sweeps=1000, restarts=1, sweep_budget=0, refresh_every=16,
-               schedule=SCHED_COLOUR, kernel=KERNEL_AUTO):
-        return _Params(max_sweeps, restarts, sweep_budget, refresh_every, schedule, kernel)
+               schedule=SCHED_COLOUR, kernel=KERNEL_AUTO, dense_variant=DENSE_OWN, dense_tensor_sweeps=0,
+               cluster_ctas=0):
+        return _Params(max_sweeps, restarts, sweep_budget, refresh_every, schedule, kernel, dense_variant,
+                       dense_tensor_sweeps, cluster_ctas)
 
     @property
     def total_spins(self):
@@ -189,11 +198,13 @@ class Handle:
         return (E, E32) if want_i32 else E
 
     def local_search(self, seeds, replicas: int, *, max_sweeps=1000, restarts=1, sweep_budget=0,
-                     refresh_every=16, schedule=SCHED_COLOUR, kernel=KERNEL_AUTO, stream=None,
-                     stats=True, want_i32=False, out=None) -> SearchResult:
+                     refresh_every=16, schedule=SCHED_COLOUR, kernel=KERNEL_AUTO, dense_variant=DENSE_OWN,
+                     dense_tensor_sweeps=0, cluster_ctas=0, stream=None, stats=True, want_i32=False,
+                     out=None) -> SearchResult:
         torch = self._torch
         seeds = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64).reshape(self.n_inst))
-        p = self.params(max_sweeps, restarts, sweep_budget, refresh_every, schedule, kernel)
+        p = self.params(max_sweeps, restarts, sweep_budget, refresh_every, schedule, kernel, dense_variant,
+                        dense_tensor_sweeps, cluster_ctas)
         if out is None:
             spins = torch.empty(replicas * self.total_spins, dtype=torch.int8, device=self.device)
             E = torch.empty((self.n_inst, replicas), dtype=torch.float64, device=self.device)
@@ -213,7 +224,8 @@ class Handle:
             sd = {k: int(getattr(st, k)) for k, _ in _Stats._fields_}
         return SearchResult(spins, E, E32, minima, sd)
 
-    def fm_search(self, seeds, replicas: int, *, restarts=1, max_passes=0, stream=None, stats=True):
+    def fm_search(self, seeds, replicas: int, *, restarts=1, max_passes=0, starts=0, reg_kernel=0, stream=None,
+                  stats=True):
         """The paper's pass-based search with hill climbing (ising_fm_search).
         Returns (spins [total], energy [instances, replicas], passes, stats)."""
         torch = self._torch
@@ -222,8 +234,9 @@ class Handle:
         E = torch.empty((self.n_inst, replicas), dtype=torch.float64, device=self.device)
         passes = torch.empty((self.n_inst, replicas), dtype=torch.int32, device=self.device)
         st = _Stats()
+        fp = _FmParams(restarts, max_passes, starts, reg_kernel)
         _check(lib().ising_fm_search(
-            self._h, C.c_void_p(seeds.ctypes.data), replicas, restarts, max_passes, C.c_void_p(spins.data_ptr()),
+            self._h, C.c_void_p(seeds.ctypes.data), replicas, C.byref(fp), C.c_void_p(spins.data_ptr()),
             C.c_void_p(E.data_ptr()), C.c_void_p(passes.data_ptr()), C.byref(st) if stats else None,
             self._stream(stream)), "ising_fm_search")
         sd = {k: int(getattr(st, k)) for k, _ in _Stats._fields_} if stats else None
@@ -276,17 +289,23 @@ def energy_noalloc(row_ptr, col, J, h, spins, replicas: int, energy, stream=None
     """ising_energy_noalloc on caller-owned device tensors (argument marshalling only).
 
     row_ptr int64 [n+1], col int32, J int8/float32, h (same dtype) or None,
-    spins int8 [replicas, n], energy float64 [replicas] (written).  Returns the
-    status code (0 = ok).
+    spins int8 [replicas, n], energy float64 [replicas] (written), all on one
+    CUDA device, which is made current for the call.  Returns the status code
+    (0 = ok).
     """
     import torch
+    dev = spins.device
+    for t in (row_ptr, col, J, h, energy):
+        if t is not None and t.device != dev:
+            raise ValueError(f"energy_noalloc: every tensor must be on {dev}, got one on {t.device}")
     n = row_ptr.numel() - 1
     dt = I8 if J.dtype == torch.int8 else F32
-    s = stream if stream is not None else torch.cuda.current_stream(spins.device)
-    return lib().ising_energy_noalloc(
-        n, C.c_void_p(row_ptr.data_ptr()), C.c_void_p(col.data_ptr()), C.c_void_p(J.data_ptr()),
-        None if h is None else C.c_void_p(h.data_ptr()), dt, C.c_void_p(spins.data_ptr()), replicas,
-        C.c_void_p(energy.data_ptr()), C.c_void_p(s.cuda_stream))
+    with torch.cuda.device(dev):
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        return lib().ising_energy_noalloc(
+            n, C.c_void_p(row_ptr.data_ptr()), C.c_void_p(col.data_ptr()), C.c_void_p(J.data_ptr()),
+            None if h is None else C.c_void_p(h.data_ptr()), dt, C.c_void_p(spins.data_ptr()), replicas,
+            C.c_void_p(energy.data_ptr()), C.c_void_p(s.cuda_stream))
 
 
 def status_string(code: int) -> str:

@@ -13,13 +13,6 @@
 #include "internal.h"
 
 namespace isg {
-std::mutex &state_mutex() {
-  static std::mutex m;
-  return m;
-}
-}  // namespace isg
-
-namespace isg {
 cudaError_t launch_plain(ising_handle *h, const ising_search_params *p, int32_t R, int8_t *spins, double *E,
                          int32_t *E32, int32_t *minima, const uint64_t *seeds_host, cudaStream_t s);
 cudaError_t launch_sweep(ising_handle *h, const ising_search_params *p, int32_t R, int8_t *spins, double *E,
@@ -369,6 +362,9 @@ ising_status validate_params(const ising_search_params *p) {
     return ISING_ERR_INVALID_ARG;
   if (p->schedule != ISING_SCHED_COLOUR && p->schedule != ISING_SCHED_SEQUENTIAL) return ISING_ERR_INVALID_ARG;
   if (p->kernel < ISING_KERNEL_AUTO || p->kernel > ISING_KERNEL_PLAIN) return ISING_ERR_INVALID_ARG;
+  if (p->dense_variant != ISING_DENSE_OWN && p->dense_variant != ISING_DENSE_LIBRARY) return ISING_ERR_INVALID_ARG;
+  if (p->cluster_ctas < 0 || p->cluster_ctas > 8 || (p->cluster_ctas & (p->cluster_ctas - 1)))
+    return ISING_ERR_INVALID_ARG;
   return ISING_OK;
 }
 
@@ -406,11 +402,10 @@ int32_t resolve_kernel(ising_handle *h, int32_t R, const ising_search_params *p)
 // power-of-two chunks of at least 1024 sites (whole Philox blocks).
 int msc_cluster_size(const ising_handle *h, int32_t R, const ising_search_params *p) {
   if (!h->msc_ok || !h->all_lattice || !h->lat_parity || p->schedule != ISING_SCHED_COLOUR) return 0;
-  if (getenv("ISING_NO_CLUSTER")) return 0;
+  if (p->cluster_ctas == 1) return 0;
   const int64_t tiles = (int64_t)h->n_inst * ((R + 31) / 32);
-  const char *force = getenv("ISING_CLUSTER_P");  // diagnostics: restrict to one cluster size
   for (int P : {8, 4, 2}) {
-    if (force && atoi(force) != P) continue;
+    if (p->cluster_ctas > 1 && p->cluster_ctas != P) continue;  // restricted to one size
     if (tiles * P > 2 * (int64_t)h->sm_count) continue;
     bool ok = true;
     int d = -1;
@@ -1068,11 +1063,12 @@ ising_status ising_destroy(ising_handle *h) {
   return ISING_OK;
 }
 
-ising_status ising_fm_search(ising_handle *h, const uint64_t *seeds, int32_t replicas, int32_t restarts,
-                             int32_t max_passes, int8_t *spins_dev, double *energy_dev, int32_t *passes_dev,
-                             ising_stats *stats, cudaStream_t stream) {
+ising_status ising_fm_search(ising_handle *h, const uint64_t *seeds, int32_t replicas, const ising_fm_params *p,
+                             int8_t *spins_dev, double *energy_dev, int32_t *passes_dev, ising_stats *stats,
+                             cudaStream_t stream) {
   const NvtxRange nvtx_range("ising_fm_search");
-  if (!h || !seeds || replicas < 1 || restarts < 1 || max_passes < 0 || !spins_dev || !energy_dev)
+  if (!h || !seeds || !p || replicas < 1 || p->restarts < 1 || p->max_passes < 0 || p->starts < 0 ||
+      p->starts > 2 || p->reg_kernel < -1 || p->reg_kernel > 1 || !spins_dev || !energy_dev)
     return ISING_ERR_INVALID_ARG;
   if (h->latched != ISING_OK) {
     ising_status l = h->latched;
@@ -1094,7 +1090,7 @@ ising_status ising_fm_search(ising_handle *h, const uint64_t *seeds, int32_t rep
     st = ISING_ERR_CUDA;
   } else {
     kt_begin(h, "fm_kernel", stream);
-    if (launch_fm(h, replicas, restarts, max_passes, spins_dev, energy_dev, passes_dev, stream) != cudaSuccess)
+    if (launch_fm(h, replicas, p, spins_dev, energy_dev, passes_dev, stream) != cudaSuccess)
       st = ISING_ERR_CUDA;
     kt_end(h, stream);
   }

@@ -294,7 +294,7 @@ __global__ void dense_tc_output(int32_t n, int32_t np, int32_t R, const __nv_bfl
   }
 }
 
-struct DenseState {
+struct DenseState : FamilyState {
   cublasHandle_t cublas = nullptr;
   void *workspace = nullptr;
   int32_t n = 0, Rp = 0;
@@ -316,10 +316,6 @@ struct DenseState {
   float *Sx = nullptr, *Fx = nullptr;  // [R][n] returned spins and their FP32 fields
 };
 
-std::map<const ising_handle *, DenseState> &dense_states() {
-  static std::map<const ising_handle *, DenseState> m;
-  return m;
-}
 
 void free_state(DenseState &D) {
   cudaFree(D.hi);
@@ -411,18 +407,15 @@ bool dense_supported(const ising_handle *h, int32_t R) {
 }
 
 void dense_free(ising_handle *h) {
-  std::lock_guard<std::mutex> guard(state_mutex());
-  auto &m = dense_states();
-  auto it = m.find(h);
-  if (it == m.end()) return;
-  free_state(it->second);
-  m.erase(it);
+  if (!h->dense_st) return;
+  free_state(static_cast<DenseState &>(*h->dense_st));
+  h->dense_st.reset();
 }
 
 cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t R, int8_t *spins, double *E,
                          int32_t *E32, int32_t *minima, const uint64_t *seeds_host, cudaStream_t s) {
   (void)E32;
-  DenseState &D = locked_slot(dense_states(), h);
+  DenseState &D = family_state<DenseState>(h->dense_st);
   cudaError_t e;
   const int Rp = (R + 7) / 8 * 8;
   int64_t joff = 0;
@@ -456,9 +449,9 @@ cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t 
     if (cublasSetStream(D.cublas, s) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
     const float *J = h->d_Jdense + joff;
     const uint64_t seed = seeds_host[b];
-    const char *force_lib = std::getenv("ISING_DENSE_CUBLAS");
+
     const float *hf = reinterpret_cast<const float *>(h->d_h) + h->inst[b].spin_off;
-    if (dense_tc_eligible(n) && !(force_lib && force_lib[0] == '1')) {
+    if (dense_tc_eligible(n) && p->dense_variant != ISING_DENSE_LIBRARY) {
       // Rounds of: the first sweeps of every replica's descent on tensor cores
       // (hand-written tcgen05 kernel), then each replica on its own until its
       // descent ends (incremental updates, CUDA cores), then the round's
@@ -488,8 +481,7 @@ cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t 
       }
       // [R][np] FP32: exported fields here, returned-energy GEMM operands afterwards
       if ((e = ensure_fx(D, (int64_t)std::max(D.Rp, R) * np)) != cudaSuccess) return e;
-      int sweeps_a = kTcSweepsA;
-      if (const char *v = std::getenv("ISING_DENSE_TC_SWEEPS")) sweeps_a = std::max(0, std::atoi(v));
+      const int sweeps_a = p->dense_tensor_sweeps == 0 ? kTcSweepsA : std::max(0, p->dense_tensor_sweeps);
       if ((e = cudaMemsetAsync(D.err, 0, 4, s)) != cudaSuccess) return e;
       const int rb = (R + 255) / 256, wb = (R * 32 + 255) / 256;
       dense_init<<<rb, 256, 0, s>>>(R, D.rep, h->d_stats);

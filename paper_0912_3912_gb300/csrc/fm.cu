@@ -800,7 +800,7 @@ __global__ void fm_best_start_kernel(const InstDesc *inst, int32_t n_inst, int32
 
 // device buffers per handle, kept across calls: the (instance, replica)
 // list, the work-queue counters and, for split starts, every start's result
-struct FmBufs {
+struct FmBufs : FamilyState {
   int2 *items = nullptr;
   size_t items_bytes = 0;
   int32_t *queues = nullptr;
@@ -812,10 +812,6 @@ struct FmBufs {
   std::vector<cudaEvent_t> join;
   cudaEvent_t fork = nullptr;
 };
-std::map<const ising_handle *, FmBufs> &fm_bufs() {
-  static std::map<const ising_handle *, FmBufs> m;
-  return m;
-}
 
 template <typename P>
 cudaError_t grow(P *&p, size_t &have, size_t need) {
@@ -911,17 +907,6 @@ cudaError_t fm_reg_shape(const ising_handle *h, int &warps, size_t &smem, int &p
   return cudaSuccess;
 }
 
-// ISING_FM_REG=0 keeps small instances on fm_kernel, =1 puts them on the
-// register kernel whatever their number (both give the same results)
-bool fm_reg_off() {
-  const char *v = std::getenv("ISING_FM_REG");
-  return v && *v && std::atoi(v) == 0;
-}
-bool fm_reg_forced() {
-  const char *v = std::getenv("ISING_FM_REG");
-  return v && *v && std::atoi(v) == 1;
-}
-
 }  // namespace
 
 int fm_max_spins() { return kFmMaxSpins; }
@@ -929,11 +914,12 @@ int fm_max_spins() { return kFmMaxSpins; }
 // Launches over every (instance, replica): one per group of instances of like
 // arithmetic and size, plus a selection launch when the starts run in
 // parallel.  seeds: device [instances].
-cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_passes, int8_t *spins, double *E,
+cudaError_t launch_fm(ising_handle *h, int32_t R, const ising_fm_params *fp, int8_t *spins, double *E,
                       int32_t *passes, cudaStream_t s) {
+  const int32_t restarts = fp->restarts, max_passes = fp->max_passes;
   const int64_t n_items = (int64_t)h->n_inst * R;
   if (n_items > 0x7fffffff) return cudaErrorInvalidValue;
-  FmBufs &B = locked_slot(fm_bufs(), h);
+  FmBufs &B = family_state<FmBufs>(h->fm_st);
   cudaError_t e;
   // groups: one-unit integer instances, per-spin-unit ones, then FP64;
   // within each, size classes (0, 256], (256, 512], ... (2048, 4096],
@@ -981,9 +967,8 @@ cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_
   const size_t sp_bytes = ((size_t)R * restarts * h->total_spins + 15) & ~(size_t)15;
   const size_t e_bytes = (size_t)n_items * restarts * sizeof(double);
   const size_t p_bytes = (size_t)n_items * restarts * sizeof(int32_t);
-  // ISING_FM_SPLIT=0 / 1 overrides the choice (both give the same results).
-  const char *force = std::getenv("ISING_FM_SPLIT");
-  const bool want = force && *force ? std::atoi(force) != 0 : n_items < 4 * resident;
+  // fp->starts overrides the choice (both give the same results).
+  const bool want = fp->starts ? fp->starts == 2 : n_items < 4 * resident;
   const bool split = want && restarts > 1 && (int64_t)n_items * restarts <= 0x7fffffff &&
                      sp_bytes + e_bytes + p_bytes <= kSplitScratchMax;
   int8_t *sp_k = nullptr;
@@ -1028,13 +1013,13 @@ cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_
     // shared-memory kernel, which holds more searches per SM.
     const int64_t work = split ? P.count * restarts : P.count;
     const bool reg8 = nmax <= 256;
-    bool reg = P.mode == kFx && nmax <= kRegMaxSpins && !fm_reg_off();
+    bool reg = P.mode == kFx && nmax <= kRegMaxSpins && fp->reg_kernel >= 0;
     if (reg) {
       le = fl ? (reg8 ? fm_reg_shape<true, 8>(h, warps, smem, per_sm) : fm_reg_shape<true, 16>(h, warps, smem, per_sm))
               : (reg8 ? fm_reg_shape<false, 8>(h, warps, smem, per_sm)
                       : fm_reg_shape<false, 16>(h, warps, smem, per_sm));
       if (le != cudaSuccess) break;
-      reg = work <= (int64_t)h->sm_count * per_sm * warps || fm_reg_forced();
+      reg = work <= (int64_t)h->sm_count * per_sm * warps || fp->reg_kernel == 1;
     }
     // int8 couplings are always exact in one unit (mode kFx)
     if (!reg)
@@ -1094,17 +1079,15 @@ cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_
 }
 
 void fm_free(ising_handle *h) {
-  std::lock_guard<std::mutex> guard(state_mutex());
-  auto &m = fm_bufs();
-  auto it = m.find(h);
-  if (it == m.end()) return;
-  cudaFree(it->second.items);
-  cudaFree(it->second.queues);
-  cudaFree(it->second.scratch);
-  for (cudaStream_t st : it->second.side) cudaStreamDestroy(st);
-  for (cudaEvent_t ev : it->second.join) cudaEventDestroy(ev);
-  if (it->second.fork) cudaEventDestroy(it->second.fork);
-  m.erase(it);
+  if (!h->fm_st) return;
+  FmBufs &B = static_cast<FmBufs &>(*h->fm_st);
+  cudaFree(B.items);
+  cudaFree(B.queues);
+  cudaFree(B.scratch);
+  for (cudaStream_t st : B.side) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : B.join) cudaEventDestroy(ev);
+  if (B.fork) cudaEventDestroy(B.fork);
+  h->fm_st.reset();
 }
 
 }  // namespace isg

@@ -6,6 +6,7 @@
 
 #include <cstdint>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <tuple>
@@ -94,6 +95,13 @@ struct TileArgs {
   unsigned long long *stats;  // [5] accumulated work counters
 };
 
+// Per-handle state of one launcher family (device buffers, graphs, streams
+// kept across calls).  The handle owns one per family that has run on it; the
+// family's *_free function releases its resources at ising_destroy.
+struct FamilyState {
+  virtual ~FamilyState() = default;
+};
+
 struct PlanKey {
   int32_t R, kernel, schedule;
   bool operator<(const PlanKey &o) const {
@@ -174,19 +182,19 @@ struct ising_handle {
   bool timing = false;
   std::vector<KTimer> ktimers;
   size_t kt_used = 0;
+  // launcher state, created by each family's first call on this handle
+  std::unique_ptr<isg::FamilyState> dense_st, fm_st, plain_st, sweep_st;
   isg::DevGraph graph() const;
 };
 
 namespace isg {
-// Per-handle state of the launchers lives in maps keyed by handle; one mutex
-// guards their insertions and erasures, so that calls on different handles
-// may run on different threads (a handle's own state is used by one call at
-// a time; references into a std::map survive other keys' insertion and erasure).
-std::mutex &state_mutex();
-template <typename Map>
-typename Map::mapped_type &locked_slot(Map &m, const ising_handle *h) {
-  std::lock_guard<std::mutex> g(state_mutex());
-  return m[h];
+// The launcher state of type T held in `slot` of a handle, created on first
+// use.  Calls on one handle do not overlap (the ABI's rule), so no lock is
+// needed; different handles share nothing.
+template <typename T>
+T &family_state(std::unique_ptr<FamilyState> &slot) {
+  if (!slot) slot.reset(new T());
+  return static_cast<T &>(*slot);
 }
 // device timing around a launch (no-ops unless timing is on); name: a static string
 void kt_begin(ising_handle *h, const char *name, cudaStream_t s);
@@ -203,7 +211,7 @@ size_t msc_cluster_smem(int csz);
 cudaError_t launch_msc_cluster(ising_handle *h, int n_tiles, int P, int csz_max, int D, cudaStream_t s);
 // the pass-based search (fm.cu)
 int fm_max_spins();
-cudaError_t launch_fm(ising_handle *h, int32_t R, int32_t restarts, int32_t max_passes, int8_t *spins, double *E,
+cudaError_t launch_fm(ising_handle *h, int32_t R, const ising_fm_params *p, int8_t *spins, double *E,
                       int32_t *passes, cudaStream_t s);
 void fm_free(ising_handle *h);
 int msc_cluster_max_active(ising_handle *h, int n_tiles, int P, int csz_max, int D);

@@ -241,7 +241,7 @@ __global__ void plain_reset(PlainRep *rep, int32_t R) {
   rep[r] = p;
 }
 
-struct PlainState {
+struct PlainState : FamilyState {
   size_t cap_elems = 0;
   int32_t cap_R = 0;
   int8_t *s = nullptr, *best = nullptr;
@@ -251,19 +251,12 @@ struct PlainState {
   int32_t *done = nullptr, *h_done = nullptr;
 };
 
-std::map<const ising_handle *, PlainState> &plain_states() {
-  static std::map<const ising_handle *, PlainState> m;
-  return m;
-}
 
 }  // namespace
 
 void plain_free(ising_handle *h) {
-  std::lock_guard<std::mutex> guard(state_mutex());
-  auto &m = plain_states();
-  auto it = m.find(h);
-  if (it == m.end()) return;
-  PlainState &P = it->second;
+  if (!h->plain_st) return;
+  PlainState &P = static_cast<PlainState &>(*h->plain_st);
   cudaFree(P.s);
   cudaFree(P.best);
   cudaFree(P.fm);
@@ -271,13 +264,13 @@ void plain_free(ising_handle *h) {
   cudaFree(P.rep);
   cudaFree(P.done);
   if (P.h_done) cudaFreeHost(P.h_done);
-  m.erase(it);
+  h->plain_st.reset();
 }
 
 // Runs the whole search for every instance, one instance after another.
 cudaError_t launch_plain(ising_handle *h, const ising_search_params *p, int32_t R, int8_t *spins, double *E,
                               int32_t *E32, int32_t *minima, const uint64_t *seeds_host, cudaStream_t s) {
-  PlainState &P = locked_slot(plain_states(), h);
+  PlainState &P = family_state<PlainState>(h->plain_st);
   const size_t need = (size_t)R * h->nmax;
   cudaError_t e;
   if (need > P.cap_elems || R > P.cap_R) {

@@ -1122,7 +1122,7 @@ struct SweepGraph {
   cudaGraphExec_t exec = nullptr;
 };
 
-struct SweepState {
+struct SweepState : FamilyState {
   size_t bytes = 0;
   void *mem = nullptr;
   int32_t *h_done = nullptr;
@@ -1130,10 +1130,6 @@ struct SweepState {
   std::map<std::string, SweepGraph> graphs;  // instantiated sweep chunks by configuration
 };
 
-std::map<const ising_handle *, SweepState> &sweep_states() {
-  static std::map<const ising_handle *, SweepState> m;
-  return m;
-}
 
 // ISING_SWEEP_DEBUG=1: launch without graphs, synchronise and report after
 // every launch (diagnostics only).
@@ -1206,7 +1202,7 @@ cudaError_t preload(int mode) {
 
 template <int LPS, bool LAT>
 cudaError_t run_instance(ising_handle *h, SweepArgs A, int mode, cudaStream_t s) {
-  SweepState &S = locked_slot(sweep_states(), h);
+  SweepState &S = family_state<SweepState>(h->sweep_st);
   const InstDesc &I = A.I;
   const int ncls = A.sequential ? I.n : I.ncls;
   int maxcls = 1;
@@ -1317,24 +1313,22 @@ cudaError_t run_instance(ising_handle *h, SweepArgs A, int mode, cudaStream_t s)
 }  // namespace
 
 void sweep_free(ising_handle *h) {
-  std::lock_guard<std::mutex> guard(state_mutex());
-  auto &m = sweep_states();
-  auto it = m.find(h);
-  if (it == m.end()) return;
-  for (auto &kv : it->second.graphs) {
+  if (!h->sweep_st) return;
+  SweepState &S = static_cast<SweepState &>(*h->sweep_st);
+  for (auto &kv : S.graphs) {
     cudaGraphExecDestroy(kv.second.exec);
     cudaGraphDestroy(kv.second.graph);
   }
-  cudaFree(it->second.mem);
-  if (it->second.h_done) cudaFreeHost(it->second.h_done);
-  for (auto &e : it->second.ev)
+  cudaFree(S.mem);
+  if (S.h_done) cudaFreeHost(S.h_done);
+  for (auto &e : S.ev)
     if (e) cudaEventDestroy(e);
-  m.erase(it);
+  h->sweep_st.reset();
 }
 
 cudaError_t launch_sweep(ising_handle *h, const ising_search_params *p, int32_t R, int8_t *spins, double *E,
                          int32_t *E32, int32_t *minima, const uint64_t *seeds_host, cudaStream_t s) {
-  SweepState &S = locked_slot(sweep_states(), h);
+  SweepState &S = family_state<SweepState>(h->sweep_st);
   const int LPS = R > 16 ? 32 : (R > 8 ? 16 : 8);
   const int G = (R + 31) / 32;
   if (LPS < 32 && R > LPS) return cudaErrorInvalidValue;

@@ -124,16 +124,15 @@ def test_fm_rejects_instances_beyond_its_size():
 
 
 @pytest.mark.parametrize("dtype", ["i8", "f32"])
-def test_fm_parallel_and_sequential_starts_agree(monkeypatch, dtype):
+def test_fm_parallel_and_sequential_starts_agree(dtype):
     """Starts run one per warp (the best chosen by a second launch) or one
     after another in a warp: identical spins, energies and pass counts."""
     insts = [W.random_graph(n, 4.0, 90 + n, dtype=dtype, n_hyper=n // 25, hyper_order=(3,)) for n in (64, 333, 1500)]
     seeds = [11, 12, 13]
     out = {}
     for mode in ("0", "1"):
-        monkeypatch.setenv("ISING_FM_SPLIT", mode)
         h = isg.Handle(insts)
-        sp, E, P, st = h.fm_search(seeds, 24, restarts=4)
+        sp, E, P, st = h.fm_search(seeds, 24, restarts=4, starts=1 if mode == "0" else 2)
         torch.cuda.synchronize()
         out[mode] = (sp.cpu().numpy(), E.cpu().numpy(), P.cpu().numpy(), st["descents"], st["sweeps"])
         h.close()
@@ -225,10 +224,10 @@ def test_two_handles_on_two_threads():
 
 
 @pytest.mark.parametrize("dtype", ["i8", "f32"])
-def test_fm_register_kernel_matches_shared_memory_kernel(monkeypatch, dtype):
+def test_fm_register_kernel_matches_shared_memory_kernel(dtype):
     """Instances of up to 512 spins in the one-unit integer form run on the
-    register-resident kernel (8 or 16 spins per lane; ISING_FM_REG=1 whatever
-    the number of searches); ISING_FM_REG=0 keeps them on the shared-memory
+    register-resident kernel (8 or 16 spins per lane; reg_kernel=1 whatever
+    the number of searches); reg_kernel=-1 keeps them on the shared-memory
     kernel.  Identical spins, energies and pass counts, including a dense
     instance (rows longer than a warp) and a hyper-edge with 40 members."""
     insts = [W.random_graph(n, 4.0, 110 + n, dtype=dtype, n_hyper=n // 20, hyper_order=(3, 4))
@@ -242,9 +241,8 @@ def test_fm_register_kernel_matches_shared_memory_kernel(monkeypatch, dtype):
     seeds = [31 + b for b in range(len(insts))]
     out = {}
     for mode in ("0", "1"):
-        monkeypatch.setenv("ISING_FM_REG", mode)
         h = isg.Handle(insts)
-        sp, E, P, st = h.fm_search(seeds, 12, restarts=3)
+        sp, E, P, st = h.fm_search(seeds, 12, restarts=3, reg_kernel=-1 if mode == "0" else 1)
         torch.cuda.synchronize()
         out[mode] = (sp.cpu().numpy(), E.cpu().numpy(), P.cpu().numpy(), st["sweeps"])
         h.close()

@@ -285,7 +285,7 @@ def test_dense_sk_tensor_core_path():
 
 
 @pytest.mark.parametrize("n,R", [(512, 96), (768, 256)])
-def test_dense_sk_tcgen05_kernel(n, R, monkeypatch):
+def test_dense_sk_tcgen05_kernel(n, R):
     """The hand-written tcgen05 kernel (n a multiple of 256): energies of the
     returned states within 1e-6 of the FP64 oracle, 1-flip minima within the
     field error bound, and the same results as the library-GEMM comparator on
@@ -305,8 +305,7 @@ def test_dense_sk_tcgen05_kernel(n, R, monkeypatch):
         f = oracle.local_fields(oi, sp[r])
         assert np.all(sp[r] * f >= -1e-4)
     assert st["minima"] == 2 * R and st["descents"] == 2 * R
-    monkeypatch.setenv("ISING_DENSE_CUBLAS", "1")
-    ref = h.local_search([29], R, max_sweeps=500, restarts=2, kernel=isg.KERNEL_DENSE_TC)
+    ref = h.local_search([29], R, max_sweeps=500, restarts=2, kernel=isg.KERNEL_DENSE_TC, dense_variant=isg.DENSE_LIBRARY)
     torch.cuda.synchronize()
     sp2 = ref.spins.view(R, n).cpu().numpy()
     same = np.mean(np.all(sp == sp2, axis=1))
@@ -336,24 +335,23 @@ def _sk_with_fields(n, seed, scale=0.3):
 
 
 @pytest.mark.parametrize("sweeps_a", ["0", "2", "1000"])
-def test_dense_tc_phases_and_fields(sweeps_a, monkeypatch):
+def test_dense_tc_phases_and_fields(sweeps_a):
     """The tensor-core path with its first-sweeps/continuation split moved
     (0: fields exported at once and every sweep continued per replica; 1000:
     every sweep on tensor cores), on an instance with fields h and a replica
     count that leaves a partial 128-replica cluster: energies of the returned
     states, 1-flip minima, work counters, and agreement with the comparator."""
-    monkeypatch.setenv("ISING_DENSE_TC_SWEEPS", sweeps_a)
+    ts = int(sweeps_a) if int(sweeps_a) > 0 else -1
     inst = _sk_with_fields(512, 77)
     R = 160
     h = isg.Handle([inst])
-    res = h.local_search([31], R, max_sweeps=500, restarts=3, kernel=isg.KERNEL_DENSE_TC)
+    res = h.local_search([31], R, max_sweeps=500, restarts=3, kernel=isg.KERNEL_DENSE_TC, dense_tensor_sweeps=ts)
     torch.cuda.synchronize()
     sp, E, m = _dense_checks(inst, res, R)
     st = dict(res.stats)
     assert st["minima"] == 3 * R and st["descents"] == 3 * R and np.all(m == 3)
     assert st["flip_evals"] == st["sweeps"] * inst.n
-    monkeypatch.setenv("ISING_DENSE_CUBLAS", "1")
-    ref = h.local_search([31], R, max_sweeps=500, restarts=3, kernel=isg.KERNEL_DENSE_TC)
+    ref = h.local_search([31], R, max_sweeps=500, restarts=3, kernel=isg.KERNEL_DENSE_TC, dense_variant=isg.DENSE_LIBRARY)
     torch.cuda.synchronize()
     sp2 = ref.spins.view(R, inst.n).cpu().numpy()
     assert np.mean(np.all(sp == sp2, axis=1)) >= 0.8
@@ -362,7 +360,7 @@ def test_dense_tc_phases_and_fields(sweeps_a, monkeypatch):
 
 
 @pytest.mark.parametrize("n", [1, 37, 300, 1000])
-def test_dense_tc_padded_sizes(n, monkeypatch):
+def test_dense_tc_padded_sizes(n):
     """Sizes that are not a multiple of 256 run zero-padded on the hand-written
     kernels: energies of the returned states, 1-flip minima, exact work
     counters (the instance's own spins), and agreement with the comparator."""
@@ -376,8 +374,7 @@ def test_dense_tc_padded_sizes(n, monkeypatch):
     st = dict(res.stats)
     assert st["minima"] == 2 * R and st["descents"] == 2 * R and np.all(m == 2)
     assert st["flip_evals"] == st["sweeps"] * n
-    monkeypatch.setenv("ISING_DENSE_CUBLAS", "1")
-    ref = h.local_search([11], R, max_sweeps=500, restarts=2, kernel=isg.KERNEL_DENSE_TC)
+    ref = h.local_search([11], R, max_sweeps=500, restarts=2, kernel=isg.KERNEL_DENSE_TC, dense_variant=isg.DENSE_LIBRARY)
     torch.cuda.synchronize()
     sp2 = ref.spins.view(R, n).cpu().numpy()
     assert np.mean(np.all(sp == sp2, axis=1)) >= 0.8
@@ -412,23 +409,25 @@ def test_dense_batch_of_instances():
 
 
 @pytest.mark.parametrize("sweeps_a", ["0", "4"])
-def test_dense_tc_sweep_cap_and_budget(sweeps_a, monkeypatch):
+def test_dense_tc_sweep_cap_and_budget(sweeps_a):
     """Descents cut by the sweep cap (inside and after the tensor-core sweeps)
     return their final states, counted as no minimum; a sweep budget ends every
     replica after exactly that many sweeps over its restarts."""
-    monkeypatch.setenv("ISING_DENSE_TC_SWEEPS", sweeps_a)
+    ts = int(sweeps_a) if int(sweeps_a) > 0 else -1
     inst = _sk_with_fields(256, 78, scale=0.1)
     R = 64
     h = isg.Handle([inst])
     for cap in (1, 3, 6):
-        res = h.local_search([5], R, max_sweeps=cap, restarts=2, kernel=isg.KERNEL_DENSE_TC)
+        res = h.local_search([5], R, max_sweeps=cap, restarts=2, kernel=isg.KERNEL_DENSE_TC,
+                             dense_tensor_sweeps=ts)
         torch.cuda.synchronize()
         sp, E, m = _dense_checks(inst, res, R)
         st = dict(res.stats)
         assert st["sweeps"] <= 2 * cap * R and st["descents"] == 2 * R
         if cap == 1:  # one sweep from a random start never ends at a minimum
             assert st["minima"] == 0 and np.all(m == 0) and st["sweeps"] == 2 * R
-    res = h.local_search([6], R, max_sweeps=1000, restarts=1 << 20, sweep_budget=37, kernel=isg.KERNEL_DENSE_TC)
+    res = h.local_search([6], R, max_sweeps=1000, restarts=1 << 20, sweep_budget=37, kernel=isg.KERNEL_DENSE_TC,
+                             dense_tensor_sweeps=ts)
     torch.cuda.synchronize()
     _dense_checks(inst, res, R)
     st = dict(res.stats)
