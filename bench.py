@@ -1,29 +1,37 @@
 #!/usr/bin/env python3
 """Benchmark: spin-flip evaluations/s and local minima/s of the GPU local search.
 
-One step = one ising_local_search call over the whole workload (every
-instance, every replica, every restart) with the instances resident on the
-GPU.  Workloads (synthetic, seeded; see workloads/):
+One step = one ising_local_search call over a whole workload (every instance,
+every replica, every restart) with the instances resident on the GPU.
+Workloads (synthetic, seeded; see workloads/):
   c1  16x16 periodic +/-J lattice, 64 replicas, 10 restarts
   c2  32^3 periodic +/-J lattice, h in {-1,0,1}, 1024 replicas, <= 100 sweeps
-      per descent, 10 restarts (multi-spin coded)            [default]
+      per descent, 10 restarts (multi-spin coded)
   c3  4096 K4,4 cell grids (side 4..16), Gaussian J, h, one 3-spin coupling
       per cell, 32 replicas, FP32 fields with FP64 refresh every 16 sweeps
   c4  dense SK, N = 4096, 4096 replicas, sequential schedule on tensor cores
-  c5  100^3 periodic Gaussian lattice, 16 replicas, 1000-sweep budget with
-      restarts, FP32 fields refreshed in FP64 every 16 sweeps
+  c5  100^3 periodic Gaussian lattice (10^6 spins), 16 replicas, 1000-sweep
+      budget with restarts, FP32 fields refreshed in FP64 every 16 sweeps
+      [headline: the largest single-GPU workload, bound by HBM]
   c5i the same lattice with +/-1 couplings
-Prints one JSON line (rank 0).  --impl reference times the CPU oracle instead.
+
+Default run: the headline workload timed for exactly --steps steps, then every
+other workload as a sub-record under "per_workload" (each timed for at least
+--min-seconds), one JSON line on rank 0.  --impl reference times the CPU
+oracle on the headline workload instead.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
+import platform
 import statistics
 import subprocess
-import tempfile
 import sys
+import tempfile
+import threading
 import time
 
 import numpy as np
@@ -35,6 +43,9 @@ import workloads as W  # noqa: E402
 
 METRIC = "spin-flip evals/s, minima/s on 1 GB300: batched/mixed vs plain at equal energy"
 UNIT = "flip_evals/s"
+HEADLINE = "c5"
+ALL_WORKLOADS = ("c1", "c2", "c3", "c4", "c5", "c5i")
+DENSE_TENSOR_SWEEPS = 3   # the library's default split of a dense descent (tensor-core sweeps first)
 
 
 def make_workload(name: str, instances: int = 0, sk_n: int = 0):
@@ -78,15 +89,17 @@ def seeds_for(name: str, n_inst: int, rank: int):
 
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons while a
+    timed region runs; start() returns once the first sample has arrived, so
+    that the samples cover the region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
         self.proc = None
-        # raw samples (summarised into the JSON line); ISING_BENCH_CLOCKS_DIR keeps them
         self.path = os.path.join(os.environ.get("ISING_BENCH_CLOCKS_DIR", tempfile.gettempdir()),
-                                 f"clocks_{os.getpid()}.csv")
+                                 f"clocks_{os.getpid()}_{id(self)}.csv")
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
@@ -95,17 +108,32 @@ class ClockSampler:
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 3.0:
+            self.fh.flush()
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
+        self.first_lines = self._count()
+
+    def _count(self):
+        try:
+            with open(self.path) as f:
+                return sum(1 for _ in f)
+        except OSError:
+            return 0
 
     def stop(self):
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
         self.fh.close()
-        sm, smax, reasons = [], [], set()
+        sm, smax, power, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
@@ -114,15 +142,20 @@ class ClockSampler:
             try:
                 sm.append(float(parts[1]))
                 smax.append(float(parts[2]))
+                power.append(float(parts[3]))
             except ValueError:
                 continue
             for nm, v in zip(names, parts[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
 # ----------------------------------------------------------------------------- peaks
@@ -135,35 +168,105 @@ def measured_peaks():
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def oracle_sample(name, insts, R, kw, budget_s=10.0):
-    """Time the CPU oracle (single thread) on a bounded sample of the workload."""
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def oracle_units(name, insts, R, kw):
+    """The CPU sample's work units and the oracle parameters they run with.
+
+    A unit is (instance, first replica, replica count); units go instance by
+    instance, replica by replica, in the workload's own order.  The 100^3
+    lattices run only the first 40 sweeps of each replica's 1000-sweep budget
+    (a full budget is about 9 s of one core per replica)."""
+    okw = {k: v for k, v in kw.items() if k in ("max_sweeps", "restarts", "sweep_budget", "refresh_every",
+                                                "schedule")}
+    note = "the workload's own parameters"
+    if name in ("c5", "c5i"):
+        okw["sweep_budget"] = 40
+        note = "the first 40 sweeps of each replica's 1000-sweep budget"
+    per = 8 if (len(insts) == 1 and insts[0].n <= 4096 and R >= 8 and name != "c4") else 1
+    units = [(b, r0, min(per, R - r0)) for b in range(len(insts)) for r0 in range(0, R, per)]
+    return units, okw, note
+
+
+def oracle_sample(name, insts, R, kw, seconds, threads, seeds=None, start=0):
+    """Time the CPU oracle on a bounded sample of the workload: `threads` host
+    threads take units in order from a shared counter until `seconds` have
+    passed (units in flight finish).  The oracle's C calls release the GIL, so
+    the threads run in parallel; the oracle itself is unchanged.  Returns a
+    dict with rates, the wall time and a description of the sample."""
     import oracle
     oracle.build()
-    seeds = seeds_for(name, len(insts), 0)
-    kw2 = {k: v for k, v in kw.items() if k in ("max_sweeps", "restarts", "sweep_budget", "refresh_every",
-                                              "schedule")}
-    evals = minima = 0
+    if seeds is None:
+        seeds = seeds_for(name, len(insts), 0)
+    units, okw, note = oracle_units(name, insts, R, kw)
+    lock = threading.Lock()
+    cache = {}
+    state = {"next": start, "evals": 0, "flips": 0, "minima": 0, "units": 0, "replicas": 0}
     t0 = time.perf_counter()
-    done_units = []
-    b = 0
-    r_per = 1
-    oinsts = {}
-    while time.perf_counter() - t0 < budget_s:
-        inst = insts[b % len(insts)]
-        if b not in oinsts:
-            oinsts[b] = oracle.OracleInstance(inst)
-        _, _, _, st = oracle.descent(oinsts[b], seeds[b % len(insts)], b % len(insts), r_per, **kw2)
-        evals += st["flip_evals"]
-        minima += st["minima"]
-        done_units.append((b % len(insts), r_per))
-        b += 1
-        if b >= len(insts):
-            b = 0
-            r_per += 1
+    deadline = t0 + seconds
+
+    def oinst(b):
+        with lock:
+            o = cache.get(b)
+        if o is None:
+            o = oracle.OracleInstance(insts[b])
+            with lock:
+                cache[b] = o
+        return o
+
+    def worker():
+        while True:
+            with lock:
+                if time.perf_counter() >= deadline:
+                    return
+                k = state["next"]
+                state["next"] += 1
+            b, r0, cnt = units[k % len(units)]
+            _, _, _, st = oracle.descent(oinst(b), seeds[b], b, cnt, first_replica=r0, **okw)
+            with lock:
+                state["evals"] += st["flip_evals"]
+                state["flips"] += st["flips"]
+                state["minima"] += st["minima"]
+                state["units"] += 1
+                state["replicas"] += cnt
+
+    ths = [threading.Thread(target=worker) for _ in range(threads)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
     dt = time.perf_counter() - t0
-    desc = (f"{len(done_units)} oracle calls (instance, first k replicas) of this workload, "
-            f"{evals} evaluations, {dt:.1f} s")
-    return evals / dt, minima / dt, desc, dt
+    desc = (f"{state['replicas']} replica searches of this workload ({note}; units of "
+            f"(instance, replica range) taken in order by {threads} host thread(s)), "
+            f"{state['evals']} evaluations in {dt:.2f} s")
+    return {"value": state["evals"] / dt, "minima_per_s": state["minima"] / dt, "wall_s": dt,
+            "evals": state["evals"], "threads": threads, "sample": desc, "next": state["next"]}
+
+
+def cpu_baseline(name, insts, R, kw, seconds):
+    """The oracle on one host thread and on every host core (half the time each)."""
+    cores = os.cpu_count() or 1
+    one = oracle_sample(name, insts, R, kw, seconds / 2, 1)
+    allc = oracle_sample(name, insts, R, kw, seconds / 2, cores)
+    return {"value": allc["value"], "unit": UNIT, "cores": cores, "kind": "oracle", "sample": allc["sample"],
+            "minima_per_s": allc["minima_per_s"], "cpu_model": cpu_model(), "nproc": cores,
+            "single_thread": {"value": one["value"], "unit": UNIT, "cores": 1, "sample": one["sample"],
+                              "minima_per_s": one["minima_per_s"]}}
 
 
 # ----------------------------------------------------------------------------- multi-rank
@@ -183,19 +286,183 @@ def job_totals(t_local, evals_local, minima_local, dist=None, device=None):
     return float(t.item()), float(w[0].item()), float(w[1].item())
 
 
+# ----------------------------------------------------------------------------- one workload on the GPU
+def gpu_record(name, args, dev, rank=0, dist=None, steps=None, min_seconds=0.0, plain=True, cpu_seconds=0.0):
+    """Measure one workload: `steps` timed steps (at least `min_seconds` of
+    device time when steps is None), end to end with host copies, the
+    roofline of its main kernel, the plain comparator at equal energy and the
+    CPU oracle.  Returns (record dict, per-step work counters)."""
+    import torch
+    import paper_0912_3912_gb300 as isg
+
+    insts, R, kw, desc = make_workload(name, args.instances if name == args.workload else 0,
+                                       args.sk_n if name == args.workload else 0)
+    if name == args.workload:
+        if args.replicas:
+            R = args.replicas
+        if args.restarts:
+            kw["restarts"] = args.restarts
+        if args.sweep_budget >= 0:
+            kw["sweep_budget"] = args.sweep_budget
+        if args.replicas or args.restarts or args.sweep_budget >= 0 or args.instances or args.sk_n:
+            desc += f" [reduced: replicas={R}, {kw}]"
+    kernel = {"auto": 0, "tile": 1, "msc": 2, "sweep": 3, "dense": 4, "plain": 5}[args.kernel]
+    seeds = seeds_for(name, len(insts), rank)
+    h = isg.Handle(insts)
+    chosen = h.plan_kernel(R, kernel=kernel, **{k: v for k, v in kw.items() if k in ("schedule",)})
+    stream = torch.cuda.current_stream()
+    total_spins = h.total_spins
+    spins = torch.empty(R * total_spins, dtype=torch.int8, device=dev)
+    E = torch.empty((len(insts), R), dtype=torch.float64, device=dev)
+    minima = torch.empty((len(insts), R), dtype=torch.int32, device=dev)
+    out = (spins, E, None, minima)
+    l2_flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step(stats=False):
+        return h.local_search(seeds, R, kernel=kernel, stats=stats, out=out, **kw)
+
+    wms = []
+    for _ in range(args.warmup):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        wms.append((a, b))
+    torch.cuda.synchronize()
+    ref = step(stats=True)        # work counters of one step (identical every step)
+    st = ref.stats
+    torch.cuda.synchronize()
+    if steps is None:
+        est = min(a.elapsed_time(b) for a, b in wms) if wms else 1.0
+        steps = max(args.steps, int(math.ceil(min_seconds * 1e3 / max(est, 1e-3))))
+
+    if dist is not None:
+        dist.barrier()
+    clocks = ClockSampler(dev.index)
+    h.set_timing(True)            # per-kernel CUDA events inside the library, over the timed steps
+    torch.cuda.synchronize()
+    ev_pairs = []
+    for _ in range(steps):
+        l2_flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        ev_pairs.append((a, b))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ktimes = h.kernel_times()
+    h.set_timing(False)
+    ms = [a.elapsed_time(b) for a, b in ev_pairs]
+    t_total, evals_job, minima_job = job_totals(sum(ms) / 1e3, st["flip_evals"] * steps,
+                                                st["minima"] * steps, dist, dev)
+    value = evals_job / t_total
+
+    # end to end: host seeds in, host results out (pinned), through the C ABI
+    h_spins = torch.empty(R * total_spins, dtype=torch.int8, pin_memory=True)
+    h_E = torch.empty((len(insts), R), dtype=torch.float64, pin_memory=True)
+    e2e_ms = []
+    for _ in range(steps):
+        l2_flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        h_spins.copy_(spins, non_blocking=True)
+        h_E.copy_(E, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    t_e2e, ev_e2e, _ = job_totals(sum(e2e_ms) / 1e3, st["flip_evals"] * steps, 0, dist, dev)
+    e2e_value = ev_e2e / t_e2e
+
+    hbm, bf16, bf16s, peak_src = measured_peaks()
+    n_launch_per_step = st.get("launches", 1)
+    eff_kernel = chosen
+    if chosen == isg.KERNEL_MSC or (chosen == isg.KERNEL_SWEEP and insts[0].dtype == "i8"):
+        eff_kernel = 2 if chosen == isg.KERNEL_MSC else 3
+    roof = roofline(name, eff_kernel, insts, R, st, t_total / steps, clk, hbm, bf16s, peak_src, ktimes, steps)
+    work = {k: v for k, v in st.items() if k != "launches"}
+
+    # equal-energy comparison with the plain comparator
+    pl = None
+    if plain and chosen != isg.KERNEL_PLAIN:
+        comparator, ckw = isg.KERNEL_PLAIN, {}
+        if chosen == isg.KERNEL_DENSE_TC:
+            # dense: the straightforward blocked version with library GEMMs
+            comparator, ckw = isg.KERNEL_DENSE_TC, {"dense_variant": isg.DENSE_LIBRARY}
+        try:
+            h.local_search(seeds, R, kernel=comparator, stats=True, **ckw, **kw)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pr = h.local_search(seeds, R, kernel=comparator, stats=True, **ckw, **kw)
+            b.record(stream)
+            torch.cuda.synchronize()
+            pms = a.elapsed_time(b)
+            m1, m2 = float(E.mean().item()), float(pr.energy.mean().item())
+            energies = {"mean_energy": m1, "comparator_mean_energy": m2,
+                        "max_abs_diff": float((pr.energy - E).abs().max().item()),
+                        "identical_replicas": float((pr.energy == E).double().mean().item())}
+            if insts[0].dtype == "i8":
+                same = bool(torch.equal(pr.energy, E))  # integer couplings: identical results
+            else:
+                # float couplings: the comparator's field arithmetic differs only
+                # in rounding where noted (dense); equal energies up to FP64
+                same = energies["max_abs_diff"] <= 1e-9 * max(1.0, abs(m1)) if chosen != isg.KERNEL_DENSE_TC \
+                    else energies["identical_replicas"]
+            pv = pr.stats["flip_evals"] / (pms / 1e3)
+            pl = {"kind": "cublas_blocked" if chosen == isg.KERNEL_DENSE_TC else "plain",
+                  "value": pv, "unit": UNIT, "ms_per_step": pms, "energy_match": same, "energies": energies,
+                  "speedup": value / pv}
+        except Exception as ex:  # comparator not available for this workload
+            pl = {"unavailable": str(ex)}
+
+    cpu = None
+    if cpu_seconds > 0 and rank == 0 and dist is None:
+        cpu = cpu_baseline(name, insts, R, kw, cpu_seconds)
+
+    rec = {
+        "workload": name, "description": desc, "value": value, "unit": UNIT,
+        "minima_per_s": minima_job / t_total, "steps": steps, "ms_per_step": t_total * 1e3 / steps,
+        "replicas": R, "instances": len(insts), "spins": total_spins, "kernel": isg.KERNEL_NAMES[chosen],
+        "params": dict(kw), "work_per_step": work,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * len(insts),
+                "d2h_bytes_per_step": R * total_spins + 8 * R * len(insts)},
+        "gpu_launches_per_step": int(n_launch_per_step),
+        "clocks": clk, "roofline": roof, "plain": pl, "cpu_baseline": cpu,
+        "dtype": "bit-packed i1/int32" if insts[0].dtype == "i8" and chosen in (isg.KERNEL_MSC, isg.KERNEL_TILE,
+                                                                               isg.KERNEL_SWEEP)
+        else ("int32" if insts[0].dtype == "i8" else
+              ("bf16 hi+lo tensor GEMMs, f32 fields, f64 energies" if chosen == isg.KERNEL_DENSE_TC
+               else "f32 fields, f64 refresh/energy")),
+    }
+    h.close()
+    del l2_flush
+    torch.cuda.empty_cache()
+    return rec
+
+
 # ----------------------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default=HEADLINE)
+    ap.add_argument("--per-workload", default=",".join(w for w in ALL_WORKLOADS if w != HEADLINE),
+                    help="comma-separated workloads measured as sub-records after the headline ('' for none)")
+    ap.add_argument("--min-seconds", type=float, default=1.5,
+                    help="minimum timed device time of each sub-record")
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--kernel", default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    # smaller variants of a workload, for profiler captures
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="CPU oracle time of the headline's baseline (half on one thread, half on all cores)")
+    ap.add_argument("--sub-cpu-seconds", type=float, default=4.0, help="the same for each sub-record")
+    ap.add_argument("--ref-seconds", type=float, default=60.0,
+                    help="--impl reference: oracle time over all warm-up and timed steps")
+    # smaller variants of the headline workload, for profiler captures
     ap.add_argument("--replicas", type=int, default=0)
     ap.add_argument("--restarts", type=int, default=0)
     ap.add_argument("--sweep-budget", type=int, default=-1)
@@ -208,39 +475,20 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    insts, R, kw, desc = make_workload(args.workload, args.instances, args.sk_n)
-    if args.replicas:
-        R = args.replicas
-    if args.restarts:
-        kw["restarts"] = args.restarts
-    if args.sweep_budget >= 0:
-        kw["sweep_budget"] = args.sweep_budget
-    if args.replicas or args.restarts or args.sweep_budget >= 0 or args.instances or args.sk_n:
-        desc += f" [reduced: replicas={R}, {kw}]"
 
-    if args.impl == "reference" and args.method == "fm":
-        if rank == 0:
-            run_fm_reference(args, insts, R, kw, desc)
-        return
     if args.impl == "reference":
         if rank != 0:
-            return
-        ev, mn, sample, dt = oracle_sample(args.workload, insts, R, kw, budget_s=args.cpu_seconds)
-        steps_t = []
-        for _ in range(args.warmup + args.steps):
-            pass
-        line = {"metric": METRIC, "value": ev, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "i8->int64" if insts[0].dtype == "i8" else "f32/f64",
-                "data": "synthetic", "minima_per_s": mn,
-                "config": {"workload": args.workload, "description": desc, "replicas": R, **{k: v for k, v in kw.items()}},
-                "cpu_baseline": {"value": ev, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
-                "e2e": {"value": ev, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line))
+            return            # the oracle runs once, on rank 0; other ranks exit without work
+        insts, R, kw, desc = make_workload(args.workload, args.instances, args.sk_n)
+        if args.method == "fm":
+            run_fm_reference(args, insts, R, kw, desc)
+        else:
+            run_reference(args, insts, R, kw, desc)
         return
 
     if args.method == "fm":
         if rank == 0:
+            insts, R, kw, desc = make_workload(args.workload, args.instances, args.sk_n)
             run_fm(args, insts, R, kw, desc)
         return
 
@@ -257,142 +505,74 @@ def main():
     dev = torch.device("cuda", local_rank if world > 1 else 0)
     torch.cuda.set_device(dev)
 
-    kernel = {"auto": 0, "tile": 1, "msc": 2, "sweep": 3, "dense": 4, "plain": 5}[args.kernel]
-    seeds = seeds_for(args.workload, len(insts), rank)
-    h = isg.Handle(insts)
-    chosen = h.plan_kernel(R, kernel=kernel, **{k: v for k, v in kw.items() if k in ("schedule",)})
-    stream = torch.cuda.current_stream()
-    total_spins = h.total_spins
-    spins = torch.empty(R * total_spins, dtype=torch.int8, device=dev)
-    E = torch.empty((len(insts), R), dtype=torch.float64, device=dev)
-    minima = torch.empty((len(insts), R), dtype=torch.int32, device=dev)
-    out = (spins, E, None, minima)
-    l2_flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
-
-    def step(stats=False):
-        return h.local_search(seeds, R, kernel=kernel, stats=stats, out=out, **kw)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    ref = step(stats=True)        # work counters of one step (identical every step)
-    st = ref.stats
-    torch.cuda.synchronize()
-
-    if dist is not None:
-        dist.barrier()
-    clocks = ClockSampler(dev.index)
-    h.set_timing(True)            # per-kernel CUDA events inside the library, over the timed steps
-    torch.cuda.synchronize()
-    ev_pairs = []
-    for _ in range(args.steps):
-        l2_flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        step()
-        b.record(stream)
-        ev_pairs.append((a, b))
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    ktimes = h.kernel_times()
-    h.set_timing(False)
-    ms = [a.elapsed_time(b) for a, b in ev_pairs]
-    t_total, evals_job, minima_job = job_totals(sum(ms) / 1e3, st["flip_evals"] * args.steps,
-                                                st["minima"] * args.steps, dist, dev)
-    value = evals_job / t_total
-
-    # end to end: host seeds in, host results out (pinned), through the C ABI
-    h_spins = torch.empty(R * total_spins, dtype=torch.int8, pin_memory=True)
-    h_E = torch.empty((len(insts), R), dtype=torch.float64, pin_memory=True)
-    e2e_ms = []
-    for _ in range(args.steps):
-        l2_flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        step()
-        h_spins.copy_(spins, non_blocking=True)
-        h_E.copy_(E, non_blocking=True)
-        b.record(stream)
-        b.synchronize()
-        e2e_ms.append(a.elapsed_time(b))
-    e2e_value = st["flip_evals"] * len(e2e_ms) / (sum(e2e_ms) / 1e3)
-
-    # roofline of the dominant kernel
-    hbm, bf16, bf16s, peak_src = measured_peaks()
-    n_launch_per_step = st.get("launches", 1)
-    eff_kernel = chosen
-    if chosen == isg.KERNEL_MSC or (chosen == isg.KERNEL_SWEEP and insts[0].dtype == "i8"):
-        eff_kernel = 2 if chosen == isg.KERNEL_MSC else 3
-    roof = roofline(args.workload, eff_kernel, insts, R, st, t_total / args.steps, clk, hbm, bf16s, peak_src,
-                    ktimes, args.steps)
-    st = {k: v for k, v in st.items() if k != "launches"}
-
-    # equal-energy comparison with the plain comparator kernel
-    plain = None
-    if not args.no_plain and chosen != isg.KERNEL_PLAIN:
-        comparator = isg.KERNEL_PLAIN
-        if chosen == isg.KERNEL_DENSE_TC:
-            # dense: the straightforward blocked version with library GEMMs
-            os.environ["ISING_DENSE_CUBLAS"] = "1"
-            comparator = isg.KERNEL_DENSE_TC
-        try:
-            pr = h.local_search(seeds, R, kernel=comparator, stats=True, **kw)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            pr = h.local_search(seeds, R, kernel=comparator, stats=True, **kw)
-            b.record(stream)
-            torch.cuda.synchronize()
-            pms = a.elapsed_time(b)
-            if insts[0].dtype == "i8":
-                same = bool(torch.equal(pr.energy, E))  # integer couplings: identical results
-            else:
-                # float couplings: the comparator's rounding differs where its field
-                # arithmetic does; report how the energies reached compare
-                m1, m2 = float(E.mean().item()), float(pr.energy.mean().item())
-                same = {"max_abs_diff": float((pr.energy - E).abs().max().item()), "mean_energy": m1,
-                        "comparator_mean_energy": m2, "rel_mean_diff": abs(m1 - m2) / max(abs(m2), 1e-300),
-                        "identical_replicas": float((pr.energy == E).double().mean().item())}
-            plain = {"kind": "cublas_blocked" if chosen == isg.KERNEL_DENSE_TC else "plain",
-                     "value": pr.stats["flip_evals"] / (pms / 1e3), "unit": UNIT, "ms_per_step": pms,
-                     "energy_match": same, "speedup": value / (pr.stats["flip_evals"] / (pms / 1e3))}
-        except Exception as ex:  # comparator not available for this workload
-            plain = {"unavailable": str(ex)}
-        finally:
-            os.environ.pop("ISING_DENSE_CUBLAS", None)
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ev, mn, sample, dt = oracle_sample(args.workload, insts, R, kw, budget_s=args.cpu_seconds)
-        cpu = {"value": ev, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
-               "minima_per_s": mn}
+    head = gpu_record(args.workload, args, dev, rank, dist, steps=args.steps, plain=not args.no_plain,
+                      cpu_seconds=0.0 if args.no_cpu_baseline else args.cpu_seconds)
+    subs = {}
+    if world == 1:
+        for w in [x for x in args.per_workload.split(",") if x and x != args.workload]:
+            try:
+                subs[w] = gpu_record(w, args, dev, 0, None, steps=None, min_seconds=args.min_seconds,
+                                     plain=not args.no_plain,
+                                     cpu_seconds=0.0 if args.no_cpu_baseline else args.sub_cpu_seconds)
+            except Exception as ex:
+                subs[w] = {"workload": w, "unavailable": f"{type(ex).__name__}: {ex}"}
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_total * 1e3 / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": "bit-packed i1/int32" if insts[0].dtype == "i8" else "f32 fields, f64 refresh/energy",
+            "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": head["dtype"],
             "data": "synthetic (seeded generators; the paper's instances are not available)",
-            "minima_per_s": minima_job / t_total,
-            "config": {"workload": args.workload, "description": desc, "replicas": R,
-                       "instances": len(insts), "spins": total_spins,
-                       "kernel": isg.KERNEL_NAMES[chosen], "l2": "flushed (512 MB write) before every timed step",
-                       **{k: v for k, v in kw.items()}},
-            "work_per_step": st,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * len(insts),
-                    "d2h_bytes_per_step": R * total_spins + 8 * R * len(insts)},
-            "gpu_launches": int(n_launch_per_step) * args.steps,
-            "clocks": clk,
-            "roofline": roof,
-            "plain": plain,
-            "cpu_baseline": cpu,
+            "minima_per_s": head["minima_per_s"],
+            "config": {"workload": args.workload, "description": head["description"], "replicas": head["replicas"],
+                       "instances": head["instances"], "spins": head["spins"], "kernel": head["kernel"],
+                       "l2": "flushed (512 MB write) before every timed step",
+                       "parallelism": f"replicas sharded over {world} GPU(s), no data-path collective",
+                       **head["params"]},
+            "work_per_step": head["work_per_step"],
+            "e2e": head["e2e"],
+            "gpu_launches": head["gpu_launches_per_step"] * args.steps,
+            "clocks": head["clocks"],
+            "roofline": head["roofline"],
+            "plain": head["plain"],
+            "cpu_baseline": head["cpu_baseline"],
+            "per_workload": subs,
         }
         print(json.dumps(line))
-    h.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_reference(args, insts, R, kw, desc):
+    """The reference arm: the CPU oracle as it stands on every host core, each
+    step a bounded sample of the workload (units continue where the previous
+    step stopped), flip evaluations per second over the timed steps."""
+    cores = os.cpu_count() or 1
+    seeds = seeds_for(args.workload, len(insts), 0)
+    per_step = max(0.25, args.ref_seconds / max(1, args.steps + args.warmup))
+    pos, evals, minima, t_all, walls, samples = 0, 0, 0.0, 0.0, [], []
+    for k in range(args.warmup + args.steps):
+        r = oracle_sample(args.workload, insts, R, kw, per_step, cores, seeds=seeds, start=pos)
+        pos = r["next"]
+        if k >= args.warmup:
+            evals += r["evals"]
+            minima += r["minima_per_s"] * r["wall_s"]
+            t_all += r["wall_s"]
+            walls.append(r["wall_s"])
+            samples.append(r["sample"])
+    value = evals / t_all
+    sample = (f"{args.steps} timed steps of about {per_step:.2f} s each on {cores} threads; last: {samples[-1]}"
+              if samples else "")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64 (oracle)" if insts[0].dtype == "i8" else "f64/f32 mirror (oracle)",
+            "data": "synthetic", "minima_per_s": minima / t_all,
+            "config": {"workload": args.workload, "description": desc, "replicas": R, **kw},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model(), "nproc": cores},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
 
 
 def run_fm(args, insts, R, kw, desc):
@@ -465,7 +645,7 @@ def run_fm(args, insts, R, kw, desc):
             if time.time() - t0 > args.cpu_seconds:
                 break
         dt = time.time() - t0
-        cpu = {"value": moves / dt, "unit": "moves/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": moves / dt, "unit": "moves/s", "cores": 1, "kind": "oracle", "cpu_model": cpu_model(),
                "sample": f"{n_runs} oracle searches (first starts of this workload), {moves} moves, {dt:.1f} s"}
     line = {"metric": "pass-based search (Sec. IV, Fig. 3) moves/s on 1 GB300", "value": value, "unit": "moves/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps,
@@ -497,7 +677,7 @@ def run_fm_reference(args, insts, R, kw, desc):
     restarts = int(kw.get("restarts", 1))
     budget = max(args.cpu_seconds / max(args.steps + args.warmup, 1), 0.05)
     units = [(b, r, k) for b in range(len(insts)) for r in range(R) for k in range(restarts)]
-    pos, rates, moves_all, runs_all, t_all = 0, [], 0, 0, 0.0
+    pos, moves_all, runs_all, t_all = 0, 0, 0, 0.0
     for step in range(args.warmup + args.steps):
         moves, runs, t0 = 0, 0, time.perf_counter()
         while time.perf_counter() - t0 < budget:
@@ -508,17 +688,18 @@ def run_fm_reference(args, insts, R, kw, desc):
             runs += 1
         dt = time.perf_counter() - t0
         if step >= args.warmup:
-            rates.append(moves / dt)
             moves_all, runs_all, t_all = moves_all + moves, runs_all + runs, t_all + dt
     value = moves_all / t_all
     sample = f"{runs_all} oracle searches (first starts of this workload, in order), {moves_all} moves, {t_all:.1f} s"
     line = {"metric": "pass-based search (Sec. IV, Fig. 3) moves/s on 1 GB300", "value": value, "unit": "moves/s",
             "impl": "reference", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_all / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 (oracle)",
             "data": "synthetic (seeded generators)",
             "config": {"workload": args.workload, "method": "fm", "description": desc, "replicas": R,
                        "restarts": restarts, "instances": len(insts)},
-            "cpu_baseline": {"value": value, "unit": "moves/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "moves/s", "cores": 1, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "moves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -572,7 +753,6 @@ def _roofline(name, kernel, insts, R, st, step_s, clk, hbm, bf16s, src):
     mhz = (clk or {}).get("sm_mhz") or 2070.0
     inst = insts[0]
     deg = sum(i.nnz for i in insts) / max(1, sum(i.n for i in insts)) if inst.row_ptr is not None else inst.n - 1
-    lattice = inst.meta.get("kind") == "lattice" and inst.meta.get("periodic") and len(set(inst.meta["dims"])) == 1
     msc = inst.dtype == "i8" and inst.hyper_ptr is None and np.all(np.abs(inst.J) == 1) and (
         inst.h is None or np.all(np.abs(inst.h) <= 1))
     if msc and kernel in (2, 3):
@@ -590,11 +770,11 @@ def _roofline(name, kernel, insts, R, st, step_s, clk, hbm, bf16s, src):
                 "peak_source": f"derived: {sm_count} SMs x 128 integer lanes x {mhz:.0f} MHz (median SM clock under load)"}
     if kernel == 4:
         # Tensor-core work actually done: each descent's first sweeps (the
-        # library's split, 3 unless overridden) and one export pass, 4 n^2 flops
-        # per replica and pass (BF16 hi and lo GEMMs).  Later sweeps run as
+        # library's default split) and one export pass, 4 n^2 flops per
+        # replica and pass (BF16 hi and lo GEMMs).  Later sweeps run as
         # incremental updates on CUDA cores and are not counted here.
         n = inst.n
-        sweeps_a = int(os.environ.get("ISING_DENSE_TC_SWEEPS", "3"))
+        sweeps_a = DENSE_TENSOR_SWEEPS
         flops = st["descents"] * (min(sweeps_a, st["sweeps"] / max(1, st["descents"])) + 1) * 4.0 * n * n
         achieved = flops / step_s / 1e12
         return {"bound": "tensor", "achieved": achieved, "peak": bf16s, "unit": "TFLOP/s", "frac": achieved / bf16s,
@@ -607,6 +787,7 @@ def _roofline(name, kernel, insts, R, st, step_s, clk, hbm, bf16s, src):
     achieved = byts / step_s / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "traffic": None, "kernel": "sweep_chunk" if kernel == 3 else "tile_kernel", "bytes_per_step": byts,
+            "bytes_model": "4.125 B per (spin, replica) visit + 16 B x degree per accepted flip",
             "peak_source": f"{src} copy bandwidth (MEASURED_PEAKS.json)"}
 
 

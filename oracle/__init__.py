@@ -75,6 +75,8 @@ def lib():
             L.orc_greedy_colouring.argtypes = [vp, vp]
             L.orc_colouring_valid.argtypes = [vp, vp]
             L.orc_descent.argtypes = [vp, u64, u32, i32, vp, vp, vp, vp, vp]
+            L.orc_descent_from.restype = C.c_int32
+            L.orc_descent_from.argtypes = [vp, u64, u32, i32, i32, vp, vp, vp, vp, vp]
             L.orc_fm_search.argtypes = [vp, vp, vp]
             L.orc_bruteforce.argtypes = [vp, vp, vp]
             L.orc_bnb.argtypes = [vp, i64, vp, vp, vp]
@@ -175,8 +177,11 @@ def colouring_valid(inst, colour):
 
 
 def descent(inst, seed, b, replicas, max_sweeps=1000, restarts=1, sweep_budget=0,
-            refresh_every=0, schedule=SCHED_COLOUR, mode=None, colour=None):
-    """Run the oracle's descent with restarts; returns (spins [R, n], E [R], minima [R], stats)."""
+            refresh_every=0, schedule=SCHED_COLOUR, mode=None, colour=None, first_replica=0):
+    """Run the oracle's descent with restarts for replicas first_replica ..
+    first_replica + replicas - 1; returns (spins [R, n], E [R], minima [R], stats).
+    The C call releases the GIL (ctypes), so host threads can run disjoint
+    replica ranges at once; the oracle keeps no global state."""
     oi = inst if isinstance(inst, OracleInstance) else OracleInstance(inst, colour=colour)
     if mode is None:
         mode = MODE_INT if oi.is_int else MODE_F32
@@ -185,8 +190,9 @@ def descent(inst, seed, b, replicas, max_sweeps=1000, restarts=1, sweep_budget=0
     E = np.empty(replicas, dtype=np.float64)
     minima = np.empty(replicas, dtype=np.int32)
     stats = np.zeros(5, dtype=np.uint64)
-    rc = lib().orc_descent(oi.ref, C.c_uint64(seed), C.c_uint32(b), C.c_int32(replicas), C.byref(p),
-                           spins.ctypes.data, E.ctypes.data, minima.ctypes.data, stats.ctypes.data)
+    rc = lib().orc_descent_from(oi.ref, C.c_uint64(seed), C.c_uint32(b), C.c_int32(first_replica),
+                                C.c_int32(replicas), C.byref(p), spins.ctypes.data, E.ctypes.data,
+                                minima.ctypes.data, stats.ctypes.data)
     if rc != 0:
         raise ValueError(f"orc_descent failed with {rc}")
     keys = ("flip_evals", "flips", "minima", "descents", "sweeps")

@@ -241,12 +241,25 @@ int32_t orc_colouring_valid(const orc_instance *in, const int32_t *colour) {
  *                       order, then hyper-edges ascending), and a from-scratch
  *                       FP64 recomputation rounded to FP32 at descent sweeps
  *                       d with d == 0 or d % refresh_every == 0.
- * stats5 accumulates {visits, flips, converged descents, descents, sweeps}.  */
+ * stats5 accumulates {visits, flips, converged descents, descents, sweeps}.
+ * orc_descent_from runs replicas first_replica .. first_replica + replicas - 1
+ * (their random starts use those replica indices) and writes row r of the
+ * outputs for replica first_replica + r; orc_descent starts at replica 0.    */
+int32_t orc_descent_from(const orc_instance *in, uint64_t seed, uint32_t b, int32_t first_replica,
+                         int32_t replicas, const orc_params *p, int8_t *out_spins, double *out_E,
+                         int32_t *out_minima, uint64_t *stats5);
+
 int32_t orc_descent(const orc_instance *in, uint64_t seed, uint32_t b, int32_t replicas,
                     const orc_params *p, int8_t *out_spins, double *out_E,
                     int32_t *out_minima, uint64_t *stats5) {
+  return orc_descent_from(in, seed, b, 0, replicas, p, out_spins, out_E, out_minima, stats5);
+}
+
+int32_t orc_descent_from(const orc_instance *in, uint64_t seed, uint32_t b, int32_t first_replica,
+                         int32_t replicas, const orc_params *p, int8_t *out_spins, double *out_E,
+                         int32_t *out_minima, uint64_t *stats5) {
   int32_t n = in->n;
-  if (n <= 0 || replicas <= 0 || p->max_sweeps < 1 || p->restarts < 1) return -1;
+  if (n <= 0 || replicas <= 0 || first_replica < 0 || p->max_sweeps < 1 || p->restarts < 1) return -1;
   int32_t *order = (int32_t *)malloc((size_t)n * sizeof(int32_t));
   int32_t *colour = (int32_t *)malloc((size_t)n * sizeof(int32_t));
   int8_t *s = (int8_t *)malloc((size_t)n);
@@ -280,7 +293,7 @@ int32_t orc_descent(const orc_instance *in, uint64_t seed, uint32_t b, int32_t r
     int32_t minima = 0;
     for (int32_t k = 0; k < p->restarts; ++k) {
       if (p->sweep_budget > 0 && total >= p->sweep_budget) break;
-      orc_random_start(n, seed, b, (uint32_t)r, (uint32_t)k, s);
+      orc_random_start(n, seed, b, (uint32_t)(first_replica + r), (uint32_t)k, s);
       stats5[3] += 1;
       for (int32_t i = 0; i < n; ++i) { vt[i] = -1; ft[i] = -2; }
       int64_t t = 0;

@@ -57,6 +57,9 @@ int32_t orc_colouring_valid(const orc_instance *in, const int32_t *colour);
 int32_t orc_descent(const orc_instance *in, uint64_t seed, uint32_t b, int32_t replicas,
                     const orc_params *p, int8_t *out_spins, double *out_E,
                     int32_t *out_minima, uint64_t *stats5);
+int32_t orc_descent_from(const orc_instance *in, uint64_t seed, uint32_t b, int32_t first_replica,
+                         int32_t replicas, const orc_params *p, int8_t *out_spins, double *out_E,
+                         int32_t *out_minima, uint64_t *stats5);
 
 double orc_fm_search(const orc_instance *in, int8_t *s, int32_t *passes);
 

@@ -27,10 +27,23 @@ def _check(line, unit):
 
 
 def test_reference_arm_descent():
-    _check(_run("--workload", "c1", "--steps", "1", "--warmup", "0", "--cpu-seconds", "1"), "flip_evals/s")
+    line = _run("--workload", "c1", "--steps", "2", "--warmup", "1", "--ref-seconds", "1.5")
+    _check(line, "flip_evals/s")
+    assert line["ms_per_step"] > 0 and line["cpu_baseline"]["nproc"] >= 1 and line["cpu_baseline"]["cpu_model"]
+
+
+def test_reference_arm_headline_workload_is_bounded():
+    """The default reference arm runs the headline workload (the 10^6-spin
+    lattice) on a bounded sample and keeps to its time budget."""
+    import time
+    t0 = time.time()
+    line = _run("--steps", "1", "--warmup", "0", "--ref-seconds", "2")
+    _check(line, "flip_evals/s")
+    assert line["config"]["workload"] == "c5"
+    assert time.time() - t0 < 120
 
 
 def test_reference_arm_pass_based_search():
     line = _run("--method", "fm", "--workload", "c1", "--steps", "2", "--warmup", "1", "--cpu-seconds", "1")
     _check(line, "moves/s")
-    assert line["config"]["method"] == "fm"
+    assert line["config"]["method"] == "fm" and line["ms_per_step"] > 0
