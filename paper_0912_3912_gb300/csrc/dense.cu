@@ -314,6 +314,12 @@ struct DenseState : FamilyState {
   int32_t *err = nullptr, *h_err = nullptr;
   int32_t *counter = nullptr;          // work counter of the per-replica continuation
   float *Sx = nullptr, *Fx = nullptr;  // [R][n] returned spins and their FP32 fields
+  // returned energies on tensor cores: digit planes of J [4][np][np] and their
+  // band copies [4][np][128], spins [Rp128][np], tile partials [np/128][Rp128]
+  __nv_bfloat16 *planes = nullptr, *bands = nullptr, *Se = nullptr;
+  long long *Epint = nullptr;
+  double *Eph = nullptr;
+  int32_t planes_F = 0;
 };
 
 
@@ -332,6 +338,11 @@ void free_state(DenseState &D) {
   cudaFree(D.counter);
   cudaFree(D.Sx);
   cudaFree(D.Fx);
+  cudaFree(D.planes);
+  cudaFree(D.bands);
+  cudaFree(D.Se);
+  cudaFree(D.Epint);
+  cudaFree(D.Eph);
   if (D.np != D.n) {  // the padded copies are owned only when padding was needed
     cudaFree(D.Jp);
     cudaFree(D.hp);
@@ -379,21 +390,16 @@ cudaError_t exact_energies(DenseState &D, ising_handle *h, int n, int R, const f
   if ((e = ensure_fx(D, (int64_t)D.Rp * n)) != cudaSuccess) return e;
   const int64_t tot = (int64_t)R * n;
   dense_spins_f32<<<(int)std::min<int64_t>((tot + 255) / 256, (int64_t)h->sm_count * 16), 256, 0, s>>>(out, D.Sx, tot);
-  // column-major view: F^T (n x R) = J (n x n, symmetric) . S^T (n x R).  FP32
-  // accuracy: by default the library's BF16x9 emulation of FP32 on tensor cores
-  // (each operand split exactly into three BF16 terms), else plain FP32 SIMT
-  // (ISING_DENSE_ENERGY_GEMM=fp32); never TF32.
-  static const bool simt = [] {
-    const char *v = std::getenv("ISING_DENSE_ENERGY_GEMM");
-    return v && std::strcmp(v, "fp32") == 0;
-  }();
+  // column-major view: F^T (n x R) = J (n x n, symmetric) . S^T (n x R), FP32
+  // accurate through the library's BF16x9 emulation (each operand split
+  // exactly into three BF16 terms); never TF32.  Used by the comparator only.
   const float one = 1.0f, zero = 0.0f;
   if (cublasSetStream(D.cublas, s) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
-  if (!simt && cublasSetEmulationStrategy(D.cublas, CUBLAS_EMULATION_STRATEGY_EAGER) != CUBLAS_STATUS_SUCCESS)
+  if (cublasSetEmulationStrategy(D.cublas, CUBLAS_EMULATION_STRATEGY_EAGER) != CUBLAS_STATUS_SUCCESS)
     return cudaErrorUnknown;
   if (cublasGemmEx(D.cublas, CUBLAS_OP_N, CUBLAS_OP_N, n, R, n, &one, J, CUDA_R_32F, n, D.Sx, CUDA_R_32F, n, &zero,
-                   D.Fx, CUDA_R_32F, n, simt ? CUBLAS_COMPUTE_32F_PEDANTIC : CUBLAS_COMPUTE_32F_EMULATED_16BFX9,
-                   CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS)
+                   D.Fx, CUDA_R_32F, n, CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUBLAS_GEMM_DEFAULT) !=
+      CUBLAS_STATUS_SUCCESS)
     return cudaErrorUnknown;
   dense_energy_from_fields<<<(R * 32 + 255) / 256, 256, 0, s>>>(out, D.Fx, hf, n, R, E);
   h->launches += 2;
@@ -423,11 +429,6 @@ cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t 
     const int n = h->inst[b].n;
     if (D.n != n || D.Rp != Rp || D.inst != b) {
       free_state(D);
-      if (cublasCreate(&D.cublas) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
-      // a fixed workspace, so that the GEMMs captured into the sweep graph never allocate
-      constexpr size_t kWs = 64u << 20;
-      if ((e = cudaMalloc(&D.workspace, kWs)) != cudaSuccess) return e;
-      if (cublasSetWorkspace(D.cublas, D.workspace, kWs) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
       if ((e = cudaFuncSetAttribute(dense_decide, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)(kDB * kDB * sizeof(float)))) != cudaSuccess)
         return e;
@@ -446,7 +447,6 @@ cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t 
       if ((e = cudaMemset(D.S, 0, (size_t)n * Rp * 2)) != cudaSuccess) return e;
       dense_split<<<h->sm_count * 8, 256, 0, s>>>(h->d_Jdense + joff, D.hi, D.lo, (int64_t)n * n);
     }
-    if (cublasSetStream(D.cublas, s) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
     const float *J = h->d_Jdense + joff;
     const uint64_t seed = seeds_host[b];
 
@@ -475,6 +475,15 @@ cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t 
         }
         if ((e = cudaMalloc(&D.S_tc, (size_t)Rp128 * np * 2)) != cudaSuccess) return e;
         if ((e = cudaMemset(D.S_tc, 0, (size_t)Rp128 * np * 2)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&D.planes, (size_t)4 * np * np * 2)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&D.bands, (size_t)4 * np * 128 * 2)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&D.Se, (size_t)Rp128 * np * 2)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&D.Epint, (size_t)(np / 128) * Rp128 * sizeof(long long))) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&D.Eph, (size_t)(np / 128) * Rp128 * sizeof(double))) != cudaSuccess) return e;
+        int F = 0;
+        if ((e = dense_planes_build(D.Jp, np, D.planes, D.bands, &F, h->sm_count, s)) != cudaSuccess) return e;
+        D.planes_F = F;
+        h->launches += 2;
         if ((e = cudaMalloc(&D.err, 64)) != cudaSuccess) return e;
         if ((e = cudaMallocHost(&D.h_err, 64)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&D.counter, 64)) != cudaSuccess) return e;
@@ -514,13 +523,30 @@ cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t 
           n, np, R, D.S_tc, D.best, D.rep, outb, E + (int64_t)b * R, minima ? minima + (int64_t)b * R : nullptr);
       h->launches += 1;
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      kt_begin(h, "dense_energy_gemm", s);
-      e = exact_energies(D, h, n, R, J, hf, outb, E + (int64_t)b * R, s);
+      // energies of the returned states: the library's own tensor-core GEMMs
+      // over the exact digit planes of J (dense_energy.cu)
+      kt_begin(h, "dense_energy_tc", s);
+      int nl = 0;
+      e = dense_energy_run(outb, n, np, R, D.hp, D.planes, D.bands, D.planes_F, D.Se, D.Epint, D.Eph,
+                           E + (int64_t)b * R, D.err, h->sm_count, &nl, s);
+      h->launches += (uint64_t)nl;
       kt_end(h, s);
       if (e != cudaSuccess) return e;
+      if ((e = cudaMemcpyAsync(D.h_err, D.err, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+      if (*D.h_err != 0) return cudaErrorLaunchTimeout;
       joff += (int64_t)n * n;
       continue;
     }
+    // the comparator: blocks with library GEMMs (cuBLAS), created on first use
+    if (!D.cublas) {
+      if (cublasCreate(&D.cublas) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+      // a fixed workspace, so that the GEMMs captured into the sweep graph never allocate
+      constexpr size_t kWs = 64u << 20;
+      if ((e = cudaMalloc(&D.workspace, kWs)) != cudaSuccess) return e;
+      if (cublasSetWorkspace(D.cublas, D.workspace, kWs) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+    }
+    if (cublasSetStream(D.cublas, s) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
     const int rb = (R + 255) / 256;
     dense_init<<<rb, 256, 0, s>>>(R, D.rep, h->d_stats);
     // capture one sweep into a graph, replay it sweep by sweep

@@ -465,8 +465,10 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
 bool dense_tc_eligible(int n) { return n >= 1 && n <= kMaxN; }
 int dense_tc_padded(int n) { return (n + 255) / 256 * 256; }
 
-static cudaError_t encode_2d(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer,
-                             uint32_t box_inner, uint32_t box_outer) {
+// A 2-D BF16 tensor map (row-major, `inner` elements per row, `outer` rows)
+// for TMA tile loads of box_inner x box_outer with 128-byte swizzling.
+cudaError_t tc_encode_2d(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer, uint32_t box_inner,
+                         uint32_t box_outer) {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
     cudaDriverEntryPointQueryResult q;
@@ -495,9 +497,9 @@ cudaError_t dense_tc_run(int n, int n_eval, int R, int Rp, int b, uint64_t seed,
                          const ising_search_params *p, cudaStream_t s) {
   CUtensorMap mS, mH, mL;
   cudaError_t e;
-  if ((e = encode_2d(&mS, S, (uint64_t)n, (uint64_t)Rp, kKC, kTM)) != cudaSuccess) return e;
-  if ((e = encode_2d(&mH, Jhi, (uint64_t)n, (uint64_t)n, kKC, kTB)) != cudaSuccess) return e;
-  if ((e = encode_2d(&mL, Jlo, (uint64_t)n, (uint64_t)n, kKC, kTB)) != cudaSuccess) return e;
+  if ((e = tc_encode_2d(&mS, S, (uint64_t)n, (uint64_t)Rp, kKC, kTM)) != cudaSuccess) return e;
+  if ((e = tc_encode_2d(&mH, Jhi, (uint64_t)n, (uint64_t)n, kKC, kTB)) != cudaSuccess) return e;
+  if ((e = tc_encode_2d(&mL, Jlo, (uint64_t)n, (uint64_t)n, kKC, kTB)) != cudaSuccess) return e;
   TcArgs A;
   if (n % 256 != 0 || n > kMaxN || n_eval > n) return cudaErrorInvalidValue;
   A.n = n;
