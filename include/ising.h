@@ -197,8 +197,16 @@ typedef struct {
 
 typedef struct ising_handle ising_handle;
 
-/* Validate and upload n_instances instances (all of one dtype).  On success
- * *out owns device copies; on failure *out is NULL.                           */
+/* Validate and upload n_instances instances (all of one dtype).  An instance
+ * is the paper's problem statement (Sec. II): spins s_i = +/-1 on the nodes of
+ * a coupling graph with couplings J_ij and fields h_i, whose energy is Eq. 1,
+ * extended by the k-spin hyper-couplings J_e of Eq. 6 (Sec. VI).  Checks:
+ * sizes and pointers (ISING_ERR_INVALID_ARG, also for non-finite FP32 values),
+ * J_ij = J_ji with matching structure (ISING_ERR_ASYMMETRIC), no self loop
+ * (ISING_ERR_SELF_LOOP), hyper-edges of >= 2 distinct in-range members
+ * (ISING_ERR_BAD_HYPEREDGE), a given colouring valid for the conflict graph
+ * (ISING_ERR_BAD_COLOURING).  On success *out owns device copies (the host
+ * arrays may be freed); on failure *out is NULL and nothing stays allocated.  */
 ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
                           ising_handle **out);
 
@@ -231,6 +239,18 @@ int32_t ising_plan_kernel(ising_handle *h, int32_t replicas, const ising_search_
  * ISING_KERNEL_AUTO calls use it.  Writes the chosen family to *chosen.        */
 ising_status ising_autotune(ising_handle *h, int32_t replicas, const ising_search_params *p,
                             int32_t *chosen, cudaStream_t stream);
+
+/* Self-check of this library's arithmetic; the paper has no counterpart.  The
+ * exact field refresh (the FP64 sum of the field and the couplings, rounded to
+ * FP32, formed exactly in 64-bit fixed point when that is exact) rounds its
+ * integer sums to FP32 with integer instructions.  This runs `count` cases
+ * (values |s| <= 2^53 with constructed rounding ties and their neighbours,
+ * random values, 0 and 2^53; units 24 .. 200) on the current device and
+ * writes to the HOST *mismatches the number whose result differs, bit for
+ * bit, from the hardware int64 -> FP32 conversion scaled by the same power of
+ * two.  `seed` picks the cases.  Returns ISING_ERR_INVALID_ARG for count < 0
+ * or a NULL pointer; the call waits for its kernel.                          */
+ising_status ising_check_rounding(uint64_t seed, int64_t count, uint64_t *mismatches);
 
 /* Allocation-free energy evaluation.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory - for example a

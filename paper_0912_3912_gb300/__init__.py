@@ -97,6 +97,8 @@ def lib():
             L.ising_set_timing.restype = i32
             L.ising_kernel_times.argtypes = [vp, vp, i32]
             L.ising_kernel_times.restype = i32
+            L.ising_check_rounding.argtypes = [C.c_uint64, C.c_int64, vp]
+            L.ising_check_rounding.restype = i32
             L.ising_status_string.argtypes = [i32]
             L.ising_status_string.restype = C.c_char_p
             _lib = L
@@ -105,7 +107,7 @@ def lib():
 
 EXPORTED = ("ising_create", "ising_energy", "ising_local_search", "ising_plan_kernel",
             "ising_autotune", "ising_destroy", "ising_status_string", "ising_energy_noalloc",
-            "ising_set_timing", "ising_kernel_times", "ising_fm_search")
+            "ising_set_timing", "ising_kernel_times", "ising_fm_search", "ising_check_rounding")
 
 
 def _check(code: int, where: str):
@@ -306,6 +308,14 @@ def energy_noalloc(row_ptr, col, J, h, spins, replicas: int, energy, stream=None
             n, C.c_void_p(row_ptr.data_ptr()), C.c_void_p(col.data_ptr()), C.c_void_p(J.data_ptr()),
             None if h is None else C.c_void_p(h.data_ptr()), dt, C.c_void_p(spins.data_ptr()), replicas,
             C.c_void_p(energy.data_ptr()), C.c_void_p(s.cuda_stream))
+
+
+def check_rounding(seed: int, count: int) -> int:
+    """ising_check_rounding: mismatches of the library's integer-only FP32
+    rounding against the hardware conversion over `count` cases."""
+    out = C.c_uint64(0)
+    _check(lib().ising_check_rounding(seed, count, C.byref(out)), "ising_check_rounding")
+    return int(out.value)
 
 
 def status_string(code: int) -> str:

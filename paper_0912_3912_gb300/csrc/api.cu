@@ -82,7 +82,7 @@ struct HostInst {
 // fits below 2^62, and the high halves of up to 2^22 terms stay below 2^53 so
 // the final conversion to FP64 rounds once.  Returns -1 when that does not hold
 // (subnormal values, a wider spread or more terms).
-int32_t energy_base_exponent(const HostInst &I) {
+int32_t energy_base_exponent(const HostInst &I, int32_t *emax_out = nullptr) {
   int emin = 256, emax = -1;
   bool sub = false;
   auto see = [&](float v) {
@@ -98,6 +98,7 @@ int32_t energy_base_exponent(const HostInst &I) {
   for (float v : I.Jf) see(v);
   for (float v : I.hf) see(v);
   for (float v : I.hJf) see(v);
+  if (emax_out) *emax_out = emax;
   if (sub) return -1;
   if (emax < 0) return 1;  // all zero
   const int64_t terms = (int64_t)I.col.size() / 2 + I.n + (int64_t)I.hJf.size();
@@ -707,8 +708,10 @@ ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
     D.max_deg = I.max_deg;
     D.lat_L = I.lat_L;
     D.lat_d = I.lat_d;
-    D.ebase = fl ? energy_base_exponent(I) : -1;
+    int32_t emax = -1;
+    D.ebase = fl ? energy_base_exponent(I, &emax) : -1;
     D.fx53 = fp64_exact(I, fl, D.ebase);
+    D.ebits = !fl ? 7 : (D.ebase >= 0 ? 24 + std::max(0, emax - D.ebase) : -1);
     h->any_lattice = h->any_lattice || I.lat_d > 0;
     h->all_lattice = (b == 0 ? true : h->all_lattice) && I.lat_d > 0;
     h->nmax = std::max(h->nmax, I.n);

@@ -78,6 +78,32 @@ __device__ __forceinline__ float xr_round(int64_t s, int unit) {
   return __ll2float_rn(s) * __int_as_float((unit - 23) << 23);
 }
 
+// The same value with integer instructions only (the int64 -> FP32 conversion
+// runs on the FP64 pipe, a small fraction of the integer rate on this GPU).
+// IEEE-754 round to nearest, ties to even, of |s| to 24 significant bits: with
+// the leading one at bit m, keep bits m .. m-23, round up when the dropped
+// part exceeds half a unit in the last place, or equals it with an odd last
+// bit.  The result is 1.f * 2^(m + unit - 150): biased exponent m + unit - 23,
+// always normal for |s| <= 2^53 and 24 <= unit <= 200 (the range xr_exact
+// admits); a carry out of the rounded significand moves into the exponent.
+__device__ __forceinline__ float xr_round_int(int64_t s, int unit) {
+  if (s == 0) return 0.0f;
+  const uint32_t sign = (uint32_t)((uint64_t)s >> 63);
+  const uint64_t a = sign ? (uint64_t)(-s) : (uint64_t)s;
+  const int m = 63 - __clzll((long long)a);
+  uint32_t sig;
+  if (m <= 23) {
+    sig = (uint32_t)a << (23 - m);
+  } else {
+    const int sh = m - 23;
+    sig = (uint32_t)(a >> sh);
+    const uint64_t rem = a & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    sig += (rem > half || (rem == half && (sig & 1u))) ? 1u : 0u;
+  }
+  const uint32_t bits = (sign << 31) + ((uint32_t)(m + unit - 23) << 23) + (sig - 0x800000u);
+  return __uint_as_float(bits);
+}
+
 // ---- exact energies ------------------------------------------------------
 // Energy terms as integers t (unit 2^(ebase - 150), |t| < 2^62) accumulated as
 // a signed high part (t >> 32) and an unsigned low part (t & 0xffffffff):

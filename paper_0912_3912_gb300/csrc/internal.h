@@ -42,6 +42,9 @@ struct InstDesc {
   //     unit (DevGraph::runit) below 2^53 units; energies are not covered;
   // 0 = neither.
   int32_t fx53;
+  // Bits of the largest energy term in fixed-point units: |term| < 2^ebits
+  // (int8: 7; FP32 with ebase >= 0: 24 + emax - ebase; else -1).
+  int32_t ebits;
 };
 
 // Everything a kernel needs to read an instance set.

@@ -31,6 +31,19 @@ namespace isg {
 namespace {
 
 constexpr int kST = 256;  // threads per CTA
+// resident CTAs per SM the FP32/int lane visits are compiled for (registers
+// per thread = 64K / (kST * this)); the multi-spin-coded visits take 8
+#ifndef ISING_SWEEP_MINB1
+#define ISING_SWEEP_MINB1 4
+#endif
+#ifndef ISING_SWEEP_REFRESH_ROLLED
+#define ISING_SWEEP_REFRESH_ROLLED 1
+#endif
+#if ISING_SWEEP_REFRESH_ROLLED
+#define ISING_REFRESH_UNROLL _Pragma("unroll 1")
+#else
+#define ISING_REFRESH_UNROLL _Pragma("unroll")
+#endif
 
 struct GroupState {
   uint32_t lane_valid, active, convround, any, upd, start;
@@ -47,10 +60,22 @@ struct SweepArgs {
   uint64_t seed;
   uint32_t *sw, *fm, *bw;
   uint32_t *pend;  // [g][n]: lanes in which some neighbour flipped since the spin's last visit
+  // Parity-coloured lattices with an even side (class position = site >> 1):
+  // per (group, class, chunk of 32 class positions) a flag word whose low
+  // byte is set when a flip pushed a pending mark into the chunk and whose
+  // high byte is set when the chunk's own last visit flipped a spin (so its
+  // flip masks are nonzero).  A non-refresh visit skips chunks whose word is
+  // zero; null when not applicable.  [g][2][nchunk]
+  uint16_t *cflag;
+  int32_t nchunk;
   float *F;
   GroupState *gs;
   double *partial;  // [2][grid_e][G][32]: FP64 sums, or fixed-point high and low halves
   int32_t grid_e;
+  // 1: energies of a lattice group taken site-parallel (lane = site, a loop over
+  // the group's LPS replicas) with int64 sums per lane and warp; set when the
+  // instance's term width and the sites per warp cannot overflow them
+  int32_t en_fast;
   unsigned int *counter;
   int32_t *all_done;
   unsigned long long *stats;
@@ -69,12 +94,6 @@ __device__ __forceinline__ int lat_nbr(int j, uint32_t meta, int k, int L) {
   return j + off;
 }
 
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __global__ void sweep_init(SweepArgs A) {
   const int g = threadIdx.x;
@@ -121,43 +140,50 @@ __device__ __forceinline__ uint32_t sliced_ge4(uint32_t q0, uint32_t q1, uint32_
 }
 
 // End of a sweep: per group, which lanes converged, which descents ended.
-// (Folding this into the last class visit - its last CTA closing the sweep -
-// was measured slower than this separate one-block launch.)
+// One warp per group, lane l = replica lane l.  (Folding this into the last
+// class visit - its last CTA closing the sweep - was measured slower than this
+// separate launch.)
 __global__ void sweep_end(SweepArgs A) {
-  const int g = threadIdx.x;
+  const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (g >= A.G) return;
   GroupState &S = A.gs[g];
-  S.start = 0;
-  S.upd = 0;
   const uint32_t active = S.active;
-  if (!active) return;
   const uint32_t any = S.any;
-  S.any = 0;
-  uint32_t ended = 0;
-  for (int r = 0; r < 32; ++r)
-    if ((active >> r) & 1u) {
-      S.total[r] += 1;
-      if (A.budget > 0 && S.total[r] >= A.budget) ended |= 1u << r;
-    }
+  __syncwarp();
+  if (lane == 0) {
+    S.start = 0;
+    S.upd = 0;
+  }
+  if (!active) return;
+  const bool mine = (active >> lane) & 1u;
+  bool over = false;
+  if (mine) {
+    const int32_t t = S.total[lane] + 1;
+    S.total[lane] = t;
+    over = A.budget > 0 && t >= A.budget;
+  }
   const uint32_t conv = active & ~any;
-  ended |= conv;
-  S.d += 1;
-  if (S.d >= A.max_sweeps) ended |= active;
-  atomicAdd(A.stats + 4, (unsigned long long)__popc(active));
-  atomicAdd(A.stats + 0, (unsigned long long)__popc(active) * (unsigned long long)A.I.n);
-  atomicAdd(A.stats + 2, (unsigned long long)__popc(conv));
-  S.convround |= conv;
-  S.active = active & ~ended;
-  if (!S.active) S.round_end = 1;
+  uint32_t ended = __ballot_sync(0xffffffffu, over) | conv;
+  const int32_t d = S.d + 1;
+  if (d >= A.max_sweeps) ended |= active;
+  if (lane == 0) {
+    S.any = 0;
+    S.d = d;
+    atomicAdd(A.stats + 4, (unsigned long long)__popc(active));
+    atomicAdd(A.stats + 0, (unsigned long long)__popc(active) * (unsigned long long)A.I.n);
+    atomicAdd(A.stats + 2, (unsigned long long)__popc(conv));
+    S.convround |= conv;
+    S.active = active & ~ended;
+    if (!(active & ~ended)) S.round_end = 1;
+  }
 }
 
 // One colour class of one sweep.  MODE 0 int lanes, 1 FP32 lanes, 2 multi-spin
 // coded.  Groups are walked in an outer loop so the per-group state is read once
 // per warp and no index needs a division.
 template <int MODE, int LPS, bool LAT>
-__global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
-  // FP32 lattice path: per-warp staging of (48 LPS + 640) words (dynamic)
-  extern __shared__ __align__(16) uint32_t s_dyn[];
+__global__ void __launch_bounds__(kST, MODE == 2 ? 8 : ISING_SWEEP_MINB1) sweep_visit(SweepArgs A, int32_t c) {
   __shared__ uint32_t s_any[32];
   __shared__ unsigned long long s_red[kST / 32];
   __shared__ int s_off[6], s_wrap[6];
@@ -187,7 +213,7 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
   unsigned long long my_flips = 0;
   constexpr uint32_t lmask = LPS == 32 ? 0xffffffffu : ((1u << LPS) - 1u);
 
-  if (MODE == 2) {
+  if constexpr (MODE == 2) {
     const int8_t *hi = reinterpret_cast<const int8_t *>(G.h);
     const int8_t *Ji = reinterpret_cast<const int8_t *>(G.J);
     const int D = I.lat_d;
@@ -197,8 +223,17 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
       const bool fresh = A.gs[g].d == 0;
       uint32_t *swg = A.sw + (size_t)g * n;
       uint32_t *pendg = A.pend + (size_t)g * n;
+      uint16_t *cf_own = A.cflag ? A.cflag + ((size_t)g * 2 + c) * A.nchunk : nullptr;
+      uint8_t *cf_oth = A.cflag ? reinterpret_cast<uint8_t *>(A.cflag + ((size_t)g * 2 + (c ^ 1)) * A.nchunk) : nullptr;
       uint32_t anyg = 0;
       for (int t = blockIdx.x * blockDim.x + tid; t < cs; t += gridDim.x * blockDim.x) {
+        if (cf_own) {
+          // t - lane is a multiple of 32: the warp's lanes share chunk t >> 5
+          const uint16_t fv = cf_own[t >> 5];
+          __syncwarp(__activemask());
+          if (lane == 0 && fv) cf_own[t >> 5] = 0;
+          if (!fresh && !fv) continue;  // no pending mark anywhere in the chunk
+        }
         const int v = c0 + t;
         const int j = A.sequential ? v : __ldg(G.order + so + v);
         // everything indexed by the site itself is read in one round trip
@@ -260,8 +295,11 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
           anyg |= flip;
           my_flips += __popc(flip);
           if (LAT) {
-            for (int d = 0; d < 2 * D; ++d)
-              atomicOr(&pendg[j + s_off[d] + (((info >> d) & 1u) ? s_wrap[d] : 0)], flip);
+            for (int d = 0; d < 2 * D; ++d) {
+              const int nb = j + s_off[d] + (((info >> d) & 1u) ? s_wrap[d] : 0);
+              atomicOr(&pendg[nb], flip);
+              if (cf_oth) cf_oth[2 * (nb >> 6)] = 1;
+            }
           } else {
             for (uint32_t kk = __ldg(G.row + so + j), k1 = __ldg(G.row + so + j + 1); kk < k1; ++kk)
               atomicOr(&pendg[__ldg(G.col + kk)], flip);
@@ -306,16 +344,16 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
         const int D2 = 2 * I.lat_d;
         const float *Jp0 = reinterpret_cast<const float *>(G.Jpos) + so;
         const float *hf = reinterpret_cast<const float *>(G.h) + so;
-        uint32_t *wsm = s_dyn + (tid >> 5) * (48 * LPS + 640);
-        float *sF = reinterpret_cast<float *>(wsm);                 // [32][LPS] stored fields
-        uint32_t *sP = wsm + 32 * LPS;                              // [19][32]: word, nbr words, nbr flips, couplings
-        uint16_t *sL = reinterpret_cast<uint16_t *>(sP + 19 * 32);  // [32 LPS] pending pairs (position << 5 | lane)
-        uint32_t *sSeg = sP + 19 * 32 + 16 * LPS;                   // [32] flips per position
+        uint16_t *cf_own = A.cflag ? A.cflag + ((size_t)g * 2 + c) * A.nchunk : nullptr;
+        uint8_t *cf_oth = A.cflag ? reinterpret_cast<uint8_t *>(A.cflag + ((size_t)g * 2 + (c ^ 1)) * A.nchunk) : nullptr;
         auto nb_of = [&](int jj, uint32_t mm, int kk) -> int {
           const int dir = (mm >> (8 + 3 * kk)) & 7;
           return jj + s_off[dir] + (((mm >> kk) & 1u) ? s_wrap[dir] : 0);
         };
         for (int base = wid * 32; base < cs; base += nwarps * 32) {
+          // chunk base >> 5 of this class: nothing pending and no flip masks to
+          // clear means nothing to do (the word is read by every lane alike)
+          if (cf_own && !refresh && cf_own[base >> 5] == 0) continue;
           const int v1 = c0 + base + lane;
           const bool valid1 = v1 < c1;
           const int j1 = valid1 ? __ldg(G.order + so + v1) : 0;
@@ -326,167 +364,163 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
           if (valid1 && p1) pendg[j1] = 0u;
           if (valid1 && !need1 && fm1) fmg[j1] = 0u;  // no flips at this visit
           uint32_t todo = __ballot_sync(0xffffffffu, need1);
-          if (!todo) continue;
+          if (!todo) {
+            if (cf_own && lane == 0) cf_own[base >> 5] = 0;
+            continue;
+          }
           if (!refresh) {
-            const uint32_t pm = need1 ? (p1 & active) : 0u;
-            uint32_t wj1 = 0u;
+            // Site-parallel: the position lane pulls, for each of its pending
+            // replicas, the flips of the neighbours since the site's previous
+            // visit (CSR order; FP32, round to nearest) into the stored field,
+            // four replicas per 16-byte access, and decides the replicas whose
+            // field changed.  With no flipped neighbour in a replica the field
+            // and the decision are unchanged.
+            uint32_t seg = 0u;
             if (need1) {
-              wj1 = swg[j1];
-              sP[lane] = wj1;
+              const uint32_t pm = p1 & active;
+              const uint32_t wj1 = swg[j1];
+              uint32_t wn[6], fn[6];
+              float w2[6];
+              uint32_t dirtym = 0u;
 #pragma unroll
-              for (int kk = 0; kk < 6; ++kk)
+              for (int kk = 0; kk < 6; ++kk) {
+                wn[kk] = 0u;
+                fn[kk] = 0u;
+                w2[kk] = 0.0f;
                 if (kk < D2) {
                   const int i = nb_of(j1, meta1, kk);
-                  sP[(1 + kk) * 32 + lane] = swg[i];
-                  sP[(7 + kk) * 32 + lane] = fmg[i];
-                  sP[(13 + kk) * 32 + lane] = __float_as_uint(__ldg(Jp0 + (int64_t)kk * G.nsp + v1));
+                  wn[kk] = swg[i];
+                  fn[kk] = fmg[i] & pm;
+                  w2[kk] = 2.0f * __ldg(Jp0 + (int64_t)kk * G.nsp + v1);
+                  dirtym |= fn[kk];
                 }
-#pragma unroll
-              for (int q = 0; q < LPS / 4; ++q) cp_async16(sF + lane * LPS + 4 * q, Fg + (size_t)v1 * LPS + 4 * q);
-            }
-            sSeg[lane] = 0u;
-            // list the pending pairs: exclusive prefix of the per-position counts
-            const int cnt = __popc(pm);
-            int inc = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-              const int y = __shfl_up_sync(0xffffffffu, inc, o);
-              if (lane >= o) inc += y;
-            }
-            const int total = __shfl_sync(0xffffffffu, inc, 31);
-            {
-              uint32_t m = pm;
-              int o = inc - cnt;
-              while (m) {
-                const int b = __ffs(m) - 1;
-                m &= m - 1u;
-                sL[o++] = (uint16_t)((lane << 5) | b);
               }
-            }
-            cp_async_wait_all();
-            __syncwarp();
-            // the flips of the neighbours since this spin's previous visit, in CSR
-            // order; with none the field and the decision are unchanged
-            for (int t = lane; t < total; t += 32) {
-              const uint32_t e = sL[t];
-              const int pos = (int)(e >> 5), l = (int)(e & 31u);
-              float f = sF[pos * LPS + l];
-              bool dirty = false;
+              float *Frow = Fg + (size_t)v1 * LPS;
 #pragma unroll
-              for (int kk = 0; kk < 6; ++kk)
-                if (kk < D2 && ((sP[(7 + kk) * 32 + pos] >> l) & 1u)) {
-                  const float w2 = 2.0f * __uint_as_float(sP[(13 + kk) * 32 + pos]);
-                  f = __fadd_rn(f, ((sP[(1 + kk) * 32 + pos] >> l) & 1u) ? w2 : -w2);
-                  dirty = true;
+              for (int r0 = 0; r0 < LPS; r0 += 4) {
+                if (!((dirtym >> r0) & 0xfu)) continue;
+                const float4 f4 = *reinterpret_cast<const float4 *>(Frow + r0);
+                float o[4] = {f4.x, f4.y, f4.z, f4.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                  const int r = r0 + q;
+                  if (!((dirtym >> r) & 1u)) continue;
+                  float f = o[q];
+#pragma unroll
+                  for (int kk = 0; kk < 6; ++kk)
+                    if ((fn[kk] >> r) & 1u) f = __fadd_rn(f, ((wn[kk] >> r) & 1u) ? w2[kk] : -w2[kk]);
+                  o[q] = f;
+                  if (((wj1 >> r) & 1u) ? (f < 0.0f) : (f > 0.0f)) seg |= 1u << r;
                 }
-              if (dirty) {
-                Fg[(size_t)(c0 + base + pos) * LPS + l] = f;
-                const bool up = (sP[pos] >> l) & 1u;
-                if (up ? (f < 0.0f) : (f > 0.0f)) atomicOr(&sSeg[pos], 1u << l);
+                *reinterpret_cast<float4 *>(Frow + r0) = make_float4(o[0], o[1], o[2], o[3]);
               }
-            }
-            __syncwarp();
-            const uint32_t seg = need1 ? sSeg[lane] : 0u;
-            if (need1) {
               if (seg) {
                 swg[j1] = wj1 ^ seg;
-                for (int kk = 0; kk < D2; ++kk) atomicOr(&pendg[nb_of(j1, meta1, kk)], seg);
+                for (int kk = 0; kk < D2; ++kk) {
+                  const int nb = nb_of(j1, meta1, kk);
+                  atomicOr(&pendg[nb], seg);
+                  if (cf_oth) cf_oth[2 * (nb >> 6)] = 1;
+                }
               }
               if (seg || fm1) fmg[j1] = seg;
             }
+            if (cf_own) {
+              const bool fl = __any_sync(0xffffffffu, seg != 0u);
+              if (lane == 0) cf_own[base >> 5] = fl ? (uint16_t)0x0100 : (uint16_t)0;
+            }
             anyg |= seg;
             my_flips += __popc(seg);
-            __syncwarp();  // staging read before the next batch overwrites it
             continue;
           }
-          // refresh sweep: every pair of every position.  The position lane forms
-          // the site's terms once - fixed-point integers when the sum is exact,
-          // else the FP32 values for the FP64 path - and stages them with the
-          // neighbour words; the per-replica steps read shared memory only.
-          uint32_t *sW = wsm;                                        // [32] words
-          uint32_t *sN = wsm + 32;                                   // [6][32] neighbour words
-          int64_t *sT = reinterpret_cast<int64_t *>(wsm + 224);      // [7][32] terms (kk 0..5, field)
-          int32_t *sU = reinterpret_cast<int32_t *>(wsm + 672);      // [32] unit exponent, -1: FP64 path
-          uint32_t *sG = wsm + 704;                                  // [32] flips per position
-          sG[lane] = 0u;
+          // refresh sweep: every pair of every position, site-parallel.  The
+          // position lane forms its site's terms once - fixed-point integers
+          // when the sum is exact, else the FP32 values for the FP64 path - and
+          // evaluates all LPS replicas of the site from registers, writing the
+          // fields four replicas at a time.
+          uint32_t segr = 0u;
           if (need1) {
-            sW[lane] = swg[j1];
+            const uint32_t wj1 = swg[j1];
             const float hj = __ldg(hf + j1);
             float jw[6];
+            uint32_t wn[6];
             XRange xr;
             xr_see(xr, hj);
 #pragma unroll
             for (int kk = 0; kk < 6; ++kk) {
               jw[kk] = 0.0f;
+              wn[kk] = 0u;
               if (kk < D2) {
-                sN[kk * 32 + lane] = swg[nb_of(j1, meta1, kk)];
+                wn[kk] = swg[nb_of(j1, meta1, kk)];
                 jw[kk] = __ldg(Jp0 + (int64_t)kk * G.nsp + v1);
                 xr_see(xr, jw[kk]);
               }
             }
-            const bool ex = xr_exact(xr);
-            const int u = xr.emax < 0 ? 24 : xr.emin;
-            sU[lane] = ex ? u : -1;
-            sT[6 * 32 + lane] = ex ? xr_term(hj, u) : (int64_t)__float_as_uint(hj);
+            float *Frow = Fg + (size_t)v1 * LPS;
+            uint32_t seg = 0u;
+            if (xr_exact(xr)) {
+              // from scratch, exactly: f = (h + sum_k J_k) - sum over the
+              // neighbours pointing down of 2 J_k, in fixed point with the
+              // site's unit, rounded once to FP32
+              const int u = xr.emax < 0 ? 24 : xr.emin;
+              int64_t base0 = xr_term(hj, u), t2[6];
 #pragma unroll
-            for (int kk = 0; kk < 6; ++kk)
-              if (kk < D2) sT[kk * 32 + lane] = ex ? xr_term(jw[kk], u) : (int64_t)__float_as_uint(jw[kk]);
-          }
-          __syncwarp();
-          while (todo) {
-            uint32_t t = todo;
-            for (int q = 0; q < sub; ++q) t &= t - 1u;
-            const int src = t ? __ffs(t) - 1 : 31;
-            const bool valid = t != 0u;
-            for (int q = 0; q < SPW; ++q) todo &= todo - 1u;
-            const int v = c0 + base + src;
-            const uint32_t wj = sW[src];
-            const bool up = (wj >> ln) & 1u;
-            bool flip = false;
-            if (valid) {
-              // from scratch: the FP64 sum rounded to FP32 (exact fixed point when
-              // the exponent range allows it, else FP64)
-              float f;
-              const int u = sU[src];
-              if (u >= 0) {
-                int64_t acc = sT[6 * 32 + src];
-#pragma unroll
-                for (int kk = 0; kk < 6; ++kk)
-                  if (kk < D2) {
-                    const int64_t tt = sT[kk * 32 + src];
-                    acc += ((sN[kk * 32 + src] >> ln) & 1u) ? tt : -tt;
-                  }
-                f = xr_round(acc, u);
-              } else {
-                double acc = (double)__uint_as_float((uint32_t)sT[6 * 32 + src]);
-#pragma unroll
-                for (int kk = 0; kk < 6; ++kk)
-                  if (kk < D2) {
-                    const double w = (double)__uint_as_float((uint32_t)sT[kk * 32 + src]);
-                    acc = __dadd_rn(acc, ((sN[kk * 32 + src] >> ln) & 1u) ? w : -w);
-                  }
-                f = __double2float_rn(acc);
+              for (int kk = 0; kk < 6; ++kk) {
+                const int64_t t = kk < D2 ? xr_term(jw[kk], u) : 0;
+                base0 += t;
+                t2[kk] = 2 * t;
               }
-              Fg[(size_t)v * LPS + ln] = f;
-              flip = (up ? (f < 0.0f) : (f > 0.0f)) && ((active >> ln) & 1u);
+              ISING_REFRESH_UNROLL
+              for (int r0 = 0; r0 < LPS; r0 += 4) {
+                float o[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                  const int r = r0 + q;
+                  int64_t acc = base0;
+#pragma unroll
+                  for (int kk = 0; kk < 6; ++kk)
+                    if (!((wn[kk] >> r) & 1u)) acc -= t2[kk];
+                  o[q] = xr_round_int(acc, u);
+                  if (((wj1 >> r) & 1u) ? (o[q] < 0.0f) : (o[q] > 0.0f)) seg |= 1u << r;
+                }
+                *reinterpret_cast<float4 *>(Frow + r0) = make_float4(o[0], o[1], o[2], o[3]);
+              }
+            } else {
+              // the FP64 sum in the defined order (field, then the row's entries)
+#pragma unroll 1
+              for (int r0 = 0; r0 < LPS; r0 += 4) {
+                float o[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                  const int r = r0 + q;
+                  double acc = (double)hj;
+#pragma unroll
+                  for (int kk = 0; kk < 6; ++kk)
+                    if (kk < D2) acc = __dadd_rn(acc, ((wn[kk] >> r) & 1u) ? (double)jw[kk] : -(double)jw[kk]);
+                  o[q] = __double2float_rn(acc);
+                  if (((wj1 >> r) & 1u) ? (o[q] < 0.0f) : (o[q] > 0.0f)) seg |= 1u << r;
+                }
+                *reinterpret_cast<float4 *>(Frow + r0) = make_float4(o[0], o[1], o[2], o[3]);
+              }
             }
-            const uint32_t m = __ballot_sync(0xffffffffu, flip);
-            const uint32_t seg = (m >> (sub * LPS)) & lmask;
-            if (valid && ln == 0) sG[src] = seg;
+            seg &= active;
+            segr = seg;
             anyg |= seg;
-          }
-          __syncwarp();
-          // the flips are applied per position, all 32 lanes at once (words of
-          // this class, pending marks of the other class, flip masks: nothing the
-          // steps above read)
-          if (need1) {
-            const uint32_t seg = sG[lane];
+            // apply: words of this class, pending marks of the other class,
+            // flip masks (nothing another lane of this visit reads)
             if (seg) {
-              swg[j1] = sW[lane] ^ seg;
-              for (int kk = 0; kk < D2; ++kk) atomicOr(&pendg[nb_of(j1, meta1, kk)], seg);
+              swg[j1] = wj1 ^ seg;
+              for (int kk = 0; kk < D2; ++kk) {
+                const int nb = nb_of(j1, meta1, kk);
+                atomicOr(&pendg[nb], seg);
+                if (cf_oth) cf_oth[2 * (nb >> 6)] = 1;
+              }
             }
             if (seg || fm1) fmg[j1] = seg;
             my_flips += __popc(seg);
+          }
+          if (cf_own) {
+            const bool fl = __any_sync(0xffffffffu, segr != 0u);
+            if (lane == 0) cf_own[base >> 5] = fl ? (uint16_t)0x0100 : (uint16_t)0;
           }
           __syncwarp();  // staging read before the next batch overwrites it
         }
@@ -595,7 +629,7 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
                     const int64_t tt = xr_term(__ldg(hJf + e), u);
                     acc += hyper_neg(e) ? -tt : tt;
                   }
-                  f = xr_round(acc, u);
+                  f = xr_round_int(acc, u);
                 } else {
                   double acc = (double)hj;
                   for (uint32_t kk = k0; kk < k1; ++kk) {
@@ -709,13 +743,43 @@ __global__ void __launch_bounds__(kST) sweep_visit(SweepArgs A, int32_t c) {
   if (tid == 0 && my_flips) atomicAdd(A.stats + 1, my_flips);
 }
 
+// Warp sums of NV per-lane values at once: NV halving exchange steps leave
+// each lane one value index, the remaining steps add across the other lanes;
+// lane r < NV returns the warp total of v[r], lanes r >= NV return 0.
+// 2 NV - 1 shuffles instead of NV * 5.
+template <int NV>
+__device__ __forceinline__ int64_t warp_sums_to_lanes(int64_t (&v)[NV], int lane) {
+  constexpr int LOG = NV == 32 ? 5 : (NV == 16 ? 4 : (NV == 8 ? 3 : (NV == 4 ? 2 : (NV == 2 ? 1 : 0))));
+  static_assert((1 << LOG) == NV, "NV must be a power of two <= 32");
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int o = 16 >> s;
+    if (s < LOG) {
+      const int h = NV >> (s + 1);
+      const bool upper = (lane & o) != 0;
+#pragma unroll
+      for (int i = 0; i < NV / 2; ++i)
+        if (i < h) {
+          const int64_t send = upper ? v[i] : v[i + h];
+          const int64_t keep = upper ? v[i + h] : v[i];
+          v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    } else {
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+    }
+  }
+  // lane L now holds the total of value index (L >> (5 - LOG)) & (NV - 1)
+  const int64_t t = __shfl_sync(0xffffffffu, v[0], (lane << (5 - LOG)) & 31);
+  return lane < NV ? t : 0;
+}
+
 // Energies of the lanes whose round ended (all lanes of the group at once,
 // lane-parallel; exact int64 for integer couplings, exact 64-bit fixed point
 // for FP32 couplings when InstDesc::ebase >= 0, else FP64), then - in the last
 // CTA to finish - the round's bookkeeping: minima, best energies, the next
 // descent's lanes.  Per-CTA partials are added in CTA order (deterministic).
 template <bool FLOAT, int LPS, bool LAT>
-__global__ void __launch_bounds__(kST) sweep_energy(SweepArgs A) {
+__global__ void __launch_bounds__(kST, 4) sweep_energy(SweepArgs A) {
   __shared__ double s_red[kST / 32][32];
   __shared__ __align__(8) uint32_t s_stage[LAT ? (kST / 32) * 704 : 1];
   __shared__ bool s_last;
@@ -738,7 +802,59 @@ __global__ void __launch_bounds__(kST) sweep_energy(SweepArgs A) {
     unsigned long long accl = 0;
     if (S.round_end || S.final_pass) {
       const uint32_t *swg = A.sw + (size_t)g * n;
-      if constexpr (LAT) {
+      if (LAT && LPS <= 16 && A.en_fast && (!FLOAT || fx)) {
+        // Lattice, site-parallel: lane = position holds the site's word, its
+        // forward neighbours' words and its terms (fixed-point integers or
+        // integers) in registers and adds its contribution to each of the LPS
+        // replicas' int64 sums; one exchange per warp then gives lane r the
+        // warp total of replica r.  Integer sums: the order does not matter.
+        constexpr int NV = LPS <= 16 ? LPS : 16;
+        int64_t acc[NV];
+#pragma unroll
+        for (int r = 0; r < NV; ++r) acc[r] = 0;
+        const int D2 = 2 * I.lat_d;
+        for (int base = (blockIdx.x * nw + warp) * 32; base < n; base += gridDim.x * nw * 32) {
+          const int v = base + lane;
+          if (v >= n) continue;
+          const int j = __ldg(G.order + I.spin_off + v);
+          const uint32_t meta = __ldg(G.meta + I.spin_off + v);
+          const uint32_t wj = swg[j];
+          int64_t th, t[6];
+          uint32_t wn[6];
+          if (FLOAT) th = xr_term(__ldg(reinterpret_cast<const float *>(G.h) + I.spin_off + j), ub);
+          else th = __ldg(reinterpret_cast<const int8_t *>(G.h) + I.spin_off + j);
+#pragma unroll
+          for (int kk = 0; kk < 6; ++kk) {
+            t[kk] = 0;
+            wn[kk] = 0u;
+            if (kk < D2) {
+              const int i = lat_nbr(j, meta, kk, L);
+              if (i > j) {
+                wn[kk] = swg[i];
+                const int64_t jp = (int64_t)kk * G.nsp + I.spin_off + v;
+                t[kk] = FLOAT ? xr_term(__ldg(reinterpret_cast<const float *>(G.Jpos) + jp), ub)
+                              : (int64_t)__ldg(reinterpret_cast<const int8_t *>(G.Jpos) + jp);
+              }
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < NV; ++r) {
+            const uint32_t bj = (wj >> r) & 1u;
+            int64_t e = bj ? -th : th;
+#pragma unroll
+            for (int kk = 0; kk < 6; ++kk)
+              if (kk < D2) e += ((((wn[kk] >> r) & 1u) ^ bj) != 0u) ? t[kk] : -t[kk];
+            acc[r] += e;
+          }
+        }
+        const int64_t tot = warp_sums_to_lanes<NV>(acc, lane);
+        if (FLOAT) {
+          acci = (long long)(tot >> 32);
+          accl = (unsigned long long)(uint32_t)tot;
+        } else {
+          acci = (long long)tot;
+        }
+      } else if constexpr (LAT) {
         // Lattice: lane = position stages the position's word, its forward
         // neighbours' words (those with a larger index, so each bond counts
         // once) and its terms - fixed-point integers, FP32 values or integers -
@@ -962,6 +1078,9 @@ __global__ void __launch_bounds__(kST) sweep_energy(SweepArgs A) {
       double a = 0.0;
       long long hi = 0;
       unsigned long long lo = 0;
+      // (independent loads: unrolled so that several are in flight at once;
+      // the additions keep their order)
+#pragma unroll 8
       for (int cta = warp; cta < (int)gridDim.x; cta += nw) {
         const size_t o = ((size_t)cta * A.G + g) * 32 + lane;
         if (FLOAT && !fx) {
@@ -1149,8 +1268,8 @@ void debug_step(const char *what, int c, cudaStream_t s) {
   std::fflush(stderr);
 }
 
-constexpr size_t visit_smem(int mode, int lps, bool lat) {
-  return (mode == 1 && lat) ? (size_t)(kST / 32) * (48 * lps + 640) * 4 : 0;
+constexpr size_t visit_smem(int, int, bool) {
+  return 0;  // the visits keep their per-position data in registers
 }
 
 template <int MODE, int LPS, bool LAT>
@@ -1175,7 +1294,7 @@ void enqueue_sweep(const SweepArgs &A, int mode, int ncls, int grid_v, cudaStrea
     else if (mode == 1) enqueue_visit<1, LPS, LAT>(A, c, grid_v, s);
     else enqueue_visit<2, LPS, LAT>(A, c, grid_v, s);
   }
-  sweep_end<<<1, 32, 0, s>>>(A);
+  sweep_end<<<(A.G + 7) / 8, 256, 0, s>>>(A);
   debug_step("end", 0, s);
   if (round_end) enqueue_round_end<LPS, LAT>(A, mode, s);
 }
@@ -1200,6 +1319,20 @@ cudaError_t preload(int mode) {
   return e;
 }
 
+// Resident CTAs per SM of the visit kernel of this configuration.
+template <int LPS, bool LAT>
+int visit_ctas_per_sm(int mode) {
+  int k = 0;
+  cudaError_t e;
+  if (mode == 0)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, sweep_visit<0, LPS, LAT>, kST, visit_smem(0, LPS, LAT));
+  else if (mode == 1)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, sweep_visit<1, LPS, LAT>, kST, visit_smem(1, LPS, LAT));
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, sweep_visit<2, LPS, LAT>, kST, visit_smem(2, LPS, LAT));
+  return (e == cudaSuccess && k > 0) ? k : 8;
+}
+
 template <int LPS, bool LAT>
 cudaError_t run_instance(ising_handle *h, SweepArgs A, int mode, cudaStream_t s) {
   SweepState &S = family_state<SweepState>(h->sweep_st);
@@ -1211,12 +1344,15 @@ cudaError_t run_instance(ising_handle *h, SweepArgs A, int mode, cudaStream_t s)
     for (int c = 0; c < I.ncls; ++c)
       maxcls = std::max(maxcls, h->h_cls[I.cls_off + c + 1] - h->h_cls[I.cls_off + c]);
   const int64_t items = mode == 2 ? (int64_t)A.G * maxcls : (int64_t)A.G * ((maxcls + 32 / LPS - 1) / (32 / LPS)) * 32;
-  const int grid_v = (int)std::max<int64_t>(1, std::min<int64_t>((items + kST - 1) / kST, (int64_t)h->sm_count * 8));
+  cudaError_t e0 = preload<LPS, LAT>(mode);
+  if (e0 != cudaSuccess) return e0;
+  // one wave of resident CTAs at most: the visits loop over their positions,
+  // so a larger grid only adds CTA start-up and barrier cost per visit
+  const int grid_v = (int)std::max<int64_t>(
+      1, std::min<int64_t>((items + kST - 1) / kST, (int64_t)h->sm_count * visit_ctas_per_sm<LPS, LAT>(mode)));
   if (sweep_debug())
     std::fprintf(stderr, "[sweep] n=%d ncls=%d G=%d LPS=%d mode=%d grid_v=%d grid_e=%d lattice=%d seq=%d\n", I.n,
                  ncls, A.G, LPS, mode, grid_v, A.grid_e, A.lattice, A.sequential);
-  cudaError_t e0 = preload<LPS, LAT>(mode);
-  if (e0 != cudaSuccess) return e0;
   sweep_init<<<1, 32, 0, s>>>(A);
   debug_step("init", 0, s);
   sweep_restart<LPS><<<A.grid_e, kST, 0, s>>>(A);
@@ -1247,10 +1383,11 @@ cudaError_t run_instance(ising_handle *h, SweepArgs A, int mode, cudaStream_t s)
   cudaGraphExec_t exec = nullptr;
   if (use_graph) {
     // everything the captured launches bake in besides the handle's own arrays
-    char key[256];
-    std::snprintf(key, sizeof key, "%d/%d/%d/%d/%d/%d/%d/%d/%d/%d/%llu/%p/%d/%d/%d/%d", A.b, A.R, A.G, A.LPS,
+    char key[320];
+    std::snprintf(key, sizeof key, "%d/%d/%d/%d/%d/%d/%d/%d/%d/%d/%llu/%p/%d/%d/%d/%d/%p/%d/%d", A.b, A.R, A.G, A.LPS,
                   A.max_sweeps, A.restarts, A.budget, A.refresh, A.sequential, A.lattice,
-                  (unsigned long long)A.seed, (void *)A.sw, mode, grid_v, chunk, ncls);
+                  (unsigned long long)A.seed, (void *)A.sw, mode, grid_v, chunk, ncls, (void *)A.cflag, A.nchunk,
+                  A.en_fast);
     auto it = S.graphs.find(key);
     if (it == S.graphs.end()) {
       SweepGraph sg;
@@ -1338,8 +1475,10 @@ cudaError_t launch_sweep(ising_handle *h, const ising_search_params *p, int32_t 
   // scratch: sw, fm, bw, pend [G][nmax]; F [G][nmax][LPS]; gs [G]; partial [2][grid_e][G][32]; counter; done
   const size_t words = (size_t)G * h->nmax;
   auto up256 = [](size_t b) { return (b + 255) / 256 * 256; };
+  const int32_t nchunk = (h->nmax / 2 + 31) / 32 + 1;
+  const size_t cflag_bytes = (size_t)G * 2 * nchunk * sizeof(uint16_t);
   const size_t need = 4 * up256(words * 4) + (fl ? up256(words * LPS * 4) : 0) + up256(G * sizeof(GroupState)) +
-                      up256((size_t)grid_e * G * 32 * 16) + 2 * 256;
+                      up256((size_t)grid_e * G * 32 * 16) + 2 * 256 + up256(cflag_bytes);
   cudaError_t e;
   if (need > S.bytes) {
     for (auto &kv : S.graphs) {  // captured against the old scratch
@@ -1382,6 +1521,8 @@ cudaError_t launch_sweep(ising_handle *h, const ising_search_params *p, int32_t 
   A.partial = (double *)take((size_t)grid_e * G * 32 * 16);  // FP64 sums, or fixed-point high | low halves
   A.counter = (unsigned int *)take(64);
   A.all_done = (int32_t *)take(64);
+  uint16_t *cflag_mem = (uint16_t *)take(cflag_bytes);
+  A.nchunk = nchunk;
   A.stats = h->d_stats;
   A.spins = spins;
   A.energy = E;
@@ -1392,8 +1533,22 @@ cudaError_t launch_sweep(ising_handle *h, const ising_search_params *p, int32_t 
     A.b = b;
     A.seed = seeds_host[b];
     A.lattice = (A.I.lat_d > 0 && !A.sequential) ? 1 : 0;
+    {
+      // site-parallel energies: at most `per_warp` terms, each below 2^ebits,
+      // go into one int64 before the high/low split of the block reduction
+      const int64_t sites_lane = ((int64_t)A.I.n + (int64_t)grid_e * kST - 1) / ((int64_t)grid_e * kST);
+      const int64_t per_warp = 32 * sites_lane * (A.I.lat_d + 1);
+      int lg = 0;
+      while (((int64_t)1 << lg) <= per_warp) ++lg;
+      A.en_fast = (A.lattice && LPS <= 16 && A.I.ebits >= 0 && A.I.ebits + lg <= 62) ? 1 : 0;
+    }
     if ((e = cudaMemsetAsync(A.fm, 0, words * 4, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(A.pend, 0, words * 4, s)) != cudaSuccess) return e;
+    // chunk flags: the two-class parity colouring of an even-sided lattice puts
+    // site j at class position j >> 1 (class order is index order)
+    const bool chunked = A.lattice && h->lat_parity && A.I.ncls == 2 && A.I.lat_L % 2 == 0 && (mode == 1 || mode == 2);
+    A.cflag = chunked ? cflag_mem : nullptr;
+    if (chunked && (e = cudaMemsetAsync(cflag_mem, 0, cflag_bytes, s)) != cudaSuccess) return e;
     if (A.lattice) {
       if (LPS == 32) e = run_instance<32, true>(h, A, mode, s);
       else if (LPS == 16) e = run_instance<16, true>(h, A, mode, s);
