@@ -2,14 +2,17 @@
 bench.py times (the same instances, seeds, replica counts, search parameters
 and kernel planner):
 
-* sampled outputs the oracle can compute one by one: the first replicas (or a
-  few whole instances) are recomputed by the oracle and must match (spins bit
-  for bit, energies exactly for integer couplings and within 1e-9 for FP32);
+* sampled outputs the oracle can compute one by one: replica ranges spread
+  over the replica words and groups (or a few whole instances) are recomputed
+  by the oracle and must match (spins bit for bit, energies exactly for
+  integer couplings and within 1e-9 for FP32);
 * properties that hold at any size, on every replica: the returned energy is
   the oracle's energy of the returned spins, and a replica with a converged
   descent returns a 1-flip local minimum (s_i f_i >= 0; for FP32 fields within
   the fields' rounding, 1e-4).
 """
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import pytest
 
@@ -41,14 +44,26 @@ def _search(name):
     return insts, R, kw, seeds, h, res
 
 
-def _check_sample(inst, b, seed, R_sample, kw, sp, E, minima, exact):
-    s, Eo, m, _ = oracle.descent(inst, seed, b, R_sample, **kw)
-    assert np.array_equal(sp[:R_sample], s), f"spins differ (instance {b})"
-    assert np.array_equal(minima[:R_sample], m), f"minima differ (instance {b})"
+def _check_sample(inst, b, seed, R_sample, kw, sp, E, minima, exact, first=0):
+    """Replicas first .. first + R_sample - 1 against the oracle."""
+    s, Eo, m, _ = oracle.descent(inst, seed, b, R_sample, first_replica=first, **kw)
+    sl = slice(first, first + R_sample)
+    assert np.array_equal(sp[sl], s), f"spins differ (instance {b}, replicas {first}..)"
+    assert np.array_equal(minima[sl], m), f"minima differ (instance {b}, replicas {first}..)"
     if exact:
-        assert np.array_equal(E[:R_sample], Eo)
+        assert np.array_equal(E[sl], Eo)
     else:
-        np.testing.assert_allclose(E[:R_sample], Eo, rtol=1e-9, atol=1e-9)
+        np.testing.assert_allclose(E[sl], Eo, rtol=1e-9, atol=1e-9)
+
+
+def _check_ranges(inst, seed, kw, sp, E, minima, exact, ranges):
+    """Several replica ranges, each in its own host thread (the oracle's C
+    calls release the GIL)."""
+    with ThreadPoolExecutor(max_workers=len(ranges)) as ex:
+        futs = [ex.submit(_check_sample, inst, 0, seed, cnt, kw, sp, E, minima, exact, first)
+                for first, cnt in ranges]
+        for f in futs:
+            f.result()
 
 
 def _check_properties(inst, sp, E, minima, exact, tol=0.0):
@@ -72,10 +87,12 @@ def test_fullsize_lattice_16x16():
 
 
 def test_fullsize_lattice_32cubed_1024_replicas():
+    """Three whole 32-replica words (every bit position: the first, a middle
+    and the last word of the multi-spin coding) against the oracle."""
     insts, R, kw, seeds, h, res = _search("c2")
     sp = h.spins_of(res.spins, 0, R).cpu().numpy()
     E, m = res.energy[0].cpu().numpy(), res.minima[0].cpu().numpy()
-    _check_sample(insts[0], 0, seeds[0], 8, kw, sp, E, m, True)
+    _check_ranges(insts[0], seeds[0], kw, sp, E, m, True, [(0, 32), (496, 32), (992, 32)])
     _check_properties(insts[0], sp, E, m, True)
     h.close()
 
@@ -90,26 +107,40 @@ def test_fullsize_chimera_batch_4096():
 
 
 def test_fullsize_dense_sk_4096():
+    """256 replicas, eight in each of the 32 tensor-core clusters of 128: the
+    returned energy against the oracle's FP64 energy of the returned spins
+    (1e-6 relative) and the 1-flip minimum property within the FP32 field
+    rounding."""
     insts, R, kw, seeds, h, res = _search("c4")
     assert res.stats["minima"] == R and res.stats["descents"] == R
     sp = h.spins_of(res.spins, 0, R).cpu().numpy()
     E = res.energy[0].cpu().numpy()
     oi = oracle.OracleInstance(insts[0])
-    pick = np.array([0, 1, 127, 128, 2048, R - 1])
-    Eo = oracle.energies(oi, sp[pick])
-    assert np.max(np.abs(E[pick] - Eo) / np.abs(Eo)) <= 1e-6
-    for r in pick:
+    pick = np.array(sorted({128 * k + 16 * j + (k % 16) for k in range(R // 128) for j in range(8)}))
+    assert len(pick) == 256
+
+    def one(r):
+        Eo = oracle.energy(oi, sp[r])
         f = oracle.local_fields(oi, sp[r])
-        assert np.all(sp[r] * f >= -1e-4)
+        return abs(E[r] - Eo) / abs(Eo), float(np.min(sp[r] * f))
+
+    with ThreadPoolExecutor(max_workers=16) as ex:
+        out = list(ex.map(one, pick))
+    rel = max(o[0] for o in out)
+    assert rel <= 1e-6, rel
+    assert min(o[1] for o in out) >= -1e-4
     h.close()
 
 
 @pytest.mark.parametrize("name,exact,tol", [("c5", False, 1e-4), ("c5i", True, 0.0)])
 def test_fullsize_lattice_100cubed(name, exact, tol):
+    """Four of the 16 replicas (first, two middle, last lane of the group)
+    through their whole 1000-sweep budgets against the oracle, one host thread
+    each; properties on all 16."""
     insts, R, kw, seeds, h, res = _search(name)
     sp = h.spins_of(res.spins, 0, R).cpu().numpy()
     E, m = res.energy[0].cpu().numpy(), res.minima[0].cpu().numpy()
-    _check_sample(insts[0], 0, seeds[0], 1, kw, sp, E, m, exact)
+    _check_ranges(insts[0], seeds[0], kw, sp, E, m, exact, [(0, 1), (5, 1), (10, 1), (R - 1, 1)])
     _check_properties(insts[0], sp, E, m, exact, tol)
     h.close()
 
