@@ -198,7 +198,7 @@ def oracle_units(name, insts, R, kw):
     if name in ("c5", "c5i"):
         okw["sweep_budget"] = 40
         note = "the first 40 sweeps of each replica's 1000-sweep budget"
-    per = 8 if (len(insts) == 1 and insts[0].n <= 4096 and R >= 8 and name != "c4") else 1
+    per = 8 if (max(i.n for i in insts) <= 4096 and R >= 8 and name != "c4") else 1
     units = [(b, r0, min(per, R - r0)) for b in range(len(insts)) for r0 in range(0, R, per)]
     return units, okw, note
 
@@ -451,6 +451,7 @@ def main():
     ap.add_argument("--workload", default=HEADLINE)
     ap.add_argument("--per-workload", default=",".join(w for w in ALL_WORKLOADS if w != HEADLINE),
                     help="comma-separated workloads measured as sub-records after the headline ('' for none)")
+    ap.add_argument("--headline-only", action="store_true", help="no sub-records (profiling captures)")
     ap.add_argument("--min-seconds", type=float, default=1.5,
                     help="minimum timed device time of each sub-record")
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
@@ -508,7 +509,7 @@ def main():
     head = gpu_record(args.workload, args, dev, rank, dist, steps=args.steps, plain=not args.no_plain,
                       cpu_seconds=0.0 if args.no_cpu_baseline else args.cpu_seconds)
     subs = {}
-    if world == 1:
+    if world == 1 and not args.headline_only:
         for w in [x for x in args.per_workload.split(",") if x and x != args.workload]:
             try:
                 subs[w] = gpu_record(w, args, dev, 0, None, steps=None, min_seconds=args.min_seconds,
