@@ -108,7 +108,16 @@ typedef enum {
   ISING_ERR_DEVICE = 10        /* a device-side consistency check failed                */
 } ising_status;
 
-typedef enum { ISING_I8 = 0, ISING_F32 = 1 } ising_dtype;
+/* Value type of an instance's couplings, fields and hyper-edge strengths.
+ * ISING_F64 instances (wide coefficients, e.g. the factoring instances of
+ * Sec. VI) run the pass-based search, plain descent (kernel family PLAIN)
+ * and ising_energy; every field, gain and energy is the FP64 value of the
+ * sequential definition: fields h, the CSR row in stored order, then the
+ * hyper-edges ascending, recomputed at every visit in descent; energies as a
+ * compensated (Neumaier) FP64 sum of the terms in the order pairs of row i
+ * (j > i, stored order) and field i for i = 0..n-1, then the hyper-edges.
+ * Other families return ISING_ERR_UNSUPPORTED for them.                     */
+typedef enum { ISING_I8 = 0, ISING_F32 = 1, ISING_F64 = 2 } ising_dtype;
 
 typedef enum { ISING_SCHED_COLOUR = 0, ISING_SCHED_SEQUENTIAL = 1 } ising_schedule;
 
@@ -134,8 +143,9 @@ typedef enum {
 } ising_kernel;
 
 /* One instance.  All pointers are HOST pointers; they are read during
- * ising_create only.  J, h and hyper_J hold int8_t for ISING_I8 and float for
- * ISING_F32.  Exactly one of (row_ptr, col, J) and J_dense is given.           */
+ * ising_create only.  J, h and hyper_J hold int8_t for ISING_I8, float for
+ * ISING_F32 and double for ISING_F64.  Exactly one of (row_ptr, col, J) and
+ * J_dense (ISING_F32 only) is given.                                           */
 typedef struct {
   int32_t n;                    /* number of spins, >= 1                            */
   const int64_t *row_ptr;       /* [n+1], row_ptr[0] = 0, non-decreasing            */
@@ -239,18 +249,6 @@ int32_t ising_plan_kernel(ising_handle *h, int32_t replicas, const ising_search_
  * ISING_KERNEL_AUTO calls use it.  Writes the chosen family to *chosen.        */
 ising_status ising_autotune(ising_handle *h, int32_t replicas, const ising_search_params *p,
                             int32_t *chosen, cudaStream_t stream);
-
-/* Self-check of this library's arithmetic; the paper has no counterpart.  The
- * exact field refresh (the FP64 sum of the field and the couplings, rounded to
- * FP32, formed exactly in 64-bit fixed point when that is exact) rounds its
- * integer sums to FP32 with integer instructions.  This runs `count` cases
- * (values |s| <= 2^53 with constructed rounding ties and their neighbours,
- * random values, 0 and 2^53; units 24 .. 200) on the current device and
- * writes to the HOST *mismatches the number whose result differs, bit for
- * bit, from the hardware int64 -> FP32 conversion scaled by the same power of
- * two.  `seed` picks the cases.  Returns ISING_ERR_INVALID_ARG for count < 0
- * or a NULL pointer; the call waits for its kernel.                          */
-ising_status ising_check_rounding(uint64_t seed, int64_t count, uint64_t *mismatches);
 
 /* Allocation-free energy evaluation.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory - for example a

@@ -18,7 +18,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libising_gb300.so")
 
-I8, F32 = 0, 1
+I8, F32, F64 = 0, 1, 2
+_DT = {"i8": (I8, np.int8), "f32": (F32, np.float32), "f64": (F64, np.float64)}
 SCHED_COLOUR, SCHED_SEQUENTIAL = 0, 1
 KERNEL_AUTO, KERNEL_TILE, KERNEL_MSC, KERNEL_SWEEP, KERNEL_DENSE_TC, KERNEL_PLAIN = range(6)
 DENSE_OWN, DENSE_LIBRARY = 0, 1
@@ -97,8 +98,6 @@ def lib():
             L.ising_set_timing.restype = i32
             L.ising_kernel_times.argtypes = [vp, vp, i32]
             L.ising_kernel_times.restype = i32
-            L.ising_check_rounding.argtypes = [C.c_uint64, C.c_int64, vp]
-            L.ising_check_rounding.restype = i32
             L.ising_status_string.argtypes = [i32]
             L.ising_status_string.restype = C.c_char_p
             _lib = L
@@ -107,7 +106,7 @@ def lib():
 
 EXPORTED = ("ising_create", "ising_energy", "ising_local_search", "ising_plan_kernel",
             "ising_autotune", "ising_destroy", "ising_status_string", "ising_energy_noalloc",
-            "ising_set_timing", "ising_kernel_times", "ising_fm_search", "ising_check_rounding")
+            "ising_set_timing", "ising_kernel_times", "ising_fm_search")
 
 
 def _check(code: int, where: str):
@@ -152,7 +151,7 @@ class Handle:
         self.n_inst = len(insts)
         keep = []
         descs = (_Desc * len(insts))()
-        jdt = np.int8 if self.dtype == "i8" else np.float32
+        code, jdt = _DT[self.dtype]
         for k, inst in enumerate(insts):
             arrs = dict(
                 row_ptr=_arr(inst.row_ptr, np.int64), col=_arr(inst.col, np.int32), J=_arr(inst.J, jdt),
@@ -164,7 +163,7 @@ class Handle:
             descs[k] = _Desc(int(inst.n), _ptr(arrs["row_ptr"]), _ptr(arrs["col"]), _ptr(arrs["J"]),
                              _ptr(arrs["J_dense"]), _ptr(arrs["h"]), nh, _ptr(arrs["hyper_ptr"]),
                              _ptr(arrs["hyper_members"]), _ptr(arrs["hyper_J"]), _ptr(arrs["colour"]),
-                             I8 if self.dtype == "i8" else F32)
+                             code)
         h = C.c_void_p()
         with torch.cuda.device(self.device):
             _check(lib().ising_create(C.cast(descs, C.c_void_p), len(insts), C.byref(h)), "ising_create")
@@ -308,14 +307,6 @@ def energy_noalloc(row_ptr, col, J, h, spins, replicas: int, energy, stream=None
             n, C.c_void_p(row_ptr.data_ptr()), C.c_void_p(col.data_ptr()), C.c_void_p(J.data_ptr()),
             None if h is None else C.c_void_p(h.data_ptr()), dt, C.c_void_p(spins.data_ptr()), replicas,
             C.c_void_p(energy.data_ptr()), C.c_void_p(s.cuda_stream))
-
-
-def check_rounding(seed: int, count: int) -> int:
-    """ising_check_rounding: mismatches of the library's integer-only FP32
-    rounding against the hardware conversion over `count` cases."""
-    out = C.c_uint64(0)
-    _check(lib().ising_check_rounding(seed, count, C.byref(out)), "ising_check_rounding")
-    return int(out.value)
 
 
 def status_string(code: int) -> str:

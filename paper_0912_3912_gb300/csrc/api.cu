@@ -64,12 +64,15 @@ struct HostInst {
   std::vector<int32_t> col;
   std::vector<float> Jf;
   std::vector<int8_t> Ji;
+  std::vector<double> Jd;  // ISING_F64
   std::vector<float> hf;
   std::vector<int8_t> hi;
+  std::vector<double> hd;
   std::vector<int64_t> hptr;
   std::vector<int32_t> hmem;
   std::vector<float> hJf;
   std::vector<int8_t> hJi;
+  std::vector<double> hJd;
   std::vector<int32_t> colour;
   int32_t ncls = 0;
   int32_t max_deg = 0;
@@ -161,10 +164,12 @@ void detect_lattice(HostInst &I) {
   }
 }
 
-double jval(const HostInst &I, int64_t k, bool fl) { return fl ? (double)I.Jf[k] : (double)I.Ji[k]; }
+double jval(const HostInst &I, int64_t k, ising_dtype dt) {
+  return dt == ISING_F64 ? I.Jd[k] : (dt == ISING_F32 ? (double)I.Jf[k] : (double)I.Ji[k]);
+}
 
 ising_status load_desc(const ising_instance_desc &d, ising_dtype dtype, HostInst &I) {
-  const bool fl = dtype == ISING_F32;
+  const bool fl = dtype == ISING_F32, f64 = dtype == ISING_F64;
   if (d.n < 1 || d.n > (1 << 30)) return ISING_ERR_INVALID_ARG;
   if (d.dtype != dtype) return ISING_ERR_INVALID_ARG;
   const int32_t n = d.n;
@@ -199,6 +204,10 @@ ising_status load_desc(const ising_instance_desc &d, ising_dtype dtype, HostInst
       I.Jf.assign((const float *)d.J, (const float *)d.J + nnz);
       for (float w : I.Jf)
         if (!std::isfinite(w)) return ISING_ERR_INVALID_ARG;
+    } else if (f64) {
+      I.Jd.assign((const double *)d.J, (const double *)d.J + nnz);
+      for (double w : I.Jd)
+        if (!std::isfinite(w)) return ISING_ERR_INVALID_ARG;
     } else {
       I.Ji.assign((const int8_t *)d.J, (const int8_t *)d.J + nnz);
     }
@@ -209,7 +218,7 @@ ising_status load_desc(const ising_instance_desc &d, ising_dtype dtype, HostInst
         const int32_t j = I.col[k];
         if (j < 0 || j >= n) return ISING_ERR_INVALID_ARG;
         if (j == i) return ISING_ERR_SELF_LOOP;
-        sorted[k] = {j, jval(I, k, fl)};
+        sorted[k] = {j, jval(I, k, dtype)};
       }
       std::sort(sorted.begin() + I.row[i], sorted.begin() + I.row[i + 1]);
       for (int64_t k = I.row[i] + 1; k < I.row[i + 1]; ++k)
@@ -229,6 +238,13 @@ ising_status load_desc(const ising_instance_desc &d, ising_dtype dtype, HostInst
     if (d.h) {
       std::memcpy(I.hf.data(), d.h, n * sizeof(float));
       for (float v : I.hf)
+        if (!std::isfinite(v)) return ISING_ERR_INVALID_ARG;
+    }
+  } else if (f64) {
+    I.hd.assign(n, 0.0);
+    if (d.h) {
+      std::memcpy(I.hd.data(), d.h, n * sizeof(double));
+      for (double v : I.hd)
         if (!std::isfinite(v)) return ISING_ERR_INVALID_ARG;
     }
   } else {
@@ -256,6 +272,10 @@ ising_status load_desc(const ising_instance_desc &d, ising_dtype dtype, HostInst
     if (fl) {
       I.hJf.assign((const float *)d.hyper_J, (const float *)d.hyper_J + d.n_hyper);
       for (float v : I.hJf)
+        if (!std::isfinite(v)) return ISING_ERR_INVALID_ARG;
+    } else if (f64) {
+      I.hJd.assign((const double *)d.hyper_J, (const double *)d.hyper_J + d.n_hyper);
+      for (double v : I.hJd)
         if (!std::isfinite(v)) return ISING_ERR_INVALID_ARG;
     } else {
       I.hJi.assign((const int8_t *)d.hyper_J, (const int8_t *)d.hyper_J + d.n_hyper);
@@ -298,7 +318,7 @@ ising_status load_desc(const ising_instance_desc &d, ising_dtype dtype, HostInst
   }
   I.ncls = 0;
   for (int32_t c : I.colour) I.ncls = std::max(I.ncls, c + 1);
-  if (I.hptr.size() == 1) detect_lattice(I);
+  if (I.hptr.size() == 1 && !f64) detect_lattice(I);  // (FP64 instances take no lattice path)
   return ISING_OK;
 }
 
@@ -378,6 +398,8 @@ bool tile_fits(const ising_handle *h, int mode) {
 // Kernel family for these arguments (ISING_KERNEL_AUTO resolved), or negative status.
 int32_t resolve_kernel(ising_handle *h, int32_t R, const ising_search_params *p) {
   int32_t k = p->kernel;
+  if (h->dtype == ISING_F64)  // FP64 couplings: the plain family only
+    return (k == ISING_KERNEL_AUTO || k == ISING_KERNEL_PLAIN) ? ISING_KERNEL_PLAIN : -(int32_t)ISING_ERR_UNSUPPORTED;
   if (k == ISING_KERNEL_AUTO) {
     auto it = h->tuned.find(R);
     if (it != h->tuned.end()) return it->second;
@@ -651,10 +673,10 @@ ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
   *out = nullptr;
   if (!descs || n_instances < 1) return ISING_ERR_INVALID_ARG;
   const ising_dtype dtype = descs[0].dtype;
-  if (dtype != ISING_I8 && dtype != ISING_F32) return ISING_ERR_INVALID_ARG;
-  const bool fl = dtype == ISING_F32;
+  if (dtype != ISING_I8 && dtype != ISING_F32 && dtype != ISING_F64) return ISING_ERR_INVALID_ARG;
+  const bool fl = dtype == ISING_F32, f64 = dtype == ISING_F64;
   std::vector<HostInst> hin(n_instances);
-  bool dense = true, msc = !fl, hyper = false;
+  bool dense = true, msc = dtype == ISING_I8, hyper = false;
   int64_t absb = 0;
   for (int32_t b = 0; b < n_instances; ++b) {
     ising_status st = load_desc(descs[b], dtype, hin[b]);
@@ -662,7 +684,7 @@ ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
     const HostInst &I = hin[b];
     dense = dense && descs[b].J_dense != nullptr;
     hyper = hyper || I.hptr.size() > 1;
-    if (!fl) {
+    if (dtype == ISING_I8) {
       for (int8_t w : I.Ji) {
         if (w != 1 && w != -1) msc = false;
         absb += std::abs((int)w);
@@ -692,6 +714,7 @@ ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
   std::vector<int32_t> col, order, cls;
   std::vector<int8_t> Ji, hi, hJi;
   std::vector<float> Jf, hf, hJf;
+  std::vector<double> Jd, hd, hJd;
   std::vector<uint32_t> inc_ptr, hptr;
   std::vector<int32_t> inc_edge, hmem;
   std::vector<std::pair<int32_t, std::vector<int32_t>>> lat_sites;
@@ -710,8 +733,8 @@ ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
     D.lat_d = I.lat_d;
     int32_t emax = -1;
     D.ebase = fl ? energy_base_exponent(I, &emax) : -1;
-    D.fx53 = fp64_exact(I, fl, D.ebase);
-    D.ebits = !fl ? 7 : (D.ebase >= 0 ? 24 + std::max(0, emax - D.ebase) : -1);
+    D.fx53 = f64 ? 0 : fp64_exact(I, fl, D.ebase);  // FP64 instances: the FP64 forms only
+    D.ebits = f64 ? -1 : (!fl ? 7 : (D.ebase >= 0 ? 24 + std::max(0, emax - D.ebase) : -1));
     h->any_lattice = h->any_lattice || I.lat_d > 0;
     h->all_lattice = (b == 0 ? true : h->all_lattice) && I.lat_d > 0;
     h->nmax = std::max(h->nmax, I.n);
@@ -721,6 +744,10 @@ ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
       Jf.insert(Jf.end(), I.Jf.begin(), I.Jf.end());
       hf.insert(hf.end(), I.hf.begin(), I.hf.end());
       hJf.insert(hJf.end(), I.hJf.begin(), I.hJf.end());
+    } else if (f64) {
+      Jd.insert(Jd.end(), I.Jd.begin(), I.Jd.end());
+      hd.insert(hd.end(), I.hd.begin(), I.hd.end());
+      hJd.insert(hJd.end(), I.hJd.begin(), I.hJd.end());
     } else {
       Ji.insert(Ji.end(), I.Ji.begin(), I.Ji.end());
       hi.insert(hi.end(), I.hi.begin(), I.hi.end());
@@ -810,6 +837,9 @@ ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
       ok = upload((float **)&h->d_J, Jf) == cudaSuccess && upload((float **)&h->d_h, hf) == cudaSuccess &&
            upload((float **)&h->d_hJ, hJf) == cudaSuccess;
       ok = ok && upload(&h->d_runit, runit) == cudaSuccess;
+    } else if (f64) {
+      ok = upload((double **)&h->d_J, Jd) == cudaSuccess && upload((double **)&h->d_h, hd) == cudaSuccess &&
+           upload((double **)&h->d_hJ, hJd) == cudaSuccess;
     } else {
       ok = upload((int8_t **)&h->d_J, Ji) == cudaSuccess && upload((int8_t **)&h->d_h, hi) == cudaSuccess &&
            upload((int8_t **)&h->d_hJ, hJi) == cudaSuccess;

@@ -78,30 +78,43 @@ __device__ __forceinline__ float xr_round(int64_t s, int unit) {
   return __ll2float_rn(s) * __int_as_float((unit - 23) << 23);
 }
 
-// The same value with integer instructions only (the int64 -> FP32 conversion
-// runs on the FP64 pipe, a small fraction of the integer rate on this GPU).
-// IEEE-754 round to nearest, ties to even, of |s| to 24 significant bits: with
-// the leading one at bit m, keep bits m .. m-23, round up when the dropped
-// part exceeds half a unit in the last place, or equals it with an odd last
-// bit.  The result is 1.f * 2^(m + unit - 150): biased exponent m + unit - 23,
-// always normal for |s| <= 2^53 and 24 <= unit <= 200 (the range xr_exact
-// admits); a carry out of the rounded significand moves into the exponent.
-__device__ __forceinline__ float xr_round_int(int64_t s, int unit) {
-  if (s == 0) return 0.0f;
-  const uint32_t sign = (uint32_t)((uint64_t)s >> 63);
-  const uint64_t a = sign ? (uint64_t)(-s) : (uint64_t)s;
-  const int m = 63 - __clzll((long long)a);
-  uint32_t sig;
-  if (m <= 23) {
-    sig = (uint32_t)a << (23 - m);
-  } else {
-    const int sh = m - 23;
-    sig = (uint32_t)(a >> sh);
-    const uint64_t rem = a & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-    sig += (rem > half || (rem == half && (sig & 1u))) ? 1u : 0u;
+// ---- FP64 instances ---------------------------------------------------------
+// The energy of one configuration of an ISING_F64 instance, as the C ABI
+// defines it: Neumaier's compensated sum (Neumaier 1974) of the terms
+// -J_ij s_i s_j (row i in stored order, j > i) and -h_i s_i for i = 0..n-1,
+// then -J_e prod_{k in e} s_k over the hyper-edges in order; every step one
+// IEEE FP64 addition (no contraction), by one thread.
+__device__ inline double energy_f64_seq(const DevGraph &G, const InstDesc &I, const int8_t *s) {
+  const double *J = reinterpret_cast<const double *>(G.J);
+  const double *h = reinterpret_cast<const double *>(G.h);
+  const double *hJ = reinterpret_cast<const double *>(G.hJ);
+  double sum = 0.0, comp = 0.0;
+  auto add = [&](double x) {
+    const double t = __dadd_rn(sum, x);
+    if (fabs(sum) >= fabs(x)) comp = __dadd_rn(comp, __dadd_rn(__dsub_rn(sum, t), x));
+    else comp = __dadd_rn(comp, __dadd_rn(__dsub_rn(x, t), sum));
+    sum = t;
+  };
+  for (int i = 0; i < I.n; ++i) {
+    const int64_t gi = I.spin_off + i;
+    for (uint32_t k = G.row[gi], ke = G.row[gi + 1]; k < ke; ++k) {
+      const int j = G.col[k];
+      if (j > i) {
+        const double w = J[k];
+        add(s[i] == s[j] ? -w : w);
+      }
+    }
+    const double hv = h[gi];
+    add(s[i] > 0 ? -hv : hv);
   }
-  const uint32_t bits = (sign << 31) + ((uint32_t)(m + unit - 23) << 23) + (sig - 0x800000u);
-  return __uint_as_float(bits);
+  for (int e = 0; e < I.n_hyper; ++e) {
+    const int64_t ge = I.hyper_off + e;
+    int neg = 0;
+    for (uint32_t q = G.hptr[ge], qe = G.hptr[ge + 1]; q < qe; ++q) neg ^= s[G.hmem[q]] < 0;
+    const double w = hJ[ge];
+    add(neg ? w : -w);
+  }
+  return __dadd_rn(sum, comp);
 }
 
 // ---- exact energies ------------------------------------------------------

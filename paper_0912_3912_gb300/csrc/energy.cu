@@ -2,7 +2,9 @@
 // Eq. 6), int8 spins [instance][replica][spin].  Two passes with a fixed
 // summation order: blocks of kChunk spins (and a proportional share of the
 // hyper-edges) write partial sums; a second kernel adds them in order.
-// FP64 for float couplings; exact int64 for integer couplings.
+// FP64 for float couplings; exact int64 for integer couplings; for FP64
+// couplings one thread per configuration takes the compensated sequential sum
+// the C ABI defines for them.
 #include "device_common.cuh"
 
 namespace isg {
@@ -98,6 +100,17 @@ __global__ void energy_finish_kernel(const int4 *__restrict__ work, int32_t nwor
   (void)nwork;
   (void)R;
 }
+// FP64 instances: the defined sequential compensated sum, one thread per
+// (instance, replica)
+__global__ void energy_f64_kernel(DevGraph G, int32_t n_inst, const int8_t *__restrict__ spins, int32_t R,
+                                  double *E) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n_inst * R) return;
+  const int b = (int)(t / R), r = (int)(t % R);
+  const InstDesc I = G.inst[b];
+  E[t] = energy_f64_seq(G, I, spins + (int64_t)R * I.spin_off + (int64_t)r * I.n);
+}
+
 }  // namespace
 
 void energy_plan_free(ising_handle *h) {
@@ -144,6 +157,11 @@ cudaError_t launch_energy(ising_handle *h, const int8_t *spins, int32_t R, doubl
   }
   const DevGraph G = h->graph();
   const bool fl = h->dtype == ISING_F32;
+  if (h->dtype == ISING_F64) {
+    const int64_t nout = (int64_t)h->n_inst * R;
+    energy_f64_kernel<<<(int)((nout + 127) / 128), 128, 0, s>>>(G, h->n_inst, spins, R, E);
+    return cudaGetLastError();
+  }
   if (fl)
     energy_partial_kernel<true><<<h->en_nwork, kThreads, 0, s>>>(G, spins, R, h->d_en_work, h->d_en_partd, h->d_en_parti);
   else

@@ -61,18 +61,15 @@ struct FmArgs {
   unsigned long long *stats;
 };
 
-__device__ __forceinline__ double coupling(const DevGraph &G, bool fl, int64_t k) {
-  return fl ? (double)__ldg(reinterpret_cast<const float *>(G.J) + k)
-            : (double)__ldg(reinterpret_cast<const int8_t *>(G.J) + k);
+// value k of coupling array p as FP64; ct: 0 int8, 1 FP32, 2 FP64 values
+__device__ __forceinline__ double value_of(const void *p, int ct, int64_t k) {
+  return ct == 2 ? __ldg(reinterpret_cast<const double *>(p) + k)
+                 : (ct == 1 ? (double)__ldg(reinterpret_cast<const float *>(p) + k)
+                            : (double)__ldg(reinterpret_cast<const int8_t *>(p) + k));
 }
-__device__ __forceinline__ double field_h(const DevGraph &G, bool fl, int64_t gi) {
-  return fl ? (double)__ldg(reinterpret_cast<const float *>(G.h) + gi)
-            : (double)__ldg(reinterpret_cast<const int8_t *>(G.h) + gi);
-}
-__device__ __forceinline__ double coupling_e(const DevGraph &G, bool fl, int64_t e) {
-  return fl ? (double)__ldg(reinterpret_cast<const float *>(G.hJ) + e)
-            : (double)__ldg(reinterpret_cast<const int8_t *>(G.hJ) + e);
-}
+__device__ __forceinline__ double coupling(const DevGraph &G, int ct, int64_t k) { return value_of(G.J, ct, k); }
+__device__ __forceinline__ double field_h(const DevGraph &G, int ct, int64_t gi) { return value_of(G.h, ct, gi); }
+__device__ __forceinline__ double coupling_e(const DevGraph &G, int ct, int64_t e) { return value_of(G.hJ, ct, e); }
 // product of the spins of hyper-edge e except `skip` (-1: all)
 __device__ __forceinline__ double hyper_prod(const DevGraph &G, int64_t e, const int8_t *s, int skip) {
   double p = 1.0;
@@ -160,21 +157,28 @@ __device__ __forceinline__ long long fm_energy_fx(const DevGraph &G, const InstD
 }
 
 // E (Eq. 1 extended by Eq. 6) by one warp: pairs once (j > i), fields,
-// hyper-edges; lane partial sums, then the warp sum (a fixed order)
-__device__ __forceinline__ double fm_energy(const DevGraph &G, const InstDesc &I, bool fl, const int8_t *s, int lane) {
+// hyper-edges; lane partial sums, then the warp sum (a fixed order).  FP64
+// instances (ct 2): the sequential compensated sum the C ABI defines for
+// them, by lane 0, the same value in every lane.
+__device__ __forceinline__ double fm_energy(const DevGraph &G, const InstDesc &I, int ct, const int8_t *s, int lane) {
+  if (ct == 2) {
+    double E = 0.0;
+    if (lane == 0) E = energy_f64_seq(G, I, s);
+    return __shfl_sync(0xffffffffu, E, 0);
+  }
   double acc = 0.0;
   for (int i = lane; i < I.n; i += 32) {
     const int64_t gi = I.spin_off + i;
     const double si = (double)s[i];
     for (uint32_t k = __ldg(G.row + gi), ke = __ldg(G.row + gi + 1); k < ke; ++k) {
       const int j = __ldg(G.col + k);
-      if (j > i) acc -= coupling(G, fl, k) * si * (double)s[j];
+      if (j > i) acc -= coupling(G, ct, k) * si * (double)s[j];
     }
-    acc -= field_h(G, fl, gi) * si;
+    acc -= field_h(G, ct, gi) * si;
   }
   for (int e = lane; e < I.n_hyper; e += 32) {
     const int64_t ge = I.hyper_off + e;
-    acc -= coupling_e(G, fl, ge) * hyper_prod(G, ge, s, -1);
+    acc -= coupling_e(G, ct, ge) * hyper_prod(G, ge, s, -1);
   }
   return warp_sum(acc);
 }
@@ -261,14 +265,15 @@ __device__ __forceinline__ void block_max(const FmState &S, int j, int lane) {
 // those of the spins whose fields changed).  M: the arithmetic (kFp64, kFx,
 // kFxSpin); every form computes the same values as FP64 in the definition's
 // order, so all give identical moves.
-template <int M, bool FL>
+template <int M, int FL>
 __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
   constexpr bool INT = M != kFp64;
   using T = std::conditional_t<INT, long long, double>;       // fields
   using TE = std::conditional_t<M == kFx, long long, double>;  // running energy
   extern __shared__ __align__(16) uint8_t fm_smem[];
   const DevGraph &G = A.g;
-  constexpr bool fl = FL;  // FP32 couplings (else int8)
+  constexpr int ct = FL;        // coupling values: 0 int8, 1 FP32, 2 FP64
+  constexpr bool fl = FL == 1;  // FP32 couplings (the integer forms' scaling)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint8_t *base = fm_smem + (size_t)warp * ((fm_warp_bytes(nmax, M) + 15) & ~(size_t)15);
   unsigned long long c_moves = 0, c_passes = 0, c_starts = 0;
@@ -306,7 +311,7 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
         return (double)Ei * scale;
       } else {
         Ei = 0;
-        return fm_energy(G, I, fl, s, lane);
+        return fm_energy(G, I, ct, s, lane);
       }
     };
     double E_all = DBL_MAX;
@@ -340,12 +345,12 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
             }
             f[i] = acc;
           } else {
-            double acc = field_h(G, fl, gi);
+            double acc = field_h(G, ct, gi);
             for (uint32_t kk = __ldg(G.row + gi), ke = __ldg(G.row + gi + 1); kk < ke; ++kk)
-              acc += coupling(G, fl, kk) * (double)s[__ldg(G.col + kk)];
+              acc += coupling(G, ct, kk) * (double)s[__ldg(G.col + kk)];
             for (uint32_t u = __ldg(G.inc_ptr + gi), ue = __ldg(G.inc_ptr + gi + 1); u < ue; ++u) {
               const int64_t e = __ldg(G.inc_edge + u);
-              acc += coupling_e(G, fl, e) * hyper_prod(G, e, s, i);
+              acc += coupling_e(G, ct, e) * hyper_prod(G, e, s, i);
             }
             f[i] = acc;
           }
@@ -410,7 +415,7 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
               const long long t2 = 2 * fx_of(G.J, fl, kk, unit_of(c));
               f[c] += snew > 0 ? t2 : -t2;
             } else {
-              f[c] += coupling(G, fl, kk) * (2.0 * (double)snew);
+              f[c] += coupling(G, ct, kk) * (2.0 * (double)snew);
             }
             if (kk - r0 < (uint32_t)kTouched) S.touched[kk - r0] = (int16_t)c;
           }
@@ -432,7 +437,7 @@ __global__ void __launch_bounds__(kFT, 3) fm_kernel(FmArgs A, int nmax) {
                 const long long w2 = 2 * fx_of(G.hJ, fl, e, unit_of(m));
                 f[m] += minus ? -w2 : w2;
               } else {
-                const double w2 = 2.0 * coupling_e(G, fl, e);
+                const double w2 = 2.0 * coupling_e(G, ct, e);
                 f[m] += w2 * (minus ? -1.0 : 1.0);
               }
             }
@@ -568,6 +573,8 @@ __global__ void __launch_bounds__(kFT, S <= 8 ? 2 : 1) fm_reg_kernel(FmArgs A) {
   extern __shared__ __align__(16) uint8_t fm_smem[];
   const DevGraph &G = A.g;
   constexpr bool fl = FL;
+  constexpr int ct = FL ? 1 : 0;
+  (void)ct;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint8_t *base = fm_smem + (size_t)warp * reg_warp_bytes(S);
   long long *fsc = reinterpret_cast<long long *>(base);  // [32 S] fields at a pass's start
@@ -864,7 +871,7 @@ struct FmPart {
 // Warps per CTA (one search each) and CTAs per SM for instances of up to
 // nmax spins: the most searches per SM that shared memory and registers allow,
 // the larger CTA among equals.
-template <int M, bool FL>
+template <int M, int FL>
 cudaError_t fm_shape(const ising_handle *h, int nmax, int &warps, size_t &smem, int &per_sm) {
   const size_t per_warp = (fm_warp_bytes(nmax, M) + 15) & ~(size_t)15;
   int smem_optin = 0;
@@ -959,9 +966,10 @@ cudaError_t launch_fm(ising_handle *h, int32_t R, const ising_fm_params *fp, int
   // the searches alone would leave the GPU underfilled.
   int warps0 = 0, per_sm0 = 0;
   size_t smem0 = 0;
-  const bool fl = h->dtype == ISING_F32;
-  if ((e = fl ? fm_shape<kFx, true>(h, h->nmax, warps0, smem0, per_sm0)
-              : fm_shape<kFx, false>(h, h->nmax, warps0, smem0, per_sm0)) != cudaSuccess)
+  const bool fl = h->dtype == ISING_F32, f64 = h->dtype == ISING_F64;
+  if ((e = f64  ? fm_shape<kFp64, 2>(h, h->nmax, warps0, smem0, per_sm0)
+           : fl ? fm_shape<kFx, 1>(h, h->nmax, warps0, smem0, per_sm0)
+                : fm_shape<kFx, 0>(h, h->nmax, warps0, smem0, per_sm0)) != cudaSuccess)
     return e;
   const int64_t resident = (int64_t)h->sm_count * per_sm0 * warps0;
   const size_t sp_bytes = ((size_t)R * restarts * h->total_spins + 15) & ~(size_t)15;
@@ -1021,12 +1029,14 @@ cudaError_t launch_fm(ising_handle *h, int32_t R, const ising_fm_params *fp, int
       if (le != cudaSuccess) break;
       reg = work <= (int64_t)h->sm_count * per_sm * warps || fp->reg_kernel == 1;
     }
-    // int8 couplings are always exact in one unit (mode kFx)
+    // int8 couplings are always exact in one unit (mode kFx); FP64 couplings
+    // take the FP64 form
     if (!reg)
-      le = !fl ? fm_shape<kFx, false>(h, nmax, warps, smem, per_sm)
-               : P.mode == kFx ? fm_shape<kFx, true>(h, nmax, warps, smem, per_sm)
-               : P.mode == kFxSpin ? fm_shape<kFxSpin, true>(h, nmax, warps, smem, per_sm)
-                                   : fm_shape<kFp64, true>(h, nmax, warps, smem, per_sm);
+      le = f64 ? fm_shape<kFp64, 2>(h, nmax, warps, smem, per_sm)
+           : !fl ? fm_shape<kFx, 0>(h, nmax, warps, smem, per_sm)
+           : P.mode == kFx ? fm_shape<kFx, 1>(h, nmax, warps, smem, per_sm)
+           : P.mode == kFxSpin ? fm_shape<kFxSpin, 1>(h, nmax, warps, smem, per_sm)
+                               : fm_shape<kFp64, 1>(h, nmax, warps, smem, per_sm);
     if (le != cudaSuccess) break;
     FmArgs A;
     A.g = h->graph();
@@ -1052,14 +1062,16 @@ cudaError_t launch_fm(ising_handle *h, int32_t R, const ising_fm_params *fp, int
       fm_reg_kernel<false, 8><<<grid, warps * 32, smem, ls>>>(A);
     else if (reg)
       fm_reg_kernel<false, 16><<<grid, warps * 32, smem, ls>>>(A);
+    else if (f64)
+      fm_kernel<kFp64, 2><<<grid, warps * 32, smem, ls>>>(A, nmax);
     else if (!fl)
-      fm_kernel<kFx, false><<<grid, warps * 32, smem, ls>>>(A, nmax);
+      fm_kernel<kFx, 0><<<grid, warps * 32, smem, ls>>>(A, nmax);
     else if (P.mode == kFx)
-      fm_kernel<kFx, true><<<grid, warps * 32, smem, ls>>>(A, nmax);
+      fm_kernel<kFx, 1><<<grid, warps * 32, smem, ls>>>(A, nmax);
     else if (P.mode == kFxSpin)
-      fm_kernel<kFxSpin, true><<<grid, warps * 32, smem, ls>>>(A, nmax);
+      fm_kernel<kFxSpin, 1><<<grid, warps * 32, smem, ls>>>(A, nmax);
     else
-      fm_kernel<kFp64, true><<<grid, warps * 32, smem, ls>>>(A, nmax);
+      fm_kernel<kFp64, 1><<<grid, warps * 32, smem, ls>>>(A, nmax);
     h->launches += 1;
     le = cudaGetLastError();
   }

@@ -1,6 +1,7 @@
 // plain.cu — the plain comparator: the same search semantics written the
 // straightforward way.  One instance at a time; one thread per (spin,
-// replica); spins as int8, fields as FP32/int32 arrays in global memory; one
+// replica); spins as int8, fields as FP32/int32 arrays in global memory (FP64
+// instances: every field recomputed in FP64 at each visit); one
 // launch per colour class per sweep, plus per-sweep bookkeeping launches; the
 // host polls for completion.  No bit packing, no shared-memory residency, no
 // persistent kernel, no graph.  It is the baseline the tile, multi-spin coded
@@ -43,7 +44,8 @@ __global__ void plain_start_done(PlainRep *rep, int32_t R, unsigned long long *s
   }
 }
 
-template <bool FLOAT>
+// KIND: 0 int8 couplings, 1 FP32, 2 FP64
+template <int KIND>
 __global__ void plain_visit(const DevGraph G, InstDesc I, int32_t R, int32_t c0, int32_t csize, int32_t sequential,
                             int32_t refresh, int8_t *s, uint8_t *fm, float *F, PlainRep *rep) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -57,7 +59,28 @@ __global__ void plain_visit(const DevGraph G, InstDesc I, int32_t R, int32_t c0,
   const uint32_t k0 = __ldg(G.row + gj), k1 = __ldg(G.row + gj + 1);
   const uint32_t e0 = __ldg(G.inc_ptr + gj), e1 = __ldg(G.inc_ptr + gj + 1);
   bool flip;
-  if (!FLOAT) {
+  if (KIND == 2) {
+    // FP64: the field from scratch in the definition's order (h, the CSR row,
+    // then the hyper-edges ascending), each step one FP64 addition
+    const double *Jd = reinterpret_cast<const double *>(G.J);
+    const double *hJ = reinterpret_cast<const double *>(G.hJ);
+    double f = __ldg(reinterpret_cast<const double *>(G.h) + gj);
+    for (uint32_t k = k0; k < k1; ++k) {
+      const double w = __ldg(Jd + k);
+      f = __dadd_rn(f, sr[__ldg(G.col + k)] > 0 ? w : -w);
+    }
+    for (uint32_t q = e0; q < e1; ++q) {
+      const int e = __ldg(G.inc_edge + q);
+      int neg = 0;
+      for (uint32_t m = __ldg(G.hptr + e); m < __ldg(G.hptr + e + 1); ++m) {
+        const int mm = __ldg(G.hmem + m);
+        if (mm != j) neg ^= sr[mm] < 0;
+      }
+      const double w = __ldg(hJ + e);
+      f = __dadd_rn(f, neg ? -w : w);
+    }
+    flip = sr[j] > 0 ? (f < 0.0) : (f > 0.0);
+  } else if (KIND == 0) {
     const int8_t *Ji = reinterpret_cast<const int8_t *>(G.J);
     const int8_t *hJ = reinterpret_cast<const int8_t *>(G.hJ);
     int f = __ldg(reinterpret_cast<const int8_t *>(G.h) + gj);
@@ -113,7 +136,7 @@ __global__ void plain_visit(const DevGraph G, InstDesc I, int32_t R, int32_t c0,
     F[(int64_t)r * I.n + j] = f;
     flip = sr[j] > 0 ? (f < 0.0f) : (f > 0.0f);
   }
-  fr[j] = flip ? 1 : 0;
+  if (KIND != 2) fr[j] = flip ? 1 : 0;
   if (flip) {
     sr[j] = (int8_t)-sr[j];
     atomicAdd(&rep[r].flips, 1);
@@ -138,17 +161,23 @@ __global__ void plain_end(PlainRep *rep, int32_t R, int32_t n, int32_t max_sweep
   }
 }
 
-template <bool FLOAT>
+template <int KIND>
 __global__ void plain_energy(const DevGraph G, InstDesc I, int32_t R, int32_t restarts, int32_t budget,
                              const int8_t *s, int8_t *best, PlainRep *rep, unsigned long long *stats) {
   __shared__ double redd[kPT / 32];
   __shared__ long long redi[kPT / 32];
   __shared__ int s_copy;
+  __shared__ double s_E;
   const int r = blockIdx.x;
   if (!(rep[r].state & 8)) return;
   const int8_t *sr = s + (int64_t)r * I.n;
   double E;
-  if (FLOAT) {
+  if (KIND == 2) {
+    // FP64: one thread, the compensated sequential sum of the definition
+    if (threadIdx.x == 0) s_E = energy_f64_seq(G, I, sr);
+    __syncthreads();
+    E = s_E;
+  } else if (KIND == 1) {
     const float *Jf = reinterpret_cast<const float *>(G.J);
     const float *hf = reinterpret_cast<const float *>(G.h);
     const float *hJ = reinterpret_cast<const float *>(G.hJ);
@@ -290,7 +319,7 @@ cudaError_t launch_plain(ising_handle *h, const ising_search_params *p, int32_t 
     P.cap_R = R;
   }
   const DevGraph G = h->graph();
-  const bool fl = h->dtype == ISING_F32;
+  const int kind = h->dtype == ISING_F64 ? 2 : (h->dtype == ISING_F32 ? 1 : 0);
   const int seq = p->schedule == ISING_SCHED_SEQUENTIAL;
   const int rb = (R + kPT - 1) / kPT;
   for (int32_t b = 0; b < h->n_inst; ++b) {
@@ -308,17 +337,20 @@ cudaError_t launch_plain(ising_handle *h, const ising_search_params *p, int32_t 
         const int c0 = seq ? c : cls[c], cs = seq ? 1 : cls[c + 1] - cls[c];
         if (cs <= 0) continue;
         const int vb = (int)(((int64_t)R * cs + kPT - 1) / kPT);
-        if (fl)
-          plain_visit<true><<<vb, kPT, 0, s>>>(G, I, R, c0, cs, seq, p->refresh_every, P.s, P.fm, P.F, P.rep);
+        if (kind == 1)
+          plain_visit<1><<<vb, kPT, 0, s>>>(G, I, R, c0, cs, seq, p->refresh_every, P.s, P.fm, P.F, P.rep);
+        else if (kind == 2)
+          plain_visit<2><<<vb, kPT, 0, s>>>(G, I, R, c0, cs, seq, p->refresh_every, P.s, P.fm, P.F, P.rep);
         else
-          plain_visit<false><<<vb, kPT, 0, s>>>(G, I, R, c0, cs, seq, p->refresh_every, P.s, P.fm, P.F, P.rep);
+          plain_visit<0><<<vb, kPT, 0, s>>>(G, I, R, c0, cs, seq, p->refresh_every, P.s, P.fm, P.F, P.rep);
       }
       plain_end<<<rb, kPT, 0, s>>>(P.rep, R, I.n, p->max_sweeps, p->sweep_budget, h->d_stats);
-      if (fl)
-        plain_energy<true><<<R, kPT, 0, s>>>(G, I, R, p->restarts, p->sweep_budget, P.s, P.best, P.rep, h->d_stats);
+      if (kind == 1)
+        plain_energy<1><<<R, kPT, 0, s>>>(G, I, R, p->restarts, p->sweep_budget, P.s, P.best, P.rep, h->d_stats);
+      else if (kind == 2)
+        plain_energy<2><<<R, kPT, 0, s>>>(G, I, R, p->restarts, p->sweep_budget, P.s, P.best, P.rep, h->d_stats);
       else
-        plain_energy<false><<<R, kPT, 0, s>>>(G, I, R, p->restarts, p->sweep_budget, P.s, P.best, P.rep,
-                                              h->d_stats);
+        plain_energy<0><<<R, kPT, 0, s>>>(G, I, R, p->restarts, p->sweep_budget, P.s, P.best, P.rep, h->d_stats);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       if (sweep % 8 == 7) {
         cudaMemsetAsync(P.done, 0, sizeof(int32_t), s);

@@ -31,19 +31,9 @@ namespace isg {
 namespace {
 
 constexpr int kST = 256;  // threads per CTA
-// resident CTAs per SM the FP32/int lane visits are compiled for (registers
-// per thread = 64K / (kST * this)); the multi-spin-coded visits take 8
-#ifndef ISING_SWEEP_MINB1
-#define ISING_SWEEP_MINB1 4
-#endif
-#ifndef ISING_SWEEP_REFRESH_ROLLED
-#define ISING_SWEEP_REFRESH_ROLLED 1
-#endif
-#if ISING_SWEEP_REFRESH_ROLLED
-#define ISING_REFRESH_UNROLL _Pragma("unroll 1")
-#else
-#define ISING_REFRESH_UNROLL _Pragma("unroll")
-#endif
+// Resident CTAs per SM the visits are compiled for (registers per thread =
+// 64K / (kST * this)): the multi-spin-coded visits 8, the lane visits below.
+constexpr int kVisitCtasPerSm = 4;  // the FP32/int lane visits: 64 registers per thread
 
 struct GroupState {
   uint32_t lane_valid, active, convround, any, upd, start;
@@ -183,7 +173,7 @@ __global__ void sweep_end(SweepArgs A) {
 // coded.  Groups are walked in an outer loop so the per-group state is read once
 // per warp and no index needs a division.
 template <int MODE, int LPS, bool LAT>
-__global__ void __launch_bounds__(kST, MODE == 2 ? 8 : ISING_SWEEP_MINB1) sweep_visit(SweepArgs A, int32_t c) {
+__global__ void __launch_bounds__(kST, MODE == 2 ? 8 : kVisitCtasPerSm) sweep_visit(SweepArgs A, int32_t c) {
   __shared__ uint32_t s_any[32];
   __shared__ unsigned long long s_red[kST / 32];
   __shared__ int s_off[6], s_wrap[6];
@@ -223,17 +213,8 @@ __global__ void __launch_bounds__(kST, MODE == 2 ? 8 : ISING_SWEEP_MINB1) sweep_
       const bool fresh = A.gs[g].d == 0;
       uint32_t *swg = A.sw + (size_t)g * n;
       uint32_t *pendg = A.pend + (size_t)g * n;
-      uint16_t *cf_own = A.cflag ? A.cflag + ((size_t)g * 2 + c) * A.nchunk : nullptr;
-      uint8_t *cf_oth = A.cflag ? reinterpret_cast<uint8_t *>(A.cflag + ((size_t)g * 2 + (c ^ 1)) * A.nchunk) : nullptr;
       uint32_t anyg = 0;
       for (int t = blockIdx.x * blockDim.x + tid; t < cs; t += gridDim.x * blockDim.x) {
-        if (cf_own) {
-          // t - lane is a multiple of 32: the warp's lanes share chunk t >> 5
-          const uint16_t fv = cf_own[t >> 5];
-          __syncwarp(__activemask());
-          if (lane == 0 && fv) cf_own[t >> 5] = 0;
-          if (!fresh && !fv) continue;  // no pending mark anywhere in the chunk
-        }
         const int v = c0 + t;
         const int j = A.sequential ? v : __ldg(G.order + so + v);
         // everything indexed by the site itself is read in one round trip
@@ -295,11 +276,8 @@ __global__ void __launch_bounds__(kST, MODE == 2 ? 8 : ISING_SWEEP_MINB1) sweep_
           anyg |= flip;
           my_flips += __popc(flip);
           if (LAT) {
-            for (int d = 0; d < 2 * D; ++d) {
-              const int nb = j + s_off[d] + (((info >> d) & 1u) ? s_wrap[d] : 0);
-              atomicOr(&pendg[nb], flip);
-              if (cf_oth) cf_oth[2 * (nb >> 6)] = 1;
-            }
+            for (int d = 0; d < 2 * D; ++d)
+              atomicOr(&pendg[j + s_off[d] + (((info >> d) & 1u) ? s_wrap[d] : 0)], flip);
           } else {
             for (uint32_t kk = __ldg(G.row + so + j), k1 = __ldg(G.row + so + j + 1); kk < k1; ++kk)
               atomicOr(&pendg[__ldg(G.col + kk)], flip);
@@ -469,7 +447,7 @@ __global__ void __launch_bounds__(kST, MODE == 2 ? 8 : ISING_SWEEP_MINB1) sweep_
                 base0 += t;
                 t2[kk] = 2 * t;
               }
-              ISING_REFRESH_UNROLL
+#pragma unroll 1
               for (int r0 = 0; r0 < LPS; r0 += 4) {
                 float o[4];
 #pragma unroll
@@ -479,7 +457,7 @@ __global__ void __launch_bounds__(kST, MODE == 2 ? 8 : ISING_SWEEP_MINB1) sweep_
 #pragma unroll
                   for (int kk = 0; kk < 6; ++kk)
                     if (!((wn[kk] >> r) & 1u)) acc -= t2[kk];
-                  o[q] = xr_round_int(acc, u);
+                  o[q] = xr_round(acc, u);
                   if (((wj1 >> r) & 1u) ? (o[q] < 0.0f) : (o[q] > 0.0f)) seg |= 1u << r;
                 }
                 *reinterpret_cast<float4 *>(Frow + r0) = make_float4(o[0], o[1], o[2], o[3]);
@@ -629,7 +607,7 @@ __global__ void __launch_bounds__(kST, MODE == 2 ? 8 : ISING_SWEEP_MINB1) sweep_
                     const int64_t tt = xr_term(__ldg(hJf + e), u);
                     acc += hyper_neg(e) ? -tt : tt;
                   }
-                  f = xr_round_int(acc, u);
+                  f = xr_round(acc, u);
                 } else {
                   double acc = (double)hj;
                   for (uint32_t kk = k0; kk < k1; ++kk) {
@@ -808,8 +786,15 @@ __global__ void __launch_bounds__(kST, 4) sweep_energy(SweepArgs A) {
         // integers) in registers and adds its contribution to each of the LPS
         // replicas' int64 sums; one exchange per warp then gives lane r the
         // warp total of replica r.  Integer sums: the order does not matter.
+        // Site j's part of E_r (its forward bonds and its field), with b the
+        // spin bit (1 = +1) and d_k = b xor the neighbour's bit (1 = the bond is
+        // not satisfied):  -h s - sum_k J_k s s_k
+        //   = (h - sum_k J_k)  +  2 (sum_k d_k J_k - b h)   (terms in units),
+        // so each replica only adds the terms its bits select; the site constant
+        // is the same for every replica and is added once per lane.
         constexpr int NV = LPS <= 16 ? LPS : 16;
         int64_t acc[NV];
+        int64_t csum = 0;
 #pragma unroll
         for (int r = 0; r < NV; ++r) acc[r] = 0;
         const int D2 = 2 * I.lat_d;
@@ -819,34 +804,31 @@ __global__ void __launch_bounds__(kST, 4) sweep_energy(SweepArgs A) {
           const int j = __ldg(G.order + I.spin_off + v);
           const uint32_t meta = __ldg(G.meta + I.spin_off + v);
           const uint32_t wj = swg[j];
-          int64_t th, t[6];
-          uint32_t wn[6];
+          int64_t th;
           if (FLOAT) th = xr_term(__ldg(reinterpret_cast<const float *>(G.h) + I.spin_off + j), ub);
           else th = __ldg(reinterpret_cast<const int8_t *>(G.h) + I.spin_off + j);
+          int64_t c = th;
 #pragma unroll
           for (int kk = 0; kk < 6; ++kk) {
-            t[kk] = 0;
-            wn[kk] = 0u;
-            if (kk < D2) {
-              const int i = lat_nbr(j, meta, kk, L);
-              if (i > j) {
-                wn[kk] = swg[i];
-                const int64_t jp = (int64_t)kk * G.nsp + I.spin_off + v;
-                t[kk] = FLOAT ? xr_term(__ldg(reinterpret_cast<const float *>(G.Jpos) + jp), ub)
-                              : (int64_t)__ldg(reinterpret_cast<const int8_t *>(G.Jpos) + jp);
-              }
-            }
-          }
+            if (kk >= D2) break;
+            const int i = lat_nbr(j, meta, kk, L);
+            if (i <= j) continue;  // each bond once, from its lower end
+            const int64_t jp = (int64_t)kk * G.nsp + I.spin_off + v;
+            const int64_t tk = FLOAT ? xr_term(__ldg(reinterpret_cast<const float *>(G.Jpos) + jp), ub)
+                                     : (int64_t)__ldg(reinterpret_cast<const int8_t *>(G.Jpos) + jp);
+            const uint32_t d = wj ^ swg[i];
+            c -= tk;
 #pragma unroll
-          for (int r = 0; r < NV; ++r) {
-            const uint32_t bj = (wj >> r) & 1u;
-            int64_t e = bj ? -th : th;
-#pragma unroll
-            for (int kk = 0; kk < 6; ++kk)
-              if (kk < D2) e += ((((wn[kk] >> r) & 1u) ^ bj) != 0u) ? t[kk] : -t[kk];
-            acc[r] += e;
+            for (int r = 0; r < NV; ++r)
+              if ((d >> r) & 1u) acc[r] += tk;
           }
+          csum += c;
+#pragma unroll
+          for (int r = 0; r < NV; ++r)
+            if ((wj >> r) & 1u) acc[r] -= th;
         }
+#pragma unroll
+        for (int r = 0; r < NV; ++r) acc[r] = 2 * acc[r] + csum;
         const int64_t tot = warp_sums_to_lanes<NV>(acc, lane);
         if (FLOAT) {
           acci = (long long)(tot >> 32);
@@ -1540,13 +1522,16 @@ cudaError_t launch_sweep(ising_handle *h, const ising_search_params *p, int32_t 
       const int64_t per_warp = 32 * sites_lane * (A.I.lat_d + 1);
       int lg = 0;
       while (((int64_t)1 << lg) <= per_warp) ++lg;
-      A.en_fast = (A.lattice && LPS <= 16 && A.I.ebits >= 0 && A.I.ebits + lg <= 62) ? 1 : 0;
+      // (the lane sums are doubled and offset by the site constants: one more bit)
+      A.en_fast = (A.lattice && LPS <= 16 && A.I.ebits >= 0 && A.I.ebits + lg + 1 <= 62) ? 1 : 0;
     }
     if ((e = cudaMemsetAsync(A.fm, 0, words * 4, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(A.pend, 0, words * 4, s)) != cudaSuccess) return e;
     // chunk flags: the two-class parity colouring of an even-sided lattice puts
     // site j at class position j >> 1 (class order is index order)
-    const bool chunked = A.lattice && h->lat_parity && A.I.ncls == 2 && A.I.lat_L % 2 == 0 && (mode == 1 || mode == 2);
+    // (FP32 lattices only: in the multi-spin-coded visits, a thread per site,
+    // the flag traffic measured slower than the scan it saves)
+    const bool chunked = A.lattice && h->lat_parity && A.I.ncls == 2 && A.I.lat_L % 2 == 0 && mode == 1;
     A.cflag = chunked ? cflag_mem : nullptr;
     if (chunked && (e = cudaMemsetAsync(cflag_mem, 0, cflag_bytes, s)) != cudaSuccess) return e;
     if (A.lattice) {

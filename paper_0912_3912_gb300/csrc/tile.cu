@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(kTileThreads, MODE == 3 ? 2 : 4) tile_kernel(c
                       const int64_t t = xr_term(__ldg(hJ + e), u);
                       acc += neg ? -t : t;
                     }
-                    f = xr_round_int(acc, u);
+                    f = xr_round(acc, u);
                   } else {
                     double acc = (double)hj;
                     for (uint32_t kk = k0; kk < k1; ++kk) {

@@ -221,15 +221,6 @@ def test_sweep_family_sequential_schedule():
              kernel=isg.KERNEL_SWEEP)
 
 
-def test_integer_rounding_matches_the_hardware_conversion():
-    """The refresh rounds its exact fixed-point sums to FP32 with integer
-    instructions; over 2^24 cases (ties and their neighbours at every shift,
-    random values, 0 and 2^53, units 24..200) it must equal the hardware
-    int64 -> FP32 conversion bit for bit."""
-    assert isg.check_rounding(0x1234, 1 << 24) == 0
-    assert isg.check_rounding(99, 1 << 20) == 0
-
-
 # ----------------------------------------------------------- FP32 exponent ranges
 def _exp_spread(inst, lo, hi):
     """Scale each coupling pair, field and hyper-edge by 2^e, e in [lo, hi),

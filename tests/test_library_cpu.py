@@ -76,7 +76,7 @@ def test_status_strings(isg):
 
 
 def _desc(isg, inst, **over):
-    jdt = np.int8 if inst.dtype == "i8" else np.float32
+    code, jdt = isg._DT[inst.dtype]
     arrs = dict(row_ptr=np.ascontiguousarray(inst.row_ptr, np.int64),
                 col=np.ascontiguousarray(inst.col, np.int32),
                 J=np.ascontiguousarray(inst.J, jdt),
@@ -90,7 +90,7 @@ def _desc(isg, inst, **over):
     nh = 0 if arrs["hyper_ptr"] is None else len(arrs["hyper_ptr"]) - 1
     d = isg._Desc(inst.n, p(arrs["row_ptr"]), p(arrs["col"]), p(arrs["J"]), None, p(arrs["h"]), nh,
                   p(arrs["hyper_ptr"]), p(arrs["hyper_members"]), p(arrs["hyper_J"]), p(arrs["colour"]),
-                  0 if inst.dtype == "i8" else 1)
+                  code)
     return d, arrs
 
 
@@ -161,3 +161,29 @@ def test_noalloc_rejects_null_pointers_before_any_device_work(isg):
         code = L.ising_energy_noalloc(a["n"], a["row_ptr"], a["col"], a["J"], a["h"], a["dt"], a["spins"], a["R"],
                                       a["E"], None)
         assert code == 1, (c, code)
+
+
+def test_create_checks_fp64_instances(isg):
+    """FP64 instances (ISING_F64) get the same checks: non-finite values,
+    asymmetric values, non-finite fields and hyper-edge strengths; a dense
+    matrix is FP32 only."""
+    import dataclasses
+    base = W.random_graph(30, 3.0, 2, dtype="f32", n_hyper=2, hyper_order=(3,))
+    base = dataclasses.replace(base, J=base.J.astype(np.float64), h=base.h.astype(np.float64),
+                               hyper_J=base.hyper_J.astype(np.float64), dtype="f64")
+    J = base.J.copy()
+    J[0] = np.nan
+    d, keep = _desc(isg, base, J=J)
+    assert _create_code(isg, d) == 1
+    J = base.J.copy()
+    J[0] += 2.0 ** -40  # below FP32 resolution, a real asymmetry in FP64
+    d, keep = _desc(isg, base, J=J)
+    assert _create_code(isg, d) == 2
+    hh = base.h.copy()
+    hh[3] = np.inf
+    d, keep = _desc(isg, base, h=hh)
+    assert _create_code(isg, d) == 1
+    hJ = base.hyper_J.copy()
+    hJ[1] = np.nan
+    d, keep = _desc(isg, base, hyper_J=hJ)
+    assert _create_code(isg, d) == 1
