@@ -41,7 +41,7 @@ class _Inst(C.Structure):
                 ("J_dense", C.c_void_p), ("h", C.c_void_p),
                 ("n_hyper", C.c_int32), ("hyper_ptr", C.c_void_p),
                 ("hyper_members", C.c_void_p), ("hyper_J", C.c_void_p),
-                ("colour", C.c_void_p), ("is_int", C.c_int32)]
+                ("colour", C.c_void_p), ("is_int", C.c_int32), ("is_f64", C.c_int32)]
 
 
 class _Params(C.Structure):
@@ -95,6 +95,7 @@ class OracleInstance:
     def __init__(self, inst, colour=None):
         self.n = int(inst.n)
         self.is_int = inst.dtype == "i8"
+        self.is_f64 = inst.dtype == "f64"
         f64 = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)
         self.row_ptr = None if inst.row_ptr is None else np.ascontiguousarray(inst.row_ptr, np.int64)
         self.col = None if inst.col is None else np.ascontiguousarray(inst.col, np.int32)
@@ -110,7 +111,7 @@ class OracleInstance:
         self.c = _Inst(self.n, _ptr(self.row_ptr), _ptr(self.col), _ptr(self.J), _ptr(self.J_dense),
                        _ptr(self.h), 0 if self.hyper_ptr is None else len(self.hyper_ptr) - 1,
                        _ptr(self.hyper_ptr), _ptr(self.hyper_members), _ptr(self.hyper_J),
-                       _ptr(self.colour), 1 if self.is_int else 0)
+                       _ptr(self.colour), 1 if self.is_int else 0, 1 if self.is_f64 else 0)
 
     @property
     def ref(self):
@@ -184,7 +185,7 @@ def descent(inst, seed, b, replicas, max_sweeps=1000, restarts=1, sweep_budget=0
     replica ranges at once; the oracle keeps no global state."""
     oi = inst if isinstance(inst, OracleInstance) else OracleInstance(inst, colour=colour)
     if mode is None:
-        mode = MODE_INT if oi.is_int else MODE_F32
+        mode = MODE_INT if oi.is_int else (MODE_F64 if oi.is_f64 else MODE_F32)
     p = _Params(max_sweeps, restarts, sweep_budget, refresh_every, schedule, mode)
     spins = np.empty((replicas, oi.n), dtype=np.int8)
     E = np.empty(replicas, dtype=np.float64)

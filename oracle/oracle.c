@@ -398,8 +398,10 @@ int32_t orc_descent_from(const orc_instance *in, uint64_t seed, uint32_t b, int3
  * is silent: ties in gain go to the lowest spin index; a prefix is recorded
  * when the running energy drops strictly below the best seen in the pass (so
  * the earliest best prefix is kept); a new pass runs while the previous pass
- * lowered the energy strictly (for float couplings, by more than 1e-9 relative,
- * so FP64 rounding of the running energy cannot fake an improvement).
+ * lowered the energy strictly (for FP32 couplings, by more than 1e-9 relative,
+ * so FP64 rounding of the running energy cannot fake an improvement; integer
+ * and FP64 instances, whose energies both implementations form as the same
+ * sequence of FP64 operations, take the strict rule as stated).
  * Starts from *s, leaves the result in *s and returns its energy.            */
 typedef struct { int32_t *heap, *pos; double *key; int32_t size; } gheap;
 
@@ -493,7 +495,7 @@ double orc_fm_search(const orc_instance *in, int8_t *s, int32_t *passes) {
     /* roll back to the best prefix of this pass (SP* := best-seen SP) */
     for (int32_t step = n - 1; step >= best_prefix; --step) s[moves[step]] = (int8_t)-s[moves[step]];
     double Enew = orc_energy(in, s);
-    double margin = in->is_int ? 0.0 : 1e-9 * (1.0 + fabs(Estar));
+    double margin = (in->is_int || in->is_f64) ? 0.0 : 1e-9 * (1.0 + fabs(Estar));
     if (Enew < Estar - margin) {
       Estar = Enew;
     } else {

@@ -34,6 +34,9 @@ typedef struct {
   const double *hyper_J;
   const int32_t *colour;  /* [n] or NULL                          */
   int32_t is_int;         /* all couplings/fields integer-valued  */
+  int32_t is_f64;         /* given as FP64 values (the library's ISING_F64):
+                             passes stop at the first pass without strict
+                             improvement, as for integer instances           */
 } orc_instance;
 
 enum { ORC_MODE_INT = 0, ORC_MODE_F64 = 1, ORC_MODE_F32 = 2 };

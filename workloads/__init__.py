@@ -33,14 +33,14 @@ class Instance:
     n: int
     row_ptr: Optional[np.ndarray]          # int64 [n+1]
     col: Optional[np.ndarray]              # int32 [nnz]
-    J: Optional[np.ndarray]                # int8 or float32 [nnz]
-    h: Optional[np.ndarray] = None         # int8 or float32 [n]
+    J: Optional[np.ndarray]                # int8, float32 or float64 [nnz]
+    h: Optional[np.ndarray] = None         # same dtype as J [n]
     hyper_ptr: Optional[np.ndarray] = None     # int64 [n_hyper+1]
     hyper_members: Optional[np.ndarray] = None  # int32
-    hyper_J: Optional[np.ndarray] = None       # int8 or float32 [n_hyper]
+    hyper_J: Optional[np.ndarray] = None       # same dtype as J [n_hyper]
     colour: Optional[np.ndarray] = None    # int32 [n]
     J_dense: Optional[np.ndarray] = None   # float32 [n, n]
-    dtype: str = "f32"                     # "i8" or "f32"
+    dtype: str = "f32"                     # "i8", "f32" or "f64"
     meta: dict = dataclasses.field(default_factory=dict)
 
     @property
@@ -53,7 +53,7 @@ class Instance:
 
 
 def _np_dtype(dtype: str):
-    return np.int8 if dtype == "i8" else np.float32
+    return {"i8": np.int8, "f32": np.float32, "f64": np.float64}[dtype]
 
 
 def csr_from_edges(n: int, u: np.ndarray, v: np.ndarray, w: np.ndarray, dtype: str):
@@ -274,7 +274,7 @@ def _poly_mul(a: dict, b: dict) -> dict:
     return {k: v for k, v in out.items() if v}
 
 
-def factoring(N: int, n_x: int, n_y: int, hyper: bool = True) -> Instance:
+def factoring(N: int, n_x: int, n_y: int, hyper: bool = True, dtype: Optional[str] = None) -> Instance:
     """Factoring N as a hyper-Ising instance (Sec. VI, Eqs. 7-9).
 
     x = 1 + sum_{i=1..n_x} 2^i b_i and y = 1 + sum_{j=1..n_y} 2^j c_j (odd
@@ -285,8 +285,11 @@ def factoring(N: int, n_x: int, n_y: int, hyper: bool = True) -> Instance:
     E = f - c_0 and the ground states (E = -c_0) are the factorisations.  Pair
     terms go to the CSR couplings, 3- and 4-spin terms to hyper-edges (left out
     with hyper=False, the reduced model whose ground states need not factor N).
-    Couplings are FP32 and must be integers below 2^24 in magnitude (exact);
-    larger N raise ValueError.  meta holds N, n_x, n_y and c_0."""
+    dtype None: "f32" when every coefficient is below 2^24 in magnitude (exact
+    in FP32), else "f64" (exact while every coefficient is below 2^53; wider
+    ones - N of more than about 26 bits - are rounded to FP64, and meta
+    "exact" is False).  An explicit "f32" with wider coefficients raises
+    ValueError.  meta holds N, n_x, n_y, c_0 and "exact"."""
     n = n_x + n_y
     x = {frozenset(): 1}
     y = {frozenset(): 1}
@@ -300,9 +303,16 @@ def factoring(N: int, n_x: int, n_y: int, hyper: bool = True) -> Instance:
     g[frozenset()] = g.get(frozenset(), 0) + N
     f = _poly_mul({kk: v for kk, v in g.items() if v}, {kk: v for kk, v in g.items() if v})
     c0 = f.pop(frozenset(), 0)
-    if any(abs(v) >= 1 << 24 for v in f.values()):
+    wide = any(abs(v) >= 1 << 24 for v in f.values())
+    if dtype is None:
+        dtype = "f64" if wide else "f32"
+    if dtype == "f32" and wide:
         raise ValueError("coefficients beyond 2^24: not exact in FP32")
-    h = np.zeros(n, dtype=np.float32)
+    if dtype not in ("f32", "f64"):
+        raise ValueError(dtype)
+    exact = all(abs(v) < 1 << 53 for v in f.values()) and sum(abs(v) for v in f.values()) < 1 << 53
+    vt = np.float32 if dtype == "f32" else np.float64
+    h = np.zeros(n, dtype=vt)
     u, v, w, hm, hp, hJ = [], [], [], [], [0], []
     for mono in sorted(f, key=lambda m: (len(m), sorted(m))):
         c = f[mono]
@@ -318,12 +328,12 @@ def factoring(N: int, n_x: int, n_y: int, hyper: bool = True) -> Instance:
             hp.append(len(hm))
             hJ.append(-c)
     row_ptr, col, J = csr_from_edges(n, np.array(u, dtype=np.int64), np.array(v, dtype=np.int64),
-                                     np.array(w, dtype=np.float32), "f32")
+                                     np.array([float(x) for x in w], dtype=vt), dtype)
     return Instance(n=n, row_ptr=row_ptr, col=col, J=J, h=h,
                     hyper_ptr=np.array(hp, dtype=np.int64) if hJ else None,
                     hyper_members=np.array(hm, dtype=np.int32) if hJ else None,
-                    hyper_J=np.array(hJ, dtype=np.float32) if hJ else None, dtype="f32",
-                    meta={"N": N, "n_x": n_x, "n_y": n_y, "c0": c0})
+                    hyper_J=np.array([float(x) for x in hJ], dtype=vt) if hJ else None, dtype=dtype,
+                    meta={"N": N, "n_x": n_x, "n_y": n_y, "c0": c0, "exact": exact})
 
 
 def factoring_decode(inst: Instance, s) -> tuple:
