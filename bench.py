@@ -424,6 +424,7 @@ def gpu_record(name, args, dev, rank=0, dist=None, steps=None, min_seconds=0.0, 
     rec = {
         "workload": name, "description": desc, "value": value, "unit": UNIT,
         "minima_per_s": minima_job / t_total, "steps": steps, "ms_per_step": t_total * 1e3 / steps,
+        "evaluated_per_s": value * st.get("evaluated", st["flip_evals"]) / max(1, st["flip_evals"]),
         "replicas": R, "instances": len(insts), "spins": total_spins, "kernel": isg.KERNEL_NAMES[chosen],
         "params": dict(kw), "work_per_step": work,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * len(insts),
@@ -524,7 +525,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": head["dtype"],
             "data": "synthetic (seeded generators; the paper's instances are not available)",
-            "minima_per_s": head["minima_per_s"],
+            "minima_per_s": head["minima_per_s"], "evaluated_per_s": head["evaluated_per_s"],
             "config": {"workload": args.workload, "description": head["description"], "replicas": head["replicas"],
                        "instances": head["instances"], "spins": head["spins"], "kernel": head["kernel"],
                        "l2": "flushed (512 MB write) before every timed step",
@@ -749,6 +750,25 @@ def roofline(name, kernel, insts, R, st, step_s, clk, hbm, bf16s, src, ktimes=No
     return out
 
 
+_LOGIC_PEAK = None
+
+
+def logic_peak_tops(sm_count, mhz):
+    """Peak of the multi-spin-coded kernels in T lane-ops/s: the lop3 issue rate
+    measured on this GPU in this run (ising_logic_peak, best of three ~10 ms
+    launches), else the derived 128 lanes per SM per clock."""
+    global _LOGIC_PEAK
+    if _LOGIC_PEAK is None:
+        try:
+            _LOGIC_PEAK = (isg.logic_peak() / 1e12, "")
+        except Exception as ex:
+            _LOGIC_PEAK = (0.0, f" (measurement failed: {ex})")
+    if _LOGIC_PEAK[0] > 0:
+        return _LOGIC_PEAK[0], "measured: lop3.b32 issue rate of this GPU in this run (ising_logic_peak)"
+    return sm_count * 128 * mhz * 1e6 / 1e12, \
+        f"derived: {sm_count} SMs x 128 integer lanes x {mhz:.0f} MHz (median SM clock under load)" + _LOGIC_PEAK[1]
+
+
 def _roofline(name, kernel, insts, R, st, step_s, clk, hbm, bf16s, src):
     sm_count = 152
     mhz = (clk or {}).get("sm_mhz") or 2070.0
@@ -759,16 +779,18 @@ def _roofline(name, kernel, insts, R, st, step_s, clk, hbm, bf16s, src):
     if msc and kernel in (2, 3):
         # integer/logic lane-operations per (spin, replica word): per bond one
         # unsatisfied-mask op, one for the field, about one adder op per input,
-        # the flip mask and the word update: 2 deg + 4
+        # the flip mask and the word update: 2 deg + 4.  Words counted are the
+        # evaluated ones (visits skipped by the pending masks do no logic).
         lanes = 32 if kernel == 2 else (32 if R > 16 else (16 if R > 8 else 8))
         ops = 2 * deg + 4
-        words = st["flip_evals"] / lanes
+        evaluated = st.get("evaluated", st["flip_evals"])
+        words = evaluated / lanes
         achieved = words * ops / step_s / 1e12
-        peak = sm_count * 128 * mhz * 1e6 / 1e12
+        peak, psrc = logic_peak_tops(sm_count, mhz)
         kname = "sweep_chunk" if kernel == 3 else "tile_kernel"
         return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlane-ops/s", "frac": achieved / peak,
                 "traffic": None, "kernel": kname, "ops_per_word": ops, "replicas_per_word": lanes,
-                "peak_source": f"derived: {sm_count} SMs x 128 integer lanes x {mhz:.0f} MHz (median SM clock under load)"}
+                "evaluated_share_of_visits": evaluated / max(1, st["flip_evals"]), "peak_source": psrc}
     if kernel == 4:
         # Tensor-core work actually done: each descent's first sweeps (the
         # library's default split) and one export pass, 4 n^2 flops per

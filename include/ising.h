@@ -200,9 +200,15 @@ typedef struct {
  * sweeps = sweeps run.  They depend only on the method's semantics, not on the
  * kernel that ran it.  launches = this library's kernel launches the call
  * enqueued (kernel nodes of replayed graphs included; library GEMMs not).
+ * evaluated = (spin, replica) visits whose gain the kernels actually computed:
+ * families TILE, MSC and SWEEP skip a visit when no neighbour of the spin (and
+ * no member of its hyper-edges) flipped since its previous visit, because its
+ * gain and its decision (no flip) are then unchanged (Sec. IV, incremental gain
+ * updates); the count depends on the kernel and its work layout, and equals
+ * flip_evals for the families that never skip.
  * When stats is non-NULL the call waits for the search to finish.              */
 typedef struct {
-  uint64_t flip_evals, flips, minima, descents, sweeps, launches;
+  uint64_t flip_evals, flips, minima, descents, sweeps, launches, evaluated;
 } ising_stats;
 
 typedef struct ising_handle ising_handle;
@@ -324,7 +330,7 @@ ising_status ising_fm_search(ising_handle *h, const uint64_t *seeds, int32_t rep
  * while it is open every ising_local_search call records a pair of CUDA events
  * on its stream around each of its main kernel launches (a family's main
  * kernel, or a graph of them: "tile_kernel", "msc_cluster_kernel",
- * "sweep_chunk", "dense_tc_kernel", "dense_push_kernel", "dense_energy_gemm",
+ * "sweep_chunk", "dense_tc_kernel", "dense_push_kernel", "dense_energy_tc",
  * "plain_path", "fm_kernel").  ising_set_timing(h, 0) stops recording.
  * ising_kernel_times waits for the recorded events and writes up to cap
  * entries {name, total ms, launches} summed over the window, in order of first
@@ -337,6 +343,16 @@ typedef struct {
 } ising_kernel_time;
 ising_status ising_set_timing(ising_handle *h, int32_t enable);
 int32_t ising_kernel_times(ising_handle *h, ising_kernel_time *out, int32_t cap);
+
+/* Measurement helper, not an operation of the method: the issue rate of 32-bit
+ * three-input logic operations (lop3) on the calling thread's current GPU, in
+ * lane-operations per second (one lane-op = one 32-bit logic op of one thread),
+ * from a self-timed kernel of register-only logic chains at full occupancy
+ * (best of three launches of about 10 ms).  This rate bounds the multi-spin-
+ * coded kernels, whose gains are word-wide logic on 32 replicas at once.
+ * *lane_ops_per_s (host) receives the rate, 0 on failure.  Blocks until done;
+ * ISING_ERR_INVALID_ARG for NULL, ISING_ERR_CUDA on a CUDA error.           */
+ising_status ising_logic_peak(double *lane_ops_per_s);
 
 /* Free everything the handle owns.  ising_destroy(NULL) returns ISING_OK.      */
 ising_status ising_destroy(ising_handle *h);

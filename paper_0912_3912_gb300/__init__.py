@@ -57,7 +57,8 @@ class _FmParams(C.Structure):
 
 class _Stats(C.Structure):
     _fields_ = [("flip_evals", C.c_uint64), ("flips", C.c_uint64), ("minima", C.c_uint64),
-                ("descents", C.c_uint64), ("sweeps", C.c_uint64), ("launches", C.c_uint64)]
+                ("descents", C.c_uint64), ("sweeps", C.c_uint64), ("launches", C.c_uint64),
+                ("evaluated", C.c_uint64)]
 
 
 class _KTime(C.Structure):
@@ -98,6 +99,8 @@ def lib():
             L.ising_set_timing.restype = i32
             L.ising_kernel_times.argtypes = [vp, vp, i32]
             L.ising_kernel_times.restype = i32
+            L.ising_logic_peak.argtypes = [vp]
+            L.ising_logic_peak.restype = i32
             L.ising_status_string.argtypes = [i32]
             L.ising_status_string.restype = C.c_char_p
             _lib = L
@@ -106,7 +109,7 @@ def lib():
 
 EXPORTED = ("ising_create", "ising_energy", "ising_local_search", "ising_plan_kernel",
             "ising_autotune", "ising_destroy", "ising_status_string", "ising_energy_noalloc",
-            "ising_set_timing", "ising_kernel_times", "ising_fm_search")
+            "ising_set_timing", "ising_kernel_times", "ising_fm_search", "ising_logic_peak")
 
 
 def _check(code: int, where: str):
@@ -307,6 +310,14 @@ def energy_noalloc(row_ptr, col, J, h, spins, replicas: int, energy, stream=None
             n, C.c_void_p(row_ptr.data_ptr()), C.c_void_p(col.data_ptr()), C.c_void_p(J.data_ptr()),
             None if h is None else C.c_void_p(h.data_ptr()), dt, C.c_void_p(spins.data_ptr()), replicas,
             C.c_void_p(energy.data_ptr()), C.c_void_p(s.cuda_stream))
+
+
+def logic_peak() -> float:
+    """Measured issue rate of 32-bit logic ops on the current CUDA device, in
+    lane-ops/s (ising_logic_peak): the roofline of the multi-spin-coded kernels."""
+    v = C.c_double(0.0)
+    _check(lib().ising_logic_peak(C.byref(v)), "ising_logic_peak")
+    return float(v.value)
 
 
 def status_string(code: int) -> str:

@@ -49,6 +49,7 @@ DevGraph ising_handle::graph() const {
   g.meta = d_meta;
   g.Jpos = d_Jpos;
   g.latinfo = d_latinfo;
+  g.Jfwd = d_Jfwd;
   g.runit = d_runit;
   g.nsp = total_spins;
   g.dtype = dtype;
@@ -356,7 +357,7 @@ void free_handle(ising_handle *h) {
   dense_free(h);
   plain_free(h);
   void *ptrs[] = {h->d_inst, h->d_row, h->d_col, h->d_J, h->d_h, h->d_inc_ptr, h->d_inc_edge, h->d_hptr,
-                  h->d_hmem, h->d_hJ, h->d_order, h->d_cls, h->d_Jdense, h->d_meta, h->d_Jpos, h->d_latinfo, h->d_runit,
+                  h->d_hmem, h->d_hJ, h->d_order, h->d_cls, h->d_Jdense, h->d_meta, h->d_Jpos, h->d_Jfwd, h->d_latinfo, h->d_runit,
                   h->d_scratch, h->d_tile_args,
                   h->d_seeds, h->d_stats, h->d_queue, h->d_tiles};
   for (void *p : ptrs)
@@ -852,6 +853,8 @@ ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
     std::vector<uint16_t> latinfo(nsp, 0);
     std::vector<float> Jpf(fl ? 6 * nsp : 0, 0.0f);
     std::vector<int8_t> Jpi(fl ? 0 : 6 * nsp, 0);
+    std::vector<float> Jff(fl ? 3 * nsp : 0, 0.0f);
+    std::vector<int8_t> Jfi(fl ? 0 : 3 * nsp, 0);
     h->lat_parity = h->all_lattice;
     for (auto &ls : lat_sites) {
       const HostInst &I = hin[ls.first];
@@ -885,12 +888,17 @@ ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
           latinfo[D.spin_off + v] |= (uint16_t)((wrap << dir) | ((w < 0 ? 1 : 0) << (8 + dir)));
           if (fl) Jpf[(int64_t)kk * nsp + D.spin_off + v] = I.Jf[k];
           else Jpi[(int64_t)kk * nsp + D.spin_off + v] = I.Ji[k];
+          if (!(dir & 1)) {  // the bond to the +a neighbour, by site
+            if (fl) Jff[(int64_t)(dir >> 1) * nsp + D.spin_off + j] = I.Jf[k];
+            else Jfi[(int64_t)(dir >> 1) * nsp + D.spin_off + j] = I.Ji[k];
+          }
         }
         meta[D.spin_off + v] = m;
       }
     }
     ok = upload(&h->d_meta, meta) == cudaSuccess && upload(&h->d_latinfo, latinfo) == cudaSuccess &&
-         (fl ? upload((float **)&h->d_Jpos, Jpf) : upload((int8_t **)&h->d_Jpos, Jpi)) == cudaSuccess;
+         (fl ? upload((float **)&h->d_Jpos, Jpf) : upload((int8_t **)&h->d_Jpos, Jpi)) == cudaSuccess &&
+         (fl ? upload((float **)&h->d_Jfwd, Jff) : upload((int8_t **)&h->d_Jfwd, Jfi)) == cudaSuccess;
   }
   if (ok && dense) {
     std::vector<float> Jd;
@@ -1006,7 +1014,7 @@ ising_status ising_local_search(ising_handle *h, const uint64_t *seeds, int32_t 
     }
   } while (0);
   if (st == ISING_OK && stats) {
-    if (cudaMemcpyAsync(h->h_stats_pinned, h->d_stats, sizeof(unsigned long long) * 5, cudaMemcpyDeviceToHost,
+    if (cudaMemcpyAsync(h->h_stats_pinned, h->d_stats, sizeof(unsigned long long) * 6, cudaMemcpyDeviceToHost,
                         stream) != cudaSuccess ||
         cudaStreamSynchronize(stream) != cudaSuccess) {
       st = ISING_ERR_CUDA;
@@ -1017,6 +1025,10 @@ ising_status ising_local_search(ising_handle *h, const uint64_t *seeds, int32_t 
       stats->descents = h->h_stats_pinned[3];
       stats->sweeps = h->h_stats_pinned[4];
       stats->launches = h->launches;
+      // the families that skip visits count the evaluated ones; the others
+      // compute every gain they visit
+      const bool skips = kernel == ISING_KERNEL_TILE || kernel == ISING_KERNEL_MSC || kernel == ISING_KERNEL_SWEEP;
+      stats->evaluated = skips ? h->h_stats_pinned[5] : h->h_stats_pinned[0];
     }
   }
   if (cur != h->device) cudaSetDevice(cur);
@@ -1139,6 +1151,7 @@ ising_status ising_fm_search(ising_handle *h, const uint64_t *seeds, int32_t rep
       stats->descents = h->h_stats_pinned[3];
       stats->sweeps = h->h_stats_pinned[4];
       stats->launches = h->launches;
+      stats->evaluated = h->h_stats_pinned[0];
     }
   }
   if (cur != h->device) cudaSetDevice(cur);

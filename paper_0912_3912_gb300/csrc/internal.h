@@ -71,6 +71,10 @@ struct DevGraph {
   //   latinfo[spin_off + v]: bit d = the neighbour in direction d (0 +x, 1 -x,
   //   2 +y, 3 -y, 4 +z, 5 -z) wraps around; bit 8 + d = its coupling is negative
   const uint16_t *latinfo;
+  //   Jfwd[a * nsp + spin_off + j]: coupling (int8_t or float) of the bond from
+  //   site j to its +a neighbour (a = 0 x, 1 y, 2 z; wrapping), by site index:
+  //   the lattice's bonds once each
+  const void *Jfwd;
   // FP32 instances: per spin, the unit (smallest biased exponent) of an exact
   // fixed-point refresh, or -1 when that spin's refresh needs FP64 (see xr_exact)
   const int16_t *runit;
@@ -148,6 +152,7 @@ struct ising_handle {
   bool all_lattice = false;  // every instance is a recognised periodic lattice
   bool lat_parity = false;   // ... coloured by site parity: class c = {x + y + z = c mod 2}
   void *d_Jpos = nullptr;
+  void *d_Jfwd = nullptr;
   bool any_lattice = false;
 
   // scratch and per-call state, grown on demand

@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(kCT, 1) msc_cluster_kernel(const TileArgs *__r
   const int64_t so = I.spin_off;
   const int lgp = min(lgL, 6) - 1;  // log2 of the class sites per row segment of a chunk
   unsigned long long my_flips = 0, my_evals = 0, my_sweeps = 0, my_minima = 0, my_desc = 0;
+  unsigned long long my_eval = 0;  // (site, replica) pairs of the chunks visited (skipped chunks excluded)
 
   // word of site j (any CTA of the cluster).  Only neighbours along the slab
   // axis (z in 3D, y in 2D) can lie in another CTA, and a warp's sites share
@@ -221,7 +222,10 @@ __global__ void __launch_bounds__(kCT, 1) msc_cluster_kernel(const TileArgs *__r
           uint32_t *pf = pend + c * nch + ch;
           if (!fresh && !*pf) continue;  // no site of the class here has a neighbour that flipped
           __syncwarp();
-          if (lane == 0) *pf = 0u;  // marks made in this phase go to the other class
+          if (lane == 0) {
+            *pf = 0u;  // marks made in this phase go to the other class
+            my_eval += 32ull * (unsigned long long)__popc(active);
+          }
           // lane's site: the lane-th site of class c in the chunk
           const int r = lane >> lgp, q = lane & ((1 << lgp) - 1);
           const int rowbase = lo + (ch << 6) + (r << (lgp + 1));
@@ -352,6 +356,8 @@ __global__ void __launch_bounds__(kCT, 1) msc_cluster_kernel(const TileArgs *__r
   __shared__ unsigned long long s_fl[kCT / 32];
   my_flips = block_sum(my_flips, s_fl);
   if (tid == 0) atomicAdd(A.stats + 1, my_flips);
+  my_eval = block_sum(my_eval, s_fl);
+  if (tid == 0) atomicAdd(A.stats + 5, my_eval);
   tc::cluster_sync();  // no CTA leaves while peers may still read its shared memory
 }
 

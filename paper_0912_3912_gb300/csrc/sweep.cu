@@ -58,9 +58,18 @@ struct SweepArgs {
   // zero; null when not applicable.  [g][2][nchunk]
   uint16_t *cflag;
   int32_t nchunk;
+  // With cflag set the class positions map to sites arithmetically: class c,
+  // position p holds site j = 2p + ((c + y + z) mod 2), y and z the row's
+  // coordinates from 2p / L (exact multiply-shift division by L for values
+  // below 2^24: q = (x * divL_m) >> divL_k)
+  uint64_t divL_m;
+  int32_t divL_k;
   float *F;
   GroupState *gs;
-  double *partial;  // [2][grid_e][G][32]: FP64 sums, or fixed-point high and low halves
+  double *partial;  // [grid_e][G][32]: FP64 sums of the CTAs (FP64 energies)
+  // [G][32][2]: integer and fixed-point energies, high and low halves, summed
+  // by atomic adds (order-free); read and zeroed by the last CTA
+  unsigned long long *eacc;
   int32_t grid_e;
   // 1: energies of a lattice group taken site-parallel (lane = site, a loop over
   // the group's LPS replicas) with int64 sums per lane and warp; set when the
@@ -173,16 +182,18 @@ __global__ void sweep_end(SweepArgs A) {
 // coded.  Groups are walked in an outer loop so the per-group state is read once
 // per warp and no index needs a division.
 template <int MODE, int LPS, bool LAT>
-__global__ void __launch_bounds__(kST, MODE == 2 ? 8 : kVisitCtasPerSm) sweep_visit(SweepArgs A, int32_t c) {
+__global__ void __launch_bounds__(kST, (MODE == 2 && LAT) ? 8 : kVisitCtasPerSm) sweep_visit(SweepArgs A, int32_t c) {
   __shared__ uint32_t s_any[32];
   __shared__ unsigned long long s_red[kST / 32];
   __shared__ int s_off[6], s_wrap[6];
+  __shared__ unsigned int s_eval;
   const DevGraph &G = A.g;
   const InstDesc &I = A.I;
   const int n = I.n, L = I.lat_L;
   const int64_t so = I.spin_off;
   const int tid = threadIdx.x, lane = threadIdx.x & 31;
   if (tid < 32) s_any[tid] = 0;
+  if (tid == 0) s_eval = 0;
   if (LAT && tid < 6) {
     // direction d: +x, -x, +y, -y, +z, -z; stride and wrap-around correction
     const int a = tid >> 1;
@@ -200,7 +211,10 @@ __global__ void __launch_bounds__(kST, MODE == 2 ? 8 : kVisitCtasPerSm) sweep_vi
     c1 = __ldg(G.cls + I.cls_off + c + 1);
   }
   const int cs = c1 - c0;
-  unsigned long long my_flips = 0;
+  // per-thread counts of one launch (each below 2^32: a thread visits at most
+  // n / threads positions of LPS replicas)
+  uint32_t my_flips = 0;
+  uint32_t my_eval = 0;  // (spin, replica) pairs whose gain this visit computed (skipped ones excluded)
   constexpr uint32_t lmask = LPS == 32 ? 0xffffffffu : ((1u << LPS) - 1u);
 
   if constexpr (MODE == 2) {
@@ -224,6 +238,7 @@ __global__ void __launch_bounds__(kST, MODE == 2 ? 8 : kVisitCtasPerSm) sweep_vi
         const uint32_t info = LAT ? __ldg(G.latinfo + so + v) : 0u;
         if (!fresh && !(pj & active)) continue;  // no neighbour flipped: still stable
         if (pj) pendg[j] = 0u;
+        my_eval += __popc(active);
         uint32_t flip;
         if (LAT) {
           // field folded into the count: flip iff >= deg/2 + 1 of bonds+field unsatisfied
@@ -328,13 +343,22 @@ __global__ void __launch_bounds__(kST, MODE == 2 ? 8 : kVisitCtasPerSm) sweep_vi
           const int dir = (mm >> (8 + 3 * kk)) & 7;
           return jj + s_off[dir] + (((mm >> kk) & 1u) ? s_wrap[dir] : 0);
         };
+        // site of class position v (parity lattices with flags: no order load)
+        auto site_of = [&](int v) -> int {
+          if (!cf_own) return __ldg(G.order + so + v);
+          const uint32_t p2 = 2u * (uint32_t)(v - c0);
+          const uint32_t rho = (uint32_t)(((uint64_t)p2 * A.divL_m) >> A.divL_k);
+          const uint32_t z = (uint32_t)(((uint64_t)rho * A.divL_m) >> A.divL_k);
+          const uint32_t y = rho - z * (uint32_t)L;
+          return (int)(p2 + (((uint32_t)c + y + z) & 1u));
+        };
         for (int base = wid * 32; base < cs; base += nwarps * 32) {
           // chunk base >> 5 of this class: nothing pending and no flip masks to
           // clear means nothing to do (the word is read by every lane alike)
           if (cf_own && !refresh && cf_own[base >> 5] == 0) continue;
           const int v1 = c0 + base + lane;
           const bool valid1 = v1 < c1;
-          const int j1 = valid1 ? __ldg(G.order + so + v1) : 0;
+          const int j1 = valid1 ? site_of(v1) : 0;
           const uint32_t p1 = valid1 ? pendg[j1] : 0u;
           const uint32_t meta1 = valid1 ? __ldg(G.meta + so + v1) : 0u;
           const uint32_t fm1 = valid1 ? fmg[j1] : 0u;
@@ -346,6 +370,8 @@ __global__ void __launch_bounds__(kST, MODE == 2 ? 8 : kVisitCtasPerSm) sweep_vi
             if (cf_own && lane == 0) cf_own[base >> 5] = 0;
             continue;
           }
+          // replica visits of the positions not skipped (one shared add per warp step)
+          if (lane == 0) atomicAdd(&s_eval, (uint32_t)__popc(todo) * (uint32_t)__popc(active));
           if (!refresh) {
             // Site-parallel: the position lane pulls, for each of its pending
             // replicas, the flips of the neighbours since the site's previous
@@ -356,6 +382,17 @@ __global__ void __launch_bounds__(kST, MODE == 2 ? 8 : kVisitCtasPerSm) sweep_vi
             uint32_t seg = 0u;
             if (need1) {
               const uint32_t pm = p1 & active;
+              float *Frow = Fg + (size_t)v1 * LPS;
+              // the pending replicas' field groups, fetched with the neighbour
+              // reads below (pending includes every replica whose field changes)
+              constexpr int NG = LPS <= 16 ? LPS / 4 : 1;
+              float4 fpre[NG];
+              if constexpr (LPS <= 16) {
+#pragma unroll
+                for (int g4 = 0; g4 < NG; ++g4)
+                  fpre[g4] = ((pm >> (4 * g4)) & 0xfu) ? *reinterpret_cast<const float4 *>(Frow + 4 * g4)
+                                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+              }
               const uint32_t wj1 = swg[j1];
               uint32_t wn[6], fn[6];
               float w2[6];
@@ -373,11 +410,12 @@ __global__ void __launch_bounds__(kST, MODE == 2 ? 8 : kVisitCtasPerSm) sweep_vi
                   dirtym |= fn[kk];
                 }
               }
-              float *Frow = Fg + (size_t)v1 * LPS;
 #pragma unroll
               for (int r0 = 0; r0 < LPS; r0 += 4) {
                 if (!((dirtym >> r0) & 0xfu)) continue;
-                const float4 f4 = *reinterpret_cast<const float4 *>(Frow + r0);
+                float4 f4;
+                if constexpr (LPS <= 16) f4 = fpre[r0 / 4];
+                else f4 = *reinterpret_cast<const float4 *>(Frow + r0);
                 float o[4] = {f4.x, f4.y, f4.z, f4.w};
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -531,6 +569,7 @@ __global__ void __launch_bounds__(kST, MODE == 2 ? 8 : kVisitCtasPerSm) sweep_vi
           const uint32_t wj = valid ? swg[j] : 0u;
           const bool up = (wj >> ln) & 1u;
           bool flip = false;
+          if (need && ((active >> ln) & 1u)) my_eval += 1;
           if (need) {
             const uint32_t k0 = LAT ? 0u : __ldg(G.row + so + j);
             const uint32_t k1 = LAT ? (uint32_t)(2 * I.lat_d) : __ldg(G.row + so + j + 1);
@@ -717,8 +756,10 @@ __global__ void __launch_bounds__(kST, MODE == 2 ? 8 : kVisitCtasPerSm) sweep_vi
   }
   __syncthreads();
   if (tid < A.G && s_any[tid]) atomicOr(&A.gs[tid].any, s_any[tid]);
-  my_flips = block_sum(my_flips, s_red);
-  if (tid == 0 && my_flips) atomicAdd(A.stats + 1, my_flips);
+  const unsigned long long flips_b = block_sum((unsigned long long)my_flips, s_red);
+  if (tid == 0 && flips_b) atomicAdd(A.stats + 1, flips_b);
+  const unsigned long long eval_b = block_sum((unsigned long long)my_eval, s_red) + s_eval;
+  if (tid == 0 && eval_b) atomicAdd(A.stats + 5, eval_b);
 }
 
 // Warp sums of NV per-lane values at once: NV halving exchange steps leave
@@ -767,7 +808,6 @@ __global__ void __launch_bounds__(kST, 4) sweep_energy(SweepArgs A) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int ub = I.ebase;
   const bool fx = FLOAT && ub >= 0;
-  const size_t half = (size_t)A.grid_e * A.G * 32;
   bool any = false;
   for (int g = 0; g < A.G; ++g) any = any || A.gs[g].round_end || A.gs[g].final_pass;
   if (!any) return;
@@ -781,15 +821,17 @@ __global__ void __launch_bounds__(kST, 4) sweep_energy(SweepArgs A) {
     if (S.round_end || S.final_pass) {
       const uint32_t *swg = A.sw + (size_t)g * n;
       if (LAT && LPS <= 16 && A.en_fast && (!FLOAT || fx)) {
-        // Lattice, site-parallel: lane = position holds the site's word, its
-        // forward neighbours' words and its terms (fixed-point integers or
-        // integers) in registers and adds its contribution to each of the LPS
-        // replicas' int64 sums; one exchange per warp then gives lane r the
-        // warp total of replica r.  Integer sums: the order does not matter.
+        // Lattice, site-parallel, in site order: lane = site j loads its word,
+        // the words of its +x, +y (+z) neighbours (wrapping; every bond once,
+        // from the site it leaves in the + direction), those bonds' couplings
+        // and its field, all coalesced, forms their terms (fixed-point integers
+        // or integers) and adds its part to each of the LPS replicas' int64
+        // sums; one exchange per warp then gives lane r the warp total of
+        // replica r.  Integer sums: the order does not matter.
         // Site j's part of E_r (its forward bonds and its field), with b the
-        // spin bit (1 = +1) and d_k = b xor the neighbour's bit (1 = the bond is
-        // not satisfied):  -h s - sum_k J_k s s_k
-        //   = (h - sum_k J_k)  +  2 (sum_k d_k J_k - b h)   (terms in units),
+        // spin bit (1 = +1) and d_a = b xor the +a neighbour's bit (1 = the
+        // bond is not satisfied):  -h s - sum_a J_a s s_a
+        //   = (h - sum_a J_a)  +  2 (sum_a d_a J_a - b h)   (terms in units),
         // so each replica only adds the terms its bits select; the site constant
         // is the same for every replica and is added once per lane.
         constexpr int NV = LPS <= 16 ? LPS : 16;
@@ -797,30 +839,49 @@ __global__ void __launch_bounds__(kST, 4) sweep_energy(SweepArgs A) {
         int64_t csum = 0;
 #pragma unroll
         for (int r = 0; r < NV; ++r) acc[r] = 0;
-        const int D2 = 2 * I.lat_d;
+        const int dl = I.lat_d;
+        const int64_t so = I.spin_off;
         for (int base = (blockIdx.x * nw + warp) * 32; base < n; base += gridDim.x * nw * 32) {
-          const int v = base + lane;
-          if (v >= n) continue;
-          const int j = __ldg(G.order + I.spin_off + v);
-          const uint32_t meta = __ldg(G.meta + I.spin_off + v);
+          const int j = base + lane;
+          if (j >= n) continue;
+          int q1, q2;
+          if (A.divL_m) {
+            q1 = (int)(((uint64_t)j * A.divL_m) >> A.divL_k);
+            q2 = (int)(((uint64_t)q1 * A.divL_m) >> A.divL_k);
+          } else {
+            q1 = j / L;
+            q2 = q1 / L;
+          }
+          const int x = j - q1 * L, y = q1 - q2 * L;  // (z = q2)
+          int nb[3];
+          nb[0] = x == L - 1 ? j - (L - 1) : j + 1;
+          nb[1] = y == L - 1 ? j - (L - 1) * L : j + L;
+          nb[2] = q2 == L - 1 ? j - (L - 1) * L * L : j + L * L;
           const uint32_t wj = swg[j];
-          int64_t th;
-          if (FLOAT) th = xr_term(__ldg(reinterpret_cast<const float *>(G.h) + I.spin_off + j), ub);
-          else th = __ldg(reinterpret_cast<const int8_t *>(G.h) + I.spin_off + j);
+          uint32_t d[3];
+          int64_t tk[3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            d[a] = 0u;
+            tk[a] = 0;
+            if (a < dl) {
+              d[a] = swg[nb[a]];
+              const int64_t jp = (int64_t)a * G.nsp + so + j;
+              tk[a] = FLOAT ? xr_term(__ldg(reinterpret_cast<const float *>(G.Jfwd) + jp), ub)
+                            : (int64_t)__ldg(reinterpret_cast<const int8_t *>(G.Jfwd) + jp);
+            }
+          }
+          const int64_t th = FLOAT ? xr_term(__ldg(reinterpret_cast<const float *>(G.h) + so + j), ub)
+                                   : (int64_t)__ldg(reinterpret_cast<const int8_t *>(G.h) + so + j);
           int64_t c = th;
 #pragma unroll
-          for (int kk = 0; kk < 6; ++kk) {
-            if (kk >= D2) break;
-            const int i = lat_nbr(j, meta, kk, L);
-            if (i <= j) continue;  // each bond once, from its lower end
-            const int64_t jp = (int64_t)kk * G.nsp + I.spin_off + v;
-            const int64_t tk = FLOAT ? xr_term(__ldg(reinterpret_cast<const float *>(G.Jpos) + jp), ub)
-                                     : (int64_t)__ldg(reinterpret_cast<const int8_t *>(G.Jpos) + jp);
-            const uint32_t d = wj ^ swg[i];
-            c -= tk;
+          for (int a = 0; a < 3; ++a) {
+            if (a >= dl) break;
+            const uint32_t da = wj ^ d[a];
+            c -= tk[a];
 #pragma unroll
             for (int r = 0; r < NV; ++r)
-              if ((d >> r) & 1u) acc[r] += tk;
+              if ((da >> r) & 1u) acc[r] += tk[a];
           }
           csum += c;
 #pragma unroll
@@ -1015,6 +1076,7 @@ __global__ void __launch_bounds__(kST, 4) sweep_energy(SweepArgs A) {
       acci += __shfl_xor_sync(0xffffffffu, acci, o);
       accl += __shfl_xor_sync(0xffffffffu, accl, o);
     }
+    if (!(S.round_end || S.final_pass)) continue;  // (uniform across the grid)
     const bool dbl = FLOAT && !fx;
     long long *ri = reinterpret_cast<long long *>(&s_red[0][0]);
     __syncthreads();
@@ -1028,9 +1090,8 @@ __global__ void __launch_bounds__(kST, 4) sweep_energy(SweepArgs A) {
         if (dbl) a = w == 0 ? s_red[0][lane] : a + s_red[w][lane];
         else b += ri[w * 32 + lane];
       }
-      const size_t o = ((size_t)blockIdx.x * A.G + g) * 32 + lane;
-      if (dbl) A.partial[o] = a;
-      else reinterpret_cast<long long *>(A.partial)[o] = b;
+      if (dbl) A.partial[((size_t)blockIdx.x * A.G + g) * 32 + lane] = a;
+      else if (b) atomicAdd(A.eacc + ((size_t)g * 32 + lane) * 2, (unsigned long long)b);
     }
     if (fx) {
       __syncthreads();
@@ -1039,7 +1100,7 @@ __global__ void __launch_bounds__(kST, 4) sweep_energy(SweepArgs A) {
       if (warp == 0) {
         unsigned long long b = 0;
         for (int w = 0; w < nw; ++w) b += reinterpret_cast<unsigned long long *>(ri)[w * 32 + lane];
-        reinterpret_cast<unsigned long long *>(A.partial)[half + ((size_t)blockIdx.x * A.G + g) * 32 + lane] = b;
+        if (b) atomicAdd(A.eacc + ((size_t)g * 32 + lane) * 2 + 1, b);
       }
     }
     __syncthreads();
@@ -1054,52 +1115,28 @@ __global__ void __launch_bounds__(kST, 4) sweep_energy(SweepArgs A) {
   for (int g = 0; g < A.G; ++g) {
     GroupState &S = A.gs[g];
     if (!(S.round_end || S.final_pass)) continue;
-    // warp w adds the partials of CTAs w, w + nw, ... (fixed order), then warp 0
-    // adds the warps' sums in ascending order: deterministic, nw times shorter
-    {
+    if (FLOAT && !fx) {
+      // FP64: warp w adds the partials of CTAs w, w + nw, ... (fixed order),
+      // then warp 0 adds the warps' sums in ascending order: deterministic
       double a = 0.0;
-      long long hi = 0;
-      unsigned long long lo = 0;
       // (independent loads: unrolled so that several are in flight at once;
       // the additions keep their order)
 #pragma unroll 8
-      for (int cta = warp; cta < (int)gridDim.x; cta += nw) {
-        const size_t o = ((size_t)cta * A.G + g) * 32 + lane;
-        if (FLOAT && !fx) {
-          a += A.partial[o];
-        } else {
-          hi += reinterpret_cast<const long long *>(A.partial)[o];
-          if (fx) lo += reinterpret_cast<const unsigned long long *>(A.partial)[half + o];
-        }
-      }
+      for (int cta = warp; cta < (int)gridDim.x; cta += nw) a += A.partial[((size_t)cta * A.G + g) * 32 + lane];
       __syncthreads();
-      long long *ri = reinterpret_cast<long long *>(&s_red[0][0]);
-      if (FLOAT && !fx) s_red[warp][lane] = a;
-      else ri[warp * 32 + lane] = hi;
+      s_red[warp][lane] = a;
       __syncthreads();
       if (warp == 0) {
-        if (FLOAT && !fx) {
-          double t = s_red[0][lane];
-          for (int w = 1; w < nw; ++w) t += s_red[w][lane];
-          S.E[lane] = t;
-        } else {
-          long long t = 0;
-          for (int w = 0; w < nw; ++w) t += ri[w * 32 + lane];
-          hi = t;
-        }
+        double t = s_red[0][lane];
+        for (int w = 1; w < nw; ++w) t += s_red[w][lane];
+        S.E[lane] = t;
       }
-      if (fx) {
-        __syncthreads();
-        reinterpret_cast<unsigned long long *>(ri)[warp * 32 + lane] = lo;
-        __syncthreads();
-        if (warp == 0) {
-          unsigned long long t = 0;
-          for (int w = 0; w < nw; ++w) t += reinterpret_cast<unsigned long long *>(ri)[w * 32 + lane];
-          S.E[lane] = xe_value(hi, t, ub);
-        }
-      } else if (!FLOAT && warp == 0) {
-        S.E[lane] = (double)hi;
-      }
+    } else if (warp == 0) {
+      // integer sums: take the totals and leave zeros for the next pass
+      unsigned long long *ea = A.eacc + ((size_t)g * 32 + lane) * 2;
+      const long long hi = (long long)atomicExch(ea, 0ull);
+      if (fx) S.E[lane] = xe_value(hi, atomicExch(ea + 1, 0ull), ub);
+      else S.E[lane] = (double)hi;
     }
     __syncthreads();
     if (tid == 0) {
@@ -1454,13 +1491,15 @@ cudaError_t launch_sweep(ising_handle *h, const ising_search_params *p, int32_t 
   const bool fl = h->dtype == ISING_F32;
   const int mode = fl ? 1 : (h->msc_ok ? 2 : 0);
   const int grid_e = h->sm_count * 4;
-  // scratch: sw, fm, bw, pend [G][nmax]; F [G][nmax][LPS]; gs [G]; partial [2][grid_e][G][32]; counter; done
+  // scratch: sw, fm, bw, pend [G][nmax]; F [G][nmax][LPS]; gs [G]; partial [grid_e][G][32]; eacc [G][32][2];
+  // counter; done
   const size_t words = (size_t)G * h->nmax;
   auto up256 = [](size_t b) { return (b + 255) / 256 * 256; };
   const int32_t nchunk = (h->nmax / 2 + 31) / 32 + 1;
   const size_t cflag_bytes = (size_t)G * 2 * nchunk * sizeof(uint16_t);
   const size_t need = 4 * up256(words * 4) + (fl ? up256(words * LPS * 4) : 0) + up256(G * sizeof(GroupState)) +
-                      up256((size_t)grid_e * G * 32 * 16) + 2 * 256 + up256(cflag_bytes);
+                      up256((size_t)grid_e * G * 32 * 8) + up256((size_t)G * 32 * 16) + 2 * 256 +
+                      up256(cflag_bytes);
   cudaError_t e;
   if (need > S.bytes) {
     for (auto &kv : S.graphs) {  // captured against the old scratch
@@ -1500,7 +1539,8 @@ cudaError_t launch_sweep(ising_handle *h, const ising_search_params *p, int32_t 
   A.F = fl ? (float *)take(words * LPS * 4) : nullptr;
   A.gs = (GroupState *)take(G * sizeof(GroupState));
   A.grid_e = grid_e;
-  A.partial = (double *)take((size_t)grid_e * G * 32 * 16);  // FP64 sums, or fixed-point high | low halves
+  A.partial = (double *)take((size_t)grid_e * G * 32 * 8);
+  A.eacc = (unsigned long long *)take((size_t)G * 32 * 16);
   A.counter = (unsigned int *)take(64);
   A.all_done = (int32_t *)take(64);
   uint16_t *cflag_mem = (uint16_t *)take(cflag_bytes);
@@ -1526,14 +1566,26 @@ cudaError_t launch_sweep(ising_handle *h, const ising_search_params *p, int32_t 
       A.en_fast = (A.lattice && LPS <= 16 && A.I.ebits >= 0 && A.I.ebits + lg + 1 <= 62) ? 1 : 0;
     }
     if ((e = cudaMemsetAsync(A.fm, 0, words * 4, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(A.eacc, 0, (size_t)G * 32 * 16, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(A.pend, 0, words * 4, s)) != cudaSuccess) return e;
     // chunk flags: the two-class parity colouring of an even-sided lattice puts
     // site j at class position j >> 1 (class order is index order)
     // (FP32 lattices only: in the multi-spin-coded visits, a thread per site,
     // the flag traffic measured slower than the scan it saves)
     const bool chunked = A.lattice && h->lat_parity && A.I.ncls == 2 && A.I.lat_L % 2 == 0 && mode == 1;
-    A.cflag = chunked ? cflag_mem : nullptr;
-    if (chunked && (e = cudaMemsetAsync(cflag_mem, 0, cflag_bytes, s)) != cudaSuccess) return e;
+    A.divL_m = 0;
+    A.divL_k = 0;
+    if (A.lattice && A.I.n <= (1 << 24)) {
+      // q = floor(x / L) for 0 <= x < 2^24 as (x m) >> k with m = ceil(2^k / L),
+      // k = 24 + ceil(log2 L): the error term x (m L - 2^k) / (L 2^k) stays below 1 / L
+      int lg = 0;
+      while ((1 << lg) < A.I.lat_L) ++lg;
+      A.divL_k = 24 + lg;
+      A.divL_m = (((uint64_t)1 << A.divL_k) + (uint64_t)A.I.lat_L - 1) / (uint64_t)A.I.lat_L;
+    }
+    // (the flagged visits find their sites by that division)
+    A.cflag = (chunked && A.divL_m) ? cflag_mem : nullptr;
+    if (A.cflag && (e = cudaMemsetAsync(cflag_mem, 0, cflag_bytes, s)) != cudaSuccess) return e;
     if (A.lattice) {
       if (LPS == 32) e = run_instance<32, true>(h, A, mode, s);
       else if (LPS == 16) e = run_instance<16, true>(h, A, mode, s);

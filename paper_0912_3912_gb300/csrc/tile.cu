@@ -247,6 +247,7 @@ __global__ void __launch_bounds__(kTileThreads, MODE == 3 ? 2 : 4) tile_kernel(c
   // FP32 fields of instances up to A.fsm_cap spins stay in shared memory
   float *Fs = reinterpret_cast<float *>(smem + (((MODE >= 2 ? 1 : 2) * nmax + (nmax + 31) / 32 + 3) & ~3));
   unsigned long long my_flips = 0, my_evals = 0, my_sweeps = 0, my_minima = 0, my_desc = 0;
+  unsigned long long my_eval = 0;  // (spin, replica) pairs whose gain was computed
 
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(A.queue, 1);
@@ -327,6 +328,7 @@ __global__ void __launch_bounds__(kTileThreads, MODE == 3 ? 2 : 4) tile_kernel(c
               const int j = __ldg(G.order + I.spin_off + v);
               if (!pending(j)) continue;
               clear_pending(j);
+              my_eval += __popc(active);
               const uint32_t info = __ldg(G.latinfo + I.spin_off + v);
               const int hv = __ldg(reinterpret_cast<const int8_t *>(G.h) + I.spin_off + j);
               const uint32_t wj = sw[j];
@@ -371,6 +373,7 @@ __global__ void __launch_bounds__(kTileThreads, MODE == 3 ? 2 : 4) tile_kernel(c
               const int j = A.sequential ? v : __ldg(G.order + I.spin_off + v);
               if (!pending(j)) continue;
               clear_pending(j);
+              my_eval += __popc(active);
               const int64_t gj = I.spin_off + j;
               const uint32_t wj = sw[j];
               uint32_t c0b = 0, c1b = 0, c2b = 0, c3b = 0;
@@ -529,6 +532,7 @@ __global__ void __launch_bounds__(kTileThreads, MODE == 3 ? 2 : 4) tile_kernel(c
               flip = flip && ((active >> lane) & 1u);
               const uint32_t m = __ballot_sync(0xffffffffu, flip);
               if (lane == 0) {
+                my_eval += __popc(active);
                 clear_pending(j);
                 sw[j] = wj ^ m;
                 if (MODE == 1) fm[j] = m;
@@ -628,7 +632,9 @@ __global__ void __launch_bounds__(kTileThreads, MODE == 3 ? 2 : 4) tile_kernel(c
 
   // work counters
   my_flips = block_sum<unsigned long long>(my_flips, reinterpret_cast<unsigned long long *>(s_red));
+  my_eval = block_sum<unsigned long long>(my_eval, reinterpret_cast<unsigned long long *>(s_red));
   if (tid == 0) {
+    atomicAdd(A.stats + 5, my_eval);
     atomicAdd(A.stats + 0, my_evals);
     atomicAdd(A.stats + 1, my_flips);
     atomicAdd(A.stats + 2, my_minima);

@@ -210,6 +210,20 @@ def test_sweep_family_gauss_lattice_fp32(R, refresh):
              refresh_every=refresh, kernel=isg.KERNEL_SWEEP)
 
 
+# Lattice energies are summed site by site from each site's +x, +y (+z) bonds:
+# 2-D and 3-D, odd and even sides, integer and FP32 couplings, with fields.
+@pytest.mark.parametrize("dims,R,couplings", [((15, 15), 8, "gauss"), ((20, 20), 16, "gauss"),
+                                              ((9, 9, 9), 16, "gauss"), ((7, 7, 7), 12, "pm1"),
+                                              ((8, 8, 8), 16, "pm2")])
+def test_sweep_family_lattice_shapes(dims, R, couplings):
+    inst = W.lattice(dims, periodic=True, couplings="pm1" if couplings == "pm2" else couplings,
+                     fields="gauss" if couplings == "gauss" else "pm1_0", seed=len(dims) * 100 + dims[0])
+    if couplings == "pm2":
+        inst.J = (inst.J * 2).astype(np.int8)  # not multi-spin codable: integer lanes
+    _compare([inst], [17], R, couplings != "gauss", max_sweeps=300, restarts=4, refresh_every=6,
+             kernel=isg.KERNEL_SWEEP)
+
+
 def test_sweep_family_csr_with_hyperedges():
     inst = W.random_graph(700, 4.0, 24, dtype="f32", n_hyper=50, hyper_order=(3, 4))
     _compare([inst], [9], 20, False, max_sweeps=500, restarts=3, refresh_every=8, kernel=isg.KERNEL_SWEEP)
