@@ -760,6 +760,7 @@ def logic_peak_tops(sm_count, mhz):
     global _LOGIC_PEAK
     if _LOGIC_PEAK is None:
         try:
+            import paper_0912_3912_gb300 as isg
             _LOGIC_PEAK = (isg.logic_peak() / 1e12, "")
         except Exception as ex:
             _LOGIC_PEAK = (0.0, f" (measurement failed: {ex})")

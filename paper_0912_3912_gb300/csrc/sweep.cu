@@ -75,6 +75,12 @@ struct SweepArgs {
   // the group's LPS replicas) with int64 sums per lane and warp; set when the
   // instance's term width and the sites per warp cannot overflow them
   int32_t en_fast;
+  // 1: a multi-spin-coded lattice (J = +/-1, h in {-1, 0, 1}) whose energies are
+  // counted bit-sliced (E = 2 U - B, U the unsatisfied bonds and fields)
+  int32_t en_count;
+  // 1: launch the chunk kernels with programmatic stream serialization
+  // (measured faster for the multi-spin-coded visits, slower for the FP32 ones)
+  int32_t pdl;
   unsigned int *counter;
   int32_t *all_done;
   unsigned long long *stats;
@@ -93,6 +99,16 @@ __device__ __forceinline__ int lat_nbr(int j, uint32_t meta, int k, int L) {
   return j + off;
 }
 
+
+// Programmatic dependent launch (multi-spin-coded lattices; SweepArgs::pdl).
+// The kernels of a sweep chunk may then be scheduled while their predecessor
+// drains: a visit lets its dependants launch once each of its CTAs has done its
+// main work (launch_dependents), and every chunk kernel waits, before reading
+// anything its predecessor writes, until that grid has completed and its writes
+// are visible (wait).  The wait is the hardware's grid dependency, not a spin on
+// memory; for a kernel launched without the attribute both return at once.
+__device__ __forceinline__ void pdl_prologue() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 __global__ void sweep_init(SweepArgs A) {
   const int g = threadIdx.x;
@@ -143,6 +159,7 @@ __device__ __forceinline__ uint32_t sliced_ge4(uint32_t q0, uint32_t q1, uint32_
 // class visit - its last CTA closing the sweep - was measured slower than this
 // separate launch.)
 __global__ void sweep_end(SweepArgs A) {
+  pdl_prologue();
   const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (g >= A.G) return;
@@ -192,6 +209,7 @@ __global__ void __launch_bounds__(kST, (MODE == 2 && LAT) ? 8 : kVisitCtasPerSm)
   const int n = I.n, L = I.lat_L;
   const int64_t so = I.spin_off;
   const int tid = threadIdx.x, lane = threadIdx.x & 31;
+  pdl_prologue();
   if (tid < 32) s_any[tid] = 0;
   if (tid == 0) s_eval = 0;
   if (LAT && tid < 6) {
@@ -384,10 +402,11 @@ __global__ void __launch_bounds__(kST, (MODE == 2 && LAT) ? 8 : kVisitCtasPerSm)
               const uint32_t pm = p1 & active;
               float *Frow = Fg + (size_t)v1 * LPS;
               // the pending replicas' field groups, fetched with the neighbour
-              // reads below (pending includes every replica whose field changes)
-              constexpr int NG = LPS <= 16 ? LPS / 4 : 1;
+              // reads below (pending includes every replica whose field changes;
+              // 16-lane groups only: with 8 lanes the registers run short)
+              constexpr int NG = LPS == 16 ? 4 : 1;
               float4 fpre[NG];
-              if constexpr (LPS <= 16) {
+              if constexpr (LPS == 16) {
 #pragma unroll
                 for (int g4 = 0; g4 < NG; ++g4)
                   fpre[g4] = ((pm >> (4 * g4)) & 0xfu) ? *reinterpret_cast<const float4 *>(Frow + 4 * g4)
@@ -414,7 +433,7 @@ __global__ void __launch_bounds__(kST, (MODE == 2 && LAT) ? 8 : kVisitCtasPerSm)
               for (int r0 = 0; r0 < LPS; r0 += 4) {
                 if (!((dirtym >> r0) & 0xfu)) continue;
                 float4 f4;
-                if constexpr (LPS <= 16) f4 = fpre[r0 / 4];
+                if constexpr (LPS == 16) f4 = fpre[r0 / 4];
                 else f4 = *reinterpret_cast<const float4 *>(Frow + r0);
                 float o[4] = {f4.x, f4.y, f4.z, f4.w};
 #pragma unroll
@@ -754,6 +773,7 @@ __global__ void __launch_bounds__(kST, (MODE == 2 && LAT) ? 8 : kVisitCtasPerSm)
       if (lane == 0 && anyg) atomicOr(&s_any[g], anyg);
     }
   }
+  pdl_trigger();
   __syncthreads();
   if (tid < A.G && s_any[tid]) atomicOr(&A.gs[tid].any, s_any[tid]);
   const unsigned long long flips_b = block_sum((unsigned long long)my_flips, s_red);
@@ -808,6 +828,7 @@ __global__ void __launch_bounds__(kST, 4) sweep_energy(SweepArgs A) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int ub = I.ebase;
   const bool fx = FLOAT && ub >= 0;
+  pdl_prologue();
   bool any = false;
   for (int g = 0; g < A.G; ++g) any = any || A.gs[g].round_end || A.gs[g].final_pass;
   if (!any) return;
@@ -820,7 +841,71 @@ __global__ void __launch_bounds__(kST, 4) sweep_energy(SweepArgs A) {
     unsigned long long accl = 0;
     if (S.round_end || S.final_pass) {
       const uint32_t *swg = A.sw + (size_t)g * n;
-      if (LAT && LPS <= 16 && A.en_fast && (!FLOAT || fx)) {
+      if (LAT && !FLOAT && A.en_count) {
+        // Multi-spin-coded lattice, site-parallel in site order: with J = +/-1
+        // and h in {-1, 0, 1} every bond and nonzero field term is +1 when
+        // unsatisfied and -1 otherwise, so E_r = 2 U_r - B with U_r the
+        // unsatisfied terms of replica r and B the number of terms.  Lane = site
+        // forms the unsatisfied masks of its forward bonds and field (bit r =
+        // replica r) and adds them into bit-sliced per-lane counters; one
+        // butterfly per warp then gives lane r the warp's U_r.
+        constexpr int Q = 8;  // per-lane counts stay below 2^8 (host-checked: 4 terms x sites per lane)
+        uint32_t cnt[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) cnt[q] = 0u;
+        int nterms = 0;
+        const int dl = I.lat_d;
+        const int64_t so = I.spin_off;
+        const int8_t *Jf8 = reinterpret_cast<const int8_t *>(G.Jfwd);
+        const int8_t *h8 = reinterpret_cast<const int8_t *>(G.h);
+        auto add_bit = [&](uint32_t m) {
+#pragma unroll
+          for (int q = 0; q < Q; ++q) {
+            const uint32_t c = cnt[q] & m;
+            cnt[q] ^= m;
+            m = c;
+          }
+        };
+        for (int base = (blockIdx.x * nw + warp) * 32; base < n; base += gridDim.x * nw * 32) {
+          const int j = base + lane;
+          if (j >= n) continue;
+          int q1, q2;
+          if (A.divL_m) {
+            q1 = (int)(((uint64_t)j * A.divL_m) >> A.divL_k);
+            q2 = (int)(((uint64_t)q1 * A.divL_m) >> A.divL_k);
+          } else {
+            q1 = j / L;
+            q2 = q1 / L;
+          }
+          const int x = j - q1 * L, y = q1 - q2 * L;  // (z = q2)
+          int nb[3];
+          nb[0] = x == L - 1 ? j - (L - 1) : j + 1;
+          nb[1] = y == L - 1 ? j - (L - 1) * L : j + L;
+          nb[2] = q2 == L - 1 ? j - (L - 1) * L * L : j + L * L;
+          const uint32_t wj = swg[j];
+          uint32_t u[3];
+          int neg[3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            u[a] = 0u;
+            neg[a] = 0;
+            if (a < dl) {
+              u[a] = swg[nb[a]];
+              neg[a] = __ldg(Jf8 + (int64_t)a * G.nsp + so + j) < 0;
+            }
+          }
+          const int hv = __ldg(h8 + so + j);
+          // unsatisfied: J s s' < 0, i.e. (spins differ) xor (J < 0); -h s > 0
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+            if (a < dl) add_bit(wj ^ u[a] ^ (neg[a] ? 0xffffffffu : 0u));
+          if (hv != 0) add_bit(hv > 0 ? ~wj : wj);
+          nterms += dl + (hv != 0 ? 1 : 0);
+        }
+        const long long U = warp_sliced_total<Q>(cnt, lane);  // lane r: replica r's warp total
+        const long long B = (long long)warp_sum(nterms);
+        acci = lane < LPS ? 2 * U - B : 0;  // (lanes beyond the group's replicas carry nothing)
+      } else if (LAT && LPS <= 16 && A.en_fast && (!FLOAT || fx)) {
         // Lattice, site-parallel, in site order: lane = site j loads its word,
         // the words of its +x, +y (+z) neighbours (wrapping; every bond once,
         // from the site it leaves in the + direction), those bonds' couplings
@@ -1184,6 +1269,7 @@ __global__ void __launch_bounds__(kST, 4) sweep_energy(SweepArgs A) {
 // same sites, so the copy never sees a new start.
 template <int LPS>
 __global__ void __launch_bounds__(kST) sweep_restart(SweepArgs A) {
+  pdl_prologue();
   const int n = A.I.n;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (int g = 0; g < A.G; ++g) {
@@ -1291,18 +1377,35 @@ constexpr size_t visit_smem(int, int, bool) {
   return 0;  // the visits keep their per-position data in registers
 }
 
+// Launch, with programmatic stream serialization when pdl is set (see
+// pdl_prologue); a launch error is left for the caller's cudaGetLastError.
+template <typename... KArgs, typename... Args>
+void launch_pdl(bool pdl, void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 template <int MODE, int LPS, bool LAT>
 void enqueue_visit(const SweepArgs &A, int c, int grid, cudaStream_t s) {
-  sweep_visit<MODE, LPS, LAT><<<grid, kST, visit_smem(MODE, LPS, LAT), s>>>(A, c);
+  launch_pdl(A.pdl != 0, sweep_visit<MODE, LPS, LAT>, grid, kST, visit_smem(MODE, LPS, LAT), s, A, (int32_t)c);
   debug_step("visit", c, s);
 }
 
 template <int LPS, bool LAT>
 void enqueue_round_end(const SweepArgs &A, int mode, cudaStream_t s) {
-  if (mode == 1) sweep_energy<true, LPS, LAT><<<A.grid_e, kST, 0, s>>>(A);
-  else sweep_energy<false, LPS, LAT><<<A.grid_e, kST, 0, s>>>(A);
+  if (mode == 1) launch_pdl(A.pdl != 0, sweep_energy<true, LPS, LAT>, A.grid_e, kST, 0, s, A);
+  else launch_pdl(A.pdl != 0, sweep_energy<false, LPS, LAT>, A.grid_e, kST, 0, s, A);
   debug_step("energy", 0, s);
-  sweep_restart<LPS><<<A.grid_e, kST, 0, s>>>(A);
+  launch_pdl(A.pdl != 0, sweep_restart<LPS>, A.grid_e, kST, 0, s, A);
   debug_step("restart", 0, s);
 }
 
@@ -1313,7 +1416,7 @@ void enqueue_sweep(const SweepArgs &A, int mode, int ncls, int grid_v, cudaStrea
     else if (mode == 1) enqueue_visit<1, LPS, LAT>(A, c, grid_v, s);
     else enqueue_visit<2, LPS, LAT>(A, c, grid_v, s);
   }
-  sweep_end<<<(A.G + 7) / 8, 256, 0, s>>>(A);
+  launch_pdl(A.pdl != 0, sweep_end, (A.G + 7) / 8, 256, 0, s, A);
   debug_step("end", 0, s);
   if (round_end) enqueue_round_end<LPS, LAT>(A, mode, s);
 }
@@ -1406,7 +1509,7 @@ cudaError_t run_instance(ising_handle *h, SweepArgs A, int mode, cudaStream_t s)
     std::snprintf(key, sizeof key, "%d/%d/%d/%d/%d/%d/%d/%d/%d/%d/%llu/%p/%d/%d/%d/%d/%p/%d/%d", A.b, A.R, A.G, A.LPS,
                   A.max_sweeps, A.restarts, A.budget, A.refresh, A.sequential, A.lattice,
                   (unsigned long long)A.seed, (void *)A.sw, mode, grid_v, chunk, ncls, (void *)A.cflag, A.nchunk,
-                  A.en_fast);
+                  A.en_fast + 2 * A.en_count);
     auto it = S.graphs.find(key);
     if (it == S.graphs.end()) {
       SweepGraph sg;
@@ -1564,6 +1667,9 @@ cudaError_t launch_sweep(ising_handle *h, const ising_search_params *p, int32_t 
       while (((int64_t)1 << lg) <= per_warp) ++lg;
       // (the lane sums are doubled and offset by the site constants: one more bit)
       A.en_fast = (A.lattice && LPS <= 16 && A.I.ebits >= 0 && A.I.ebits + lg + 1 <= 62) ? 1 : 0;
+      // bit-sliced counts: at most 4 terms per site, sites_lane sites per lane, below 2^8
+      A.en_count = (A.lattice && mode == 2 && 4 * sites_lane <= 255) ? 1 : 0;
+      A.pdl = mode == 2 ? 1 : 0;
     }
     if ((e = cudaMemsetAsync(A.fm, 0, words * 4, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(A.eacc, 0, (size_t)G * 32 * 16, s)) != cudaSuccess) return e;

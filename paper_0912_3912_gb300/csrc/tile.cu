@@ -246,8 +246,13 @@ __global__ void __launch_bounds__(kTileThreads, MODE == 3 ? 2 : 4) tile_kernel(c
   float *F = A.F ? A.F + (size_t)blockIdx.x * nmax * 32 : nullptr;
   // FP32 fields of instances up to A.fsm_cap spins stay in shared memory
   float *Fs = reinterpret_cast<float *>(smem + (((MODE >= 2 ? 1 : 2) * nmax + (nmax + 31) / 32 + 3) & ~3));
-  unsigned long long my_flips = 0, my_evals = 0, my_sweeps = 0, my_minima = 0, my_desc = 0;
-  unsigned long long my_eval = 0;  // (spin, replica) pairs whose gain was computed
+  // Work counters: thread 0's sweep-level counts go straight to shared memory;
+  // every thread counts its flips and evaluated pairs of the current sweep in
+  // 32 bits and adds the warp's total at the end of each sweep.
+  //   s_work: 0 flip_evals, 1 flips, 2 minima, 3 descents, 4 sweeps, 5 evaluated
+  __shared__ unsigned long long s_work[6];
+  if (tid < 6) s_work[tid] = 0;
+  uint32_t my_flips = 0, my_eval = 0;
 
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(A.queue, 1);
@@ -277,7 +282,7 @@ __global__ void __launch_bounds__(kTileThreads, MODE == 3 ? 2 : 4) tile_kernel(c
             if (((lane_valid >> r) & 1u) && (A.budget <= 0 || s_total[r] < A.budget)) start |= 1u << r;
         s_active = start;
         s_convround = 0;
-        my_desc += __popc(start);
+        s_work[3] += __popc(start);
       }
       __syncthreads();
       uint32_t active = s_active;
@@ -556,6 +561,13 @@ __global__ void __launch_bounds__(kTileThreads, MODE == 3 ? 2 : 4) tile_kernel(c
         // end of sweep: which lanes flipped at all?
         anyf = __reduce_or_sync(0xffffffffu, anyf);
         if (lane == 0 && anyf) atomicOr(&s_any, anyf);
+        {
+          const uint32_t wf = __reduce_add_sync(0xffffffffu, my_flips);
+          const uint32_t we = __reduce_add_sync(0xffffffffu, my_eval);
+          if (lane == 0 && wf) atomicAdd(&s_work[1], (unsigned long long)wf);
+          if (lane == 0 && we) atomicAdd(&s_work[5], (unsigned long long)we);
+          my_flips = my_eval = 0;
+        }
         __syncthreads();
         if (tid == 0) {
           const uint32_t any = s_any;
@@ -568,9 +580,9 @@ __global__ void __launch_bounds__(kTileThreads, MODE == 3 ? 2 : 4) tile_kernel(c
           if (A.budget > 0)
             for (int r = 0; r < 32; ++r)
               if (((active >> r) & 1u) && s_total[r] >= A.budget) ended |= 1u << r;
-          my_sweeps += __popc(active);
-          my_evals += (unsigned long long)__popc(active) * (unsigned long long)n;
-          my_minima += __popc(conv);
+          s_work[4] += __popc(active);
+          s_work[0] += (unsigned long long)__popc(active) * (unsigned long long)n;
+          s_work[2] += __popc(conv);
           s_convround |= conv;
           s_active = active & ~ended;
         }
@@ -631,16 +643,8 @@ __global__ void __launch_bounds__(kTileThreads, MODE == 3 ? 2 : 4) tile_kernel(c
   }
 
   // work counters
-  my_flips = block_sum<unsigned long long>(my_flips, reinterpret_cast<unsigned long long *>(s_red));
-  my_eval = block_sum<unsigned long long>(my_eval, reinterpret_cast<unsigned long long *>(s_red));
-  if (tid == 0) {
-    atomicAdd(A.stats + 5, my_eval);
-    atomicAdd(A.stats + 0, my_evals);
-    atomicAdd(A.stats + 1, my_flips);
-    atomicAdd(A.stats + 2, my_minima);
-    atomicAdd(A.stats + 3, my_desc);
-    atomicAdd(A.stats + 4, my_sweeps);
-  }
+  __syncthreads();
+  if (tid < 6 && s_work[tid]) atomicAdd(A.stats + tid, s_work[tid]);
 }
 
 size_t tile_smem_bytes(int mode, int nmax) {
