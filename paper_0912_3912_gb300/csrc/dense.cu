@@ -1,6 +1,6 @@
 // dense.cu — fully connected instances (Sherrington-Kirkpatrick): the
 // sequential schedule with fields computed on tensor cores.  Where the
-// hand-written kernels apply (n a multiple of 256, at most 4096) a round of the
+// hand-written kernels apply (n zero-padded to a multiple of 256, at most 8192) a round of the
 // search is: the first sweeps of every replica's descent in lockstep on tcgen05
 // (dense_tc.cu), each replica's remaining sweeps as incremental gain updates
 // (dense_push.cu), then the round's bookkeeping (best state, next restart).

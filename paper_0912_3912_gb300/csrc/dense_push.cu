@@ -29,8 +29,9 @@ namespace isg {
 
 namespace {
 
-constexpr int kThreads = 128;  // one CTA per replica
-constexpr int kSlots = 8;      // most float4 field slots per thread: n <= 4 * kThreads * kSlots = 4096
+// One CTA per replica: 128 threads for n <= 4096, 256 for n <= 8192, each with
+// at most kSlots float4 field slots.
+constexpr int kSlots = 8;
 constexpr int kNone = 0x7fffffff;
 
 struct PushArgs {
@@ -44,10 +45,10 @@ struct PushArgs {
   unsigned long long *stats;
 };
 
-// Layout: thread t holds, in slot k, the fields and spins of the four spins
-// j = 4 (t + kThreads k) + e, e = 0..3, so slot k of the CTA covers the
-// 512-spin group [512 k, 512 k + 512) in order of (t, e), and a coupling row is
-// read as one coalesced float4 per thread and slot.
+// Layout: thread t of TH holds, in slot k, the fields and spins of the four
+// spins j = 4 (t + TH k) + e, e = 0..3, so slot k of the CTA covers the
+// 4 TH-spin group [4 TH k, 4 TH (k + 1)) in order of (t, e), and a coupling row
+// is read as one coalesced float4 per thread and slot.
 //
 // A sweep visits the groups in order.  In a group every thread evaluates its
 // own four spins (those after the last flip), the CTA takes the first one in
@@ -58,10 +59,11 @@ struct PushArgs {
 // passes over keep their decisions, as in a one-by-one visit, because fields
 // change only at flips.
 //
-// NS = slots per thread (groups); GUARD: n is not 512 NS, so the last group is
+// NS = slots per thread (groups); GUARD: n is not 4 TH NS, so the last group is
 // partial and spins j >= n are masked out.
-template <int NS, bool GUARD>
-__global__ void __launch_bounds__(kThreads, 6) dense_push_kernel(PushArgs A) {
+template <int NS, bool GUARD, int TH>
+__global__ void __launch_bounds__(TH, TH == 128 ? 6 : 3) dense_push_kernel(PushArgs A) {
+  constexpr int kThreads = TH;
   __shared__ int s_r;
   __shared__ int s_min[2][kThreads / 32];
   __shared__ double s_e[kThreads / 32];
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(kThreads, 6) dense_push_kernel(PushArgs A) {
 #pragma unroll
       for (int g = 0; g < NS; ++g) {
         const int j0 = 4 * (t + kThreads * g);
-        int from = 512 * g;  // first spin of the group still to decide
+        int from = 4 * kThreads * g;  // first spin of the group still to decide
         for (;;) {
           // this thread's first flipping spin of group g at or after `from`:
           // spin e flips iff its field is nonzero with the sign of its spin
@@ -207,20 +209,20 @@ __global__ void __launch_bounds__(kThreads, 6) dense_push_kernel(PushArgs A) {
   }
 }
 
-template <int NS, bool GUARD>
+template <int NS, bool GUARD, int TH>
 cudaError_t launch_push(const PushArgs &A, int sm_count, cudaStream_t s) {
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense_push_kernel<NS, GUARD>, kThreads, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense_push_kernel<NS, GUARD, TH>, TH, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int grid = std::max(1, std::min(sm_count * per_sm, A.R));
-  dense_push_kernel<NS, GUARD><<<grid, kThreads, 0, s>>>(A);
+  dense_push_kernel<NS, GUARD, TH><<<grid, TH, 0, s>>>(A);
   return cudaGetLastError();
 }
 
-template <int NS>
+template <int NS, int TH>
 cudaError_t launch_push_ns(const PushArgs &A, int sm_count, cudaStream_t s) {
-  return A.n == 4 * kThreads * NS ? launch_push<NS, false>(A, sm_count, s) : launch_push<NS, true>(A, sm_count, s);
+  return A.n == 4 * TH * NS ? launch_push<NS, false, TH>(A, sm_count, s) : launch_push<NS, true, TH>(A, sm_count, s);
 }
 
 }  // namespace
@@ -228,8 +230,8 @@ cudaError_t launch_push_ns(const PushArgs &A, int sm_count, cudaStream_t s) {
 cudaError_t dense_push_run(int n, int n_eval, int R, int max_sweeps, int budget, const float *J, const float *h,
                            const float *F, __nv_bfloat16 *S, DenseRep *rep, int32_t *counter,
                            unsigned long long *stats, int sm_count, cudaStream_t s) {
-  // whole float4 groups, 16-byte aligned rows, fields in registers: n % 4 == 0, n <= 4096
-  if (n % 4 != 0 || n < 4 || n > 4 * kThreads * kSlots) return cudaErrorInvalidValue;
+  // whole float4 groups, 16-byte aligned rows, fields in registers: n % 4 == 0, n <= 8192
+  if (n % 4 != 0 || n < 4 || n > 4 * 256 * kSlots) return cudaErrorInvalidValue;
   PushArgs A;
   A.n = n;
   A.n_eval = n_eval;
@@ -243,15 +245,23 @@ cudaError_t dense_push_run(int n, int n_eval, int R, int max_sweeps, int budget,
   A.rep = rep;
   A.counter = counter;
   A.stats = stats;
-  switch ((n + 4 * kThreads - 1) / (4 * kThreads)) {
-    case 1: return launch_push_ns<1>(A, sm_count, s);
-    case 2: return launch_push_ns<2>(A, sm_count, s);
-    case 3: return launch_push_ns<3>(A, sm_count, s);
-    case 4: return launch_push_ns<4>(A, sm_count, s);
-    case 5: return launch_push_ns<5>(A, sm_count, s);
-    case 6: return launch_push_ns<6>(A, sm_count, s);
-    case 7: return launch_push_ns<7>(A, sm_count, s);
-    default: return launch_push_ns<8>(A, sm_count, s);
+  if (n > 4 * 128 * kSlots) {  // 4096 < n <= 8192: 256 threads, 5 to 8 slots
+    switch ((n + 4 * 256 - 1) / (4 * 256)) {
+      case 5: return launch_push_ns<5, 256>(A, sm_count, s);
+      case 6: return launch_push_ns<6, 256>(A, sm_count, s);
+      case 7: return launch_push_ns<7, 256>(A, sm_count, s);
+      default: return launch_push_ns<8, 256>(A, sm_count, s);
+    }
+  }
+  switch ((n + 4 * 128 - 1) / (4 * 128)) {
+    case 1: return launch_push_ns<1, 128>(A, sm_count, s);
+    case 2: return launch_push_ns<2, 128>(A, sm_count, s);
+    case 3: return launch_push_ns<3, 128>(A, sm_count, s);
+    case 4: return launch_push_ns<4, 128>(A, sm_count, s);
+    case 5: return launch_push_ns<5, 128>(A, sm_count, s);
+    case 6: return launch_push_ns<6, 128>(A, sm_count, s);
+    case 7: return launch_push_ns<7, 128>(A, sm_count, s);
+    default: return launch_push_ns<8, 128>(A, sm_count, s);
   }
 }
 

@@ -44,16 +44,23 @@ namespace {
 constexpr int kTM = 128;        // replicas per cluster (MMA M)
 constexpr int kTB = 128;        // spins per block (MMA N)
 constexpr int kKC = 64;         // K per TMA chunk (128 bytes of BF16)
-constexpr int kStages = 3;
 constexpr int kClus = 4;        // CTAs per cluster (split K)
 constexpr int kThreads = 1024;  // one warp per decided replica (32 per CTA)
 constexpr int kFl = kTB + 1;    // padded row of the block fields [replica][spin]
 constexpr int kTileBytes = kTM * kKC * 2;                 // 16 KB
 constexpr int kStageBytes = 3 * kTileBytes;               // A, B_hi, B_lo
 constexpr int kPartialBytes = kTB * kTM * 4;              // 64 KB, [spin][replica]
-constexpr int kMaxN = 4096;                                 // spins whose bits fit in shared memory
-constexpr int kSbitsBytes = 32 * (kMaxN / 32) * 4;          // this CTA's 32 replicas, 1 bit per spin
-constexpr int kSmemBytes = kStages * kStageBytes + kPartialBytes + kSbitsBytes + 1024;  // + alignment slack
+// Two shapes: n <= 4096 with a 3-stage operand pipeline, n <= 8192 with 2
+// stages (the spin bits of 8192 spins take the third stage's shared memory).
+// Shared memory: STAGES x (A, Bhi, Blo), the partial block fields, this CTA's
+// 32 replicas' spin bits (1 bit per spin), alignment slack.
+constexpr int kMaxN = 8192;
+constexpr int smem_bytes(int stages, int maxn) {
+  return stages * kStageBytes + kPartialBytes + 32 * (maxn / 32) * 4 + 1024;
+}
+// the decision phase reuses the stage buffers for its fields and couplings
+static_assert(32 * kFl * 4 + 128 + kTB * kTB * 4 <= 2 * kStageBytes, "decision staging must fit two stages");
+static_assert(smem_bytes(2, kMaxN) <= 227 * 1024 && smem_bytes(3, 4096) <= 227 * 1024, "shared memory per CTA");
 
 struct TcArgs {
   int32_t n, R, Rp, b;             // spins (padded to a multiple of 256), replicas, padded replicas, instance
@@ -90,18 +97,19 @@ __device__ __forceinline__ void write_start_warp(const TcArgs &A, int r, int k, 
 // every block's fields once more without decisions, giving the energy of each
 // replica's state and, for replicas still descending, their full field vectors
 // (exported to Fx for the per-replica continuation).
+template <int STAGES>
 __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
     dense_tc_kernel(const __grid_constant__ CUtensorMap mapS, const __grid_constant__ CUtensorMap mapJhi,
                     const __grid_constant__ CUtensorMap mapJlo, TcArgs A) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t *stage = smem;                                              // kStages x (A, Bhi, Blo)
-  float *P = reinterpret_cast<float *>(smem + kStages * kStageBytes);  // partial fields [spin][replica]
+  uint8_t *stage = smem;                                              // STAGES x (A, Bhi, Blo)
+  float *P = reinterpret_cast<float *>(smem + STAGES * kStageBytes);  // partial fields [spin][replica]
   float *Floc = reinterpret_cast<float *>(smem);                      // reuses stages: [32 replicas][kFl]
   float *Jblk = reinterpret_cast<float *>(smem + 32 * kFl * 4 + 128); // reuses stages: [128][128]
-  uint32_t *sbits = reinterpret_cast<uint32_t *>(smem + kStages * kStageBytes + kPartialBytes);  // [32][n/32]
+  uint32_t *sbits = reinterpret_cast<uint32_t *>(smem + STAGES * kStageBytes + kPartialBytes);  // [32][n/32]
 
-  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], done_bar, drain_bar, stall_bar;
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar, drain_bar, stall_bar;
   __shared__ uint32_t tmem_base_s;
   __shared__ int32_t s_flag[2];   // cluster-visible: [0] my replicas still busy, [1] my failure
   __shared__ int32_t s_ctrl[4];   // broadcast inside the CTA
@@ -118,7 +126,7 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
   constexpr uint32_t idesc = tc::idesc_bf16_f32(kTM, kTB);
 
   if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < STAGES; ++s) {
       tc::mbar_init(&full_bar[s], 1);
       tc::mbar_init(&empty_bar[s], 1);
     }
@@ -169,8 +177,10 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
   if (rq + warp < A.R && s_run[warp]) write_start_warp(A, rq + warp, s_nfl[warp], sbits + warp * nw32, lane);
   tc::fence_proxy_async_global();
   bool failed = false;
-  uint32_t ph_full[kStages] = {0, 0, 0}, ph_empty[kStages] = {0, 0, 0}, ph_done = 0;
-  int tma_pending[kStages] = {0, 0, 0}, mma_pending = 0;
+  uint32_t ph_full[STAGES], ph_empty[STAGES], ph_done = 0;
+  int tma_pending[STAGES], mma_pending = 0;
+#pragma unroll
+  for (int st2 = 0; st2 < STAGES; ++st2) ph_full[st2] = ph_empty[st2] = 0, tma_pending[st2] = 0;
   tc::cluster_sync();
 
   for (int sw = 0; sw <= A.sweeps_a; ++sw) {
@@ -203,7 +213,7 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
     for (int blk = 0; blk < nblk; ++blk) {
       const int b0 = blk * kTB;
       // Phase 1: partial fields of the block over this CTA's K-slice.  Thread 0
-      // keeps kStages chunks in flight: after issuing chunk kc's MMAs it refills
+      // keeps STAGES chunks in flight: after issuing chunk kc's MMAs it refills
       // the stage of chunk kc-1 once those MMAs have read it, so the tensor pipe
       // always has the next chunk queued.
       if (tid == 0 && !failed) {
@@ -216,12 +226,12 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
           tc::tma_load_2d(st_ + 2 * kTileBytes, &mapJlo, &full_bar[s], kbase + kn * kKC, b0);
           tma_pending[s] = 1;
         };
-        for (int s = 0; s < kStages && s < kchunks; ++s) load(s, s);
+        for (int s = 0; s < STAGES && s < kchunks; ++s) load(s, s);
         if (A.stall_test && blockIdx.x == 0 && sw == 0 && blk == 0 && !tc::mbar_wait(&stall_bar, 0, 20000))
           failed = true;  // nothing arrives on stall_bar: the wait gives up after 20 us
         int waited = 0;  // chunks whose MMA completion (empty barrier) has been consumed
         for (int kc = 0; kc < kchunks && !failed; ++kc) {
-          const int s = kc % kStages;
+          const int s = kc % STAGES;
           if (!tc::mbar_wait(&full_bar[s], ph_full[s])) {
             failed = true;
             break;
@@ -241,21 +251,21 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
           tc::mma_commit(&empty_bar[s]);
           mma_pending = 1;
           if (kc >= 1) {
-            const int pc = kc - 1, sp = pc % kStages;
+            const int pc = kc - 1, sp = pc % STAGES;
             if (!tc::mbar_wait(&empty_bar[sp], ph_empty[sp])) {
               failed = true;
               break;
             }
             ph_empty[sp] ^= 1u;
             waited = kc;
-            if (pc + kStages < kchunks) load(sp, pc + kStages);
+            if (pc + STAGES < kchunks) load(sp, pc + STAGES);
           }
         }
         if (!failed) {
           tc::mma_commit(&done_bar);
           // consume the MMA completions not waited for above
           for (int c = waited; c < kchunks && !failed; ++c) {
-            const int sp = c % kStages;
+            const int sp = c % STAGES;
             if (!tc::mbar_wait(&empty_bar[sp], ph_empty[sp])) failed = true;
             ph_empty[sp] ^= 1u;
           }
@@ -444,7 +454,7 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
   if (failed && tid == 0) {
     atomicExch(A.error, (int32_t)ISING_ERR_TIMEOUT);
     // let copies and MMAs still in flight land before the CTA releases its memory
-    for (int s = 0; s < kStages; ++s)
+    for (int s = 0; s < STAGES; ++s)
       if (tma_pending[s]) tc::mbar_wait(&full_bar[s], ph_full[s]);
     if (mma_pending) {  // a barrier of its own: done_bar's phase may not match after a failure
       tc::mma_commit(&drain_bar);
@@ -522,11 +532,18 @@ cudaError_t dense_tc_run(int n, int n_eval, int R, int Rp, int b, uint64_t seed,
     const char *f = std::getenv("ISING_FAULT");
     A.stall_test = (f && std::strcmp(f, "device_timeout") == 0) ? 1 : 0;
   }
-  if ((e = cudaFuncSetAttribute(dense_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)) !=
-      cudaSuccess)
-    return e;
   const int grid = (Rp / kTM) * kClus;
-  dense_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(mS, mH, mL, A);
+  if (n <= 4096) {
+    constexpr int sm = smem_bytes(3, 4096);
+    if ((e = cudaFuncSetAttribute(dense_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess)
+      return e;
+    dense_tc_kernel<3><<<grid, kThreads, sm, s>>>(mS, mH, mL, A);
+  } else {
+    constexpr int sm = smem_bytes(2, kMaxN);
+    if ((e = cudaFuncSetAttribute(dense_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess)
+      return e;
+    dense_tc_kernel<2><<<grid, kThreads, sm, s>>>(mS, mH, mL, A);
+  }
   return cudaGetLastError();
 }
 

@@ -395,6 +395,28 @@ def test_dense_tc_padded_sizes(n):
     h.close()
 
 
+@pytest.mark.parametrize("n", [5000, 8192])
+def test_dense_tc_sizes_above_4096(n):
+    """4096 < n <= 8192 on the hand-written kernels (two-stage operand pipeline on
+    tensor cores, 256-thread continuation; 5000 zero-padded to 5120): energies of
+    the returned states against the oracle, 1-flip minima, work counters."""
+    inst = _sk_with_fields(n, 200 + n)
+    R = 130
+    h = isg.Handle([inst])
+    assert h.plan_kernel(R) == isg.KERNEL_DENSE_TC
+    h.set_timing(True)
+    res = h.local_search([13], R, max_sweeps=500, restarts=1, kernel=isg.KERNEL_DENSE_TC)
+    torch.cuda.synchronize()
+    names = set(h.kernel_times())
+    h.set_timing(False)
+    assert "dense_tc_kernel" in names and "dense_push_kernel" in names, names
+    sp, E, m = _dense_checks(inst, res, R)
+    st = dict(res.stats)
+    assert st["minima"] == R and st["descents"] == R and np.all(m == 1)
+    assert st["flip_evals"] == st["sweeps"] * n
+    h.close()
+
+
 def test_dense_batch_of_instances():
     """Several dense instances in one handle (sizes with and without padding,
     one with fields): each block of results checked on its own instance, and
