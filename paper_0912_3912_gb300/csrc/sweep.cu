@@ -1224,33 +1224,38 @@ __global__ void __launch_bounds__(kST, 4) sweep_energy(SweepArgs A) {
       else S.E[lane] = (double)hi;
     }
     __syncthreads();
-    if (tid == 0) {
+    if (warp == 0) {
+      // lane = replica: minima, best energies and the next descent's lanes
       if (S.final_pass) {
-        S.final_pass = 0;
+        __syncwarp();
+        if (lane == 0) S.final_pass = 0;
       } else {
-        uint32_t upd = 0;
         const uint32_t cr = S.convround;
-        for (int r = 0; r < 32; ++r)
-          if ((cr >> r) & 1u) {
-            S.minima[r] += 1;
-            if (S.E[r] < S.best[r]) {
-              S.best[r] = S.E[r];
-              upd |= 1u << r;
-            }
+        bool better = false;
+        if ((cr >> lane) & 1u) {
+          S.minima[lane] += 1;
+          const double e = S.E[lane];
+          if (e < S.best[lane]) {
+            S.best[lane] = e;
+            better = true;
           }
-        S.upd = upd;
-        S.k += 1;
-        uint32_t start = 0;
-        if (S.k < A.restarts)
-          for (int r = 0; r < 32; ++r)
-            if (((S.lane_valid >> r) & 1u) && (A.budget <= 0 || S.total[r] < A.budget)) start |= 1u << r;
-        S.start = start;
-        S.active = start;
-        S.convround = 0;
-        S.d = 0;
-        S.round_end = 0;
-        if (!start) S.done = 1;
-        atomicAdd(A.stats + 3, (unsigned long long)__popc(start));
+        }
+        const uint32_t upd = __ballot_sync(0xffffffffu, better);
+        const int k1 = S.k + 1;
+        const bool go = k1 < A.restarts && ((S.lane_valid >> lane) & 1u) && (A.budget <= 0 || S.total[lane] < A.budget);
+        const uint32_t start = __ballot_sync(0xffffffffu, go);
+        __syncwarp();  // every lane has read the group state before lane 0 rewrites it
+        if (lane == 0) {
+          S.upd = upd;
+          S.k = k1;
+          S.start = start;
+          S.active = start;
+          S.convround = 0;
+          S.d = 0;
+          S.round_end = 0;
+          if (!start) S.done = 1;
+          atomicAdd(A.stats + 3, (unsigned long long)__popc(start));
+        }
       }
     }
     __syncthreads();
