@@ -30,7 +30,7 @@ struct DenseRep {
 // registers, one coupling-row update per flip.
 //   J [n][n] FP32, h [n] FP32 (zeros allowed), F [R][n] fields (h included),
 //   S [Rp][n] BF16 spins (rows of the replicas it finishes are rewritten);
-//   n <= 8192, a multiple of 4 (padded; n_eval = the instance's own spins,
+//   n <= 16384, a multiple of 4 (padded; n_eval = the instance's own spins,
 //   for the work counters).
 cudaError_t dense_push_run(int n, int n_eval, int R, int max_sweeps, int budget, const float *J, const float *h,
                            const float *F, __nv_bfloat16 *S, DenseRep *rep, int32_t *counter,

@@ -29,8 +29,8 @@ namespace isg {
 
 namespace {
 
-// One CTA per replica: 128 threads for n <= 4096, 256 for n <= 8192, each with
-// at most kSlots float4 field slots.
+// One CTA per replica: 128 threads for n <= 4096, 256 for n <= 8192, 512 for
+// n <= 16384, each with at most kSlots float4 field slots.
 constexpr int kSlots = 8;
 constexpr int kNone = 0x7fffffff;
 
@@ -62,7 +62,7 @@ struct PushArgs {
 // NS = slots per thread (groups); GUARD: n is not 4 TH NS, so the last group is
 // partial and spins j >= n are masked out.
 template <int NS, bool GUARD, int TH>
-__global__ void __launch_bounds__(TH, TH == 128 ? 6 : 3) dense_push_kernel(PushArgs A) {
+__global__ void __launch_bounds__(TH, TH == 128 ? 6 : (TH == 256 ? 3 : 1)) dense_push_kernel(PushArgs A) {
   constexpr int kThreads = TH;
   __shared__ int s_r;
   __shared__ int s_min[2][kThreads / 32];
@@ -230,8 +230,8 @@ cudaError_t launch_push_ns(const PushArgs &A, int sm_count, cudaStream_t s) {
 cudaError_t dense_push_run(int n, int n_eval, int R, int max_sweeps, int budget, const float *J, const float *h,
                            const float *F, __nv_bfloat16 *S, DenseRep *rep, int32_t *counter,
                            unsigned long long *stats, int sm_count, cudaStream_t s) {
-  // whole float4 groups, 16-byte aligned rows, fields in registers: n % 4 == 0, n <= 8192
-  if (n % 4 != 0 || n < 4 || n > 4 * 256 * kSlots) return cudaErrorInvalidValue;
+  // whole float4 groups, 16-byte aligned rows, fields in registers: n % 4 == 0, n <= 16384
+  if (n % 4 != 0 || n < 4 || n > 4 * 512 * kSlots) return cudaErrorInvalidValue;
   PushArgs A;
   A.n = n;
   A.n_eval = n_eval;
@@ -245,6 +245,14 @@ cudaError_t dense_push_run(int n, int n_eval, int R, int max_sweeps, int budget,
   A.rep = rep;
   A.counter = counter;
   A.stats = stats;
+  if (n > 4 * 256 * kSlots) {  // 8192 < n <= 16384: 512 threads, 5 to 8 slots
+    switch ((n + 4 * 512 - 1) / (4 * 512)) {
+      case 5: return launch_push_ns<5, 512>(A, sm_count, s);
+      case 6: return launch_push_ns<6, 512>(A, sm_count, s);
+      case 7: return launch_push_ns<7, 512>(A, sm_count, s);
+      default: return launch_push_ns<8, 512>(A, sm_count, s);
+    }
+  }
   if (n > 4 * 128 * kSlots) {  // 4096 < n <= 8192: 256 threads, 5 to 8 slots
     switch ((n + 4 * 256 - 1) / (4 * 256)) {
       case 5: return launch_push_ns<5, 256>(A, sm_count, s);

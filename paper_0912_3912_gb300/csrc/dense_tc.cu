@@ -50,17 +50,19 @@ constexpr int kFl = kTB + 1;    // padded row of the block fields [replica][spin
 constexpr int kTileBytes = kTM * kKC * 2;                 // 16 KB
 constexpr int kStageBytes = 3 * kTileBytes;               // A, B_hi, B_lo
 constexpr int kPartialBytes = kTB * kTM * 4;              // 64 KB, [spin][replica]
-// Two shapes: n <= 4096 with a 3-stage operand pipeline, n <= 8192 with 2
-// stages (the spin bits of 8192 spins take the third stage's shared memory).
+// Three shapes: n <= 4096 with a 3-stage operand pipeline, n <= 8192 with 2
+// stages (the spin bits of 8192 spins take the third stage's shared memory),
+// n <= 16384 with 2 stages and the spin bits in global memory.
 // Shared memory: STAGES x (A, Bhi, Blo), the partial block fields, this CTA's
-// 32 replicas' spin bits (1 bit per spin), alignment slack.
-constexpr int kMaxN = 8192;
+// 32 replicas' spin bits (1 bit per spin, maxn = 0: none), alignment slack.
+constexpr int kMaxN = 16384;
+constexpr int kMaxNSmemBits = 8192;
 constexpr int smem_bytes(int stages, int maxn) {
   return stages * kStageBytes + kPartialBytes + 32 * (maxn / 32) * 4 + 1024;
 }
 // the decision phase reuses the stage buffers for its fields and couplings
 static_assert(32 * kFl * 4 + 128 + kTB * kTB * 4 <= 2 * kStageBytes, "decision staging must fit two stages");
-static_assert(smem_bytes(2, kMaxN) <= 227 * 1024 && smem_bytes(3, 4096) <= 227 * 1024, "shared memory per CTA");
+static_assert(smem_bytes(2, kMaxNSmemBits) <= 227 * 1024 && smem_bytes(3, 4096) <= 227 * 1024, "shared memory per CTA");
 
 struct TcArgs {
   int32_t n, R, Rp, b;             // spins (padded to a multiple of 256), replicas, padded replicas, instance
@@ -75,6 +77,7 @@ struct TcArgs {
   DenseRep *rep;                   // [R] per-replica state, read at entry and written back
   unsigned long long *stats;
   int32_t *error;                  // set to ISING_ERR_TIMEOUT when a wait gives up
+  uint32_t *gbits;                 // spin bits in global memory ([CTA][32][n/32]) when GBITS
   int32_t stall_test;              // nonzero: CTA 0 waits, with a short limit, on a barrier nothing
                                    // completes (exercises the failure path in tests)
 };
@@ -97,7 +100,7 @@ __device__ __forceinline__ void write_start_warp(const TcArgs &A, int r, int k, 
 // every block's fields once more without decisions, giving the energy of each
 // replica's state and, for replicas still descending, their full field vectors
 // (exported to Fx for the per-replica continuation).
-template <int STAGES>
+template <int STAGES, bool GBITS>
 __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
     dense_tc_kernel(const __grid_constant__ CUtensorMap mapS, const __grid_constant__ CUtensorMap mapJhi,
                     const __grid_constant__ CUtensorMap mapJlo, TcArgs A) {
@@ -107,7 +110,8 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
   float *P = reinterpret_cast<float *>(smem + STAGES * kStageBytes);  // partial fields [spin][replica]
   float *Floc = reinterpret_cast<float *>(smem);                      // reuses stages: [32 replicas][kFl]
   float *Jblk = reinterpret_cast<float *>(smem + 32 * kFl * 4 + 128); // reuses stages: [128][128]
-  uint32_t *sbits = reinterpret_cast<uint32_t *>(smem + STAGES * kStageBytes + kPartialBytes);  // [32][n/32]
+  uint32_t *sbits = GBITS ? A.gbits + (size_t)blockIdx.x * 32 * (A.n / 32)
+                          : reinterpret_cast<uint32_t *>(smem + STAGES * kStageBytes + kPartialBytes);  // [32][n/32]
 
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar, drain_bar, stall_bar;
   __shared__ uint32_t tmem_base_s;
@@ -500,10 +504,11 @@ cudaError_t tc_encode_2d(CUtensorMap *map, const void *base, uint64_t inner, uin
 // One round's tensor-core sweeps (see dense_tc_kernel).  n a multiple of 256
 // (n_eval <= n the instance's own spins); S: [Rp][n] BF16 spins (Rp a multiple
 // of 128), Jhi/Jlo [n][n] BF16, J [n][n] FP32, h [n] FP32, Fx [R][n] FP32
-// exported fields, rep [R] per-replica state.
+// exported fields, rep [R] per-replica state, gbits: spin bits for n > 8192
+// ((Rp / 128) * 4 CTAs x 32 replicas x n / 32 words; may be null below).
 cudaError_t dense_tc_run(int n, int n_eval, int R, int Rp, int b, uint64_t seed, const float *J, const float *h,
                          const __nv_bfloat16 *Jhi, const __nv_bfloat16 *Jlo, __nv_bfloat16 *S, float *Fx,
-                         DenseRep *rep, int sweeps_a, unsigned long long *stats, int32_t *error,
+                         DenseRep *rep, int sweeps_a, unsigned long long *stats, int32_t *error, uint32_t *gbits,
                          const ising_search_params *p, cudaStream_t s) {
   CUtensorMap mS, mH, mL;
   cudaError_t e;
@@ -533,16 +538,26 @@ cudaError_t dense_tc_run(int n, int n_eval, int R, int Rp, int b, uint64_t seed,
     A.stall_test = (f && std::strcmp(f, "device_timeout") == 0) ? 1 : 0;
   }
   const int grid = (Rp / kTM) * kClus;
+  A.gbits = gbits;
   if (n <= 4096) {
     constexpr int sm = smem_bytes(3, 4096);
-    if ((e = cudaFuncSetAttribute(dense_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(dense_tc_kernel<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) !=
+        cudaSuccess)
       return e;
-    dense_tc_kernel<3><<<grid, kThreads, sm, s>>>(mS, mH, mL, A);
+    dense_tc_kernel<3, false><<<grid, kThreads, sm, s>>>(mS, mH, mL, A);
+  } else if (n <= kMaxNSmemBits) {
+    constexpr int sm = smem_bytes(2, kMaxNSmemBits);
+    if ((e = cudaFuncSetAttribute(dense_tc_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) !=
+        cudaSuccess)
+      return e;
+    dense_tc_kernel<2, false><<<grid, kThreads, sm, s>>>(mS, mH, mL, A);
   } else {
-    constexpr int sm = smem_bytes(2, kMaxN);
-    if ((e = cudaFuncSetAttribute(dense_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) != cudaSuccess)
+    if (!gbits) return cudaErrorInvalidValue;
+    constexpr int sm = smem_bytes(2, 0);
+    if ((e = cudaFuncSetAttribute(dense_tc_kernel<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) !=
+        cudaSuccess)
       return e;
-    dense_tc_kernel<2><<<grid, kThreads, sm, s>>>(mS, mH, mL, A);
+    dense_tc_kernel<2, true><<<grid, kThreads, sm, s>>>(mS, mH, mL, A);
   }
   return cudaGetLastError();
 }

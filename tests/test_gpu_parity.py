@@ -395,11 +395,13 @@ def test_dense_tc_padded_sizes(n):
     h.close()
 
 
-@pytest.mark.parametrize("n", [5000, 8192])
+@pytest.mark.parametrize("n", [5000, 8192, 10000])
 def test_dense_tc_sizes_above_4096(n):
-    """4096 < n <= 8192 on the hand-written kernels (two-stage operand pipeline on
-    tensor cores, 256-thread continuation; 5000 zero-padded to 5120): energies of
-    the returned states against the oracle, 1-flip minima, work counters."""
+    """4096 < n <= 16384 on the hand-written kernels (two-stage operand pipeline
+    on tensor cores with the spin bits in shared memory up to 8192 spins and in
+    global memory above; 256- and 512-thread continuation; 5000 and 10000
+    zero-padded to 5120 and 10240): energies of the returned states against the
+    oracle, 1-flip minima, work counters."""
     inst = _sk_with_fields(n, 200 + n)
     R = 130
     h = isg.Handle([inst])
