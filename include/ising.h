@@ -134,8 +134,8 @@ typedef enum {
   ISING_KERNEL_DENSE_TC = 4, /* dense couplings (J_dense, no hyper-edges), sequential
                                 schedule: a descent's first sweeps with block fields as
                                 a tcgen05 GEMM (BF16 hi+lo), the rest as per-replica
-                                incremental gain updates (n <= 16384; larger n: blocks
-                                with library GEMMs).  Decisions can differ from the FP64
+                                incremental gain updates (any dense instance: at most
+                                16384 spins).  Decisions can differ from the FP64
                                 definition only for fields within ~1e-5 of zero          */
   ISING_KERNEL_PLAIN = 5     /* plain comparator: one launch per instance and colour
                                 class, one thread per (spin, replica), the same field
