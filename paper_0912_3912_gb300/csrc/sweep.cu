@@ -1269,9 +1269,9 @@ __global__ void __launch_bounds__(kST, 4) sweep_energy(SweepArgs A) {
 }
 
 // Best-state copies and random starts decided by the last bookkeeping pass.
-// One warp owns a block of 128 sites: it first copies the improved lanes'
-// current words into the best-state words, then draws the new starts for the
-// same sites, so the copy never sees a new start.
+// One warp owns 32 / LPS consecutive blocks of 128 sites: it first copies the
+// improved lanes' current words into the best-state words, then draws the new
+// starts for the same sites, so the copy never sees a new start.
 template <int LPS>
 __global__ void __launch_bounds__(kST) sweep_restart(SweepArgs A) {
   pdl_prologue();
@@ -1285,26 +1285,36 @@ __global__ void __launch_bounds__(kST) sweep_restart(SweepArgs A) {
     uint32_t *swg = A.sw + (size_t)g * n;
     uint32_t *bwg = A.bw + (size_t)g * n;
     uint32_t *fmg = A.fm + (size_t)g * n;
-    for (int w = blockIdx.x * nw + warp; w < nwb; w += gridDim.x * nw) {
+    // One warp step covers P = 32 / LPS blocks of 128 sites: lane l draws the
+    // bits of replica l % LPS for block w0 + l / LPS, so that a warp transpose
+    // of the 32 lanes' words hands lane u, in bit field j, the word of site u of
+    // the same 32-site quarter of block w0 + j.
+    constexpr int P = 32 / LPS;
+    constexpr uint32_t lmask = LPS == 32 ? 0xffffffffu : ((1u << LPS) - 1u);
+    for (int w0 = (blockIdx.x * nw + warp) * P; w0 < nwb; w0 += gridDim.x * nw * P) {
       if (upd)
-        for (int t = lane; t < 128; t += 32) {
-          const int i = w * 128 + t;
+        for (int t = lane; t < 128 * P; t += 32) {
+          const int i = w0 * 128 + t;
           if (i < n) bwg[i] = (bwg[i] & ~upd) | (swg[i] & upd);
         }
       __syncwarp();
       if (start) {
-        // lane l draws replica 32g + l's bits; a warp transpose hands lane u
-        // the word of site 128w + 32q + u
-        const uint4 x = start_bits(A.seed, (uint32_t)w, (uint32_t)(32 * g + lane), (uint32_t)S.k, (uint32_t)A.b);
+        const int wl = w0 + lane / LPS, rl = lane % LPS;
+        const uint4 x = (wl < nwb && ((start >> rl) & 1u))
+                            ? start_bits(A.seed, (uint32_t)wl, (uint32_t)(32 * g + rl), (uint32_t)S.k, (uint32_t)A.b)
+                            : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const uint32_t xw = word_of(x, q);
-          const uint32_t mine = warp_transpose32(xw, lane);  // lane u: site u's word
-          const int i = w * 128 + q * 32 + lane;
-          if (i < n) {
-            swg[i] = (swg[i] & ~start) | (mine & start);
-            const uint32_t f = fmg[i];
-            if (f & start) fmg[i] = f & ~start;
+          const uint32_t mine = warp_transpose32(word_of(x, q), lane);  // field j: site u of block w0 + j
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            const int i = (w0 + j) * 128 + q * 32 + lane;
+            if (i < n) {
+              const uint32_t word = (mine >> (j * LPS)) & lmask;
+              swg[i] = (swg[i] & ~start) | (word & start);
+              const uint32_t f = fmg[i];
+              if (f & start) fmg[i] = f & ~start;
+            }
           }
         }
       }
