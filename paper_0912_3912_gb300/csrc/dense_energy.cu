@@ -22,9 +22,11 @@
 // take part - the diagonal block I x I through band copies of the planes with
 // the entries j <= i set to zero, the columns to the right of I through the
 // planes themselves.  One CTA per (spin tile, replica tile), tiles with the
-// most columns first; thread 0 keeps a 6-stage TMA -> MMA pipeline full
-// (128-byte swizzled K-major tiles: spins [128 x 64], plane rows [128 x 64]),
-// one FP32 accumulator of 128 columns per plane in tensor memory; warps 0-3
+// most columns first; thread 0 keeps a 2-stage TMA -> MMA pipeline full, a
+// stage holding one spin tile [128 x 64] and the four planes' row tiles
+// [128 x 64] of the same columns (128-byte swizzled K-major), so that a spin
+// tile is loaded once for all four planes; one FP32 accumulator of 128 columns
+// per plane in tensor memory; warps 0-3
 // then read the four accumulators (warp w: tensor-memory lanes 32w .. 32w+31,
 // one replica per thread) and form the tile's integer dot products with the
 // replica's spins.  Every wait is bounded; a CTA whose wait gives up records
@@ -49,12 +51,12 @@ namespace {
 constexpr int kEM = 128;                    // replicas per tile (MMA M)
 constexpr int kEN = 128;                    // spins per tile (MMA N)
 constexpr int kEK = 64;                     // K per chunk (128 bytes of BF16)
-constexpr int kESt = 6;                     // pipeline stages
+constexpr int kESt = 2;                     // pipeline stages
 constexpr int kEPl = 4;                     // digit planes
 constexpr int kEThreads = 128;              // 4 warps: one thread feeds the pipeline, all read the result
 constexpr int kEA = kEM * kEK * 2;          // 16 KB spin tile
 constexpr int kEB = kEN * kEK * 2;          // 16 KB plane tile
-constexpr int kEStage = kEA + kEB;
+constexpr int kEStage = kEA + kEPl * kEB;   // 80 KB: a spin tile and the four planes' tiles
 constexpr int kESmem = kESt * kEStage + 1024;  // + alignment slack
 
 struct EnArgs {
@@ -83,8 +85,7 @@ __global__ void __launch_bounds__(kEThreads, 1)
   const int tn = blockIdx.x / tm_count, tm = blockIdx.x % tm_count;  // spin tile 0 has the most columns
   const int r0 = tm * kEM, i0 = tn * kEN;
   constexpr int kd = kEN / kEK;                      // band chunks (the diagonal block), per plane
-  const int per_p = kd + (A.np - i0 - kEN) / kEK;    // chunks per plane
-  const int nchunks = kEPl * per_p;
+  const int nchunks = kd + (A.np - i0 - kEN) / kEK;  // column chunks (each for all four planes)
 
   if (tid == 0) {
     for (int s = 0; s < kESt; ++s) {
@@ -108,21 +109,22 @@ __global__ void __launch_bounds__(kEThreads, 1)
     for (int s = 0; s < kESt; ++s) ph_full[s] = ph_empty[s] = 0u;
     int issued = 0, consumed = 0;
     bool ok = true;
-    auto load = [&](int c) {
-      const int s = c % kESt;
-      const int d = c / per_p, q = c % per_p;
+    const CUtensorMap *mu[kEPl] = {&mapU0, &mapU1, &mapU2, &mapU3};
+    const CUtensorMap *mp[kEPl] = {&mapP0, &mapP1, &mapP2, &mapP3};
+    auto load = [&](int q) {
+      const int s = q % kESt;
       uint8_t *st = smem + s * kEStage;
       tc::mbar_arrive_expect_tx(&full_bar[s], kEStage);
       if (q < kd) {
         // band chunk: columns i0 + 64 q .. of the diagonal block, band-local
         tc::tma_load_2d(st, &mapS, &full_bar[s], i0 + q * kEK, r0);
-        const CUtensorMap *mu = d == 0 ? &mapU0 : (d == 1 ? &mapU1 : (d == 2 ? &mapU2 : &mapU3));
-        tc::tma_load_2d(st + kEA, mu, &full_bar[s], q * kEK, i0);
+#pragma unroll
+        for (int d = 0; d < kEPl; ++d) tc::tma_load_2d(st + kEA + d * kEB, mu[d], &full_bar[s], q * kEK, i0);
       } else {
         const int col = i0 + kEN + (q - kd) * kEK;
         tc::tma_load_2d(st, &mapS, &full_bar[s], col, r0);
-        const CUtensorMap *mp = d == 0 ? &mapP0 : (d == 1 ? &mapP1 : (d == 2 ? &mapP2 : &mapP3));
-        tc::tma_load_2d(st + kEA, mp, &full_bar[s], col, i0);
+#pragma unroll
+        for (int d = 0; d < kEPl; ++d) tc::tma_load_2d(st + kEA + d * kEB, mp[d], &full_bar[s], col, i0);
       }
     };
     for (; issued < kESt && issued < nchunks; ++issued) load(issued);
@@ -134,13 +136,16 @@ __global__ void __launch_bounds__(kEThreads, 1)
       }
       ph_full[s] ^= 1u;
       tc::tc_fence_after();
-      const int d = c / per_p, q = c % per_p;
       uint8_t *st = smem + s * kEStage;
-      const uint64_t da = tc::smem_desc_k_sw128(st), db = tc::smem_desc_k_sw128(st + kEA);
-      const uint32_t dst = tmem + (uint32_t)(d * kEN);
+      const uint64_t da = tc::smem_desc_k_sw128(st);
 #pragma unroll
-      for (int kk = 0; kk < kEK / 16; ++kk)
-        tc::mma_bf16(dst, da + 2 * kk, db + 2 * kk, idesc, (q > 0 || kk > 0) ? 1u : 0u);
+      for (int d = 0; d < kEPl; ++d) {
+        const uint64_t db = tc::smem_desc_k_sw128(st + kEA + d * kEB);
+        const uint32_t dst = tmem + (uint32_t)(d * kEN);
+#pragma unroll
+        for (int kk = 0; kk < kEK / 16; ++kk)
+          tc::mma_bf16(dst, da + 2 * kk, db + 2 * kk, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+      }
       tc::mma_commit(&empty_bar[s]);
       consumed = c + 1;
       // refill the stage of the previous chunk once its MMAs have read it
