@@ -11,8 +11,9 @@
 // integer (|J_ij - Q_ij 2^-F| <= 2^(-F-1) <= max|J| 2^-31) and is written in
 // balanced base 256:  Q = P0 + 256 P1 + 256^2 P2 + 256^3 P3,  P_d in [-128, 128],
 // each plane exact in BF16.  Against spins +/-1 every product of a plane GEMM
-// is an integer of magnitude <= 128 and every partial sum over K <= 8192 terms
-// stays below 2^20, so the tensor cores' FP32 accumulation never rounds: each
+// is an integer of magnitude <= 128 and every partial sum over K <= 16384 terms
+// stays below 2^21 (FP32 holds every integer below 2^24), so the tensor cores'
+// FP32 accumulation never rounds: each
 // plane's result G_d = P_d . s is exact, whatever the accumulator's rounding
 // mode.  The energy is then assembled in integers:
 //     E_r = - 2^-F sum_{i<j} Q_ij s_ri s_rj - sum_i h_i s_ri,
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(kEThreads, 1)
       }
       up[w] = bits;
     }
-    // sum_i s_i G_d,i for each plane, exact integers (|G| < 2^20, 128 columns)
+    // sum_i s_i G_d,i for each plane, exact integers (|G| < 2^21, 128 columns)
     long long tot = 0;
 #pragma unroll 1
     for (int d = 0; d < kEPl; ++d) {
