@@ -566,3 +566,39 @@ def test_kernel_timing_window():
     kt2 = h2.kernel_times()
     assert kt2["sweep_chunk"][1] >= 1 and kt2["tile_kernel"][1] == 1
     h2.close()
+
+
+# ----------------------------------------------------------- evaluated visits and the logic-op peak
+@pytest.mark.parametrize("kernel", [isg.KERNEL_TILE, isg.KERNEL_MSC, isg.KERNEL_SWEEP, isg.KERNEL_PLAIN])
+def test_evaluated_visits_counter(kernel):
+    """ising_stats.evaluated: at most the visits (flip_evals), every visit of the
+    fresh first sweeps at least (a descent's first sweep evaluates everything),
+    equal to the visits for the family that never skips, and independent of
+    whether the counters were requested twice (the search itself is unchanged)."""
+    inst = W.lattice((16, 16, 16), periodic=True, couplings="pm1", fields="pm1_0", seed=93)
+    R, restarts = 32, 3
+    h = isg.Handle([inst])
+    a = h.local_search([8], R, max_sweeps=100, restarts=restarts, kernel=kernel, stats=True)
+    b = h.local_search([8], R, max_sweeps=100, restarts=restarts, kernel=kernel, stats=True)
+    torch.cuda.synchronize()
+    sa, sb = dict(a.stats), dict(b.stats)
+    assert sa == sb
+    assert sa["evaluated"] <= sa["flip_evals"]
+    assert sa["evaluated"] >= sa["descents"] * inst.n  # first sweeps visit every spin of every replica
+    if kernel == isg.KERNEL_PLAIN:
+        assert sa["evaluated"] == sa["flip_evals"]
+    else:
+        assert sa["evaluated"] < sa["flip_evals"]  # later sweeps skip stable spins
+    assert np.array_equal(a.spins.cpu().numpy(), b.spins.cpu().numpy())
+    h.close()
+
+
+def test_logic_peak_measurement():
+    """ising_logic_peak: a positive issue rate of 32-bit logic ops, below 128
+    lanes per SM per clock at the highest SM clock any GB300 runs (2.1 GHz), and
+    repeatable to within a few percent."""
+    p1 = isg.logic_peak()
+    p2 = isg.logic_peak()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert 0 < p1 <= sms * 128 * 2.1e9
+    assert abs(p1 - p2) <= 0.05 * max(p1, p2)
