@@ -38,7 +38,7 @@ bool dense_tc_eligible(int n);
 int dense_tc_padded(int n);
 cudaError_t dense_tc_run(int n, int n_eval, int R, int Rp, int b, uint64_t seed, const float *J, const float *h,
                          const __nv_bfloat16 *Jhi, const __nv_bfloat16 *Jlo, __nv_bfloat16 *S, float *Fx,
-                         DenseRep *rep, int sweeps_a, unsigned long long *stats, int32_t *error, uint32_t *gbits,
+                         DenseRep *rep, int sweeps_a, unsigned long long *stats, int32_t *error,
                          const ising_search_params *p, cudaStream_t s);
 
 namespace {
@@ -305,7 +305,6 @@ struct DenseState : FamilyState {
   int8_t *best = nullptr;
   int32_t *active = nullptr, *h_active = nullptr;
   __nv_bfloat16 *S_tc = nullptr;  // [Rp128][np] replica-major spins for the tcgen05 kernel
-  uint32_t *gbits = nullptr;      // the tcgen05 kernel's spin bits above 8192 spins [Rp128][np / 32]
   // tensor-core path with n padded to np (a multiple of 256): own copies of J
   // (FP32 and BF16 split) and h when np != n, else the unpadded ones
   int32_t np = 0;
@@ -335,7 +334,6 @@ void free_state(DenseState &D) {
   cudaFree(D.active);
   cudaFree(D.workspace);
   cudaFree(D.S_tc);
-  cudaFree(D.gbits);
   cudaFree(D.err);
   cudaFree(D.counter);
   cudaFree(D.Sx);
@@ -477,7 +475,6 @@ cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t 
         }
         if ((e = cudaMalloc(&D.S_tc, (size_t)Rp128 * np * 2)) != cudaSuccess) return e;
         if ((e = cudaMemset(D.S_tc, 0, (size_t)Rp128 * np * 2)) != cudaSuccess) return e;
-        if (np > 8192 && (e = cudaMalloc(&D.gbits, (size_t)Rp128 * (np / 32) * 4)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&D.planes, (size_t)4 * np * np * 2)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&D.bands, (size_t)4 * np * 128 * 2)) != cudaSuccess) return e;
         if ((e = cudaMalloc(&D.Se, (size_t)Rp128 * np * 2)) != cudaSuccess) return e;
@@ -501,7 +498,7 @@ cudaError_t launch_dense(ising_handle *h, const ising_search_params *p, int32_t 
       for (;;) {
         kt_begin(h, "dense_tc_kernel", s);
         e = dense_tc_run(np, n, R, Rp128, b, seed, D.Jp, D.hp, D.tc_hi, D.tc_lo, D.S_tc, D.Fx, D.rep, sweeps_a,
-                         h->d_stats, D.err, D.gbits, p, s);
+                         h->d_stats, D.err, p, s);
         kt_end(h, s);
         if (e != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(D.counter, 0, 4, s)) != cudaSuccess) return e;

@@ -16,9 +16,15 @@
 // states together and sweep in lockstep.  CTA q multiplies the K-slice
 // j in [q n/4, (q+1) n/4) into its own tensor-memory accumulator; the four
 // partial blocks are exchanged through distributed shared memory and summed in
-// a fixed order; CTA q then decides replicas 32q..32q+31.  Thread 0 of each CTA
-// issues the TMA loads (128-byte swizzled K-major tiles) and the MMAs through a
-// 3-stage mbarrier pipeline.  A last pass without decisions exports the full
+// a fixed order; CTA q then decides replicas 32q..32q+31.  The spin operand
+// comes from tensor memory: CTA q keeps the spin bits of all 128 replicas over
+// its K-slice in shared memory, and four warps expand each 64-spin chunk to
+// BF16 +/-1 and store it to tensor memory (tcgen05.st), so that only the
+// coupling tiles pass through shared memory (TMA loads, 128-byte swizzled
+// K-major) and the MMAs read one shared-memory operand instead of two.
+// Thread 0 of each CTA issues the loads and the MMAs through a 4-stage mbarrier
+// pipeline.  The deciding warps read and write their replicas' bits of a block
+// in the owning CTA's shared memory (distributed shared memory).  A last pass without decisions exports the full
 // field vectors of the replicas still descending, which dense_push.cu continues
 // one replica at a time: the first sweeps flip most spins (a GEMM per block is
 // then cheap per flip), the later ones few, and their number varies widely
@@ -47,22 +53,26 @@ constexpr int kKC = 64;         // K per TMA chunk (128 bytes of BF16)
 constexpr int kClus = 4;        // CTAs per cluster (split K)
 constexpr int kThreads = 1024;  // one warp per decided replica (32 per CTA)
 constexpr int kFl = kTB + 1;    // padded row of the block fields [replica][spin]
-constexpr int kTileBytes = kTM * kKC * 2;                 // 16 KB
-constexpr int kStageBytes = 3 * kTileBytes;               // A, B_hi, B_lo
+constexpr int kTileBytes = kTB * kKC * 2;                 // 16 KB, one coupling tile
+constexpr int kStages = 4;                                // operand pipeline depth
+constexpr int kStageBytes = 2 * kTileBytes;               // B_hi, B_lo
 constexpr int kPartialBytes = kTB * kTM * 4;              // 64 KB, [spin][replica]
-// Three shapes: n <= 4096 with a 3-stage operand pipeline, n <= 8192 with 2
-// stages (the spin bits of 8192 spins take the third stage's shared memory),
-// n <= 16384 with 2 stages and the spin bits in global memory.
-// Shared memory: STAGES x (A, Bhi, Blo), the partial block fields, this CTA's
-// 32 replicas' spin bits (1 bit per spin, maxn = 0: none), alignment slack.
+constexpr int kJblkBytes = kTB * kTB * 4;                 // 64 KB, the block's couplings in FP32
+constexpr int kFlocBytes = 32 * kFl * 4;                  // this CTA's replicas' block fields
+constexpr int kAcc = kTB;                                 // tensor-memory columns of the accumulator
+constexpr int kACols = kKC / 2;                           // columns of one spin chunk (two BF16 per column)
+constexpr int kTmemCols = 256;                            // accumulator + kStages spin chunks
+constexpr int kGen0 = 4;                                  // warps kGen0..kGen0+3 write the spin chunks
 constexpr int kMaxN = 16384;
-constexpr int kMaxNSmemBits = 8192;
-constexpr int smem_bytes(int stages, int maxn) {
-  return stages * kStageBytes + kPartialBytes + 32 * (maxn / 32) * 4 + 1024;
-}
-// the decision phase reuses the stage buffers for its fields and couplings
-static_assert(32 * kFl * 4 + 128 + kTB * kTB * 4 <= 2 * kStageBytes, "decision staging must fit two stages");
-static_assert(smem_bytes(2, kMaxNSmemBits) <= 227 * 1024 && smem_bytes(3, 4096) <= 227 * 1024, "shared memory per CTA");
+// Shared memory: the stages (once a block's MMAs have completed they hold its
+// partial fields and FP32 couplings until the next block's loads), the decided
+// replicas' fields, the spin bits [n / 128 words][128 replicas] of the CTA's
+// K-slice, alignment slack.
+constexpr int smem_bytes(int n) { return kStages * kStageBytes + kFlocBytes + 4 * n + 1024; }
+static_assert(kPartialBytes + kJblkBytes <= kStages * kStageBytes, "partials and couplings must fit the stages");
+static_assert(smem_bytes(kMaxN) + 2048 <= 227 * 1024, "shared memory per CTA (2 KB for the static part)");
+static_assert(kAcc + kStages * kACols <= kTmemCols, "tensor-memory columns");
+static_assert(kGen0 >= 1 && kGen0 + 4 <= kThreads / 32, "spin-chunk warps: not warp 0 (thread 0 issues)");
 
 struct TcArgs {
   int32_t n, R, Rp, b;             // spins (padded to a multiple of 256), replicas, padded replicas, instance
@@ -77,20 +87,35 @@ struct TcArgs {
   DenseRep *rep;                   // [R] per-replica state, read at entry and written back
   unsigned long long *stats;
   int32_t *error;                  // set to ISING_ERR_TIMEOUT when a wait gives up
-  uint32_t *gbits;                 // spin bits in global memory ([CTA][32][n/32]) when GBITS
   int32_t stall_test;              // nonzero: CTA 0 waits, with a short limit, on a barrier nothing
                                    // completes (exercises the failure path in tests)
 };
 
-// Philox start R(b, r, k) of replica r, written as BF16 +/-1 into S[r][:] and
-// as bits; warp-cooperative, lane l handles the 128-spin blocks l, l + 32, ...
-__device__ __forceinline__ void write_start_warp(const TcArgs &A, int r, int k, uint32_t *bits, int lane) {
+// Philox start R(b, r, k) of replica r, written as BF16 +/-1 into S[r][:];
+// warp-cooperative, lane l handles the 128-spin blocks l, l + 32, ...
+__device__ __forceinline__ void write_start_warp(const TcArgs &A, int r, int k, int lane) {
   __nv_bfloat16 *row = A.S + (size_t)r * A.n;
   for (int w = lane; w * 128 < A.n; w += 32) {
     const uint4 x = start_bits(A.seed, (uint32_t)w, (uint32_t)r, (uint32_t)k, (uint32_t)A.b);
-    for (int q = 0; q < 4; ++q) bits[w * 4 + q] = word_of(x, q);
     for (int t = 0; t < 128 && w * 128 + t < A.n; ++t)
       row[w * 128 + t] = __float2bfloat16_rn(((word_of(x, t / 32) >> (t % 32)) & 1u) ? 1.0f : -1.0f);
+  }
+}
+
+// Spins 2c and 2c + 1 of a 32-spin word (bit = 1: +1) as two BF16 +/-1 in one
+// 32-bit tensor-memory column (the lower K index in the low half).
+__device__ __forceinline__ uint32_t pm1_pair(uint32_t w, int c) {
+  return 0xBF80BF80u ^ (((w >> (2 * c)) & 1u) << 15) ^ (((w >> (2 * c + 1)) & 1u) << 31);
+}
+
+// Bounded wait of the spin-chunk warps; gives up at once when thread 0 has
+// failed (its MMAs, which complete the barrier, will not come).
+__device__ __forceinline__ bool gen_wait(uint64_t *bar, uint32_t parity, const volatile int32_t *abort) {
+  const uint64_t t0 = tc::global_ns();
+  for (;;) {
+    for (int it = 0; it < 64; ++it)
+      if (tc::mbar_try_wait(bar, parity)) return true;
+    if (*abort || tc::global_ns() - t0 > 1000000000ull) return false;
   }
 }
 
@@ -100,20 +125,22 @@ __device__ __forceinline__ void write_start_warp(const TcArgs &A, int r, int k, 
 // every block's fields once more without decisions, giving the energy of each
 // replica's state and, for replicas still descending, their full field vectors
 // (exported to Fx for the per-replica continuation).
-template <int STAGES, bool GBITS>
 __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
-    dense_tc_kernel(const __grid_constant__ CUtensorMap mapS, const __grid_constant__ CUtensorMap mapJhi,
-                    const __grid_constant__ CUtensorMap mapJlo, TcArgs A) {
+    dense_tc_kernel(const __grid_constant__ CUtensorMap mapJhi, const __grid_constant__ CUtensorMap mapJlo, TcArgs A) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t *stage = smem;                                              // STAGES x (A, Bhi, Blo)
-  float *P = reinterpret_cast<float *>(smem + STAGES * kStageBytes);  // partial fields [spin][replica]
-  float *Floc = reinterpret_cast<float *>(smem);                      // reuses stages: [32 replicas][kFl]
-  float *Jblk = reinterpret_cast<float *>(smem + 32 * kFl * 4 + 128); // reuses stages: [128][128]
-  uint32_t *sbits = GBITS ? A.gbits + (size_t)blockIdx.x * 32 * (A.n / 32)
-                          : reinterpret_cast<uint32_t *>(smem + STAGES * kStageBytes + kPartialBytes);  // [32][n/32]
+  uint8_t *stage = smem;                                              // kStages x (Bhi, Blo)
+  float *P = reinterpret_cast<float *>(smem);                         // in the stages: partial fields [spin][replica]
+  float *Jblk = reinterpret_cast<float *>(smem + kPartialBytes);      // in the stages: [128][128]
+  float *Floc = reinterpret_cast<float *>(smem + kStages * kStageBytes);  // [32 replicas][kFl]
+  // spin bits of the cluster's 128 replicas over this CTA's K-slice: word w
+  // (spins kbase + 32 w .. + 31, bit t = spin kbase + 32 w + t, 1 = +1) of
+  // replica r0 + row at kbits[w * 128 + row]
+  uint32_t *kbits = reinterpret_cast<uint32_t *>(smem + kStages * kStageBytes + kFlocBytes);
 
-  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar, drain_bar, stall_bar;
+  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], afull_bar[kStages], done_bar, drain_bar,
+      stall_bar;
+  __shared__ volatile int32_t s_abort;  // thread 0 failed: the spin-chunk warps stop waiting
   __shared__ uint32_t tmem_base_s;
   __shared__ int32_t s_flag[2];   // cluster-visible: [0] my replicas still busy, [1] my failure
   __shared__ int32_t s_ctrl[4];   // broadcast inside the CTA
@@ -126,23 +153,24 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
   const int r0 = tile * kTM;                 // first replica of the cluster
   const int rq = r0 + 32 * (int)q;           // first replica this CTA decides
   const int n = A.n, nblk = n / kTB, kslice = n / kClus;
-  const int kchunks = kslice / kKC;
+  const int kchunks = kslice / kKC, kbase = (int)q * kslice;
   constexpr uint32_t idesc = tc::idesc_bf16_f32(kTM, kTB);
 
   if (tid == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < kStages; ++s) {
       tc::mbar_init(&full_bar[s], 1);
       tc::mbar_init(&empty_bar[s], 1);
+      tc::mbar_init(&afull_bar[s], 4);  // one arrival per spin-chunk warp
     }
     tc::mbar_init(&done_bar, 1);
     tc::mbar_init(&drain_bar, 1);
     tc::mbar_init(&stall_bar, 1);
     tc::fence_barrier_init();
-    tc::prefetch_tmap(&mapS);
     tc::prefetch_tmap(&mapJhi);
     tc::prefetch_tmap(&mapJlo);
+    s_abort = 0;
   }
-  if (warp == 0) tc::tmem_alloc(&tmem_base_s, 128);
+  if (warp == 0) tc::tmem_alloc(&tmem_base_s, kTmemCols);
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
@@ -176,15 +204,24 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
     }
   }
   unsigned long long c_evals = 0, c_flips = 0, c_sweeps = 0;
-  const int nw32 = n / 32;
   __syncthreads();
-  if (rq + warp < A.R && s_run[warp]) write_start_warp(A, rq + warp, s_nfl[warp], sbits + warp * nw32, lane);
-  tc::fence_proxy_async_global();
+  if (rq + warp < A.R && s_run[warp]) write_start_warp(A, rq + warp, s_nfl[warp], lane);
+  // the start bits of every replica of the cluster taking part in the round,
+  // over this CTA's K-slice (item e: replica r0 + e % 128, word e / 128; the
+  // slice need not start on a 128-spin block)
+  for (int e = tid; e < kTM * (kslice / 32); e += kThreads) {
+    const int row = e & (kTM - 1), w = e / kTM, r = r0 + row, g = kbase / 32 + w;
+    if (r < A.R && A.rep[r].round) {
+      const uint4 x = start_bits(A.seed, (uint32_t)(g / 4), (uint32_t)r, (uint32_t)A.rep[r].k, (uint32_t)A.b);
+      kbits[w * kTM + row] = word_of(x, g & 3);
+    }
+  }
   bool failed = false;
-  uint32_t ph_full[STAGES], ph_empty[STAGES], ph_done = 0;
-  int tma_pending[STAGES], mma_pending = 0;
+  uint32_t ph_full[kStages], ph_empty[kStages], ph_a[kStages], ph_done = 0;
+  int tma_pending[kStages], mma_pending = 0;
 #pragma unroll
-  for (int st2 = 0; st2 < STAGES; ++st2) ph_full[st2] = ph_empty[st2] = 0, tma_pending[st2] = 0;
+  for (int st2 = 0; st2 < kStages; ++st2) ph_full[st2] = ph_empty[st2] = ph_a[st2] = 0, tma_pending[st2] = 0;
+  uint32_t g_used = 0, g_ph = 0;  // spin-chunk warps: stages written before, parity of their next completion
   tc::cluster_sync();
 
   for (int sw = 0; sw <= A.sweeps_a; ++sw) {
@@ -217,68 +254,98 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
     for (int blk = 0; blk < nblk; ++blk) {
       const int b0 = blk * kTB;
       // Phase 1: partial fields of the block over this CTA's K-slice.  Thread 0
-      // keeps STAGES chunks in flight: after issuing chunk kc's MMAs it refills
+      // keeps kStages chunks in flight: after issuing chunk kc's MMAs it refills
       // the stage of chunk kc-1 once those MMAs have read it, so the tensor pipe
-      // always has the next chunk queued.
+      // always has the next chunk queued.  The spin-chunk warps write chunk kc's
+      // spins to the tensor-memory columns of its stage once the MMAs of the
+      // stage's previous chunk have completed.
       if (tid == 0 && !failed) {
-        const int kbase = (int)q * kslice;
         auto load = [&](int s, int kn) {
           uint8_t *st_ = stage + s * kStageBytes;
           tc::mbar_arrive_expect_tx(&full_bar[s], kStageBytes);
-          tc::tma_load_2d(st_, &mapS, &full_bar[s], kbase + kn * kKC, r0);
-          tc::tma_load_2d(st_ + kTileBytes, &mapJhi, &full_bar[s], kbase + kn * kKC, b0);
-          tc::tma_load_2d(st_ + 2 * kTileBytes, &mapJlo, &full_bar[s], kbase + kn * kKC, b0);
+          tc::tma_load_2d(st_, &mapJhi, &full_bar[s], kbase + kn * kKC, b0);
+          tc::tma_load_2d(st_ + kTileBytes, &mapJlo, &full_bar[s], kbase + kn * kKC, b0);
           tma_pending[s] = 1;
         };
-        for (int s = 0; s < STAGES && s < kchunks; ++s) load(s, s);
+        for (int s = 0; s < kStages && s < kchunks; ++s) load(s, s);
         if (A.stall_test && blockIdx.x == 0 && sw == 0 && blk == 0 && !tc::mbar_wait(&stall_bar, 0, 20000))
           failed = true;  // nothing arrives on stall_bar: the wait gives up after 20 us
         int waited = 0;  // chunks whose MMA completion (empty barrier) has been consumed
         for (int kc = 0; kc < kchunks && !failed; ++kc) {
-          const int s = kc % STAGES;
+          const int s = kc % kStages;
           if (!tc::mbar_wait(&full_bar[s], ph_full[s])) {
             failed = true;
             break;
           }
           ph_full[s] ^= 1u;
           tma_pending[s] = 0;
+          if (!tc::mbar_wait(&afull_bar[s], ph_a[s])) {
+            failed = true;
+            break;
+          }
+          ph_a[s] ^= 1u;
           tc::tc_fence_after();
           uint8_t *st_ = stage + s * kStageBytes;
-          const uint64_t da = tc::smem_desc_k_sw128(st_);
-          const uint64_t dh = tc::smem_desc_k_sw128(st_ + kTileBytes);
-          const uint64_t dl = tc::smem_desc_k_sw128(st_ + 2 * kTileBytes);
+          const uint64_t dh = tc::smem_desc_k_sw128(st_);
+          const uint64_t dl = tc::smem_desc_k_sw128(st_ + kTileBytes);
+          const uint32_t ta = tmem + (uint32_t)(kAcc + s * kACols);
 #pragma unroll
           for (int kk = 0; kk < kKC / 16; ++kk)
-            tc::mma_bf16(tmem, da + 2 * kk, dh + 2 * kk, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+            tc::mma_bf16_ts(tmem, ta + 8 * kk, dh + 2 * kk, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
 #pragma unroll
-          for (int kk = 0; kk < kKC / 16; ++kk) tc::mma_bf16(tmem, da + 2 * kk, dl + 2 * kk, idesc, 1u);
+          for (int kk = 0; kk < kKC / 16; ++kk) tc::mma_bf16_ts(tmem, ta + 8 * kk, dl + 2 * kk, idesc, 1u);
           tc::mma_commit(&empty_bar[s]);
           mma_pending = 1;
           if (kc >= 1) {
-            const int pc = kc - 1, sp = pc % STAGES;
+            const int pc = kc - 1, sp = pc % kStages;
             if (!tc::mbar_wait(&empty_bar[sp], ph_empty[sp])) {
               failed = true;
               break;
             }
             ph_empty[sp] ^= 1u;
             waited = kc;
-            if (pc + STAGES < kchunks) load(sp, pc + STAGES);
+            if (pc + kStages < kchunks) load(sp, pc + kStages);
           }
         }
         if (!failed) {
           tc::mma_commit(&done_bar);
           // consume the MMA completions not waited for above
           for (int c = waited; c < kchunks && !failed; ++c) {
-            const int sp = c % STAGES;
+            const int sp = c % kStages;
             if (!tc::mbar_wait(&empty_bar[sp], ph_empty[sp])) failed = true;
             ph_empty[sp] ^= 1u;
           }
         }
+        if (failed) s_abort = 1;
+      } else if (warp >= kGen0 && warp < kGen0 + 4 && !failed) {
+        // spin-chunk warp: tensor-memory lanes 32 lq .. + 31 = replicas r0 + 32 lq + lane
+        const int lq = warp - kGen0, row = 32 * lq + lane;
+        const uint32_t trow = tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)kAcc;
+        for (int kc = 0; kc < kchunks; ++kc) {
+          const int s = kc % kStages;
+          if ((g_used >> s) & 1u) {
+            if (!gen_wait(&empty_bar[s], (g_ph >> s) & 1u, &s_abort)) {
+              failed = true;
+              break;
+            }
+            g_ph ^= 1u << s;
+          }
+          g_used |= 1u << s;
+          const uint32_t w0 = kbits[(2 * kc) * kTM + row], w1 = kbits[(2 * kc + 1) * kTM + row];
+          uint32_t v[32];
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            v[c] = pm1_pair(w0, c);
+            v[16 + c] = pm1_pair(w1, c);
+          }
+          tc::tc_fence_after();
+          tc::tmem_st32(trow + (uint32_t)(s * kACols), v);
+          tc::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&afull_bar[s]);
+        }
       }
-      __syncthreads();
-      if (tid == 0) s_ctrl[2] = failed ? 1 : 0;
-      __syncthreads();
-      failed = s_ctrl[2] != 0;
+      failed = __syncthreads_or(failed) != 0;
       // Phase 2: accumulator -> shared memory, transposed to [spin][replica]
       {
         const bool ok = failed ? true : tc::mbar_wait(&done_bar, ph_done);
@@ -339,12 +406,17 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
       {
         const int rr = rq + warp;
         const bool valid_r = rr < A.R && !failed;
-        uint32_t *mybits = sbits + warp * nw32 + (b0 >> 5);
-        uint32_t wq[4] = {0u, 0u, 0u, 0u};  // the block's 128 spins of replica rr (1 = +1)
+        // word j of the block's bits of replica rr lives in the CTA whose K-slice
+        // holds spins b0 + 32 j .. + 31 (a K-slice may end inside a block); lane
+        // j < 4 fetches it
+        const int gw = (b0 >> 5) + (lane & 3), qb = (32 * gw) / kslice;
+        const uint32_t baddr = tc::map_shared(kbits + (gw - qb * (kslice >> 5)) * kTM + 32 * (int)q + warp, (uint32_t)qb);
+        const uint32_t mine = (valid_r && lane < 4) ? tc::ld_cluster_u32(baddr) : 0u;
+        uint32_t wq[4];  // the block's 128 spins of replica rr (1 = +1)
         float f[4];
 #pragma unroll
         for (int qq = 0; qq < 4; ++qq) {
-          if (valid_r) wq[qq] = mybits[qq];
+          wq[qq] = __shfl_sync(0xffffffffu, mine, qq);
           f[qq] = valid_r ? Floc[warp * kFl + 32 * qq + lane] : 0.0f;
         }
         if (export_pass) {
@@ -392,10 +464,8 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
             }
           }
           if (nfl) {
-            if (lane == 0) {
-#pragma unroll
-              for (int qq = 0; qq < 4; ++qq) mybits[qq] = wq[qq];
-            }
+            if (lane < 4)
+              tc::st_cluster_u32(baddr, lane == 0 ? wq[0] : lane == 1 ? wq[1] : lane == 2 ? wq[2] : wq[3]);
             __nv_bfloat16 *row = A.S + (size_t)rr * n + b0;
 #pragma unroll
             for (int qq = 0; qq < 4; ++qq)
@@ -413,12 +483,11 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
           c_flips += (unsigned long long)s_nfl[lane];
         }
       }
-      // generic-proxy writes (new spins in global memory, the staged fields and
-      // couplings in shared memory) are ordered before the next TMA writes/reads
-      tc::fence_proxy_async_global();
+      // generic-proxy writes to the stages (partials, fields, couplings) are
+      // ordered before the next block's TMA writes
       tc::fence_proxy_async_shared();
       __syncthreads();
-      tc::cluster_sync();  // new spins visible to every CTA's next TMA loads
+      tc::cluster_sync();  // new spin bits visible to every CTA's next block
     }
     // (a CTA that failed keeps the cluster's barrier sequence; the control step
     // of the next sweep ends the cluster together)
@@ -458,7 +527,7 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
   if (failed && tid == 0) {
     atomicExch(A.error, (int32_t)ISING_ERR_TIMEOUT);
     // let copies and MMAs still in flight land before the CTA releases its memory
-    for (int s = 0; s < STAGES; ++s)
+    for (int s = 0; s < kStages; ++s)
       if (tma_pending[s]) tc::mbar_wait(&full_bar[s], ph_full[s]);
     if (mma_pending) {  // a barrier of its own: done_bar's phase may not match after a failure
       tc::mma_commit(&drain_bar);
@@ -467,7 +536,7 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
   }
   tc::tc_fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, 128);
+  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
 }  // namespace
@@ -504,19 +573,17 @@ cudaError_t tc_encode_2d(CUtensorMap *map, const void *base, uint64_t inner, uin
 // One round's tensor-core sweeps (see dense_tc_kernel).  n a multiple of 256
 // (n_eval <= n the instance's own spins); S: [Rp][n] BF16 spins (Rp a multiple
 // of 128), Jhi/Jlo [n][n] BF16, J [n][n] FP32, h [n] FP32, Fx [R][n] FP32
-// exported fields, rep [R] per-replica state, gbits: spin bits for n > 8192
-// ((Rp / 128) * 4 CTAs x 32 replicas x n / 32 words; may be null below).
+// exported fields, rep [R] per-replica state.
 cudaError_t dense_tc_run(int n, int n_eval, int R, int Rp, int b, uint64_t seed, const float *J, const float *h,
                          const __nv_bfloat16 *Jhi, const __nv_bfloat16 *Jlo, __nv_bfloat16 *S, float *Fx,
-                         DenseRep *rep, int sweeps_a, unsigned long long *stats, int32_t *error, uint32_t *gbits,
+                         DenseRep *rep, int sweeps_a, unsigned long long *stats, int32_t *error,
                          const ising_search_params *p, cudaStream_t s) {
-  CUtensorMap mS, mH, mL;
+  if (n % 256 != 0 || n > kMaxN || n_eval > n || Rp % kTM != 0) return cudaErrorInvalidValue;
+  CUtensorMap mH, mL;
   cudaError_t e;
-  if ((e = tc_encode_2d(&mS, S, (uint64_t)n, (uint64_t)Rp, kKC, kTM)) != cudaSuccess) return e;
   if ((e = tc_encode_2d(&mH, Jhi, (uint64_t)n, (uint64_t)n, kKC, kTB)) != cudaSuccess) return e;
   if ((e = tc_encode_2d(&mL, Jlo, (uint64_t)n, (uint64_t)n, kKC, kTB)) != cudaSuccess) return e;
   TcArgs A;
-  if (n % 256 != 0 || n > kMaxN || n_eval > n) return cudaErrorInvalidValue;
   A.n = n;
   A.n_eval = n_eval;
   A.R = R;
@@ -538,27 +605,10 @@ cudaError_t dense_tc_run(int n, int n_eval, int R, int Rp, int b, uint64_t seed,
     A.stall_test = (f && std::strcmp(f, "device_timeout") == 0) ? 1 : 0;
   }
   const int grid = (Rp / kTM) * kClus;
-  A.gbits = gbits;
-  if (n <= 4096) {
-    constexpr int sm = smem_bytes(3, 4096);
-    if ((e = cudaFuncSetAttribute(dense_tc_kernel<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) !=
-        cudaSuccess)
-      return e;
-    dense_tc_kernel<3, false><<<grid, kThreads, sm, s>>>(mS, mH, mL, A);
-  } else if (n <= kMaxNSmemBits) {
-    constexpr int sm = smem_bytes(2, kMaxNSmemBits);
-    if ((e = cudaFuncSetAttribute(dense_tc_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) !=
-        cudaSuccess)
-      return e;
-    dense_tc_kernel<2, false><<<grid, kThreads, sm, s>>>(mS, mH, mL, A);
-  } else {
-    if (!gbits) return cudaErrorInvalidValue;
-    constexpr int sm = smem_bytes(2, 0);
-    if ((e = cudaFuncSetAttribute(dense_tc_kernel<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) !=
-        cudaSuccess)
-      return e;
-    dense_tc_kernel<2, true><<<grid, kThreads, sm, s>>>(mS, mH, mL, A);
-  }
+  if ((e = cudaFuncSetAttribute(dense_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(kMaxN))) !=
+      cudaSuccess)
+    return e;
+  dense_tc_kernel<<<grid, kThreads, smem_bytes(n), s>>>(mH, mL, A);
   return cudaGetLastError();
 }
 
