@@ -62,7 +62,7 @@ struct PushArgs {
 // NS = slots per thread (groups); GUARD: n is not 4 TH NS, so the last group is
 // partial and spins j >= n are masked out.
 template <int NS, bool GUARD, int TH>
-__global__ void __launch_bounds__(TH, TH == 128 ? 6 : (TH == 256 ? 3 : 1)) dense_push_kernel(PushArgs A) {
+__global__ void __launch_bounds__(TH, TH == 128 ? (GUARD ? 6 : 7) : (TH == 256 ? 3 : 1)) dense_push_kernel(PushArgs A) {
   constexpr int kThreads = TH;
   __shared__ int s_r;
   __shared__ int s_min[2][kThreads / 32];
@@ -88,8 +88,9 @@ __global__ void __launch_bounds__(TH, TH == 128 ? 6 : (TH == 256 ? 3 : 1)) dense
     const int r = s_r;
     __syncthreads();  // s_r is rewritten only after every thread has read it
     if (r >= A.R) break;
-    DenseRep st = A.rep[r];
-    if (!st.active) continue;
+    if (!A.rep[r].active) continue;
+    // the only state the sweeps change (the rest of DenseRep stays in memory)
+    int st_d = A.rep[r].d, st_total = A.rep[r].total, st_conv = 0;
     float4 f[NS];
     uint32_t sb = 0;  // bit 4 k + e: spin 4 (t + kThreads k) + e is +1
     const float4 *F4 = reinterpret_cast<const float4 *>(A.F + (size_t)r * n);
@@ -162,13 +163,12 @@ __global__ void __launch_bounds__(TH, TH == 128 ? 6 : (TH == 256 ? 3 : 1)) dense
           from = i + 1;
         }
       }
-      st.d += 1;
-      st.total += 1;
+      st_d += 1;
+      st_total += 1;
       c_sweeps += 1;
       c_flips += (unsigned long long)nfl;
-      if (nfl == 0 || st.d >= A.max_sweeps || (A.budget > 0 && st.total >= A.budget)) {
-        st.conv = nfl == 0 ? 1 : 0;
-        st.active = 0;
+      if (nfl == 0 || st_d >= A.max_sweeps || (A.budget > 0 && st_total >= A.budget)) {
+        st_conv = nfl == 0 ? 1 : 0;
         break;
       }
     }
@@ -198,8 +198,12 @@ __global__ void __launch_bounds__(TH, TH == 128 ? 6 : (TH == 256 ? 3 : 1)) dense
     if (t == 0) {
       double e = 0.0;
       for (int w = 0; w < kThreads / 32; ++w) e += s_e[w];
-      st.E = -0.5 * e;
-      A.rep[r] = st;
+      DenseRep &g = A.rep[r];
+      g.active = 0;
+      g.conv = st_conv;
+      g.d = st_d;
+      g.total = st_total;
+      g.E = -0.5 * e;
     }
   }
   if (t == 0 && c_sweeps) {
