@@ -128,7 +128,9 @@ __device__ __forceinline__ bool gen_wait(uint64_t *bar, uint32_t parity, const v
 __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
     dense_tc_kernel(const __grid_constant__ CUtensorMap mapJhi, const __grid_constant__ CUtensorMap mapJlo, TcArgs A) {
   extern __shared__ uint8_t smem_raw[];
-  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // 1024-byte alignment as an offset into the shared array, so that the
+  // compiler keeps the shared address space of every pointer below
+  uint8_t *smem = smem_raw + ((1024u - (tc::smem_addr(smem_raw) & 1023u)) & 1023u);
   uint8_t *stage = smem;                                              // kStages x (Bhi, Blo)
   float *P = reinterpret_cast<float *>(smem);                         // in the stages: partial fields [spin][replica]
   float *Jblk = reinterpret_cast<float *>(smem + kPartialBytes);      // in the stages: [128][128]
@@ -249,7 +251,7 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
     if (sw == 0 && !any_busy) break;  // no replica of the cluster takes part in this round
     // the export pass: fields and energies of the current states, no decisions
     const bool export_pass = !any_busy || sw == A.sweeps_a;
-    double e_acc = 0.0;  // warp 0: energy sums of the CTA's replicas over the blocks
+    double e_lane = 0.0;  // export pass: this lane's part of its warp's replica energy sum
     // ---- one sweep (or the export pass) over the blocks
     for (int blk = 0; blk < nblk; ++blk) {
       const int b0 = blk * kTB;
@@ -420,15 +422,27 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
           f[qq] = valid_r ? Floc[warp * kFl + 32 * qq + lane] : 0.0f;
         }
         if (export_pass) {
-          // E = -1/2 sum_i s_i (f_i + h_i), f including h
-          double acc = 0.0;
+          // E = -1/2 sum_i s_i (f_i + h_i), f including h: FP64 sums per lane over
+          // the blocks (one warp reduction after the last block); FP64 issues
+          // slowly, so a warp whose four h values are all zero adds s_i f_i
+          // (exact in FP32) with one conversion and one FP64 add each
+          float hq[4];
+          bool hz = true;
 #pragma unroll
           for (int qq = 0; qq < 4; ++qq) {
-            const double v = (double)f[qq] + (double)__ldg(A.h + b0 + 32 * qq + lane);
-            acc += ((wq[qq] >> lane) & 1u) ? v : -v;
+            hq[qq] = __ldg(A.h + b0 + 32 * qq + lane);
+            hz = hz && hq[qq] == 0.0f;
           }
-          acc = warp_sum(acc);
-          if (lane == 0) s_en[warp] = valid_r ? acc : 0.0;
+          if (__all_sync(0xffffffffu, hz)) {
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) e_lane += (double)(((wq[qq] >> lane) & 1u) ? f[qq] : -f[qq]);
+          } else {
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+              const double v = (double)f[qq] + (double)hq[qq];
+              e_lane += ((wq[qq] >> lane) & 1u) ? v : -v;
+            }
+          }
           if (valid_r && s_act[warp]) {
             float *dst = A.Fx + (size_t)rr * n + b0;
 #pragma unroll
@@ -436,32 +450,38 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
           }
         } else {
           const bool act = valid_r && s_act[warp] != 0;
-          int nfl = 0;
-          uint32_t fl[4] = {0u, 0u, 0u, 0u};
+          const uint32_t w_old[4] = {wq[0], wq[1], wq[2], wq[3]};
           if (act) {
 #pragma unroll
             for (int qq = 0; qq < 4; ++qq) {
               uint32_t from = 0xffffffffu;  // lanes not yet decided in this quarter
               for (;;) {
-                const bool up = (wq[qq] >> lane) & 1u;
-                const bool dec = up ? (f[qq] < 0.0f) : (f[qq] > 0.0f);
-                const uint32_t m = __ballot_sync(0xffffffffu, dec) & from;
+                // spin 32 qq + lane flips iff its field is nonzero with the sign
+                // of the spin (+1 and f < 0, or -1 and f > 0): the field's sign
+                // bit xor the spin bit is clear and the rest nonzero
+                const int32_t t = (int32_t)(__float_as_uint(f[qq]) ^ (((wq[qq] >> lane) & 1u) << 31));
+                const uint32_t m = __ballot_sync(0xffffffffu, t > 0) & from;
                 if (!m) break;
-                const int li = __ffs(m) - 1, i = 32 * qq + li;
-                const bool s_up = (wq[qq] >> li) & 1u;
+                const int li = __ffs(m) - 1;
+                const float c = ((wq[qq] >> li) & 1u) ? -2.0f : 2.0f;  // 2 s_i with the new spin
                 wq[qq] ^= 1u << li;
-                fl[qq] |= 1u << li;
-                ++nfl;
-                const float sgn = s_up ? -2.0f : 2.0f;  // 2 s_i with the new spin
-                const float *Jrow = Jblk + i * kTB;     // J symmetric: row i = column i
+                from = 0xfffffffeu << li;
+                // J symmetric: row i = column i.  c J is exact, so one FMA rounds
+                // like adding c J; later spins of this quarter, then the later quarters
+                const float *Jrow = Jblk + (32 * qq + li) * kTB + lane;
+                const float jq = Jrow[32 * qq];
+                if (lane > li) f[qq] = __fmaf_rn(c, jq, f[qq]);
 #pragma unroll
-                for (int q2 = qq; q2 < 4; ++q2) {
-                  const int jj = 32 * q2 + lane;
-                  if (jj > i) f[q2] = __fadd_rn(f[q2], sgn * Jrow[jj]);
-                }
-                from = li == 31 ? 0u : (0xffffffffu << (li + 1));
+                for (int q2 = qq + 1; q2 < 4; ++q2) f[q2] = __fmaf_rn(c, Jrow[32 * q2], f[q2]);
               }
             }
+          }
+          uint32_t fl[4];
+          int nfl = 0;
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) {
+            fl[qq] = wq[qq] ^ w_old[qq];
+            nfl += __popc(fl[qq]);
           }
           if (nfl) {
             if (lane < 4)
@@ -475,13 +495,9 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
         }
       }
       __syncthreads();
-      if (warp == 0 && my_r < A.R && !failed) {
-        if (export_pass) {
-          e_acc += s_en[lane];
-        } else {
-          st.flips += s_nfl[lane];
-          c_flips += (unsigned long long)s_nfl[lane];
-        }
+      if (warp == 0 && my_r < A.R && !failed && !export_pass) {
+        st.flips += s_nfl[lane];
+        c_flips += (unsigned long long)s_nfl[lane];
       }
       // generic-proxy writes to the stages (partials, fields, couplings) are
       // ordered before the next block's TMA writes
@@ -492,7 +508,10 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
     // (a CTA that failed keeps the cluster's barrier sequence; the control step
     // of the next sweep ends the cluster together)
     if (export_pass) {
-      if (real && st.round) st.E = -0.5 * e_acc;
+      const double e = warp_sum(e_lane);
+      if (lane == 0) s_en[warp] = e;
+      __syncthreads();
+      if (real && st.round) st.E = -0.5 * s_en[lane];
       break;
     }
     // ---- end of sweep: per-replica bookkeeping (warp 0)
