@@ -14,9 +14,10 @@
 // Work split: a cluster of 4 CTAs owns 128 replicas for the first sweeps of a
 // round (one descent of every replica): the replicas start from their Philox
 // states together and sweep in lockstep.  CTA q multiplies the K-slice
-// j in [q n/4, (q+1) n/4) into its own tensor-memory accumulator; the four
-// partial blocks are exchanged through distributed shared memory and summed in
-// a fixed order; CTA q then decides replicas 32q..32q+31.  The spin operand
+// j in [q n/4, (q+1) n/4) into its own tensor-memory accumulator; every CTA
+// stores the rows of its partial block that belong to CTA q straight into CTA
+// q's receive buffer (distributed shared memory), and CTA q sums the four in a
+// fixed order and decides replicas 32q..32q+31.  The spin operand
 // comes from tensor memory: CTA q keeps the spin bits of all 128 replicas over
 // its K-slice in shared memory, and four warps expand each 64-spin chunk to
 // BF16 +/-1 and store it to tensor memory (tcgen05.st), so that only the
@@ -54,9 +55,9 @@ constexpr int kClus = 4;        // CTAs per cluster (split K)
 constexpr int kThreads = 1024;  // one warp per decided replica (32 per CTA)
 constexpr int kFl = kTB + 1;    // padded row of the block fields [replica][spin]
 constexpr int kTileBytes = kTB * kKC * 2;                 // 16 KB, one coupling tile
-constexpr int kStages = 4;                                // operand pipeline depth
+constexpr int kStages = 3;                                // operand pipeline depth
 constexpr int kStageBytes = 2 * kTileBytes;               // B_hi, B_lo
-constexpr int kPartialBytes = kTB * kTM * 4;              // 64 KB, [spin][replica]
+constexpr int kRxBytes = kClus * kTB * 32 * 4;            // 64 KB, received partials [source][spin][replica]
 constexpr int kJblkBytes = kTB * kTB * 4;                 // 64 KB, the block's couplings in FP32
 constexpr int kFlocBytes = 32 * kFl * 4;                  // this CTA's replicas' block fields
 constexpr int kAcc = kTB;                                 // tensor-memory columns of the accumulator
@@ -65,14 +66,18 @@ constexpr int kTmemCols = 256;                            // accumulator + kStag
 constexpr int kGen0 = 4;                                  // warps kGen0..kGen0+3 write the spin chunks
 constexpr int kMaxN = 16384;
 // Shared memory: the stages (once a block's MMAs have completed they hold its
-// partial fields and FP32 couplings until the next block's loads), the decided
-// replicas' fields, the spin bits [n / 128 words][128 replicas] of the CTA's
-// K-slice, alignment slack.
-constexpr int smem_bytes(int n) { return kStages * kStageBytes + kFlocBytes + 4 * n + 1024; }
-static_assert(kPartialBytes + kJblkBytes <= kStages * kStageBytes, "partials and couplings must fit the stages");
+// FP32 couplings until the next block's loads), the receive buffer (the
+// decided replicas' summed fields replace the partials once read), the spin
+// bits [n / 128 words][128 replicas] of the CTA's K-slice, alignment slack.
+// The receive buffer lies outside the stages: other CTAs write into it while
+// this CTA's MMAs may still read its stages.
+constexpr int smem_bytes(int n) { return kStages * kStageBytes + kRxBytes + 4 * n + 1024; }
+static_assert(kJblkBytes <= kStages * kStageBytes, "couplings must fit the stages");
+static_assert(kFlocBytes <= kRxBytes, "fields must fit the receive buffer");
 static_assert(smem_bytes(kMaxN) + 2048 <= 227 * 1024, "shared memory per CTA (2 KB for the static part)");
 static_assert(kAcc + kStages * kACols <= kTmemCols, "tensor-memory columns");
 static_assert(kGen0 >= 1 && kGen0 + 4 <= kThreads / 32, "spin-chunk warps: not warp 0 (thread 0 issues)");
+static_assert(kThreads == kTB * 8 && kThreads > 512, "phase-3 and staging thread maps");
 
 struct TcArgs {
   int32_t n, R, Rp, b;             // spins (padded to a multiple of 256), replicas, padded replicas, instance
@@ -132,13 +137,13 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
   // compiler keeps the shared address space of every pointer below
   uint8_t *smem = smem_raw + ((1024u - (tc::smem_addr(smem_raw) & 1023u)) & 1023u);
   uint8_t *stage = smem;                                              // kStages x (Bhi, Blo)
-  float *P = reinterpret_cast<float *>(smem);                         // in the stages: partial fields [spin][replica]
-  float *Jblk = reinterpret_cast<float *>(smem + kPartialBytes);      // in the stages: [128][128]
-  float *Floc = reinterpret_cast<float *>(smem + kStages * kStageBytes);  // [32 replicas][kFl]
+  float *Jblk = reinterpret_cast<float *>(smem);                      // in the stages: [128][128]
+  float *Rx = reinterpret_cast<float *>(smem + kStages * kStageBytes);  // [source CTA][spin][replica]
+  float *Floc = Rx;                                                   // after the sum: [32 replicas][kFl]
   // spin bits of the cluster's 128 replicas over this CTA's K-slice: word w
   // (spins kbase + 32 w .. + 31, bit t = spin kbase + 32 w + t, 1 = +1) of
   // replica r0 + row at kbits[w * 128 + row]
-  uint32_t *kbits = reinterpret_cast<uint32_t *>(smem + kStages * kStageBytes + kFlocBytes);
+  uint32_t *kbits = reinterpret_cast<uint32_t *>(smem + kStages * kStageBytes + kRxBytes);
 
   __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], afull_bar[kStages], done_bar, drain_bar,
       stall_bar;
@@ -348,7 +353,9 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
         }
       }
       failed = __syncthreads_or(failed) != 0;
-      // Phase 2: accumulator -> shared memory, transposed to [spin][replica]
+      // Phase 2: accumulator -> the deciding CTAs' receive buffers; meanwhile
+      // the other warps stage the block's couplings in FP32 (the stages are free
+      // once the MMAs have completed)
       {
         const bool ok = failed ? true : tc::mbar_wait(&done_bar, ph_done);
         failed = __syncthreads_or(failed || !ok) != 0;
@@ -357,45 +364,52 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
       }
       ph_done ^= 1u;
       if (!failed && warp < 16) {
-        // warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its lane quarter)
-        // and accumulator columns 32 (w / 4) .. + 31
+        // warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its lane quarter:
+        // replicas of CTA w % 4) and accumulator columns 32 (w / 4) .. + 31, and
+        // stores them to slot q of that CTA's receive buffer
         const int lq = warp & 3, cc = warp >> 2;
         uint32_t v[32];
         tc::tmem_ld32(tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(cc * 32), v);
+        const uint32_t dst = tc::map_shared(Rx + ((int)q * kTB + cc * 32) * 32 + lane, (uint32_t)lq);
 #pragma unroll
-        for (int k = 0; k < 32; ++k) P[(cc * 32 + k) * kTM + 32 * lq + lane] = __uint_as_float(v[k]);
+        for (int k = 0; k < 32; ++k) tc::st_cluster_u32(dst + 128u * k, v[k]);
+      } else if (!failed && !export_pass) {
+        for (int e = tid - 512; e < kTB * kTB / 4; e += kThreads - 512) {
+          const int i = e / (kTB / 4), c4 = e % (kTB / 4);
+          reinterpret_cast<float4 *>(Jblk)[e] =
+              *reinterpret_cast<const float4 *>(A.J + (size_t)(b0 + i) * n + b0 + 4 * c4);
+        }
       }
       tc::tc_fence_before();
       __syncthreads();
-      tc::cluster_sync();
+      tc::cluster_sync();  // every CTA's partials have arrived
       // Phase 3: sum the four partials (fixed order) and add h for this CTA's 32
-      // replicas, stage the block's couplings in FP32
-      if (!failed) {
-        for (int e = tid; e < kTB * 8; e += kThreads) {
-          const int i = e >> 3, c4 = e & 7;
-          float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-          for (uint32_t c = 0; c < kClus; ++c) {
-            const float4 p = tc::ld_cluster_f4(tc::map_shared(P + i * kTM + 32 * q + 4 * c4, c));
+      // replicas; the sums replace the partials in the receive buffer
+      {
+        const int i = tid >> 3, c4 = tid & 7;  // kThreads = kTB x 8
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!failed) {
+          for (int c = 0; c < kClus; ++c) {
+            const float4 p = *reinterpret_cast<const float4 *>(Rx + (c * kTB + i) * 32 + 4 * c4);
             acc.x += p.x;
             acc.y += p.y;
             acc.z += p.z;
             acc.w += p.w;
           }
           const float hv = __ldg(A.h + b0 + i);
-          Floc[(4 * c4 + 0) * kFl + i] = acc.x + hv;
-          Floc[(4 * c4 + 1) * kFl + i] = acc.y + hv;
-          Floc[(4 * c4 + 2) * kFl + i] = acc.z + hv;
-          Floc[(4 * c4 + 3) * kFl + i] = acc.w + hv;
+          acc.x += hv;
+          acc.y += hv;
+          acc.z += hv;
+          acc.w += hv;
         }
-        if (!export_pass)
-          for (int e = tid; e < kTB * kTB / 4; e += kThreads) {
-            const int i = e / (kTB / 4), c4 = e % (kTB / 4);
-            reinterpret_cast<float4 *>(Jblk)[e] =
-                *reinterpret_cast<const float4 *>(A.J + (size_t)(b0 + i) * n + b0 + 4 * c4);
-          }
+        __syncthreads();
+        if (!failed) {
+          Floc[(4 * c4 + 0) * kFl + i] = acc.x;
+          Floc[(4 * c4 + 1) * kFl + i] = acc.y;
+          Floc[(4 * c4 + 2) * kFl + i] = acc.z;
+          Floc[(4 * c4 + 3) * kFl + i] = acc.w;
+        }
       }
-      __syncthreads();
-      tc::cluster_sync();  // partials consumed: P may be overwritten by the next block
       // Phase 4: sequential decisions (or the export).  Warp w decides replica
       // rq + w; lane l keeps the fields of spins 32q + l (q = 0..3) in
       // registers.  Spins are decided in index order; between two flips no field
@@ -499,8 +513,8 @@ __global__ void __cluster_dims__(kClus, 1, 1) __launch_bounds__(kThreads, 1)
         st.flips += s_nfl[lane];
         c_flips += (unsigned long long)s_nfl[lane];
       }
-      // generic-proxy writes to the stages (partials, fields, couplings) are
-      // ordered before the next block's TMA writes
+      // generic-proxy writes to the stages (the couplings) are ordered before
+      // the next block's TMA writes
       tc::fence_proxy_async_shared();
       __syncthreads();
       tc::cluster_sync();  // new spin bits visible to every CTA's next block
