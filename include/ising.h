@@ -354,6 +354,17 @@ int32_t ising_kernel_times(ising_handle *h, ising_kernel_time *out, int32_t cap)
  * ISING_ERR_INVALID_ARG for NULL, ISING_ERR_CUDA on a CUDA error.           */
 ising_status ising_logic_peak(double *lane_ops_per_s);
 
+/* Measurement helper, not an operation of the method: replica-bit logic
+ * operations per second on word_bits-wide words (32 or 64), from chains of
+ * two-input XORs of that width (PTX xor.b32 / xor.b64) on registers at full
+ * occupancy, counted as XORs x word_bits (one replica per bit, as in
+ * multi-spin coding; best of three
+ * launches of about 10 ms).  Compares the two word widths multi-spin coding
+ * could use.  *bit_ops_per_s (host) receives the rate, 0 on failure.  Blocks
+ * until done; ISING_ERR_INVALID_ARG for NULL or another width, ISING_ERR_CUDA
+ * on a CUDA error.                                                           */
+ising_status ising_logic_bits_rate(int32_t word_bits, double *bit_ops_per_s);
+
 /* Free everything the handle owns.  ising_destroy(NULL) returns ISING_OK.      */
 ising_status ising_destroy(ising_handle *h);
 

@@ -101,6 +101,8 @@ def lib():
             L.ising_kernel_times.restype = i32
             L.ising_logic_peak.argtypes = [vp]
             L.ising_logic_peak.restype = i32
+            L.ising_logic_bits_rate.argtypes = [i32, vp]
+            L.ising_logic_bits_rate.restype = i32
             L.ising_status_string.argtypes = [i32]
             L.ising_status_string.restype = C.c_char_p
             _lib = L
@@ -109,7 +111,8 @@ def lib():
 
 EXPORTED = ("ising_create", "ising_energy", "ising_local_search", "ising_plan_kernel",
             "ising_autotune", "ising_destroy", "ising_status_string", "ising_energy_noalloc",
-            "ising_set_timing", "ising_kernel_times", "ising_fm_search", "ising_logic_peak")
+            "ising_set_timing", "ising_kernel_times", "ising_fm_search", "ising_logic_peak",
+            "ising_logic_bits_rate")
 
 
 def _check(code: int, where: str):
@@ -317,6 +320,14 @@ def logic_peak() -> float:
     lane-ops/s (ising_logic_peak): the roofline of the multi-spin-coded kernels."""
     v = C.c_double(0.0)
     _check(lib().ising_logic_peak(C.byref(v)), "ising_logic_peak")
+    return float(v.value)
+
+
+def logic_bits_rate(word_bits: int) -> float:
+    """Replica-bit logic operations per second on 32- or 64-bit words on the
+    current CUDA device (ising_logic_bits_rate)."""
+    v = C.c_double(0.0)
+    _check(lib().ising_logic_bits_rate(int(word_bits), C.byref(v)), "ising_logic_bits_rate")
     return float(v.value)
 
 

@@ -602,3 +602,21 @@ def test_logic_peak_measurement():
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     assert 0 < p1 <= sms * 128 * 2.1e9
     assert abs(p1 - p2) <= 0.05 * max(p1, p2)
+
+
+def test_multi_spin_word_width():
+    """ising_logic_bits_rate: replica-bit logic operations per second on 32- and
+    64-bit words.  A 64-bit logic op issues as two 32-bit ones, so the wider word
+    does not raise the rate at which replica bits are processed (the reason the
+    multi-spin-coded kernels use 32-bit words).  A two-input XOR issues at least
+    as fast as the three-input lop3 and at most twice as fast (measured 1.86x:
+    the denominator of the logic rooflines is the three-input rate)."""
+    r32 = isg.logic_bits_rate(32)
+    r64 = isg.logic_bits_rate(64)
+    lop = isg.logic_peak()
+    print(f"replica-bit ops/s: 32-bit words {r32:.4g}, 64-bit words {r64:.4g}; lop3 lane-ops/s {lop:.4g}")
+    assert r32 > 0 and r64 > 0
+    assert r64 <= 1.1 * r32, (r32, r64)
+    assert 0.8 * lop * 32 <= r32 <= 2.2 * lop * 32, (r32, lop)
+    with pytest.raises(RuntimeError):
+        isg.logic_bits_rate(16)
