@@ -501,7 +501,29 @@ __global__ void __launch_bounds__(kTileThreads, MODE == 3 ? 2 : 4) tile_kernel(c
                   // none for this lane, field and decision are unchanged.
                   f = Fc[(size_t)j * 32 + lane];
                   bool dirty = false;
-                  for (uint32_t kk = k0; kk < k1; ++kk) {
+                  // the first kPre entries of the row fetched together (one round
+                  // trip instead of one per entry), then applied in CSR order
+                  constexpr int kPre = 6;
+                  const int dg = (int)(k1 - k0);
+                  int ci[kPre];
+                  float cw[kPre];
+#pragma unroll
+                  for (int q = 0; q < kPre; ++q)
+                    if (q < dg) {
+                      ci[q] = __ldg(G.col + k0 + q);
+                      cw[q] = __ldg(Jf + k0 + q);
+                    }
+#pragma unroll
+                  for (int q = 0; q < kPre; ++q)
+                    if (q < dg) {
+                      const int i = ci[q];
+                      if ((fm[i] >> lane) & 1u) {
+                        const float w2 = 2.0f * cw[q];
+                        f = __fadd_rn(f, ((sw[i] >> lane) & 1u) ? w2 : -w2);
+                        dirty = true;
+                      }
+                    }
+                  for (uint32_t kk = k0 + kPre; kk < k1; ++kk) {
                     const int i = __ldg(G.col + kk);
                     if ((fm[i] >> lane) & 1u) {
                       const float w2 = 2.0f * __ldg(Jf + kk);
