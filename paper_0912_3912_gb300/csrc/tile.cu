@@ -418,12 +418,21 @@ __global__ void __launch_bounds__(kTileThreads, MODE == 3 ? 2 : 4) tile_kernel(c
               my_flips += __popc(flip);
             }
           } else {
-            for (int v = c0 + warp; v < c1; v += nwarps) {
-              const int j = A.sequential ? v : __ldg(G.order + I.spin_off + v);
-              if (!pending(j)) {  // warp-uniform; the visit flips nothing
-                if (MODE == 1 && lane == 0 && fm[j]) fm[j] = 0u;
-                continue;
-              }
+            // The warp's positions v = c0 + warp + k nwarps, 32 at a time: lane k
+            // reads position k's spin and pending bit (one round trip for the 32),
+            // a position with nothing pending is settled at once (its visit flips
+            // nothing), and the others are visited in order.
+            for (int vb = c0 + warp; vb < c1; vb += 32 * nwarps) {
+              const int vl = vb + lane * nwarps;
+              const bool inr = vl < c1;
+              const int jl = inr ? (A.sequential ? vl : __ldg(G.order + I.spin_off + vl)) : 0;
+              const bool pl = inr && pending(jl);
+              if (MODE == 1 && inr && !pl && fm[jl]) fm[jl] = 0u;
+              uint32_t todo = __ballot_sync(0xffffffffu, pl);
+              while (todo) {
+              const int src = __ffs(todo) - 1;
+              todo &= todo - 1u;
+              const int j = __shfl_sync(0xffffffffu, jl, src);
               const int64_t gj = I.spin_off + j;
               const uint32_t wj = sw[j];
               const bool up = (wj >> lane) & 1u;
@@ -576,6 +585,7 @@ __global__ void __launch_bounds__(kTileThreads, MODE == 3 ? 2 : 4) tile_kernel(c
               }
               anyf |= m;
               my_flips += flip ? 1 : 0;
+              }
             }
           }
           __syncthreads();
