@@ -428,6 +428,15 @@ __global__ void __launch_bounds__(kTileThreads, MODE == 3 ? 2 : 4) tile_kernel(c
               const int jl = inr ? (A.sequential ? vl : __ldg(G.order + I.spin_off + vl)) : 0;
               const bool pl = inr && pending(jl);
               if (MODE == 1 && inr && !pl && fm[jl]) fm[jl] = 0u;
+              // a pending position's row and hyper-edge bounds, read with the batch
+              uint32_t k0l = 0, k1l = 0, e0l = 0, e1l = 0;
+              if (pl) {
+                const int64_t g = I.spin_off + jl;
+                k0l = __ldg(G.row + g);
+                k1l = __ldg(G.row + g + 1);
+                e0l = __ldg(G.inc_ptr + g);
+                e1l = __ldg(G.inc_ptr + g + 1);
+              }
               uint32_t todo = __ballot_sync(0xffffffffu, pl);
               while (todo) {
               const int src = __ffs(todo) - 1;
@@ -436,8 +445,8 @@ __global__ void __launch_bounds__(kTileThreads, MODE == 3 ? 2 : 4) tile_kernel(c
               const int64_t gj = I.spin_off + j;
               const uint32_t wj = sw[j];
               const bool up = (wj >> lane) & 1u;
-              const uint32_t k0 = __ldg(G.row + gj), k1 = __ldg(G.row + gj + 1);
-              const uint32_t e0 = __ldg(G.inc_ptr + gj), e1 = __ldg(G.inc_ptr + gj + 1);
+              const uint32_t k0 = __shfl_sync(0xffffffffu, k0l, src), k1 = __shfl_sync(0xffffffffu, k1l, src);
+              const uint32_t e0 = __shfl_sync(0xffffffffu, e0l, src), e1 = __shfl_sync(0xffffffffu, e1l, src);
               bool flip;
               if (MODE == 0) {
                 const int8_t *Ji = reinterpret_cast<const int8_t *>(G.J);
