@@ -53,46 +53,61 @@ __device__ void tile_energy_lanes(const DevGraph &G, const InstDesc &I, const ui
   double accd = 0.0;
   long long acci = 0;
   unsigned long long accl = 0;
-  for (int i = warp; i < n; i += nw) {
-    const int64_t gi = I.spin_off + i;
-    const uint32_t bi = (sw[i] >> lane) & 1u;
-    const uint32_t k0 = __ldg(G.row + gi), k1 = __ldg(G.row + gi + 1);
-    if (FLOAT) {
-      const float *Jf = reinterpret_cast<const float *>(G.J);
-      const float hv = __ldg(reinterpret_cast<const float *>(G.h) + gi);
-      if (fx) {
-        const int64_t th = xr_term(hv, ub);
-        xe_add(acci, accl, bi ? -th : th);
-        for (uint32_t k = k0; k < k1; ++k) {
-          const int j = __ldg(G.col + k);
-          if (j > i) {
-            const int64_t t = xr_term(__ldg(Jf + k), ub);
-            xe_add(acci, accl, (((sw[j] >> lane) & 1u) ^ bi) ? t : -t);
+  // the warp's spins i = warp + k nw, 32 at a time: lane k reads spin k's row
+  // bounds and field in one pass, then the spins are taken in order
+  for (int ib = warp; ib < n; ib += 32 * nw) {
+    const int il = ib + lane * nw;
+    uint32_t k0l = 0, k1l = 0, hvl = 0;
+    if (il < n) {
+      const int64_t g = I.spin_off + il;
+      k0l = __ldg(G.row + g);
+      k1l = __ldg(G.row + g + 1);
+      hvl = FLOAT ? __float_as_uint(__ldg(reinterpret_cast<const float *>(G.h) + g))
+                  : (uint32_t)(int32_t)__ldg(reinterpret_cast<const int8_t *>(G.h) + g);
+    }
+    const int cnt = min(32, (n - ib + nw - 1) / nw);
+    for (int src = 0; src < cnt; ++src) {
+      const int i = ib + src * nw;
+      const uint32_t bi = (sw[i] >> lane) & 1u;
+      const uint32_t k0 = __shfl_sync(0xffffffffu, k0l, src), k1 = __shfl_sync(0xffffffffu, k1l, src);
+      const uint32_t hraw = __shfl_sync(0xffffffffu, hvl, src);
+      if (FLOAT) {
+        const float *Jf = reinterpret_cast<const float *>(G.J);
+        const float hv = __uint_as_float(hraw);
+        if (fx) {
+          const int64_t th = xr_term(hv, ub);
+          xe_add(acci, accl, bi ? -th : th);
+          for (uint32_t k = k0; k < k1; ++k) {
+            const int j = __ldg(G.col + k);
+            if (j > i) {
+              const int64_t t = xr_term(__ldg(Jf + k), ub);
+              xe_add(acci, accl, (((sw[j] >> lane) & 1u) ^ bi) ? t : -t);
+            }
           }
+        } else {
+          double e = bi ? (double)hv : -(double)hv;
+          for (uint32_t k = k0; k < k1; ++k) {
+            const int j = __ldg(G.col + k);
+            if (j > i) {
+              const double w = (double)__ldg(Jf + k);
+              e += (((sw[j] >> lane) & 1u) ^ bi) ? -w : w;
+            }
+          }
+          accd -= e;
         }
       } else {
-        double e = bi ? (double)hv : -(double)hv;
+        const int8_t *Ji = reinterpret_cast<const int8_t *>(G.J);
+        const int hv = (int)hraw;
+        int e = bi ? hv : -hv;
         for (uint32_t k = k0; k < k1; ++k) {
           const int j = __ldg(G.col + k);
           if (j > i) {
-            const double w = (double)__ldg(Jf + k);
+            const int w = __ldg(Ji + k);
             e += (((sw[j] >> lane) & 1u) ^ bi) ? -w : w;
           }
         }
-        accd -= e;
+        acci -= e;
       }
-    } else {
-      const int8_t *Ji = reinterpret_cast<const int8_t *>(G.J);
-      const int hv = __ldg(reinterpret_cast<const int8_t *>(G.h) + gi);
-      int e = bi ? hv : -hv;
-      for (uint32_t k = k0; k < k1; ++k) {
-        const int j = __ldg(G.col + k);
-        if (j > i) {
-          const int w = __ldg(Ji + k);
-          e += (((sw[j] >> lane) & 1u) ^ bi) ? -w : w;
-        }
-      }
-      acci -= e;
     }
   }
   for (int e = warp; e < I.n_hyper; e += nw) {
