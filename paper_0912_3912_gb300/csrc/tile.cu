@@ -596,14 +596,15 @@ __global__ void __launch_bounds__(kTileThreads, MODE == 3 ? 2 : 4) tile_kernel(c
                 clear_pending(j);
                 sw[j] = wj ^ m;
                 if (MODE == 1) fm[j] = m;
-                if (m) {
-                  for (uint32_t kk = k0; kk < k1; ++kk) mark(__ldg(G.col + kk));
-                  for (uint32_t q = e0; q < e1; ++q) {
-                    const int e = __ldg(G.inc_edge + q);
-                    for (uint32_t mm = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); mm < me; ++mm) {
-                      const int o = __ldg(G.hmem + mm);
-                      if (o != j) mark(o);
-                    }
+              }
+              if (m) {
+                // the neighbours' pending marks, one lane per row entry / member
+                for (uint32_t kk = k0 + lane; kk < k1; kk += 32) mark(__ldg(G.col + kk));
+                for (uint32_t q = e0; q < e1; ++q) {
+                  const int e = __ldg(G.inc_edge + q);
+                  for (uint32_t mm = __ldg(G.hptr + e) + lane, me = __ldg(G.hptr + e + 1); mm < me; mm += 32) {
+                    const int o = __ldg(G.hmem + mm);
+                    if (o != j) mark(o);
                   }
                 }
               }
