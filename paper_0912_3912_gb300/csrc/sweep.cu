@@ -1497,11 +1497,17 @@ cudaError_t run_instance(ising_handle *h, SweepArgs A, int mode, cudaStream_t s)
   debug_step("restart0", 0, s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  // The round-end kernels (energy pass, restarts) follow every kRoundEnd-th
+  // sweep of a captured chunk: most of their launches find no round ended, and
+  // a group whose round ended only waits (no active lane: it visits and counts
+  // nothing) until they come.
+  constexpr int kRoundEnd = 4;
   // upper bound on the sweeps any group can need
-  // (each round may wait one sweep for its round-end kernels)
-  int64_t max_sweeps_total = (int64_t)A.restarts * (A.max_sweeps + 2) + A.restarts;
+  // (each round may wait kRoundEnd - 1 sweeps for its round-end kernels)
+  int64_t max_sweeps_total = (int64_t)A.restarts * (A.max_sweeps + kRoundEnd) + A.restarts;
   if (A.budget > 0)
-    max_sweeps_total = std::min<int64_t>(max_sweeps_total, (int64_t)A.R * A.budget * 2 + A.max_sweeps + 2);
+    max_sweeps_total =
+        std::min<int64_t>(max_sweeps_total, (int64_t)A.R * A.budget * kRoundEnd + A.max_sweeps + kRoundEnd);
   // Capture a chunk of sweeps once per configuration (cached) and replay it
   // until every group is done, polling a done flag one chunk behind so the GPU
   // always has queued work.  A graph holds at most kMaxNodes launches; when one
@@ -1532,11 +1538,8 @@ cudaError_t run_instance(ising_handle *h, SweepArgs A, int mode, cudaStream_t s)
       if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return e;
       e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        // The round-end kernels (energy pass, restarts) follow every second
-        // sweep: a group whose round ended has no active lane, so the sweep in
-        // between visits nothing for it and counts nothing; it only waits.
         for (int k = 0; k < chunk; ++k)
-          enqueue_sweep<LPS, LAT>(A, mode, ncls, grid_v, cs, (k & 1) || chunk == 1);
+          enqueue_sweep<LPS, LAT>(A, mode, ncls, grid_v, cs, (k % kRoundEnd) == kRoundEnd - 1 || k == chunk - 1);
         e = cudaStreamEndCapture(cs, &sg.graph);
       }
       if (e == cudaSuccess) e = cudaGraphInstantiate(&sg.exec, sg.graph, 0);
@@ -1552,8 +1555,10 @@ cudaError_t run_instance(ising_handle *h, SweepArgs A, int mode, cudaStream_t s)
   const int64_t max_chunks = max_sweeps_total / chunk + 2;
   int64_t launched = 0;
   for (;;) {
-    // sweeps k = 0, 2, 4, ... of a captured chunk have no round-end kernels
-    h->launches += (uint64_t)chunk * per_sweep - (use_graph && chunk > 1 ? (uint64_t)((chunk + 1) / 2) * 2 : 0);
+    // sweeps of a captured chunk without round-end kernels launch two fewer
+    int with_re = 0;
+    for (int k = 0; k < chunk; ++k) with_re += ((k % kRoundEnd) == kRoundEnd - 1 || k == chunk - 1) ? 1 : 0;
+    h->launches += (uint64_t)chunk * per_sweep - (use_graph ? (uint64_t)(chunk - with_re) * 2 : 0);
     kt_begin(h, "sweep_chunk", s);
     if (use_graph) {
       if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) break;
