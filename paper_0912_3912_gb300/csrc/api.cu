@@ -41,6 +41,7 @@ DevGraph ising_handle::graph() const {
   g.h = d_h;
   g.inc_ptr = d_inc_ptr;
   g.inc_edge = d_inc_edge;
+  g.inc_oth = d_inc_oth;
   g.hptr = d_hptr;
   g.hmem = d_hmem;
   g.hJ = d_hJ;
@@ -356,7 +357,7 @@ void free_handle(ising_handle *h) {
   fm_free(h);
   dense_free(h);
   plain_free(h);
-  void *ptrs[] = {h->d_inst, h->d_row, h->d_col, h->d_J, h->d_h, h->d_inc_ptr, h->d_inc_edge, h->d_hptr,
+  void *ptrs[] = {h->d_inst, h->d_row, h->d_col, h->d_J, h->d_h, h->d_inc_ptr, h->d_inc_edge, h->d_inc_oth, h->d_hptr,
                   h->d_hmem, h->d_hJ, h->d_order, h->d_cls, h->d_Jdense, h->d_meta, h->d_Jpos, h->d_Jfwd, h->d_latinfo, h->d_runit,
                   h->d_scratch, h->d_tile_args,
                   h->d_seeds, h->d_stats, h->d_queue, h->d_tiles};
@@ -718,6 +719,7 @@ ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
   std::vector<double> Jd, hd, hJd;
   std::vector<uint32_t> inc_ptr, hptr;
   std::vector<int32_t> inc_edge, hmem;
+  std::vector<int2> inc_oth;  // per incidence: the other two members of a 3-member edge
   std::vector<std::pair<int32_t, std::vector<int32_t>>> lat_sites;
   int64_t spin_off = 0, nnz_off = 0, edge_off = 0, mem_off = 0, cls_off = 0;
   for (int32_t b = 0; b < n_instances; ++b) {
@@ -760,7 +762,17 @@ ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
       for (int64_t q = I.hptr[e]; q < I.hptr[e + 1]; ++q) inc[I.hmem[q]].push_back(e);
     for (int32_t i = 0; i < I.n; ++i) {
       inc_ptr.push_back((uint32_t)inc_edge.size());
-      for (int32_t e : inc[i]) inc_edge.push_back((int32_t)(edge_off + e));
+      for (int32_t e : inc[i]) {
+        inc_edge.push_back((int32_t)(edge_off + e));
+        int2 o = make_int2(-1, -1);
+        if (I.hptr[e + 1] - I.hptr[e] == 3) {
+          int32_t m[2], k = 0;
+          for (int64_t q = I.hptr[e]; q < I.hptr[e + 1]; ++q)
+            if (I.hmem[q] != i && k < 2) m[k++] = I.hmem[q];
+          if (k == 2) o = make_int2(m[0], m[1]);
+        }
+        inc_oth.push_back(o);
+      }
     }
     for (int32_t e = 0; e < D.n_hyper; ++e) hptr.push_back((uint32_t)(mem_off + I.hptr[e]));
     hmem.insert(hmem.end(), I.hmem.begin(), I.hmem.end());
@@ -830,7 +842,8 @@ ising_status ising_create(const ising_instance_desc *descs, int32_t n_instances,
 
   bool ok = upload(&h->d_inst, inst) == cudaSuccess && upload(&h->d_row, row) == cudaSuccess &&
             upload(&h->d_col, col) == cudaSuccess && upload(&h->d_inc_ptr, inc_ptr) == cudaSuccess &&
-            upload(&h->d_inc_edge, inc_edge) == cudaSuccess && upload(&h->d_hptr, hptr) == cudaSuccess &&
+            upload(&h->d_inc_edge, inc_edge) == cudaSuccess && upload(&h->d_inc_oth, inc_oth) == cudaSuccess &&
+            upload(&h->d_hptr, hptr) == cudaSuccess &&
             upload(&h->d_hmem, hmem) == cudaSuccess && upload(&h->d_order, order) == cudaSuccess &&
             upload(&h->d_cls, cls) == cudaSuccess;
   if (ok) {

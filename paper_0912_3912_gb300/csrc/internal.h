@@ -56,6 +56,8 @@ struct DevGraph {
   const void *h;            // [total_spins] int8_t or float (zeros when absent)
   const uint32_t *inc_ptr;  // [total_spins + 1] offsets into inc_edge
   const int32_t *inc_edge;  // global hyper-edge ids containing the spin, ascending
+  const int2 *inc_oth;      // per incidence: the edge's two other members (local) when it
+                            // has exactly three, else (-1, -1)
   const uint32_t *hptr;     // [total_edges + 1] offsets into hmem
   const int32_t *hmem;      // local member indices
   const void *hJ;           // [total_edges] int8_t or float
@@ -140,6 +142,7 @@ struct ising_handle {
   void *d_h = nullptr;
   uint32_t *d_inc_ptr = nullptr;
   int32_t *d_inc_edge = nullptr;
+  int2 *d_inc_oth = nullptr;
   uint32_t *d_hptr = nullptr;
   int32_t *d_hmem = nullptr;
   void *d_hJ = nullptr;

@@ -566,12 +566,18 @@ __global__ void __launch_bounds__(kTileThreads, MODE == 3 ? 2 : 4) tile_kernel(c
                   }
                   for (uint32_t q = e0; q < e1; ++q) {
                     const int e = __ldg(G.inc_edge + q);
+                    const int2 oth = __ldg(G.inc_oth + q);  // a 3-member edge's other two, with the id
                     uint32_t neg = 0, par = 0;
-                    for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
-                      const int mm = __ldg(G.hmem + m);
-                      if (mm != j) {
-                        neg ^= ~(sw[mm] >> lane) & 1u;
-                        par ^= (fm[mm] >> lane) & 1u;
+                    if (oth.x >= 0) {
+                      neg = (~(sw[oth.x] >> lane) & 1u) ^ (~(sw[oth.y] >> lane) & 1u);
+                      par = ((fm[oth.x] >> lane) & 1u) ^ ((fm[oth.y] >> lane) & 1u);
+                    } else {
+                      for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
+                        const int mm = __ldg(G.hmem + m);
+                        if (mm != j) {
+                          neg ^= ~(sw[mm] >> lane) & 1u;
+                          par ^= (fm[mm] >> lane) & 1u;
+                        }
                       }
                     }
                     if (par) {
@@ -601,6 +607,11 @@ __global__ void __launch_bounds__(kTileThreads, MODE == 3 ? 2 : 4) tile_kernel(c
                 // the neighbours' pending marks, one lane per row entry / member
                 for (uint32_t kk = k0 + lane; kk < k1; kk += 32) mark(__ldg(G.col + kk));
                 for (uint32_t q = e0; q < e1; ++q) {
+                  const int2 oth = __ldg(G.inc_oth + q);
+                  if (oth.x >= 0) {
+                    if (lane < 2) mark(lane == 0 ? oth.x : oth.y);
+                    continue;
+                  }
                   const int e = __ldg(G.inc_edge + q);
                   for (uint32_t mm = __ldg(G.hptr + e) + lane, me = __ldg(G.hptr + e + 1); mm < me; mm += 32) {
                     const int o = __ldg(G.hmem + mm);
