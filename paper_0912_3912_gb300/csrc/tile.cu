@@ -474,10 +474,15 @@ __global__ void __launch_bounds__(kTileThreads, MODE == 3 ? 2 : 4) tile_kernel(c
                 }
                 for (uint32_t q = e0; q < e1; ++q) {
                   const int e = __ldg(G.inc_edge + q);
+                  const int2 oth = __ldg(G.inc_oth + q);
                   uint32_t neg = 0;
-                  for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
-                    const int mm = __ldg(G.hmem + m);
-                    if (mm != j) neg ^= ~(sw[mm] >> lane) & 1u;
+                  if (oth.x >= 0) {
+                    neg = (~(sw[oth.x] >> lane) & 1u) ^ (~(sw[oth.y] >> lane) & 1u);
+                  } else {
+                    for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
+                      const int mm = __ldg(G.hmem + m);
+                      if (mm != j) neg ^= ~(sw[mm] >> lane) & 1u;
+                    }
                   }
                   const int w = __ldg(hJ + e);
                   f += neg ? -w : w;
@@ -500,10 +505,15 @@ __global__ void __launch_bounds__(kTileThreads, MODE == 3 ? 2 : 4) tile_kernel(c
                     }
                     for (uint32_t q = e0; q < e1; ++q) {
                       const int e = __ldg(G.inc_edge + q);
+                      const int2 oth = __ldg(G.inc_oth + q);
                       uint32_t neg = 0;
-                      for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
-                        const int mm = __ldg(G.hmem + m);
-                        if (mm != j) neg ^= ~(sw[mm] >> lane) & 1u;
+                      if (oth.x >= 0) {
+                        neg = (~(sw[oth.x] >> lane) & 1u) ^ (~(sw[oth.y] >> lane) & 1u);
+                      } else {
+                        for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
+                          const int mm = __ldg(G.hmem + m);
+                          if (mm != j) neg ^= ~(sw[mm] >> lane) & 1u;
+                        }
                       }
                       const int64_t t = xr_term(__ldg(hJ + e), u);
                       acc += neg ? -t : t;
@@ -518,10 +528,15 @@ __global__ void __launch_bounds__(kTileThreads, MODE == 3 ? 2 : 4) tile_kernel(c
                     }
                     for (uint32_t q = e0; q < e1; ++q) {
                       const int e = __ldg(G.inc_edge + q);
+                      const int2 oth = __ldg(G.inc_oth + q);
                       uint32_t neg = 0;
-                      for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
-                        const int mm = __ldg(G.hmem + m);
-                        if (mm != j) neg ^= ~(sw[mm] >> lane) & 1u;
+                      if (oth.x >= 0) {
+                        neg = (~(sw[oth.x] >> lane) & 1u) ^ (~(sw[oth.y] >> lane) & 1u);
+                      } else {
+                        for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
+                          const int mm = __ldg(G.hmem + m);
+                          if (mm != j) neg ^= ~(sw[mm] >> lane) & 1u;
+                        }
                       }
                       const double w = (double)__ldg(hJ + e);
                       acc = __dadd_rn(acc, neg ? -w : w);
