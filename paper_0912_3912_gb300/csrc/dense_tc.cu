@@ -23,13 +23,13 @@
 // BF16 +/-1 and store it to tensor memory (tcgen05.st), so that only the
 // coupling tiles pass through shared memory (TMA loads, 128-byte swizzled
 // K-major) and the MMAs read one shared-memory operand instead of two.
-// Thread 0 of each CTA issues the loads and the MMAs through a 4-stage mbarrier
+// Thread 0 of each CTA issues the loads and the MMAs through a 3-stage mbarrier
 // pipeline.  The deciding warps read and write their replicas' bits of a block
-// in the owning CTA's shared memory (distributed shared memory).  A last pass without decisions exports the full
-// field vectors of the replicas still descending, which dense_push.cu continues
-// one replica at a time: the first sweeps flip most spins (a GEMM per block is
-// then cheap per flip), the later ones few, and their number varies widely
-// between replicas.  Every mbarrier wait is bounded; a CTA whose wait gives up
+// in the owning CTA's shared memory (distributed shared memory).  A last pass
+// without decisions exports the full field vectors of the replicas still
+// descending, which dense_push.cu continues one replica at a time: the first
+// sweeps flip most spins (a GEMM per block is then cheap per flip), the later
+// ones few, and their number varies widely between replicas.  Every mbarrier wait is bounded; a CTA whose wait gives up
 // records ISING_ERR_TIMEOUT, keeps the cluster's barrier sequence and skips its
 // remaining work, and the cluster ends together at the next sweep.
 #include <cuda_bf16.h>
