@@ -1,7 +1,7 @@
 // sweep.cu — large instances (too big for one CTA's shared memory): every
 // colour class is one launch over the whole GPU; a sweep is the sequence of
 // class launches plus a one-block end-of-sweep launch, with the round-end
-// kernels (energy pass, restarts) after every second sweep; chunks of sweeps
+// kernels (energy pass, restarts) after every fourth sweep; chunks of sweeps
 // are captured once into a CUDA graph (cached) and replayed until every replica
 // is done, the host polling a done flag one chunk behind.
 //
