@@ -393,3 +393,26 @@ def test_greedy_colouring():
     bad = col.copy()
     bad[ch.col[0]] = bad[0]
     assert not oracle.colouring_valid(ch, bad)
+
+
+@pytest.mark.parametrize("seed,scale", [(3, 1), (11, 1), (29, 4096)])
+def test_fp32_incremental_fields_exact_on_integer_couplings(seed, scale):
+    """The FP32 path's incremental field updates (every flip adds +/-2 J to the
+    neighbours' stored fields and hyper-edge terms, refreshed only at the start
+    of a descent) against the exact integer path: with integer couplings and
+    fields, scaled so that every sum stays below 2^24, FP32 arithmetic is exact,
+    so both must take the same decisions move for move - same spins, energies,
+    minima and work counters.  A dropped term, a wrong sign or a wrong index in
+    the FP32 update would show here."""
+    gi = W.random_graph(120, 4.0, seed, dtype="i8", n_hyper=12, hyper_order=(2, 3, 4))
+    gf = W.Instance(n=gi.n, row_ptr=gi.row_ptr, col=gi.col, J=(gi.J.astype(np.float32) * scale),
+                    h=None if gi.h is None else gi.h.astype(np.float32) * scale,
+                    hyper_ptr=gi.hyper_ptr, hyper_members=gi.hyper_members,
+                    hyper_J=None if gi.hyper_J is None else gi.hyper_J.astype(np.float32) * scale,
+                    dtype="f32")
+    a = oracle.descent(gi, 5 + seed, 0, 16, max_sweeps=300, restarts=3, mode=oracle.MODE_INT)
+    b = oracle.descent(gf, 5 + seed, 0, 16, max_sweeps=300, restarts=3, refresh_every=0,
+                       mode=oracle.MODE_F32)
+    assert np.array_equal(a[0], b[0])
+    assert np.array_equal(a[2], b[2]) and a[3] == b[3]
+    assert np.array_equal(a[1] * scale, b[1])
