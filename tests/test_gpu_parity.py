@@ -328,6 +328,63 @@ def test_dense_sk_tcgen05_kernel(n, R):
     h.close()
 
 
+def _dense_eighths(n, seed):
+    """A dense instance whose couplings and fields are multiples of 1/8 with
+    numerators in [-8, 8] (couplings) and [-4, 4] (fields): BF16 holds every
+    such coupling exactly (its lo part is zero), and every FP32 sum of such
+    terms that a field of n <= 16384 spins forms is exact, so the dense path's
+    fields, decisions and FP64 energies carry no rounding at all."""
+    rng = np.random.default_rng(seed)
+    upper = np.triu(rng.integers(-8, 9, size=(n, n)), 1)
+    Jd = ((upper + upper.T) / 8.0).astype(np.float32)
+    h = (rng.integers(-4, 5, size=n) / 8.0).astype(np.float32)
+    return W.Instance(n=n, row_ptr=None, col=None, J=None, J_dense=Jd, h=h, dtype="f32",
+                      meta={"kind": "dense-eighths"})
+
+
+_EIGHTHS_ORACLE = {}
+
+
+@pytest.mark.parametrize("n,R,restarts,variant,ts", [
+    (256, 128, 3, isg.DENSE_OWN, 0),
+    (384, 130, 3, isg.DENSE_OWN, 0),
+    (384, 130, 3, isg.DENSE_OWN, -1),
+    (384, 130, 3, isg.DENSE_OWN, 1000),
+    (384, 130, 3, isg.DENSE_LIBRARY, 0),
+    (768, 96, 2, isg.DENSE_OWN, 0),
+    (5000, 4, 1, isg.DENSE_OWN, 0),
+])
+def test_dense_exact_fields_match_sequential_oracle_per_replica(n, R, restarts, variant, ts):
+    """With fields that carry no rounding, every replica's search on the dense
+    path is the oracle's sequential (index-order, Sec. IV) descent with
+    restarts from the same Philox starts, move for move: spins, FP64
+    energies, minima counts and the work counters all equal, for the
+    tensor-core sweeps, the per-replica continuation, both mixed, the
+    library-GEMM comparator, a zero-padded size, a partial 128-replica
+    cluster, and a size above 4096."""
+    inst = _dense_eighths(n, 300 + n)
+    key = (n, R, restarts)
+    if key not in _EIGHTHS_ORACLE:
+        _EIGHTHS_ORACLE[key] = oracle.descent(oracle.OracleInstance(inst), 23, 0, R, max_sweeps=500,
+                                              restarts=restarts, schedule=oracle.SCHED_SEQUENTIAL,
+                                              mode=oracle.MODE_F64)
+    so, Eo, mo, sto = _EIGHTHS_ORACLE[key]
+    h = isg.Handle([inst])
+    res = h.local_search([23], R, max_sweeps=500, restarts=restarts, kernel=isg.KERNEL_DENSE_TC,
+                         dense_variant=variant, dense_tensor_sweeps=ts)
+    torch.cuda.synchronize()
+    sp = res.spins.view(R, n).cpu().numpy()
+    E = res.energy.view(R).cpu().numpy()
+    m = res.minima.view(R).cpu().numpy()
+    st = dict(res.stats)
+    h.close()
+    same = np.all(sp == so, axis=1)
+    assert same.all(), f"replicas {np.nonzero(~same)[0][:8]} differ from the sequential descent"
+    assert np.array_equal(E, Eo)
+    assert np.array_equal(m, mo)
+    assert {k: st[k] for k in sto} == sto
+
+
 def _dense_checks(inst, res, R, tol=1e-4):
     sp = res.spins.view(R, inst.n).cpu().numpy().copy()
     E = res.energy.view(R).cpu().numpy().copy()
