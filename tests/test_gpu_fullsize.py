@@ -132,6 +132,40 @@ def test_fullsize_dense_sk_4096():
     h.close()
 
 
+def test_fullsize_dense_exact_fields_per_replica():
+    """The dense launch configuration at full size (4096 spins, 4096 replicas,
+    the benchmark's search parameters, seed and planner) on an instance whose
+    couplings and fields are multiples of 1/8, so that no field carries a
+    rounding: 32 replicas, one in each tensor-core cluster of 128 at a varying
+    lane, each equal to the oracle's sequential FP64 descent from the same
+    Philox start move for move (spins, energy, minima count)."""
+    _, R, kw, _ = bench.make_workload("c4")
+    seed = bench.seeds_for("c4", 1, 0)[0]
+    inst = W.sk_eighths(4096, 4096)
+    h = isg.Handle([inst])
+    assert h.plan_kernel(R) == isg.KERNEL_DENSE_TC
+    res = h.local_search([seed], R, kernel=isg.KERNEL_AUTO, **kw)
+    torch.cuda.synchronize()
+    sp = h.spins_of(res.spins, 0, R).cpu().numpy()
+    E = res.energy[0].cpu().numpy()
+    m = res.minima[0].cpu().numpy()
+    assert res.stats["descents"] == R
+    h.close()
+    oi = oracle.OracleInstance(inst)
+    pick = [128 * k + (37 * k + 5) % 128 for k in range(R // 128)]
+    kw_o = dict(kw, mode=oracle.MODE_F64)
+
+    def one(r):
+        s, Eo, mo, _ = oracle.descent(oi, seed, 0, 1, first_replica=r, **kw_o)
+        return r, s[0], Eo[0], mo[0]
+
+    with ThreadPoolExecutor(max_workers=16) as ex:
+        out = list(ex.map(one, pick))
+    for r, s, Eo, mo in out:
+        assert np.array_equal(sp[r], s), f"replica {r} differs from the sequential descent"
+        assert E[r] == Eo and m[r] == mo, (r, E[r], Eo, m[r], mo)
+
+
 @pytest.mark.parametrize("name,exact,tol", [("c5", False, 1e-4), ("c5i", True, 0.0)])
 def test_fullsize_lattice_100cubed(name, exact, tol):
     """Four of the 16 replicas (first, two middle, last lane of the group)

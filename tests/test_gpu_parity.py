@@ -328,20 +328,6 @@ def test_dense_sk_tcgen05_kernel(n, R):
     h.close()
 
 
-def _dense_eighths(n, seed):
-    """A dense instance whose couplings and fields are multiples of 1/8 with
-    numerators in [-8, 8] (couplings) and [-4, 4] (fields): BF16 holds every
-    such coupling exactly (its lo part is zero), and every FP32 sum of such
-    terms that a field of n <= 16384 spins forms is exact, so the dense path's
-    fields, decisions and FP64 energies carry no rounding at all."""
-    rng = np.random.default_rng(seed)
-    upper = np.triu(rng.integers(-8, 9, size=(n, n)), 1)
-    Jd = ((upper + upper.T) / 8.0).astype(np.float32)
-    h = (rng.integers(-4, 5, size=n) / 8.0).astype(np.float32)
-    return W.Instance(n=n, row_ptr=None, col=None, J=None, J_dense=Jd, h=h, dtype="f32",
-                      meta={"kind": "dense-eighths"})
-
-
 _EIGHTHS_ORACLE = {}
 
 
@@ -355,14 +341,16 @@ _EIGHTHS_ORACLE = {}
     (5000, 4, 1, isg.DENSE_OWN, 0),
 ])
 def test_dense_exact_fields_match_sequential_oracle_per_replica(n, R, restarts, variant, ts):
-    """With fields that carry no rounding, every replica's search on the dense
+    """With couplings and fields in multiples of 1/8 the dense path's fields
+    carry no rounding (BF16 holds each coupling exactly, every FP32 sum of
+    such terms is exact), so every replica's search on the dense
     path is the oracle's sequential (index-order, Sec. IV) descent with
     restarts from the same Philox starts, move for move: spins, FP64
     energies, minima counts and the work counters all equal, for the
     tensor-core sweeps, the per-replica continuation, both mixed, the
     library-GEMM comparator, a zero-padded size, a partial 128-replica
     cluster, and a size above 4096."""
-    inst = _dense_eighths(n, 300 + n)
+    inst = W.sk_eighths(n, 300 + n)
     key = (n, R, restarts)
     if key not in _EIGHTHS_ORACLE:
         _EIGHTHS_ORACLE[key] = oracle.descent(oracle.OracleInstance(inst), 23, 0, R, max_sweeps=500,

@@ -187,3 +187,26 @@ def test_create_checks_fp64_instances(isg):
     hJ[1] = np.nan
     d, keep = _desc(isg, base, hyper_J=hJ)
     assert _create_code(isg, d) == 1
+
+
+def test_sk_eighths_fields_are_exact_in_bf16_and_fp32():
+    """The premise of the dense path's exact-field parity cases: the
+    generator's couplings are symmetric with a zero diagonal, round-trip
+    through BF16 unchanged, and FP32 sums of a field's terms - in index order,
+    reversed, and pairwise - equal the FP64 sums."""
+    torch = pytest.importorskip("torch")
+    n = 1024
+    inst = W.sk_eighths(n, 5)
+    J, h = inst.J_dense, inst.h
+    assert np.array_equal(J, J.T) and not np.any(np.diag(J))
+    assert np.array_equal(np.unique(J * 8), np.arange(-8, 9)) and np.array_equal(np.unique(h * 8), np.arange(-4, 5))
+    assert np.array_equal(torch.from_numpy(J).to(torch.bfloat16).float().numpy(), J)
+    rng = np.random.default_rng(1)
+    s = rng.choice(np.array([-1.0, 1.0], dtype=np.float32), size=(4, n))
+    terms = J[None, :, :] * s[:, None, :]  # [replica, i, j] = J_ij s_j
+    exact = terms.astype(np.float64).sum(axis=2) + h
+    fwd = np.cumsum(terms, axis=2, dtype=np.float32)[:, :, -1] + h
+    rev = np.cumsum(terms[:, :, ::-1], axis=2, dtype=np.float32)[:, :, -1] + h
+    pair = terms.sum(axis=2, dtype=np.float32) + h
+    for f in (fwd, rev, pair):
+        assert f.dtype == np.float32 and np.array_equal(f.astype(np.float64), exact)

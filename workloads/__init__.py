@@ -206,6 +206,19 @@ def sk(n: int, seed: int = 0) -> Instance:
                     meta={"kind": "sk"})
 
 
+def sk_eighths(n: int, seed: int = 0) -> Instance:
+    """A dense instance with couplings J_ij = k / 8, k uniform in [-8, 8]
+    (symmetric, zero diagonal), and fields h_i = m / 8, m uniform in [-4, 4]:
+    every coupling is exact in BF16, and every sum of at most 16384 such terms
+    with +/-1 spins is exact in FP32, so a search over it carries no rounding."""
+    rng = np.random.default_rng(seed)
+    upper = np.triu(rng.integers(-8, 9, size=(n, n)), 1)
+    Jd = ((upper + upper.T) / 8.0).astype(np.float32)
+    h = (rng.integers(-4, 5, size=n) / 8.0).astype(np.float32)
+    return Instance(n=n, row_ptr=None, col=None, J=None, J_dense=Jd, h=h, dtype="f32",
+                    meta={"kind": "sk-eighths"})
+
+
 def dense_to_csr(inst: Instance) -> Instance:
     """The same couplings as a CSR listing every off-diagonal pair."""
     n = inst.n
