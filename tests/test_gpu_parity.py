@@ -177,6 +177,36 @@ def test_energy_api_random_configurations():
     h.close()
 
 
+def test_energy_api_dense_instances():
+    """ising_energy on a batch of dense instances (Gaussian SK with fields, the
+    1/8-multiple instance whose energies are exact in FP64, a size that is not
+    a multiple of 256): random configurations against the oracle, and the
+    energies a dense search returns against the energy call on its spins."""
+    insts = [_sk_with_fields(300, 41), W.sk_eighths(512, 42), W.sk(1000, seed=43)]
+    R = 5
+    h = isg.Handle(insts)
+    rng = np.random.default_rng(7)
+    spins = (rng.integers(0, 2, size=R * h.total_spins) * 2 - 1).astype(np.int8)
+    E = h.energy(torch.from_numpy(spins).cuda(), R).cpu().numpy()
+    off = 0
+    for b, inst in enumerate(insts):
+        blk = spins[off: off + R * inst.n].reshape(R, inst.n)
+        off += R * inst.n
+        ref = oracle.energies(inst, blk)
+        if b == 1:
+            assert np.array_equal(E[b], ref)
+        else:
+            np.testing.assert_allclose(E[b], ref, rtol=1e-12, atol=1e-9)
+    res = h.local_search([3, 4, 5], 64, max_sweeps=300, restarts=1, kernel=isg.KERNEL_DENSE_TC)
+    E_api = h.energy(res.spins, 64).cpu().numpy()
+    torch.cuda.synchronize()
+    # the search's energies quantise J to 32-bit fixed point (at most pairs x max|J| x 2^-31
+    # from the definition); the 1/8-multiple couplings are exact in it
+    np.testing.assert_allclose(res.energy.cpu().numpy(), E_api, rtol=1e-7, atol=1e-9)
+    assert np.array_equal(res.energy[1].cpu().numpy(), E_api[1])
+    h.close()
+
+
 def test_msc_rejected_for_float_and_large_fields():
     inst = W.chimera(2, seed=1)
     h = isg.Handle([inst])
@@ -462,6 +492,39 @@ def test_dense_tc_sizes_above_4096(n):
     assert st["minima"] == R and st["descents"] == R and np.all(m == 1)
     assert st["flip_evals"] == st["sweeps"] * n
     h.close()
+
+
+def test_dense_maximum_size_exact_per_replica():
+    """The dense family's largest instance, 16384 spins (spin bits in global
+    memory, 512-thread continuation, one partial 128-replica cluster), on the
+    1/8-multiple couplings: both replicas equal the oracle's sequential FP64
+    descent from the same starts move for move, and the returned energies are
+    the oracle's energies of the returned spins exactly."""
+    from concurrent.futures import ThreadPoolExecutor
+    n, R = 16384, 2
+    inst = W.sk_eighths(n, n)
+    h = isg.Handle([inst])
+    assert h.plan_kernel(R) == isg.KERNEL_DENSE_TC
+    res = h.local_search([5], R, max_sweeps=1000, restarts=1, kernel=isg.KERNEL_DENSE_TC)
+    torch.cuda.synchronize()
+    sp = res.spins.view(R, n).cpu().numpy()
+    E = res.energy.view(R).cpu().numpy()
+    m = res.minima.view(R).cpu().numpy()
+    st = dict(res.stats)
+    h.close()
+    oi = oracle.OracleInstance(inst)
+
+    def one(r):
+        return oracle.descent(oi, 5, 0, 1, first_replica=r, max_sweeps=1000, restarts=1,
+                              schedule=oracle.SCHED_SEQUENTIAL, mode=oracle.MODE_F64)
+
+    with ThreadPoolExecutor(max_workers=R) as ex:
+        out = list(ex.map(one, range(R)))
+    for r, (s, Eo, mo, _) in enumerate(out):
+        assert np.array_equal(sp[r], s[0]), f"replica {r} differs from the sequential descent"
+        assert E[r] == Eo[0] == oracle.energy(oi, sp[r]) and m[r] == mo[0] == 1
+    assert st["sweeps"] == sum(o[3]["sweeps"] for o in out)
+    assert st["flips"] == sum(o[3]["flips"] for o in out)
 
 
 def test_dense_batch_of_instances():

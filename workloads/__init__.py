@@ -212,9 +212,11 @@ def sk_eighths(n: int, seed: int = 0) -> Instance:
     every coupling is exact in BF16, and every sum of at most 16384 such terms
     with +/-1 spins is exact in FP32, so a search over it carries no rounding."""
     rng = np.random.default_rng(seed)
-    upper = np.triu(rng.integers(-8, 9, size=(n, n)), 1)
-    Jd = ((upper + upper.T) / 8.0).astype(np.float32)
-    h = (rng.integers(-4, 5, size=n) / 8.0).astype(np.float32)
+    upper = np.triu(rng.integers(-8, 9, size=(n, n), dtype=np.int8), 1)
+    Jd = (upper + upper.T).astype(np.float32)
+    del upper
+    Jd *= np.float32(0.125)
+    h = (rng.integers(-4, 5, size=n).astype(np.float32) * np.float32(0.125))
     return Instance(n=n, row_ptr=None, col=None, J=None, J_dense=Jd, h=h, dtype="f32",
                     meta={"kind": "sk-eighths"})
 
