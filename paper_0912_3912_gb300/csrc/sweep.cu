@@ -622,7 +622,7 @@ __global__ void __launch_bounds__(kST, (MODE == 2 && LAT) ? 8 : kVisitCtasPerSm)
                   f += ((swg[nbr(kk)] >> ln) & 1u) ? w : -w;
                 }
               }
-              for (uint32_t q = e0; q < e1; ++q) {
+              if constexpr (!LAT) for (uint32_t q = e0; q < e1; ++q) {  // no hyper-edges on lattices
                 const int e = __ldg(G.inc_edge + q);
                 uint32_t neg = 0;
                 for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
@@ -660,7 +660,7 @@ __global__ void __launch_bounds__(kST, (MODE == 2 && LAT) ? 8 : kVisitCtasPerSm)
                     const int64_t tt = xr_term(coup(kk), u);
                     acc += ((swg[nbr(kk)] >> ln) & 1u) ? tt : -tt;
                   }
-                  for (uint32_t q = e0; q < e1; ++q) {
+                  if constexpr (!LAT) for (uint32_t q = e0; q < e1; ++q) {  // no hyper-edges on lattices
                     const int e = __ldg(G.inc_edge + q);
                     const int64_t tt = xr_term(__ldg(hJf + e), u);
                     acc += hyper_neg(e) ? -tt : tt;
@@ -672,7 +672,7 @@ __global__ void __launch_bounds__(kST, (MODE == 2 && LAT) ? 8 : kVisitCtasPerSm)
                     const double w = (double)coup(kk);
                     acc = __dadd_rn(acc, ((swg[nbr(kk)] >> ln) & 1u) ? w : -w);
                   }
-                  for (uint32_t q = e0; q < e1; ++q) {
+                  if constexpr (!LAT) for (uint32_t q = e0; q < e1; ++q) {  // no hyper-edges on lattices
                     const int e = __ldg(G.inc_edge + q);
                     const double w = (double)__ldg(hJf + e);
                     acc = __dadd_rn(acc, hyper_neg(e) ? -w : w);
@@ -714,7 +714,7 @@ __global__ void __launch_bounds__(kST, (MODE == 2 && LAT) ? 8 : kVisitCtasPerSm)
                       dirty = true;
                     }
                   }
-                  for (uint32_t q = e0; q < e1; ++q) {
+                  if constexpr (!LAT) for (uint32_t q = e0; q < e1; ++q) {  // no hyper-edges on lattices
                     const int e = __ldg(G.inc_edge + q);
                     uint32_t neg = 0, par = 0;
                     for (uint32_t m = __ldg(G.hptr + e), me = __ldg(G.hptr + e + 1); m < me; ++m) {
