@@ -416,3 +416,50 @@ def test_fp32_incremental_fields_exact_on_integer_couplings(seed, scale):
     assert np.array_equal(a[0], b[0])
     assert np.array_equal(a[2], b[2]) and a[3] == b[3]
     assert np.array_equal(a[1] * scale, b[1])
+
+
+@pytest.mark.parametrize("n,seed", [(24, 3), (37, 8)])
+def test_sequential_descent_on_dense_instance_equals_plain_loop(n, seed):
+    """The sequential (index-order) schedule on a dense instance, as the dense
+    GPU path runs it, restated as a plain loop (Sec. IV): each restart starts
+    from the pinned Philox start, visits spins 0..n-1 and flips a spin whose
+    field points against it, until a sweep flips nothing; the best energy
+    over the converged restarts is returned.  Couplings and fields are
+    multiples of 1/8, so FP64 fields and energies are exact and the two must
+    agree on spins, energies, minima counts and every work counter."""
+    inst = W.sk_eighths(n, seed)
+    J = inst.J_dense.astype(np.float64)
+    h = inst.h.astype(np.float64)
+    R, K, cap = 5, 3, 100
+    so, Eo, mo, sto = oracle.descent(inst, 77, 0, R, max_sweeps=cap, restarts=K,
+                                     schedule=oracle.SCHED_SEQUENTIAL, mode=oracle.MODE_F64)
+    tot = dict(flip_evals=0, flips=0, minima=0, descents=0, sweeps=0)
+    for r in range(R):
+        best, bestE, minima, last = None, None, 0, None
+        for k in range(K):
+            s = oracle.random_start(n, 77, 0, r, k).astype(np.float64)
+            tot["descents"] += 1
+            converged = False
+            for _ in range(cap):
+                flips = 0
+                for i in range(n):
+                    f = J[i] @ s + h[i]
+                    if s[i] * f < 0:
+                        s[i] = -s[i]
+                        flips += 1
+                tot["sweeps"] += 1
+                tot["flip_evals"] += n
+                tot["flips"] += flips
+                if flips == 0:
+                    converged = True
+                    break
+            E = -(0.5 * s @ J @ s + h @ s)
+            last = (s.copy(), E)
+            if converged:
+                minima += 1
+                tot["minima"] += 1
+                if bestE is None or E < bestE:
+                    best, bestE = s.copy(), E
+        sr, Er = (best, bestE) if minima else last
+        assert np.array_equal(so[r], sr.astype(np.int8)) and Eo[r] == Er and mo[r] == minima
+    assert sto == tot
